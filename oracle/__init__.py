@@ -1,0 +1,185 @@
+"""FP64 CPU oracle of the pseudospectral Navier-Stokes hot path (Sec. 2,
+Eqs. 1-2), loaded through ctypes from ``ns_oracle.c``.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE: only the test suite, the smoke check
+of the package entry file and the benchmark's CPU-baseline / reference leg may
+import this module.  The CUDA path never imports, links or executes it, and it
+never imports the CUDA path.  It shares nothing with the CUDA path; inputs
+reach both sides from ``paper_1003_4322_gb300.inputs`` as plain arrays.
+
+Arrays use the half layout ``[3][N][N][N//2+1]`` complex128 for spectral
+vector fields (normalised coefficients, u(x) = sum_k a(k) e^{ik.x}) and
+``[ncomp][N][N][N]`` float64 for fields on the grid.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ns_oracle.c")
+_SO = os.path.join(_HERE, "libns_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP loops over lines/modes)."""
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nu", ctypes.c_double),
+                ("dt", ctypes.c_double), ("force_amp", ctypes.c_double),
+                ("force_k", ctypes.c_int), ("dealias", ctypes.c_int)]
+
+
+@dataclass
+class Params:
+    n: int
+    nu: float = 0.0
+    dt: float = 0.0
+    force_amp: float = 0.0
+    force_k: int = 0
+    dealias: int = 0
+
+    def c(self) -> _Params:
+        return _Params(self.n, self.nu, self.dt, self.force_amp,
+                       self.force_k, self.dealias)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        L.or_fft3_r2c.argtypes = [ctypes.c_int, ctypes.c_int, P, P]
+        L.or_fft3_c2r.argtypes = [ctypes.c_int, ctypes.c_int, P, P]
+        L.or_project.argtypes = [ctypes.c_int, ctypes.c_int, P]
+        L.or_curl.argtypes = [ctypes.c_int, P, P]
+        L.or_forcing.argtypes = [ctypes.POINTER(_Params), P]
+        L.or_nonlinear.argtypes = [ctypes.POINTER(_Params), P, P]
+        L.or_step.argtypes = [ctypes.POINTER(_Params), P, ctypes.c_int]
+        L.or_nbins.argtypes = [ctypes.c_int]
+        L.or_diagnostics.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with status {rc}")
+
+
+def set_threads(nthreads: int) -> int:
+    """Set the OpenMP thread count; returns the count in effect."""
+    return lib().or_set_threads(int(nthreads))
+
+
+def fft3_r2c(u: np.ndarray) -> np.ndarray:
+    """Unnormalised forward r2c of real fields [ncomp][N][N][N] (or [N][N][N])."""
+    squeeze = u.ndim == 3
+    u = np.ascontiguousarray(u.reshape((1,) + u.shape) if squeeze else u,
+                             dtype=np.float64)
+    nc, n = u.shape[0], u.shape[1]
+    out = np.empty((nc, n, n, n // 2 + 1), dtype=np.complex128)
+    _check(lib().or_fft3_r2c(n, nc, _ptr(u), _ptr(out)), "r2c")
+    return out[0] if squeeze else out
+
+
+def fft3_c2r(a: np.ndarray) -> np.ndarray:
+    """Unnormalised inverse c2r of half-layout arrays [ncomp][N][N][N/2+1]."""
+    squeeze = a.ndim == 3
+    a = np.ascontiguousarray(a.reshape((1,) + a.shape) if squeeze else a,
+                             dtype=np.complex128)
+    nc, n = a.shape[0], a.shape[1]
+    out = np.empty((nc, n, n, n), dtype=np.float64)
+    _check(lib().or_fft3_c2r(n, nc, _ptr(a), _ptr(out)), "c2r")
+    return out[0] if squeeze else out
+
+
+def project(a: np.ndarray, dealias: int = 0) -> np.ndarray:
+    """Pi then P(k) v = v - k (k.v)/|k|^2 of a half-layout vector field."""
+    v = np.array(a, dtype=np.complex128, order="C", copy=True)
+    _check(lib().or_project(v.shape[1], dealias, _ptr(v)), "project")
+    return v
+
+
+def curl(a: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    w = np.empty_like(a)
+    _check(lib().or_curl(a.shape[1], _ptr(a), _ptr(w)), "curl")
+    return w
+
+
+def forcing(p: Params) -> np.ndarray:
+    fh = np.empty((3, p.n, p.n, p.n // 2 + 1), dtype=np.complex128)
+    cp = p.c()
+    _check(lib().or_forcing(ctypes.byref(cp), _ptr(fh)), "forcing")
+    return fh
+
+
+def nonlinear(a: np.ndarray, p: Params) -> np.ndarray:
+    """N(a) = P Pi FFT(u x w)/N^3 + f_hat."""
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    out = np.empty_like(a)
+    cp = p.c()
+    _check(lib().or_nonlinear(ctypes.byref(cp), _ptr(a), _ptr(out)), "nonlinear")
+    return out
+
+
+def step(a: np.ndarray, p: Params, nsteps: int) -> np.ndarray:
+    """nsteps integrating-factor RK2 steps; returns the new state (a copy)."""
+    v = np.array(a, dtype=np.complex128, order="C", copy=True)
+    cp = p.c()
+    _check(lib().or_step(ctypes.byref(cp), _ptr(v), int(nsteps)), "step")
+    return v
+
+
+def nbins(n: int) -> int:
+    return lib().or_nbins(n)
+
+
+def diagnostics(a: np.ndarray):
+    """(E, Omega, E(K)) with K = round-half-up(|k|), K = 0..ceil(sqrt3 N/2)."""
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    n = a.shape[1]
+    nb = nbins(n)
+    spec = np.empty(nb, dtype=np.float64)
+    e = ctypes.c_double()
+    om = ctypes.c_double()
+    _check(lib().or_diagnostics(n, _ptr(a), ctypes.byref(e), ctypes.byref(om),
+                                _ptr(spec), nb), "diagnostics")
+    return e.value, om.value, spec
+
+
+def rel_l2(test: np.ndarray, ref: np.ndarray) -> float:
+    """Relative L2 distance of two half-layout spectral arrays, each mode
+    weighted by its multiplicity in the full spectrum (2 for 0 < kz < N/2)."""
+    n = ref.shape[-3]
+    w = np.full(ref.shape[-1], 2.0)
+    w[0] = 1.0
+    if n % 2 == 0:
+        w[n // 2] = 1.0
+    num = np.sum(w * np.abs(test - ref) ** 2)
+    den = np.sum(w * np.abs(ref) ** 2)
+    return math.sqrt(num / den) if den > 0 else math.sqrt(num)

@@ -1,0 +1,451 @@
+/*
+ * ns_oracle.c -- plain FP64 CPU oracle of the pseudospectral Navier-Stokes
+ * hot path of Mininni, Rosenberg, Reddy and Pouquet, "A hybrid MPI-OpenMP
+ * scheme for scalable parallel pseudospectral computations for fluid
+ * turbulence" (Sec. 2, Eqs. 1-2).
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test suite, the smoke check
+ * of the package entry file and the CPU-baseline / reference leg of the
+ * benchmark may load this library.  It shares no code, header, table or
+ * helper with the CUDA path.
+ *
+ * Everything here is the definition written out, in double precision, with no
+ * blocking, fusion or reordering beyond what the definitions state:
+ *
+ *   grid        x_j = 2 pi j / N on the (2 pi)^3 periodic box (Sec. 2);
+ *   transforms  unnormalised, forward exp(-i k.x), inverse exp(+i k.x); the
+ *               r2c result is kept in the half layout [N][N][N/2+1] with the
+ *               halved index fastest (Sec. 2, Fig. 1 caption);  a(-k) =
+ *               conj(a(k)) is the symmetry that makes the half sufficient
+ *               (the printed relation carries a spurious minus sign; this is
+ *               its reading);
+ *   state       a(k) = FFT(u)(k) / N^3, so that u(x) = sum_k a(k) e^{ik.x};
+ *   Eqs. 1-2    d_t u = u x w - grad(p + |u|^2/2) + nu lap u + f, div u = 0,
+ *               i.e. the convective form of Eq. 1 rewritten in rotational
+ *               form, the gradient being removed by the projection;
+ *   nonlinear   N(a) = P(k) Pi(k) FFT(u x w)/N^3 + f_hat, u = IFFT(Pi a),
+ *               w = IFFT(i k x Pi a)  (Sec. 2: product in physical space,
+ *               projection onto divergence-free fields, dealiasing);
+ *   Pi          cubic 2/3 rule: keep iff 3 max|k_i| < N (dealias = 0), or the
+ *               sphere 9|k|^2 < N^2 (dealias = 1);  the Nyquist index is
+ *               never kept;
+ *   P           P(k) v = v - k (k.v)/|k|^2, and N(k=0) = 0;
+ *   forcing     ABC: f = F (sin kf z + cos kf y, sin kf x + cos kf z,
+ *               sin kf y + cos kf x), constant in time, added inside N;
+ *   time step   integrating-factor Heun (RK2), E(k) = exp(-nu |k|^2 dt):
+ *               a1 = E (a + dt N(a)),  a' = E a / 2 + (a1 + dt N(a1)) / 2;
+ *   diagnostics E = 1/2 sum |a|^2, Omega = 1/2 sum |k|^2 |a|^2 over the full
+ *               spectrum (half-layout weight 2 for 0 < kz < N/2, else 1), and
+ *               the shell spectrum binned by round-half-up(|k|) (the
+ *               reductions for global quantities and spectra of Sec. 3).
+ *
+ * The paper leaves the dealiasing rule, the integrator, the form of the
+ * nonlinear term and the shell binning unstated; the choices above are the
+ * readings this oracle fixes.
+ *
+ * OpenMP pragmas parallelise the loops over independent lines and modes only
+ * (the loop-level threading of Sec. 3); results do not depend on the thread
+ * count.  Diagnostic sums run serially in a fixed order.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_OOM = 3 };
+
+/* Same field list as the run parameters of the boundary (problem statement
+ * of Sec. 2: N, nu, dt, forcing, dealiasing rule). */
+typedef struct {
+    int n;
+    double nu, dt;
+    double force_amp;
+    int force_k;
+    int dealias;
+} or_params;
+
+static const double OR_TWO_PI = 6.283185307179586476925286766559;
+
+int or_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* 1D discrete Fourier transform                                       */
+/* ------------------------------------------------------------------ */
+
+static int smallest_factor(int n)
+{
+    for (int r = 2; r * r <= n; r++)
+        if (n % r == 0) return r;
+    return n;
+}
+
+/* out[k] = sum_{j<n} in[j*is] * w[((j*k) mod n) * ws]  for k < n, where
+ * w[t*ws] = exp(sign * 2 pi i t / n).  Decimation in time on the smallest
+ * prime factor r of n (Cooley-Tukey): with m = n/r and Y_q the length-m DFT
+ * of in[q + r j],  X[k + m s] = sum_q w^{q (k + m s)} Y_q[k].  A prime length
+ * is the definition itself. */
+static void dft_line(cplx *out, const cplx *in, int n, long is,
+                     const cplx *w, int ws)
+{
+    if (n == 1) {
+        out[0] = in[0];
+        return;
+    }
+    int r = smallest_factor(n);
+    if (r == n) {
+        for (int k = 0; k < n; k++) {
+            cplx acc = 0;
+            for (int j = 0; j < n; j++)
+                acc += in[j * is] * w[(int)(((long)j * k) % n) * ws];
+            out[k] = acc;
+        }
+        return;
+    }
+    int m = n / r;
+    for (int q = 0; q < r; q++)
+        dft_line(out + q * m, in + q * is, m, is * r, w, ws * r);
+    cplx t[r], y[r];
+    for (int k = 0; k < m; k++) {
+        for (int q = 0; q < r; q++) t[q] = out[q * m + k];
+        for (int s = 0; s < r; s++) {
+            cplx acc = 0;
+            for (int q = 0; q < r; q++)
+                acc += t[q] * w[(int)(((long)q * (k + m * s)) % n) * ws];
+            y[s] = acc;
+        }
+        for (int s = 0; s < r; s++) out[k + m * s] = y[s];
+    }
+}
+
+/* Table w[t] = exp(sign * 2 pi i t / n), t < n, from libm in double. */
+static cplx *twiddles(int n, int sign)
+{
+    cplx *w = malloc(sizeof(cplx) * (size_t)n);
+    if (!w) return NULL;
+    for (int t = 0; t < n; t++) {
+        double a = OR_TWO_PI * (double)t / (double)n;
+        w[t] = cos(a) + I * (sign * sin(a));
+    }
+    return w;
+}
+
+/* Transform every line of a full complex n^3 array (x slowest, z fastest)
+ * along one axis (0 = x, 1 = y, 2 = z). */
+static int fft3_axis(cplx *a, int n, int axis, int sign)
+{
+    cplx *w = twiddles(n, sign);
+    if (!w) return OR_ERR_OOM;
+    const long nn = (long)n * n;
+    const long stride = axis == 0 ? nn : (axis == 1 ? n : 1);
+    int err = 0;
+#pragma omp parallel
+    {
+        cplx *buf = malloc(sizeof(cplx) * 2 * (size_t)n);
+        if (!buf) {
+#pragma omp atomic write
+            err = 1;
+        }
+#pragma omp for schedule(static)
+        for (long l = 0; l < nn; l++) {
+            if (!buf) continue;
+            long p = l / n, q = l % n;
+            long base = axis == 0 ? l : (axis == 1 ? p * nn + q : p * nn + q * n);
+            for (int j = 0; j < n; j++) buf[j] = a[base + j * stride];
+            dft_line(buf + n, buf, n, 1, w, 1);
+            for (int j = 0; j < n; j++) a[base + j * stride] = buf[n + j];
+        }
+        free(buf);
+    }
+    free(w);
+    return err ? OR_ERR_OOM : OR_OK;
+}
+
+static int fft3_full(cplx *a, int n, int sign)
+{
+    for (int axis = 2; axis >= 0; axis--) {
+        int e = fft3_axis(a, n, axis, sign);
+        if (e) return e;
+    }
+    return OR_OK;
+}
+
+/* Forward r2c of ncomp real n^3 fields [c][x][y][z] into the half layout
+ * [c][kx][ky][kz], kz <= n/2:  X(k) = sum_x u(x) exp(-i k.x). */
+int or_fft3_r2c(int n, int ncomp, const double *in, cplx *out)
+{
+    if (n < 2 || ncomp < 1 || !in || !out) return OR_ERR_ARG;
+    const long V = (long)n * n * n, nh = n / 2 + 1;
+    cplx *a = malloc(sizeof(cplx) * (size_t)V);
+    if (!a) return OR_ERR_OOM;
+    for (int c = 0; c < ncomp; c++) {
+        for (long i = 0; i < V; i++) a[i] = in[c * V + i];
+        int e = fft3_full(a, n, -1);
+        if (e) { free(a); return e; }
+        cplx *o = out + (long)c * n * n * nh;
+        for (long xy = 0; xy < (long)n * n; xy++)
+            for (long kz = 0; kz < nh; kz++) o[xy * nh + kz] = a[xy * n + kz];
+    }
+    free(a);
+    return OR_OK;
+}
+
+/* Inverse c2r: complete the half layout by a(kx,ky,kz) = conj(a(-kx,-ky,-kz))
+ * for kz > n/2 (the kz = 0 and n/2 planes are taken as given), apply the
+ * unnormalised inverse transform u(x) = sum_k a(k) exp(+i k.x) and keep the
+ * real part. */
+int or_fft3_c2r(int n, int ncomp, const cplx *in, double *out)
+{
+    if (n < 2 || ncomp < 1 || !in || !out) return OR_ERR_ARG;
+    const long V = (long)n * n * n, nh = n / 2 + 1;
+    cplx *a = malloc(sizeof(cplx) * (size_t)V);
+    if (!a) return OR_ERR_OOM;
+    for (int c = 0; c < ncomp; c++) {
+        const cplx *h = in + (long)c * n * n * nh;
+        for (long x = 0; x < n; x++)
+            for (long y = 0; y < n; y++)
+                for (long z = 0; z < n; z++) {
+                    cplx v;
+                    if (z < nh)
+                        v = h[(x * n + y) * nh + z];
+                    else
+                        v = conj(h[(((n - x) % n) * n + (n - y) % n) * nh + (n - z)]);
+                    a[(x * n + y) * n + z] = v;
+                }
+        int e = fft3_full(a, n, +1);
+        if (e) { free(a); return e; }
+        for (long i = 0; i < V; i++) out[c * V + i] = creal(a[i]);
+    }
+    free(a);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Spectral operators                                                  */
+/* ------------------------------------------------------------------ */
+
+/* Signed wavenumber of full index i (index n/2 maps to -n/2, the Nyquist). */
+static int wavenumber(int i, int n) { return 2 * i < n ? i : i - n; }
+
+/* Dealiasing mask Pi: 1 if the mode is kept. */
+static int keep(int kx, int ky, int kz, int n, int dealias)
+{
+    int m = abs(kx);
+    if (abs(ky) > m) m = abs(ky);
+    if (abs(kz) > m) m = abs(kz);
+    if (3 * m >= n) return 0;
+    if (dealias == 1 && 9L * (kx * kx + ky * ky + kz * kz) >= (long)n * n) return 0;
+    return 1;
+}
+
+/* Apply Pi and then P(k) v = v - k (k.v)/|k|^2 to a half-layout vector field
+ * in place; the k = 0 mode is set to zero. */
+int or_project(int n, int dealias, cplx *v)
+{
+    if (n < 2 || !v) return OR_ERR_ARG;
+    const long nh = n / 2 + 1, M = (long)n * n * nh;
+#pragma omp parallel for schedule(static)
+    for (long ix = 0; ix < n; ix++) {
+        int kx = wavenumber((int)ix, n);
+        for (long iy = 0; iy < n; iy++) {
+            int ky = wavenumber((int)iy, n);
+            for (long kz = 0; kz < nh; kz++) {
+                long m = (ix * n + iy) * nh + kz;
+                double k2 = (double)kx * kx + (double)ky * ky + (double)kz * kz;
+                if (!keep(kx, ky, (int)kz, n, dealias) || k2 == 0.0) {
+                    v[m] = v[M + m] = v[2 * M + m] = 0;
+                    continue;
+                }
+                cplx kv = kx * v[m] + ky * v[M + m] + (double)kz * v[2 * M + m];
+                v[m] -= kx * kv / k2;
+                v[M + m] -= ky * kv / k2;
+                v[2 * M + m] -= (double)kz * kv / k2;
+            }
+        }
+    }
+    return OR_OK;
+}
+
+/* Apply Pi alone (zero every mode that is not kept). */
+static void apply_mask(int n, int dealias, int ncomp, cplx *v)
+{
+    const long nh = n / 2 + 1, M = (long)n * n * nh;
+    for (long ix = 0; ix < n; ix++)
+        for (long iy = 0; iy < n; iy++)
+            for (long kz = 0; kz < nh; kz++)
+                if (!keep(wavenumber((int)ix, n), wavenumber((int)iy, n), (int)kz, n, dealias))
+                    for (int c = 0; c < ncomp; c++) v[c * M + (ix * n + iy) * nh + kz] = 0;
+}
+
+/* Vorticity coefficients w = i k x a of a half-layout vector field. */
+int or_curl(int n, const cplx *a, cplx *w)
+{
+    if (n < 2 || !a || !w) return OR_ERR_ARG;
+    const long nh = n / 2 + 1, M = (long)n * n * nh;
+#pragma omp parallel for schedule(static)
+    for (long ix = 0; ix < n; ix++) {
+        double kx = wavenumber((int)ix, n);
+        for (long iy = 0; iy < n; iy++) {
+            double ky = wavenumber((int)iy, n);
+            for (long kz = 0; kz < nh; kz++) {
+                long m = (ix * n + iy) * nh + kz;
+                cplx ax = a[m], ay = a[M + m], az = a[2 * M + m];
+                w[m] = I * (ky * az - (double)kz * ay);
+                w[M + m] = I * ((double)kz * ax - kx * az);
+                w[2 * M + m] = I * (kx * ay - ky * ax);
+            }
+        }
+    }
+    return OR_OK;
+}
+
+/* Coefficients of the ABC forcing, f_hat = FFT(f)/N^3 restricted to Pi,
+ * with f sampled on the grid from its definition. */
+int or_forcing(const or_params *p, cplx *fh)
+{
+    if (!p || !fh || p->n < 2) return OR_ERR_ARG;
+    const int n = p->n;
+    const long V = (long)n * n * n, nh = n / 2 + 1, M = (long)n * n * nh;
+    memset(fh, 0, sizeof(cplx) * 3 * (size_t)M);
+    if (p->force_k == 0 || p->force_amp == 0.0) return OR_OK;
+    double *f = malloc(sizeof(double) * 3 * (size_t)V);
+    if (!f) return OR_ERR_OOM;
+    const double F = p->force_amp, kf = p->force_k;
+    for (long ix = 0; ix < n; ix++)
+        for (long iy = 0; iy < n; iy++)
+            for (long iz = 0; iz < n; iz++) {
+                double x = OR_TWO_PI * ix / n, y = OR_TWO_PI * iy / n, z = OR_TWO_PI * iz / n;
+                long i = (ix * n + iy) * n + iz;
+                f[i] = F * (sin(kf * z) + cos(kf * y));
+                f[V + i] = F * (sin(kf * x) + cos(kf * z));
+                f[2 * V + i] = F * (sin(kf * y) + cos(kf * x));
+            }
+    int e = or_fft3_r2c(n, 3, f, fh);
+    free(f);
+    if (e) return e;
+    for (long i = 0; i < 3 * M; i++) fh[i] /= (double)V;
+    apply_mask(n, p->dealias, 3, fh);
+    return OR_OK;
+}
+
+/* Nonlinear term N(a) = P Pi FFT(u x w)/N^3 + f_hat (Sec. 2, Eqs. 1-2). */
+int or_nonlinear(const or_params *p, const cplx *a_in, cplx *out)
+{
+    if (!p || !a_in || !out || p->n < 2) return OR_ERR_ARG;
+    const int n = p->n;
+    const long V = (long)n * n * n, nh = n / 2 + 1, M = (long)n * n * nh;
+    int e = OR_ERR_OOM;
+    cplx *a = malloc(sizeof(cplx) * 3 * (size_t)M);
+    cplx *wh = malloc(sizeof(cplx) * 3 * (size_t)M);
+    cplx *fh = malloc(sizeof(cplx) * 3 * (size_t)M);
+    double *u = malloc(sizeof(double) * 3 * (size_t)V);
+    double *w = malloc(sizeof(double) * 3 * (size_t)V);
+    double *c = malloc(sizeof(double) * 3 * (size_t)V);
+    if (!a || !wh || !fh || !u || !w || !c) goto done;
+
+    memcpy(a, a_in, sizeof(cplx) * 3 * (size_t)M);
+    apply_mask(n, p->dealias, 3, a);                 /* Galerkin truncation */
+    if ((e = or_curl(n, a, wh))) goto done;          /* w_hat = i k x a */
+    if ((e = or_fft3_c2r(n, 3, a, u))) goto done;    /* u on the grid */
+    if ((e = or_fft3_c2r(n, 3, wh, w))) goto done;   /* w on the grid */
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < V; i++) {                   /* u x w, pointwise */
+        c[i] = u[V + i] * w[2 * V + i] - u[2 * V + i] * w[V + i];
+        c[V + i] = u[2 * V + i] * w[i] - u[i] * w[2 * V + i];
+        c[2 * V + i] = u[i] * w[V + i] - u[V + i] * w[i];
+    }
+    if ((e = or_fft3_r2c(n, 3, c, out))) goto done;
+    for (long i = 0; i < 3 * M; i++) out[i] /= (double)V;
+    if ((e = or_project(n, p->dealias, out))) goto done;   /* Pi, then P */
+    if ((e = or_forcing(p, fh))) goto done;
+    for (long i = 0; i < 3 * M; i++) out[i] += fh[i];
+    e = OR_OK;
+done:
+    free(a); free(wh); free(fh); free(u); free(w); free(c);
+    return e;
+}
+
+/* nsteps integrating-factor RK2 (Heun) steps of the state a, in place.
+ * The state is first restricted to Pi (the Galerkin space). */
+int or_step(const or_params *p, cplx *a, int nsteps)
+{
+    if (!p || !a || p->n < 2 || nsteps < 0) return OR_ERR_ARG;
+    const int n = p->n;
+    const long nh = n / 2 + 1, M = (long)n * n * nh;
+    int e = OR_ERR_OOM;
+    double *E = malloc(sizeof(double) * (size_t)M);
+    cplx *N0 = malloc(sizeof(cplx) * 3 * (size_t)M);
+    cplx *a1 = malloc(sizeof(cplx) * 3 * (size_t)M);
+    if (!E || !N0 || !a1) goto done;
+    for (long ix = 0; ix < n; ix++) {
+        double kx = wavenumber((int)ix, n);
+        for (long iy = 0; iy < n; iy++) {
+            double ky = wavenumber((int)iy, n);
+            for (long kz = 0; kz < nh; kz++)
+                E[(ix * n + iy) * nh + kz] =
+                    exp(-p->nu * (kx * kx + ky * ky + (double)kz * kz) * p->dt);
+        }
+    }
+    apply_mask(n, p->dealias, 3, a);
+    for (int s = 0; s < nsteps; s++) {
+        if ((e = or_nonlinear(p, a, N0))) goto done;
+        for (long i = 0; i < 3 * M; i++) a1[i] = E[i % M] * (a[i] + p->dt * N0[i]);
+        if ((e = or_nonlinear(p, a1, N0))) goto done;
+        for (long i = 0; i < 3 * M; i++)
+            a[i] = 0.5 * E[i % M] * a[i] + 0.5 * (a1[i] + p->dt * N0[i]);
+    }
+    e = OR_OK;
+done:
+    free(E); free(N0); free(a1);
+    return e;
+}
+
+/* Number of shells: K = 0 .. ceil(sqrt(3) n / 2). */
+int or_nbins(int n) { return (int)ceil(sqrt(3.0) * n / 2.0) + 1; }
+
+/* Energy, enstrophy and shell spectrum of a half-layout vector field. */
+int or_diagnostics(int n, const cplx *a, double *energy, double *enstrophy,
+                   double *spec, int nbins)
+{
+    if (n < 2 || !a) return OR_ERR_ARG;
+    const long nh = n / 2 + 1, M = (long)n * n * nh;
+    double e = 0.0, om = 0.0;
+    if (spec) memset(spec, 0, sizeof(double) * (size_t)nbins);
+    for (long ix = 0; ix < n; ix++) {
+        double kx = wavenumber((int)ix, n);
+        for (long iy = 0; iy < n; iy++) {
+            double ky = wavenumber((int)iy, n);
+            for (long kz = 0; kz < nh; kz++) {
+                long m = (ix * n + iy) * nh + kz;
+                double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
+                double k2 = kx * kx + ky * ky + (double)kz * kz;
+                double a2 = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    cplx v = a[c * M + m];
+                    a2 += creal(v) * creal(v) + cimag(v) * cimag(v);
+                }
+                double de = 0.5 * w * a2;
+                e += de;
+                om += k2 * de;
+                long K = (long)floor(sqrt(k2) + 0.5);
+                if (spec && K < nbins) spec[K] += de;
+            }
+        }
+    }
+    if (energy) *energy = e;
+    if (enstrophy) *enstrophy = om;
+    return OR_OK;
+}
