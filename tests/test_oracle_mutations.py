@@ -1,0 +1,123 @@
+"""The oracle's pins must catch plausible mistakes.  Each case below plants
+one mistake in a private copy of the oracle source (on the CPU), compiles it,
+and requires that at least one pin of a fast battery fails on it, while the
+unmodified source passes every pin."""
+import ctypes
+import math
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1003_4322_gb300 import inputs
+from tests.spectral_ref import rel_l2, triad_nonlinear
+
+SRC = open(os.path.join(os.path.dirname(oracle.__file__), "ns_oracle.c")).read()
+
+MUTATIONS = {
+    "cross product order (w x u)":
+        ("c[i] = u[V + i] * w[2 * V + i] - u[2 * V + i] * w[V + i];",
+         "c[i] = w[V + i] * u[2 * V + i] - w[2 * V + i] * u[V + i];"),
+    "curl sign":
+        ("w[m] = I * (ky * az - (double)kz * ay);", "w[m] = I * ((double)kz * ay - ky * az);"),
+    "projection sign":
+        ("v[m] -= kx * kv / k2;", "v[m] += kx * kv / k2;"),
+    "2/3 rule replaced by 1/2 rule":
+        ("if (3 * m >= n) return 0;", "if (2 * m >= n) return 0;"),
+    "missing 1/N^3 on the nonlinear term":
+        ("for (long i = 0; i < 3 * M; i++) out[i] /= (double)V;", ""),
+    "Heun second-stage weight dropped":
+        ("a[i] = 0.5 * E[i % M] * a[i] + 0.5 * (a1[i] + p->dt * N0[i]);",
+         "a[i] = 0.5 * E[i % M] * a[i] + (a1[i] + p->dt * N0[i]);"),
+    "integrating factor outside the Euler stage":
+        ("a1[i] = E[i % M] * (a[i] + p->dt * N0[i]);", "a1[i] = E[i % M] * a[i] + p->dt * N0[i];"),
+    "half viscous factor":
+        ("exp(-p->nu * (kx * kx + ky * ky + (double)kz * kz) * p->dt);",
+         "exp(-0.5 * p->nu * (kx * kx + ky * ky + (double)kz * kz) * p->dt);"),
+    "forcing sin/cos swapped":
+        ("f[i] = F * (sin(kf * z) + cos(kf * y));", "f[i] = F * (cos(kf * z) + sin(kf * y));"),
+    "twiddle sign":
+        ("w[t] = cos(a) + I * (sign * sin(a));", "w[t] = cos(a) - I * (sign * sin(a));"),
+    "Hermitian completion without conjugate":
+        ("v = conj(h[(((n - x) % n) * n + (n - y) % n) * nh + (n - z)]);",
+         "v = h[(((n - x) % n) * n + (n - y) % n) * nh + (n - z)];"),
+    "energy weight 2 on every plane":
+        ("double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;", "double w = 2.0;"),
+    "shell binning by truncation":
+        ("long K = (long)floor(sqrt(k2) + 0.5);", "long K = (long)floor(sqrt(k2));"),
+}
+
+
+def _pins():
+    """A fast battery of independent pins; returns the names that fail."""
+    failed = []
+    # FFT against numpy
+    u = inputs.random_real(12, 1, 0)[0]
+    if np.abs(oracle.fft3_r2c(u) - np.fft.rfftn(u)).max() > 1e-9:
+        failed.append("r2c")
+    a = inputs.random_hermitian_half(12, 1, 1)[0]
+    if np.abs(oracle.fft3_c2r(a) - np.fft.irfftn(a, s=(12, 12, 12), axes=(0, 1, 2)) * 12 ** 3).max() > 1e-9:
+        failed.append("c2r")
+    # nonlinear term against the triad sum
+    s = inputs.random_solenoidal_state(8, 1.0, 4.0, 0.7, seed=8)
+    if np.abs(oracle.nonlinear(s, oracle.Params(n=8)) - triad_nonlinear(s)).max() > 1e-12:
+        failed.append("triad")
+    # forcing closed form (one coefficient)
+    fh = oracle.forcing(oracle.Params(n=16, force_amp=0.5, force_k=3))
+    if abs(fh[0, 0, 0, 3] - 0.5 / 2j) > 1e-14:
+        failed.append("forcing")
+    # exact ABC decay
+    b = oracle.step(inputs.abc_state(16), oracle.Params(n=16, nu=0.01, dt=0.05), 4)
+    if abs(oracle.diagnostics(b)[0] - 1.5 * math.exp(-2 * 0.01 * 0.2)) > 1e-13:
+        failed.append("abc")
+    # second-order convergence on a nonlinear case (Richardson ratio)
+    a0 = inputs.random_solenoidal_state(8, 1.0, 3.5, 1.5, seed=21)
+    res = [oracle.step(a0, oracle.Params(n=8, nu=0.05, dt=0.2 / k), k) for k in (10, 20, 40)]
+    ratio = rel_l2(res[0], res[1]) / rel_l2(res[1], res[2])
+    if not 3.6 < ratio < 4.4:
+        failed.append("order")
+    # diagnostics: Parseval and shell of k = (3, 4, 0)
+    t = inputs.turbulence_state(16, 4, rms=0.8)
+    if abs(oracle.diagnostics(t)[0] - 1.5 * 0.64) > 1e-13:
+        failed.append("parseval")
+    c = np.zeros_like(t)
+    c[2, 3, 4, 0] = c[2, 13, 12, 0] = 0.5
+    if abs(oracle.diagnostics(c)[2][5] - 0.25) > 1e-15:
+        failed.append("shell")
+    if abs(oracle.diagnostics(inputs.taylor_green_state(8))[2][2] - 0.125) > 1e-15:
+        failed.append("shell-round")     # |k| = sqrt3 rounds to shell 2
+    return failed
+
+
+def _with_source(src: str):
+    d = tempfile.mkdtemp(prefix="oracle_mut_")
+    c = os.path.join(d, "m.c")
+    so = os.path.join(d, "m.so")
+    with open(c, "w") as f:
+        f.write(src)
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", c, "-o", so, "-lm"],
+                   check=True)
+    saved = oracle._lib
+    oracle._lib = None
+    real = oracle.build
+    oracle.build = lambda force=False: so
+    try:
+        return _pins()
+    finally:
+        oracle.build = real
+        oracle._lib = saved
+
+
+def test_unmodified_oracle_passes_battery():
+    assert _pins() == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name):
+    old, new = MUTATIONS[name]
+    assert SRC.count(old) == 1, "mutation anchor not found"
+    failed = _with_source(SRC.replace(old, new))
+    assert failed, f"no pin caught: {name}"
