@@ -1,0 +1,461 @@
+#!/usr/bin/env python3
+"""Benchmark of the pseudospectral Navier-Stokes hot path on one GB300.
+
+One "step" is one integrating-factor RK2 step (two nonlinear-term
+evaluations: 6 inverse + 3 forward 3D transforms each, the cross product,
+projection, dealiasing and update) plus the per-step FP64 energy/enstrophy
+reduction, over the whole grid.
+
+Default workload (the configuration the headline metric is quoted on):
+256^3 decaying Taylor-Green vortex, nu = 1/1600, dt = 2e-3, in the plain FP64
+form, timed over 200 RK2 steps; the FP32 form runs the same workload beside it
+and its relative L2 distance to the FP64 state is reported.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference      # the FP64 CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank advances its own replica (weak scaling,
+no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RK2 steps/s and 3D-FFT HBM GB/s, FP32 fused vs FP64 plain at stated L2 error"
+
+WORKLOADS = {
+    "tg256": dict(desc="256^3 decaying Taylor-Green vortex, nu=1/1600, dt=2e-3, plain FP64 "
+                       "(FP32 form alongside)", n=256, nu=1 / 1600, dt=2e-3, ic="tg",
+                  prec="fp64", companion="fp32"),
+    "forced512": dict(desc="512^3 forced turbulence, ABC forcing k=3 F=0.5, nu=2e-3, dt=1e-3, "
+                           "seeded k^-2 start on 1<=|k|<=4 (seed 3), FP32 (plain FP64 alongside)",
+                      n=512, nu=2e-3, dt=1e-3, force_amp=0.5, force_k=3, ic=("turb", 3),
+                      prec="fp32", companion="fp64"),
+    "forced1024": dict(desc="1024^3 forced turbulence, ABC forcing k=3 F=0.5, nu=5e-4, dt=5e-4, "
+                            "seeded k^-2 start (seed 5), FP32", n=1024, nu=5e-4, dt=5e-4,
+                       force_amp=0.5, force_k=3, ic=("turb", 5), prec="fp32", companion=None),
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+# FP64 FMA pipes: GB300 lists 1.25 TFLOP/s FP64 at its 2070 MHz maximum SM
+# clock over 152 SMs, i.e. 2 FP64 FMA (4 flop) per SM per clock.
+FP64_FLOP_PER_SM_CLK = 4.0
+N_SM = 152
+
+
+def initial_state(w):
+    from paper_1003_4322_gb300 import inputs
+    if w["ic"] == "tg":
+        return inputs.taylor_green_state(w["n"])
+    kind, seed = w["ic"]
+    return inputs.turbulence_state(w["n"], seed)
+
+
+def run_params(w):
+    return dict(n=w["n"], nu=w["nu"], dt=w["dt"], force_amp=w.get("force_amp", 0.0),
+                force_k=w.get("force_k", 0))
+
+
+# ---------------------------------------------------------------- kernel model
+
+def kernel_model(name, n, prec):
+    """Algorithmic (bytes, flops) of one launch of a kernel of the step (three
+    vector components per launch).  FFT flops use 5 n log2 n per complex
+    line of length n."""
+    es = 8 if prec == "fp64" else 4
+    nh = n // 2 + 1
+    M = n * n * nh          # half-layout modes per component
+    V = n ** 3
+    lines_strided = n * nh
+    f_line = 5 * n * math.log2(n)
+    f_zline = 5 * (n // 2) * math.log2(n // 2) + 10 * (n // 2)
+    if name in ("fft_x_inverse", "fft_y_inverse", "fft_x_forward", "fft_y_forward"):
+        return 2 * 3 * M * 2 * es, 3 * lines_strided * f_line
+    if name in ("fft_z_c2r", "fft_z_r2c"):
+        return 3 * (M * 2 * es + V * es), 3 * n * n * f_zline
+    if name == "curl":
+        return 2 * 3 * M * 2 * es, 3 * M * 6
+    if name == "cross":
+        return 9 * V * es, 9 * V
+    if name == "update":
+        return 7.5 * 3 * M * 2 * es, 3 * M * 20
+    return 0, 0
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        load = [s for s, p in zip(sm, pw)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def time_form(w, prec, a0, steps, warmup, census_steps, dist):
+    """Advance one solver through warm-up, K timed steps and a kernel census;
+    returns timing, census, final state and the energy series."""
+    import torch
+
+    from paper_1003_4322_gb300 import _native as nat
+    from paper_1003_4322_gb300.solver import Solver
+    stream = torch.cuda.current_stream()
+    s = Solver([run_params(w)], prec=prec, stream=stream)
+    s.set_state(a0)
+    s.step(warmup)
+    s.sync()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    E, O = s.series(count=steps)
+    census = nat.ns_kernel_census(s.ctx, census_steps) if census_steps > 0 else []
+    state = s.get_state()
+    return dict(solver=s, ms=ms, clocks=clk, census=census, state=state, E=E, O=O)
+
+
+def roofline_of(census, w, prec, census_steps, peaks, sm_mhz):
+    """Dominant kernel (largest share of device time in the census) against
+    HBM or the FP64 ALU roof, whichever its algorithmic model says binds."""
+    if not census:
+        return None, None
+    total = sum(t for _, _, t in census)
+    name, launches, tms = max(census, key=lambda r: r[2])
+    per_launch_ms = tms / launches
+    bytes_, flops = kernel_model(name, w["n"], prec)
+    gbs = bytes_ / (per_launch_ms * 1e-3) / 1e9
+    hbm_frac = gbs / peaks["hbm_gbs"]
+    roof = {"kernel": name, "launches_per_step": launches / census_steps,
+            "share": tms / total, "avg_launch_ms": per_launch_ms, "traffic": None}
+    if prec == "fp64":
+        peak_flops = N_SM * FP64_FLOP_PER_SM_CLK * peaks["sm_max_mhz"] * 1e6
+        tflops = flops / (per_launch_ms * 1e-3) / 1e12
+        alu_frac = tflops * 1e12 / peak_flops
+        if alu_frac >= hbm_frac:
+            roof.update(bound="alu", achieved=tflops, peak=peak_flops / 1e12, unit="TFLOP/s",
+                        frac=alu_frac, peak_source="FP64 FMA pipes x max SM clock (derived)",
+                        hbm_frac=hbm_frac)
+            return roof, total
+    roof.update(bound="hbm", achieved=gbs, peak=peaks["hbm_gbs"], unit="GB/s", frac=hbm_frac,
+                peak_source=peaks["source"])
+    return roof, total
+
+
+def fft_stage(n, prec, reps=5):
+    """Standalone ns_fft_r2c + ns_fft_c2r of 3 components: HBM GB/s by the
+    algorithmic model (each of the 3 passes reads and writes the array)."""
+    import torch
+
+    from paper_1003_4322_gb300 import _native as nat
+    rt = torch.float32 if prec == "fp32" else torch.float64
+    ct = torch.complex64 if prec == "fp32" else torch.complex128
+    g = torch.Generator(device="cuda").manual_seed(1)
+    u = torch.randn((3, n, n, n), device="cuda", dtype=rt, generator=g)
+    uh = torch.empty((3, n, n, n // 2 + 1), device="cuda", dtype=ct)
+    back = torch.empty_like(u)
+    stream = torch.cuda.current_stream()
+    ctx = nat.ns_init([dict(n=8, dt=1e-3)], nat.NS_FP32 if prec == "fp32" else nat.NS_FP64,
+                      stream)
+    try:
+        for _ in range(2):
+            nat.ns_fft_r2c(ctx, n, 3, u, uh)
+            nat.ns_fft_c2r(ctx, n, 3, uh, back)
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        evs[0].record(stream)
+        for _ in range(reps):
+            nat.ns_fft_r2c(ctx, n, 3, u, uh)
+        evs[1].record(stream)
+        for _ in range(reps):
+            nat.ns_fft_c2r(ctx, n, 3, uh, back)
+        evs[2].record(stream)
+        torch.cuda.synchronize()
+        r2c_ms = evs[0].elapsed_time(evs[1]) / reps
+        c2r_ms = evs[1].elapsed_time(evs[2]) / reps
+    finally:
+        nat.ns_destroy(ctx)
+    es = 4 if prec == "fp32" else 8
+    half = n * n * (n // 2 + 1) * 2 * es
+    real = n ** 3 * es
+    model = 3 * ((real + half) + 2 * half + 2 * half)   # z, y, x passes (read + write)
+    return {"n": n, "ncomp": 3, "prec": prec, "r2c_ms": r2c_ms, "c2r_ms": c2r_ms,
+            "r2c_gbs": model / (r2c_ms * 1e-3) / 1e9, "c2r_gbs": model / (c2r_ms * 1e-3) / 1e9,
+            "bytes_model": model}
+
+
+def e2e(w, prec, a0, steps):
+    """Through the public API with host buffers: every step uploads its input
+    state from pinned host memory (ns_set_state), advances one RK2 step
+    (ns_step) and reads its diagnostics back (ns_energy_spectrum)."""
+    import numpy as np
+    import torch
+
+    from paper_1003_4322_gb300 import _native as nat
+    from paper_1003_4322_gb300.solver import Solver
+    pinned = torch.empty(a0.shape, dtype=torch.complex128, pin_memory=True)
+    pinned.numpy()[...] = a0
+    host = pinned.numpy()
+    s = Solver([run_params(w)], prec=prec, stream=torch.cuda.current_stream())
+    try:
+        for _ in range(2):
+            s.set_state(host)
+            s.step(1)
+            s.energy_spectrum()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            s.set_state(host)
+            s.step(1)
+            E, O, spec = s.energy_spectrum()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    finally:
+        s.close()
+    return {"value": steps / dt, "unit": "steps/s", "h2d_bytes_per_step": int(a0.nbytes),
+            "d2h_bytes_per_step": int(spec.nbytes + 16), "steps": steps}
+
+
+def cpu_baseline(w, a0, budget_s=30.0):
+    """The FP64 oracle (test infrastructure, as it stands) on the host cores:
+    whole RK2 steps of the same workload until the time budget is used."""
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    p = oracle.Params(n=w["n"], nu=w["nu"], dt=w["dt"], force_amp=w.get("force_amp", 0.0),
+                      force_k=w.get("force_k", 0))
+    a = a0
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        a = oracle.step(a, p, 1)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s or steps >= 1000:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": steps / dt, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} whole RK2 step(s) of the {w['n']}^3 workload on {cores} "
+                      f"host threads ({dt:.1f} s)"}
+
+
+def ours(args, w):
+    import numpy as np
+    import torch
+
+    from paper_1003_4322_gb300 import _native as nat
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = td
+    torch.cuda.set_device(local)
+    nat.load()
+    peaks = load_peaks()
+    a0 = initial_state(w)
+    warmup = max(args.warmup, 3)
+    census_steps = min(args.steps, 3)
+
+    main = time_form(w, w["prec"], a0, args.steps, warmup, census_steps, dist)
+    ms = main["ms"]
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms * 1e-3)
+    clk = main["clocks"] or {}
+    roof, census_total = roofline_of(main["census"], w, w["prec"], census_steps, peaks,
+                                     clk.get("sm_mhz"))
+    launches_per_step = sum(l for _, l, _ in main["census"]) / census_steps if main["census"] else 0
+    main["solver"].close()
+
+    comp = None
+    if w.get("companion") and not args.no_companion:
+        c = time_form(w, w["companion"], a0, args.steps, warmup, census_steps, dist)
+        croof, _ = roofline_of(c["census"], w, w["companion"], census_steps, peaks, None)
+        from oracle import rel_l2
+        fp32, fp64 = (c["state"], main["state"]) if w["companion"] == "fp32" else \
+            (main["state"], c["state"])
+        comp = {"form": w["companion"], "value": args.steps / (c["ms"] * 1e-3),
+                "unit": "steps/s", "ms_per_step": c["ms"] / args.steps,
+                "rel_l2_fp32_vs_fp64": rel_l2(fp32, fp64),
+                "after_steps": warmup + args.steps + census_steps, "roofline": croof,
+                "kernels": [{"name": n, "launches": l, "ms": t} for n, l, t in c["census"]]}
+        c["solver"].close()
+
+    fft = fft_stage(w["n"], "fp32") if not args.no_fft else None
+    ee = e2e(w, w["prec"], a0, min(args.steps, 20))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, a0, args.cpu_budget)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    step_idx = [i for i in (49, 99, 149, 199) if i < len(main["E"])]
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if w["prec"] == "fp64" else "f32",
+        "data": "synthetic (analytic / seeded initial condition, no dataset)",
+        "config": {"workload": args.workload, "description": w["desc"], "n": w["n"],
+                   "nu": w["nu"], "dt": w["dt"], "form": "plain FP64" if w["prec"] == "fp64"
+                   else "fused FP32", "parallelism": f"replicas x{world}",
+                   "l2": "working set above 129 MB L2 (no flush needed)"},
+        "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
+        "e2e": ee, "cpu_baseline": cpu, "clocks": clk or None,
+        "kernels": [{"name": n, "launches": l, "ms": t} for n, l, t in main["census"]],
+        "series": {"at_step": [i + 1 + warmup for i in step_idx],
+                   "energy": [float(main["E"][i]) for i in step_idx],
+                   "enstrophy": [float(main["O"][i]) for i in step_idx]},
+        "companion": comp, "fft": fft,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+
+def reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    a0 = initial_state(w)
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    p = oracle.Params(n=w["n"], nu=w["nu"], dt=w["dt"], force_amp=w.get("force_amp", 0.0),
+                      force_k=w.get("force_k", 0))
+    a = a0
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < args.steps:
+        a = oracle.step(a, p, 1)
+        steps += 1
+        if time.perf_counter() - t0 > args.cpu_budget * 4:
+            break
+    dt = time.perf_counter() - t0
+    v = steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": steps, "warmup": 0,
+            "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": w["desc"], "n": w["n"]},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} of {args.steps} RK2 steps of the {w['n']}^3 "
+                                       f"workload (bounded to {args.cpu_budget * 4:.0f} s)"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="tg256", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-companion", action="store_true")
+    ap.add_argument("--no-fft", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        reference(args, w)
+    else:
+        ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

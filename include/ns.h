@@ -1,0 +1,183 @@
+/*
+ * ns.h -- C ABI of libns, the GB300 (sm_103a) hot path of the pseudospectral
+ * incompressible Navier-Stokes solver of Mininni, Rosenberg, Reddy and
+ * Pouquet, "A hybrid MPI-OpenMP scheme for scalable parallel pseudospectral
+ * computations for fluid turbulence" (Sec. 2, Eqs. 1-2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Box and grid: the (2 pi)^3 periodic box sampled on N^3 points
+ *   x_j = 2 pi j / N (Sec. 2).  Physical fields are [ncomp][N][N][N]
+ *   (C order, z fastest).
+ * Spectral fields: the r2c half layout [ncomp][N][N][N/2+1] (kx, ky, kz with
+ *   kz in [0, N/2] fastest), the C-order mirror of the (N/2+1) x N x M
+ *   arrays of Sec. 2, Fig. 1.  Full index i stands for the wavenumber
+ *   i (i < N/2) or i - N.  a(-k) = conj(a(k)) supplies the other half (the
+ *   printed relation of Sec. 2 carries a spurious minus sign; this is its
+ *   reading).  Complex numbers are interleaved (re, im).
+ * Transforms: unnormalised both ways, forward exp(-i k.x), inverse
+ *   exp(+i k.x).  The c2r direction treats the kz = 0 and kz = N/2 planes as
+ *   given and returns the real part of the inverse, so it is exact for
+ *   Hermitian-consistent input.
+ * Solver state: normalised coefficients a(k) = FFT(u)(k) / N^3, so that
+ *   u(x) = sum_k a(k) e^{ik.x}, restricted to the dealiased set Pi.
+ * Equations (Sec. 2, Eqs. 1-2, rotational form):
+ *   da/dt = -nu |k|^2 a + N(a),
+ *   N(a)  = P(k) Pi FFT(u x w)/N^3 + f_hat,  u = IFFT(a), w = IFFT(i k x a),
+ *   P(k) v = v - k (k.v)/|k|^2 (projection onto divergence-free fields),
+ *   Pi: the 2/3 rule, keep iff 3 max|k_i| < N (dealias = 0) or also
+ *   9|k|^2 < N^2 (dealias = 1); the Nyquist index is never kept.
+ *   f = F (sin kf z + cos kf y, sin kf x + cos kf z, sin kf y + cos kf x).
+ *   Time step: integrating-factor Heun (RK2), E = exp(-nu |k|^2 dt):
+ *   a1 = E (a + dt N(a)),  a_next = E a / 2 + (a1 + dt N(a1)) / 2.
+ * Supported N: 2^a 3^b with N >= 8 and N even (N <= 1024 for NS_FP32,
+ *   N <= 768 for NS_FP64); other N give NS_ERR_UNSUPPORTED_N.
+ * Precision: NS_FP64 is the plain form (unfused, unpruned, FP64
+ *   throughout).  NS_FP32 is the fused form (pruned FP32 transforms and
+ *   nonlinear term); its twiddle and integrating-factor tables are generated
+ *   in FP64 and rounded once, and its energy, enstrophy and spectrum sums
+ *   accumulate in FP64.
+ *
+ * Ownership: the caller owns every pointer it passes; the context owns its
+ *   internal device buffers and frees them in ns_destroy.  Nothing is kept
+ *   from a caller pointer after a call returns.
+ * Errors: every call returns a status; nothing is thrown across the ABI.
+ *   CUDA errors are sticky per context: once a call has returned
+ *   NS_ERR_CUDA, later calls on the context return it too.  A non-finite
+ *   energy, found by ns_sync, ns_energy_spectrum or ns_get_state, returns
+ *   NS_ERR_NONFINITE.
+ * Streams: work is queued on the stream given to ns_init (NULL = the legacy
+ *   default stream) and runs asynchronously unless a call says it syncs.
+ * Threading: one context per host thread.
+ */
+#ifndef NS_H
+#define NS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ns_ctx ns_ctx;
+
+typedef enum {
+    NS_OK = 0,
+    NS_ERR_ARG = 1,            /* invalid argument (null pointer, range) */
+    NS_ERR_CUDA = 2,           /* a CUDA runtime call or kernel failed */
+    NS_ERR_OOM = 3,            /* device or host allocation failed */
+    NS_ERR_UNSUPPORTED_N = 4,  /* N is not 2^a 3^b, even, >= 8, in range */
+    NS_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+    NS_ERR_NONFINITE = 6       /* the energy of a run is NaN or infinite */
+} ns_status;
+
+typedef enum { NS_FP64 = 0, NS_FP32 = 1 } ns_prec;
+
+/* One run of the solver (the problem statement of Sec. 2, Eqs. 1-2). */
+typedef struct {
+    int n;             /* grid points per axis */
+    double nu;         /* kinematic viscosity, >= 0 */
+    double dt;         /* time step, > 0 */
+    double force_amp;  /* ABC forcing amplitude F (0 = unforced) */
+    int force_k;       /* ABC forcing wavenumber kf (0 = unforced) */
+    int dealias;       /* 0 = cubic 2/3 rule, 1 = spherical 2/3 rule */
+} ns_run_params;
+
+/* Create a context for nruns independent runs (an ensemble when nruns > 1;
+ * runs may have different N) in precision prec, queueing work on
+ * cuda_stream (a cudaStream_t, or NULL).  Allocates every device buffer the
+ * runs need; states start at zero.  *out receives the context, or NULL on
+ * error.  Errors: NS_ERR_ARG (null pointer, nruns < 1, nu < 0, dt <= 0,
+ * dealias not 0/1, force_k < 0), NS_ERR_UNSUPPORTED_N, NS_ERR_OOM,
+ * NS_ERR_CUDA. */
+ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec,
+                  void *cuda_stream, ns_ctx **out);
+
+/* Load the state of one run from a full half-layout FP64 complex array
+ * [3][N][N][N/2+1] (host memory if on_device = 0, device memory if 1).
+ * Modes outside Pi are dropped (the Galerkin truncation of Sec. 2); the
+ * context converts to its precision and layout.  Synchronous with respect to
+ * the host buffer: it may be reused when the call returns.  Errors:
+ * NS_ERR_ARG (bad run index or null pointer), NS_ERR_CUDA. */
+ns_status ns_set_state(ns_ctx *ctx, int run, const void *uhat, int on_device);
+
+/* Store the state of one run into a full half-layout FP64 complex array
+ * [3][N][N][N/2+1] (host if on_device = 0, device if 1); modes outside Pi
+ * are written as zero.  Synchronises the context's stream.  Errors:
+ * NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_NONFINITE. */
+ns_status ns_get_state(ns_ctx *ctx, int run, void *uhat, int on_device);
+
+/* Advance every run by nsteps integrating-factor RK2 steps (Sec. 2,
+ * Eqs. 1-2), queued asynchronously; each step also records the run's energy
+ * and enstrophy (FP64) on the device.  Errors: NS_ERR_ARG (nsteps < 0),
+ * NS_ERR_CUDA. */
+ns_status ns_step(ns_ctx *ctx, int nsteps);
+
+/* Unnormalised forward r2c transform (Sec. 2, Fig. 1) of ncomp real fields
+ * [ncomp][n][n][n] at device pointer in, into the half layout
+ * [ncomp][n][n][n/2+1] at device pointer out, in the context's precision
+ * (float/double in, interleaved complex out).  in and out must not
+ * overlap.  Asynchronous on the context's stream.  Errors: NS_ERR_ARG,
+ * NS_ERR_UNSUPPORTED_N, NS_ERR_OOM (first call for a new n allocates its
+ * tables), NS_ERR_CUDA. */
+ns_status ns_fft_r2c(ns_ctx *ctx, int n, int ncomp, const void *in, void *out);
+
+/* Unnormalised inverse c2r transform of ncomp half-layout complex fields at
+ * device pointer in into real fields [ncomp][n][n][n] at device pointer out.
+ * in is not modified; the context keeps one field of complex scratch per n
+ * (allocated on the first call for that n).  Errors as ns_fft_r2c. */
+ns_status ns_fft_c2r(ns_ctx *ctx, int n, int ncomp, const void *in, void *out);
+
+/* Energy E = 1/2 sum |a|^2, enstrophy Omega = 1/2 sum |k|^2 |a|^2 (sums
+ * over the full spectrum) and the shell spectrum E(K), K = round-half-up
+ * |k|, of one run's current state, accumulated in FP64 (the reductions for
+ * global quantities and spectra of Sec. 3).  spec receives
+ * min(nbins, ns_nbins(N)) shells (spec may be NULL when nbins = 0); energy
+ * and enstrophy may be NULL.  Host outputs; synchronises the stream.
+ * Errors: NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_NONFINITE. */
+ns_status ns_energy_spectrum(ns_ctx *ctx, int run, double *spec, int nbins,
+                             double *energy, double *enstrophy);
+
+/* Number of shells of an N^3 grid: ceil(sqrt(3) N / 2) + 1. */
+int ns_nbins(int n);
+
+/* Energy and enstrophy recorded by the last `count` steps of one run
+ * (oldest first, at most the ring size ns_series_capacity()); fewer are
+ * written if fewer steps ran.  *written receives the count.  Host outputs;
+ * synchronises the stream.  Errors: NS_ERR_ARG, NS_ERR_CUDA. */
+ns_status ns_series(ns_ctx *ctx, int run, int count, double *energy,
+                    double *enstrophy, int *written);
+int ns_series_capacity(void);
+
+/* Per-kernel timing (the profiling of Sec. 3's benchmarks, which time only
+ * the main time-advance loop): runs nsteps steps of every run WITHOUT the
+ * CUDA graph, bracketing each kernel launch with a pair of CUDA events on the
+ * context's stream, and reports per kernel name the launch count and the
+ * summed device time.  The state advances by nsteps steps.  out receives up
+ * to max entries; *count receives the number of distinct kernels.
+ * Synchronises the stream.  Errors: NS_ERR_ARG, NS_ERR_CUDA. */
+typedef struct {
+    char name[48];
+    int launches;
+    double total_ms;
+} ns_kernel_time;
+ns_status ns_kernel_census(ns_ctx *ctx, int nsteps, ns_kernel_time *out, int max, int *count);
+
+/* Wait for all queued work and report any sticky or device-side error. */
+ns_status ns_sync(ns_ctx *ctx);
+
+/* Detail of the last CUDA failure the context recorded (CUDA error name,
+ * message and source location), or "" if none.  Owned by the context. */
+const char *ns_last_error(ns_ctx *ctx);
+
+/* Static description of a status code. */
+const char *ns_status_str(ns_status s);
+
+/* Free the context and all its device buffers (NULL is accepted). */
+void ns_destroy(ns_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NS_H */

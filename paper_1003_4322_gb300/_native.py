@@ -1,0 +1,195 @@
+"""ctypes binding of libns (include/ns.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; all
+computation happens in the CUDA kernels of libns.  Loading fails loudly (an
+exception) when libns.so is missing or cannot be opened: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libns.so")
+
+NS_OK, NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_OOM, NS_ERR_UNSUPPORTED_N, NS_ERR_TIMEOUT, \
+    NS_ERR_NONFINITE = range(7)
+NS_FP64, NS_FP32 = 0, 1
+
+# every symbol include/ns.h declares
+SYMBOLS = ("ns_init", "ns_set_state", "ns_get_state", "ns_step", "ns_fft_r2c", "ns_fft_c2r",
+           "ns_energy_spectrum", "ns_nbins", "ns_series", "ns_series_capacity",
+           "ns_kernel_census", "ns_sync", "ns_last_error", "ns_status_str", "ns_destroy")
+
+
+class NsError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        msg = f"{what}: {ns_status_str(status)} (status {status})"
+        super().__init__(msg + (f" [{detail}]" if detail else ""))
+
+
+class ns_run_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nu", ctypes.c_double), ("dt", ctypes.c_double),
+                ("force_amp", ctypes.c_double), ("force_k", ctypes.c_int),
+                ("dealias", ctypes.c_int)]
+
+
+class ns_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int),
+                ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Open libns.so and declare its signatures (raises if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libns.so not found at {path}: build it with "
+                          "paper_1003_4322_gb300.build.build() (needs nvcc)")
+    L = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "ns_init": ([ctypes.POINTER(ns_run_params), I, I, P, ctypes.POINTER(P)], I),
+        "ns_set_state": ([P, I, P, I], I),
+        "ns_get_state": ([P, I, P, I], I),
+        "ns_step": ([P, I], I),
+        "ns_fft_r2c": ([P, I, I, P, P], I),
+        "ns_fft_c2r": ([P, I, I, P, P], I),
+        "ns_energy_spectrum": ([P, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D)], I),
+        "ns_nbins": ([I], I),
+        "ns_series": ([P, I, I, P, P, ctypes.POINTER(I)], I),
+        "ns_series_capacity": ([], I),
+        "ns_kernel_census": ([P, I, ctypes.POINTER(ns_kernel_time), I, ctypes.POINTER(I)], I),
+        "ns_sync": ([P], I),
+        "ns_status_str": ([I], ctypes.c_char_p),
+        "ns_last_error": ([P], ctypes.c_char_p),
+        "ns_destroy": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(st: int, what: str, ctx=None) -> None:
+    if st != NS_OK:
+        detail = load().ns_last_error(ctx).decode() if ctx is not None else ""
+        raise NsError(st, what, detail)
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (must be contiguous)."""
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data_as(ctypes.c_void_p)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _on_device(x) -> int:
+    return int(hasattr(x, "is_cuda") and x.is_cuda)
+
+
+def ns_status_str(st: int) -> str:
+    return load().ns_status_str(st).decode()
+
+
+def ns_nbins(n: int) -> int:
+    return load().ns_nbins(n)
+
+
+def ns_series_capacity() -> int:
+    return load().ns_series_capacity()
+
+
+def ns_init(runs, prec: int, stream=None):
+    """runs: list of dicts or ns_run_params; stream: torch.cuda.Stream, a raw
+    cudaStream_t integer, or None (legacy default stream)."""
+    arr = (ns_run_params * len(runs))()
+    for i, r in enumerate(runs):
+        if isinstance(r, ns_run_params):
+            arr[i] = r
+        else:
+            arr[i] = ns_run_params(int(r["n"]), float(r.get("nu", 0.0)), float(r["dt"]),
+                                   float(r.get("force_amp", 0.0)), int(r.get("force_k", 0)),
+                                   int(r.get("dealias", 0)))
+    if stream is None:
+        s = None
+    elif hasattr(stream, "cuda_stream"):
+        s = ctypes.c_void_p(stream.cuda_stream)
+    else:
+        s = ctypes.c_void_p(int(stream))
+    ctx = ctypes.c_void_p()
+    _check(load().ns_init(arr, len(runs), prec, s, ctypes.byref(ctx)), "ns_init")
+    return ctx
+
+
+def ns_destroy(ctx) -> None:
+    load().ns_destroy(ctx)
+
+
+def ns_set_state(ctx, run: int, uhat) -> None:
+    """uhat: complex128 [3][N][N][N/2+1], numpy (host) or torch (host/device)."""
+    _check(load().ns_set_state(ctx, run, _ptr(uhat), _on_device(uhat)), "ns_set_state", ctx)
+
+
+def ns_get_state(ctx, run: int, out) -> None:
+    _check(load().ns_get_state(ctx, run, _ptr(out), _on_device(out)), "ns_get_state", ctx)
+
+
+def ns_step(ctx, nsteps: int) -> None:
+    _check(load().ns_step(ctx, nsteps), "ns_step", ctx)
+
+
+def ns_fft_r2c(ctx, n: int, ncomp: int, inp, out) -> None:
+    _check(load().ns_fft_r2c(ctx, n, ncomp, _ptr(inp), _ptr(out)), "ns_fft_r2c", ctx)
+
+
+def ns_fft_c2r(ctx, n: int, ncomp: int, inp, out) -> None:
+    _check(load().ns_fft_c2r(ctx, n, ncomp, _ptr(inp), _ptr(out)), "ns_fft_c2r", ctx)
+
+
+def ns_energy_spectrum(ctx, run: int, n: int):
+    """Returns (E, Omega, spectrum as a numpy array of ns_nbins(n) shells)."""
+    nb = ns_nbins(n)
+    spec = np.zeros(nb, dtype=np.float64)
+    e, om = ctypes.c_double(), ctypes.c_double()
+    _check(load().ns_energy_spectrum(ctx, run, _ptr(spec), nb, ctypes.byref(e), ctypes.byref(om)),
+           "ns_energy_spectrum", ctx)
+    return e.value, om.value, spec
+
+
+def ns_series(ctx, run: int, count: int):
+    E = np.zeros(max(count, 1), dtype=np.float64)
+    O = np.zeros(max(count, 1), dtype=np.float64)
+    w = ctypes.c_int()
+    _check(load().ns_series(ctx, run, count, _ptr(E), _ptr(O), ctypes.byref(w)), "ns_series", ctx)
+    return E[: w.value].copy(), O[: w.value].copy()
+
+
+def ns_kernel_census(ctx, nsteps: int):
+    """Per-kernel launches and device time over nsteps un-graphed steps:
+    list of (name, launches, total_ms)."""
+    arr = (ns_kernel_time * 64)()
+    cnt = ctypes.c_int()
+    _check(load().ns_kernel_census(ctx, nsteps, arr, 64, ctypes.byref(cnt)), "ns_kernel_census", ctx)
+    return [(arr[i].name.decode(), arr[i].launches, arr[i].total_ms)
+            for i in range(min(cnt.value, 64))]
+
+
+def ns_sync(ctx) -> None:
+    _check(load().ns_sync(ctx), "ns_sync", ctx)

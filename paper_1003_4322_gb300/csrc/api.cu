@@ -1,0 +1,665 @@
+// api.cu -- the C ABI of libns (include/ns.h): context, state transfer,
+// time stepping (captured once per context into a CUDA graph), standalone
+// transforms and FP64 diagnostics.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "../../include/ns.h"
+#include "fused.h"
+#include "ns_internal.h"
+#include "plain.h"
+
+using namespace nsk;
+
+namespace {
+
+const int kSeriesCap = 4096;
+
+struct FftRes {
+    int n = 0;
+    Plan plN{}, plH{};
+    void *tw = nullptr;       // Cx<T>[n], exp(-2 pi i t / n)
+    void *scratch = nullptr;  // one half-layout field (c2r)
+};
+
+struct Run {
+    ns_run_params p{};
+    int n = 0, nh = 0;
+    long M = 0;   // modes per component, half layout
+    long V = 0;   // grid points per component
+    // plain form (full half layout)
+    void *un = nullptr, *u1 = nullptr, *wn = nullptr, *work = nullptr, *phys = nullptr;
+    void *etab = nullptr;   // exp(-nu k^2 dt) by integer k^2
+    // fused form
+    FusedRun fz{};
+    // diagnostics
+    double *part = nullptr;
+    double *series = nullptr;
+    unsigned long long *counter = nullptr;
+    int nparts = 0;
+};
+
+}  // namespace
+
+struct ns_ctx {
+    ns_prec prec = NS_FP64;
+    cudaStream_t stream = nullptr;   // caller's stream
+    cudaStream_t cap = nullptr;      // private stream for graph capture
+    std::vector<Run> runs;
+    std::map<int, FftRes> fft;
+    ns_status sticky = NS_OK;
+    int *flags = nullptr;            // device error word (bit 0: non-finite energy)
+    double *spec = nullptr, *ens = nullptr;
+    int spec_cap = 0;
+    void *staging = nullptr;
+    size_t staging_bytes = 0;
+    cudaGraphExec_t graph = nullptr;
+    char last_error[256] = {0};
+};
+
+namespace {
+
+size_t elem_bytes(ns_prec p) { return p == NS_FP64 ? sizeof(double) : sizeof(float); }
+
+ns_status fail_cuda_at(ns_ctx *c, cudaError_t e, int line) {
+    if (c)
+        snprintf(c->last_error, sizeof(c->last_error), "%s (%s) at api.cu:%d", cudaGetErrorName(e),
+                 cudaGetErrorString(e), line);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return NS_ERR_OOM;
+    }
+    if (c) c->sticky = NS_ERR_CUDA;
+    return NS_ERR_CUDA;
+}
+#define fail_cuda(c, e) fail_cuda_at((c), (e), __LINE__)
+
+#define NS_CK(expr)                                   \
+    do {                                              \
+        cudaError_t _e = (expr);                      \
+        if (_e != cudaSuccess) return fail_cuda(c, _e); \
+    } while (0)
+
+template <typename P> cudaError_t dalloc(P **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    return cudaMalloc((void **)p, bytes);
+}
+
+// Per-n transform resources (plans, twiddles, c2r scratch), created once.
+ns_status get_fft(ns_ctx *c, int n, FftRes **out) {
+    auto it = c->fft.find(n);
+    if (it != c->fft.end()) {
+        *out = &it->second;
+        return NS_OK;
+    }
+    FftRes f;
+    f.n = n;
+    if (!make_plan(n, &f.plN) || !make_plan(n / 2, &f.plH)) return NS_ERR_UNSUPPORTED_N;
+    cudaError_t e;
+    if (c->prec == NS_FP64) f.tw = make_twiddles<double>(n, &e);
+    else f.tw = make_twiddles<float>(n, &e);
+    if (!f.tw) return fail_cuda(c, e);
+    c->fft[n] = f;
+    *out = &c->fft[n];
+    return NS_OK;
+}
+
+ns_status ensure_scratch(ns_ctx *c, FftRes *f) {
+    if (f->scratch) return NS_OK;
+    const size_t bytes = (size_t)f->n * f->n * (f->n / 2 + 1) * 2 * elem_bytes(c->prec);
+    NS_CK(dalloc(&f->scratch, bytes));
+    return NS_OK;
+}
+
+// ---------------------------------------------------------------- transforms
+
+// c2r of ncomp half fields: x pass (in -> tmp), y pass (tmp in place), z pass
+// (tmp -> out).  tmp holds ncomp_tmp fields; components go in batches.
+template <typename T>
+cudaError_t c2r_batch(const typename Cx<T>::type *in, typename Cx<T>::type *tmp, T *out, int n,
+                      int ncomp, const FftRes &f, int ct, cudaStream_t s, Tracer *tr = nullptr) {
+    const long nh = n / 2 + 1, plane = (long)n * nh, M = (long)n * plane;
+    const typename Cx<T>::type *tw = (const typename Cx<T>::type *)f.tw;
+    cudaError_t e = NSK_TIMED(tr, "fft_x_inverse",
+                              fft_strided<T>(in, tmp, plane, plane, M, M, ncomp, +1, f.plN, tw, n, ct, s));
+    if (e != cudaSuccess) return e;
+    e = NSK_TIMED(tr, "fft_y_inverse",
+                  fft_strided<T>(tmp, tmp, nh, nh, plane, plane, ncomp * n, +1, f.plN, tw, n, ct, s));
+    if (e != cudaSuccess) return e;
+    return NSK_TIMED(tr, "fft_z_c2r", fft_z_c2r<T>(tmp, out, n, (long)ncomp * n * n, f.plH, tw, s));
+}
+
+// r2c of ncomp real fields: z pass (in -> out), y and x passes in place.
+template <typename T>
+cudaError_t r2c_batch(const T *in, typename Cx<T>::type *out, int n, int ncomp, const FftRes &f,
+                      int ct, cudaStream_t s, Tracer *tr = nullptr) {
+    const long nh = n / 2 + 1, plane = (long)n * nh, M = (long)n * plane;
+    const typename Cx<T>::type *tw = (const typename Cx<T>::type *)f.tw;
+    cudaError_t e = NSK_TIMED(tr, "fft_z_r2c", fft_z_r2c<T>(in, out, n, (long)ncomp * n * n, f.plH, tw, s));
+    if (e != cudaSuccess) return e;
+    e = NSK_TIMED(tr, "fft_y_forward",
+                  fft_strided<T>(out, out, nh, nh, plane, plane, ncomp * n, -1, f.plN, tw, n, ct, s));
+    if (e != cudaSuccess) return e;
+    return NSK_TIMED(tr, "fft_x_forward",
+                     fft_strided<T>(out, out, plane, plane, M, M, ncomp, -1, f.plN, tw, n, ct, s));
+}
+
+// ---------------------------------------------------------------- state transfer
+
+__device__ __forceinline__ int wn_(int i, int n) { return 2 * i < n ? i : i - n; }
+
+__device__ __forceinline__ bool kept_(int kx, int ky, int kz, int n, int dealias) {
+    int m = max(abs(kx), max(abs(ky), abs(kz)));
+    if (3 * m >= n) return false;
+    if (dealias == 1 && 9L * (kx * kx + ky * ky + kz * kz) >= (long)n * n) return false;
+    return true;
+}
+
+// dst (half layout, precision T) <- src (FP64 half layout) for modes
+// [m0, m0 + cnt) of one component, zeroing modes outside Pi.
+template <typename T>
+__global__ void k_load_half(const double2 *__restrict__ src, typename Cx<T>::type *__restrict__ dst,
+                            int n, long m0, long cnt, int dealias) {
+    const int nh = n / 2 + 1;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < cnt; i += (long)gridDim.x * blockDim.x) {
+        const long m = m0 + i;
+        const int kz = (int)(m % nh), iy = (int)((m / nh) % n), ix = (int)(m / ((long)nh * n));
+        typename Cx<T>::type v;
+        if (kept_(wn_(ix, n), wn_(iy, n), kz, n, dealias)) {
+            v.x = (T)src[i].x;
+            v.y = (T)src[i].y;
+        } else {
+            v.x = 0;
+            v.y = 0;
+        }
+        dst[m] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_store_half(const typename Cx<T>::type *__restrict__ src, double2 *__restrict__ dst,
+                             long m0, long cnt) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < cnt; i += (long)gridDim.x * blockDim.x)
+        dst[i] = make_double2((double)src[m0 + i].x, (double)src[m0 + i].y);
+}
+
+ns_status ensure_staging(ns_ctx *c, size_t bytes) {
+    if (c->staging_bytes >= bytes) return NS_OK;
+    if (c->staging) cudaFree(c->staging);
+    c->staging = nullptr;
+    c->staging_bytes = 0;
+    NS_CK(dalloc(&c->staging, bytes));
+    c->staging_bytes = bytes;
+    return NS_OK;
+}
+
+const size_t kStageChunk = 64u << 20;   // bytes of FP64 complex per host transfer
+
+template <typename T>
+ns_status plain_set_state(ns_ctx *c, Run &r, const double2 *src, int on_device) {
+    typedef typename Cx<T>::type C;
+    C *dst = (C *)r.un;
+    const long total = 3 * r.M;
+    const long chunk = on_device ? total : (long)(kStageChunk / sizeof(double2));
+    if (!on_device) {
+        ns_status st = ensure_staging(c, (size_t)std::min(total, chunk) * sizeof(double2));
+        if (st != NS_OK) return st;
+    }
+    for (long m0 = 0; m0 < total; m0 += chunk) {
+        const long cnt = std::min(chunk, total - m0);
+        const double2 *s = src + m0;
+        if (!on_device) {
+            NS_CK(cudaMemcpyAsync(c->staging, src + m0, cnt * sizeof(double2),
+                                  cudaMemcpyHostToDevice, c->stream));
+            s = (const double2 *)c->staging;
+        }
+        // component boundaries: mode index within the component
+        long done = 0;
+        while (done < cnt) {
+            const long g = m0 + done;
+            const int comp = (int)(g / r.M);
+            const long mm = g % r.M;
+            const long seg = std::min(cnt - done, r.M - mm);
+            k_load_half<T><<<(unsigned)std::min<long>((seg + 255) / 256, 152 * 16), 256, 0, c->stream>>>(
+                s + done, dst + (long)comp * r.M, r.n, mm, seg, r.p.dealias);
+            NS_CK(cudaGetLastError());
+            done += seg;
+        }
+        if (!on_device) NS_CK(cudaStreamSynchronize(c->stream));
+    }
+    return NS_OK;
+}
+
+template <typename T>
+ns_status plain_get_state(ns_ctx *c, Run &r, double2 *dst, int on_device) {
+    typedef typename Cx<T>::type C;
+    const C *src = (const C *)r.un;
+    const long total = 3 * r.M;
+    const long chunk = on_device ? total : (long)(kStageChunk / sizeof(double2));
+    if (!on_device) {
+        ns_status st = ensure_staging(c, (size_t)std::min(total, chunk) * sizeof(double2));
+        if (st != NS_OK) return st;
+    }
+    for (long m0 = 0; m0 < total; m0 += chunk) {
+        const long cnt = std::min(chunk, total - m0);
+        double2 *d = on_device ? dst + m0 : (double2 *)c->staging;
+        k_store_half<T><<<(unsigned)std::min<long>((cnt + 255) / 256, 152 * 16), 256, 0, c->stream>>>(
+            src, d, m0, cnt);
+        NS_CK(cudaGetLastError());
+        if (!on_device) {
+            NS_CK(cudaMemcpyAsync(dst + m0, c->staging, cnt * sizeof(double2), cudaMemcpyDeviceToHost,
+                                  c->stream));
+            NS_CK(cudaStreamSynchronize(c->stream));
+        }
+    }
+    return NS_OK;
+}
+
+// ---------------------------------------------------------------- plain step
+
+template <typename T> ns_status plain_alloc(ns_ctx *c, Run &r) {
+    typedef typename Cx<T>::type C;
+    const size_t half = (size_t)r.M * sizeof(C), real = (size_t)r.V * sizeof(T);
+    NS_CK(dalloc(&r.un, 3 * half));
+    NS_CK(dalloc(&r.u1, 3 * half));
+    NS_CK(dalloc(&r.wn, 3 * half));
+    NS_CK(dalloc(&r.work, 3 * half));
+    NS_CK(dalloc(&r.phys, 6 * real));
+    NS_CK(cudaMemsetAsync(r.un, 0, 3 * half, c->stream));
+    NS_CK(cudaMemsetAsync(r.u1, 0, 3 * half, c->stream));
+    const int nk2 = 3 * (r.n / 2) * (r.n / 2) + 1;
+    std::vector<T> h(nk2);
+    for (int k2 = 0; k2 < nk2; k2++) h[k2] = (T)exp(-r.p.nu * (double)k2 * r.p.dt);
+    NS_CK(dalloc(&r.etab, nk2 * sizeof(T)));
+    NS_CK(cudaMemcpy(r.etab, h.data(), nk2 * sizeof(T), cudaMemcpyHostToDevice));
+    return NS_OK;
+}
+
+template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tracer *tr) {
+    typedef typename Cx<T>::type C;
+    FftRes *f;
+    ns_status st = get_fft(c, r.n, &f);
+    if (st != NS_OK) return st;
+    const int ct = default_ct(sizeof(C), r.n);
+    T *phys = (T *)r.phys;
+    for (int stage = 1; stage <= 2; stage++) {
+        C *src = (C *)(stage == 1 ? r.un : r.u1);
+        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, (C *)r.wn, r.n, s)));
+        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, r.n, 3, *f, ct, s, tr));
+        NS_CK(c2r_batch<T>((C *)r.wn, (C *)r.work, phys + 3 * r.V, r.n, 3, *f, ct, s, tr));
+        NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, r.n, s)));
+        NS_CK(r2c_batch<T>(phys, (C *)r.wn, r.n, 3, *f, ct, s, tr));
+        UpdateArgs ua{stage, r.p.dt, r.p.force_amp, r.p.force_k, r.p.dealias};
+        NS_CK(NSK_TIMED(tr, "update",
+                        plain_update<T>((C *)r.un, (C *)r.u1, (const C *)r.wn, (const T *)r.etab, r.n, ua, s)));
+    }
+    NS_CK(NSK_TIMED(tr, "energy_partials", plain_energy_partials<T>((const C *)r.un, r.n, r.part, s)));
+    NS_CK(NSK_TIMED(tr, "energy_final",
+                    energy_final(r.part, r.nparts, r.series, kSeriesCap, r.counter, c->flags, s)));
+    return NS_OK;
+}
+
+bool use_fused(const ns_ctx *c) { return c->prec == NS_FP32 && fused_enabled(); }
+
+ns_status run_step(ns_ctx *c, Run &r, cudaStream_t s, Tracer *tr) {
+    if (use_fused(c)) {
+        cudaError_t e = fused_step(r.fz, r.series, kSeriesCap, r.counter, c->flags, s, tr);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+        return NS_OK;
+    }
+    return c->prec == NS_FP64 ? plain_step<double>(c, r, s, tr) : plain_step<float>(c, r, s, tr);
+}
+
+ns_status build_graph(ns_ctx *c) {
+    if (c->graph) return NS_OK;
+    // Resources the step needs must exist before capture (no allocation inside).
+    for (Run &r : c->runs) {
+        FftRes *f;
+        ns_status st = get_fft(c, r.n, &f);
+        if (st != NS_OK) return st;
+    }
+    NS_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    ns_status st = NS_OK;
+    for (Run &r : c->runs) {
+        st = run_step(c, r, c->cap, nullptr);
+        if (st != NS_OK) break;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    if (st != NS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    return NS_OK;
+}
+
+void free_run(Run &r) {
+    void *ps[] = {r.un, r.u1, r.wn, r.work, r.phys, r.etab, r.part, r.series, r.counter};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    fused_free(r.fz);
+}
+
+// Entry check: a null context is an argument error; a context that already
+// failed stays failed.  A stale error left in the runtime's per-thread slot by
+// some earlier, unrelated call is cleared so that the kernel launches of this
+// call report only their own failures.
+ns_status check_ctx(ns_ctx *c) {
+    if (!c) return NS_ERR_ARG;
+    if (c->sticky == NS_OK) (void)cudaGetLastError();
+    return c->sticky;
+}
+
+ns_status check_flags(ns_ctx *c) {
+    int h = 0;
+    NS_CK(cudaMemcpy(&h, c->flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & 1) return NS_ERR_NONFINITE;
+    return NS_OK;
+}
+
+}  // namespace
+
+// ================================================================ public ABI
+
+extern "C" {
+
+const char *ns_status_str(ns_status s) {
+    switch (s) {
+    case NS_OK: return "ok";
+    case NS_ERR_ARG: return "invalid argument";
+    case NS_ERR_CUDA: return "CUDA error";
+    case NS_ERR_OOM: return "out of memory";
+    case NS_ERR_UNSUPPORTED_N: return "unsupported grid size";
+    case NS_ERR_TIMEOUT: return "device wait timed out";
+    case NS_ERR_NONFINITE: return "non-finite energy";
+    }
+    return "unknown status";
+}
+
+int ns_nbins(int n) { return n < 1 ? 0 : (int)ceil(sqrt(3.0) * n / 2.0) + 1; }
+
+int ns_series_capacity(void) { return kSeriesCap; }
+
+const char *ns_last_error(ns_ctx *c) { return c ? c->last_error : ""; }
+
+ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda_stream,
+                  ns_ctx **out) {
+    if (!out) return NS_ERR_ARG;
+    *out = nullptr;
+    if (!runs || nruns < 1 || (prec != NS_FP64 && prec != NS_FP32)) return NS_ERR_ARG;
+    for (int i = 0; i < nruns; i++) {
+        const ns_run_params &p = runs[i];
+        if (!(p.nu >= 0.0) || !(p.dt > 0.0) || (p.dealias != 0 && p.dealias != 1) ||
+            p.force_k < 0 || !isfinite(p.force_amp) || !isfinite(p.nu) || !isfinite(p.dt))
+            return NS_ERR_ARG;
+        if (!supported_n(p.n) || p.n > (prec == NS_FP32 ? 1024 : 768)) return NS_ERR_UNSUPPORTED_N;
+    }
+    ns_ctx *c = new (std::nothrow) ns_ctx;
+    if (!c) return NS_ERR_OOM;
+    c->prec = prec;
+    c->stream = (cudaStream_t)cuda_stream;
+    ns_status st = NS_OK;
+    auto bail = [&](ns_status s) {
+        ns_destroy(c);
+        return s;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(fail_cuda(nullptr, e));
+    if ((e = dalloc(&c->flags, sizeof(int))) != cudaSuccess) return bail(fail_cuda(nullptr, e));
+    cudaMemset(c->flags, 0, sizeof(int));
+    c->runs.resize(nruns);
+    int maxbins = 0;
+    for (int i = 0; i < nruns; i++) {
+        Run &r = c->runs[i];
+        r.p = runs[i];
+        r.n = r.p.n;
+        r.nh = r.n / 2 + 1;
+        r.M = (long)r.n * r.n * r.nh;
+        r.V = (long)r.n * r.n * r.n;
+        r.nparts = energy_nparts(r.n);
+        maxbins = std::max(maxbins, ns_nbins(r.n));
+        FftRes *f;
+        if ((st = get_fft(c, r.n, &f)) != NS_OK) return bail(st);
+        if (use_fused(c)) {
+            e = fused_alloc(r.fz, r.p, (const float2 *)f->tw, c->stream);
+            if (e != cudaSuccess) return bail(fail_cuda(nullptr, e));
+            r.nparts = r.fz.nparts;
+        } else {
+            st = prec == NS_FP64 ? plain_alloc<double>(c, r) : plain_alloc<float>(c, r);
+            if (st != NS_OK) return bail(st);
+        }
+        if ((e = dalloc(&r.part, sizeof(double) * 2 * std::max(r.nparts, 1))) != cudaSuccess ||
+            (e = dalloc(&r.series, sizeof(double) * 2 * kSeriesCap)) != cudaSuccess ||
+            (e = dalloc(&r.counter, sizeof(unsigned long long))) != cudaSuccess)
+            return bail(fail_cuda(nullptr, e));
+        if (use_fused(c)) r.fz.part = r.part;
+        cudaMemset(r.counter, 0, sizeof(unsigned long long));
+    }
+    if ((e = dalloc(&c->spec, sizeof(double) * maxbins)) != cudaSuccess ||
+        (e = dalloc(&c->ens, sizeof(double) * maxbins)) != cudaSuccess)
+        return bail(fail_cuda(nullptr, e));
+    c->spec_cap = maxbins;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(fail_cuda(nullptr, e));
+    *out = c;
+    return NS_OK;
+}
+
+void ns_destroy(ns_ctx *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (Run &r : c->runs) free_run(r);
+    for (auto &kv : c->fft) {
+        if (kv.second.tw) cudaFree(kv.second.tw);
+        if (kv.second.scratch) cudaFree(kv.second.scratch);
+    }
+    if (c->flags) cudaFree(c->flags);
+    if (c->spec) cudaFree(c->spec);
+    if (c->ens) cudaFree(c->ens);
+    if (c->staging) cudaFree(c->staging);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+ns_status ns_set_state(ns_ctx *c, int run, const void *uhat, int on_device) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (run < 0 || run >= (int)c->runs.size() || !uhat) return NS_ERR_ARG;
+    Run &r = c->runs[run];
+    if (use_fused(c)) {
+        if (!on_device) {
+            ns_status s2 = ensure_staging(c, kStageChunk);
+            if (s2 != NS_OK) return s2;
+        }
+        cudaError_t e = fused_set_state(r.fz, (const double2 *)uhat, on_device, c->staging,
+                                        kStageChunk, c->stream);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+        return NS_OK;
+    }
+    return c->prec == NS_FP64 ? plain_set_state<double>(c, r, (const double2 *)uhat, on_device)
+                              : plain_set_state<float>(c, r, (const double2 *)uhat, on_device);
+}
+
+ns_status ns_get_state(ns_ctx *c, int run, void *uhat, int on_device) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (run < 0 || run >= (int)c->runs.size() || !uhat) return NS_ERR_ARG;
+    Run &r = c->runs[run];
+    if (use_fused(c)) {
+        if (!on_device) {
+            ns_status s2 = ensure_staging(c, kStageChunk);
+            if (s2 != NS_OK) return s2;
+        }
+        cudaError_t e = fused_get_state(r.fz, (double2 *)uhat, on_device, c->staging, kStageChunk,
+                                        c->stream);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+    } else {
+        st = c->prec == NS_FP64 ? plain_get_state<double>(c, r, (double2 *)uhat, on_device)
+                                : plain_get_state<float>(c, r, (double2 *)uhat, on_device);
+        if (st != NS_OK) return st;
+    }
+    NS_CK(cudaStreamSynchronize(c->stream));
+    return check_flags(c);
+}
+
+ns_status ns_step(ns_ctx *c, int nsteps) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (nsteps < 0) return NS_ERR_ARG;
+    if (nsteps == 0) return NS_OK;
+    if ((st = build_graph(c)) != NS_OK) return st;
+    for (int i = 0; i < nsteps; i++) NS_CK(cudaGraphLaunch(c->graph, c->stream));
+    return NS_OK;
+}
+
+ns_status ns_fft_r2c(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (!in || !out || ncomp < 1 || ncomp > 65535 / (n > 0 ? n : 1)) return NS_ERR_ARG;
+    if (!supported_n(n)) return NS_ERR_UNSUPPORTED_N;
+    FftRes *f;
+    if ((st = get_fft(c, n, &f)) != NS_OK) return st;
+    if (c->prec == NS_FP64)
+        NS_CK(r2c_batch<double>((const double *)in, (double2 *)out, n, ncomp, *f,
+                                default_ct(sizeof(double2), n), c->stream));
+    else
+        NS_CK(r2c_batch<float>((const float *)in, (float2 *)out, n, ncomp, *f,
+                               default_ct(sizeof(float2), n), c->stream));
+    return NS_OK;
+}
+
+ns_status ns_fft_c2r(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (!in || !out || ncomp < 1) return NS_ERR_ARG;
+    if (!supported_n(n)) return NS_ERR_UNSUPPORTED_N;
+    FftRes *f;
+    if ((st = get_fft(c, n, &f)) != NS_OK) return st;
+    if ((st = ensure_scratch(c, f)) != NS_OK) return st;
+    const long M = (long)n * n * (n / 2 + 1), V = (long)n * n * n;
+    for (int k = 0; k < ncomp; k++) {
+        if (c->prec == NS_FP64)
+            NS_CK(c2r_batch<double>((const double2 *)in + k * M, (double2 *)f->scratch,
+                                    (double *)out + k * V, n, 1, *f,
+                                    default_ct(sizeof(double2), n), c->stream));
+        else
+            NS_CK(c2r_batch<float>((const float2 *)in + k * M, (float2 *)f->scratch,
+                                   (float *)out + k * V, n, 1, *f, default_ct(sizeof(float2), n),
+                                   c->stream));
+    }
+    return NS_OK;
+}
+
+ns_status ns_energy_spectrum(ns_ctx *c, int run, double *spec, int nbins, double *energy,
+                             double *enstrophy) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (run < 0 || run >= (int)c->runs.size() || nbins < 0 || (nbins > 0 && !spec))
+        return NS_ERR_ARG;
+    Run &r = c->runs[run];
+    const int nb = ns_nbins(r.n);
+    if (use_fused(c))
+        NS_CK(fused_spectrum(r.fz, nb, c->spec, c->ens, c->stream));
+    else if (c->prec == NS_FP64)
+        NS_CK(plain_spectrum<double>((const double2 *)r.un, r.n, nb, c->spec, c->ens, c->stream));
+    else
+        NS_CK(plain_spectrum<float>((const float2 *)r.un, r.n, nb, c->spec, c->ens, c->stream));
+    std::vector<double> hs(nb), he(nb);
+    NS_CK(cudaMemcpyAsync(hs.data(), c->spec, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    NS_CK(cudaMemcpyAsync(he.data(), c->ens, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    NS_CK(cudaStreamSynchronize(c->stream));
+    double e = 0.0, om = 0.0;
+    for (int k = 0; k < nb; k++) {
+        e += hs[k];
+        om += he[k];
+    }
+    for (int k = 0; k < nbins && k < nb; k++) spec[k] = hs[k];
+    if (energy) *energy = e;
+    if (enstrophy) *enstrophy = om;
+    if (!isfinite(e)) return NS_ERR_NONFINITE;
+    return check_flags(c);
+}
+
+ns_status ns_series(ns_ctx *c, int run, int count, double *energy, double *enstrophy,
+                    int *written) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (run < 0 || run >= (int)c->runs.size() || count < 0 || !written ||
+        (count > 0 && (!energy || !enstrophy)))
+        return NS_ERR_ARG;
+    Run &r = c->runs[run];
+    std::vector<double> ring(2 * kSeriesCap);
+    unsigned long long cnt = 0;
+    NS_CK(cudaMemcpyAsync(ring.data(), r.series, ring.size() * sizeof(double),
+                          cudaMemcpyDeviceToHost, c->stream));
+    NS_CK(cudaMemcpyAsync(&cnt, r.counter, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+    NS_CK(cudaStreamSynchronize(c->stream));
+    unsigned long long avail = cnt < (unsigned long long)kSeriesCap ? cnt : kSeriesCap;
+    int w = (int)std::min<unsigned long long>(avail, (unsigned long long)count);
+    for (int i = 0; i < w; i++) {
+        const unsigned long long idx = (cnt - w + i) % kSeriesCap;
+        energy[i] = ring[2 * idx];
+        enstrophy[i] = ring[2 * idx + 1];
+    }
+    *written = w;
+    return NS_OK;
+}
+
+ns_status ns_kernel_census(ns_ctx *c, int nsteps, ns_kernel_time *out, int max, int *count) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (nsteps < 1 || max < 0 || !count || (max > 0 && !out)) return NS_ERR_ARG;
+    for (Run &r : c->runs) {
+        FftRes *f;
+        if ((st = get_fft(c, r.n, &f)) != NS_OK) return st;
+    }
+    Tracer tr;
+    tr.s = c->stream;
+    for (int i = 0; i < nsteps; i++)
+        for (Run &r : c->runs)
+            if ((st = run_step(c, r, c->stream, &tr)) != NS_OK) return st;
+    if (tr.err != cudaSuccess) return fail_cuda(c, tr.err);
+    NS_CK(cudaStreamSynchronize(c->stream));
+    std::vector<ns_kernel_time> agg;
+    for (const Tracer::Rec &rec : tr.recs) {
+        float ms = 0.f;
+        NS_CK(cudaEventElapsedTime(&ms, rec.a, rec.b));
+        size_t i = 0;
+        while (i < agg.size() && strncmp(agg[i].name, rec.name, sizeof(agg[i].name)) != 0) i++;
+        if (i == agg.size()) {
+            ns_kernel_time k;
+            memset(&k, 0, sizeof(k));
+            strncpy(k.name, rec.name, sizeof(k.name) - 1);
+            agg.push_back(k);
+        }
+        agg[i].launches++;
+        agg[i].total_ms += ms;
+    }
+    int w = 0;
+    for (size_t i = 0; i < agg.size() && w < max; i++) out[w++] = agg[i];
+    *count = (int)agg.size();
+    return check_flags(c);
+}
+
+ns_status ns_sync(ns_ctx *c) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    NS_CK(cudaStreamSynchronize(c->stream));
+    NS_CK(cudaGetLastError());
+    return check_flags(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// fft_passes.cu -- the axis passes of the unpruned 3D r2c / c2r transforms
+// (Sec. 2, Fig. 1: 1D FFTs along each direction of the N^3 box with the
+// (N/2+1) x N x N half storage).  On one GPU the slab transposes of the
+// paper become the data layout of these passes: the strided passes read and
+// write rows of contiguous columns (coalesced 128-byte rows), so no separate
+// transpose ever touches HBM.
+#include <math.h>
+
+#include <mutex>
+#include <set>
+#include <vector>
+
+#include "ns_internal.h"
+
+namespace nsk {
+
+// ---------------------------------------------------------------- plans
+
+static void factor23(int n, int &a, int &b, int &rest) {
+    a = b = 0;
+    while (n > 1 && n % 2 == 0) { n /= 2; a++; }
+    while (n > 1 && n % 3 == 0) { n /= 3; b++; }
+    rest = n;
+}
+
+bool make_plan(int n, Plan *pl) {
+    int a, b, rest;
+    if (n < 4) return false;
+    factor23(n, a, b, rest);
+    if (rest != 1) return false;
+    int E;
+    if (b == 0) E = n < 16 ? n : 16;
+    else if (a >= 2) E = 12;
+    else if (a == 1) E = 6;
+    else E = b >= 2 ? 9 : 3;
+    if (E == 3 || E == 2) return false;
+    static const int cand[] = {16, 12, 9, 8, 6, 4, 3, 2};
+    pl->n = n;
+    pl->E = E;
+    pl->nst = 0;
+    pl->radix = 0;
+    int m = n;
+    while (m > 1) {
+        int R = 0;
+        for (int r : cand)
+            if (E % r == 0 && m % r == 0) { R = r; break; }
+        if (R == 0 || pl->nst >= 12) return false;
+        pl->radix |= (unsigned long long)R << (5 * pl->nst);
+        pl->nst++;
+        m /= R;
+    }
+    return true;
+}
+
+bool supported_n(int n) {
+    if (n < 8 || n % 2) return false;
+    Plan p;
+    return make_plan(n, &p) && make_plan(n / 2, &p);
+}
+
+int default_ct(int elem_bytes, int n) {
+    // 128-byte rows, within the thread bound of the strided kernel
+    // (512 threads for float, 384 for double: no register spills).
+    int ct = 128 / elem_bytes;
+    const int bound = elem_bytes == 8 ? 512 : 384;
+    Plan p;
+    if (make_plan(n, &p)) {
+        const int T = n / p.E;
+        while (ct > 1 && ct * T > bound) ct /= 2;
+    }
+    return ct;
+}
+
+cudaError_t allow_smem(const void *kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, size_t>> done;
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair(kernel, bytes);
+    if (done.count(key)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
+
+template <typename T> typename Cx<T>::type *make_twiddles(int n, cudaError_t *err) {
+    typedef typename Cx<T>::type C;
+    std::vector<C> h(n);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int t = 0; t < n; t++) {
+        const double a = two_pi * (double)t / (double)n;
+        h[t].x = (T)cos(a);
+        h[t].y = (T)(-sin(a));
+    }
+    C *d = nullptr;
+    *err = cudaMalloc(&d, sizeof(C) * n);
+    if (*err != cudaSuccess) return nullptr;
+    *err = cudaMemcpy(d, h.data(), sizeof(C) * n, cudaMemcpyHostToDevice);
+    if (*err != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    return d;
+}
+template float2 *make_twiddles<float>(int, cudaError_t *);
+template double2 *make_twiddles<double>(int, cudaError_t *);
+
+// ---------------------------------------------------------------- strided pass
+
+template <typename T> struct Bounds;
+template <> struct Bounds<float> { enum { threads = 512 }; };
+template <> struct Bounds<double> { enum { threads = 384 }; };
+
+// One CTA: ct contiguous columns of one plane, T = n/E threads per column,
+// lanes along columns (coalesced rows).  Shared tile: element (e, c) at
+// e * ct + c.
+template <typename T, int E, int DIR>
+__global__ void __launch_bounds__(Bounds<T>::threads)
+k_fft_strided(const typename Cx<T>::type *__restrict__ in, typename Cx<T>::type *out, long ncols,
+              long es, long ps_in, long ps_out, Plan pl, const typename Cx<T>::type *__restrict__ tw,
+              int ntab) {
+    typedef typename Cx<T>::type C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    const int ct = blockDim.x / (pl.n / E);
+    const int c = threadIdx.x % ct;
+    const int slot = threadIdx.x / ct;
+    const long col = (long)blockIdx.x * ct + c;
+    const bool valid = col < ncols;
+    const C *src = in + (long)blockIdx.y * ps_in + col;
+    C *dst = out + (long)blockIdx.y * ps_out + col;
+    auto gl = [&](int e) -> C { return valid ? src[e * es] : czero<C>(); };
+    auto gs = [&](int e, C v) {
+        if (valid) dst[e * es] = v;
+    };
+    auto sl = [&](int e) -> C { return sm[e * ct + c]; };
+    auto ss = [&](int e, C v) { sm[e * ct + c] = v; };
+    fft_line<E, DIR, false, false, true>(pl, slot, tw, ntab, gl, sl, ss, gs);
+}
+
+template <typename T, int DIR>
+static const void *strided_kernel(int E) {
+    switch (E) {
+    case 4: return (const void *)k_fft_strided<T, 4, DIR>;
+    case 6: return (const void *)k_fft_strided<T, 6, DIR>;
+    case 8: return (const void *)k_fft_strided<T, 8, DIR>;
+    case 9: return (const void *)k_fft_strided<T, 9, DIR>;
+    case 12: return (const void *)k_fft_strided<T, 12, DIR>;
+    case 16: return (const void *)k_fft_strided<T, 16, DIR>;
+    }
+    return nullptr;
+}
+
+template <typename T>
+cudaError_t fft_strided(const typename Cx<T>::type *in, typename Cx<T>::type *out, long ncols,
+                        long es, long ps_in, long ps_out, int planes, int dir, const Plan &pl,
+                        const typename Cx<T>::type *tw, int ntab, int ct, cudaStream_t s) {
+    typedef typename Cx<T>::type C;
+    const void *k = dir < 0 ? strided_kernel<T, -1>(pl.E) : strided_kernel<T, +1>(pl.E);
+    if (!k || planes < 1 || planes > 65535) return cudaErrorInvalidValue;
+    const int T_ = pl.n / pl.E;
+    if (ct < 1 || ct * T_ > (int)Bounds<T>::threads) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)pl.n * ct * sizeof(C);
+    cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((ncols + ct - 1) / ct), (unsigned)planes);
+    Plan p = pl;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&ncols, (void *)&es, (void *)&ps_in,
+                    (void *)&ps_out, (void *)&p, (void *)&tw, (void *)&ntab};
+    return cudaLaunchKernel(k, grid, dim3(ct * T_), args, smem, s);
+}
+template cudaError_t fft_strided<float>(const float2 *, float2 *, long, long, long, long, int, int,
+                                        const Plan &, const float2 *, int, int, cudaStream_t);
+template cudaError_t fft_strided<double>(const double2 *, double2 *, long, long, long, long, int,
+                                         int, const Plan &, const double2 *, int, int,
+                                         cudaStream_t);
+
+// ---------------------------------------------------------------- z passes
+
+// Shared-memory line with a skew of one element every 128 bytes, so that the
+// stride-R writes of the early Stockham stages spread over the banks.
+template <typename C> struct Skew;
+template <> struct Skew<float2> { enum { shift = 4 }; };
+template <> struct Skew<double2> { enum { shift = 3 }; };
+template <typename C> __host__ __device__ inline int skew_len(int n) {
+    return n + (n >> Skew<C>::shift) + 2;
+}
+
+// r2c along z.  The N reals of a line, read as n = N/2 complex values
+// z[m] = x[2m] + i x[2m+1], go through one length-n FFT; then
+// X[k] = (Z[k] + conj Z[n-k])/2 - i W^k (Z[k] - conj Z[n-k])/2, W = e^{-2 pi i/N},
+// for k = 0..n (Z[n] = Z[0]).  One CTA holds lb lines, T = n/E threads each.
+template <typename T, int E>
+__global__ void __launch_bounds__(256)
+k_fft_z_r2c(const T *__restrict__ in, typename Cx<T>::type *__restrict__ out, int N, long nlines,
+            Plan pl, const typename Cx<T>::type *__restrict__ tw) {
+    typedef typename Cx<T>::type C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = N / 2, Tn = n / E;
+    const int slot = threadIdx.x % Tn, li = threadIdx.x / Tn;
+    const int lb = blockDim.x / Tn;
+    const long line = (long)blockIdx.x * lb + li;
+    const bool valid = line < nlines;
+    C *ls = reinterpret_cast<C *>(smraw) + li * skew_len<C>(n);
+    const int sh = Skew<C>::shift;
+    const C *src = reinterpret_cast<const C *>(in + line * N);
+    auto gl = [&](int e) -> C { return valid ? src[e] : czero<C>(); };
+    auto sl = [&](int e) -> C { return ls[e + (e >> sh)]; };
+    auto ss = [&](int e, C v) { ls[e + (e >> sh)] = v; };
+    fft_line<E, -1, false, true, false>(pl, slot, tw, N, gl, sl, ss, ss);
+    if (!valid) return;
+    C *dst = out + line * (n + 1);
+    const T half = (T)0.5;
+    for (int k = slot; k <= n; k += Tn) {
+        const C zk = sl(k == n ? 0 : k);
+        const C zc = cconj(sl(k == 0 ? 0 : n - k));
+        const C ev = cscale(cadd(zk, zc), half);
+        const C od = cmul_i<-1>(cscale(csub(zk, zc), half));  // (zk - zc) / (2i)
+        dst[k] = cadd(ev, cmul(od, ldg_c(tw + k)));
+    }
+}
+
+// c2r along z: Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]),
+// k < n, with the real parts of X[0] and X[n]; one inverse length-n FFT gives
+// z[m] = x[2m] + i x[2m+1].
+template <typename T, int E>
+__global__ void __launch_bounds__(256)
+k_fft_z_c2r(const typename Cx<T>::type *__restrict__ in, T *__restrict__ out, int N, long nlines,
+            Plan pl, const typename Cx<T>::type *__restrict__ tw) {
+    typedef typename Cx<T>::type C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = N / 2, Tn = n / E;
+    const int slot = threadIdx.x % Tn, li = threadIdx.x / Tn;
+    const int lb = blockDim.x / Tn;
+    const long line = (long)blockIdx.x * lb + li;
+    const bool valid = line < nlines;
+    C *ls = reinterpret_cast<C *>(smraw) + li * skew_len<C>(n);
+    const int sh = Skew<C>::shift;
+    auto sl = [&](int e) -> C { return ls[e + (e >> sh)]; };
+    auto ss = [&](int e, C v) { ls[e + (e >> sh)] = v; };
+    const C *src = in + line * (n + 1);
+    for (int k = slot; k < n; k += Tn) {
+        C xk = czero<C>(), xc = czero<C>();
+        if (valid) {
+            xk = src[k];
+            xc = cconj(src[n - k]);
+            if (k == 0) {
+                xk.y = 0;
+                xc.y = 0;
+            }
+        }
+        const C a = cadd(xk, xc);
+        const C wb = cmulc(csub(xk, xc), ldg_c(tw + k));  // W^{-k} (X[k] - conj X[n-k])
+        ss(k, cadd(a, cmul_i<1>(wb)));
+    }
+    __syncthreads();
+    C *dst = reinterpret_cast<C *>(out + line * N);
+    auto gs = [&](int e, C v) {
+        if (valid) dst[e] = v;
+    };
+    fft_line<E, +1, true, false, false>(pl, slot, tw, N, sl, sl, ss, gs);
+}
+
+template <typename T, bool R2C>
+static const void *z_kernel(int E) {
+#define NSK_ZK(EE) \
+    return R2C ? (const void *)k_fft_z_r2c<T, EE> : (const void *)k_fft_z_c2r<T, EE>
+    switch (E) {
+    case 4: NSK_ZK(4);
+    case 6: NSK_ZK(6);
+    case 8: NSK_ZK(8);
+    case 9: NSK_ZK(9);
+    case 12: NSK_ZK(12);
+    case 16: NSK_ZK(16);
+    }
+#undef NSK_ZK
+    return nullptr;
+}
+
+template <typename T, bool R2C>
+static cudaError_t launch_z(const void *in, void *out, int N, long nlines, const Plan &pl,
+                            const typename Cx<T>::type *tw, cudaStream_t s) {
+    typedef typename Cx<T>::type C;
+    const void *k = z_kernel<T, R2C>(pl.E);
+    if (!k || pl.n * 2 != N || nlines < 1) return cudaErrorInvalidValue;
+    const int Tn = pl.n / pl.E;
+    int lb = 256 / Tn;
+    if (lb < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)lb * skew_len<C>(pl.n) * sizeof(C);
+    cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const long blocks = (nlines + lb - 1) / lb;
+    if (blocks > 0x7fffffffL) return cudaErrorInvalidValue;
+    Plan p = pl;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&N, (void *)&nlines, (void *)&p,
+                    (void *)&tw};
+    return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(lb * Tn), args, smem, s);
+}
+
+template <typename T>
+cudaError_t fft_z_r2c(const T *in, typename Cx<T>::type *out, int N, long nlines, const Plan &pl,
+                      const typename Cx<T>::type *tw, cudaStream_t s) {
+    return launch_z<T, true>(in, out, N, nlines, pl, tw, s);
+}
+template <typename T>
+cudaError_t fft_z_c2r(const typename Cx<T>::type *in, T *out, int N, long nlines,
+                      const Plan &pl, const typename Cx<T>::type *tw, cudaStream_t s) {
+    return launch_z<T, false>(in, out, N, nlines, pl, tw, s);
+}
+template cudaError_t fft_z_r2c<float>(const float *, float2 *, int, long, const Plan &,
+                                      const float2 *, cudaStream_t);
+template cudaError_t fft_z_r2c<double>(const double *, double2 *, int, long, const Plan &,
+                                       const double2 *, cudaStream_t);
+template cudaError_t fft_z_c2r<float>(const float2 *, float *, int, long, const Plan &,
+                                      const float2 *, cudaStream_t);
+template cudaError_t fft_z_c2r<double>(const double2 *, double *, int, long, const Plan &,
+                                       const double2 *, cudaStream_t);
+
+}  // namespace nsk

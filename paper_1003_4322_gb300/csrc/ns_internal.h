@@ -1,0 +1,99 @@
+// ns_internal.h -- host-side declarations shared by the translation units of
+// libns (not part of the public ABI, which is include/ns.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "fft_core.cuh"
+
+namespace nsk {
+
+// Optional per-launch timing: when a Tracer is active, every kernel launch of
+// a step is bracketed by a pair of CUDA events on the launching stream.
+struct Tracer {
+    struct Rec {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    cudaStream_t s = nullptr;
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    cudaError_t err = cudaSuccess;
+    cudaEvent_t take() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) {
+                err = r;
+                return nullptr;
+            }
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void begin(const char *name) {
+        Rec r{name, take(), nullptr};
+        if (r.a) cudaEventRecord(r.a, s);
+        recs.push_back(r);
+    }
+    void end() {
+        cudaEvent_t b = take();
+        if (b) cudaEventRecord(b, s);
+        recs.back().b = b;
+    }
+    ~Tracer() {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
+
+// Run one launch expression, timed when tr is non-null; yields its error.
+#define NSK_TIMED(tr, name, expr)                         \
+    ([&]() -> cudaError_t {                               \
+        if (tr) (tr)->begin(name);                        \
+        cudaError_t _te = (expr);                         \
+        if (tr) (tr)->end();                              \
+        return _te;                                       \
+    }())
+
+// Radix plan for a line of length n = 2^a 3^b (false if n has another factor).
+bool make_plan(int n, Plan *pl);
+
+// Is N a supported grid size (2^a 3^b, even, >= 8)?
+bool supported_n(int n);
+
+// Twiddle table exp(-2 pi i t / n), t < n, computed on the host in FP64 and
+// uploaded (rounded once to float for the FP32 path).
+template <typename T> typename Cx<T>::type *make_twiddles(int n, cudaError_t *err);
+
+// Batched FFT along a strided axis.  Element e (< pl.n) of column c (< ncols)
+// of plane b (< planes) sits at base + b * plane_stride + e * es + c (in
+// complex units); columns are contiguous.  dir = -1 forward, +1 inverse.
+// in == out is allowed (in place).  ct = columns per CTA.
+template <typename T>
+cudaError_t fft_strided(const typename Cx<T>::type *in, typename Cx<T>::type *out, long ncols,
+                        long es, long ps_in, long ps_out, int planes, int dir, const Plan &pl,
+                        const typename Cx<T>::type *tw, int ntab, int ct, cudaStream_t s);
+
+// Real-to-complex transform along z (contiguous) of nlines lines of N reals
+// into nlines lines of N/2+1 complex values; pl is the plan of length N/2 and
+// tw the table of length N.
+template <typename T>
+cudaError_t fft_z_r2c(const T *in, typename Cx<T>::type *out, int N, long nlines, const Plan &pl,
+                      const typename Cx<T>::type *tw, cudaStream_t s);
+
+// Complex-to-real transform along z: nlines lines of N/2+1 complex values into
+// nlines lines of N reals (real parts of the kz = 0 and N/2 entries only).
+template <typename T>
+cudaError_t fft_z_c2r(const typename Cx<T>::type *in, T *out, int N, long nlines,
+                      const Plan &pl, const typename Cx<T>::type *tw, cudaStream_t s);
+
+// Columns per CTA of the strided pass for a given precision and length.
+int default_ct(int elem_bytes, int n);
+
+// Opt a kernel into more than 48 KB of dynamic shared memory (once).
+cudaError_t allow_smem(const void *kernel, size_t bytes);
+
+}  // namespace nsk

@@ -1,0 +1,330 @@
+// plain.cu -- the unfused, unpruned ("plain") form of the solver's pointwise
+// steps on full half-layout arrays [3][N][N][N/2+1] (Sec. 2, Eqs. 1-2): the
+// vorticity i k x a, the cross product u x w on the grid, and the projected,
+// dealiased, forced integrating-factor RK2 update; plus the deterministic
+// FP64 reductions for energy, enstrophy and the shell spectrum (the global
+// quantities and spectra of Sec. 3).
+#include "ns_internal.h"
+#include "plain.h"
+
+namespace nsk {
+
+__device__ __forceinline__ int wavenum(int i, int n) { return 2 * i < n ? i : i - n; }
+
+// ---------------------------------------------------------------- curl
+
+template <typename T>
+__global__ void k_curl(const typename Cx<T>::type *__restrict__ a, typename Cx<T>::type *__restrict__ w,
+                       int n, long M) {
+    typedef typename Cx<T>::type C;
+    const int nh = n / 2 + 1;
+    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(m % nh);
+        const int iy = (int)((m / nh) % n);
+        const int ix = (int)(m / ((long)nh * n));
+        const T kx = (T)wavenum(ix, n), ky = (T)wavenum(iy, n), kzz = (T)kz;
+        const C ax = a[m], ay = a[M + m], az = a[2 * M + m];
+        // w = i k x a
+        w[m] = cmul_i<1>(csub(cscale(az, ky), cscale(ay, kzz)));
+        w[M + m] = cmul_i<1>(csub(cscale(ax, kzz), cscale(az, kx)));
+        w[2 * M + m] = cmul_i<1>(csub(cscale(ay, kx), cscale(ax, ky)));
+    }
+}
+
+// ---------------------------------------------------------------- cross product
+
+// c = u x w at every grid point; c may alias u.
+template <typename T>
+__global__ void k_cross(T *u, const T *__restrict__ w, long V) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x) {
+        const T ux = u[i], uy = u[V + i], uz = u[2 * V + i];
+        const T wx = w[i], wy = w[V + i], wz = w[2 * V + i];
+        u[i] = uy * wz - uz * wy;
+        u[V + i] = uz * wx - ux * wz;
+        u[2 * V + i] = ux * wy - uy * wx;
+    }
+}
+
+// ---------------------------------------------------------------- update
+
+// ABC forcing coefficients at signed k (closed form of
+// f = F (sin kf z + cos kf y, sin kf x + cos kf z, sin kf y + cos kf x)).
+template <typename C, typename T>
+__device__ __forceinline__ void abc_forcing(int kx, int ky, int kz, int kf, T F, C &fx, C &fy, C &fz) {
+    const T h = F * (T)0.5;
+    if (kf <= 0) return;
+    if (kx == 0 && ky == 0 && kz == kf) {          // e^{i kf z}: sin -> -i/2, cos -> 1/2
+        fx = cadd(fx, mkc((T)0, -h));
+        fy = cadd(fy, mkc(h, (T)0));
+    }
+    if (kx == 0 && kz == 0 && (ky == kf || ky == -kf)) {
+        fx = cadd(fx, mkc(h, (T)0));
+        fz = cadd(fz, mkc((T)0, ky > 0 ? -h : h));
+    }
+    if (ky == 0 && kz == 0 && (kx == kf || kx == -kf)) {
+        fy = cadd(fy, mkc((T)0, kx > 0 ? -h : h));
+        fz = cadd(fz, mkc(h, (T)0));
+    }
+}
+
+__device__ __forceinline__ bool kept(int kx, int ky, int kz, int n, int dealias) {
+    int m = abs(kx);
+    m = max(m, abs(ky));
+    m = max(m, abs(kz));
+    if (3 * m >= n) return false;
+    if (dealias == 1 && 9L * (kx * kx + ky * ky + kz * kz) >= (long)n * n) return false;
+    return true;
+}
+
+// Stage 1: a1 = E (a + dt N);  stage 2: a = E a / 2 + (a1 + dt N) / 2, with
+// N = P Pi (nl / N^3) + f_hat; every mode outside Pi (and k = 0) set to 0.
+template <typename T>
+__global__ void k_update(typename Cx<T>::type *__restrict__ a, typename Cx<T>::type *__restrict__ a1,
+                         const typename Cx<T>::type *__restrict__ nl, const T *__restrict__ etab,
+                         int n, long M, UpdateArgs ua) {
+    typedef typename Cx<T>::type C;
+    const int nh = n / 2 + 1;
+    const T inv = (T)(1.0 / ((double)n * n * n));
+    const T dt = (T)ua.dt, F = (T)ua.force_amp;
+    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(m % nh);
+        const int iy = (int)((m / nh) % n);
+        const int ix = (int)(m / ((long)nh * n));
+        const int kx = wavenum(ix, n), ky = wavenum(iy, n);
+        const int k2 = kx * kx + ky * ky + kz * kz;
+        C o0 = czero<C>(), o1 = czero<C>(), o2 = czero<C>();
+        if (kept(kx, ky, kz, n, ua.dealias) && k2 > 0) {
+            C vx = cscale(nl[m], inv), vy = cscale(nl[M + m], inv), vz = cscale(nl[2 * M + m], inv);
+            const T fkx = (T)kx, fky = (T)ky, fkz = (T)kz, ik2 = (T)1 / (T)k2;
+            const C kv = cadd(cadd(cscale(vx, fkx), cscale(vy, fky)), cscale(vz, fkz));
+            vx = csub(vx, cscale(kv, fkx * ik2));
+            vy = csub(vy, cscale(kv, fky * ik2));
+            vz = csub(vz, cscale(kv, fkz * ik2));
+            abc_forcing(kx, ky, kz, ua.force_k, F, vx, vy, vz);
+            const T e = etab[k2];
+            if (ua.stage == 1) {
+                o0 = cscale(cadd(a[m], cscale(vx, dt)), e);
+                o1 = cscale(cadd(a[M + m], cscale(vy, dt)), e);
+                o2 = cscale(cadd(a[2 * M + m], cscale(vz, dt)), e);
+            } else {
+                const T he = (T)0.5 * e, h = (T)0.5;
+                o0 = cadd(cscale(a[m], he), cscale(cadd(a1[m], cscale(vx, dt)), h));
+                o1 = cadd(cscale(a[M + m], he), cscale(cadd(a1[M + m], cscale(vy, dt)), h));
+                o2 = cadd(cscale(a[2 * M + m], he), cscale(cadd(a1[2 * M + m], cscale(vz, dt)), h));
+            }
+        }
+        C *dst = ua.stage == 1 ? a1 : a;
+        dst[m] = o0;
+        dst[M + m] = o1;
+        dst[2 * M + m] = o2;
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+
+// Block tree sum of two doubles in a fixed order (deterministic).
+__device__ __forceinline__ void block_sum2(double &s0, double &s1, double *sh) {
+    const int t = threadIdx.x;
+    sh[2 * t] = s0;
+    sh[2 * t + 1] = s1;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            sh[2 * t] += sh[2 * (t + w)];
+            sh[2 * t + 1] += sh[2 * (t + w) + 1];
+        }
+        __syncthreads();
+    }
+    s0 = sh[0];
+    s1 = sh[1];
+}
+
+// Per-block partial energy and enstrophy of a half-layout state.  Block b
+// owns the contiguous chunk [b*chunk, (b+1)*chunk) of modes.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_energy_partials(const typename Cx<T>::type *__restrict__ a, int n, long M, long chunk, double *part) {
+    __shared__ double sh[512];
+    const int nh = n / 2 + 1;
+    double e = 0.0, om = 0.0;
+    const long beg = blockIdx.x * chunk, end = min(M, beg + chunk);
+    for (long m = beg + threadIdx.x; m < end; m += blockDim.x) {
+        const int kz = (int)(m % nh);
+        const int iy = (int)((m / nh) % n);
+        const int ix = (int)(m / ((long)nh * n));
+        const double kx = wavenum(ix, n), ky = wavenum(iy, n);
+        const double w = (kz == 0 || 2 * kz == n) ? 0.5 : 1.0;   // 1/2 * multiplicity
+        double a2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const double re = (double)a[c * M + m].x, im = (double)a[c * M + m].y;
+            a2 += re * re + im * im;
+        }
+        e += w * a2;
+        om += w * a2 * (kx * kx + ky * ky + (double)kz * kz);
+    }
+    block_sum2(e, om, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = e;
+        part[2 * blockIdx.x + 1] = om;
+    }
+}
+
+// Sum nparts partials in a fixed order, append (E, Omega) to the run's ring
+// buffer series[cap][2] at slot counter % cap, bump the counter, and raise
+// bit 0 of *flags if E is not finite.
+__global__ void __launch_bounds__(256)
+k_energy_final(const double *__restrict__ part, int nparts, double *series, int cap,
+               unsigned long long *counter, int *flags) {
+    __shared__ double sh[512];
+    double e = 0.0, om = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        e += part[2 * i];
+        om += part[2 * i + 1];
+    }
+    block_sum2(e, om, sh);
+    if (threadIdx.x == 0) {
+        const unsigned long long c = *counter;
+        series[2 * (c % cap)] = e;
+        series[2 * (c % cap) + 1] = om;
+        *counter = c + 1;
+        if (!isfinite(e)) atomicOr(flags, 1);
+    }
+}
+
+// Shell spectrum: block K sums the modes with round-half-up(|k|) = K, i.e.
+// K^2 - K + 1 <= |k|^2 <= K^2 + K (|k|^2 = 0 for K = 0), enumerating (kx, ky)
+// pairs and the kz interval they allow.  Per-thread sums in a fixed order and
+// a fixed tree make the result deterministic.  Acc maps signed (kx, ky, kz)
+// with kz >= 0 to the squared magnitude of the 3-vector coefficient, or 0.
+template <class Acc>
+__global__ void __launch_bounds__(256)
+k_shell_spectrum(Acc acc, int n, int nbins, double *spec, double *ens) {
+    __shared__ double sh[512];
+    const int K = blockIdx.x;
+    if (K >= nbins) return;
+    const long lo = K == 0 ? 0 : (long)K * K - K + 1, hi = (long)K * K + K;
+    const int kmin = -n / 2, kmax = n / 2 - 1;
+    const int lim = K;   // |k_i| <= K inside the shell
+    const int a0 = max(kmin, -lim), a1 = min(kmax, lim);
+    const long side = a1 - a0 + 1;
+    double e = 0.0, om = 0.0;
+    for (long pidx = threadIdx.x; pidx < side * side; pidx += blockDim.x) {
+        const int kx = a0 + (int)(pidx / side), ky = a0 + (int)(pidx % side);
+        const long r2 = (long)kx * kx + (long)ky * ky;
+        if (r2 > hi) continue;
+        long zlo2 = lo - r2;
+        int z0 = 0;
+        if (zlo2 > 0) {
+            z0 = (int)ceil(sqrt((double)zlo2));
+            while ((long)z0 * z0 < zlo2) z0++;
+            while (z0 > 0 && (long)(z0 - 1) * (z0 - 1) >= zlo2) z0--;
+        }
+        int z1 = (int)floor(sqrt((double)(hi - r2)));
+        while ((long)(z1 + 1) * (z1 + 1) <= hi - r2) z1++;
+        while (z1 >= 0 && (long)z1 * z1 > hi - r2) z1--;
+        z1 = min(z1, n / 2);
+        for (int kz = z0; kz <= z1; kz++) {
+            const double w = (kz == 0 || 2 * kz == n) ? 0.5 : 1.0;
+            const double de = w * acc(kx, ky, kz);
+            e += de;
+            om += de * (double)(r2 + (long)kz * kz);
+        }
+    }
+    block_sum2(e, om, sh);
+    if (threadIdx.x == 0) {
+        spec[K] = e;
+        ens[K] = om;
+    }
+}
+
+template <typename T> struct HalfAcc {
+    const typename Cx<T>::type *a;
+    int n;
+    long M;
+    __device__ double operator()(int kx, int ky, int kz) const {
+        const long m = ((long)((kx + n) % n) * n + (ky + n) % n) * (n / 2 + 1) + kz;
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const double re = (double)a[c * M + m].x, im = (double)a[c * M + m].y;
+            s += re * re + im * im;
+        }
+        return s;
+    }
+};
+
+// ---------------------------------------------------------------- launchers
+
+static unsigned grid_for(long work, int threads) {
+    long b = (work + threads - 1) / threads;
+    if (b > 152L * 32) b = 152L * 32;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+cudaError_t plain_curl(const typename Cx<T>::type *a, typename Cx<T>::type *w, int n, cudaStream_t s) {
+    const long M = (long)n * n * (n / 2 + 1);
+    k_curl<T><<<grid_for(M, 256), 256, 0, s>>>(a, w, n, M);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t plain_cross(T *u, const T *w, int n, cudaStream_t s) {
+    const long V = (long)n * n * n;
+    k_cross<T><<<grid_for(V, 256), 256, 0, s>>>(u, w, V);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t plain_update(typename Cx<T>::type *a, typename Cx<T>::type *a1,
+                         const typename Cx<T>::type *nl, const T *etab, int n, const UpdateArgs &ua,
+                         cudaStream_t s) {
+    const long M = (long)n * n * (n / 2 + 1);
+    k_update<T><<<grid_for(M, 256), 256, 0, s>>>(a, a1, nl, etab, n, M, ua);
+    return cudaGetLastError();
+}
+
+int energy_nparts(int n) {
+    const long M = (long)n * n * (n / 2 + 1);
+    long np = (M + 4095) / 4096;
+    if (np > 1024) np = 1024;
+    return (int)(np < 1 ? 1 : np);
+}
+
+template <typename T>
+cudaError_t plain_energy_partials(const typename Cx<T>::type *a, int n, double *part, cudaStream_t s) {
+    const long M = (long)n * n * (n / 2 + 1);
+    const int np = energy_nparts(n);
+    const long chunk = (M + np - 1) / np;
+    k_energy_partials<T><<<np, 256, 0, s>>>(a, n, M, chunk, part);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t plain_spectrum(const typename Cx<T>::type *a, int n, int nbins, double *spec, double *ens,
+                           cudaStream_t s) {
+    HalfAcc<T> acc{a, n, (long)n * n * (n / 2 + 1)};
+    k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, n, nbins, spec, ens);
+    return cudaGetLastError();
+}
+
+cudaError_t energy_final(const double *part, int nparts, double *series, int cap,
+                         unsigned long long *counter, int *flags, cudaStream_t s) {
+    k_energy_final<<<1, 256, 0, s>>>(part, nparts, series, cap, counter, flags);
+    return cudaGetLastError();
+}
+
+#define NSK_INST(T)                                                                                \
+    template cudaError_t plain_curl<T>(const Cx<T>::type *, Cx<T>::type *, int, cudaStream_t);    \
+    template cudaError_t plain_cross<T>(T *, const T *, int, cudaStream_t);                       \
+    template cudaError_t plain_update<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,       \
+                                         const T *, int, const UpdateArgs &, cudaStream_t);       \
+    template cudaError_t plain_energy_partials<T>(const Cx<T>::type *, int, double *, cudaStream_t); \
+    template cudaError_t plain_spectrum<T>(const Cx<T>::type *, int, int, double *, double *,     \
+                                           cudaStream_t);
+NSK_INST(float)
+NSK_INST(double)
+#undef NSK_INST
+
+}  // namespace nsk

@@ -1,0 +1,31 @@
+// plain.h -- launchers of the plain-form pointwise kernels and reductions.
+#pragma once
+#include "ns_internal.h"
+
+namespace nsk {
+
+struct UpdateArgs {
+    int stage;        // 1 or 2
+    double dt;
+    double force_amp;
+    int force_k;
+    int dealias;
+};
+
+template <typename T>
+cudaError_t plain_curl(const typename Cx<T>::type *a, typename Cx<T>::type *w, int n, cudaStream_t s);
+template <typename T> cudaError_t plain_cross(T *u, const T *w, int n, cudaStream_t s);
+template <typename T>
+cudaError_t plain_update(typename Cx<T>::type *a, typename Cx<T>::type *a1,
+                         const typename Cx<T>::type *nl, const T *etab, int n, const UpdateArgs &ua,
+                         cudaStream_t s);
+int energy_nparts(int n);
+template <typename T>
+cudaError_t plain_energy_partials(const typename Cx<T>::type *a, int n, double *part, cudaStream_t s);
+template <typename T>
+cudaError_t plain_spectrum(const typename Cx<T>::type *a, int n, int nbins, double *spec, double *ens,
+                           cudaStream_t s);
+cudaError_t energy_final(const double *part, int nparts, double *series, int cap,
+                         unsigned long long *counter, int *flags, cudaStream_t s);
+
+}  // namespace nsk

@@ -1,0 +1,158 @@
+"""GPU parity of the solver step (Sec. 2, Eqs. 1-2) against the FP64 oracle,
+through the C ABI: FP64 (plain form) to 1e-12 relative L2, FP32 to 2e-5,
+plus invariants the method fixes at any size (exact Beltrami decay,
+divergence-free state, Taylor-Green energy and enstrophy, determinism)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1003_4322_gb300 import inputs
+from tests.spectral_ref import rel_l2, wavenumbers
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 2e-5}
+
+
+def _solver(ns, prec, **run):
+    from paper_1003_4322_gb300.solver import Solver
+    return Solver([run], prec=prec)
+
+
+def _oracle_run(a0, run, steps):
+    return oracle.step(a0, oracle.Params(n=run["n"], nu=run.get("nu", 0.0), dt=run["dt"],
+                                         force_amp=run.get("force_amp", 0.0),
+                                         force_k=run.get("force_k", 0),
+                                         dealias=run.get("dealias", 0)), steps)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_config1_32cubed_ten_steps(ns, prec):
+    """ABC + random perturbation on 2 <= |k| <= 4 (rms 0.1), nu = 0.01,
+    dt = 1e-3, 10 RK2 steps on 32^3."""
+    run = dict(n=32, nu=0.01, dt=1e-3)
+    a0 = inputs.config1_state(32, seed=1)
+    ref = _oracle_run(a0, run, 10)
+    with _solver(ns, prec, **run) as s:
+        s.set_state(a0)
+        s.step(10)
+        got = s.get_state()
+    assert rel_l2(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,dealias,forced", [(8, 0, False), (12, 0, True), (16, 1, False),
+                                              (24, 0, True), (48, 1, True), (96, 0, True)])
+def test_sizes_dealias_forcing(ns, prec, n, dealias, forced):
+    run = dict(n=n, nu=0.02, dt=2e-3, dealias=dealias)
+    if forced:
+        run.update(force_amp=0.5, force_k=min(3, (n - 1) // 3))
+    a0 = inputs.turbulence_state(n, seed=n + 7, dealias=dealias)
+    steps = 3
+    ref = _oracle_run(a0, run, steps)
+    with _solver(ns, prec, **run) as s:
+        s.set_state(a0)
+        s.step(steps)
+        got = s.get_state()
+    assert rel_l2(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_beltrami_decays_exactly(ns, prec):
+    n, nu, dt, steps = 32, 0.05, 0.01, 20
+    with _solver(ns, prec, n=n, nu=nu, dt=dt) as s:
+        s.set_state(inputs.abc_state(n))
+        s.step(steps)
+        E, Om, spec = s.energy_spectrum()
+    want = 1.5 * math.exp(-2 * nu * dt * steps)
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    assert abs(E - want) < tol and abs(Om - want) < tol
+    assert abs(spec[1] - want) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_state_is_divergence_free_and_dealiased(ns, prec):
+    n = 48
+    with _solver(ns, prec, n=n, nu=0.01, dt=1e-3, force_amp=0.5, force_k=3) as s:
+        s.set_state(inputs.random_hermitian_half(n, 3, 1))   # neither solenoidal nor truncated
+        s.step(2)
+        a = s.get_state()
+    k = wavenumbers(n).astype(float)
+    KX, KY, KZ = np.meshgrid(k, k, np.arange(n // 2 + 1.0), indexing="ij")
+    div = np.abs(KX * a[0] + KY * a[1] + KZ * a[2]).max() / np.abs(a).max()
+    assert div < (1e-13 if prec == "fp64" else 1e-5)
+    outside = 3 * np.maximum(np.maximum(abs(KX), abs(KY)), KZ) >= n
+    assert np.abs(a[:, outside]).max() == 0.0
+
+
+def test_set_get_round_trip_drops_modes_outside_the_kept_set(ns):
+    n = 24
+    a = inputs.random_hermitian_half(n, 3, 3)
+    with _solver(ns, "fp64", n=n, nu=0.0, dt=1e-3) as s:
+        s.set_state(a)
+        b = s.get_state()
+    k = wavenumbers(n)
+    KX, KY, KZ = np.meshgrid(k, k, np.arange(n // 2 + 1), indexing="ij")
+    keep = 3 * np.maximum(np.maximum(abs(KX), abs(KY)), KZ) < n
+    assert np.array_equal(b[:, keep], a[:, keep])
+    assert np.all(b[:, ~keep] == 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_diagnostics_and_series_match_oracle(ns, prec):
+    run = dict(n=32, nu=0.01, dt=1e-3, force_amp=0.5, force_k=3)
+    a0 = inputs.turbulence_state(32, seed=9)
+    with _solver(ns, prec, **run) as s:
+        s.set_state(a0)
+        s.step(4)
+        E, Om, spec = s.energy_spectrum()
+        Es, Os = s.series(count=10)
+        st = s.get_state()
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    rE, rO, rspec = oracle.diagnostics(st)
+    assert abs(E - rE) < tol * rE and abs(Om - rO) < tol * rO
+    assert np.abs(spec - rspec).max() < tol * rE
+    assert len(Es) == 4
+    ref = a0
+    for i in range(4):
+        ref = _oracle_run(ref, run, 1)
+        e_i, o_i, _ = oracle.diagnostics(ref)
+        assert abs(Es[i] - e_i) < 20 * TOL[prec] * e_i
+        assert abs(Os[i] - o_i) < 20 * TOL[prec] * o_i
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_repeated_runs_are_bitwise_identical(ns, prec):
+    run = dict(n=64, nu=0.01, dt=1e-3, force_amp=0.5, force_k=3)
+    a0 = inputs.turbulence_state(64, seed=2)
+    outs = []
+    for _ in range(2):
+        with _solver(ns, prec, **run) as s:
+            s.set_state(a0)
+            s.step(3)
+            outs.append((s.get_state(), s.energy_spectrum()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1][0] == outs[1][1][0] and np.array_equal(outs[0][1][2], outs[1][1][2])
+
+
+def test_taylor_green_256_against_oracle_on_the_64_sublattice(ns):
+    """Config 2's flow at full size (256^3, nu = 1/1600, dt = 2e-3): the GPU
+    FP64 state after 2 steps against the oracle, compared on the grid points
+    of the 64^3 sub-lattice (every 4th point), and the initial invariants."""
+    import torch
+    n, steps = 256, 2
+    run = dict(n=n, nu=1 / 1600, dt=2e-3)
+    a0 = inputs.taylor_green_state(n)
+    with _solver(ns, "fp64", **run) as s:
+        s.set_state(a0)
+        E0, Om0, _ = s.energy_spectrum()
+        s.step(steps)
+        got = s.get_state()
+    assert abs(E0 - 0.125) < 1e-15 and abs(Om0 - 0.375) < 1e-14
+    ref = _oracle_run(a0, run, steps)
+    ug = np.fft.irfftn(got, s=(n, n, n), axes=(1, 2, 3))[:, ::4, ::4, ::4]
+    ur = np.fft.irfftn(ref, s=(n, n, n), axes=(1, 2, 3))[:, ::4, ::4, ::4]
+    assert np.linalg.norm(ug - ur) / np.linalg.norm(ur) < TOL["fp64"]
+    assert rel_l2(got, ref) < TOL["fp64"]
