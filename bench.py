@@ -449,8 +449,23 @@ def main():
     ap.add_argument("--no-fft", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--mode", default="step", choices=["step", "fft"],
+                    help="fft: only the standalone 3-component r2c/c2r stage")
+    ap.add_argument("--fft-n", type=int, default=256)
+    ap.add_argument("--fft-prec", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.mode == "fft":
+        import torch
+
+        from paper_1003_4322_gb300 import _native as nat
+        nat.load()
+        peaks = load_peaks()
+        r = fft_stage(args.fft_n, args.fft_prec)
+        r["r2c_frac"] = r["r2c_gbs"] / peaks["hbm_gbs"]
+        r["c2r_frac"] = r["c2r_gbs"] / peaks["hbm_gbs"]
+        print(json.dumps(r), flush=True)
+        return
     if args.impl == "reference":
         reference(args, w)
     else:

@@ -418,6 +418,7 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
     };
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(fail_cuda(nullptr, e));
+    if ((e = prepare_fft_kernels()) != cudaSuccess) return bail(fail_cuda(nullptr, e));
     if ((e = dalloc(&c->flags, sizeof(int))) != cudaSuccess) return bail(fail_cuda(nullptr, e));
     cudaMemset(c->flags, 0, sizeof(int));
     c->runs.resize(nruns);

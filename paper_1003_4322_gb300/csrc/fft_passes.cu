@@ -71,15 +71,24 @@ int default_ct(int elem_bytes, int n) {
     return ct;
 }
 
+// Raise a kernel's dynamic shared-memory opt-in to the device maximum, once
+// per (device, kernel).  Occupancy depends on what a launch asks for, not on
+// this limit, so one setting serves every launch size.
 cudaError_t allow_smem(const void *kernel, size_t bytes) {
     static std::mutex mu;
-    static std::set<std::pair<const void *, size_t>> done;
+    static std::set<std::pair<int, const void *>> done;
     if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_pair(kernel, bytes);
+    auto key = std::make_pair(dev, kernel);
     if (done.count(key)) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
+    int maxopt = 0;
+    e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > (size_t)maxopt) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt);
     if (e == cudaSuccess) done.insert(key);
     return e;
 }
@@ -308,6 +317,22 @@ cudaError_t fft_z_c2r(const typename Cx<T>::type *in, T *out, int N, long nlines
                       const Plan &pl, const typename Cx<T>::type *tw, cudaStream_t s) {
     return launch_z<T, false>(in, out, N, nlines, pl, tw, s);
 }
+cudaError_t prepare_fft_kernels() {
+    const size_t big = 48 * 1024 + 1;
+    const int Es[] = {4, 6, 8, 9, 12, 16};
+    for (int E : Es) {
+        const void *ks[] = {strided_kernel<float, -1>(E), strided_kernel<float, 1>(E),
+                            strided_kernel<double, -1>(E), strided_kernel<double, 1>(E),
+                            z_kernel<float, true>(E), z_kernel<float, false>(E),
+                            z_kernel<double, true>(E), z_kernel<double, false>(E)};
+        for (const void *k : ks) {
+            cudaError_t e = allow_smem(k, big);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 template cudaError_t fft_z_r2c<float>(const float *, float2 *, int, long, const Plan &,
                                       const float2 *, cudaStream_t);
 template cudaError_t fft_z_r2c<double>(const double *, double2 *, int, long, const Plan &,

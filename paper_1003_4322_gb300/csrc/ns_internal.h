@@ -93,7 +93,12 @@ cudaError_t fft_z_c2r(const typename Cx<T>::type *in, T *out, int N, long nlines
 // Columns per CTA of the strided pass for a given precision and length.
 int default_ct(int elem_bytes, int n);
 
-// Opt a kernel into more than 48 KB of dynamic shared memory (once).
+// Opt a kernel into more than 48 KB of dynamic shared memory (once per
+// device); fails if bytes exceeds the device's opt-in maximum.
 cudaError_t allow_smem(const void *kernel, size_t bytes);
+
+// Opt every transform kernel in up front (called by ns_init, so that nothing
+// of the kind happens while a step is being captured into a graph).
+cudaError_t prepare_fft_kernels();
 
 }  // namespace nsk

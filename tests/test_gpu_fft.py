@@ -139,3 +139,21 @@ def test_full_size_plane_waves_and_round_trip(ns, n, prec):
         assert err < 2 * TOL[prec] * 5
     finally:
         ns.ns_destroy(ctx)
+
+
+def test_sizes_in_any_order_fp64(ns):
+    """Launch sizes that need different amounts of shared memory, larger
+    after smaller after larger, in one process (regression: the dynamic
+    shared-memory opt-in of a kernel must cover every size it is used at)."""
+    import torch
+    for n in (32, 24, 32, 96, 24, 32):
+        a = inputs.random_hermitian_half(n, 1, n)
+        ad = torch.from_numpy(a).cuda()
+        out = torch.empty((1, n, n, n), dtype=torch.float64, device="cuda")
+        ctx = _ctx(ns, "fp64")
+        try:
+            ns.ns_fft_c2r(ctx, n, 1, ad, out)
+            ns.ns_sync(ctx)
+        finally:
+            ns.ns_destroy(ctx)
+        assert _rel(out.cpu().numpy(), oracle.fft3_c2r(a)) < TOL["fp64"]
