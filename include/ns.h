@@ -128,6 +128,28 @@ ns_status ns_fft_r2c(ns_ctx *ctx, int n, int ncomp, const void *in, void *out);
  * (allocated on the first call for that n).  Errors as ns_fft_r2c. */
 ns_status ns_fft_c2r(ns_ctx *ctx, int n, int ncomp, const void *in, void *out);
 
+/* FP32 inverse c2r transform, as ns_fft_c2r for a context of precision
+ * NS_FP32, that allocates nothing.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, such as applications
+ * whose device memory is owned by a caching pool allocator (a raw cudaMalloc
+ * can fail or fragment memory the pool holds) and real-time loops that forbid
+ * allocation after start-up.  No context is needed.
+ *   in:  device pointer, ncomp complex64 fields [ncomp][n][n][n/2+1];
+ *   out: device pointer, ncomp float fields [ncomp][n][n][n];
+ *   cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
+ * Scratch space (one complex field of 128^3 half layout, 8,519,680 bytes)
+ * and a 128-entry twiddle table sit in fixed device arrays inside the library,
+ * which every GPU that loads libns holds until the process exits; n above 128
+ * (or an unsupported n) returns NS_ERR_UNSUPPORTED_N.  The first call on a
+ * device looks up the arrays' device addresses for that device; make that
+ * first call before any stream capture.  Every call shares the same arrays and
+ * overwrites them: calls whose work overlaps on the GPU (other streams, other
+ * threads) race and give wrong results, so serialise them.  The function
+ * calls no cudaMalloc, cudaFree or allocating library routine.  Asynchronous
+ * on cuda_stream.  Errors: NS_ERR_ARG (null pointer, ncomp < 1),
+ * NS_ERR_UNSUPPORTED_N, NS_ERR_CUDA. */
+ns_status ns_fft_c2r_noalloc(int n, int ncomp, const void *in, void *out, void *cuda_stream);
+
 /* Energy E = 1/2 sum |a|^2, enstrophy Omega = 1/2 sum |k|^2 |a|^2 (sums
  * over the full spectrum) and the shell spectrum E(K), K = round-half-up
  * |k|, of one run's current state, accumulated in FP64 (the reductions for

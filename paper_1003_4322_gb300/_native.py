@@ -22,7 +22,8 @@ NS_FP64, NS_FP32 = 0, 1
 # every symbol include/ns.h declares
 SYMBOLS = ("ns_init", "ns_set_state", "ns_get_state", "ns_step", "ns_fft_r2c", "ns_fft_c2r",
            "ns_energy_spectrum", "ns_nbins", "ns_series", "ns_series_capacity",
-           "ns_kernel_census", "ns_sync", "ns_last_error", "ns_status_str", "ns_destroy")
+           "ns_kernel_census", "ns_sync", "ns_last_error", "ns_status_str", "ns_destroy",
+           "ns_fft_c2r_noalloc")
 
 
 class NsError(RuntimeError):
@@ -63,6 +64,7 @@ def load(path: str = LIB_PATH):
         "ns_step": ([P, I], I),
         "ns_fft_r2c": ([P, I, I, P, P], I),
         "ns_fft_c2r": ([P, I, I, P, P], I),
+        "ns_fft_c2r_noalloc": ([I, I, P, P, P], I),
         "ns_energy_spectrum": ([P, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D)], I),
         "ns_nbins": ([I], I),
         "ns_series": ([P, I, I, P, P, ctypes.POINTER(I)], I),
@@ -161,6 +163,17 @@ def ns_fft_r2c(ctx, n: int, ncomp: int, inp, out) -> None:
 
 def ns_fft_c2r(ctx, n: int, ncomp: int, inp, out) -> None:
     _check(load().ns_fft_c2r(ctx, n, ncomp, _ptr(inp), _ptr(out)), "ns_fft_c2r", ctx)
+
+
+def ns_fft_c2r_noalloc(n: int, ncomp: int, inp, out, stream=None) -> None:
+    """FP32 c2r that allocates nothing (fixed in-library scratch, n <= 128)."""
+    if stream is None:
+        s = None
+    elif hasattr(stream, "cuda_stream"):
+        s = ctypes.c_void_p(stream.cuda_stream)
+    else:
+        s = ctypes.c_void_p(int(stream))
+    _check(load().ns_fft_c2r_noalloc(n, ncomp, _ptr(inp), _ptr(out), s), "ns_fft_c2r_noalloc")
 
 
 def ns_energy_spectrum(ctx, run: int, n: int):
