@@ -19,7 +19,7 @@ def load():
 
 
 def __getattr__(name):
-    if name.startswith("ns_") or name in ("NS_FP32", "NS_FP64", "NsError", "SYMBOLS"):
+    if name.startswith("ns_") or name.startswith("NS_") or name in ("NsError", "SYMBOLS"):
         from . import _native
         return getattr(_native, name)
     if name in ("Solver",):

@@ -181,50 +181,55 @@ template <typename C> NSK_DEV C ldg_c(const C *p) { return __ldg(p); }
 // direction uses its conjugate.
 template <int R, int E, int DIR, typename C, class Ld, class St>
 NSK_DEV void stage(C (&v)[E], int slot, int T, int n, int p, const C *__restrict__ tw,
-                   int ntab, Ld ld, St st, bool sync_mid) {
+                   int ntab, Ld ld, St st, bool sync_mid, bool active = true) {
     const int nR = n / R;
+    if (active) {
 #pragma unroll
-    for (int b = 0; b < E / R; b++) {
-        const int i = slot + b * T;
+        for (int b = 0; b < E / R; b++) {
+            const int i = slot + b * T;
 #pragma unroll
-        for (int q = 0; q < R; q++) v[b * R + q] = ld(i + q * nR);
-    }
-    const int tstride = ntab / (p * R);
-#pragma unroll
-    for (int b = 0; b < E / R; b++) {
-        if (p > 1) {
-            const int k = (slot + b * T) % p;
-#pragma unroll
-            for (int q = 1; q < R; q++) {
-                const C w = ldg_c(tw + q * k * tstride);
-                v[b * R + q] = DIR < 0 ? cmul(v[b * R + q], w) : cmulc(v[b * R + q], w);
-            }
+            for (int q = 0; q < R; q++) v[b * R + q] = ld(i + q * nR);
         }
-        Dft<R, DIR, C>::run(&v[b * R]);
+        const int tstride = ntab / (p * R);
+#pragma unroll
+        for (int b = 0; b < E / R; b++) {
+            if (p > 1) {
+                const int k = (slot + b * T) % p;
+#pragma unroll
+                for (int q = 1; q < R; q++) {
+                    const C w = ldg_c(tw + q * k * tstride);
+                    v[b * R + q] = DIR < 0 ? cmul(v[b * R + q], w) : cmulc(v[b * R + q], w);
+                }
+            }
+            Dft<R, DIR, C>::run(&v[b * R]);
+        }
     }
     if (sync_mid) __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int b = 0; b < E / R; b++) {
-        const int i = slot + b * T;
-        const int k = i % p;
-        const int j = (i - k) * R + k;
+        for (int b = 0; b < E / R; b++) {
+            const int i = slot + b * T;
+            const int k = i % p;
+            const int j = (i - k) * R + k;
 #pragma unroll
-        for (int q = 0; q < R; q++) st(j + q * p, v[b * R + q]);
+            for (int q = 0; q < R; q++) st(j + q * p, v[b * R + q]);
+        }
     }
 }
 
 template <int E, int DIR, typename C, class Ld, class St>
 NSK_DEV void stage_dispatch(int R, C (&v)[E], int slot, int T, int n, int p,
-                            const C *__restrict__ tw, int ntab, Ld ld, St st, bool sync_mid) {
+                            const C *__restrict__ tw, int ntab, Ld ld, St st, bool sync_mid,
+                            bool active = true) {
     switch (R) {
-    case 2: if constexpr (E % 2 == 0) stage<2, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid); break;
-    case 3: if constexpr (E % 3 == 0) stage<3, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid); break;
-    case 4: if constexpr (E % 4 == 0) stage<4, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid); break;
-    case 6: if constexpr (E % 6 == 0) stage<6, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid); break;
-    case 8: if constexpr (E % 8 == 0) stage<8, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid); break;
-    case 9: if constexpr (E % 9 == 0) stage<9, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid); break;
-    case 12: if constexpr (E % 12 == 0) stage<12, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid); break;
-    case 16: if constexpr (E % 16 == 0) stage<16, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid); break;
+    case 2: if constexpr (E % 2 == 0) stage<2, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid, active); break;
+    case 3: if constexpr (E % 3 == 0) stage<3, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid, active); break;
+    case 4: if constexpr (E % 4 == 0) stage<4, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid, active); break;
+    case 6: if constexpr (E % 6 == 0) stage<6, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid, active); break;
+    case 8: if constexpr (E % 8 == 0) stage<8, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid, active); break;
+    case 9: if constexpr (E % 9 == 0) stage<9, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid, active); break;
+    case 12: if constexpr (E % 12 == 0) stage<12, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid, active); break;
+    case 16: if constexpr (E % 16 == 0) stage<16, E, DIR>(v, slot, T, n, p, tw, ntab, ld, st, sync_mid, active); break;
     default: break;
     }
 }
@@ -237,12 +242,14 @@ NSK_DEV void stage_dispatch(int R, C (&v)[E], int slot, int T, int n, int p,
 // The first radix of every plan is E (make_plan picks the largest radix
 // first), so stage 0 is compiled for radix E with span 1 (no twiddles); the
 // later stages share one dispatch whose store target (shared memory or GS)
-// is a uniform runtime choice.  Ends with the last stores issued and, if
-// LAST_SMEM, synchronised.
+// is a uniform runtime choice.  A thread with active == false skips every
+// load, butterfly and store but takes every barrier, so blocks in which only
+// some thread groups have a line stay in step.  Ends with the last stores
+// issued and, if LAST_SMEM, synchronised.
 template <int E, int DIR, bool FIRST_SMEM, bool LAST_SMEM, bool INPLACE, typename C,
           class GL, class SL, class SS, class GS>
-NSK_DEV void fft_line(const Plan &pl, int slot, const C *__restrict__ tw, int ntab, GL gl, SL sl,
-                      SS ss, GS gs) {
+NSK_DEV void fft_line_impl(bool active, const Plan &pl, int slot, const C *__restrict__ tw,
+                           int ntab, GL gl, SL sl, SS ss, GS gs) {
     C v[E];
     const int T = pl.n / E;
     const int nst = pl.nst;
@@ -254,7 +261,7 @@ NSK_DEV void fft_line(const Plan &pl, int slot, const C *__restrict__ tw, int nt
         };
         const bool wr_smem = !last || LAST_SMEM;
         const bool mid = (FIRST_SMEM && wr_smem) || (last && INPLACE);
-        stage<E, E, DIR>(v, slot, T, pl.n, 1, tw, ntab, gl, st, mid);
+        stage<E, E, DIR>(v, slot, T, pl.n, 1, tw, ntab, gl, st, mid, active);
         if (wr_smem) __syncthreads();
     }
     int p = E;
@@ -266,10 +273,24 @@ NSK_DEV void fft_line(const Plan &pl, int slot, const C *__restrict__ tw, int nt
         };
         const bool wr_smem = !last || LAST_SMEM;
         const int R = pl.rad(s);
-        stage_dispatch<E, DIR>(R, v, slot, T, pl.n, p, tw, ntab, sl, st, wr_smem);
+        stage_dispatch<E, DIR>(R, v, slot, T, pl.n, p, tw, ntab, sl, st, wr_smem, active);
         if (wr_smem) __syncthreads();
         p *= R;
     }
+}
+
+template <int E, int DIR, bool FIRST_SMEM, bool LAST_SMEM, bool INPLACE, typename C,
+          class GL, class SL, class SS, class GS>
+NSK_DEV void fft_line(const Plan &pl, int slot, const C *__restrict__ tw, int ntab, GL gl, SL sl,
+                      SS ss, GS gs) {
+    fft_line_impl<E, DIR, FIRST_SMEM, LAST_SMEM, INPLACE>(true, pl, slot, tw, ntab, gl, sl, ss, gs);
+}
+
+template <int E, int DIR, bool FIRST_SMEM, bool LAST_SMEM, typename C, class GL, class SL,
+          class SS, class GS>
+NSK_DEV void fft_line_masked(bool active, const Plan &pl, int slot, const C *__restrict__ tw,
+                             int ntab, GL gl, SL sl, SS ss, GS gs) {
+    fft_line_impl<E, DIR, FIRST_SMEM, LAST_SMEM, false>(active, pl, slot, tw, ntab, gl, sl, ss, gs);
 }
 
 }  // namespace nsk

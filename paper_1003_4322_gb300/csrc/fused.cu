@@ -1,22 +1,547 @@
-// fused.cu -- placeholder until the fused form lands.
+// fused.cu -- the fused, pruned FP32 form of the RK2 step (Sec. 2, Eqs. 1-2).
+//
+// Only the modes the 2/3 rule keeps (|kx|, |ky|, kz <= K, K = ceil(N/3) - 1)
+// are ever stored or read, and the physical fields u and w never reach HBM.
+// One RK2 stage is five transform passes and an update:
+//
+//   A  x inverse + curl:  S[c][ikx][iky][kz] (3 comps)  -> A[f][iky][x][kz] (6: u, w)
+//   B  y inverse:         A[f][iky][x][kz]              -> B[f][y][x][kz]
+//   C  z c2r, u x w, z r2c (shared memory only):  B (6 fields) -> B (3 fields, in place)
+//   D  y forward:         B[f][y][x][kz]                -> D[f][x][iky][kz] (kept ky only)
+//   E  x forward:         D[f][x][iky][kz]              -> N[c][ikx][iky][kz] (kept kx only)
+//   update: 1/N^3, mask, projection P(k), ABC forcing, integrating-factor RK2
+//           stage, and (stage 2) the FP64 energy / enstrophy partial sums.
+//
+// Every strided pass sees its columns flattened and contiguous, so a CTA tile
+// is always ct consecutive complex values of one row (128 bytes for ct = 16).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "fused.h"
+#include "plain.h"
+#include "reduce.cuh"
 
 namespace nsk {
-bool fused_enabled() { return false; }
-cudaError_t fused_alloc(FusedRun &, const ns_run_params &, const float2 *, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+bool fused_enabled() { return true; }
+
+__device__ __forceinline__ int fz_full_signed(int e, int n) { return 2 * e < n ? e : e - n; }
+__device__ __forceinline__ int fz_compact_signed(int i, int Mx, int K) { return i <= K ? i : i - Mx; }
+// full index e (0..n-1) -> compact index, or -1 when the wavenumber is not kept
+__device__ __forceinline__ int fz_compact(int e, int n, int K, int Mx) {
+    if (e <= K) return e;
+    if (e >= n - K) return e - n + Mx;
+    return -1;
 }
-void fused_free(FusedRun &) {}
-cudaError_t fused_set_state(FusedRun &, const double2 *, int, void *, size_t, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+struct FzPass {
+    const float2 *in;
+    float2 *out;
+    long ncols;          // flattened columns per field plane
+    long ifs, irs;       // input field / row strides (complex elements)
+    long ofs, ors, obs;  // output field / row strides; outer stride of a column
+    int nfields;         // output fields handled by the grid
+    int Mz, K, Mx;
+};
+
+// One CTA: field f, ct consecutive columns; lanes run along the columns.
+// IN_C: the input rows are compact (only kept wavenumbers stored), the
+// others are read as zero.  OUT_C: only the kept output rows are stored.
+// CURL: pass A, whose fields 3..5 are the vorticity i k x a of the input.
+template <int E, int DIR, bool IN_C, bool OUT_C, bool CURL>
+__global__ void __launch_bounds__(512)
+k_fused_strided(FzPass ps, Plan pl, const float2 *__restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int n = pl.n;
+    const int ct = blockDim.x / (n / E);
+    const int c = threadIdx.x % ct, slot = threadIdx.x / ct;
+    const int f = blockIdx.x % ps.nfields;
+    const long tile = blockIdx.x / ps.nfields;
+    const long col = tile * ct + c;
+    const bool valid = col < ps.ncols;
+    const long ou = valid ? col / ps.Mz : 0;
+    const long iz = valid ? col % ps.Mz : 0;
+    const int K = ps.K, Mx = ps.Mx;
+    auto gl = [&](int e) -> float2 {
+        const int r = IN_C ? fz_compact(e, n, K, Mx) : e;
+        if (!valid || r < 0) return make_float2(0.f, 0.f);
+        if constexpr (!CURL) {
+            return ps.in[f * ps.ifs + r * ps.irs + col];
+        } else {
+            const float2 *b = ps.in + r * ps.irs + col;
+            if (f < 3) return b[f * ps.ifs];
+            const float kx = (float)fz_full_signed(e, n);
+            const float ky = (float)fz_compact_signed((int)ou, Mx, K);
+            const float kz = (float)iz;
+            float2 p, q;
+            float sp, sq;
+            if (f == 3) { p = b[2 * ps.ifs]; sp = ky; q = b[ps.ifs]; sq = kz; }       // i(ky az - kz ay)
+            else if (f == 4) { p = b[0]; sp = kz; q = b[2 * ps.ifs]; sq = kx; }       // i(kz ax - kx az)
+            else { p = b[ps.ifs]; sp = kx; q = b[0]; sq = ky; }                       // i(kx ay - ky ax)
+            const float re = sp * p.x - sq * q.x, im = sp * p.y - sq * q.y;
+            return make_float2(-im, re);
+        }
+    };
+    auto gs = [&](int e, float2 v) {
+        const int r = OUT_C ? fz_compact(e, n, K, Mx) : e;
+        if (!valid || r < 0) return;
+        ps.out[f * ps.ofs + r * ps.ors + ou * ps.obs + iz] = v;
+    };
+    auto sl = [&](int e) -> float2 { return sm[e * ct + c]; };
+    auto ss = [&](int e, float2 v) { sm[e * ct + c] = v; };
+    fft_line<E, DIR, false, false, false>(pl, slot, tw, n, gl, sl, ss, gs);
 }
-cudaError_t fused_get_state(FusedRun &, double2 *, int, void *, size_t, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+// Line stride (complex elements) of a shared-memory line in pass C: room for
+// n values plus the skew of one element per 16, rounded to 8 (mod 16) so that
+// the lines a warp touches fall in alternate halves of the banks.
+__host__ __device__ inline int fz_line_stride(int n) {
+    int ls = n + (n >> 4) + 1;
+    while (ls % 16 != 8) ls++;
+    return ls;
 }
-cudaError_t fused_step(FusedRun &, double *, int, unsigned long long *, int *, cudaStream_t, Tracer *) {
-    return cudaErrorNotSupported;
+
+// Pass C.  One CTA holds L (y, x) lines, each with the six fields u, w.  Per
+// field: c2r along z through one complex FFT of length n = N/2 (even/odd
+// packing), which leaves the N real samples in shared memory; then u x w at
+// every point; then r2c of the three products and the kept kz < Mz written
+// back over fields 0..2 of the same lines.
+template <int E>
+__global__ void __launch_bounds__(256)
+k_fused_z(float2 *buf, long fs, int N, int Mz, long nlines, int L, Plan pl,
+          const float2 *__restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int n = N / 2, Tn = n / E;
+    const int g = threadIdx.x / Tn, slot = threadIdx.x % Tn;
+    const int l = g / 6, f = g % 6;
+    const long line = (long)blockIdx.x * L + l;
+    const bool valid = line < nlines;
+    const int LS = fz_line_stride(n);
+    float2 *ls = sm + (long)g * LS;
+    auto sl = [&](int e) -> float2 { return ls[e + (e >> 4)]; };
+    auto ss = [&](int e, float2 v) { ls[e + (e >> 4)] = v; };
+
+    // c2r packing: Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]),
+    // with X[k] = 0 for k >= Mz and the real parts of X[0], X[n].
+    const float2 *src = buf + f * fs + line * Mz;
+    for (int k = slot; k < n; k += Tn) {
+        float2 xk = make_float2(0.f, 0.f), xm = make_float2(0.f, 0.f);
+        if (valid && k < Mz) xk = src[k];
+        if (valid && n - k < Mz) xm = src[n - k];
+        if (k == 0) {
+            xk.y = 0.f;
+            xm.y = 0.f;
+        }
+        const float2 xc = cconj(xm);
+        const float2 a = cadd(xk, xc);
+        const float2 wb = cmulc(csub(xk, xc), ldg_c(tw + k));
+        ss(k, cadd(a, cmul_i<1>(wb)));
+    }
+    __syncthreads();
+    fft_line<E, +1, true, true, false>(pl, slot, tw, N, sl, sl, ss, ss);
+
+    // u x w at the 2n points of each line (complex element m holds points 2m, 2m+1)
+    for (int idx = threadIdx.x; idx < L * n; idx += blockDim.x) {
+        const int l2 = idx / n, m = idx % n;
+        const int o = m + (m >> 4);
+        float2 *base = sm + (long)(6 * l2) * LS + o;
+        const float2 ux = base[0], uy = base[LS], uz = base[2 * LS];
+        const float2 wx = base[3 * LS], wy = base[4 * LS], wz = base[5 * LS];
+        base[0] = make_float2(uy.x * wz.x - uz.x * wy.x, uy.y * wz.y - uz.y * wy.y);
+        base[LS] = make_float2(uz.x * wx.x - ux.x * wz.x, uz.y * wx.y - ux.y * wz.y);
+        base[2 * LS] = make_float2(ux.x * wy.x - uy.x * wx.x, ux.y * wy.y - uy.y * wx.y);
+    }
+    __syncthreads();
+    fft_line_masked<E, -1, true, true>(f < 3, pl, slot, tw, N, sl, sl, ss, ss);
+
+    // r2c unpacking of the kept kz:
+    // X[k] = (Z[k] + conj Z[n-k])/2 - i W^k (Z[k] - conj Z[n-k])/2
+    if (f < 3 && valid) {
+        float2 *dst = buf + f * fs + line * Mz;
+        for (int k = slot; k < Mz; k += Tn) {
+            const float2 zk = sl(k);
+            const float2 zc = cconj(sl(k == 0 ? 0 : n - k));
+            const float2 ev = cscale(cadd(zk, zc), 0.5f);
+            const float2 od = cmul_i<-1>(cscale(csub(zk, zc), 0.5f));
+            dst[k] = cadd(ev, cmul(od, ldg_c(tw + k)));
+        }
+    }
 }
-cudaError_t fused_spectrum(FusedRun &, int, double *, double *, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+// 1/N^3, projection, forcing and the RK2 stage on the compact state; at
+// stage 2 also the per-block FP64 energy and enstrophy partial sums of the
+// new state (grid-stride with a fixed grid: deterministic).
+struct FzUpdate {
+    int n, K, Mx, Mz;
+    int stage, dealias, force_k;
+    float dt, force_amp;
+    long M;   // compact modes per component
+};
+
+__device__ __forceinline__ void fz_forcing(int kx, int ky, int kz, int kf, float F, float2 &fx,
+                                           float2 &fy, float2 &fz) {
+    const float h = 0.5f * F;
+    if (kf <= 0) return;
+    if (kx == 0 && ky == 0 && kz == kf) {
+        fx = cadd(fx, make_float2(0.f, -h));
+        fy = cadd(fy, make_float2(h, 0.f));
+    }
+    if (kx == 0 && kz == 0 && (ky == kf || ky == -kf)) {
+        fx = cadd(fx, make_float2(h, 0.f));
+        fz = cadd(fz, make_float2(0.f, ky > 0 ? -h : h));
+    }
+    if (ky == 0 && kz == 0 && (kx == kf || kx == -kf)) {
+        fy = cadd(fy, make_float2(0.f, kx > 0 ? -h : h));
+        fz = cadd(fz, make_float2(h, 0.f));
+    }
 }
+
+__global__ void __launch_bounds__(256)
+k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__restrict__ nl,
+               const float *__restrict__ etab, FzUpdate u, double *part) {
+    __shared__ double sh[512];
+    const long M = u.M;
+    const float inv = (float)(1.0 / ((double)u.n * u.n * u.n));
+    double e_acc = 0.0, o_acc = 0.0;
+    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(m % u.Mz);
+        const int iky = (int)((m / u.Mz) % u.Mx);
+        const int ikx = (int)(m / ((long)u.Mz * u.Mx));
+        const int kx = fz_compact_signed(ikx, u.Mx, u.K), ky = fz_compact_signed(iky, u.Mx, u.K);
+        const int k2 = kx * kx + ky * ky + kz * kz;
+        bool keep = k2 > 0;
+        if (u.dealias == 1 && 9L * k2 >= (long)u.n * u.n) keep = false;
+        float2 o0 = make_float2(0.f, 0.f), o1 = o0, o2 = o0;
+        if (keep) {
+            float2 vx = cscale(nl[m], inv), vy = cscale(nl[M + m], inv), vz = cscale(nl[2 * M + m], inv);
+            const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz, ik2 = 1.f / (float)k2;
+            const float2 kv = cadd(cadd(cscale(vx, fkx), cscale(vy, fky)), cscale(vz, fkz));
+            vx = csub(vx, cscale(kv, fkx * ik2));
+            vy = csub(vy, cscale(kv, fky * ik2));
+            vz = csub(vz, cscale(kv, fkz * ik2));
+            fz_forcing(kx, ky, kz, u.force_k, u.force_amp, vx, vy, vz);
+            const float e = etab[k2];
+            if (u.stage == 1) {
+                o0 = cscale(cadd(a[m], cscale(vx, u.dt)), e);
+                o1 = cscale(cadd(a[M + m], cscale(vy, u.dt)), e);
+                o2 = cscale(cadd(a[2 * M + m], cscale(vz, u.dt)), e);
+            } else {
+                const float he = 0.5f * e;
+                o0 = cadd(cscale(a[m], he), cscale(cadd(a1[m], cscale(vx, u.dt)), 0.5f));
+                o1 = cadd(cscale(a[M + m], he), cscale(cadd(a1[M + m], cscale(vy, u.dt)), 0.5f));
+                o2 = cadd(cscale(a[2 * M + m], he), cscale(cadd(a1[2 * M + m], cscale(vz, u.dt)), 0.5f));
+            }
+        }
+        float2 *dst = u.stage == 1 ? a1 : a;
+        dst[m] = o0;
+        dst[M + m] = o1;
+        dst[2 * M + m] = o2;
+        if (u.stage == 2) {
+            const double w = kz == 0 ? 0.5 : 1.0;
+            const double a2 = (double)o0.x * o0.x + (double)o0.y * o0.y + (double)o1.x * o1.x +
+                              (double)o1.y * o1.y + (double)o2.x * o2.x + (double)o2.y * o2.y;
+            e_acc += w * a2;
+            o_acc += w * a2 * (double)k2;
+        }
+    }
+    if (u.stage == 2) {
+        block_sum2(e_acc, o_acc, sh);
+        if (threadIdx.x == 0) {
+            part[2 * blockIdx.x] = e_acc;
+            part[2 * blockIdx.x + 1] = o_acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- state transfer
+
+// cnt full kx planes starting at kx0 (FP64 half layout, plane = n (n/2+1)
+// modes) -> compact rows; modes outside the sphere (dealias = 1) dropped.
+__global__ void k_fz_load(const double2 *__restrict__ src, float2 *__restrict__ dst, int kx0, int cnt,
+                          int n, int K, int Mx, int Mz, int dealias) {
+    const int nh = n / 2 + 1;
+    const long total = (long)cnt * Mx * Mz;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(i % Mz);
+        const int iky = (int)((i / Mz) % Mx);
+        const int p = (int)(i / ((long)Mz * Mx));
+        const int fx = kx0 + p;
+        const int ikx = fz_compact(fx, n, K, Mx);
+        if (ikx < 0) continue;
+        const int ky = fz_compact_signed(iky, Mx, K);
+        const int fy = ky >= 0 ? ky : ky + n;
+        const int kx = fz_full_signed(fx, n);
+        double2 v = src[(long)p * n * nh + (long)fy * nh + kz];
+        if (dealias == 1 && 9L * (kx * kx + ky * ky + kz * kz) >= (long)n * n) v = make_double2(0.0, 0.0);
+        dst[((long)ikx * Mx + iky) * Mz + kz] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// compact -> cnt full kx planes starting at kx0 (zeros outside the kept set)
+__global__ void k_fz_store(const float2 *__restrict__ src, double2 *__restrict__ dst, int kx0, int cnt,
+                           int n, int K, int Mx, int Mz) {
+    const int nh = n / 2 + 1;
+    const long total = (long)cnt * n * nh;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(i % nh);
+        const int fy = (int)((i / nh) % n);
+        const int p = (int)(i / ((long)nh * n));
+        const int ikx = fz_compact(kx0 + p, n, K, Mx);
+        const int iky = fz_compact(fy, n, K, Mx);
+        double2 v = make_double2(0.0, 0.0);
+        if (ikx >= 0 && iky >= 0 && kz < Mz) {
+            const float2 s = src[((long)ikx * Mx + iky) * Mz + kz];
+            v = make_double2((double)s.x, (double)s.y);
+        }
+        dst[i] = v;
+    }
+}
+
+struct CompactAcc {
+    const float2 *a;
+    int K, Mx, Mz;
+    long M;
+    __device__ double operator()(int kx, int ky, int kz) const {
+        if (kx > K || kx < -K || ky > K || ky < -K || kz >= Mz) return 0.0;
+        const int ikx = kx >= 0 ? kx : kx + Mx, iky = ky >= 0 ? ky : ky + Mx;
+        const long m = ((long)ikx * Mx + iky) * Mz + kz;
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const double re = (double)a[c * M + m].x, im = (double)a[c * M + m].y;
+            s += re * re + im * im;
+        }
+        return s;
+    }
+};
+
+// ---------------------------------------------------------------- host side
+
+static unsigned grid_of(long work, int threads, long cap) {
+    long b = (work + threads - 1) / threads;
+    b = std::min(b, cap);
+    return (unsigned)std::max(b, 1L);
+}
+
+template <int E, int DIR, bool IN_C, bool OUT_C, bool CURL>
+static const void *strided_k() {
+    return (const void *)k_fused_strided<E, DIR, IN_C, OUT_C, CURL>;
+}
+
+template <int DIR, bool IN_C, bool OUT_C, bool CURL>
+static const void *strided_for(int E) {
+    switch (E) {
+    case 4: return strided_k<4, DIR, IN_C, OUT_C, CURL>();
+    case 6: return strided_k<6, DIR, IN_C, OUT_C, CURL>();
+    case 8: return strided_k<8, DIR, IN_C, OUT_C, CURL>();
+    case 9: return strided_k<9, DIR, IN_C, OUT_C, CURL>();
+    case 12: return strided_k<12, DIR, IN_C, OUT_C, CURL>();
+    case 16: return strided_k<16, DIR, IN_C, OUT_C, CURL>();
+    }
+    return nullptr;
+}
+
+static const void *z_for(int E) {
+    switch (E) {
+    case 4: return (const void *)k_fused_z<4>;
+    case 6: return (const void *)k_fused_z<6>;
+    case 8: return (const void *)k_fused_z<8>;
+    case 9: return (const void *)k_fused_z<9>;
+    case 12: return (const void *)k_fused_z<12>;
+    case 16: return (const void *)k_fused_z<16>;
+    }
+    return nullptr;
+}
+
+cudaError_t prepare_fused_kernels() {
+    const int Es[] = {4, 6, 8, 9, 12, 16};
+    for (int E : Es) {
+        const void *ks[] = {strided_for<+1, true, false, true>(E), strided_for<+1, true, false, false>(E),
+                            strided_for<-1, false, true, false>(E), z_for(E)};
+        for (const void *k : ks) {
+            cudaError_t e = allow_smem(k, 48 * 1024 + 1);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t launch_strided(const void *k, const FzPass &ps, const Plan &pl, const float2 *tw,
+                                  int ct, cudaStream_t s) {
+    if (!k) return cudaErrorInvalidValue;
+    const int T = pl.n / pl.E;
+    const size_t smem = (size_t)pl.n * ct * sizeof(float2);
+    cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const long tiles = (ps.ncols + ct - 1) / ct;
+    const long blocks = tiles * ps.nfields;
+    if (blocks > 0x7fffffffL) return cudaErrorInvalidValue;
+    FzPass p = ps;
+    Plan q = pl;
+    void *args[] = {(void *)&p, (void *)&q, (void *)&tw};
+    return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(ct * T), args, smem, s);
+}
+
+static cudaError_t launch_z(FusedRun &f, cudaStream_t s) {
+    const void *k = z_for(f.plH.E);
+    if (!k) return cudaErrorInvalidValue;
+    const int n = f.n / 2, Tn = n / f.plH.E;
+    const int L = std::max(1, 192 / (6 * Tn));
+    const size_t smem = (size_t)6 * L * fz_line_stride(n) * sizeof(float2);
+    cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    const long nlines = (long)f.n * f.n;
+    const long blocks = (nlines + L - 1) / L;
+    float2 *buf = f.bbuf;
+    long fs = (long)f.n * f.n * f.Mz;
+    int N = f.n, Mz = f.Mz;
+    Plan q = f.plH;
+    const float2 *tw = f.tw;
+    void *args[] = {(void *)&buf, (void *)&fs, (void *)&N, (void *)&Mz, (void *)&nlines, (void *)&L,
+                    (void *)&q, (void *)&tw};
+    return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(6 * L * Tn), args, smem, s);
+}
+
+cudaError_t fused_alloc(FusedRun &f, const ns_run_params &p, const float2 *tw, cudaStream_t s) {
+    f.p = p;
+    f.n = p.n;
+    f.K = (p.n - 1) / 3;     // largest k with 3k < n
+    f.Mx = 2 * f.K + 1;
+    f.Mz = f.K + 1;
+    f.tw = tw;
+    if (!make_plan(f.n, &f.plN) || !make_plan(f.n / 2, &f.plH)) return cudaErrorInvalidValue;
+    f.M = (long)f.Mx * f.Mx * f.Mz;
+    const long Aelems = 6L * f.Mx * f.n * f.Mz;          // also holds D (3 fields)
+    const long Belems = 6L * f.n * f.n * f.Mz;           // also holds C (3 fields)
+    cudaError_t e;
+    if ((e = cudaMalloc(&f.a, 3 * f.M * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.a1, 3 * f.M * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.nl, 3 * f.M * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.abuf, Aelems * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.bbuf, Belems * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(f.a, 0, 3 * f.M * sizeof(float2), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(f.a1, 0, 3 * f.M * sizeof(float2), s)) != cudaSuccess) return e;
+    const int nk2 = 3 * f.K * f.K + 1;
+    std::vector<float> h(nk2);
+    for (int k2 = 0; k2 < nk2; k2++) h[k2] = (float)exp(-p.nu * (double)k2 * p.dt);
+    if ((e = cudaMalloc(&f.etab, nk2 * sizeof(float))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(f.etab, h.data(), nk2 * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    f.nparts = (int)std::min<long>(1024, std::max<long>(1, (f.M + 4095) / 4096));
+    f.ct = default_ct(sizeof(float2), f.n);
+    return prepare_fused_kernels();
+}
+
+void fused_free(FusedRun &f) {
+    void *ps[] = {f.a, f.a1, f.nl, f.abuf, f.bbuf, f.etab};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    f.a = f.a1 = f.nl = f.abuf = f.bbuf = nullptr;
+    f.etab = nullptr;
+}
+
+static cudaError_t launch_update(FusedRun &f, const FzUpdate &u, cudaStream_t s) {
+    k_fused_update<<<f.nparts, 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, u, f.part);
+    return cudaGetLastError();
+}
+
+cudaError_t fused_step(FusedRun &f, double *series, int cap, unsigned long long *counter, int *flags,
+                       cudaStream_t s, Tracer *tr) {
+    const int E = f.plN.E, N = f.n, K = f.K, Mx = f.Mx, Mz = f.Mz;
+    const long MxMz = (long)Mx * Mz, NMz = (long)N * Mz;
+    const void *kA = strided_for<+1, true, false, true>(E);
+    const void *kB = strided_for<+1, true, false, false>(E);
+    const void *kDE = strided_for<-1, false, true, false>(E);
+    cudaError_t e;
+    for (int stage = 1; stage <= 2; stage++) {
+        const float2 *src = stage == 1 ? f.a : f.a1;
+        FzPass A{src, f.abuf, MxMz, f.M, MxMz, (long)Mx * NMz, Mz, NMz, 6, Mz, K, Mx};
+        e = NSK_TIMED(tr, "fused_A_x_inverse_curl", launch_strided(kA, A, f.plN, f.tw, f.ct, s));
+        if (e != cudaSuccess) return e;
+        FzPass B{f.abuf, f.bbuf, NMz, (long)Mx * NMz, NMz, (long)N * NMz, NMz, Mz, 6, Mz, K, Mx};
+        e = NSK_TIMED(tr, "fused_B_y_inverse", launch_strided(kB, B, f.plN, f.tw, f.ct, s));
+        if (e != cudaSuccess) return e;
+        e = NSK_TIMED(tr, "fused_C_z_nonlinear", launch_z(f, s));
+        if (e != cudaSuccess) return e;
+        FzPass D{f.bbuf, f.abuf, NMz, (long)N * NMz, NMz, (long)N * MxMz, Mz, MxMz, 3, Mz, K, Mx};
+        e = NSK_TIMED(tr, "fused_D_y_forward", launch_strided(kDE, D, f.plN, f.tw, f.ct, s));
+        if (e != cudaSuccess) return e;
+        FzPass Ep{f.abuf, f.nl, MxMz, (long)N * MxMz, MxMz, f.M, MxMz, Mz, 3, Mz, K, Mx};
+        e = NSK_TIMED(tr, "fused_E_x_forward", launch_strided(kDE, Ep, f.plN, f.tw, f.ct, s));
+        if (e != cudaSuccess) return e;
+        FzUpdate u{N, K, Mx, Mz, stage, f.p.dealias, f.p.force_k, (float)f.p.dt,
+                   (float)f.p.force_amp, f.M};
+        e = NSK_TIMED(tr, "fused_update", launch_update(f, u, s));
+        if (e != cudaSuccess) return e;
+    }
+    return NSK_TIMED(tr, "energy_final", energy_final(f.part, f.nparts, series, cap, counter, flags, s));
+}
+
+cudaError_t fused_set_state(FusedRun &f, const double2 *src, int on_device, void *staging,
+                            size_t staging_bytes, cudaStream_t s) {
+    const int n = f.n, nh = n / 2 + 1;
+    const long plane = (long)n * nh, M = (long)n * plane;
+    const int pc = on_device ? n : (int)std::max<size_t>(1, staging_bytes / (plane * sizeof(double2)));
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(f.a, 0, 3 * f.M * sizeof(float2), s)) != cudaSuccess) return e;
+    const int ranges[2][2] = {{0, f.K + 1}, {n - f.K, n}};
+    for (int c = 0; c < 3; c++) {
+        for (auto &r : ranges) {
+            for (int kx0 = r[0]; kx0 < r[1]; kx0 += pc) {
+                const int cnt = std::min(pc, r[1] - kx0);
+                const double2 *p = src + c * M + (long)kx0 * plane;
+                if (!on_device) {
+                    if ((e = cudaMemcpyAsync(staging, p, cnt * plane * sizeof(double2),
+                                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                        return e;
+                    p = (const double2 *)staging;
+                }
+                const long work = (long)cnt * f.Mx * f.Mz;
+                k_fz_load<<<grid_of(work, 256, 152L * 16), 256, 0, s>>>(p, f.a + c * f.M, kx0, cnt, n, f.K,
+                                                                      f.Mx, f.Mz, f.p.dealias);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                if (!on_device && (e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t fused_get_state(FusedRun &f, double2 *dst, int on_device, void *staging,
+                            size_t staging_bytes, cudaStream_t s) {
+    const int n = f.n, nh = n / 2 + 1;
+    const long plane = (long)n * nh, M = (long)n * plane;
+    const int pc = on_device ? n : (int)std::max<size_t>(1, staging_bytes / (plane * sizeof(double2)));
+    cudaError_t e;
+    for (int c = 0; c < 3; c++) {
+        for (int kx0 = 0; kx0 < n; kx0 += pc) {
+            const int cnt = std::min(pc, n - kx0);
+            double2 *out = dst + c * M + (long)kx0 * plane;
+            double2 *d = on_device ? out : (double2 *)staging;
+            const long work = (long)cnt * plane;
+            k_fz_store<<<grid_of(work, 256, 152L * 16), 256, 0, s>>>(f.a + c * f.M, d, kx0, cnt, n, f.K,
+                                                                   f.Mx, f.Mz);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (!on_device) {
+                if ((e = cudaMemcpyAsync(out, staging, work * sizeof(double2), cudaMemcpyDeviceToHost,
+                                         s)) != cudaSuccess)
+                    return e;
+                if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t fused_spectrum(FusedRun &f, int nbins, double *spec, double *ens, cudaStream_t s) {
+    CompactAcc acc{f.a, f.K, f.Mx, f.Mz, f.M};
+    k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, f.n, nbins, spec, ens);
+    return cudaGetLastError();
+}
+
 }  // namespace nsk

@@ -5,10 +5,24 @@
 
 namespace nsk {
 
+// One run of the fused form.  Compact state layout [c][ikx][iky][kz] with
+// ikx, iky in [0, Mx) (index k for k >= 0, k + Mx for k < 0) and kz in
+// [0, Mz): only the modes the cubic 2/3 rule keeps, |kx|, |ky|, kz <= K.
 struct FusedRun {
-    int n = 0;
-    int nparts = 0;
-    double *part = nullptr;
+    ns_run_params p{};
+    int n = 0, K = 0, Mx = 0, Mz = 0;
+    long M = 0;                  // compact modes per component, Mx * Mx * Mz
+    int ct = 16;                 // columns per CTA of the strided passes
+    Plan plN{}, plH{};           // plans of length n (x, y) and n/2 (z)
+    const float2 *tw = nullptr;  // exp(-2 pi i t / n), t < n (owned by the context)
+    float2 *a = nullptr;         // state
+    float2 *a1 = nullptr;        // first-stage state
+    float2 *nl = nullptr;        // unnormalised transform of u x w (compact)
+    float2 *abuf = nullptr;      // pass A output (6 fields), reused for pass D (3)
+    float2 *bbuf = nullptr;      // pass B output (6 fields), pass C in place (3)
+    float *etab = nullptr;       // exp(-nu k^2 dt) by integer k^2 <= 3 K^2
+    int nparts = 0;              // energy partial sums (update kernel blocks)
+    double *part = nullptr;      // [nparts][2], owned by the context
 };
 
 bool fused_enabled();
