@@ -100,6 +100,25 @@ def kernel_model(name, n, prec):
         return 9 * V * es, 9 * V
     if name == "update":
         return 7.5 * 3 * M * 2 * es, 3 * M * 20
+    # fused form (FP32 complex = 8 bytes; only the kept modes move)
+    K = (n - 1) // 3
+    Mx, Mz = 2 * K + 1, K + 1
+    S = Mx * Mx * Mz            # compact modes per component
+    Ax = Mx * n * Mz            # pass A / D field size
+    Bx = n * n * Mz             # pass B / C field size
+    cb = 8
+    if name == "fused_A_x_inverse_curl":
+        return (3 * S + 6 * Ax) * cb, 6 * Mx * Mz * f_line
+    if name == "fused_B_y_inverse":
+        return (6 * Ax + 6 * Bx) * cb, 6 * n * Mz * f_line
+    if name == "fused_C_z_nonlinear":
+        return (6 * Bx + 3 * Bx) * cb, n * n * (9 * f_zline + 9 * n)
+    if name == "fused_D_y_forward":
+        return (3 * Bx + 3 * Ax) * cb, 3 * n * Mz * f_line
+    if name == "fused_E_x_forward":
+        return (3 * Ax + 3 * S) * cb, 3 * Mx * Mz * f_line
+    if name == "fused_update":
+        return 10.5 * S * cb, 3 * S * 30   # reads N, a (and a1 at stage 2), writes 3
     return 0, 0
 
 
@@ -198,8 +217,9 @@ def time_form(w, prec, a0, steps, warmup, census_steps, dist):
     clk = clocks.stop()
     E, O = s.series(count=steps)
     census = nat.ns_kernel_census(s.ctx, census_steps) if census_steps > 0 else []
+    desc = nat.ns_describe_run(s.ctx, 0)
     state = s.get_state()
-    return dict(solver=s, ms=ms, clocks=clk, census=census, state=state, E=E, O=O)
+    return dict(solver=s, ms=ms, clocks=clk, census=census, state=state, E=E, O=O, desc=desc)
 
 
 def roofline_of(census, w, prec, census_steps, peaks, sm_mhz):
@@ -368,6 +388,7 @@ def ours(args, w):
                 "unit": "steps/s", "ms_per_step": c["ms"] / args.steps,
                 "rel_l2_fp32_vs_fp64": rel_l2(fp32, fp64),
                 "after_steps": warmup + args.steps + census_steps, "roofline": croof,
+                "execution": c["desc"],
                 "kernels": [{"name": n, "launches": l, "ms": t} for n, l, t in c["census"]]}
         c["solver"].close()
 
@@ -390,7 +411,8 @@ def ours(args, w):
         "config": {"workload": args.workload, "description": w["desc"], "n": w["n"],
                    "nu": w["nu"], "dt": w["dt"], "form": "plain FP64" if w["prec"] == "fp64"
                    else "fused FP32", "parallelism": f"replicas x{world}",
-                   "l2": "working set above 129 MB L2 (no flush needed)"},
+                   "l2": "working set above 129 MB L2 (no flush needed)",
+                   "execution": main["desc"]},
         "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
         "e2e": ee, "cpu_baseline": cpu, "clocks": clk or None,
         "kernels": [{"name": n, "launches": l, "ms": t} for n, l, t in main["census"]],
@@ -453,8 +475,13 @@ def main():
                     help="fft: only the standalone 3-component r2c/c2r stage")
     ap.add_argument("--fft-n", type=int, default=256)
     ap.add_argument("--fft-prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default=None, choices=["fp32", "fp64"],
+                    help="override the workload's headline form")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.prec and args.prec != w["prec"]:
+        w["prec"] = args.prec
+        w["companion"] = None
     if args.mode == "fft":
         import torch
 

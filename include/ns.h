@@ -188,6 +188,14 @@ ns_status ns_kernel_census(ns_ctx *ctx, int nsteps, ns_kernel_time *out, int max
 /* Wait for all queued work and report any sticky or device-side error. */
 ns_status ns_sync(ns_ctx *ctx);
 
+/* JSON description of how one run is executed: its form, sizes and, for the
+ * fused form, the radix split and tile the autotuner chose for each pass
+ * (ns_init runs each pass with a few candidate configurations on the run's
+ * own buffers and keeps the fastest, per N, for the life of the process).
+ * Writes at most len bytes including the terminating zero.  Errors:
+ * NS_ERR_ARG. */
+ns_status ns_describe_run(ns_ctx *ctx, int run, char *out, int len);
+
 /* Detail of the last CUDA failure the context recorded (CUDA error name,
  * message and source location), or "" if none.  Owned by the context. */
 const char *ns_last_error(ns_ctx *ctx);

@@ -23,7 +23,7 @@ NS_FP64, NS_FP32 = 0, 1
 SYMBOLS = ("ns_init", "ns_set_state", "ns_get_state", "ns_step", "ns_fft_r2c", "ns_fft_c2r",
            "ns_energy_spectrum", "ns_nbins", "ns_series", "ns_series_capacity",
            "ns_kernel_census", "ns_sync", "ns_last_error", "ns_status_str", "ns_destroy",
-           "ns_fft_c2r_noalloc")
+           "ns_fft_c2r_noalloc", "ns_describe_run")
 
 
 class NsError(RuntimeError):
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         "ns_sync": ([P], I),
         "ns_status_str": ([I], ctypes.c_char_p),
         "ns_last_error": ([P], ctypes.c_char_p),
+        "ns_describe_run": ([P, I, ctypes.c_char_p, I], I),
         "ns_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
@@ -202,6 +203,14 @@ def ns_kernel_census(ctx, nsteps: int):
     _check(load().ns_kernel_census(ctx, nsteps, arr, 64, ctypes.byref(cnt)), "ns_kernel_census", ctx)
     return [(arr[i].name.decode(), arr[i].launches, arr[i].total_ms)
             for i in range(min(cnt.value, 64))]
+
+
+def ns_describe_run(ctx, run: int = 0) -> dict:
+    """How a run is executed (form, sizes, autotuned per-pass configuration)."""
+    import json
+    buf = ctypes.create_string_buffer(2048)
+    _check(load().ns_describe_run(ctx, run, buf, 2048), "ns_describe_run", ctx)
+    return json.loads(buf.value.decode())
 
 
 def ns_sync(ctx) -> None:

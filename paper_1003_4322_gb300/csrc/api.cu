@@ -395,6 +395,24 @@ int ns_series_capacity(void) { return kSeriesCap; }
 
 const char *ns_last_error(ns_ctx *c) { return c ? c->last_error : ""; }
 
+ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
+    if (!c || run < 0 || run >= (int)c->runs.size() || !out || len < 1) return NS_ERR_ARG;
+    const Run &r = c->runs[run];
+    if (use_fused(c)) {
+        char tune[512];
+        fused_describe(r.fz, tune, sizeof(tune));
+        snprintf(out, len,
+                 "{\"form\": \"fused FP32\", \"n\": %d, \"K\": %d, \"state_modes\": %ld, "
+                 "\"passes\": %s}",
+                 r.n, r.fz.K, 3 * r.fz.M, tune);
+    } else {
+        snprintf(out, len, "{\"form\": \"plain %s\", \"n\": %d, \"cols_per_cta\": %d}",
+                 c->prec == NS_FP64 ? "FP64" : "FP32", r.n,
+                 default_ct(c->prec == NS_FP64 ? 16 : 8, r.n));
+    }
+    return NS_OK;
+}
+
 ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda_stream,
                   ns_ctx **out) {
     if (!out) return NS_ERR_ARG;

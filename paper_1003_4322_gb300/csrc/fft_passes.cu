@@ -33,7 +33,15 @@ bool make_plan(int n, Plan *pl) {
     else if (a >= 2) E = 12;
     else if (a == 1) E = 6;
     else E = b >= 2 ? 9 : 3;
-    if (E == 3 || E == 2) return false;
+    return make_plan_e(n, E, pl);
+}
+
+bool make_plan_e(int n, int E, Plan *pl) {
+    int a, b, rest;
+    if (n < 4) return false;
+    factor23(n, a, b, rest);
+    if (rest != 1 || n % E != 0) return false;
+    if (E != 4 && E != 6 && E != 8 && E != 9 && E != 12 && E != 16) return false;
     static const int cand[] = {16, 12, 9, 8, 6, 4, 3, 2};
     pl->n = n;
     pl->E = E;

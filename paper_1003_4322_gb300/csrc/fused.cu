@@ -15,9 +15,12 @@
 // Every strided pass sees its columns flattened and contiguous, so a CTA tile
 // is always ct consecutive complex values of one row (128 bytes for ct = 16).
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "fused.h"
@@ -128,18 +131,27 @@ k_fused_z(float2 *buf, long fs, int N, int Mz, long nlines, int L, Plan pl,
 
     // c2r packing: Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]),
     // with X[k] = 0 for k >= Mz and the real parts of X[0], X[n].
+    // The n/Tn = E iterations are unrolled so that all 2E loads of a thread
+    // are in flight together.
     const float2 *src = buf + f * fs + line * Mz;
-    for (int k = slot; k < n; k += Tn) {
-        float2 xk = make_float2(0.f, 0.f), xm = make_float2(0.f, 0.f);
-        if (valid && k < Mz) xk = src[k];
-        if (valid && n - k < Mz) xm = src[n - k];
+    float2 xk[E], xm[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        const int k = slot + j * Tn;
+        xk[j] = (valid && k < Mz) ? src[k] : make_float2(0.f, 0.f);
+        xm[j] = (valid && n - k < Mz) ? src[n - k] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        const int k = slot + j * Tn;
+        float2 a0 = xk[j], am = xm[j];
         if (k == 0) {
-            xk.y = 0.f;
-            xm.y = 0.f;
+            a0.y = 0.f;
+            am.y = 0.f;
         }
-        const float2 xc = cconj(xm);
-        const float2 a = cadd(xk, xc);
-        const float2 wb = cmulc(csub(xk, xc), ldg_c(tw + k));
+        const float2 xc = cconj(am);
+        const float2 a = cadd(a0, xc);
+        const float2 wb = cmulc(csub(a0, xc), ldg_c(tw + k));
         ss(k, cadd(a, cmul_i<1>(wb)));
     }
     __syncthreads();
@@ -373,7 +385,7 @@ cudaError_t prepare_fused_kernels() {
 
 static cudaError_t launch_strided(const void *k, const FzPass &ps, const Plan &pl, const float2 *tw,
                                   int ct, cudaStream_t s) {
-    if (!k) return cudaErrorInvalidValue;
+    if (!k || ct < 1 || ct * (pl.n / pl.E) > 512) return cudaErrorInvalidValue;
     const int T = pl.n / pl.E;
     const size_t smem = (size_t)pl.n * ct * sizeof(float2);
     cudaError_t e = allow_smem(k, smem);
@@ -387,11 +399,12 @@ static cudaError_t launch_strided(const void *k, const FzPass &ps, const Plan &p
     return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(ct * T), args, smem, s);
 }
 
-static cudaError_t launch_z(FusedRun &f, cudaStream_t s) {
-    const void *k = z_for(f.plH.E);
+static cudaError_t launch_z(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
+    const void *k = z_for(cfg.pl.E);
     if (!k) return cudaErrorInvalidValue;
-    const int n = f.n / 2, Tn = n / f.plH.E;
-    const int L = std::max(1, 192 / (6 * Tn));
+    const int n = f.n / 2, Tn = n / cfg.pl.E;
+    const int L = cfg.ct;
+    if (L < 1 || 6 * L * Tn > 256) return cudaErrorInvalidValue;
     const size_t smem = (size_t)6 * L * fz_line_stride(n) * sizeof(float2);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
@@ -400,11 +413,133 @@ static cudaError_t launch_z(FusedRun &f, cudaStream_t s) {
     float2 *buf = f.bbuf;
     long fs = (long)f.n * f.n * f.Mz;
     int N = f.n, Mz = f.Mz;
-    Plan q = f.plH;
+    Plan q = cfg.pl;
     const float2 *tw = f.tw;
-    void *args[] = {(void *)&buf, (void *)&fs, (void *)&N, (void *)&Mz, (void *)&nlines, (void *)&L,
+    int LL = L;
+    void *args[] = {(void *)&buf, (void *)&fs, (void *)&N, (void *)&Mz, (void *)&nlines, (void *)&LL,
                     (void *)&q, (void *)&tw};
     return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(6 * L * Tn), args, smem, s);
+}
+
+// Pass descriptors of one RK2 stage reading the state src.
+static void pass_descs(const FusedRun &f, const float2 *src, FzPass &A, FzPass &B, FzPass &D, FzPass &Ep) {
+    const int N = f.n, K = f.K, Mx = f.Mx, Mz = f.Mz;
+    const long MxMz = (long)Mx * Mz, NMz = (long)N * Mz;
+    A = FzPass{src, f.abuf, MxMz, f.M, MxMz, (long)Mx * NMz, Mz, NMz, 6, Mz, K, Mx};
+    B = FzPass{f.abuf, f.bbuf, NMz, (long)Mx * NMz, NMz, (long)N * NMz, NMz, Mz, 6, Mz, K, Mx};
+    D = FzPass{f.bbuf, f.abuf, NMz, (long)N * NMz, NMz, (long)N * MxMz, Mz, MxMz, 3, Mz, K, Mx};
+    Ep = FzPass{f.abuf, f.nl, MxMz, (long)N * MxMz, MxMz, f.M, MxMz, Mz, 3, Mz, K, Mx};
+}
+
+static cudaError_t run_pass(FusedRun &f, int which, const PassCfg &cfg, const FzPass &ps, cudaStream_t s) {
+    const int E = cfg.pl.E;
+    const void *k = which == 0 ? strided_for<+1, true, false, true>(E)
+                  : which == 1 ? strided_for<+1, true, false, false>(E)
+                               : strided_for<-1, false, true, false>(E);
+    return launch_strided(k, ps, cfg.pl, f.tw, cfg.ct, s);
+}
+
+// ---------------------------------------------------------------- autotuner
+
+// Candidate radix splits (elements per thread) for a line of length n.
+static std::vector<Plan> plan_candidates(int n) {
+    std::vector<Plan> out;
+    const int Es[] = {16, 12, 9, 8, 6, 4};
+    for (int E : Es) {
+        Plan p;
+        if (make_plan_e(n, E, &p) && p.nst <= 4) out.push_back(p);
+    }
+    return out;
+}
+
+struct TunedCfgs {
+    PassCfg s[4];   // A, B, D, E
+    PassCfg c;      // pass C (ct = lines per CTA)
+};
+
+// Time `launch` (after one warm-up) over `reps` launches; returns ms per launch
+// or a negative number if it failed.
+template <class F> static float time_launch(F launch, cudaStream_t s, int reps) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1.f;
+    }
+    float ms = -1.f;
+    if (launch() == cudaSuccess && cudaEventRecord(a, s) == cudaSuccess) {
+        bool ok = true;
+        for (int i = 0; i < reps && ok; i++) ok = launch() == cudaSuccess;
+        if (ok && cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+            ms /= reps;
+        else
+            ms = -1.f;
+    }
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+// Choose, per pass, the radix split E and the tile (columns per CTA for the
+// strided passes, lines per CTA for pass C) that run fastest on this run's
+// own buffers; results are kept per N for the life of the process.
+static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
+    static std::mutex mu;
+    static std::map<int, TunedCfgs> cache;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(f.n);
+        if (it != cache.end()) {
+            for (int i = 0; i < 4; i++) f.sp[i] = it->second.s[i];
+            f.zc = it->second.c;
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    const int reps = 3;
+    FzPass P[4];
+    pass_descs(f, f.a, P[0], P[1], P[2], P[3]);
+    const int which[4] = {0, 1, 2, 2};
+    for (int i = 0; i < 4; i++) {
+        float best = -1.f;
+        for (const Plan &pl : plan_candidates(f.n)) {
+            const int T = pl.n / pl.E;
+            for (int ct = 4; ct <= 16; ct *= 2) {
+                if (ct * T > 512 || (ct * T < 32 && ct < 16)) continue;
+                PassCfg cfg{pl, ct};
+                const float ms = time_launch([&]() { return run_pass(f, which[i], cfg, P[i], s); }, s, reps);
+                if (ms > 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    f.sp[i] = cfg;
+                }
+            }
+        }
+        if (best < 0.f) return cudaErrorInvalidValue;
+    }
+    {
+        float best = -1.f;
+        for (const Plan &pl : plan_candidates(f.n / 2)) {
+            const int Tn = pl.n / pl.E;
+            for (int L = 1; 6 * L * Tn <= 256; L *= 2) {
+                PassCfg cfg{pl, L};
+                const float ms = time_launch([&]() { return launch_z(f, cfg, s); }, s, reps);
+                if (ms > 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    f.zc = cfg;
+                }
+            }
+        }
+        if (best < 0.f) return cudaErrorInvalidValue;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    TunedCfgs t;
+    for (int i = 0; i < 4; i++) t.s[i] = f.sp[i];
+    t.c = f.zc;
+    cache[f.n] = t;
+    return cudaSuccess;
 }
 
 cudaError_t fused_alloc(FusedRun &f, const ns_run_params &p, const float2 *tw, cudaStream_t s) {
@@ -433,8 +568,11 @@ cudaError_t fused_alloc(FusedRun &f, const ns_run_params &p, const float2 *tw, c
     if ((e = cudaMemcpy(f.etab, h.data(), nk2 * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
     f.nparts = (int)std::min<long>(1024, std::max<long>(1, (f.M + 4095) / 4096));
-    f.ct = default_ct(sizeof(float2), f.n);
-    return prepare_fused_kernels();
+    if ((e = prepare_fused_kernels()) != cudaSuccess) return e;
+    const int ct = default_ct(sizeof(float2), f.n);
+    for (int i = 0; i < 4; i++) f.sp[i] = PassCfg{f.plN, ct};
+    f.zc = PassCfg{f.plH, std::max(1, 192 / (6 * (f.n / 2 / f.plH.E)))};
+    return fused_autotune(f, s);
 }
 
 void fused_free(FusedRun &f) {
@@ -452,34 +590,39 @@ static cudaError_t launch_update(FusedRun &f, const FzUpdate &u, cudaStream_t s)
 
 cudaError_t fused_step(FusedRun &f, double *series, int cap, unsigned long long *counter, int *flags,
                        cudaStream_t s, Tracer *tr) {
-    const int E = f.plN.E, N = f.n, K = f.K, Mx = f.Mx, Mz = f.Mz;
-    const long MxMz = (long)Mx * Mz, NMz = (long)N * Mz;
-    const void *kA = strided_for<+1, true, false, true>(E);
-    const void *kB = strided_for<+1, true, false, false>(E);
-    const void *kDE = strided_for<-1, false, true, false>(E);
     cudaError_t e;
     for (int stage = 1; stage <= 2; stage++) {
-        const float2 *src = stage == 1 ? f.a : f.a1;
-        FzPass A{src, f.abuf, MxMz, f.M, MxMz, (long)Mx * NMz, Mz, NMz, 6, Mz, K, Mx};
-        e = NSK_TIMED(tr, "fused_A_x_inverse_curl", launch_strided(kA, A, f.plN, f.tw, f.ct, s));
+        FzPass A, B, D, Ep;
+        pass_descs(f, stage == 1 ? f.a : f.a1, A, B, D, Ep);
+        e = NSK_TIMED(tr, "fused_A_x_inverse_curl", run_pass(f, 0, f.sp[0], A, s));
         if (e != cudaSuccess) return e;
-        FzPass B{f.abuf, f.bbuf, NMz, (long)Mx * NMz, NMz, (long)N * NMz, NMz, Mz, 6, Mz, K, Mx};
-        e = NSK_TIMED(tr, "fused_B_y_inverse", launch_strided(kB, B, f.plN, f.tw, f.ct, s));
+        e = NSK_TIMED(tr, "fused_B_y_inverse", run_pass(f, 1, f.sp[1], B, s));
         if (e != cudaSuccess) return e;
-        e = NSK_TIMED(tr, "fused_C_z_nonlinear", launch_z(f, s));
+        e = NSK_TIMED(tr, "fused_C_z_nonlinear", launch_z(f, f.zc, s));
         if (e != cudaSuccess) return e;
-        FzPass D{f.bbuf, f.abuf, NMz, (long)N * NMz, NMz, (long)N * MxMz, Mz, MxMz, 3, Mz, K, Mx};
-        e = NSK_TIMED(tr, "fused_D_y_forward", launch_strided(kDE, D, f.plN, f.tw, f.ct, s));
+        e = NSK_TIMED(tr, "fused_D_y_forward", run_pass(f, 2, f.sp[2], D, s));
         if (e != cudaSuccess) return e;
-        FzPass Ep{f.abuf, f.nl, MxMz, (long)N * MxMz, MxMz, f.M, MxMz, Mz, 3, Mz, K, Mx};
-        e = NSK_TIMED(tr, "fused_E_x_forward", launch_strided(kDE, Ep, f.plN, f.tw, f.ct, s));
+        e = NSK_TIMED(tr, "fused_E_x_forward", run_pass(f, 2, f.sp[3], Ep, s));
         if (e != cudaSuccess) return e;
-        FzUpdate u{N, K, Mx, Mz, stage, f.p.dealias, f.p.force_k, (float)f.p.dt,
+        FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.p.dealias, f.p.force_k, (float)f.p.dt,
                    (float)f.p.force_amp, f.M};
         e = NSK_TIMED(tr, "fused_update", launch_update(f, u, s));
         if (e != cudaSuccess) return e;
     }
     return NSK_TIMED(tr, "energy_final", energy_final(f.part, f.nparts, series, cap, counter, flags, s));
+}
+
+int fused_describe(const FusedRun &f, char *out, int len) {
+    const char *names[4] = {"A_x_inverse_curl", "B_y_inverse", "D_y_forward", "E_x_forward"};
+    int w = snprintf(out, len, "{");
+    for (int i = 0; i < 4 && w < len; i++)
+        w += snprintf(out + w, len - w, "\"%s\": {\"E\": %d, \"stages\": %d, \"cols_per_cta\": %d}, ",
+                      names[i], f.sp[i].pl.E, f.sp[i].pl.nst, f.sp[i].ct);
+    if (w < len)
+        w += snprintf(out + w, len - w,
+                      "\"C_z_nonlinear\": {\"E\": %d, \"stages\": %d, \"lines_per_cta\": %d}}",
+                      f.zc.pl.E, f.zc.pl.nst, f.zc.ct);
+    return w;
 }
 
 cudaError_t fused_set_state(FusedRun &f, const double2 *src, int on_device, void *staging,

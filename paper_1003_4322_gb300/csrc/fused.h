@@ -5,6 +5,13 @@
 
 namespace nsk {
 
+// Launch configuration of one pass: its radix plan (elements per thread) and
+// its tile (columns per CTA for a strided pass, lines per CTA for pass C).
+struct PassCfg {
+    Plan pl{};
+    int ct = 16;
+};
+
 // One run of the fused form.  Compact state layout [c][ikx][iky][kz] with
 // ikx, iky in [0, Mx) (index k for k >= 0, k + Mx for k < 0) and kz in
 // [0, Mz): only the modes the cubic 2/3 rule keeps, |kx|, |ky|, kz <= K.
@@ -12,8 +19,9 @@ struct FusedRun {
     ns_run_params p{};
     int n = 0, K = 0, Mx = 0, Mz = 0;
     long M = 0;                  // compact modes per component, Mx * Mx * Mz
-    int ct = 16;                 // columns per CTA of the strided passes
-    Plan plN{}, plH{};           // plans of length n (x, y) and n/2 (z)
+    Plan plN{}, plH{};           // default plans of length n (x, y) and n/2 (z)
+    PassCfg sp[4];               // passes A, B, D, E (chosen by the autotuner)
+    PassCfg zc;                  // pass C
     const float2 *tw = nullptr;  // exp(-2 pi i t / n), t < n (owned by the context)
     float2 *a = nullptr;         // state
     float2 *a1 = nullptr;        // first-stage state
@@ -34,6 +42,8 @@ cudaError_t fused_get_state(FusedRun &f, double2 *dst, int on_device, void *stag
                             size_t staging_bytes, cudaStream_t s);
 cudaError_t fused_step(FusedRun &f, double *series, int cap, unsigned long long *counter,
                        int *flags, cudaStream_t s, Tracer *tr);
+// JSON text describing the chosen per-pass configuration; returns its length.
+int fused_describe(const FusedRun &f, char *out, int len);
 cudaError_t fused_spectrum(FusedRun &f, int nbins, double *spec, double *ens, cudaStream_t s);
 
 }  // namespace nsk

@@ -61,6 +61,10 @@ struct Tracer {
 // Radix plan for a line of length n = 2^a 3^b (false if n has another factor).
 bool make_plan(int n, Plan *pl);
 
+// Radix plan with E elements per thread (the first, largest radix is E and
+// every radix divides E); false if E does not suit n.
+bool make_plan_e(int n, int E, Plan *pl);
+
 // Is N a supported grid size (2^a 3^b, even, >= 8)?
 bool supported_n(int n);
 
