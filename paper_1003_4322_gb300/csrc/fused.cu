@@ -94,8 +94,11 @@ k_fused_strided(FzPass ps, Plan pl, const float2 *__restrict__ tw) {
         if (!valid || r < 0) return;
         ps.out[f * ps.ofs + r * ps.ors + ou * ps.obs + iz] = v;
     };
-    auto sl = [&](int e) -> float2 { return sm[e * ct + c]; };
-    auto ss = [&](int e, float2 v) { sm[e * ct + c] = v; };
+    // tile rows padded by one element: with 8 or 16 columns, the rows a warp
+    // touches in any Stockham stage cover the banks with no extra wavefront
+    const int rs = ct + 1;
+    auto sl = [&](int e) -> float2 { return sm[e * rs + c]; };
+    auto ss = [&](int e, float2 v) { sm[e * rs + c] = v; };
     fft_line<E, DIR, false, false, false>(pl, slot, tw, n, gl, sl, ss, gs);
 }
 
@@ -387,7 +390,7 @@ static cudaError_t launch_strided(const void *k, const FzPass &ps, const Plan &p
                                   int ct, cudaStream_t s) {
     if (!k || ct < 1 || ct * (pl.n / pl.E) > 512) return cudaErrorInvalidValue;
     const int T = pl.n / pl.E;
-    const size_t smem = (size_t)pl.n * ct * sizeof(float2);
+    const size_t smem = (size_t)pl.n * (ct + 1) * sizeof(float2);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     const long tiles = (ps.ncols + ct - 1) / ct;
@@ -507,7 +510,7 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
         float best = -1.f;
         for (const Plan &pl : plan_candidates(f.n)) {
             const int T = pl.n / pl.E;
-            for (int ct = 4; ct <= 16; ct *= 2) {
+            for (int ct = 8; ct <= 16; ct *= 2) {
                 if (ct * T > 512 || (ct * T < 32 && ct < 16)) continue;
                 PassCfg cfg{pl, ct};
                 const float ms = time_launch([&]() { return run_pass(f, which[i], cfg, P[i], s); }, s, reps);
