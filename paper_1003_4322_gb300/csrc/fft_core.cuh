@@ -45,40 +45,56 @@ template <int S, typename C> NSK_DEV C cmul_i(C a) {
 }
 template <typename C> NSK_DEV C czero() { C z; z.x = 0; z.y = 0; return z; }
 
-// cos and sin of 2 pi key / 144 for the angles the register butterflies use
-// (radices 2, 3, 4, 6, 8, 9, 12, 16); values of the mathematical constants.
-NSK_DEV void angle144(int key, double &c, double &s) {
+// cos and sin of 2 pi key / 288 for the angles the register butterflies use
+// (radices 2, 3, 4, 6, 8, 9, 12, 16, 32); values of the mathematical constants.
+NSK_DEV void angle288(int key, double &c, double &s) {
     switch (key) {
     case 0: c = 1.0; s = 0.0; break;
-    case 9: c = 0.9238795325112867; s = 0.3826834323650898; break;
-    case 12: c = 0.8660254037844386; s = 0.5; break;
-    case 16: c = 0.766044443118978; s = 0.6427876096865394; break;
-    case 18: c = 0.7071067811865476; s = 0.7071067811865476; break;
-    case 24: c = 0.5; s = 0.8660254037844386; break;
-    case 27: c = 0.3826834323650898; s = 0.9238795325112867; break;
-    case 32: c = 0.17364817766693036; s = 0.984807753012208; break;
-    case 36: c = 0.0; s = 1.0; break;
-    case 45: c = -0.3826834323650898; s = 0.9238795325112867; break;
-    case 48: c = -0.5; s = 0.8660254037844386; break;
-    case 54: c = -0.7071067811865476; s = 0.7071067811865476; break;
-    case 60: c = -0.8660254037844386; s = 0.5; break;
-    case 63: c = -0.9238795325112867; s = 0.3826834323650898; break;
-    case 64: c = -0.9396926207859084; s = 0.3420201433256687; break;
-    case 72: c = -1.0; s = 0.0; break;
-    case 80: c = -0.9396926207859084; s = -0.3420201433256687; break;
-    case 81: c = -0.9238795325112867; s = -0.3826834323650898; break;
-    case 84: c = -0.8660254037844386; s = -0.5; break;
-    case 90: c = -0.7071067811865476; s = -0.7071067811865476; break;
-    case 96: c = -0.5; s = -0.8660254037844386; break;
-    case 99: c = -0.3826834323650898; s = -0.9238795325112867; break;
-    case 108: c = 0.0; s = -1.0; break;
-    case 112: c = 0.17364817766693036; s = -0.984807753012208; break;
-    case 117: c = 0.3826834323650898; s = -0.9238795325112867; break;
-    case 120: c = 0.5; s = -0.8660254037844386; break;
-    case 126: c = 0.7071067811865476; s = -0.7071067811865476; break;
-    case 128: c = 0.766044443118978; s = -0.6427876096865394; break;
-    case 132: c = 0.8660254037844386; s = -0.5; break;
-    case 135: c = 0.9238795325112867; s = -0.3826834323650898; break;
+    case 9: c = 0.9807852804032304; s = 0.19509032201612828; break;
+    case 18: c = 0.9238795325112867; s = 0.3826834323650898; break;
+    case 24: c = 0.8660254037844386; s = 0.5; break;
+    case 27: c = 0.8314696123025452; s = 0.5555702330196022; break;
+    case 32: c = 0.766044443118978; s = 0.6427876096865394; break;
+    case 36: c = 0.7071067811865476; s = 0.7071067811865476; break;
+    case 45: c = 0.5555702330196022; s = 0.8314696123025452; break;
+    case 48: c = 0.5; s = 0.8660254037844386; break;
+    case 54: c = 0.3826834323650898; s = 0.9238795325112867; break;
+    case 63: c = 0.19509032201612828; s = 0.9807852804032304; break;
+    case 64: c = 0.17364817766693036; s = 0.984807753012208; break;
+    case 72: c = 0.0; s = 1.0; break;
+    case 81: c = -0.19509032201612828; s = 0.9807852804032304; break;
+    case 90: c = -0.3826834323650898; s = 0.9238795325112867; break;
+    case 96: c = -0.5; s = 0.8660254037844386; break;
+    case 99: c = -0.5555702330196022; s = 0.8314696123025452; break;
+    case 108: c = -0.7071067811865476; s = 0.7071067811865476; break;
+    case 117: c = -0.8314696123025452; s = 0.5555702330196022; break;
+    case 120: c = -0.8660254037844386; s = 0.5; break;
+    case 126: c = -0.9238795325112867; s = 0.3826834323650898; break;
+    case 128: c = -0.9396926207859084; s = 0.3420201433256687; break;
+    case 135: c = -0.9807852804032304; s = 0.19509032201612828; break;
+    case 144: c = -1.0; s = 0.0; break;
+    case 153: c = -0.9807852804032304; s = -0.19509032201612828; break;
+    case 160: c = -0.9396926207859084; s = -0.3420201433256687; break;
+    case 162: c = -0.9238795325112867; s = -0.3826834323650898; break;
+    case 168: c = -0.8660254037844386; s = -0.5; break;
+    case 171: c = -0.8314696123025452; s = -0.5555702330196022; break;
+    case 180: c = -0.7071067811865476; s = -0.7071067811865476; break;
+    case 189: c = -0.5555702330196022; s = -0.8314696123025452; break;
+    case 192: c = -0.5; s = -0.8660254037844386; break;
+    case 198: c = -0.3826834323650898; s = -0.9238795325112867; break;
+    case 207: c = -0.19509032201612828; s = -0.9807852804032304; break;
+    case 216: c = 0.0; s = -1.0; break;
+    case 224: c = 0.17364817766693036; s = -0.984807753012208; break;
+    case 225: c = 0.19509032201612828; s = -0.9807852804032304; break;
+    case 234: c = 0.3826834323650898; s = -0.9238795325112867; break;
+    case 240: c = 0.5; s = -0.8660254037844386; break;
+    case 243: c = 0.5555702330196022; s = -0.8314696123025452; break;
+    case 252: c = 0.7071067811865476; s = -0.7071067811865476; break;
+    case 256: c = 0.766044443118978; s = -0.6427876096865394; break;
+    case 261: c = 0.8314696123025452; s = -0.5555702330196022; break;
+    case 264: c = 0.8660254037844386; s = -0.5; break;
+    case 270: c = 0.9238795325112867; s = -0.3826834323650898; break;
+    case 279: c = 0.9807852804032304; s = -0.19509032201612828; break;
     default: c = 1.0; s = 0.0; break;
     }
 }
@@ -92,7 +108,7 @@ template <int R, int DIR, typename C> NSK_DEV C twc(C v, int m) {
     if (2 * m == R) return cneg(v);
     if (4 * m == 3 * R) return cmul_i<-DIR>(v);
     double c, s;
-    angle144(m * (144 / R), c, s);
+    angle288(m * (288 / R), c, s);
     typedef decltype(v.x) T;
     const T cc = (T)c, ss = (T)(DIR * s);
     return mkc(v.x * cc - v.y * ss, v.x * ss + v.y * cc);
@@ -164,6 +180,7 @@ template <int DIR, typename C> struct Dft<8, DIR, C> : DftComposite<2, 4, DIR, C
 template <int DIR, typename C> struct Dft<9, DIR, C> : DftComposite<3, 3, DIR, C> {};
 template <int DIR, typename C> struct Dft<12, DIR, C> : DftComposite<4, 3, DIR, C> {};
 template <int DIR, typename C> struct Dft<16, DIR, C> : DftComposite<4, 4, DIR, C> {};
+template <int DIR, typename C> struct Dft<32, DIR, C> : DftComposite<4, 8, DIR, C> {};
 
 // Radix plan of one line length: n = prod rad[s]; every radix divides E.
 struct Plan {

@@ -25,30 +25,12 @@
 
 #include "fused.h"
 #include "plain.h"
+#include "fused_access.cuh"
 #include "reduce.cuh"
 
 namespace nsk {
 
 bool fused_enabled() { return true; }
-
-__device__ __forceinline__ int fz_full_signed(int e, int n) { return 2 * e < n ? e : e - n; }
-__device__ __forceinline__ int fz_compact_signed(int i, int Mx, int K) { return i <= K ? i : i - Mx; }
-// full index e (0..n-1) -> compact index, or -1 when the wavenumber is not kept
-__device__ __forceinline__ int fz_compact(int e, int n, int K, int Mx) {
-    if (e <= K) return e;
-    if (e >= n - K) return e - n + Mx;
-    return -1;
-}
-
-struct FzPass {
-    const float2 *in;
-    float2 *out;
-    long ncols;          // flattened columns per field plane
-    long ifs, irs;       // input field / row strides (complex elements)
-    long ofs, ors, obs;  // output field / row strides; outer stride of a column
-    int nfields;         // output fields handled by the grid
-    int Mz, K, Mx;
-};
 
 // One CTA: field f, ct consecutive columns; lanes run along the columns.
 // IN_C: the input rows are compact (only kept wavenumbers stored), the
@@ -62,38 +44,9 @@ k_fused_strided(FzPass ps, Plan pl, const float2 *__restrict__ tw) {
     const int n = pl.n;
     const int ct = blockDim.x / (n / E);
     const int c = threadIdx.x % ct, slot = threadIdx.x / ct;
-    const int f = blockIdx.x % ps.nfields;
-    const long tile = blockIdx.x / ps.nfields;
-    const long col = tile * ct + c;
-    const bool valid = col < ps.ncols;
-    const long ou = valid ? col / ps.Mz : 0;
-    const long iz = valid ? col % ps.Mz : 0;
-    const int K = ps.K, Mx = ps.Mx;
-    auto gl = [&](int e) -> float2 {
-        const int r = IN_C ? fz_compact(e, n, K, Mx) : e;
-        if (!valid || r < 0) return make_float2(0.f, 0.f);
-        if constexpr (!CURL) {
-            return ps.in[f * ps.ifs + r * ps.irs + col];
-        } else {
-            const float2 *b = ps.in + r * ps.irs + col;
-            if (f < 3) return b[f * ps.ifs];
-            const float kx = (float)fz_full_signed(e, n);
-            const float ky = (float)fz_compact_signed((int)ou, Mx, K);
-            const float kz = (float)iz;
-            float2 p, q;
-            float sp, sq;
-            if (f == 3) { p = b[2 * ps.ifs]; sp = ky; q = b[ps.ifs]; sq = kz; }       // i(ky az - kz ay)
-            else if (f == 4) { p = b[0]; sp = kz; q = b[2 * ps.ifs]; sq = kx; }       // i(kz ax - kx az)
-            else { p = b[ps.ifs]; sp = kx; q = b[0]; sq = ky; }                       // i(kx ay - ky ax)
-            const float re = sp * p.x - sq * q.x, im = sp * p.y - sq * q.y;
-            return make_float2(-im, re);
-        }
-    };
-    auto gs = [&](int e, float2 v) {
-        const int r = OUT_C ? fz_compact(e, n, K, Mx) : e;
-        if (!valid || r < 0) return;
-        ps.out[f * ps.ofs + r * ps.ors + ou * ps.obs + iz] = v;
-    };
+    const FzColumn<IN_C, OUT_C, CURL> col(ps, n, ct, c);
+    auto gl = [&](int e) -> float2 { return col.load(ps, e); };
+    auto gs = [&](int e, float2 v) { col.store(ps, e, v); };
     // tile rows padded by one element: with 8 or 16 columns, the rows a warp
     // touches in any Stockham stage cover the banks with no extra wavefront
     const int rs = ct + 1;
@@ -373,7 +326,34 @@ static const void *z_for(int E) {
     return nullptr;
 }
 
+// Compile-time-length strided kernel of a pass mode (0: A, 1: B, 2: D/E).
+static bool fzs_lookup(int which, int N, int E, int CT, FzsKernel *o) {
+    return which == 0 ? fzs_lookup_A(N, E, CT, o)
+         : which == 1 ? fzs_lookup_B(N, E, CT, o)
+                      : fzs_lookup_DE(N, E, CT, o);
+}
+
 cudaError_t prepare_fused_kernels() {
+    const int Ns[] = {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+    for (int N : Ns)
+        for (int wpb = 2; wpb <= 4; wpb *= 2) {
+            ZctKernel z;
+            if (zct_lookup(N, wpb, &z)) {
+                cudaError_t e = allow_smem(z.k, 48 * 1024 + 1);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    const int Ects[] = {8, 12, 16, 32};
+    for (int N : Ns)
+        for (int E : Ects)
+            for (int ct = 8; ct <= 16; ct *= 2)
+                for (int which = 0; which < 3; which++) {
+                    FzsKernel z;
+                    if (fzs_lookup(which, N, E, ct, &z)) {
+                        cudaError_t e = allow_smem(z.k, 48 * 1024 + 1);
+                        if (e != cudaSuccess) return e;
+                    }
+                }
     const int Es[] = {4, 6, 8, 9, 12, 16};
     for (int E : Es) {
         const void *ks[] = {strided_for<+1, true, false, true>(E), strided_for<+1, true, false, false>(E),
@@ -402,7 +382,23 @@ static cudaError_t launch_strided(const void *k, const FzPass &ps, const Plan &p
     return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(ct * T), args, smem, s);
 }
 
+static cudaError_t launch_z_ct(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
+    ZctKernel z;
+    if (!zct_lookup(f.n, cfg.ct, &z)) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(z.k, z.smem);
+    if (e != cudaSuccess) return e;
+    long nlines = (long)f.n * f.n;
+    const long blocks = (nlines + z.lines_per_block - 1) / z.lines_per_block;
+    float2 *buf = f.bbuf;
+    long fs = (long)f.n * f.n * f.Mz;
+    int Mz = f.Mz;
+    const float2 *tw = f.tw;
+    void *args[] = {(void *)&buf, (void *)&fs, (void *)&Mz, (void *)&nlines, (void *)&tw};
+    return cudaLaunchKernel(z.k, dim3((unsigned)blocks), dim3(z.threads), args, z.smem, s);
+}
+
 static cudaError_t launch_z(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
+    if (cfg.kind == 1) return launch_z_ct(f, cfg, s);
     const void *k = z_for(cfg.pl.E);
     if (!k) return cudaErrorInvalidValue;
     const int n = f.n / 2, Tn = n / cfg.pl.E;
@@ -434,7 +430,23 @@ static void pass_descs(const FusedRun &f, const float2 *src, FzPass &A, FzPass &
     Ep = FzPass{f.abuf, f.nl, MxMz, (long)N * MxMz, MxMz, f.M, MxMz, Mz, 3, Mz, K, Mx};
 }
 
+static cudaError_t run_pass_ct(FusedRun &f, int which, const PassCfg &cfg, const FzPass &ps,
+                               cudaStream_t s) {
+    FzsKernel z;
+    if (!fzs_lookup(which, f.n, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(z.k, z.smem);
+    if (e != cudaSuccess) return e;
+    const long tiles = (ps.ncols + cfg.ct - 1) / cfg.ct;
+    const long blocks = tiles * ps.nfields;
+    if (blocks > 0x7fffffffL) return cudaErrorInvalidValue;
+    FzPass p = ps;
+    const float2 *tw = f.tw;
+    void *args[] = {(void *)&p, (void *)&tw};
+    return cudaLaunchKernel(z.k, dim3((unsigned)blocks), dim3(z.threads), args, z.smem, s);
+}
+
 static cudaError_t run_pass(FusedRun &f, int which, const PassCfg &cfg, const FzPass &ps, cudaStream_t s) {
+    if (cfg.kind == 1) return run_pass_ct(f, which, cfg, ps, s);
     const int E = cfg.pl.E;
     const void *k = which == 0 ? strided_for<+1, true, false, true>(E)
                   : which == 1 ? strided_for<+1, true, false, false>(E)
@@ -508,11 +520,24 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
     const int which[4] = {0, 1, 2, 2};
     for (int i = 0; i < 4; i++) {
         float best = -1.f;
+        const int Es[] = {8, 12, 16, 32};
+        for (int E : Es)
+            for (int ct = 8; ct <= 16; ct *= 2) {
+                FzsKernel z;
+                if (!fzs_lookup(which[i], f.n, E, ct, &z)) continue;
+                PassCfg cfg{f.plN, ct, 1};
+                cfg.pl.E = E;
+                const float ms = time_launch([&]() { return run_pass(f, which[i], cfg, P[i], s); }, s, reps);
+                if (ms > 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    f.sp[i] = cfg;
+                }
+            }
         for (const Plan &pl : plan_candidates(f.n)) {
             const int T = pl.n / pl.E;
             for (int ct = 8; ct <= 16; ct *= 2) {
                 if (ct * T > 512 || (ct * T < 32 && ct < 16)) continue;
-                PassCfg cfg{pl, ct};
+                PassCfg cfg{pl, ct, 0};
                 const float ms = time_launch([&]() { return run_pass(f, which[i], cfg, P[i], s); }, s, reps);
                 if (ms > 0.f && (best < 0.f || ms < best)) {
                     best = ms;
@@ -524,10 +549,20 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
     }
     {
         float best = -1.f;
+        for (int wpb = 2; wpb <= 4; wpb *= 2) {
+            ZctKernel z;
+            if (!zct_lookup(f.n, wpb, &z)) continue;
+            PassCfg cfg{f.plH, wpb, 1};
+            const float ms = time_launch([&]() { return launch_z(f, cfg, s); }, s, reps);
+            if (ms > 0.f && (best < 0.f || ms < best)) {
+                best = ms;
+                f.zc = cfg;
+            }
+        }
         for (const Plan &pl : plan_candidates(f.n / 2)) {
             const int Tn = pl.n / pl.E;
             for (int L = 1; 6 * L * Tn <= 256; L *= 2) {
-                PassCfg cfg{pl, L};
+                PassCfg cfg{pl, L, 0};
                 const float ms = time_launch([&]() { return launch_z(f, cfg, s); }, s, reps);
                 if (ms > 0.f && (best < 0.f || ms < best)) {
                     best = ms;
@@ -619,9 +654,15 @@ int fused_describe(const FusedRun &f, char *out, int len) {
     const char *names[4] = {"A_x_inverse_curl", "B_y_inverse", "D_y_forward", "E_x_forward"};
     int w = snprintf(out, len, "{");
     for (int i = 0; i < 4 && w < len; i++)
-        w += snprintf(out + w, len - w, "\"%s\": {\"E\": %d, \"stages\": %d, \"cols_per_cta\": %d}, ",
-                      names[i], f.sp[i].pl.E, f.sp[i].pl.nst, f.sp[i].ct);
-    if (w < len)
+        w += snprintf(out + w, len - w,
+                      "\"%s\": {\"kernel\": \"%s\", \"E\": %d, \"cols_per_cta\": %d}, ", names[i],
+                      f.sp[i].kind == 1 ? "compile-time length" : "runtime length", f.sp[i].pl.E,
+                      f.sp[i].ct);
+    if (w < len && f.zc.kind == 1)
+        w += snprintf(out + w, len - w,
+                      "\"C_z_nonlinear\": {\"kernel\": \"compile-time length\", \"warps_per_cta\": %d}}",
+                      f.zc.ct);
+    else if (w < len)
         w += snprintf(out + w, len - w,
                       "\"C_z_nonlinear\": {\"E\": %d, \"stages\": %d, \"lines_per_cta\": %d}}",
                       f.zc.pl.E, f.zc.pl.nst, f.zc.ct);

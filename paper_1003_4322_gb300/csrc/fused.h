@@ -10,7 +10,28 @@ namespace nsk {
 struct PassCfg {
     Plan pl{};
     int ct = 16;
+    int kind = 0;   // 0: runtime-length kernel; 1: compile-time-length kernel (ct = warps per CTA)
 };
+
+// A pass-C kernel specialised for one grid size (fused_z.cu).
+struct ZctKernel {
+    const void *k = nullptr;
+    size_t smem = 0;
+    int lines_per_block = 0;
+    int threads = 0;
+};
+// Kernel for grid size N with wpb warps per CTA, if one was compiled.
+bool zct_lookup(int N, int wpb, ZctKernel *out);
+
+// A strided-pass kernel specialised for one (N, E, CT) shape (fused_s*.cu).
+struct FzsKernel {
+    const void *k = nullptr;
+    size_t smem = 0;
+    int threads = 0;
+};
+bool fzs_lookup_A(int N, int E, int CT, FzsKernel *out);    // x inverse + curl
+bool fzs_lookup_B(int N, int E, int CT, FzsKernel *out);    // y inverse
+bool fzs_lookup_DE(int N, int E, int CT, FzsKernel *out);   // y / x forward
 
 // One run of the fused form.  Compact state layout [c][ikx][iky][kz] with
 // ikx, iky in [0, Mx) (index k for k >= 0, k + Mx for k < 0) and kz in

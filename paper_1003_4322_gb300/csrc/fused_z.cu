@@ -1,0 +1,135 @@
+// fused_z.cu -- pass C of the fused form for compile-time grid sizes.
+//
+// Pass C (z c2r of u and w, the cross product u x w on the grid, z r2c of
+// the product; Sec. 2, Eqs. 1-2) is the arithmetic-heaviest pass: nine
+// length-N/2 transforms per (y, x) line for every 9 * N/3 complex values that
+// cross HBM.  Here one warp owns whole lines (32 / T lines of T = N/2 / E
+// threads each) and works through the six fields one after another, so the
+// exchange between Stockham stages needs only __syncwarp, and with N fixed
+// at compile time every index, stride and span is a constant.
+#include "fft_ct.cuh"
+#include "fused.h"
+
+namespace nsk {
+
+template <int N> struct ZShape {
+    static constexpr int n = N / 2;
+    static constexpr int E = (n % 3 == 0) ? 12 : 16;
+    static constexpr int T = n / E;
+    static constexpr int LPW = 32 / T;                      // lines per warp
+    static constexpr int LS = ct_line_stride(n, E, 6);      // elements per field line
+    static_assert(ct_valid(n, E), "no radix plan");
+    static_assert(T >= 1 && T <= 32 && 32 % T == 0, "a line must fit a warp");
+};
+
+template <int N, int WPB>
+__global__ void __launch_bounds__(32 * WPB)
+k_fused_z_ct(float2 *buf, long fs, int Mz, long nlines, const float2 *__restrict__ tw) {
+    typedef ZShape<N> Z;
+    constexpr int n = Z::n, E = Z::E, T = Z::T, LPW = Z::LPW, LS = Z::LS;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ll = lane / T, slot = lane % T;
+    const long line = ((long)blockIdx.x * WPB + warp) * LPW + ll;
+    const bool valid = line < nlines;
+    float2 *L6 = sm + (long)(warp * LPW + ll) * 6 * LS;
+
+    // c2r of the six fields: Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]),
+    // X[k] = 0 for k >= Mz, real parts of X[0] and X[n]; then one inverse
+    // length-n FFT leaves the 2n real samples in natural order.
+    for (int f = 0; f < 6; f++) {
+        float2 *Lf = L6 + f * LS;
+        auto sl = [&](int e) -> float2 { return Lf[ct_skew(e)]; };
+        auto ss = [&](int e, float2 v) { Lf[ct_skew(e)] = v; };
+        const float2 *src = buf + f * fs + line * Mz;
+        float2 xk[E], xm[E];
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            xk[j] = (valid && k < Mz) ? src[k] : make_float2(0.f, 0.f);
+            xm[j] = (valid && n - k < Mz) ? src[n - k] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            float2 a0 = xk[j], am = xm[j];
+            if (k == 0) {
+                a0.y = 0.f;
+                am.y = 0.f;
+            }
+            const float2 xc = cconj(am);
+            const float2 wb = cmulc(csub(a0, xc), __ldg(tw + k));
+            ss(k, cadd(cadd(a0, xc), cmul_i<1>(wb)));
+        }
+        __syncwarp();
+        ct_fft_smem<n, E, +1, N>(slot, tw, sl, ss);
+    }
+
+    // u x w at the 2n points (complex element m holds points 2m and 2m + 1)
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        float2 *b = L6 + ct_skew(slot + j * T);
+        const float2 ux = b[0], uy = b[LS], uz = b[2 * LS];
+        const float2 wx = b[3 * LS], wy = b[4 * LS], wz = b[5 * LS];
+        b[0] = make_float2(uy.x * wz.x - uz.x * wy.x, uy.y * wz.y - uz.y * wy.y);
+        b[LS] = make_float2(uz.x * wx.x - ux.x * wz.x, uz.y * wx.y - ux.y * wz.y);
+        b[2 * LS] = make_float2(ux.x * wy.x - uy.x * wx.x, ux.y * wy.y - uy.y * wx.y);
+    }
+    __syncwarp();
+
+    // r2c of the three products and the kept kz < Mz written over fields 0..2:
+    // X[k] = (Z[k] + conj Z[n-k])/2 - i W^k (Z[k] - conj Z[n-k])/2
+    for (int f = 0; f < 3; f++) {
+        float2 *Lf = L6 + f * LS;
+        auto sl = [&](int e) -> float2 { return Lf[ct_skew(e)]; };
+        auto ss = [&](int e, float2 v) { Lf[ct_skew(e)] = v; };
+        ct_fft_smem<n, E, -1, N>(slot, tw, sl, ss);
+        float2 *dst = buf + f * fs + line * Mz;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            if (valid && k < Mz) {
+                const float2 zk = sl(k);
+                const float2 zc = cconj(sl(k == 0 ? 0 : n - k));
+                const float2 ev = cscale(cadd(zk, zc), 0.5f);
+                const float2 od = cmul_i<-1>(cscale(csub(zk, zc), 0.5f));
+                dst[k] = cadd(ev, cmul(od, __ldg(tw + k)));
+            }
+        }
+    }
+}
+
+template <int N, int WPB> static void zct_entry(ZctKernel *o) {
+    typedef ZShape<N> Z;
+    o->k = (const void *)k_fused_z_ct<N, WPB>;
+    o->smem = (size_t)WPB * Z::LPW * 6 * Z::LS * sizeof(float2);
+    o->lines_per_block = WPB * Z::LPW;
+    o->threads = 32 * WPB;
+}
+
+template <int N> static bool zct_by_wpb(int wpb, ZctKernel *o) {
+    switch (wpb) {
+    case 2: zct_entry<N, 2>(o); return true;
+    case 4: zct_entry<N, 4>(o); return true;
+    }
+    return false;
+}
+
+bool zct_lookup(int N, int wpb, ZctKernel *o) {
+    switch (N) {
+    case 32: return zct_by_wpb<32>(wpb, o);
+    case 64: return zct_by_wpb<64>(wpb, o);
+    case 96: return zct_by_wpb<96>(wpb, o);
+    case 128: return zct_by_wpb<128>(wpb, o);
+    case 192: return zct_by_wpb<192>(wpb, o);
+    case 256: return zct_by_wpb<256>(wpb, o);
+    case 384: return zct_by_wpb<384>(wpb, o);
+    case 512: return zct_by_wpb<512>(wpb, o);
+    case 768: return zct_by_wpb<768>(wpb, o);
+    case 1024: return zct_by_wpb<1024>(wpb, o);
+    }
+    return false;
+}
+
+}  // namespace nsk
