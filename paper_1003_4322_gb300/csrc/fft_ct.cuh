@@ -114,6 +114,70 @@ constexpr int ct_line_stride(int n, int E, int fields) {
     return best;
 }
 
+// Stage twiddles of one thread, kept in registers across many transforms of
+// the same length: W_{pR}^{q k} for stages s >= 1, k = (slot + b T) mod p.
+template <int n, int E, int NTAB> struct CtTwiddles {
+    static constexpr int offset(int s) {
+        int o = 0;
+        for (int i = 1; i < s; i++) o += (E / ct_radix(n, E, i)) * (ct_radix(n, E, i) - 1);
+        return o;
+    }
+    static constexpr int count() { return offset(ct_nst(n, E)) > 0 ? offset(ct_nst(n, E)) : 1; }
+    float2 w[count()];
+    template <int S = 1> NSK_DEV void load(int slot, const float2 *__restrict__ tw) {
+        if constexpr (S < ct_nst(n, E)) {
+            constexpr int R = ct_radix(n, E, S), p = ct_span(n, E, S), T = n / E, o = offset(S);
+#pragma unroll
+            for (int b = 0; b < E / R; b++) {
+                const int k = (slot + b * T) % p;
+#pragma unroll
+                for (int q = 1; q < R; q++) w[o + b * (R - 1) + q - 1] = __ldg(tw + q * k * (NTAB / (p * R)));
+            }
+            load<S + 1>(slot, tw);
+        }
+    }
+};
+
+// In-place FFT as ct_fft_smem, with the stage twiddles already in registers.
+template <int n, int E, int DIR, int NTAB, int S = 0, class SL, class SS>
+NSK_DEV void ct_fft_smem_tw(int slot, const CtTwiddles<n, E, NTAB> &twr, SL sl, SS ss) {
+    constexpr int NST = ct_nst(n, E);
+    if constexpr (S < NST) {
+        constexpr int R = ct_radix(n, E, S), T = n / E, nR = n / R;
+        constexpr int p = ct_span(n, E, S);
+        float2 v[E];
+#pragma unroll
+        for (int b = 0; b < E / R; b++) {
+            const int i = slot + b * T;
+#pragma unroll
+            for (int q = 0; q < R; q++) v[b * R + q] = sl(i + q * nR);
+        }
+#pragma unroll
+        for (int b = 0; b < E / R; b++) {
+            if constexpr (S > 0) {
+                constexpr int o = CtTwiddles<n, E, NTAB>::offset(S);
+#pragma unroll
+                for (int q = 1; q < R; q++) {
+                    const float2 w = twr.w[o + b * (R - 1) + q - 1];
+                    v[b * R + q] = DIR < 0 ? cmul(v[b * R + q], w) : cmulc(v[b * R + q], w);
+                }
+            }
+            Dft<R, DIR, float2>::run(&v[b * R]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < E / R; b++) {
+            const int i = slot + b * T;
+            const int k = i % p;
+            const int j = (i - k) * R + k;
+#pragma unroll
+            for (int q = 0; q < R; q++) ss(j + q * p, v[b * R + q]);
+        }
+        __syncwarp();
+        ct_fft_smem_tw<n, E, DIR, NTAB, S + 1>(slot, twr, sl, ss);
+    }
+}
+
 // In-place FFT of one line in shared memory (sl/ss read and write element e)
 // by T = n/E threads of one warp, slot = the thread's index in its line.
 // tw: exp(-2 pi i t / NTAB), t < NTAB, with n dividing NTAB.

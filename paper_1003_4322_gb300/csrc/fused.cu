@@ -18,8 +18,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <map>
+#include <string>
 #include <mutex>
 #include <vector>
 
@@ -497,14 +500,83 @@ template <class F> static float time_launch(F launch, cudaStream_t s, int reps) 
     return ms;
 }
 
-// Choose, per pass, the radix split E and the tile (columns per CTA for the
-// strided passes, lines per CTA for pass C) that run fastest on this run's
-// own buffers; results are kept per N for the life of the process.
+// Plan cache file (environment variable NS_PLAN_CACHE): one JSON object
+// mapping N to five [kind, E, tile] triples (passes A, B, D, E, C).  Entries
+// found there are used as they are; newly tuned sizes are written back.
+static bool cfg_from_triple(int n, int kind, int E, int tile, bool zpass, PassCfg &out) {
+    Plan pl;
+    const int len = zpass ? n / 2 : n;
+    if (kind == 1) {
+        if (!make_plan(len, &pl)) return false;
+        pl.E = E;   // compile-time kernels carry their own plan; E names the shape
+    } else if (!make_plan_e(len, E, &pl)) {
+        return false;
+    }
+    out = PassCfg{pl, tile, kind};
+    return true;
+}
+
+static void plan_cache_read(std::map<int, TunedCfgs> &cache) {
+    const char *path = getenv("NS_PLAN_CACHE");
+    if (!path) return;
+    FILE *fp = fopen(path, "r");
+    if (!fp) return;
+    std::string txt;
+    char buf[4096];
+    size_t r;
+    while ((r = fread(buf, 1, sizeof(buf), fp)) > 0) txt.append(buf, r);
+    fclose(fp);
+    size_t pos = 0;
+    while ((pos = txt.find('"', pos)) != std::string::npos) {
+        int n = 0, v[15], used = 0;
+        if (sscanf(txt.c_str() + pos, "\"%d\": [[%d, %d, %d], [%d, %d, %d], [%d, %d, %d], [%d, %d, %d], [%d, %d, %d]]%n",
+                   &n, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &v[10],
+                   &v[11], &v[12], &v[13], &v[14], &used) == 16 && used > 0) {
+            TunedCfgs t;
+            bool ok = true;
+            for (int i = 0; i < 4 && ok; i++) ok = cfg_from_triple(n, v[3 * i], v[3 * i + 1], v[3 * i + 2], false, t.s[i]);
+            ok = ok && cfg_from_triple(n, v[12], v[13], v[14], true, t.c);
+            if (ok) cache[n] = t;
+            pos += used;
+        } else {
+            pos++;
+        }
+    }
+}
+
+static void plan_cache_write(const std::map<int, TunedCfgs> &cache) {
+    const char *path = getenv("NS_PLAN_CACHE");
+    if (!path) return;
+    FILE *fp = fopen(path, "w");
+    if (!fp) return;
+    fprintf(fp, "{");
+    bool first = true;
+    for (const auto &kv : cache) {
+        const TunedCfgs &t = kv.second;
+        fprintf(fp, "%s\n  \"%d\": [", first ? "" : ",", kv.first);
+        for (int i = 0; i < 4; i++)
+            fprintf(fp, "[%d, %d, %d], ", t.s[i].kind, t.s[i].pl.E, t.s[i].ct);
+        fprintf(fp, "[%d, %d, %d]]", t.c.kind, t.c.pl.E, t.c.ct);
+        first = false;
+    }
+    fprintf(fp, "\n}\n");
+    fclose(fp);
+}
+
+// Choose, per pass, the kernel (runtime or compile-time length), the radix
+// split E and the tile (columns per CTA for the strided passes, lines or warps
+// per CTA for pass C) that run fastest on this run's own buffers; results
+// are kept per N for the life of the process (and in the plan cache file).
 static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
     static std::mutex mu;
     static std::map<int, TunedCfgs> cache;
+    static bool loaded = false;
     {
         std::lock_guard<std::mutex> g(mu);
+        if (!loaded) {
+            plan_cache_read(cache);
+            loaded = true;
+        }
         auto it = cache.find(f.n);
         if (it != cache.end()) {
             for (int i = 0; i < 4; i++) f.sp[i] = it->second.s[i];
@@ -577,6 +649,7 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
     for (int i = 0; i < 4; i++) t.s[i] = f.sp[i];
     t.c = f.zc;
     cache[f.n] = t;
+    plan_cache_write(cache);
     return cudaSuccess;
 }
 

@@ -35,21 +35,33 @@ k_fused_z_ct(float2 *buf, long fs, int Mz, long nlines, const float2 *__restrict
     const bool valid = line < nlines;
     float2 *L6 = sm + (long)(warp * LPW + ll) * 6 * LS;
 
+    // Stage twiddles and the packing twiddles W^k, k = slot + j T, stay in
+    // registers for all nine transforms of the line.
+    CtTwiddles<n, E, N> twr;
+    twr.load(slot, tw);
+    float2 wk[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) wk[j] = __ldg(tw + slot + j * T);
+
     // c2r of the six fields: Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]),
     // X[k] = 0 for k >= Mz, real parts of X[0] and X[n]; then one inverse
-    // length-n FFT leaves the 2n real samples in natural order.
-    for (int f = 0; f < 6; f++) {
-        float2 *Lf = L6 + f * LS;
-        auto sl = [&](int e) -> float2 { return Lf[ct_skew(e)]; };
-        auto ss = [&](int e, float2 v) { Lf[ct_skew(e)] = v; };
+    // length-n FFT leaves the 2n real samples in natural order.  The loads of
+    // field f + 1 are issued before the transform of field f.
+    float2 xk[E], xm[E];
+    auto fetch = [&](int f) {
         const float2 *src = buf + f * fs + line * Mz;
-        float2 xk[E], xm[E];
 #pragma unroll
         for (int j = 0; j < E; j++) {
             const int k = slot + j * T;
             xk[j] = (valid && k < Mz) ? src[k] : make_float2(0.f, 0.f);
             xm[j] = (valid && n - k < Mz) ? src[n - k] : make_float2(0.f, 0.f);
         }
+    };
+    fetch(0);
+    for (int f = 0; f < 6; f++) {
+        float2 *Lf = L6 + f * LS;
+        auto sl = [&](int e) -> float2 { return Lf[ct_skew(e)]; };
+        auto ss = [&](int e, float2 v) { Lf[ct_skew(e)] = v; };
 #pragma unroll
         for (int j = 0; j < E; j++) {
             const int k = slot + j * T;
@@ -59,11 +71,12 @@ k_fused_z_ct(float2 *buf, long fs, int Mz, long nlines, const float2 *__restrict
                 am.y = 0.f;
             }
             const float2 xc = cconj(am);
-            const float2 wb = cmulc(csub(a0, xc), __ldg(tw + k));
+            const float2 wb = cmulc(csub(a0, xc), wk[j]);
             ss(k, cadd(cadd(a0, xc), cmul_i<1>(wb)));
         }
+        if (f < 5) fetch(f + 1);
         __syncwarp();
-        ct_fft_smem<n, E, +1, N>(slot, tw, sl, ss);
+        ct_fft_smem_tw<n, E, +1, N>(slot, twr, sl, ss);
     }
 
     // u x w at the 2n points (complex element m holds points 2m and 2m + 1)
@@ -84,7 +97,7 @@ k_fused_z_ct(float2 *buf, long fs, int Mz, long nlines, const float2 *__restrict
         float2 *Lf = L6 + f * LS;
         auto sl = [&](int e) -> float2 { return Lf[ct_skew(e)]; };
         auto ss = [&](int e, float2 v) { Lf[ct_skew(e)] = v; };
-        ct_fft_smem<n, E, -1, N>(slot, tw, sl, ss);
+        ct_fft_smem_tw<n, E, -1, N>(slot, twr, sl, ss);
         float2 *dst = buf + f * fs + line * Mz;
 #pragma unroll
         for (int j = 0; j < E; j++) {
@@ -94,7 +107,7 @@ k_fused_z_ct(float2 *buf, long fs, int Mz, long nlines, const float2 *__restrict
                 const float2 zc = cconj(sl(k == 0 ? 0 : n - k));
                 const float2 ev = cscale(cadd(zk, zc), 0.5f);
                 const float2 od = cmul_i<-1>(cscale(csub(zk, zc), 0.5f));
-                dst[k] = cadd(ev, cmul(od, __ldg(tw + k)));
+                dst[k] = cadd(ev, cmul(od, wk[j]));
             }
         }
     }
