@@ -45,6 +45,13 @@ WORKLOADS = {
     "forced1024": dict(desc="1024^3 forced turbulence, ABC forcing k=3 F=0.5, nu=5e-4, dt=5e-4, "
                             "seeded k^-2 start (seed 5), FP32", n=1024, nu=5e-4, dt=5e-4,
                        force_amp=0.5, force_k=3, ic=("turb", 5), prec="fp32", companion=None),
+    "ensemble48": dict(desc="48 independent runs, 16 each at 64^3, 96^3 and 128^3, FP32, "
+                            "nu_r = 5e-3 + 1.5e-2 U(4999, r), dt=1e-3, seeded k^-2 starts on "
+                            "1<=|k|<=4 (seeds 4000+r); FP64 plain ensemble alongside",
+                       n=128, ensemble=48, dt=1e-3, prec="fp32", companion="fp64"),
+    "plain768": dict(desc="768^3 forced turbulence, ABC forcing k=3 F=0.5, nu=5e-4, dt=5e-4, "
+                          "seeded k^-2 start (seed 5), plain FP64", n=768, nu=5e-4, dt=5e-4,
+                     force_amp=0.5, force_k=3, ic=("turb", 5), prec="fp64", companion=None),
 }
 
 
@@ -64,17 +71,22 @@ FP64_FLOP_PER_SM_CLK = 4.0
 N_SM = 152
 
 
-def initial_state(w):
+def members(w):
+    """(run parameters, initial states) of every run of the workload."""
     from paper_1003_4322_gb300 import inputs
+    if w.get("ensemble"):
+        runs, ics = [], []
+        for r in range(w["ensemble"]):
+            n = (64, 96, 128)[r * 3 // w["ensemble"]]
+            runs.append(dict(n=n, nu=inputs.ensemble_nu(r), dt=w["dt"]))
+            ics.append(inputs.turbulence_state(n, 4000 + r))
+        return runs, ics
+    run = dict(n=w["n"], nu=w["nu"], dt=w["dt"], force_amp=w.get("force_amp", 0.0),
+               force_k=w.get("force_k", 0))
     if w["ic"] == "tg":
-        return inputs.taylor_green_state(w["n"])
+        return [run], [inputs.taylor_green_state(w["n"])]
     kind, seed = w["ic"]
-    return inputs.turbulence_state(w["n"], seed)
-
-
-def run_params(w):
-    return dict(n=w["n"], nu=w["nu"], dt=w["dt"], force_amp=w.get("force_amp", 0.0),
-                force_k=w.get("force_k", 0))
+    return [run], [inputs.turbulence_state(w["n"], seed)]
 
 
 # ---------------------------------------------------------------- kernel model
@@ -188,16 +200,19 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- GPU arm
 
-def time_form(w, prec, a0, steps, warmup, census_steps, dist):
-    """Advance one solver through warm-up, K timed steps and a kernel census;
-    returns timing, census, final state and the energy series."""
+def time_form(w, prec, mem, steps, warmup, census_steps, dist):
+    """Advance one solver (all runs of the workload) through warm-up, K timed
+    steps and a kernel census; returns timing, census, final states and the
+    energy series of run 0."""
     import torch
 
     from paper_1003_4322_gb300 import _native as nat
     from paper_1003_4322_gb300.solver import Solver
     stream = torch.cuda.current_stream()
-    s = Solver([run_params(w)], prec=prec, stream=stream)
-    s.set_state(a0)
+    runs, ics = mem
+    s = Solver(runs, prec=prec, stream=stream)
+    for i, a0 in enumerate(ics):
+        s.set_state(a0, run=i)
     s.step(warmup)
     s.sync()
     clocks = ClockSampler(torch.cuda.current_device())
@@ -218,11 +233,11 @@ def time_form(w, prec, a0, steps, warmup, census_steps, dist):
     E, O = s.series(count=steps)
     census = nat.ns_kernel_census(s.ctx, census_steps) if census_steps > 0 else []
     desc = nat.ns_describe_run(s.ctx, 0)
-    state = s.get_state()
-    return dict(solver=s, ms=ms, clocks=clk, census=census, state=state, E=E, O=O, desc=desc)
+    states = [s.get_state(run=i) for i in range(len(runs))]
+    return dict(solver=s, ms=ms, clocks=clk, census=census, states=states, E=E, O=O, desc=desc)
 
 
-def roofline_of(census, w, prec, census_steps, peaks, sm_mhz):
+def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
     """Dominant kernel (largest share of device time in the census) against
     HBM or the FP64 ALU roof, whichever its algorithmic model says binds."""
     if not census:
@@ -230,7 +245,12 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz):
     total = sum(t for _, _, t in census)
     name, launches, tms = max(census, key=lambda r: r[2])
     per_launch_ms = tms / launches
-    bytes_, flops = kernel_model(name, w["n"], prec)
+    # one launch covers every run of a group; launches per step = groups x passes
+    sizes = sizes or [w["n"]]
+    per_size = [kernel_model(name, n, prec) for n in sizes]
+    groups = len(set(sizes))
+    bytes_ = sum(b for b, _ in per_size) / groups
+    flops = sum(f for _, f in per_size) / groups
     gbs = bytes_ / (per_launch_ms * 1e-3) / 1e9
     hbm_frac = gbs / peaks["hbm_gbs"]
     roof = {"kernel": name, "launches_per_step": launches / census_steps,
@@ -291,7 +311,7 @@ def fft_stage(n, prec, reps=5):
             "bytes_model": model}
 
 
-def e2e(w, prec, a0, steps):
+def e2e(w, prec, mem, steps):
     """Through the public API with host buffers: every step uploads its input
     state from pinned host memory (ns_set_state), advances one RK2 step
     (ns_step) and reads its diagnostics back (ns_energy_spectrum)."""
@@ -300,48 +320,66 @@ def e2e(w, prec, a0, steps):
 
     from paper_1003_4322_gb300 import _native as nat
     from paper_1003_4322_gb300.solver import Solver
-    pinned = torch.empty(a0.shape, dtype=torch.complex128, pin_memory=True)
-    pinned.numpy()[...] = a0
-    host = pinned.numpy()
-    s = Solver([run_params(w)], prec=prec, stream=torch.cuda.current_stream())
+    runs, ics = mem
+    hosts = []
+    for a0 in ics:
+        pinned = torch.empty(a0.shape, dtype=torch.complex128, pin_memory=True)
+        pinned.numpy()[...] = a0
+        hosts.append(pinned.numpy())
+    s = Solver(runs, prec=prec, stream=torch.cuda.current_stream())
+    nr = len(runs)
+
+    def one_step():
+        for i, h in enumerate(hosts):
+            s.set_state(h, run=i)
+        s.step(1)
+        return [s.energy_spectrum(run=i)[2] for i in range(nr)]
     try:
         for _ in range(2):
-            s.set_state(host)
-            s.step(1)
-            s.energy_spectrum()
+            one_step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(steps):
-            s.set_state(host)
-            s.step(1)
-            E, O, spec = s.energy_spectrum()
+            specs = one_step()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
     finally:
         s.close()
-    return {"value": steps / dt, "unit": "steps/s", "h2d_bytes_per_step": int(a0.nbytes),
-            "d2h_bytes_per_step": int(spec.nbytes + 16), "steps": steps}
+    return {"value": nr * steps / dt, "unit": "run-steps/s" if nr > 1 else "steps/s",
+            "h2d_bytes_per_step": int(sum(h.nbytes for h in hosts)),
+            "d2h_bytes_per_step": int(sum(sp.nbytes + 16 for sp in specs)), "steps": steps}
 
 
-def cpu_baseline(w, a0, budget_s=30.0):
-    """The FP64 oracle (test infrastructure, as it stands) on the host cores:
-    whole RK2 steps of the same workload until the time budget is used."""
+def oracle_steps(mem, budget_s, max_steps):
+    """Whole RK2 steps of the oracle (as it stands) over the workload's runs,
+    cycling through the members, until the time budget is used."""
     import oracle
     cores = oracle.set_threads(os.cpu_count() or 1)
-    p = oracle.Params(n=w["n"], nu=w["nu"], dt=w["dt"], force_amp=w.get("force_amp", 0.0),
-                      force_k=w.get("force_k", 0))
-    a = a0
+    runs, ics = mem
+    states = list(ics)
     t0 = time.perf_counter()
     steps = 0
-    while True:
-        a = oracle.step(a, p, 1)
+    while steps < max_steps:
+        i = steps % len(runs)
+        r = runs[i]
+        p = oracle.Params(n=r["n"], nu=r["nu"], dt=r["dt"], force_amp=r.get("force_amp", 0.0),
+                          force_k=r.get("force_k", 0))
+        states[i] = oracle.step(states[i], p, 1)
         steps += 1
-        if time.perf_counter() - t0 > budget_s or steps >= 1000:
+        if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    return {"value": steps / dt, "unit": "steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{steps} whole RK2 step(s) of the {w['n']}^3 workload on {cores} "
-                      f"host threads ({dt:.1f} s)"}
+    return steps, time.perf_counter() - t0, cores
+
+
+def cpu_baseline(w, mem, budget_s=30.0):
+    """The FP64 oracle (test infrastructure, as it stands) on the host cores:
+    whole RK2 steps of the same workload until the time budget is used."""
+    steps, dt, cores = oracle_steps(mem, budget_s, 1000)
+    nr = len(mem[0])
+    unit = "run-steps/s" if nr > 1 else "steps/s"
+    return {"value": steps / dt, "unit": unit, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} whole RK2 step(s) of {'members of ' if nr > 1 else ''}the "
+                      f"workload on {cores} host threads ({dt:.1f} s)"}
 
 
 def ours(args, w):
@@ -360,56 +398,60 @@ def ours(args, w):
     torch.cuda.set_device(local)
     nat.load()
     peaks = load_peaks()
-    a0 = initial_state(w)
+    mem = members(w)
+    nr = len(mem[0])
     warmup = max(args.warmup, 3)
     census_steps = min(args.steps, 3)
 
-    main = time_form(w, w["prec"], a0, args.steps, warmup, census_steps, dist)
+    main = time_form(w, w["prec"], mem, args.steps, warmup, census_steps, dist)
     ms = main["ms"]
     if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * args.steps / (ms * 1e-3)
+    value = world * nr * args.steps / (ms * 1e-3)
+    points = sum(r["n"] ** 3 for r in mem[0])
     clk = main["clocks"] or {}
+    sizes = [r["n"] for r in mem[0]]
     roof, census_total = roofline_of(main["census"], w, w["prec"], census_steps, peaks,
-                                     clk.get("sm_mhz"))
+                                     clk.get("sm_mhz"), sizes)
     launches_per_step = sum(l for _, l, _ in main["census"]) / census_steps if main["census"] else 0
     main["solver"].close()
 
     comp = None
     if w.get("companion") and not args.no_companion:
-        c = time_form(w, w["companion"], a0, args.steps, warmup, census_steps, dist)
-        croof, _ = roofline_of(c["census"], w, w["companion"], census_steps, peaks, None)
+        c = time_form(w, w["companion"], mem, args.steps, warmup, census_steps, dist)
+        croof, _ = roofline_of(c["census"], w, w["companion"], census_steps, peaks, None, sizes)
         from oracle import rel_l2
-        fp32, fp64 = (c["state"], main["state"]) if w["companion"] == "fp32" else \
-            (main["state"], c["state"])
-        comp = {"form": w["companion"], "value": args.steps / (c["ms"] * 1e-3),
-                "unit": "steps/s", "ms_per_step": c["ms"] / args.steps,
-                "rel_l2_fp32_vs_fp64": rel_l2(fp32, fp64),
+        fp32, fp64 = (c["states"], main["states"]) if w["companion"] == "fp32" else \
+            (main["states"], c["states"])
+        comp = {"form": w["companion"], "value": nr * args.steps / (c["ms"] * 1e-3),
+                "unit": "run-steps/s" if nr > 1 else "steps/s", "ms_per_step": c["ms"] / args.steps,
+                "rel_l2_fp32_vs_fp64": max(rel_l2(a, b) for a, b in zip(fp32, fp64)),
                 "after_steps": warmup + args.steps + census_steps, "roofline": croof,
                 "execution": c["desc"],
                 "kernels": [{"name": n, "launches": l, "ms": t} for n, l, t in c["census"]]}
         c["solver"].close()
 
     fft = fft_stage(w["n"], "fp32") if not args.no_fft else None
-    ee = e2e(w, w["prec"], a0, min(args.steps, 20))
+    ee = e2e(w, w["prec"], mem, min(args.steps, 20))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, a0, args.cpu_budget)
+        cpu = cpu_baseline(w, mem, args.cpu_budget)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     step_idx = [i for i in (49, 99, 149, 199) if i < len(main["E"])]
     line = {
-        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": "run-steps/s" if nr > 1 else "steps/s",
+        "n_gpus": world, "runs": nr, "grid_point_steps_per_s": value * points / nr,
         "steps": args.steps, "warmup": warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if w["prec"] == "fp64" else "f32",
         "data": "synthetic (analytic / seeded initial condition, no dataset)",
         "config": {"workload": args.workload, "description": w["desc"], "n": w["n"],
-                   "nu": w["nu"], "dt": w["dt"], "form": "plain FP64" if w["prec"] == "fp64"
+                   "nu": w.get("nu"), "dt": w["dt"], "form": "plain FP64" if w["prec"] == "fp64"
                    else "fused FP32", "parallelism": f"replicas x{world}",
                    "l2": "working set above 129 MB L2 (no flush needed)",
                    "execution": main["desc"]},
@@ -432,30 +474,19 @@ def reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    a0 = initial_state(w)
-    import oracle
-    cores = oracle.set_threads(os.cpu_count() or 1)
-    p = oracle.Params(n=w["n"], nu=w["nu"], dt=w["dt"], force_amp=w.get("force_amp", 0.0),
-                      force_k=w.get("force_k", 0))
-    a = a0
-    t0 = time.perf_counter()
-    steps = 0
-    while steps < args.steps:
-        a = oracle.step(a, p, 1)
-        steps += 1
-        if time.perf_counter() - t0 > args.cpu_budget * 4:
-            break
-    dt = time.perf_counter() - t0
+    mem = members(w)
+    steps, dt, cores = oracle_steps(mem, args.cpu_budget * 4, args.steps)
     v = steps / dt
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s",
+    unit = "run-steps/s" if len(mem[0]) > 1 else "steps/s"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit,
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": steps, "warmup": 0,
             "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": w["desc"], "n": w["n"]},
-            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
                              "sample": f"{steps} of {args.steps} RK2 steps of the {w['n']}^3 "
                                        f"workload (bounded to {args.cpu_budget * 4:.0f} s)"},
-            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -38,13 +38,14 @@ struct Run {
     // plain form (full half layout)
     void *un = nullptr, *u1 = nullptr, *wn = nullptr, *work = nullptr, *phys = nullptr;
     void *etab = nullptr;   // exp(-nu k^2 dt) by integer k^2
-    // fused form
-    FusedRun fz{};
-    // diagnostics
+    // fused form: the run is member gidx of group `group` of the context
+    int group = -1, gidx = 0;
+    // diagnostics (plain form owns them; fused runs point into their group)
     double *part = nullptr;
     double *series = nullptr;
     unsigned long long *counter = nullptr;
     int nparts = 0;
+    bool owns_diag = true;
 };
 
 }  // namespace
@@ -54,6 +55,7 @@ struct ns_ctx {
     cudaStream_t stream = nullptr;   // caller's stream
     cudaStream_t cap = nullptr;      // private stream for graph capture
     std::vector<Run> runs;
+    std::vector<FusedRun> groups;   // fused form: runs grouped by N
     std::map<int, FftRes> fft;
     ns_status sticky = NS_OK;
     int *flags = nullptr;            // device error word (bit 0: non-finite energy)
@@ -310,13 +312,21 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
 
 bool use_fused(const ns_ctx *c) { return c->prec == NS_FP32 && fused_enabled(); }
 
-ns_status run_step(ns_ctx *c, Run &r, cudaStream_t s, Tracer *tr) {
+// One RK2 step of every run of the context: one batched sequence of launches
+// per group of the fused form, or the plain sequence per run.
+ns_status step_all(ns_ctx *c, cudaStream_t s, Tracer *tr) {
     if (use_fused(c)) {
-        cudaError_t e = fused_step(r.fz, r.series, kSeriesCap, r.counter, c->flags, s, tr);
-        if (e != cudaSuccess) return fail_cuda(c, e);
+        for (FusedRun &g : c->groups) {
+            cudaError_t e = fused_step(g, c->flags, s, tr);
+            if (e != cudaSuccess) return fail_cuda(c, e);
+        }
         return NS_OK;
     }
-    return c->prec == NS_FP64 ? plain_step<double>(c, r, s, tr) : plain_step<float>(c, r, s, tr);
+    for (Run &r : c->runs) {
+        ns_status st = c->prec == NS_FP64 ? plain_step<double>(c, r, s, tr) : plain_step<float>(c, r, s, tr);
+        if (st != NS_OK) return st;
+    }
+    return NS_OK;
 }
 
 ns_status build_graph(ns_ctx *c) {
@@ -328,11 +338,7 @@ ns_status build_graph(ns_ctx *c) {
         if (st != NS_OK) return st;
     }
     NS_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    ns_status st = NS_OK;
-    for (Run &r : c->runs) {
-        st = run_step(c, r, c->cap, nullptr);
-        if (st != NS_OK) break;
-    }
+    ns_status st = step_all(c, c->cap, nullptr);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap, &g);
     if (st != NS_OK) {
@@ -347,10 +353,14 @@ ns_status build_graph(ns_ctx *c) {
 }
 
 void free_run(Run &r) {
-    void *ps[] = {r.un, r.u1, r.wn, r.work, r.phys, r.etab, r.part, r.series, r.counter};
+    void *ps[] = {r.un, r.u1, r.wn, r.work, r.phys, r.etab};
     for (void *p : ps)
         if (p) cudaFree(p);
-    fused_free(r.fz);
+    if (r.owns_diag) {
+        void *qs[] = {r.part, r.series, r.counter};
+        for (void *p : qs)
+            if (p) cudaFree(p);
+    }
 }
 
 // Entry check: a null context is an argument error; a context that already
@@ -399,12 +409,13 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
     if (!c || run < 0 || run >= (int)c->runs.size() || !out || len < 1) return NS_ERR_ARG;
     const Run &r = c->runs[run];
     if (use_fused(c)) {
+        const FusedRun &g = c->groups[r.group];
         char tune[512];
-        fused_describe(r.fz, tune, sizeof(tune));
+        fused_describe(g, tune, sizeof(tune));
         snprintf(out, len,
                  "{\"form\": \"fused FP32\", \"n\": %d, \"K\": %d, \"state_modes\": %ld, "
-                 "\"passes\": %s}",
-                 r.n, r.fz.K, 3 * r.fz.M, tune);
+                 "\"runs_in_group\": %d, \"passes\": %s}",
+                 r.n, g.K, 3 * g.M, g.nr, tune);
     } else {
         snprintf(out, len, "{\"form\": \"plain %s\", \"n\": %d, \"cols_per_cta\": %d}",
                  c->prec == NS_FP64 ? "FP64" : "FP32", r.n,
@@ -452,20 +463,42 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
         maxbins = std::max(maxbins, ns_nbins(r.n));
         FftRes *f;
         if ((st = get_fft(c, r.n, &f)) != NS_OK) return bail(st);
-        if (use_fused(c)) {
-            e = fused_alloc(r.fz, r.p, (const float2 *)f->tw, c->stream);
-            if (e != cudaSuccess) return bail(fail_cuda(nullptr, e));
-            r.nparts = r.fz.nparts;
-        } else {
-            st = prec == NS_FP64 ? plain_alloc<double>(c, r) : plain_alloc<float>(c, r);
-            if (st != NS_OK) return bail(st);
-        }
+        if (use_fused(c)) continue;   // grouped below
+        st = prec == NS_FP64 ? plain_alloc<double>(c, r) : plain_alloc<float>(c, r);
+        if (st != NS_OK) return bail(st);
         if ((e = dalloc(&r.part, sizeof(double) * 2 * std::max(r.nparts, 1))) != cudaSuccess ||
             (e = dalloc(&r.series, sizeof(double) * 2 * kSeriesCap)) != cudaSuccess ||
             (e = dalloc(&r.counter, sizeof(unsigned long long))) != cudaSuccess)
             return bail(fail_cuda(nullptr, e));
-        if (use_fused(c)) r.fz.part = r.part;
         cudaMemset(r.counter, 0, sizeof(unsigned long long));
+    }
+    if (use_fused(c)) {
+        // runs of the same N form one group (in order of first appearance)
+        std::vector<int> order;
+        std::map<int, std::vector<int>> members;
+        for (int i = 0; i < nruns; i++) {
+            if (!members.count(c->runs[i].n)) order.push_back(c->runs[i].n);
+            members[c->runs[i].n].push_back(i);
+        }
+        c->groups.resize(order.size());
+        for (size_t gi = 0; gi < order.size(); gi++) {
+            std::vector<ns_run_params> ps;
+            for (int i : members[order[gi]]) ps.push_back(c->runs[i].p);
+            FftRes *f;
+            if ((st = get_fft(c, order[gi], &f)) != NS_OK) return bail(st);
+            e = fused_alloc(c->groups[gi], ps, (const float2 *)f->tw, kSeriesCap, c->stream);
+            if (e != cudaSuccess) return bail(fail_cuda(nullptr, e));
+            const std::vector<int> &mem = members[order[gi]];
+            for (size_t j = 0; j < mem.size(); j++) {
+                Run &r = c->runs[mem[j]];
+                FusedRun &g = c->groups[gi];
+                r.group = (int)gi;
+                r.gidx = (int)j;
+                r.owns_diag = false;
+                r.series = g.series + (long)j * g.cap * 2;
+                r.counter = g.counter + j;
+            }
+        }
     }
     if ((e = dalloc(&c->spec, sizeof(double) * maxbins)) != cudaSuccess ||
         (e = dalloc(&c->ens, sizeof(double) * maxbins)) != cudaSuccess)
@@ -481,6 +514,7 @@ void ns_destroy(ns_ctx *c) {
     cudaDeviceSynchronize();
     if (c->graph) cudaGraphExecDestroy(c->graph);
     for (Run &r : c->runs) free_run(r);
+    for (FusedRun &g : c->groups) fused_free(g);
     for (auto &kv : c->fft) {
         if (kv.second.tw) cudaFree(kv.second.tw);
         if (kv.second.scratch) cudaFree(kv.second.scratch);
@@ -503,8 +537,8 @@ ns_status ns_set_state(ns_ctx *c, int run, const void *uhat, int on_device) {
             ns_status s2 = ensure_staging(c, kStageChunk);
             if (s2 != NS_OK) return s2;
         }
-        cudaError_t e = fused_set_state(r.fz, (const double2 *)uhat, on_device, c->staging,
-                                        kStageChunk, c->stream);
+        cudaError_t e = fused_set_state(c->groups[r.group], r.gidx, (const double2 *)uhat, on_device,
+                                        c->staging, kStageChunk, c->stream);
         if (e != cudaSuccess) return fail_cuda(c, e);
         return NS_OK;
     }
@@ -522,8 +556,8 @@ ns_status ns_get_state(ns_ctx *c, int run, void *uhat, int on_device) {
             ns_status s2 = ensure_staging(c, kStageChunk);
             if (s2 != NS_OK) return s2;
         }
-        cudaError_t e = fused_get_state(r.fz, (double2 *)uhat, on_device, c->staging, kStageChunk,
-                                        c->stream);
+        cudaError_t e = fused_get_state(c->groups[r.group], r.gidx, (double2 *)uhat, on_device,
+                                        c->staging, kStageChunk, c->stream);
         if (e != cudaSuccess) return fail_cuda(c, e);
     } else {
         st = c->prec == NS_FP64 ? plain_get_state<double>(c, r, (double2 *)uhat, on_device)
@@ -591,7 +625,7 @@ ns_status ns_energy_spectrum(ns_ctx *c, int run, double *spec, int nbins, double
     Run &r = c->runs[run];
     const int nb = ns_nbins(r.n);
     if (use_fused(c))
-        NS_CK(fused_spectrum(r.fz, nb, c->spec, c->ens, c->stream));
+        NS_CK(fused_spectrum(c->groups[r.group], r.gidx, nb, c->spec, c->ens, c->stream));
     else if (c->prec == NS_FP64)
         NS_CK(plain_spectrum<double>((const double2 *)r.un, r.n, nb, c->spec, c->ens, c->stream));
     else
@@ -648,8 +682,7 @@ ns_status ns_kernel_census(ns_ctx *c, int nsteps, ns_kernel_time *out, int max, 
     Tracer tr;
     tr.s = c->stream;
     for (int i = 0; i < nsteps; i++)
-        for (Run &r : c->runs)
-            if ((st = run_step(c, r, c->stream, &tr)) != NS_OK) return st;
+        if ((st = step_all(c, c->stream, &tr)) != NS_OK) return st;
     if (tr.err != cudaSuccess) return fail_cuda(c, tr.err);
     NS_CK(cudaStreamSynchronize(c->stream));
     std::vector<ns_kernel_time> agg;

@@ -74,8 +74,9 @@ __host__ __device__ inline int fz_line_stride(int n) {
 // back over fields 0..2 of the same lines.
 template <int E>
 __global__ void __launch_bounds__(256)
-k_fused_z(float2 *buf, long fs, int N, int Mz, long nlines, int L, Plan pl,
+k_fused_z(float2 *buf, long fs, int N, int Mz, long nlines, int L, long brun, Plan pl,
           const float2 *__restrict__ tw) {
+    buf += blockIdx.y * brun;   // run of the group
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *sm = reinterpret_cast<float2 *>(smraw);
     const int n = N / 2, Tn = n / E;
@@ -146,12 +147,14 @@ k_fused_z(float2 *buf, long fs, int N, int Mz, long nlines, int L, Plan pl,
 
 // 1/N^3, projection, forcing and the RK2 stage on the compact state; at
 // stage 2 also the per-block FP64 energy and enstrophy partial sums of the
-// new state (grid-stride with a fixed grid: deterministic).
+// new state (grid-stride with a fixed grid: deterministic).  Grid y is the
+// run of the group; each run has its own parameters and factor table.
 struct FzUpdate {
     int n, K, Mx, Mz;
-    int stage, dealias, force_k;
-    float dt, force_amp;
-    long M;   // compact modes per component
+    int stage;
+    long M;          // compact modes per component
+    int nk2;         // entries of one run's factor table
+    int nparts;      // partial sums per run
 };
 
 __device__ __forceinline__ void fz_forcing(int kx, int ky, int kz, int kf, float F, float2 &fx,
@@ -174,9 +177,16 @@ __device__ __forceinline__ void fz_forcing(int kx, int ky, int kz, int kf, float
 
 __global__ void __launch_bounds__(256)
 k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__restrict__ nl,
-               const float *__restrict__ etab, FzUpdate u, double *part) {
+               const float *__restrict__ etab, const FzRunParams *__restrict__ rp, FzUpdate u,
+               double *part) {
     __shared__ double sh[512];
     const long M = u.M;
+    const int run = blockIdx.y;
+    a += run * 3 * M;
+    a1 += run * 3 * M;
+    nl += run * 3 * M;
+    etab += (long)run * u.nk2;
+    const FzRunParams q = rp[run];
     const float inv = (float)(1.0 / ((double)u.n * u.n * u.n));
     double e_acc = 0.0, o_acc = 0.0;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
@@ -186,7 +196,7 @@ k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__
         const int kx = fz_compact_signed(ikx, u.Mx, u.K), ky = fz_compact_signed(iky, u.Mx, u.K);
         const int k2 = kx * kx + ky * ky + kz * kz;
         bool keep = k2 > 0;
-        if (u.dealias == 1 && 9L * k2 >= (long)u.n * u.n) keep = false;
+        if (q.dealias == 1 && 9L * k2 >= (long)u.n * u.n) keep = false;
         float2 o0 = make_float2(0.f, 0.f), o1 = o0, o2 = o0;
         if (keep) {
             float2 vx = cscale(nl[m], inv), vy = cscale(nl[M + m], inv), vz = cscale(nl[2 * M + m], inv);
@@ -195,17 +205,17 @@ k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__
             vx = csub(vx, cscale(kv, fkx * ik2));
             vy = csub(vy, cscale(kv, fky * ik2));
             vz = csub(vz, cscale(kv, fkz * ik2));
-            fz_forcing(kx, ky, kz, u.force_k, u.force_amp, vx, vy, vz);
+            fz_forcing(kx, ky, kz, q.force_k, q.force_amp, vx, vy, vz);
             const float e = etab[k2];
             if (u.stage == 1) {
-                o0 = cscale(cadd(a[m], cscale(vx, u.dt)), e);
-                o1 = cscale(cadd(a[M + m], cscale(vy, u.dt)), e);
-                o2 = cscale(cadd(a[2 * M + m], cscale(vz, u.dt)), e);
+                o0 = cscale(cadd(a[m], cscale(vx, q.dt)), e);
+                o1 = cscale(cadd(a[M + m], cscale(vy, q.dt)), e);
+                o2 = cscale(cadd(a[2 * M + m], cscale(vz, q.dt)), e);
             } else {
                 const float he = 0.5f * e;
-                o0 = cadd(cscale(a[m], he), cscale(cadd(a1[m], cscale(vx, u.dt)), 0.5f));
-                o1 = cadd(cscale(a[M + m], he), cscale(cadd(a1[M + m], cscale(vy, u.dt)), 0.5f));
-                o2 = cadd(cscale(a[2 * M + m], he), cscale(cadd(a1[2 * M + m], cscale(vz, u.dt)), 0.5f));
+                o0 = cadd(cscale(a[m], he), cscale(cadd(a1[m], cscale(vx, q.dt)), 0.5f));
+                o1 = cadd(cscale(a[M + m], he), cscale(cadd(a1[M + m], cscale(vy, q.dt)), 0.5f));
+                o2 = cadd(cscale(a[2 * M + m], he), cscale(cadd(a1[2 * M + m], cscale(vz, q.dt)), 0.5f));
             }
         }
         float2 *dst = u.stage == 1 ? a1 : a;
@@ -223,9 +233,35 @@ k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__
     if (u.stage == 2) {
         block_sum2(e_acc, o_acc, sh);
         if (threadIdx.x == 0) {
-            part[2 * blockIdx.x] = e_acc;
-            part[2 * blockIdx.x + 1] = o_acc;
+            double *pp = part + 2 * ((long)run * u.nparts + blockIdx.x);
+            pp[0] = e_acc;
+            pp[1] = o_acc;
         }
+    }
+}
+
+// One block per run: sum that run's partials in a fixed order, append
+// (E, Omega) to its ring buffer at slot counter % cap, bump the counter, and
+// raise bit 0 of *flags if E is not finite.
+__global__ void __launch_bounds__(256)
+k_fz_energy_final(const double *__restrict__ part, int nparts, double *series, int cap,
+                  unsigned long long *counter, int *flags) {
+    __shared__ double sh[512];
+    const int run = blockIdx.x;
+    const double *pp = part + 2L * run * nparts;
+    double e = 0.0, om = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        e += pp[2 * i];
+        om += pp[2 * i + 1];
+    }
+    block_sum2(e, om, sh);
+    if (threadIdx.x == 0) {
+        const unsigned long long c = counter[run];
+        double *sr = series + 2L * run * cap;
+        sr[2 * (c % cap)] = e;
+        sr[2 * (c % cap) + 1] = om;
+        counter[run] = c + 1;
+        if (!isfinite(e)) atomicOr(flags, 1);
     }
 }
 
@@ -370,7 +406,7 @@ cudaError_t prepare_fused_kernels() {
 }
 
 static cudaError_t launch_strided(const void *k, const FzPass &ps, const Plan &pl, const float2 *tw,
-                                  int ct, cudaStream_t s) {
+                                  int ct, int nr, cudaStream_t s) {
     if (!k || ct < 1 || ct * (pl.n / pl.E) > 512) return cudaErrorInvalidValue;
     const int T = pl.n / pl.E;
     const size_t smem = (size_t)pl.n * (ct + 1) * sizeof(float2);
@@ -382,7 +418,7 @@ static cudaError_t launch_strided(const void *k, const FzPass &ps, const Plan &p
     FzPass p = ps;
     Plan q = pl;
     void *args[] = {(void *)&p, (void *)&q, (void *)&tw};
-    return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(ct * T), args, smem, s);
+    return cudaLaunchKernel(k, dim3((unsigned)blocks, (unsigned)nr), dim3(ct * T), args, smem, s);
 }
 
 static cudaError_t launch_z_ct(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
@@ -395,9 +431,11 @@ static cudaError_t launch_z_ct(FusedRun &f, const PassCfg &cfg, cudaStream_t s) 
     float2 *buf = f.bbuf;
     long fs = (long)f.n * f.n * f.Mz;
     int Mz = f.Mz;
+    long brun = f.sB;
     const float2 *tw = f.tw;
-    void *args[] = {(void *)&buf, (void *)&fs, (void *)&Mz, (void *)&nlines, (void *)&tw};
-    return cudaLaunchKernel(z.k, dim3((unsigned)blocks), dim3(z.threads), args, z.smem, s);
+    void *args[] = {(void *)&buf, (void *)&fs, (void *)&Mz, (void *)&nlines, (void *)&brun, (void *)&tw};
+    return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem,
+                            s);
 }
 
 static cudaError_t launch_z(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
@@ -418,19 +456,21 @@ static cudaError_t launch_z(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
     Plan q = cfg.pl;
     const float2 *tw = f.tw;
     int LL = L;
+    long brun = f.sB;
     void *args[] = {(void *)&buf, (void *)&fs, (void *)&N, (void *)&Mz, (void *)&nlines, (void *)&LL,
-                    (void *)&q, (void *)&tw};
-    return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(6 * L * Tn), args, smem, s);
+                    (void *)&brun, (void *)&q, (void *)&tw};
+    return cudaLaunchKernel(k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(6 * L * Tn), args, smem, s);
 }
 
 // Pass descriptors of one RK2 stage reading the state src.
 static void pass_descs(const FusedRun &f, const float2 *src, FzPass &A, FzPass &B, FzPass &D, FzPass &Ep) {
     const int N = f.n, K = f.K, Mx = f.Mx, Mz = f.Mz;
     const long MxMz = (long)Mx * Mz, NMz = (long)N * Mz;
-    A = FzPass{src, f.abuf, MxMz, f.M, MxMz, (long)Mx * NMz, Mz, NMz, 6, Mz, K, Mx};
-    B = FzPass{f.abuf, f.bbuf, NMz, (long)Mx * NMz, NMz, (long)N * NMz, NMz, Mz, 6, Mz, K, Mx};
-    D = FzPass{f.bbuf, f.abuf, NMz, (long)N * NMz, NMz, (long)N * MxMz, Mz, MxMz, 3, Mz, K, Mx};
-    Ep = FzPass{f.abuf, f.nl, MxMz, (long)N * MxMz, MxMz, f.M, MxMz, Mz, 3, Mz, K, Mx};
+    const long S3 = 3 * f.M;
+    A = FzPass{src, f.abuf, MxMz, f.M, MxMz, (long)Mx * NMz, Mz, NMz, 6, Mz, K, Mx, S3, f.sA};
+    B = FzPass{f.abuf, f.bbuf, NMz, (long)Mx * NMz, NMz, (long)N * NMz, NMz, Mz, 6, Mz, K, Mx, f.sA, f.sB};
+    D = FzPass{f.bbuf, f.abuf, NMz, (long)N * NMz, NMz, (long)N * MxMz, Mz, MxMz, 3, Mz, K, Mx, f.sB, f.sA};
+    Ep = FzPass{f.abuf, f.nl, MxMz, (long)N * MxMz, MxMz, f.M, MxMz, Mz, 3, Mz, K, Mx, f.sA, S3};
 }
 
 static cudaError_t run_pass_ct(FusedRun &f, int which, const PassCfg &cfg, const FzPass &ps,
@@ -445,7 +485,7 @@ static cudaError_t run_pass_ct(FusedRun &f, int which, const PassCfg &cfg, const
     FzPass p = ps;
     const float2 *tw = f.tw;
     void *args[] = {(void *)&p, (void *)&tw};
-    return cudaLaunchKernel(z.k, dim3((unsigned)blocks), dim3(z.threads), args, z.smem, s);
+    return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem, s);
 }
 
 static cudaError_t run_pass(FusedRun &f, int which, const PassCfg &cfg, const FzPass &ps, cudaStream_t s) {
@@ -454,7 +494,7 @@ static cudaError_t run_pass(FusedRun &f, int which, const PassCfg &cfg, const Fz
     const void *k = which == 0 ? strided_for<+1, true, false, true>(E)
                   : which == 1 ? strided_for<+1, true, false, false>(E)
                                : strided_for<-1, false, true, false>(E);
-    return launch_strided(k, ps, cfg.pl, f.tw, cfg.ct, s);
+    return launch_strided(k, ps, cfg.pl, f.tw, cfg.ct, f.nr, s);
 }
 
 // ---------------------------------------------------------------- autotuner
@@ -653,32 +693,52 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
     return cudaSuccess;
 }
 
-cudaError_t fused_alloc(FusedRun &f, const ns_run_params &p, const float2 *tw, cudaStream_t s) {
-    f.p = p;
-    f.n = p.n;
-    f.K = (p.n - 1) / 3;     // largest k with 3k < n
+cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, const float2 *tw,
+                        int series_cap, cudaStream_t s) {
+    if (runs.empty()) return cudaErrorInvalidValue;
+    f.p = runs;
+    f.nr = (int)runs.size();
+    f.n = runs[0].n;
+    for (const ns_run_params &q : runs)
+        if (q.n != f.n) return cudaErrorInvalidValue;
+    f.K = (f.n - 1) / 3;     // largest k with 3k < n
     f.Mx = 2 * f.K + 1;
     f.Mz = f.K + 1;
     f.tw = tw;
+    f.cap = series_cap;
     if (!make_plan(f.n, &f.plN) || !make_plan(f.n / 2, &f.plH)) return cudaErrorInvalidValue;
     f.M = (long)f.Mx * f.Mx * f.Mz;
-    const long Aelems = 6L * f.Mx * f.n * f.Mz;          // also holds D (3 fields)
-    const long Belems = 6L * f.n * f.n * f.Mz;           // also holds C (3 fields)
+    f.sA = 6L * f.Mx * f.n * f.Mz;          // also holds D (3 fields)
+    f.sB = 6L * f.n * f.n * f.Mz;           // also holds C (3 fields)
+    const long S3 = 3 * f.M, nr = f.nr;
     cudaError_t e;
-    if ((e = cudaMalloc(&f.a, 3 * f.M * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.a1, 3 * f.M * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.nl, 3 * f.M * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.abuf, Aelems * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.bbuf, Belems * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(f.a, 0, 3 * f.M * sizeof(float2), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(f.a1, 0, 3 * f.M * sizeof(float2), s)) != cudaSuccess) return e;
-    const int nk2 = 3 * f.K * f.K + 1;
-    std::vector<float> h(nk2);
-    for (int k2 = 0; k2 < nk2; k2++) h[k2] = (float)exp(-p.nu * (double)k2 * p.dt);
-    if ((e = cudaMalloc(&f.etab, nk2 * sizeof(float))) != cudaSuccess) return e;
-    if ((e = cudaMemcpy(f.etab, h.data(), nk2 * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMalloc(&f.a, nr * S3 * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.a1, nr * S3 * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.nl, nr * S3 * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.abuf, nr * f.sA * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.bbuf, nr * f.sB * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(f.a, 0, nr * S3 * sizeof(float2), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(f.a1, 0, nr * S3 * sizeof(float2), s)) != cudaSuccess) return e;
+    // factor tables exp(-nu k^2 dt) in FP64, rounded once, and per-run parameters
+    f.nk2 = 3 * f.K * f.K + 1;
+    std::vector<float> h((size_t)nr * f.nk2);
+    std::vector<FzRunParams> hp(nr);
+    for (long r = 0; r < nr; r++) {
+        const ns_run_params &q = runs[r];
+        for (int k2 = 0; k2 < f.nk2; k2++) h[r * f.nk2 + k2] = (float)exp(-q.nu * (double)k2 * q.dt);
+        hp[r] = FzRunParams{(float)q.dt, (float)q.force_amp, q.force_k, q.dealias};
+    }
+    if ((e = cudaMalloc(&f.etab, h.size() * sizeof(float))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(f.etab, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&f.rp, nr * sizeof(FzRunParams))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(f.rp, hp.data(), nr * sizeof(FzRunParams), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
     f.nparts = (int)std::min<long>(1024, std::max<long>(1, (f.M + 4095) / 4096));
+    if ((e = cudaMalloc(&f.part, nr * f.nparts * 2 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.series, nr * (long)f.cap * 2 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.counter, nr * sizeof(unsigned long long))) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(f.counter, 0, nr * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if ((e = prepare_fused_kernels()) != cudaSuccess) return e;
     const int ct = default_ct(sizeof(float2), f.n);
     for (int i = 0; i < 4; i++) f.sp[i] = PassCfg{f.plN, ct};
@@ -687,20 +747,27 @@ cudaError_t fused_alloc(FusedRun &f, const ns_run_params &p, const float2 *tw, c
 }
 
 void fused_free(FusedRun &f) {
-    void *ps[] = {f.a, f.a1, f.nl, f.abuf, f.bbuf, f.etab};
+    void *ps[] = {f.a, f.a1, f.nl, f.abuf, f.bbuf, f.etab, f.rp, f.part, f.series, f.counter};
     for (void *p : ps)
         if (p) cudaFree(p);
     f.a = f.a1 = f.nl = f.abuf = f.bbuf = nullptr;
     f.etab = nullptr;
+    f.rp = nullptr;
+    f.part = f.series = nullptr;
+    f.counter = nullptr;
 }
 
 static cudaError_t launch_update(FusedRun &f, const FzUpdate &u, cudaStream_t s) {
-    k_fused_update<<<f.nparts, 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, u, f.part);
+    k_fused_update<<<dim3(f.nparts, f.nr), 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, f.rp, u, f.part);
     return cudaGetLastError();
 }
 
-cudaError_t fused_step(FusedRun &f, double *series, int cap, unsigned long long *counter, int *flags,
-                       cudaStream_t s, Tracer *tr) {
+static cudaError_t launch_energy_final(FusedRun &f, int *flags, cudaStream_t s) {
+    k_fz_energy_final<<<f.nr, 256, 0, s>>>(f.part, f.nparts, f.series, f.cap, f.counter, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t fused_step(FusedRun &f, int *flags, cudaStream_t s, Tracer *tr) {
     cudaError_t e;
     for (int stage = 1; stage <= 2; stage++) {
         FzPass A, B, D, Ep;
@@ -715,12 +782,11 @@ cudaError_t fused_step(FusedRun &f, double *series, int cap, unsigned long long 
         if (e != cudaSuccess) return e;
         e = NSK_TIMED(tr, "fused_E_x_forward", run_pass(f, 2, f.sp[3], Ep, s));
         if (e != cudaSuccess) return e;
-        FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.p.dealias, f.p.force_k, (float)f.p.dt,
-                   (float)f.p.force_amp, f.M};
+        FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.M, f.nk2, f.nparts};
         e = NSK_TIMED(tr, "fused_update", launch_update(f, u, s));
         if (e != cudaSuccess) return e;
     }
-    return NSK_TIMED(tr, "energy_final", energy_final(f.part, f.nparts, series, cap, counter, flags, s));
+    return NSK_TIMED(tr, "energy_final", launch_energy_final(f, flags, s));
 }
 
 int fused_describe(const FusedRun &f, char *out, int len) {
@@ -742,13 +808,15 @@ int fused_describe(const FusedRun &f, char *out, int len) {
     return w;
 }
 
-cudaError_t fused_set_state(FusedRun &f, const double2 *src, int on_device, void *staging,
+cudaError_t fused_set_state(FusedRun &f, int run, const double2 *src, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s) {
     const int n = f.n, nh = n / 2 + 1;
     const long plane = (long)n * nh, M = (long)n * plane;
     const int pc = on_device ? n : (int)std::max<size_t>(1, staging_bytes / (plane * sizeof(double2)));
+    float2 *a = f.a + (long)run * 3 * f.M;
+    const int dealias = f.p[run].dealias;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(f.a, 0, 3 * f.M * sizeof(float2), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a, 0, 3 * f.M * sizeof(float2), s)) != cudaSuccess) return e;
     const int ranges[2][2] = {{0, f.K + 1}, {n - f.K, n}};
     for (int c = 0; c < 3; c++) {
         for (auto &r : ranges) {
@@ -762,8 +830,8 @@ cudaError_t fused_set_state(FusedRun &f, const double2 *src, int on_device, void
                     p = (const double2 *)staging;
                 }
                 const long work = (long)cnt * f.Mx * f.Mz;
-                k_fz_load<<<grid_of(work, 256, 152L * 16), 256, 0, s>>>(p, f.a + c * f.M, kx0, cnt, n, f.K,
-                                                                      f.Mx, f.Mz, f.p.dealias);
+                k_fz_load<<<grid_of(work, 256, 152L * 16), 256, 0, s>>>(p, a + c * f.M, kx0, cnt, n, f.K,
+                                                                      f.Mx, f.Mz, dealias);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
                 if (!on_device && (e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
             }
@@ -772,11 +840,12 @@ cudaError_t fused_set_state(FusedRun &f, const double2 *src, int on_device, void
     return cudaSuccess;
 }
 
-cudaError_t fused_get_state(FusedRun &f, double2 *dst, int on_device, void *staging,
+cudaError_t fused_get_state(FusedRun &f, int run, double2 *dst, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s) {
     const int n = f.n, nh = n / 2 + 1;
     const long plane = (long)n * nh, M = (long)n * plane;
     const int pc = on_device ? n : (int)std::max<size_t>(1, staging_bytes / (plane * sizeof(double2)));
+    const float2 *a = f.a + (long)run * 3 * f.M;
     cudaError_t e;
     for (int c = 0; c < 3; c++) {
         for (int kx0 = 0; kx0 < n; kx0 += pc) {
@@ -784,7 +853,7 @@ cudaError_t fused_get_state(FusedRun &f, double2 *dst, int on_device, void *stag
             double2 *out = dst + c * M + (long)kx0 * plane;
             double2 *d = on_device ? out : (double2 *)staging;
             const long work = (long)cnt * plane;
-            k_fz_store<<<grid_of(work, 256, 152L * 16), 256, 0, s>>>(f.a + c * f.M, d, kx0, cnt, n, f.K,
+            k_fz_store<<<grid_of(work, 256, 152L * 16), 256, 0, s>>>(a + c * f.M, d, kx0, cnt, n, f.K,
                                                                    f.Mx, f.Mz);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if (!on_device) {
@@ -798,8 +867,8 @@ cudaError_t fused_get_state(FusedRun &f, double2 *dst, int on_device, void *stag
     return cudaSuccess;
 }
 
-cudaError_t fused_spectrum(FusedRun &f, int nbins, double *spec, double *ens, cudaStream_t s) {
-    CompactAcc acc{f.a, f.K, f.Mx, f.Mz, f.M};
+cudaError_t fused_spectrum(FusedRun &f, int run, int nbins, double *spec, double *ens, cudaStream_t s) {
+    CompactAcc acc{f.a + (long)run * 3 * f.M, f.K, f.Mx, f.Mz, f.M};
     k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, f.n, nbins, spec, ens);
     return cudaGetLastError();
 }

@@ -3,6 +3,8 @@
 #include "../../include/ns.h"
 #include "ns_internal.h"
 
+#include <vector>
+
 namespace nsk {
 
 // Launch configuration of one pass: its radix plan (elements per thread) and
@@ -33,38 +35,55 @@ bool fzs_lookup_A(int N, int E, int CT, FzsKernel *out);    // x inverse + curl
 bool fzs_lookup_B(int N, int E, int CT, FzsKernel *out);    // y inverse
 bool fzs_lookup_DE(int N, int E, int CT, FzsKernel *out);   // y / x forward
 
-// One run of the fused form.  Compact state layout [c][ikx][iky][kz] with
+// Per-run parameters of the update kernel (device array, one per run).
+struct FzRunParams {
+    float dt, force_amp;
+    int force_k, dealias;
+};
+
+// A group of nr runs of the fused form that share the grid size N; their
+// buffers are contiguous ([run][...]) so that one launch per pass (grid y =
+// run) advances all of them.  Compact state layout [c][ikx][iky][kz] with
 // ikx, iky in [0, Mx) (index k for k >= 0, k + Mx for k < 0) and kz in
 // [0, Mz): only the modes the cubic 2/3 rule keeps, |kx|, |ky|, kz <= K.
 struct FusedRun {
-    ns_run_params p{};
+    int nr = 0;
+    std::vector<ns_run_params> p;   // per run
     int n = 0, K = 0, Mx = 0, Mz = 0;
     long M = 0;                  // compact modes per component, Mx * Mx * Mz
     Plan plN{}, plH{};           // default plans of length n (x, y) and n/2 (z)
     PassCfg sp[4];               // passes A, B, D, E (chosen by the autotuner)
     PassCfg zc;                  // pass C
     const float2 *tw = nullptr;  // exp(-2 pi i t / n), t < n (owned by the context)
-    float2 *a = nullptr;         // state
-    float2 *a1 = nullptr;        // first-stage state
-    float2 *nl = nullptr;        // unnormalised transform of u x w (compact)
-    float2 *abuf = nullptr;      // pass A output (6 fields), reused for pass D (3)
-    float2 *bbuf = nullptr;      // pass B output (6 fields), pass C in place (3)
-    float *etab = nullptr;       // exp(-nu k^2 dt) by integer k^2 <= 3 K^2
-    int nparts = 0;              // energy partial sums (update kernel blocks)
-    double *part = nullptr;      // [nparts][2], owned by the context
+    float2 *a = nullptr;         // state                       [nr][3][M]
+    float2 *a1 = nullptr;        // first-stage state           [nr][3][M]
+    float2 *nl = nullptr;        // transform of u x w (compact)[nr][3][M]
+    float2 *abuf = nullptr;      // pass A output (6 fields), reused for pass D (3)   [nr][sA]
+    float2 *bbuf = nullptr;      // pass B output (6 fields), pass C in place (3)     [nr][sB]
+    long sA = 0, sB = 0;         // per-run elements of abuf and bbuf
+    float *etab = nullptr;       // exp(-nu k^2 dt) by integer k^2 <= 3 K^2            [nr][nk2]
+    int nk2 = 0;
+    FzRunParams *rp = nullptr;   // [nr]
+    int nparts = 0;              // energy partial sums per run (update kernel blocks)
+    double *part = nullptr;      // [nr][nparts][2]
+    double *series = nullptr;    // [nr][cap][2] energy / enstrophy ring buffers
+    unsigned long long *counter = nullptr;   // [nr] steps recorded
+    int cap = 0;
 };
 
 bool fused_enabled();
-cudaError_t fused_alloc(FusedRun &f, const ns_run_params &p, const float2 *tw, cudaStream_t s);
+// Allocate a group for runs (all of the same N) and tune its passes.
+cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, const float2 *tw,
+                        int series_cap, cudaStream_t s);
 void fused_free(FusedRun &f);
-cudaError_t fused_set_state(FusedRun &f, const double2 *src, int on_device, void *staging,
+cudaError_t fused_set_state(FusedRun &f, int run, const double2 *src, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s);
-cudaError_t fused_get_state(FusedRun &f, double2 *dst, int on_device, void *staging,
+cudaError_t fused_get_state(FusedRun &f, int run, double2 *dst, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s);
-cudaError_t fused_step(FusedRun &f, double *series, int cap, unsigned long long *counter,
-                       int *flags, cudaStream_t s, Tracer *tr);
+// One RK2 step of every run of the group.
+cudaError_t fused_step(FusedRun &f, int *flags, cudaStream_t s, Tracer *tr);
 // JSON text describing the chosen per-pass configuration; returns its length.
 int fused_describe(const FusedRun &f, char *out, int len);
-cudaError_t fused_spectrum(FusedRun &f, int nbins, double *spec, double *ens, cudaStream_t s);
+cudaError_t fused_spectrum(FusedRun &f, int run, int nbins, double *spec, double *ens, cudaStream_t s);
 
 }  // namespace nsk

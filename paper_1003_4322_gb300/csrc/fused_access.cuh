@@ -24,9 +24,11 @@ struct FzPass {
     long ofs, ors, obs;  // output field / row strides; outer stride of a column
     int nfields;         // output fields handled by the grid
     int Mz, K, Mx;
+    long irun, orun;     // input / output strides between the runs of a group (grid y)
 };
 
-// One column of a strided pass: the grid is fields x tiles (field fastest),
+// One column of a strided pass: grid x is fields x tiles (field fastest),
+// grid y the run of the group;
 // column `col` of field f, its outer index ou = col / Mz and kz = col % Mz.
 // IN_C: input rows are compact (only kept wavenumbers stored), the others
 // read as zero.  OUT_C: only kept output rows are stored.  CURL: pass A,
@@ -35,7 +37,11 @@ template <bool IN_C, bool OUT_C, bool CURL> struct FzColumn {
     int n, f;
     long col, ou, iz;
     bool valid;
+    const float2 *in;
+    float2 *out;
     __device__ __forceinline__ FzColumn(const FzPass &ps, int n_, int ct, int c) : n(n_) {
+        in = ps.in + blockIdx.y * ps.irun;
+        out = ps.out + blockIdx.y * ps.orun;
         f = blockIdx.x % ps.nfields;
         const long tile = blockIdx.x / ps.nfields;
         col = tile * ct + c;
@@ -47,9 +53,9 @@ template <bool IN_C, bool OUT_C, bool CURL> struct FzColumn {
         const int r = IN_C ? fz_compact(e, n, ps.K, ps.Mx) : e;
         if (!valid || r < 0) return make_float2(0.f, 0.f);
         if constexpr (!CURL) {
-            return ps.in[f * ps.ifs + r * ps.irs + col];
+            return in[f * ps.ifs + r * ps.irs + col];
         } else {
-            const float2 *b = ps.in + r * ps.irs + col;
+            const float2 *b = in + r * ps.irs + col;
             if (f < 3) return b[f * ps.ifs];
             const float kx = (float)fz_full_signed(e, n);
             const float ky = (float)fz_compact_signed((int)ou, ps.Mx, ps.K);
@@ -66,7 +72,7 @@ template <bool IN_C, bool OUT_C, bool CURL> struct FzColumn {
     __device__ __forceinline__ void store(const FzPass &ps, int e, float2 v) const {
         const int r = OUT_C ? fz_compact(e, n, ps.K, ps.Mx) : e;
         if (!valid || r < 0) return;
-        ps.out[f * ps.ofs + r * ps.ors + ou * ps.obs + iz] = v;
+        out[f * ps.ofs + r * ps.ors + ou * ps.obs + iz] = v;
     }
 };
 

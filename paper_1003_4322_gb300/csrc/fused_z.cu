@@ -24,8 +24,9 @@ template <int N> struct ZShape {
 
 template <int N, int WPB>
 __global__ void __launch_bounds__(32 * WPB)
-k_fused_z_ct(float2 *buf, long fs, int Mz, long nlines, const float2 *__restrict__ tw) {
+k_fused_z_ct(float2 *buf, long fs, int Mz, long nlines, long brun, const float2 *__restrict__ tw) {
     typedef ZShape<N> Z;
+    buf += blockIdx.y * brun;   // run of the group
     constexpr int n = Z::n, E = Z::E, T = Z::T, LPW = Z::LPW, LS = Z::LS;
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *sm = reinterpret_cast<float2 *>(smraw);

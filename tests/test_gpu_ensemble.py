@@ -1,0 +1,72 @@
+"""Ensembles: independent runs of uneven grid sizes in one context (runs of
+the same N are advanced together by one launch per pass).  Every member must
+equal the same run done alone, bit for bit, and match the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1003_4322_gb300 import inputs
+from tests.spectral_ref import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _members():
+    runs, ics = [], []
+    for r, n in enumerate([32, 48, 32, 24, 48, 32]):
+        runs.append(dict(n=n, nu=inputs.ensemble_nu(r), dt=1e-3,
+                         force_amp=0.5 if r % 2 else 0.0, force_k=3 if r % 2 else 0,
+                         dealias=r % 3 == 2 and 1 or 0))
+        ics.append(inputs.random_solenoidal_state(n, 1.0, 4.0, 1.0, 4000 + r,
+                                                  dealias=runs[-1]["dealias"]))
+    return runs, ics
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_ensemble_members_equal_single_runs_and_oracle(ns, prec):
+    from paper_1003_4322_gb300.solver import Solver
+    runs, ics = _members()
+    steps = 3
+    with Solver(runs, prec=prec) as s:
+        for i, a in enumerate(ics):
+            s.set_state(a, run=i)
+        s.step(steps)
+        got = [s.get_state(run=i) for i in range(len(runs))]
+        series = [s.series(run=i, count=steps) for i in range(len(runs))]
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    for i, (run, a0) in enumerate(zip(runs, ics)):
+        with Solver([run], prec=prec) as s1:
+            s1.set_state(a0)
+            s1.step(steps)
+            alone = s1.get_state()
+        assert np.array_equal(got[i], alone), f"member {i} differs from its single run"
+        ref = oracle.step(a0, oracle.Params(n=run["n"], nu=run["nu"], dt=run["dt"],
+                                            force_amp=run["force_amp"], force_k=run["force_k"],
+                                            dealias=run["dealias"]), steps)
+        assert rel_l2(got[i], ref) < tol
+        assert len(series[i][0]) == steps
+        assert abs(series[i][0][-1] - oracle.diagnostics(ref)[0]) < 20 * tol * series[i][0][-1]
+
+
+def test_config4_ensemble_shapes(ns):
+    """The 48-member ensemble of config 4 (16 runs each at 64^3, 96^3 and
+    128^3, FP32) initialises, steps and stays finite; one member of each size
+    matches its single run."""
+    from paper_1003_4322_gb300.solver import Solver
+    runs, ics = [], []
+    for r in range(48):
+        n = (64, 96, 128)[r // 16]
+        runs.append(dict(n=n, nu=inputs.ensemble_nu(r), dt=1e-3))
+        ics.append(inputs.turbulence_state(n, 4000 + r))
+    with Solver(runs, prec="fp32") as s:
+        for i, a in enumerate(ics):
+            s.set_state(a, run=i)
+        s.step(2)
+        picks = {i: s.get_state(run=i) for i in (3, 20, 40)}
+        energies = [s.energy_spectrum(run=i)[0] for i in range(48)]
+    assert all(np.isfinite(energies))
+    for i, st in picks.items():
+        with Solver([runs[i]], prec="fp32") as s1:
+            s1.set_state(ics[i])
+            s1.step(2)
+            assert np.array_equal(st, s1.get_state())
