@@ -65,6 +65,25 @@ def load_peaks():
     return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
 
 
+def captured_traffic(workload, prec, kernel):
+    """DRAM bytes per launch of a kernel from the committed ncu summary of this
+    workload, if the kernel sources are unchanged since the capture."""
+    import glob
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    h = hashlib.sha256()
+    for fn in sorted(glob.glob(os.path.join(ROOT, "paper_1003_4322_gb300", "csrc", "*"))):
+        with open(fn, "rb") as g:
+            h.update(g.read())
+    if h.hexdigest() != t.get("source_sha256"):
+        return None
+    return t.get(prec, {}).get(kernel)
+
+
 # FP64 FMA pipes: GB300 lists 1.25 TFLOP/s FP64 at its 2070 MHz maximum SM
 # clock over 152 SMs, i.e. 2 FP64 FMA (4 flop) per SM per clock.
 FP64_FLOP_PER_SM_CLK = 4.0
@@ -254,7 +273,8 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
     gbs = bytes_ / (per_launch_ms * 1e-3) / 1e9
     hbm_frac = gbs / peaks["hbm_gbs"]
     roof = {"kernel": name, "launches_per_step": launches / census_steps,
-            "share": tms / total, "avg_launch_ms": per_launch_ms, "traffic": None}
+            "share": tms / total, "avg_launch_ms": per_launch_ms,
+            "traffic": captured_traffic(w.get("name", ""), prec, name), "algorithmic_bytes": bytes_}
     if prec == "fp64":
         peak_flops = N_SM * FP64_FLOP_PER_SM_CLK * peaks["sm_max_mhz"] * 1e6
         tflops = flops / (per_launch_ms * 1e-3) / 1e12
@@ -510,6 +530,7 @@ def main():
                     help="override the workload's headline form")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
+    w["name"] = args.workload
     if args.prec and args.prec != w["prec"]:
         w["prec"] = args.prec
         w["companion"] = None
