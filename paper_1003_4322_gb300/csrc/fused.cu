@@ -374,14 +374,16 @@ static bool fzs_lookup(int which, int N, int E, int CT, FzsKernel *o) {
 
 cudaError_t prepare_fused_kernels() {
     const int Ns[] = {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+    const int zEs[] = {16, 12, 8, 6};
     for (int N : Ns)
-        for (int wpb = 2; wpb <= 4; wpb *= 2) {
-            ZctKernel z;
-            if (zct_lookup(N, wpb, &z)) {
-                cudaError_t e = allow_smem(z.k, 48 * 1024 + 1);
-                if (e != cudaSuccess) return e;
+        for (int zE : zEs)
+            for (int wpb = 1; wpb <= 4; wpb *= 2) {
+                ZctKernel z;
+                if (zct_lookup(N, zE, wpb, &z)) {
+                    cudaError_t e = allow_smem(z.k, 48 * 1024 + 1);
+                    if (e != cudaSuccess) return e;
+                }
             }
-        }
     const int Ects[] = {8, 12, 16, 32};
     for (int N : Ns)
         for (int E : Ects)
@@ -423,7 +425,7 @@ static cudaError_t launch_strided(const void *k, const FzPass &ps, const Plan &p
 
 static cudaError_t launch_z_ct(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
     ZctKernel z;
-    if (!zct_lookup(f.n, cfg.ct, &z)) return cudaErrorInvalidValue;
+    if (!zct_lookup(f.n, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(z.k, z.smem);
     if (e != cudaSuccess) return e;
     long nlines = (long)f.n * f.n;
@@ -661,10 +663,13 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
     }
     {
         float best = -1.f;
-        for (int wpb = 2; wpb <= 4; wpb *= 2) {
+        const int zEs[] = {16, 12, 8, 6};
+        for (int zE : zEs)
+        for (int wpb = 1; wpb <= 4; wpb *= 2) {
             ZctKernel z;
-            if (!zct_lookup(f.n, wpb, &z)) continue;
+            if (!zct_lookup(f.n, zE, wpb, &z)) continue;
             PassCfg cfg{f.plH, wpb, 1};
+            cfg.pl.E = zE;
             const float ms = time_launch([&]() { return launch_z(f, cfg, s); }, s, reps);
             if (ms > 0.f && (best < 0.f || ms < best)) {
                 best = ms;
@@ -799,8 +804,9 @@ int fused_describe(const FusedRun &f, char *out, int len) {
                       f.sp[i].ct);
     if (w < len && f.zc.kind == 1)
         w += snprintf(out + w, len - w,
-                      "\"C_z_nonlinear\": {\"kernel\": \"compile-time length\", \"warps_per_cta\": %d}}",
-                      f.zc.ct);
+                      "\"C_z_nonlinear\": {\"kernel\": \"compile-time length\", \"E\": %d, "
+                      "\"warps_per_cta\": %d}}",
+                      f.zc.pl.E, f.zc.ct);
     else if (w < len)
         w += snprintf(out + w, len - w,
                       "\"C_z_nonlinear\": {\"E\": %d, \"stages\": %d, \"lines_per_cta\": %d}}",

@@ -12,7 +12,7 @@ namespace nsk {
 struct PassCfg {
     Plan pl{};
     int ct = 16;
-    int kind = 0;   // 0: runtime-length kernel; 1: compile-time-length kernel (ct = warps per CTA)
+    int kind = 0;   // 0: runtime-length kernel; 1: compile-time-length kernel (for pass C, ct = warps per CTA)
 };
 
 // A pass-C kernel specialised for one grid size (fused_z.cu).
@@ -22,8 +22,9 @@ struct ZctKernel {
     int lines_per_block = 0;
     int threads = 0;
 };
-// Kernel for grid size N with wpb warps per CTA, if one was compiled.
-bool zct_lookup(int N, int wpb, ZctKernel *out);
+// Kernel for grid size N, E elements per thread and wpb warps per CTA, if one
+// was compiled (E in {16, 8} or {12, 6}; wpb in {1, 2, 4}).
+bool zct_lookup(int N, int E, int wpb, ZctKernel *out);
 
 // A strided-pass kernel specialised for one (N, E, CT) shape (fused_s*.cu).
 struct FzsKernel {

@@ -12,22 +12,24 @@
 
 namespace nsk {
 
-template <int N> struct ZShape {
+// Shape of pass C for grid size N with E elements per thread: T threads per
+// line, 32 / T lines per warp.  `ok` is false when E does not suit N/2 or a
+// line would not fit one warp.
+template <int N, int E_> struct ZShape {
     static constexpr int n = N / 2;
-    static constexpr int E = (n % 3 == 0) ? 12 : 16;
+    static constexpr int E = E_;
     static constexpr int T = n / E;
-    static constexpr int LPW = 32 / T;                      // lines per warp
-    static constexpr int LS = ct_line_stride(n, E, 6);      // elements per field line
-    static_assert(ct_valid(n, E), "no radix plan");
-    static_assert(T >= 1 && T <= 32 && 32 % T == 0, "a line must fit a warp");
+    static constexpr bool ok = n % E == 0 && ct_valid(n, E) && T >= 1 && T <= 32 && 32 % T == 0;
+    static constexpr int LPW = ok ? 32 / T : 1;                 // lines per warp
+    static constexpr int LS = ok ? ct_line_stride(n, E, 6) : 1; // elements per field line
 };
 
-template <int N, int WPB>
+template <int N, int E, int WPB>
 __global__ void __launch_bounds__(32 * WPB)
 k_fused_z_ct(float2 *buf, long fs, int Mz, long nlines, long brun, const float2 *__restrict__ tw) {
-    typedef ZShape<N> Z;
+    typedef ZShape<N, E> Z;
     buf += blockIdx.y * brun;   // run of the group
-    constexpr int n = Z::n, E = Z::E, T = Z::T, LPW = Z::LPW, LS = Z::LS;
+    constexpr int n = Z::n, T = Z::T, LPW = Z::LPW, LS = Z::LS;
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *sm = reinterpret_cast<float2 *>(smraw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -114,34 +116,49 @@ k_fused_z_ct(float2 *buf, long fs, int Mz, long nlines, long brun, const float2 
     }
 }
 
-template <int N, int WPB> static void zct_entry(ZctKernel *o) {
-    typedef ZShape<N> Z;
-    o->k = (const void *)k_fused_z_ct<N, WPB>;
-    o->smem = (size_t)WPB * Z::LPW * 6 * Z::LS * sizeof(float2);
-    o->lines_per_block = WPB * Z::LPW;
-    o->threads = 32 * WPB;
+template <int N, int E, int WPB> static bool zct_entry(ZctKernel *o) {
+    typedef ZShape<N, E> Z;
+    if constexpr (!Z::ok) {
+        return false;
+    } else {
+        o->k = (const void *)k_fused_z_ct<N, E, WPB>;
+        o->smem = (size_t)WPB * Z::LPW * 6 * Z::LS * sizeof(float2);
+        o->lines_per_block = WPB * Z::LPW;
+        o->threads = 32 * WPB;
+        return true;
+    }
 }
 
-template <int N> static bool zct_by_wpb(int wpb, ZctKernel *o) {
+template <int N, int E> static bool zct_by_wpb(int wpb, ZctKernel *o) {
     switch (wpb) {
-    case 2: zct_entry<N, 2>(o); return true;
-    case 4: zct_entry<N, 4>(o); return true;
+    case 1: return zct_entry<N, E, 1>(o);
+    case 2: return zct_entry<N, E, 2>(o);
+    case 4: return zct_entry<N, E, 4>(o);
     }
     return false;
 }
 
-bool zct_lookup(int N, int wpb, ZctKernel *o) {
+// E = 16 (12 for N divisible by 3) or half of it (8, 6).
+template <int N> static bool zct_by_e(int E, int wpb, ZctKernel *o) {
+    constexpr bool three = (N / 2) % 3 == 0;
+    constexpr int Ebig = three ? 12 : 16, Esmall = three ? 6 : 8;
+    if (E == Ebig) return zct_by_wpb<N, Ebig>(wpb, o);
+    if (E == Esmall) return zct_by_wpb<N, Esmall>(wpb, o);
+    return false;
+}
+
+bool zct_lookup(int N, int E, int wpb, ZctKernel *o) {
     switch (N) {
-    case 32: return zct_by_wpb<32>(wpb, o);
-    case 64: return zct_by_wpb<64>(wpb, o);
-    case 96: return zct_by_wpb<96>(wpb, o);
-    case 128: return zct_by_wpb<128>(wpb, o);
-    case 192: return zct_by_wpb<192>(wpb, o);
-    case 256: return zct_by_wpb<256>(wpb, o);
-    case 384: return zct_by_wpb<384>(wpb, o);
-    case 512: return zct_by_wpb<512>(wpb, o);
-    case 768: return zct_by_wpb<768>(wpb, o);
-    case 1024: return zct_by_wpb<1024>(wpb, o);
+    case 32: return zct_by_e<32>(E, wpb, o);
+    case 64: return zct_by_e<64>(E, wpb, o);
+    case 96: return zct_by_e<96>(E, wpb, o);
+    case 128: return zct_by_e<128>(E, wpb, o);
+    case 192: return zct_by_e<192>(E, wpb, o);
+    case 256: return zct_by_e<256>(E, wpb, o);
+    case 384: return zct_by_e<384>(E, wpb, o);
+    case 512: return zct_by_e<512>(E, wpb, o);
+    case 768: return zct_by_e<768>(E, wpb, o);
+    case 1024: return zct_by_e<1024>(E, wpb, o);
     }
     return false;
 }
