@@ -585,12 +585,17 @@ ns_status ns_fft_r2c(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
     if (!supported_n(n)) return NS_ERR_UNSUPPORTED_N;
     FftRes *f;
     if ((st = get_fft(c, n, &f)) != NS_OK) return st;
-    if (c->prec == NS_FP64)
+    if (c->prec == NS_FP64) {
         NS_CK(r2c_batch<double>((const double *)in, (double2 *)out, n, ncomp, *f,
                                 default_ct(sizeof(double2), n), c->stream));
-    else
-        NS_CK(r2c_batch<float>((const float *)in, (float2 *)out, n, ncomp, *f,
-                               default_ct(sizeof(float2), n), c->stream));
+    } else {
+        cudaError_t e = cudaSuccess;
+        if (std_r2c_fp32((const float *)in, (float2 *)out, n, ncomp, (const float2 *)f->tw, c->stream, &e))
+            NS_CK(e);
+        else
+            NS_CK(r2c_batch<float>((const float *)in, (float2 *)out, n, ncomp, *f,
+                                   default_ct(sizeof(float2), n), c->stream));
+    }
     return NS_OK;
 }
 
@@ -608,10 +613,16 @@ ns_status ns_fft_c2r(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
             NS_CK(c2r_batch<double>((const double2 *)in + k * M, (double2 *)f->scratch,
                                     (double *)out + k * V, n, 1, *f,
                                     default_ct(sizeof(double2), n), c->stream));
-        else
-            NS_CK(c2r_batch<float>((const float2 *)in + k * M, (float2 *)f->scratch,
-                                   (float *)out + k * V, n, 1, *f, default_ct(sizeof(float2), n),
-                                   c->stream));
+        else {
+            cudaError_t e = cudaSuccess;
+            if (std_c2r_fp32((const float2 *)in + k * M, (float2 *)f->scratch, (float *)out + k * V, n,
+                             (const float2 *)f->tw, c->stream, &e))
+                NS_CK(e);
+            else
+                NS_CK(c2r_batch<float>((const float2 *)in + k * M, (float2 *)f->scratch,
+                                       (float *)out + k * V, n, 1, *f, default_ct(sizeof(float2), n),
+                                       c->stream));
+        }
     }
     return NS_OK;
 }

@@ -469,10 +469,10 @@ static void pass_descs(const FusedRun &f, const float2 *src, FzPass &A, FzPass &
     const int N = f.n, K = f.K, Mx = f.Mx, Mz = f.Mz;
     const long MxMz = (long)Mx * Mz, NMz = (long)N * Mz;
     const long S3 = 3 * f.M;
-    A = FzPass{src, f.abuf, MxMz, f.M, MxMz, (long)Mx * NMz, Mz, NMz, 6, Mz, K, Mx, S3, f.sA};
-    B = FzPass{f.abuf, f.bbuf, NMz, (long)Mx * NMz, NMz, (long)N * NMz, NMz, Mz, 6, Mz, K, Mx, f.sA, f.sB};
-    D = FzPass{f.bbuf, f.abuf, NMz, (long)N * NMz, NMz, (long)N * MxMz, Mz, MxMz, 3, Mz, K, Mx, f.sB, f.sA};
-    Ep = FzPass{f.abuf, f.nl, MxMz, (long)N * MxMz, MxMz, f.M, MxMz, Mz, 3, Mz, K, Mx, f.sA, S3};
+    A = FzPass{src, f.abuf, MxMz, f.M, MxMz, (long)Mx * NMz, Mz, NMz, 6, Mz, K, Mx, S3, f.sA, Mz};
+    B = FzPass{f.abuf, f.bbuf, NMz, (long)Mx * NMz, NMz, (long)N * NMz, NMz, Mz, 6, Mz, K, Mx, f.sA, f.sB, Mz};
+    D = FzPass{f.bbuf, f.abuf, NMz, (long)N * NMz, NMz, (long)N * MxMz, Mz, MxMz, 3, Mz, K, Mx, f.sB, f.sA, Mz};
+    Ep = FzPass{f.abuf, f.nl, MxMz, (long)N * MxMz, MxMz, f.M, MxMz, Mz, 3, Mz, K, Mx, f.sA, S3, Mz};
 }
 
 static cudaError_t run_pass_ct(FusedRun &f, int which, const PassCfg &cfg, const FzPass &ps,

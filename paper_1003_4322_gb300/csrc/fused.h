@@ -35,6 +35,18 @@ struct FzsKernel {
 bool fzs_lookup_A(int N, int E, int CT, FzsKernel *out);    // x inverse + curl
 bool fzs_lookup_B(int N, int E, int CT, FzsKernel *out);    // y inverse
 bool fzs_lookup_DE(int N, int E, int CT, FzsKernel *out);   // y / x forward
+bool fzs_lookup_PF(int N, int E, int CT, FzsKernel *out);   // every row, forward
+bool fzs_lookup_PI(int N, int E, int CT, FzsKernel *out);   // every row, inverse
+
+// Standalone-transform z-pass kernel (fft_std_ct.cu).
+bool zstd_lookup(int N, bool r2c, int E, int wpb, ZctKernel *out);
+// FP32 standalone transforms on compile-time-length kernels.  Return false
+// (and launch nothing) when N has no compiled kernels; otherwise *err holds
+// the launch status.  c2r handles one field through the scratch tmp.
+bool std_r2c_fp32(const float *in, float2 *out, int N, int ncomp, const float2 *tw, cudaStream_t s,
+                  cudaError_t *err);
+bool std_c2r_fp32(const float2 *in, float2 *tmp, float *out, int N, const float2 *tw, cudaStream_t s,
+                  cudaError_t *err);
 
 // Per-run parameters of the update kernel (device array, one per run).
 struct FzRunParams {

@@ -25,6 +25,7 @@ struct FzPass {
     int nfields;         // output fields handled by the grid
     int Mz, K, Mx;
     long irun, orun;     // input / output strides between the runs of a group (grid y)
+    long ibs;            // input outer stride of a column (input element: ou * ibs + iz)
 };
 
 // One column of a strided pass: grid x is fields x tiles (field fastest),
@@ -53,9 +54,9 @@ template <bool IN_C, bool OUT_C, bool CURL> struct FzColumn {
         const int r = IN_C ? fz_compact(e, n, ps.K, ps.Mx) : e;
         if (!valid || r < 0) return make_float2(0.f, 0.f);
         if constexpr (!CURL) {
-            return in[f * ps.ifs + r * ps.irs + col];
+            return in[f * ps.ifs + r * ps.irs + ou * ps.ibs + iz];
         } else {
-            const float2 *b = in + r * ps.irs + col;
+            const float2 *b = in + r * ps.irs + ou * ps.ibs + iz;
             if (f < 3) return b[f * ps.ifs];
             const float kx = (float)fz_full_signed(e, n);
             const float ky = (float)fz_compact_signed((int)ou, ps.Mx, ps.K);
