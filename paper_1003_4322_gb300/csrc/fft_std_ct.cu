@@ -3,6 +3,9 @@
 // reuse the column machinery of the fused form with every row present (the y
 // pass flattens (x, kz) into columns, so no tile is ragged), and the z pass is
 // a warp-level r2c / c2r with the line in shared memory.
+#include <map>
+#include <mutex>
+
 #include "fft_ct.cuh"
 #include "fused.h"
 #include "fused_access.cuh"
@@ -162,56 +165,127 @@ static cudaError_t launch_col(const FzsKernel &k, const FzPass &ps, int ct, cons
     return cudaLaunchKernel(k.k, dim3((unsigned)blocks), dim3(k.threads), args, k.smem, s);
 }
 
-// Shapes of the standalone transform for grid size N: the strided passes'
-// (E, columns per CTA) and the z pass's (E, warps per CTA).
-static bool std_shapes(int N, bool fwd, FzsKernel *kx, FzsKernel *ky, int *ct, ZctKernel *kz) {
-    const bool three = N % 3 == 0;
-    const int Es = N == 1024 ? 32 : (three ? 12 : 16);
-    const int Ez = three ? 12 : 16;
-    *ct = 16;
-    const bool okx = fwd ? fzs_lookup_PF(N, Es, 16, kx) : fzs_lookup_PI(N, Es, 16, kx);
-    const bool oky = fwd ? fzs_lookup_PF(N, Es, 16, ky) : fzs_lookup_PI(N, Es, 16, ky);
-    return okx && oky && zstd_lookup(N, fwd, Ez, 2, kz);
+// Tuned shapes of the standalone transform for one (N, direction): the x
+// and y passes' (E, columns per CTA) and the z pass's (E, warps per CTA).
+struct StdShapes {
+    int ex = 0, cx = 0, ey = 0, cy = 0, ez = 0, wz = 0;
+};
+
+static bool std_lookup_col(bool fwd, int N, int E, int CT, FzsKernel *k) {
+    return fwd ? fzs_lookup_PF(N, E, CT, k) : fzs_lookup_PI(N, E, CT, k);
+}
+
+template <class F> static float std_time(F launch, cudaStream_t s) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1.f;
+    }
+    float ms = -1.f;
+    if (launch() == cudaSuccess && cudaEventRecord(a, s) == cudaSuccess) {
+        bool ok = true;
+        for (int i = 0; i < 3 && ok; i++) ok = launch() == cudaSuccess;
+        if (ok && cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+            ms /= 3;
+        else
+            ms = -1.f;
+    }
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
 }
 
 // Column descriptors of the y and x passes over ncomp half-layout fields
 // [c][x][y][kz] (kz < Nh): y pass columns (x, kz), x pass columns (y, kz).
-static void std_descs(const float2 *in, float2 *out, int N, int ncomp, FzPass &py, FzPass &px,
-                      bool y_first_in) {
+static void std_descs(const float2 *in, float2 *out, int N, int ncomp, FzPass &py, FzPass &px) {
     const long Nh = N / 2 + 1, plane = (long)N * Nh, M = (long)N * plane;
-    (void)y_first_in;
     py = FzPass{in, out, plane, M, Nh, M, Nh, plane, ncomp, (int)Nh, 0, 0, 0, 0, plane};
     px = FzPass{in, out, plane, M, plane, M, plane, Nh, ncomp, (int)Nh, 0, 0, 0, 0, Nh};
 }
 
+// Choose the shapes on the first call for (N, direction), timing every
+// compiled candidate on the call's own buffers (the passes run in place on
+// `work`, whose contents the real transform then overwrites); kept for the
+// life of the process.
+static bool std_shapes(int N, bool fwd, const void *zin, void *zout, float2 *work, int ncomp,
+                       const float2 *tw, cudaStream_t s, StdShapes *out) {
+    static std::mutex mu;
+    static std::map<std::pair<int, bool>, StdShapes> cache;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find({N, fwd});
+        if (it != cache.end()) {
+            *out = it->second;
+            return true;
+        }
+    }
+    FzsKernel k;
+    ZctKernel z;
+    const int Es[] = {8, 12, 16, 32};
+    StdShapes best;
+    float bx = -1.f, by = -1.f, bz = -1.f;
+    FzPass py, px;
+    std_descs(work, work, N, ncomp, py, px);
+    for (int E : Es)
+        for (int ct = 8; ct <= 16; ct *= 2) {
+            if (!std_lookup_col(fwd, N, E, ct, &k)) continue;
+            const float ty = std_time([&]() { return launch_col(k, py, ct, tw, s); }, s);
+            if (ty > 0.f && (by < 0.f || ty < by)) { by = ty; best.ey = E; best.cy = ct; }
+            const float tx = std_time([&]() { return launch_col(k, px, ct, tw, s); }, s);
+            if (tx > 0.f && (bx < 0.f || tx < bx)) { bx = tx; best.ex = E; best.cx = ct; }
+        }
+    const int Ezs[] = {16, 12, 8, 6};
+    const long nlines = (long)(fwd ? ncomp : 1) * N * N;
+    for (int E : Ezs)
+        for (int w = 2; w <= 4; w *= 2) {
+            if (!zstd_lookup(N, fwd, E, w, &z)) continue;
+            const float t = std_time([&]() { return launch_zstd(z, zin, zout, nlines, tw, s); }, s);
+            if (t > 0.f && (bz < 0.f || t < bz)) { bz = t; best.ez = E; best.wz = w; }
+        }
+    if (bx < 0.f || by < 0.f || bz < 0.f) return false;
+    std::lock_guard<std::mutex> g(mu);
+    cache[{N, fwd}] = best;
+    *out = best;
+    return true;
+}
+
 bool std_r2c_fp32(const float *in, float2 *out, int N, int ncomp, const float2 *tw, cudaStream_t s,
                   cudaError_t *err) {
+    StdShapes sh;
+    if (!std_shapes(N, true, in, out, out, ncomp, tw, s, &sh)) return false;
     FzsKernel kx, ky;
     ZctKernel kz;
-    int ct;
-    if (!std_shapes(N, true, &kx, &ky, &ct, &kz)) return false;
+    if (!std_lookup_col(true, N, sh.ex, sh.cx, &kx) || !std_lookup_col(true, N, sh.ey, sh.cy, &ky) ||
+        !zstd_lookup(N, true, sh.ez, sh.wz, &kz))
+        return false;
     *err = launch_zstd(kz, in, out, (long)ncomp * N * N, tw, s);
     if (*err != cudaSuccess) return true;
     FzPass py, px;
-    std_descs(out, out, N, ncomp, py, px, false);
-    *err = launch_col(ky, py, ct, tw, s);
+    std_descs(out, out, N, ncomp, py, px);
+    *err = launch_col(ky, py, sh.cy, tw, s);
     if (*err != cudaSuccess) return true;
-    *err = launch_col(kx, px, ct, tw, s);
+    *err = launch_col(kx, px, sh.cx, tw, s);
     return true;
 }
 
 bool std_c2r_fp32(const float2 *in, float2 *tmp, float *out, int N, const float2 *tw, cudaStream_t s,
                   cudaError_t *err) {
+    StdShapes sh;
+    if (!std_shapes(N, false, tmp, out, tmp, 1, tw, s, &sh)) return false;
     FzsKernel kx, ky;
     ZctKernel kz;
-    int ct;
-    if (!std_shapes(N, false, &kx, &ky, &ct, &kz)) return false;
+    if (!std_lookup_col(false, N, sh.ex, sh.cx, &kx) || !std_lookup_col(false, N, sh.ey, sh.cy, &ky) ||
+        !zstd_lookup(N, false, sh.ez, sh.wz, &kz))
+        return false;
     FzPass py, px;
-    std_descs(in, tmp, N, 1, py, px, true);
-    *err = launch_col(kx, px, ct, tw, s);
+    std_descs(in, tmp, N, 1, py, px);
+    *err = launch_col(kx, px, sh.cx, tw, s);
     if (*err != cudaSuccess) return true;
-    std_descs(tmp, tmp, N, 1, py, px, false);
-    *err = launch_col(ky, py, ct, tw, s);
+    std_descs(tmp, tmp, N, 1, py, px);
+    *err = launch_col(ky, py, sh.cy, tw, s);
     if (*err != cudaSuccess) return true;
     *err = launch_zstd(kz, tmp, out, (long)N * N, tw, s);
     return true;
