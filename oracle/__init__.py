@@ -77,6 +77,7 @@ def lib():
         L.or_step.argtypes = [ctypes.POINTER(_Params), P, ctypes.c_int]
         L.or_nbins.argtypes = [ctypes.c_int]
         L.or_diagnostics.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int]
+        L.or_helicity.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -170,6 +171,17 @@ def diagnostics(a: np.ndarray):
     _check(lib().or_diagnostics(n, _ptr(a), ctypes.byref(e), ctypes.byref(om),
                                 _ptr(spec), nb), "diagnostics")
     return e.value, om.value, spec
+
+
+def helicity(a: np.ndarray):
+    """(H, H(K)): helicity 1/2 <u . w> and its shell spectrum."""
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    n = a.shape[1]
+    nb = nbins(n)
+    spec = np.empty(nb, dtype=np.float64)
+    h = ctypes.c_double()
+    _check(lib().or_helicity(n, _ptr(a), ctypes.byref(h), _ptr(spec), nb), "helicity")
+    return h.value, spec
 
 
 def rel_l2(test: np.ndarray, ref: np.ndarray) -> float:

@@ -37,7 +37,9 @@
  *   diagnostics E = 1/2 sum |a|^2, Omega = 1/2 sum |k|^2 |a|^2 over the full
  *               spectrum (half-layout weight 2 for 0 < kz < N/2, else 1), and
  *               the shell spectrum binned by round-half-up(|k|) (the
- *               reductions for global quantities and spectra of Sec. 3).
+ *               reductions for global quantities and spectra of Sec. 3);
+ *               helicity H = 1/2 <u . w> = 1/2 sum Re(a . conj(i k x a)) and
+ *               its shell spectrum, with the same weights and bins.
  *
  * The paper leaves the dealiasing rule, the integrator, the form of the
  * nonlinear term and the shell binning unstated; the choices above are the
@@ -447,5 +449,37 @@ int or_diagnostics(int n, const cplx *a, double *energy, double *enstrophy,
     }
     if (energy) *energy = e;
     if (enstrophy) *enstrophy = om;
+    return OR_OK;
+}
+
+/* Helicity H = 1/2 sum Re(a . conj(w)), w = i k x a, over the full spectrum,
+ * and its shell spectrum (same weights and shells as or_diagnostics). */
+int or_helicity(int n, const cplx *a, double *helicity, double *spec, int nbins)
+{
+    if (n < 2 || !a) return OR_ERR_ARG;
+    const long nh = n / 2 + 1, M = (long)n * n * nh;
+    cplx *w = malloc(sizeof(cplx) * 3 * (size_t)M);
+    if (!w) return OR_ERR_OOM;
+    or_curl(n, a, w);
+    double h = 0.0;
+    if (spec) memset(spec, 0, sizeof(double) * (size_t)nbins);
+    for (long ix = 0; ix < n; ix++) {
+        double kx = wavenumber((int)ix, n);
+        for (long iy = 0; iy < n; iy++) {
+            double ky = wavenumber((int)iy, n);
+            for (long kz = 0; kz < nh; kz++) {
+                long m = (ix * n + iy) * nh + kz;
+                double wt = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
+                double s = 0.0;
+                for (int c = 0; c < 3; c++) s += creal(a[c * M + m] * conj(w[c * M + m]));
+                double dh = 0.5 * wt * s;
+                h += dh;
+                long K = (long)floor(sqrt(kx * kx + ky * ky + (double)kz * kz) + 0.5);
+                if (spec && K < nbins) spec[K] += dh;
+            }
+        }
+    }
+    free(w);
+    if (helicity) *helicity = h;
     return OR_OK;
 }

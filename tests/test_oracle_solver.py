@@ -231,3 +231,31 @@ def test_energy_half_helper_agrees_with_oracle():
     assert abs(energy_half(a) - oracle.diagnostics(a)[0]) < 1e-14
     assert len(kept_modes(32)) == 21 ** 3
     assert np.allclose(half_to_full(a)[:, :, :, :17], a)
+
+
+# ---------------------------------------------------------------- helicity
+
+def test_helicity_of_beltrami_and_taylor_green():
+    # ABC with k = 1 is a Beltrami field, w = u: H = 1/2 <u . u> = E = 1.5,
+    # all in shell 1; Taylor-Green carries no helicity.
+    H, spec = oracle.helicity(inputs.abc_state(16))
+    assert abs(H - 1.5) < 1e-14 and abs(spec[1] - 1.5) < 1e-14
+    H, _ = oracle.helicity(inputs.taylor_green_state(16))
+    assert abs(H) < 1e-15
+    # ABC at k = 2: w = 2u, H = 2E
+    H, spec = oracle.helicity(inputs.abc_state(16, k=2))
+    assert abs(H - 3.0) < 1e-14 and abs(spec[2] - 3.0) < 1e-14
+
+
+def test_helicity_matches_grid_average():
+    n = 16
+    a = inputs.turbulence_state(n, 12, rms=0.9)
+    H, spec = oracle.helicity(a)
+    u = np.fft.irfftn(a, s=(n, n, n), axes=(1, 2, 3)) * n ** 3
+    w = np.fft.irfftn(oracle.curl(a), s=(n, n, n), axes=(1, 2, 3)) * n ** 3
+    assert abs(0.5 * np.mean(np.sum(u * w, axis=0)) - H) < 1e-13
+    assert abs(spec.sum() - H) < 1e-14
+    # mirror image (u(x) -> -u(-x) is a reflection: H changes sign)
+    b = np.conj(a) * -1.0   # coefficients of -u(-x)
+    Hb, _ = oracle.helicity(b)
+    assert abs(Hb + H) < 1e-14
