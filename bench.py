@@ -402,6 +402,22 @@ def cpu_baseline(w, mem, budget_s=30.0):
                       f"workload on {cores} host threads ({dt:.1f} s)"}
 
 
+def max_over_ranks(ms, dist, device=None):
+    """Largest elapsed time over all ranks (the job's time); a plain float
+    when there is no process group."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed over the job time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def ours(args, w):
     import numpy as np
     import torch
@@ -424,12 +440,8 @@ def ours(args, w):
     census_steps = min(args.steps, 3)
 
     main = time_form(w, w["prec"], mem, args.steps, warmup, census_steps, dist)
-    ms = main["ms"]
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nr * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(main["ms"], dist, "cuda")
+    value = job_rate(nr * args.steps, world, ms)
     points = sum(r["n"] ** 3 for r in mem[0])
     clk = main["clocks"] or {}
     sizes = [r["n"] for r in mem[0]]

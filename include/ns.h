@@ -160,6 +160,17 @@ ns_status ns_fft_c2r_noalloc(int n, int ncomp, const void *in, void *out, void *
 ns_status ns_energy_spectrum(ns_ctx *ctx, int run, double *spec, int nbins,
                              double *energy, double *enstrophy);
 
+/* Helicity H = 1/2 <u . w> = 1/2 sum Re(a . conj(i k x a)) over the full
+ * spectrum and its shell spectrum H(K) (same shells and FP64 accumulation as
+ * ns_energy_spectrum) of one run's current state.  The paper does not define
+ * it: it is one more global quantity and spectrum of the kind Sec. 3 reduces,
+ * the standard invariant of ideal 3D flow; a Beltrami (ABC) field with
+ * w = k u has H = k E.  spec
+ * receives min(nbins, ns_nbins(N)) shells; helicity may be NULL.  Host
+ * outputs; synchronises the stream.  Errors: NS_ERR_ARG, NS_ERR_CUDA,
+ * NS_ERR_NONFINITE (H is not finite). */
+ns_status ns_helicity(ns_ctx *ctx, int run, double *spec, int nbins, double *helicity);
+
 /* Number of shells of an N^3 grid: ceil(sqrt(3) N / 2) + 1. */
 int ns_nbins(int n);
 

@@ -23,7 +23,7 @@ NS_FP64, NS_FP32 = 0, 1
 SYMBOLS = ("ns_init", "ns_set_state", "ns_get_state", "ns_step", "ns_fft_r2c", "ns_fft_c2r",
            "ns_energy_spectrum", "ns_nbins", "ns_series", "ns_series_capacity",
            "ns_kernel_census", "ns_sync", "ns_last_error", "ns_status_str", "ns_destroy",
-           "ns_fft_c2r_noalloc", "ns_describe_run")
+           "ns_fft_c2r_noalloc", "ns_describe_run", "ns_helicity")
 
 
 class NsError(RuntimeError):
@@ -67,6 +67,7 @@ def load(path: str = LIB_PATH):
         "ns_fft_c2r_noalloc": ([I, I, P, P, P], I),
         "ns_energy_spectrum": ([P, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D)], I),
         "ns_nbins": ([I], I),
+        "ns_helicity": ([P, I, P, I, ctypes.POINTER(D)], I),
         "ns_series": ([P, I, I, P, P, ctypes.POINTER(I)], I),
         "ns_series_capacity": ([], I),
         "ns_kernel_census": ([P, I, ctypes.POINTER(ns_kernel_time), I, ctypes.POINTER(I)], I),
@@ -185,6 +186,15 @@ def ns_energy_spectrum(ctx, run: int, n: int):
     _check(load().ns_energy_spectrum(ctx, run, _ptr(spec), nb, ctypes.byref(e), ctypes.byref(om)),
            "ns_energy_spectrum", ctx)
     return e.value, om.value, spec
+
+
+def ns_helicity(ctx, run: int, n: int):
+    """Returns (H, helicity spectrum as a numpy array of ns_nbins(n) shells)."""
+    nb = ns_nbins(n)
+    spec = np.zeros(nb, dtype=np.float64)
+    h = ctypes.c_double()
+    _check(load().ns_helicity(ctx, run, _ptr(spec), nb, ctypes.byref(h)), "ns_helicity", ctx)
+    return h.value, spec
 
 
 def ns_series(ctx, run: int, count: int):

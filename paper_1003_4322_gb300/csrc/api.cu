@@ -657,6 +657,30 @@ ns_status ns_energy_spectrum(ns_ctx *c, int run, double *spec, int nbins, double
     return check_flags(c);
 }
 
+ns_status ns_helicity(ns_ctx *c, int run, double *spec, int nbins, double *helicity) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (run < 0 || run >= (int)c->runs.size() || nbins < 0 || (nbins > 0 && !spec))
+        return NS_ERR_ARG;
+    Run &r = c->runs[run];
+    const int nb = ns_nbins(r.n);
+    if (use_fused(c))
+        NS_CK(fused_helicity(c->groups[r.group], r.gidx, nb, c->spec, c->ens, c->stream));
+    else if (c->prec == NS_FP64)
+        NS_CK(plain_helicity<double>((const double2 *)r.un, r.n, nb, c->spec, c->ens, c->stream));
+    else
+        NS_CK(plain_helicity<float>((const float2 *)r.un, r.n, nb, c->spec, c->ens, c->stream));
+    std::vector<double> hs(nb);
+    NS_CK(cudaMemcpyAsync(hs.data(), c->spec, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    NS_CK(cudaStreamSynchronize(c->stream));
+    double h = 0.0;
+    for (int k = 0; k < nb; k++) h += hs[k];
+    for (int k = 0; k < nbins && k < nb; k++) spec[k] = hs[k];
+    if (helicity) *helicity = h;
+    if (!isfinite(h)) return NS_ERR_NONFINITE;
+    return check_flags(c);
+}
+
 ns_status ns_series(ns_ctx *c, int run, int count, double *energy, double *enstrophy,
                     int *written) {
     ns_status st = check_ctx(c);

@@ -327,6 +327,19 @@ struct CompactAcc {
     }
 };
 
+struct CompactHelAcc {
+    const float2 *a;
+    int K, Mx, Mz;
+    long M;
+    __device__ double operator()(int kx, int ky, int kz) const {
+        if (kx > K || kx < -K || ky > K || ky < -K || kz >= Mz) return 0.0;
+        const int ikx = kx >= 0 ? kx : kx + Mx, iky = ky >= 0 ? ky : ky + Mx;
+        const long m = ((long)ikx * Mx + iky) * Mz + kz;
+        return helicity_density(kx, ky, kz, a[m].x, a[m].y, a[M + m].x, a[M + m].y, a[2 * M + m].x,
+                                a[2 * M + m].y);
+    }
+};
+
 // ---------------------------------------------------------------- host side
 
 static unsigned grid_of(long work, int threads, long cap) {
@@ -876,6 +889,12 @@ cudaError_t fused_get_state(FusedRun &f, int run, double2 *dst, int on_device, v
 cudaError_t fused_spectrum(FusedRun &f, int run, int nbins, double *spec, double *ens, cudaStream_t s) {
     CompactAcc acc{f.a + (long)run * 3 * f.M, f.K, f.Mx, f.Mz, f.M};
     k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, f.n, nbins, spec, ens);
+    return cudaGetLastError();
+}
+
+cudaError_t fused_helicity(FusedRun &f, int run, int nbins, double *spec, double *aux, cudaStream_t s) {
+    CompactHelAcc acc{f.a + (long)run * 3 * f.M, f.K, f.Mx, f.Mz, f.M};
+    k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, f.n, nbins, spec, aux);
     return cudaGetLastError();
 }
 

@@ -98,5 +98,6 @@ cudaError_t fused_step(FusedRun &f, int *flags, cudaStream_t s, Tracer *tr);
 // JSON text describing the chosen per-pass configuration; returns its length.
 int fused_describe(const FusedRun &f, char *out, int len);
 cudaError_t fused_spectrum(FusedRun &f, int run, int nbins, double *spec, double *ens, cudaStream_t s);
+cudaError_t fused_helicity(FusedRun &f, int run, int nbins, double *spec, double *aux, cudaStream_t s);
 
 }  // namespace nsk

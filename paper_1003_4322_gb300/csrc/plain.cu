@@ -192,6 +192,17 @@ template <typename T> struct HalfAcc {
     }
 };
 
+template <typename T> struct HalfHelAcc {
+    const typename Cx<T>::type *a;
+    int n;
+    long M;
+    __device__ double operator()(int kx, int ky, int kz) const {
+        const long m = ((long)((kx + n) % n) * n + (ky + n) % n) * (n / 2 + 1) + kz;
+        return helicity_density(kx, ky, kz, a[m].x, a[m].y, a[M + m].x, a[M + m].y, a[2 * M + m].x,
+                                a[2 * M + m].y);
+    }
+};
+
 // ---------------------------------------------------------------- launchers
 
 static unsigned grid_for(long work, int threads) {
@@ -247,6 +258,14 @@ cudaError_t plain_spectrum(const typename Cx<T>::type *a, int n, int nbins, doub
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t plain_helicity(const typename Cx<T>::type *a, int n, int nbins, double *spec, double *aux,
+                           cudaStream_t s) {
+    HalfHelAcc<T> acc{a, n, (long)n * n * (n / 2 + 1)};
+    k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, n, nbins, spec, aux);
+    return cudaGetLastError();
+}
+
 cudaError_t energy_final(const double *part, int nparts, double *series, int cap,
                          unsigned long long *counter, int *flags, cudaStream_t s) {
     k_energy_final<<<1, 256, 0, s>>>(part, nparts, series, cap, counter, flags);
@@ -260,6 +279,8 @@ cudaError_t energy_final(const double *part, int nparts, double *series, int cap
                                          const T *, int, const UpdateArgs &, cudaStream_t);       \
     template cudaError_t plain_energy_partials<T>(const Cx<T>::type *, int, double *, cudaStream_t); \
     template cudaError_t plain_spectrum<T>(const Cx<T>::type *, int, int, double *, double *,     \
+                                           cudaStream_t);                                         \
+    template cudaError_t plain_helicity<T>(const Cx<T>::type *, int, int, double *, double *,     \
                                            cudaStream_t);
 NSK_INST(float)
 NSK_INST(double)

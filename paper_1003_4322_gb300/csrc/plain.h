@@ -25,6 +25,9 @@ cudaError_t plain_energy_partials(const typename Cx<T>::type *a, int n, double *
 template <typename T>
 cudaError_t plain_spectrum(const typename Cx<T>::type *a, int n, int nbins, double *spec, double *ens,
                            cudaStream_t s);
+template <typename T>
+cudaError_t plain_helicity(const typename Cx<T>::type *a, int n, int nbins, double *spec, double *aux,
+                           cudaStream_t s);
 cudaError_t energy_final(const double *part, int nparts, double *series, int cap,
                          unsigned long long *counter, int *flags, cudaStream_t s);
 

@@ -70,4 +70,16 @@ k_shell_spectrum(Acc acc, int n, int nbins, double *spec, double *ens) {
     }
 }
 
+// Re(a . conj(w)) with w = i k x a, for the helicity 1/2 <u . w>.
+__device__ __forceinline__ double helicity_density(double kx, double ky, double kz, double axr,
+                                                   double axi, double ayr, double ayi, double azr,
+                                                   double azi) {
+    // k x a
+    const double cxr = ky * azr - kz * ayr, cxi = ky * azi - kz * ayi;
+    const double cyr = kz * axr - kx * azr, cyi = kz * axi - kx * azi;
+    const double czr = kx * ayr - ky * axr, czi = kx * ayi - ky * axi;
+    // w = i (k x a) = (-ci, cr); Re(a conj w) = ar * wr + ai * wi = -ar ci + ai cr
+    return -axr * cxi + axi * cxr - ayr * cyi + ayi * cyr - azr * czi + azi * czr;
+}
+
 }  // namespace nsk

@@ -59,6 +59,9 @@ class Solver:
     def energy_spectrum(self, run: int = 0):
         return nat.ns_energy_spectrum(self.ctx, run, self.n(run))
 
+    def helicity(self, run: int = 0):
+        return nat.ns_helicity(self.ctx, run, self.n(run))
+
     def series(self, run: int = 0, count: int = 4096):
         return nat.ns_series(self.ctx, run, count)
 

@@ -165,3 +165,74 @@ def test_taylor_green_256_against_oracle_on_the_64_sublattice(ns):
     ur = np.fft.irfftn(ref, s=(n, n, n), axes=(1, 2, 3))[:, ::4, ::4, ::4]
     assert np.linalg.norm(ug - ur) / np.linalg.norm(ur) < TOL["fp64"]
     assert rel_l2(got, ref) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_non_finite_state_is_reported(ns, prec):
+    from paper_1003_4322_gb300 import _native as nat
+    n = 16
+    a = inputs.turbulence_state(n, seed=1)
+    a[0, 1, 1, 1] = np.nan
+    with _solver(ns, prec, n=n, nu=0.01, dt=1e-3) as s:
+        s.set_state(a)
+        s.step(1)
+        with pytest.raises(nat.NsError) as ei:
+            s.sync()
+        assert ei.value.status == nat.NS_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_resume_from_saved_state_is_bitwise_equal(ns, prec):
+    run = dict(n=48, nu=0.01, dt=1e-3, force_amp=0.5, force_k=3)
+    a0 = inputs.turbulence_state(48, seed=6)
+    with _solver(ns, prec, **run) as s:
+        s.set_state(a0)
+        s.step(4)
+        straight = s.get_state()
+    with _solver(ns, prec, **run) as s:
+        s.set_state(a0)
+        s.step(2)
+        saved = s.get_state()
+    with _solver(ns, prec, **run) as s:
+        s.set_state(saved)
+        s.step(2)
+        resumed = s.get_state()
+    assert np.array_equal(resumed, straight)
+
+
+def test_allocation_failure_is_reported_and_cleaned_up(ns):
+    """Forty 768^3 plain-FP64 runs need far more than the GPU's memory: ns_init
+    must return NS_ERR_OOM (no fault), free what it took, and later contexts
+    must work."""
+    from paper_1003_4322_gb300 import _native as nat
+    import torch
+    free0, _ = torch.cuda.mem_get_info()
+    with pytest.raises(nat.NsError) as ei:
+        nat.ns_init([dict(n=768, nu=1e-3, dt=1e-3)] * 40, nat.NS_FP64)
+    assert ei.value.status == nat.NS_ERR_OOM
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 > free0 - (1 << 30)
+    with _solver(ns, "fp64", n=16, nu=0.01, dt=1e-3) as s:
+        s.set_state(inputs.abc_state(16))
+        s.step(1)
+        s.sync()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_helicity_matches_oracle(ns, prec):
+    n = 48
+    a0 = inputs.turbulence_state(n, seed=13)
+    with _solver(ns, prec, n=n, nu=0.01, dt=1e-3, force_amp=0.5, force_k=3) as s:
+        s.set_state(a0)
+        s.step(2)
+        H, spec = s.helicity()
+        st = s.get_state()
+    rH, rspec = oracle.helicity(st)
+    scale = np.abs(rspec).sum()
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    assert abs(H - rH) < tol * scale
+    assert np.abs(spec - rspec).max() < tol * scale
+    with _solver(ns, prec, n=32, nu=0.0, dt=1e-3) as s:
+        s.set_state(inputs.abc_state(32))
+        H, spec = s.helicity()
+    assert abs(H - 1.5) < (1e-14 if prec == "fp64" else 1e-6)
