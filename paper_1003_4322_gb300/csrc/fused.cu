@@ -175,6 +175,42 @@ __device__ __forceinline__ void fz_forcing(int kx, int ky, int kz, int kf, float
     }
 }
 
+// Compensated FP32 accumulator (value hi + lo) for the energy partials of
+// the update.  A square of an FP32 value splits exactly into p + e with
+// e = fma(x, x, -p), each addition keeps its rounding error (Knuth's TwoSum)
+// and the pair is renormalised once per mode (Dekker's Fast2Sum), so a
+// thread's few hundred terms sum to within a few units of 2^-48 relative --
+// FP64-quality accumulation without FP64 instructions, which this GPU issues
+// at 1/64 of the FP32 rate.  Block and final sums are FP64.
+// The _rn intrinsics keep each rounding where it is written (no contraction
+// into FMA), which the error terms rely on.
+struct DfAcc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float b) {
+        const float s = __fadd_rn(hi, b), bb = __fsub_rn(s, hi);
+        lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+        hi = s;
+    }
+    __device__ __forceinline__ void add_sq(float x) {
+        const float p = __fmul_rn(x, x);
+        add(p);
+        lo += fmaf(x, x, -p);
+    }
+    __device__ __forceinline__ void renorm() {
+        const float s = __fadd_rn(hi, lo);
+        lo = __fsub_rn(lo, __fsub_rn(s, hi));
+        hi = s;
+    }
+    // += c * v for an exactly representable weight c (c * v.hi split exactly)
+    __device__ __forceinline__ void add_scaled(const DfAcc &v, float c) {
+        const float q = __fmul_rn(c, v.hi);
+        add(q);
+        lo += fmaf(c, v.hi, -q) + c * v.lo;
+        renorm();
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 __global__ void __launch_bounds__(256)
 k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__restrict__ nl,
                const float *__restrict__ etab, const FzRunParams *__restrict__ rp, FzUpdate u,
@@ -188,11 +224,13 @@ k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__
     etab += (long)run * u.nk2;
     const FzRunParams q = rp[run];
     const float inv = (float)(1.0 / ((double)u.n * u.n * u.n));
-    double e_acc = 0.0, o_acc = 0.0;
+    DfAcc e_acc, o_acc;
+    const unsigned Mz = (unsigned)u.Mz, Mx = (unsigned)u.Mx;   // M < 2^31 for every supported N
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        const int kz = (int)(m % u.Mz);
-        const int iky = (int)((m / u.Mz) % u.Mx);
-        const int ikx = (int)(m / ((long)u.Mz * u.Mx));
+        const unsigned row = (unsigned)m / Mz;
+        const int kz = (int)((unsigned)m - row * Mz);
+        const int iky = (int)(row % Mx);
+        const int ikx = (int)(row / Mx);
         const int kx = fz_compact_signed(ikx, u.Mx, u.K), ky = fz_compact_signed(iky, u.Mx, u.K);
         const int k2 = kx * kx + ky * ky + kz * kz;
         bool keep = k2 > 0;
@@ -223,19 +261,26 @@ k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__
         dst[M + m] = o1;
         dst[2 * M + m] = o2;
         if (u.stage == 2) {
-            const double w = kz == 0 ? 0.5 : 1.0;
-            const double a2 = (double)o0.x * o0.x + (double)o0.y * o0.y + (double)o1.x * o1.x +
-                              (double)o1.y * o1.y + (double)o2.x * o2.x + (double)o2.y * o2.y;
-            e_acc += w * a2;
-            o_acc += w * a2 * (double)k2;
+            DfAcc me;   // |a(k)|^2 of this mode, exact up to the pair's rounding
+            me.add_sq(o0.x);
+            me.add_sq(o0.y);
+            me.add_sq(o1.x);
+            me.add_sq(o1.y);
+            me.add_sq(o2.x);
+            me.add_sq(o2.y);
+            me.renorm();
+            const float w = kz == 0 ? 0.5f : 1.0f;   // half-layout weight / 2
+            e_acc.add_scaled(me, w);
+            o_acc.add_scaled(me, w * (float)k2);   // k2 <= 3 K^2 < 2^24: exact
         }
     }
     if (u.stage == 2) {
-        block_sum2(e_acc, o_acc, sh);
+        double e = e_acc.value(), o = o_acc.value();
+        block_sum2(e, o, sh);
         if (threadIdx.x == 0) {
             double *pp = part + 2 * ((long)run * u.nparts + blockIdx.x);
-            pp[0] = e_acc;
-            pp[1] = o_acc;
+            pp[0] = e;
+            pp[1] = o;
         }
     }
 }
@@ -397,6 +442,17 @@ cudaError_t prepare_fused_kernels() {
                     if (e != cudaSuccess) return e;
                 }
             }
+    const int zrEs[] = {16, 12, 8, 6, 4};
+    const int zrTiles[] = {1, 2, ZR_PARK + 1, ZR_PARK + 2};
+    for (int N : Ns)
+        for (int zE : zrEs)
+            for (int tile : zrTiles) {
+                ZctKernel z;
+                if (zr_lookup(N, zE, tile, &z)) {
+                    cudaError_t e = allow_smem(z.k, 48 * 1024 + 1);
+                    if (e != cudaSuccess) return e;
+                }
+            }
     const int Ects[] = {8, 12, 16, 32};
     for (int N : Ns)
         for (int E : Ects)
@@ -436,6 +492,22 @@ static cudaError_t launch_strided(const void *k, const FzPass &ps, const Plan &p
     return cudaLaunchKernel(k, dim3((unsigned)blocks, (unsigned)nr), dim3(ct * T), args, smem, s);
 }
 
+static cudaError_t launch_zr(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
+    ZctKernel z;
+    if (!zr_lookup(f.n, cfg.pl.E, cfg.ct, &z) || f.Mz != (f.n - 1) / 3 + 1) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(z.k, z.smem);
+    if (e != cudaSuccess) return e;
+    long nlines = (long)f.n * f.n;
+    const long blocks = (nlines + z.lines_per_block - 1) / z.lines_per_block;
+    float2 *buf = f.bbuf;
+    long fs = (long)f.n * f.n * f.Mz;
+    long brun = f.sB;
+    const float2 *tw = f.tw;
+    void *args[] = {(void *)&buf, (void *)&fs, (void *)&nlines, (void *)&brun, (void *)&tw};
+    return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem,
+                            s);
+}
+
 static cudaError_t launch_z_ct(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
     ZctKernel z;
     if (!zct_lookup(f.n, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
@@ -455,6 +527,7 @@ static cudaError_t launch_z_ct(FusedRun &f, const PassCfg &cfg, cudaStream_t s) 
 
 static cudaError_t launch_z(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
     if (cfg.kind == 1) return launch_z_ct(f, cfg, s);
+    if (cfg.kind == 2) return launch_zr(f, cfg, s);
     const void *k = z_for(cfg.pl.E);
     if (!k) return cudaErrorInvalidValue;
     const int n = f.n / 2, Tn = n / cfg.pl.E;
@@ -561,7 +634,7 @@ template <class F> static float time_launch(F launch, cudaStream_t s, int reps) 
 static bool cfg_from_triple(int n, int kind, int E, int tile, bool zpass, PassCfg &out) {
     Plan pl;
     const int len = zpass ? n / 2 : n;
-    if (kind == 1) {
+    if (kind == 1 || (kind == 2 && zpass)) {
         if (!make_plan(len, &pl)) return false;
         pl.E = E;   // compile-time kernels carry their own plan; E names the shape
     } else if (!make_plan_e(len, E, &pl)) {
@@ -689,6 +762,20 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
                 f.zc = cfg;
             }
         }
+        const int zrEs[] = {16, 12, 8, 6, 4};
+        const int zrTiles[] = {1, 2, ZR_PARK + 1, ZR_PARK + 2};
+        for (int zE : zrEs)
+            for (int tile : zrTiles) {
+                ZctKernel z;
+                if (!zr_lookup(f.n, zE, tile, &z)) continue;
+                PassCfg cfg{f.plH, tile, 2};
+                cfg.pl.E = zE;
+                const float ms = time_launch([&]() { return launch_z(f, cfg, s); }, s, reps);
+                if (ms > 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    f.zc = cfg;
+                }
+            }
         for (const Plan &pl : plan_candidates(f.n / 2)) {
             const int Tn = pl.n / pl.E;
             for (int L = 1; 6 * L * Tn <= 256; L *= 2) {
@@ -761,7 +848,23 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     const int ct = default_ct(sizeof(float2), f.n);
     for (int i = 0; i < 4; i++) f.sp[i] = PassCfg{f.plN, ct};
     f.zc = PassCfg{f.plH, std::max(1, 192 / (6 * (f.n / 2 / f.plH.E)))};
-    return fused_autotune(f, s);
+    cudaError_t e2 = fused_autotune(f, s);
+    if (e2 != cudaSuccess) return e2;
+    // Diagnostic override of the pass-C kernel, NS_FORCE_PASS_C="kind,E,tile"
+    // (the plan-cache triple); ignored when no such kernel is compiled for N.
+    if (const char *fz = getenv("NS_FORCE_PASS_C")) {
+        int kind = -1, E = 0, tile = 0;
+        PassCfg c;
+        ZctKernel z;
+        if (sscanf(fz, "%d,%d,%d", &kind, &E, &tile) == 3 && cfg_from_triple(f.n, kind, E, tile, true, c)) {
+            const bool ok = kind == 2   ? zr_lookup(f.n, E, tile, &z)
+                            : kind == 1 ? zct_lookup(f.n, E, tile, &z)
+                                        : (kind == 0 && z_for(E) && tile >= 1 &&
+                                           6 * tile * (f.n / 2 / E) <= 256);
+            if (ok) f.zc = c;
+        }
+    }
+    return cudaSuccess;
 }
 
 void fused_free(FusedRun &f) {
@@ -815,7 +918,12 @@ int fused_describe(const FusedRun &f, char *out, int len) {
                       "\"%s\": {\"kernel\": \"%s\", \"E\": %d, \"cols_per_cta\": %d}, ", names[i],
                       f.sp[i].kind == 1 ? "compile-time length" : "runtime length", f.sp[i].pl.E,
                       f.sp[i].ct);
-    if (w < len && f.zc.kind == 1)
+    if (w < len && f.zc.kind == 2)
+        w += snprintf(out + w, len - w,
+                      "\"C_z_nonlinear\": {\"kernel\": \"register-resident\", \"E\": %d, "
+                      "\"warps_per_cta\": %d, \"park_ux\": %s}}",
+                      f.zc.pl.E, f.zc.ct & (ZR_PARK - 1), (f.zc.ct & ZR_PARK) ? "true" : "false");
+    else if (w < len && f.zc.kind == 1)
         w += snprintf(out + w, len - w,
                       "\"C_z_nonlinear\": {\"kernel\": \"compile-time length\", \"E\": %d, "
                       "\"warps_per_cta\": %d}}",

@@ -12,7 +12,8 @@ namespace nsk {
 struct PassCfg {
     Plan pl{};
     int ct = 16;
-    int kind = 0;   // 0: runtime-length kernel; 1: compile-time-length kernel (for pass C, ct = warps per CTA)
+    int kind = 0;   // 0: runtime-length kernel; 1: compile-time-length kernel (for pass C, ct = warps per CTA);
+                    // 2 (pass C only): register-resident compile-time kernel, ct = zr_lookup tile
 };
 
 // A pass-C kernel specialised for one grid size (fused_z.cu).
@@ -25,6 +26,11 @@ struct ZctKernel {
 // Kernel for grid size N, E elements per thread and wpb warps per CTA, if one
 // was compiled (E in {16, 8} or {12, 6}; wpb in {1, 2, 4}).
 bool zct_lookup(int N, int E, int wpb, ZctKernel *out);
+// Register-resident pass-C kernel (fused_zr.cuh, fused_zr2.cu, fused_zr3.cu):
+// tile = warps per CTA (1 or 2) plus ZR_PARK when u_x is parked in shared
+// memory.
+constexpr int ZR_PARK = 8;
+bool zr_lookup(int N, int E, int tile, ZctKernel *out);
 
 // A strided-pass kernel specialised for one (N, E, CT) shape (fused_s*.cu).
 struct FzsKernel {

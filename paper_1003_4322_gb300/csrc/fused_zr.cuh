@@ -1,0 +1,245 @@
+// fused_zr.cuh -- pass C of the fused form with each line held in registers.
+//
+// Pass C (z c2r of u and w, the cross product u x w on the grid, z r2c of
+// the product; Sec. 2, Eqs. 1-2) is the pass with the most arithmetic per
+// byte.  This form keeps a (y, x) line's six transformed fields in the
+// registers of the T = N/2 / E threads that own it instead of in shared
+// memory:
+//
+//  * the first Stockham stage of a length-n transform reads the elements
+//    slot + j T of the line, which are exactly the ones a thread loads (or,
+//    for the forward transform, holds after the cross product), and the last
+//    stage leaves the thread the same set of positions, so the line crosses
+//    shared memory only between stages (one exchange for a two-stage plan);
+//  * the even/odd packing of the real transforms pairs element k with
+//    element n - k, which the partner lane (T - slot) mod T holds in register
+//    E - 1 - j: it arrives by warp shuffle;
+//  * the cross product is taken in registers, with the fields transformed in
+//    the order u_x, w_y, u_y, w_x, u_z, w_z so that at most five field arrays
+//    are live (u_x, the longest-lived, optionally parked in thread-private
+//    shared memory).
+// With N fixed at compile time the kept range kz < (N-1)/3 + 1 is a constant
+// too, so the registers that only ever hold dealiased zeros fold away.
+#pragma once
+#include "fft_ct.cuh"
+#include "fused.h"
+
+namespace nsk {
+
+// Length-n line FFT over the T = n/E threads of a line.  v enters holding
+// positions slot + j T (j < E) and leaves holding the transform at the same
+// positions; stages after the first exchange through the line's shared
+// buffer (sl/ss).
+template <int n, int E, int DIR, int NTAB, int S = 0, class SL, class SS>
+NSK_DEV void ct_fft_reg(float2 (&v)[E], int slot, const CtTwiddles<n, E, NTAB> &twr, SL sl, SS ss) {
+    constexpr int NST = ct_nst(n, E);
+    constexpr int R = ct_radix(n, E, S), T = n / E, nR = n / R, p = ct_span(n, E, S);
+    if constexpr (S > 0) {
+#pragma unroll
+        for (int b = 0; b < E / R; b++) {
+            const int i = slot + b * T;
+#pragma unroll
+            for (int q = 0; q < R; q++) v[b * R + q] = sl(i + q * nR);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < E / R; b++) {
+        if constexpr (S > 0) {
+            constexpr int o = CtTwiddles<n, E, NTAB>::offset(S);
+#pragma unroll
+            for (int q = 1; q < R; q++) {
+                const float2 w = twr.w[o + b * (R - 1) + q - 1];
+                v[b * R + q] = DIR < 0 ? cmul(v[b * R + q], w) : cmulc(v[b * R + q], w);
+            }
+        }
+        Dft<R, DIR, float2>::run(&v[b * R]);
+    }
+    if constexpr (S + 1 < NST) {
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < E / R; b++) {
+            const int i = slot + b * T;
+            const int k = i % p;
+            const int j = (i - k) * R + k;
+#pragma unroll
+            for (int q = 0; q < R; q++) ss(j + q * p, v[b * R + q]);
+        }
+        __syncwarp();
+        ct_fft_reg<n, E, DIR, NTAB, S + 1>(v, slot, twr, sl, ss);
+    } else {
+        // The last stage's butterfly b leaves output q at slot + T (b + q E/R).
+        float2 t[E];
+#pragma unroll
+        for (int b = 0; b < E / R; b++)
+#pragma unroll
+            for (int q = 0; q < R; q++) t[b + q * (E / R)] = v[b * R + q];
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = t[j];
+    }
+}
+
+// Shape of the register form for grid size N with E elements per thread.
+template <int N, int E_> struct ZrShape {
+    static constexpr int n = N / 2;
+    static constexpr int E = E_;
+    static constexpr int T = n / E;
+    static constexpr bool ok = n % E == 0 && ct_valid(n, E) && T >= 1 && T <= 32 && 32 % T == 0;
+    static constexpr int LPW = ok ? 32 / T : 1;                       // lines per warp
+    static constexpr int NST = ok ? ct_nst(n, E) : 1;
+    static constexpr int LS = (ok && NST > 1) ? ct_line_stride(n, E, 1) : 0;   // exchange buffer
+    static constexpr int Mz = (N - 1) / 3 + 1;                        // kept kz
+};
+
+NSK_DEV float2 pmul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+NSK_DEV float2 shfl2(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+template <int N, int E, int WPB, bool PARK>
+__global__ void __launch_bounds__(32 * WPB)
+k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restrict__ tw) {
+    typedef ZrShape<N, E> Z;
+    constexpr int n = Z::n, T = Z::T, LPW = Z::LPW, LS = Z::LS, Mz = Z::Mz;
+    buf += blockIdx.y * brun;   // run of the group
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ll = lane / T, slot = lane % T;
+    const int partner = ll * T + (T - slot) % T;   // holds position n - k of this line
+    const long line = ((long)blockIdx.x * WPB + warp) * LPW + ll;
+    const bool valid = line < nlines;
+    float2 *L = sm + (long)(warp * LPW + ll) * LS;
+    float2 *park = sm + (long)WPB * LPW * LS + (long)warp * E * 32 + lane;
+    auto sl = [&](int e) -> float2 { return L[ct_skew(e)]; };
+    auto ss = [&](int e, float2 v) { L[ct_skew(e)] = v; };
+
+    CtTwiddles<n, E, N> twr;
+    twr.load(slot, tw);
+    float2 wk[E];   // W^k = exp(-2 pi i k / N), k = slot + j T
+#pragma unroll
+    for (int j = 0; j < E; j++) wk[j] = __ldg(tw + slot + j * T);
+
+    float2 x[E];   // X[k], k = slot + j T, of the field being loaded
+    auto fetch = [&](int f) {
+        const float2 *src = buf + f * fs + line * Mz;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            x[j] = make_float2(0.f, 0.f);
+            if (j * T < Mz && valid && k < Mz) x[j] = src[k];
+        }
+    };
+    // c2r: Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]) with
+    // the imaginary parts of X[0] and X[n] dropped, then the inverse length-n
+    // FFT; complex element m of the result holds the real points 2m, 2m + 1.
+    auto inverse = [&](float2 (&v)[E], int fnext) {
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            float2 a0 = x[j];
+            float2 am = make_float2(0.f, 0.f);
+            if ((E - 1 - j) * T < Mz) am = shfl2(x[E - 1 - j], partner);
+            if (slot == 0) am = (j > 0 && (E - j) * T < Mz) ? x[(E - j) % E] : make_float2(0.f, 0.f);
+            if (k == 0) {
+                a0.y = 0.f;
+                am.y = 0.f;
+            }
+            const float2 xc = cconj(am);
+            const float2 wb = cmulc(csub(a0, xc), wk[j]);
+            v[j] = cadd(cadd(a0, xc), cmul_i<1>(wb));
+        }
+        if (fnext >= 0) fetch(fnext);
+        ct_fft_reg<n, E, +1, N>(v, slot, twr, sl, ss);
+    };
+    // r2c of a product held as Z[m] = x[2m] + i x[2m+1]: forward length-n FFT,
+    // then X[k] = (Z[k] + conj Z[n-k])/2 - i W^k (Z[k] - conj Z[n-k])/2 for
+    // the kept k < Mz, written over field f of the line.
+    auto forward_store = [&](float2 (&v)[E], int f) {
+        ct_fft_reg<n, E, -1, N>(v, slot, twr, sl, ss);
+        float2 *dst = buf + f * fs + line * Mz;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            if (j * T < Mz) {
+                const int k = slot + j * T;
+                float2 zm = shfl2(v[E - 1 - j], partner);
+                if (slot == 0) zm = v[(E - j) % E];
+                const float2 zk = v[j], zc = cconj(zm);
+                const float2 ev = cscale(cadd(zk, zc), 0.5f);
+                const float2 od = cmul_i<-1>(cscale(csub(zk, zc), 0.5f));
+                if (valid && k < Mz) dst[k] = cadd(ev, cmul(od, wk[j]));
+            }
+        }
+    };
+
+    // fields: 0..2 = u_x, u_y, u_z; 3..5 = w_x, w_y, w_z; output over 0..2.
+    // Order u_x, w_y, u_y, w_x (then (u x w)_z is complete), u_z, w_z: at
+    // most five field arrays are live.  A thread stores only positions it
+    // loaded itself, and its loads of a field precede its stores to it.
+    float2 A[E], B[E], C[E], D[E], P[E];
+    fetch(0);
+    inverse(A, 4);   // u_x
+    if constexpr (PARK) {
+#pragma unroll
+        for (int j = 0; j < E; j++) park[j * 32] = A[j];
+    }
+    inverse(B, 1);   // w_y
+#pragma unroll
+    for (int j = 0; j < E; j++) P[j] = pmul(PARK ? park[j * 32] : A[j], B[j]);   // u_x w_y
+    inverse(C, 3);   // u_y
+    inverse(D, 2);   // w_x
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        const float2 t = pmul(C[j], D[j]);   // u_y w_x
+        P[j] = make_float2(P[j].x - t.x, P[j].y - t.y);
+    }
+    forward_store(P, 2);
+    float2 px[E], py[E];
+    inverse(P, 5);   // u_z
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        px[j] = pmul(P[j], B[j]);   // u_z w_y (subtracted below)
+        py[j] = pmul(P[j], D[j]);   // u_z w_x
+    }
+    inverse(B, -1);  // w_z
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        const float2 a = PARK ? park[j * 32] : A[j];
+        const float2 s = pmul(C[j], B[j]);   // u_y w_z
+        const float2 t = pmul(a, B[j]);      // u_x w_z
+        px[j] = make_float2(s.x - px[j].x, s.y - px[j].y);
+        py[j] = make_float2(py[j].x - t.x, py[j].y - t.y);
+    }
+    forward_store(px, 0);
+    forward_store(py, 1);
+}
+
+template <int N, int E, int WPB, bool PARK> bool zr_entry(ZctKernel *o) {
+    typedef ZrShape<N, E> Z;
+    if constexpr (!Z::ok) {
+        return false;
+    } else {
+        o->k = (const void *)k_fused_zr<N, E, WPB, PARK>;
+        o->smem = (size_t)WPB * (Z::LPW * Z::LS + (PARK ? E * 32 : 0)) * sizeof(float2);
+        o->lines_per_block = WPB * Z::LPW;
+        o->threads = 32 * WPB;
+        return true;
+    }
+}
+
+// tile = warps per CTA (1 or 2), plus ZR_PARK to park u_x in shared memory.
+template <int N, int E, bool PARK> bool zr_by_tile(int tile, ZctKernel *o) {
+    const bool park = (tile & ZR_PARK) != 0;
+    if (park != PARK) return false;
+    switch (tile & (ZR_PARK - 1)) {
+    case 1: return zr_entry<N, E, 1, PARK>(o);
+    case 2: return zr_entry<N, E, 2, PARK>(o);
+    }
+    return false;
+}
+
+// Lookups per family of grid sizes (fused_zr2.cu: powers of two, fused_zr3.cu:
+// with a factor 3).
+bool zr_lookup2(int N, int E, int tile, ZctKernel *o);
+bool zr_lookup3(int N, int E, int tile, ZctKernel *o);
+
+}  // namespace nsk

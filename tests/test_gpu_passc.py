@@ -1,0 +1,67 @@
+"""Every compiled pass-C kernel of the fused FP32 form (z c2r of u and w,
+u x w on the grid, z r2c of the product; Sec. 2, Eqs. 1-2), forced in turn
+through NS_FORCE_PASS_C, against the plain FP64 form on the same GPU (itself
+pinned to the oracle).  The autotuner picks one kernel per N; this checks the
+ones it did not pick as well, at sizes that span several lines per CTA, the
+ragged last CTA and both families of N (powers of two, factor 3)."""
+import pytest
+
+from paper_1003_4322_gb300 import inputs
+from tests.spectral_ref import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+# (kind, E, tile) triples as the plan cache writes them: kind 2 =
+# register-resident (tile = warps per CTA, + 8 with u_x parked), kind 1 =
+# shared-memory line kernel (tile = warps per CTA).
+CANDIDATES = ([(2, E, t) for E in (16, 12, 8, 6, 4) for t in (1, 2, 9, 10)]
+              + [(1, E, w) for E in (16, 12, 8, 6) for w in (1, 2, 4)])
+
+
+def _matches(desc, kind, E, tile):
+    c = desc["C_z_nonlinear"]
+    if c.get("E") != E:
+        return False
+    if kind == 2:
+        return (c.get("kernel") == "register-resident" and c["warps_per_cta"] == tile % 8
+                and c["park_ux"] == (tile >= 8))
+    return c.get("kernel") == "compile-time length" and c["warps_per_cta"] == tile
+
+
+def _find_c(desc):
+    if "C_z_nonlinear" in desc:
+        return desc
+    for v in desc.values():
+        if isinstance(v, dict):
+            r = _find_c(v)
+            if r is not None:
+                return r
+    return None
+
+
+@pytest.mark.parametrize("n", [32, 64, 96, 128, 192, 256])
+def test_every_pass_c_kernel(ns, n, monkeypatch):
+    from paper_1003_4322_gb300 import _native as nat
+    from paper_1003_4322_gb300.solver import Solver
+    run = dict(n=n, nu=2e-3, dt=1e-3, force_amp=0.5, force_k=3)
+    a0 = inputs.turbulence_state(n, seed=3)
+    steps = 2
+    with Solver([run], prec="fp64") as s:
+        s.set_state(a0)
+        s.step(steps)
+        ref = s.get_state()
+    tried = []
+    for kind, E, tile in CANDIDATES:
+        monkeypatch.setenv("NS_FORCE_PASS_C", f"{kind},{E},{tile}")
+        with Solver([run], prec="fp32") as s:
+            desc = _find_c(nat.ns_describe_run(s.ctx, 0))
+            if desc is None or not _matches(desc, kind, E, tile):
+                continue
+            s.set_state(a0)
+            s.step(steps)
+            got = s.get_state()
+        err = rel_l2(got, ref)
+        assert err < 2e-5, (kind, E, tile, err)
+        tried.append((kind, E, tile))
+    # at least one register-resident and one shared-memory kernel per N
+    assert any(t[0] == 2 for t in tried) and any(t[0] == 1 for t in tried), tried

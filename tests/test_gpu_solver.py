@@ -236,3 +236,22 @@ def test_helicity_matches_oracle(ns, prec):
         s.set_state(inputs.abc_state(32))
         H, spec = s.helicity()
     assert abs(H - 1.5) < (1e-14 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("n", [64, 256])
+def test_fused_series_accumulation_is_fp64_quality(ns, n):
+    """The fused form's per-step (E, Omega) come from compensated FP32 partial
+    sums inside the update kernel; against an FP64 sum of the very state the
+    step stored they agree to ~1e-12 (a plain FP32 running sum would be off by
+    ~1e-7)."""
+    run = dict(n=n, nu=2e-3, dt=1e-3, force_amp=0.5, force_k=3)
+    with _solver(ns, "fp32", **run) as s:
+        s.set_state(inputs.turbulence_state(n, seed=3))
+        s.step(2)
+        Es, Os = s.series(count=10)
+        E, Om, _ = s.energy_spectrum()
+        st = s.get_state() if n <= 64 else None
+    assert abs(Es[-1] - E) < 1e-12 * E and abs(Os[-1] - Om) < 1e-12 * Om
+    if st is not None:
+        rE, rO, _ = oracle.diagnostics(st)
+        assert abs(Es[-1] - rE) < 1e-12 * rE and abs(Os[-1] - rO) < 1e-12 * rO
