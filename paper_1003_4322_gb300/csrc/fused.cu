@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "fused.h"
+#include "fused_k.cuh"
 #include "plain.h"
 #include "fused_access.cuh"
 #include "reduce.cuh"
@@ -146,8 +147,8 @@ k_fused_z(float2 *buf, long fs, int N, int Mz, long nlines, int L, long brun, Pl
 }
 
 // 1/N^3, projection, forcing and the RK2 stage on the compact state; at
-// stage 2 also the per-block FP64 energy and enstrophy partial sums of the
-// new state (grid-stride with a fixed grid: deterministic).  Grid y is the
+// stage 2 also the per-block energy and enstrophy partial sums of the new
+// state, FP64 quality (grid-stride with a fixed grid: deterministic).  Grid y is the
 // run of the group; each run has its own parameters and factor table.
 struct FzUpdate {
     int n, K, Mx, Mz;
@@ -211,6 +212,56 @@ struct DfAcc {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// One mode of the update: N = P Pi (transform of u x w)/N^3 + f, then the
+// IF-RK2 stage, from operands already loaded (b = a, c = a1, v = nl).
+struct FzMode {
+    float2 o0, o1, o2;
+    int k2, kz;
+};
+
+__device__ __forceinline__ FzMode fz_update_mode(long m, const FzUpdate &u, const FzRunParams &q,
+                                                 const float *__restrict__ etab, float inv, float2 vx,
+                                                 float2 vy, float2 vz, float2 b0, float2 b1, float2 b2,
+                                                 float2 c0, float2 c1, float2 c2) {
+    const unsigned Mz = (unsigned)u.Mz, Mx = (unsigned)u.Mx;   // M < 2^31 for every supported N
+    const unsigned row = (unsigned)m / Mz;
+    FzMode r;
+    r.kz = (int)((unsigned)m - row * Mz);
+    const int iky = (int)(row % Mx);
+    const int ikx = (int)(row / Mx);
+    const int kx = fz_compact_signed(ikx, u.Mx, u.K), ky = fz_compact_signed(iky, u.Mx, u.K);
+    const int kz = r.kz;
+    r.k2 = kx * kx + ky * ky + kz * kz;
+    bool keep = r.k2 > 0;
+    if (q.dealias == 1 && 9L * r.k2 >= (long)u.n * u.n) keep = false;
+    r.o0 = r.o1 = r.o2 = make_float2(0.f, 0.f);
+    if (keep) {
+        vx = cscale(vx, inv);
+        vy = cscale(vy, inv);
+        vz = cscale(vz, inv);
+        const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz, ik2 = 1.f / (float)r.k2;
+        const float2 kv = cadd(cadd(cscale(vx, fkx), cscale(vy, fky)), cscale(vz, fkz));
+        vx = csub(vx, cscale(kv, fkx * ik2));
+        vy = csub(vy, cscale(kv, fky * ik2));
+        vz = csub(vz, cscale(kv, fkz * ik2));
+        fz_forcing(kx, ky, kz, q.force_k, q.force_amp, vx, vy, vz);
+        const float e = etab[r.k2];
+        if (u.stage == 1) {
+            r.o0 = cscale(cadd(b0, cscale(vx, q.dt)), e);
+            r.o1 = cscale(cadd(b1, cscale(vy, q.dt)), e);
+            r.o2 = cscale(cadd(b2, cscale(vz, q.dt)), e);
+        } else {
+            const float he = 0.5f * e;
+            r.o0 = cadd(cscale(b0, he), cscale(cadd(c0, cscale(vx, q.dt)), 0.5f));
+            r.o1 = cadd(cscale(b1, he), cscale(cadd(c1, cscale(vy, q.dt)), 0.5f));
+            r.o2 = cadd(cscale(b2, he), cscale(cadd(c2, cscale(vz, q.dt)), 0.5f));
+        }
+    }
+    return r;
+}
+
+// Two modes per thread and iteration, every operand load issued before any
+// arithmetic, so that enough bytes are in flight to stream HBM.
 __global__ void __launch_bounds__(256)
 k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__restrict__ nl,
                const float *__restrict__ etab, const FzRunParams *__restrict__ rp, FzUpdate u,
@@ -224,57 +275,51 @@ k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__
     etab += (long)run * u.nk2;
     const FzRunParams q = rp[run];
     const float inv = (float)(1.0 / ((double)u.n * u.n * u.n));
+    const bool two = u.stage == 2;
+    float2 *dst = two ? a : a1;
     DfAcc e_acc, o_acc;
-    const unsigned Mz = (unsigned)u.Mz, Mx = (unsigned)u.Mx;   // M < 2^31 for every supported N
-    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        const unsigned row = (unsigned)m / Mz;
-        const int kz = (int)((unsigned)m - row * Mz);
-        const int iky = (int)(row % Mx);
-        const int ikx = (int)(row / Mx);
-        const int kx = fz_compact_signed(ikx, u.Mx, u.K), ky = fz_compact_signed(iky, u.Mx, u.K);
-        const int k2 = kx * kx + ky * ky + kz * kz;
-        bool keep = k2 > 0;
-        if (q.dealias == 1 && 9L * k2 >= (long)u.n * u.n) keep = false;
-        float2 o0 = make_float2(0.f, 0.f), o1 = o0, o2 = o0;
-        if (keep) {
-            float2 vx = cscale(nl[m], inv), vy = cscale(nl[M + m], inv), vz = cscale(nl[2 * M + m], inv);
-            const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz, ik2 = 1.f / (float)k2;
-            const float2 kv = cadd(cadd(cscale(vx, fkx), cscale(vy, fky)), cscale(vz, fkz));
-            vx = csub(vx, cscale(kv, fkx * ik2));
-            vy = csub(vy, cscale(kv, fky * ik2));
-            vz = csub(vz, cscale(kv, fkz * ik2));
-            fz_forcing(kx, ky, kz, q.force_k, q.force_amp, vx, vy, vz);
-            const float e = etab[k2];
-            if (u.stage == 1) {
-                o0 = cscale(cadd(a[m], cscale(vx, q.dt)), e);
-                o1 = cscale(cadd(a[M + m], cscale(vy, q.dt)), e);
-                o2 = cscale(cadd(a[2 * M + m], cscale(vz, q.dt)), e);
-            } else {
-                const float he = 0.5f * e;
-                o0 = cadd(cscale(a[m], he), cscale(cadd(a1[m], cscale(vx, q.dt)), 0.5f));
-                o1 = cadd(cscale(a[M + m], he), cscale(cadd(a1[M + m], cscale(vy, q.dt)), 0.5f));
-                o2 = cadd(cscale(a[2 * M + m], he), cscale(cadd(a1[2 * M + m], cscale(vz, q.dt)), 0.5f));
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long m0 = blockIdx.x * (long)blockDim.x + threadIdx.x; m0 < M; m0 += 2 * stride) {
+        const long m1 = m0 + stride;
+        const bool has1 = m1 < M;
+        const float2 z = make_float2(0.f, 0.f);
+        float2 v[2][3], b[2][3], c[2][3];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const long m = i ? m1 : m0;
+            const bool ok = i == 0 || has1;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                v[i][d] = ok ? nl[d * M + m] : z;
+                b[i][d] = ok ? a[d * M + m] : z;
+                c[i][d] = (ok && two) ? a1[d * M + m] : z;
             }
         }
-        float2 *dst = u.stage == 1 ? a1 : a;
-        dst[m] = o0;
-        dst[M + m] = o1;
-        dst[2 * M + m] = o2;
-        if (u.stage == 2) {
-            DfAcc me;   // |a(k)|^2 of this mode, exact up to the pair's rounding
-            me.add_sq(o0.x);
-            me.add_sq(o0.y);
-            me.add_sq(o1.x);
-            me.add_sq(o1.y);
-            me.add_sq(o2.x);
-            me.add_sq(o2.y);
-            me.renorm();
-            const float w = kz == 0 ? 0.5f : 1.0f;   // half-layout weight / 2
-            e_acc.add_scaled(me, w);
-            o_acc.add_scaled(me, w * (float)k2);   // k2 <= 3 K^2 < 2^24: exact
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            if (i == 1 && !has1) break;
+            const long m = i ? m1 : m0;
+            const FzMode r = fz_update_mode(m, u, q, etab, inv, v[i][0], v[i][1], v[i][2], b[i][0],
+                                            b[i][1], b[i][2], c[i][0], c[i][1], c[i][2]);
+            dst[m] = r.o0;
+            dst[M + m] = r.o1;
+            dst[2 * M + m] = r.o2;
+            if (two) {
+                DfAcc me;   // |a(k)|^2 of this mode, exact up to the pair's rounding
+                me.add_sq(r.o0.x);
+                me.add_sq(r.o0.y);
+                me.add_sq(r.o1.x);
+                me.add_sq(r.o1.y);
+                me.add_sq(r.o2.x);
+                me.add_sq(r.o2.y);
+                me.renorm();
+                const float w = r.kz == 0 ? 0.5f : 1.0f;   // half-layout weight / 2
+                e_acc.add_scaled(me, w);
+                o_acc.add_scaled(me, w * (float)r.k2);   // k2 <= 3 K^2 < 2^24: exact
+            }
         }
     }
-    if (u.stage == 2) {
+    if (two) {
         double e = e_acc.value(), o = o_acc.value();
         block_sum2(e, o, sh);
         if (threadIdx.x == 0) {
@@ -430,6 +475,17 @@ static bool fzs_lookup(int which, int N, int E, int CT, FzsKernel *o) {
                       : fzs_lookup_DE(N, E, CT, o);
 }
 
+// Constant-geometry kernel of pass 0..3 (A, B, D, E).
+static bool fzk_lookup(int pass, int N, int E, int CT, FzsKernel *o) {
+    switch (pass) {
+    case 0: return fzk_lookup_A(N, E, CT, o);
+    case 1: return fzk_lookup_B(N, E, CT, o);
+    case 2: return fzk_lookup_D(N, E, CT, o);
+    case 3: return fzk_lookup_E(N, E, CT, o);
+    }
+    return false;
+}
+
 cudaError_t prepare_fused_kernels() {
     const int Ns[] = {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
     const int zEs[] = {16, 12, 8, 6};
@@ -456,7 +512,7 @@ cudaError_t prepare_fused_kernels() {
     const int Ects[] = {8, 12, 16, 32};
     for (int N : Ns)
         for (int E : Ects)
-            for (int ct = 8; ct <= 16; ct *= 2)
+            for (int ct = 8; ct <= 16; ct *= 2) {
                 for (int which = 0; which < 3; which++) {
                     FzsKernel z;
                     if (fzs_lookup(which, N, E, ct, &z)) {
@@ -464,6 +520,14 @@ cudaError_t prepare_fused_kernels() {
                         if (e != cudaSuccess) return e;
                     }
                 }
+                for (int pass = 0; pass < 4; pass++) {
+                    FzsKernel z;
+                    if (fzk_lookup(pass, N, E, ct, &z)) {
+                        cudaError_t e = allow_smem(z.k, 48 * 1024 + 1);
+                        if (e != cudaSuccess) return e;
+                    }
+                }
+            }
     const int Es[] = {4, 6, 8, 9, 12, 16};
     for (int E : Es) {
         const void *ks[] = {strided_for<+1, true, false, true>(E), strided_for<+1, true, false, false>(E),
@@ -576,7 +640,24 @@ static cudaError_t run_pass_ct(FusedRun &f, int which, const PassCfg &cfg, const
     return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem, s);
 }
 
-static cudaError_t run_pass(FusedRun &f, int which, const PassCfg &cfg, const FzPass &ps, cudaStream_t s) {
+static cudaError_t run_pass_k(FusedRun &f, int pass, const PassCfg &cfg, const FzPass &ps, cudaStream_t s) {
+    FzsKernel z;
+    if (!fzk_lookup(pass, f.n, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(z.k, z.smem);
+    if (e != cudaSuccess) return e;
+    const long tiles = (ps.ncols + cfg.ct - 1) / cfg.ct;
+    const long blocks = tiles * ps.nfields;
+    if (blocks > 0x7fffffffL) return cudaErrorInvalidValue;
+    const float2 *in = ps.in, *tw = f.tw;
+    float2 *out = ps.out;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&tw};
+    return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem, s);
+}
+
+// Pass 0..3 (A, B, D, E) with configuration cfg on the buffers of ps.
+static cudaError_t run_pass(FusedRun &f, int pass, const PassCfg &cfg, const FzPass &ps, cudaStream_t s) {
+    if (cfg.kind == 2) return run_pass_k(f, pass, cfg, ps, s);
+    const int which = pass < 2 ? pass : 2;
     if (cfg.kind == 1) return run_pass_ct(f, which, cfg, ps, s);
     const int E = cfg.pl.E;
     const void *k = which == 0 ? strided_for<+1, true, false, true>(E)
@@ -634,7 +715,7 @@ template <class F> static float time_launch(F launch, cudaStream_t s, int reps) 
 static bool cfg_from_triple(int n, int kind, int E, int tile, bool zpass, PassCfg &out) {
     Plan pl;
     const int len = zpass ? n / 2 : n;
-    if (kind == 1 || (kind == 2 && zpass)) {
+    if (kind == 1 || kind == 2) {
         if (!make_plan(len, &pl)) return false;
         pl.E = E;   // compile-time kernels carry their own plan; E names the shape
     } else if (!make_plan_e(len, E, &pl)) {
@@ -721,24 +802,26 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
     for (int i = 0; i < 4; i++) {
         float best = -1.f;
         const int Es[] = {8, 12, 16, 32};
-        for (int E : Es)
-            for (int ct = 8; ct <= 16; ct *= 2) {
-                FzsKernel z;
-                if (!fzs_lookup(which[i], f.n, E, ct, &z)) continue;
-                PassCfg cfg{f.plN, ct, 1};
-                cfg.pl.E = E;
-                const float ms = time_launch([&]() { return run_pass(f, which[i], cfg, P[i], s); }, s, reps);
-                if (ms > 0.f && (best < 0.f || ms < best)) {
-                    best = ms;
-                    f.sp[i] = cfg;
+        for (int kind = 2; kind >= 1; kind--)
+            for (int E : Es)
+                for (int ct = 8; ct <= 16; ct *= 2) {
+                    FzsKernel z;
+                    if (kind == 1 ? !fzs_lookup(which[i], f.n, E, ct, &z) : !fzk_lookup(i, f.n, E, ct, &z))
+                        continue;
+                    PassCfg cfg{f.plN, ct, kind};
+                    cfg.pl.E = E;
+                    const float ms = time_launch([&]() { return run_pass(f, i, cfg, P[i], s); }, s, reps);
+                    if (ms > 0.f && (best < 0.f || ms < best)) {
+                        best = ms;
+                        f.sp[i] = cfg;
+                    }
                 }
-            }
         for (const Plan &pl : plan_candidates(f.n)) {
             const int T = pl.n / pl.E;
             for (int ct = 8; ct <= 16; ct *= 2) {
                 if (ct * T > 512 || (ct * T < 32 && ct < 16)) continue;
                 PassCfg cfg{pl, ct, 0};
-                const float ms = time_launch([&]() { return run_pass(f, which[i], cfg, P[i], s); }, s, reps);
+                const float ms = time_launch([&]() { return run_pass(f, i, cfg, P[i], s); }, s, reps);
                 if (ms > 0.f && (best < 0.f || ms < best)) {
                     best = ms;
                     f.sp[i] = cfg;
@@ -864,6 +947,20 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
             if (ok) f.zc = c;
         }
     }
+    // The same for the strided passes A, B, D, E: NS_FORCE_STRIDED="kind,E,ct"
+    // (kind 1 or 2) applies to each pass that has such a kernel compiled.
+    if (const char *fs = getenv("NS_FORCE_STRIDED")) {
+        int kind = -1, E = 0, ct = 0;
+        PassCfg c;
+        if (sscanf(fs, "%d,%d,%d", &kind, &E, &ct) == 3 && (kind == 1 || kind == 2) &&
+            cfg_from_triple(f.n, kind, E, ct, false, c))
+            for (int i = 0; i < 4; i++) {
+                FzsKernel z;
+                const bool ok = kind == 2 ? fzk_lookup(i, f.n, E, ct, &z)
+                                          : fzs_lookup(i < 2 ? i : 2, f.n, E, ct, &z);
+                if (ok) f.sp[i] = c;
+            }
+    }
     return cudaSuccess;
 }
 
@@ -901,7 +998,7 @@ cudaError_t fused_step(FusedRun &f, int *flags, cudaStream_t s, Tracer *tr) {
         if (e != cudaSuccess) return e;
         e = NSK_TIMED(tr, "fused_D_y_forward", run_pass(f, 2, f.sp[2], D, s));
         if (e != cudaSuccess) return e;
-        e = NSK_TIMED(tr, "fused_E_x_forward", run_pass(f, 2, f.sp[3], Ep, s));
+        e = NSK_TIMED(tr, "fused_E_x_forward", run_pass(f, 3, f.sp[3], Ep, s));
         if (e != cudaSuccess) return e;
         FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.M, f.nk2, f.nparts};
         e = NSK_TIMED(tr, "fused_update", launch_update(f, u, s));
@@ -916,7 +1013,10 @@ int fused_describe(const FusedRun &f, char *out, int len) {
     for (int i = 0; i < 4 && w < len; i++)
         w += snprintf(out + w, len - w,
                       "\"%s\": {\"kernel\": \"%s\", \"E\": %d, \"cols_per_cta\": %d}, ", names[i],
-                      f.sp[i].kind == 1 ? "compile-time length" : "runtime length", f.sp[i].pl.E,
+                      f.sp[i].kind == 2   ? "constant geometry"
+                      : f.sp[i].kind == 1 ? "compile-time length"
+                                          : "runtime length",
+                      f.sp[i].pl.E,
                       f.sp[i].ct);
     if (w < len && f.zc.kind == 2)
         w += snprintf(out + w, len - w,

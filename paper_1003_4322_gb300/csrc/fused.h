@@ -13,7 +13,8 @@ struct PassCfg {
     Plan pl{};
     int ct = 16;
     int kind = 0;   // 0: runtime-length kernel; 1: compile-time-length kernel (for pass C, ct = warps per CTA);
-                    // 2 (pass C only): register-resident compile-time kernel, ct = zr_lookup tile
+                    // 2: pass C register-resident kernel (ct = zr_lookup tile), passes A, B, D, E
+                    //    constant-geometry kernel (fused_k.cuh)
 };
 
 // A pass-C kernel specialised for one grid size (fused_z.cu).

@@ -1,0 +1,123 @@
+// fused_k.cuh -- strided passes A, B, D and E of the fused form with the
+// whole geometry fixed at compile time.
+//
+// For grid size N the pruned layouts are constants: K = (N-1)/3 kept
+// wavenumbers per side, Mx = 2K+1 kept rows along x and y, Mz = K+1 kept kz,
+// and every field, row, column and run stride of every pass follows from
+// them.  With those strides as constants, a column splits into (outer, kz)
+// by a division by a constant, each thread forms its column's base pointers
+// once, and the per-element offsets are 32-bit multiples of constants, which
+// keeps the integer work of a load or store to a couple of instructions.
+#pragma once
+#include "fused_s.cuh"
+
+namespace nsk {
+
+enum { FZ_A = 0, FZ_B = 1, FZ_D = 2, FZ_E = 3 };
+
+// Layouts (per run; runs of a group follow each other):
+//   state      [3][ikx][iky][kz]   (M = Mx Mx Mz per component)
+//   A out      [6][iky][x][kz]     (pass A: x inverse of u and w = i k x u)
+//   B out      [6][y][x][kz]       (pass B: y inverse; pass C works in place)
+//   D out      [3][x][iky][kz]     (pass D: y forward of u x w, kept ky)
+//   E out      [3][ikx][iky][kz]   (pass E: x forward, kept kx)
+template <int N, int PASS> struct FzGeom {
+    static constexpr int K = (N - 1) / 3, Mx = 2 * K + 1, Mz = K + 1;
+    static constexpr long M = (long)Mx * Mx * Mz;
+    static constexpr int MxMz = Mx * Mz, NMz = N * Mz;
+    static constexpr long sA = 6L * Mx * N * Mz, sB = 6L * N * N * Mz, S3 = 3 * M;
+    static constexpr bool in_c = PASS == FZ_A || PASS == FZ_B;    // input rows compact
+    static constexpr bool out_c = PASS == FZ_D || PASS == FZ_E;   // output rows compact
+    static constexpr bool curl = PASS == FZ_A;
+    static constexpr int DIR = in_c ? +1 : -1;
+    static constexpr int nfields = in_c ? 6 : 3;
+    static constexpr int ncols = (PASS == FZ_A || PASS == FZ_E) ? MxMz : NMz;
+    static constexpr long ifs = PASS == FZ_A ? M : PASS == FZ_B ? (long)Mx * NMz
+                              : PASS == FZ_D ? (long)N * NMz : (long)N * MxMz;
+    static constexpr int irs = (PASS == FZ_A || PASS == FZ_E) ? MxMz : NMz;
+    static constexpr long ofs = PASS == FZ_A ? (long)Mx * NMz : PASS == FZ_B ? (long)N * NMz
+                              : PASS == FZ_D ? (long)N * MxMz : M;
+    static constexpr int ors = PASS == FZ_A ? Mz : PASS == FZ_B ? NMz : PASS == FZ_D ? Mz : MxMz;
+    static constexpr long obs = PASS == FZ_A ? NMz : PASS == FZ_B ? Mz : PASS == FZ_D ? MxMz : Mz;
+    static constexpr long irun = PASS == FZ_A ? S3 : PASS == FZ_B ? sA : PASS == FZ_D ? sB : sA;
+    static constexpr long orun = PASS == FZ_A ? sA : PASS == FZ_B ? sB : PASS == FZ_D ? sA : S3;
+    // row offsets stay below 2^31 for every supported N
+    static_assert((long)N * (irs > ors ? irs : ors) < (1L << 31), "32-bit row offsets");
+};
+
+// One column of a pass: grid x is fields x tiles (field fastest), grid y the
+// run; column col of field f splits into the outer index ou and kz = iz.
+template <int N, int PASS> struct FzColK {
+    typedef FzGeom<N, PASS> G;
+    int f;
+    bool valid;
+    const float2 *ib;
+    float2 *ob;
+    float ky, kz;   // pass A: wavenumbers of the column for the curl
+    __device__ __forceinline__ FzColK(const float2 *in, float2 *out, int ct, int c) {
+        f = blockIdx.x % G::nfields;
+        const int tile = blockIdx.x / G::nfields;
+        const int col = tile * ct + c;
+        valid = col < G::ncols;
+        const int cc = valid ? col : 0;
+        const int ou = cc / G::Mz, iz = cc - (cc / G::Mz) * G::Mz;
+        ib = in + blockIdx.y * G::irun + (long)ou * G::Mz + iz + (G::curl ? 0L : f * G::ifs);
+        ob = out + blockIdx.y * G::orun + f * G::ofs + ou * G::obs + iz;
+        ky = (float)(ou <= G::K ? ou : ou - G::Mx);
+        kz = (float)iz;
+    }
+    __device__ __forceinline__ static int compact(int e) {
+        return e <= G::K ? e : (e >= N - G::K ? e - N + G::Mx : -1);
+    }
+    __device__ __forceinline__ float2 load(int e) const {
+        const int r = G::in_c ? compact(e) : e;
+        if (!valid || r < 0) return make_float2(0.f, 0.f);
+        const float2 *b = ib + r * G::irs;
+        if constexpr (!G::curl) {
+            return *b;
+        } else {
+            if (f < 3) return b[f * G::ifs];
+            const float kx = (float)(2 * e < N ? e : e - N);
+            float2 p, q;
+            float sp, sq;
+            if (f == 3) { p = b[2 * G::ifs]; sp = ky; q = b[G::ifs]; sq = kz; }   // i(ky az - kz ay)
+            else if (f == 4) { p = b[0]; sp = kz; q = b[2 * G::ifs]; sq = kx; }   // i(kz ax - kx az)
+            else { p = b[G::ifs]; sp = kx; q = b[0]; sq = ky; }                   // i(kx ay - ky ax)
+            const float re = sp * p.x - sq * q.x, im = sp * p.y - sq * q.y;
+            return make_float2(-im, re);
+        }
+    }
+    __device__ __forceinline__ void store(int e, float2 v) const {
+        const int r = G::out_c ? compact(e) : e;
+        if (!valid || r < 0) return;
+        ob[r * G::ors] = v;
+    }
+};
+
+template <int N, int E, int CT, int PASS>
+__global__ void __launch_bounds__(CT *(N / E))
+k_fzk(const float2 *__restrict__ in, float2 *__restrict__ out, const float2 *__restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int c = threadIdx.x % CT, slot = threadIdx.x / CT;
+    const FzColK<N, PASS> col(in, out, CT, c);
+    auto gl = [&](int e) -> float2 { return col.load(e); };
+    auto gs = [&](int e, float2 v) { col.store(e, v); };
+    auto sl = [&](int e) -> float2 { return sm[TileIndex<E, CT>::at(e, c)]; };
+    auto ss = [&](int e, float2 v) { sm[TileIndex<E, CT>::at(e, c)] = v; };
+    ct_fft_block<N, E, FzGeom<N, PASS>::DIR, N>(slot, tw, gl, sl, ss, gs);
+}
+
+template <int N, int E, int CT, int PASS> static void fzk_fill(FzsKernel *o) {
+    o->k = (const void *)k_fzk<N, E, CT, PASS>;
+    o->smem = (size_t)(N + 1) * TileIndex<E, CT>::rows_stride() * sizeof(float2);
+    o->threads = CT * (N / E);
+}
+
+// Per-pass lookups (fused_kA.cu, fused_kB.cu, fused_kD.cu, fused_kE.cu).
+bool fzk_lookup_A(int N, int E, int CT, FzsKernel *o);
+bool fzk_lookup_B(int N, int E, int CT, FzsKernel *o);
+bool fzk_lookup_D(int N, int E, int CT, FzsKernel *o);
+bool fzk_lookup_E(int N, int E, int CT, FzsKernel *o);
+
+}  // namespace nsk

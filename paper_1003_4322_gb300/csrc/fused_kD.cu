@@ -1,0 +1,17 @@
+// fused_kD.cu -- constant-geometry kernels of pass D (y forward).
+#include "fused_k.cuh"
+
+namespace nsk {
+
+bool fzk_lookup_D(int N, int E, int CT, FzsKernel *o) {
+#define NSK_CASE(n_, e_, ct_)                          \
+    if (N == n_ && E == e_ && CT == ct_) {             \
+        fzk_fill<n_, e_, ct_, FZ_D>(o);               \
+        return true;                                   \
+    }
+    NSK_FZS_SHAPES(NSK_CASE)
+#undef NSK_CASE
+    return false;
+}
+
+}  // namespace nsk

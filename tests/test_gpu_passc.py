@@ -65,3 +65,39 @@ def test_every_pass_c_kernel(ns, n, monkeypatch):
         tried.append((kind, E, tile))
     # at least one register-resident and one shared-memory kernel per N
     assert any(t[0] == 2 for t in tried) and any(t[0] == 1 for t in tried), tried
+
+
+STRIDED = [(k, E, ct) for k in (2, 1) for E in (8, 12, 16, 32) for ct in (8, 16)]
+
+
+@pytest.mark.parametrize("n", [64, 96, 128, 256])
+def test_every_strided_pass_kernel(ns, n, monkeypatch):
+    """Passes A, B, D, E (x/y transforms with the curl, the pruning of rows
+    and the dealiased output rows) on every compiled compile-time kernel,
+    forced through NS_FORCE_STRIDED, against the plain FP64 form."""
+    from paper_1003_4322_gb300 import _native as nat
+    from paper_1003_4322_gb300.solver import Solver
+    run = dict(n=n, nu=2e-3, dt=1e-3, force_amp=0.5, force_k=3)
+    a0 = inputs.turbulence_state(n, seed=4)
+    with Solver([run], prec="fp64") as s:
+        s.set_state(a0)
+        s.step(2)
+        ref = s.get_state()
+    names = {1: "compile-time length", 2: "constant geometry"}
+    tried = []
+    for kind, E, ct in STRIDED:
+        monkeypatch.setenv("NS_FORCE_STRIDED", f"{kind},{E},{ct}")
+        with Solver([run], prec="fp32") as s:
+            passes = _find_c(nat.ns_describe_run(s.ctx, 0))
+            forced = [p for p in ("A_x_inverse_curl", "B_y_inverse", "D_y_forward", "E_x_forward")
+                      if passes[p]["kernel"] == names[kind] and passes[p]["E"] == E
+                      and passes[p]["cols_per_cta"] == ct]
+            if not forced:
+                continue
+            s.set_state(a0)
+            s.step(2)
+            got = s.get_state()
+        err = rel_l2(got, ref)
+        assert err < 2e-5, (kind, E, ct, forced, err)
+        tried.append((kind, E, ct))
+    assert any(t[0] == 2 for t in tried) and any(t[0] == 1 for t in tried), tried
