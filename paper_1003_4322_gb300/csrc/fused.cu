@@ -499,7 +499,7 @@ cudaError_t prepare_fused_kernels() {
                 }
             }
     const int zrEs[] = {16, 12, 8, 6, 4};
-    const int zrTiles[] = {1, 2, ZR_PARK + 1, ZR_PARK + 2};
+    const int zrTiles[] = {1, 2, ZR_PARK + 1, ZR_PARK + 2, 2 * ZR_PARK + 1, 2 * ZR_PARK + 2};
     for (int N : Ns)
         for (int zE : zrEs)
             for (int tile : zrTiles) {
@@ -846,7 +846,7 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
             }
         }
         const int zrEs[] = {16, 12, 8, 6, 4};
-        const int zrTiles[] = {1, 2, ZR_PARK + 1, ZR_PARK + 2};
+        const int zrTiles[] = {1, 2, ZR_PARK + 1, ZR_PARK + 2, 2 * ZR_PARK + 1, 2 * ZR_PARK + 2};
         for (int zE : zrEs)
             for (int tile : zrTiles) {
                 ZctKernel z;
@@ -1021,8 +1021,8 @@ int fused_describe(const FusedRun &f, char *out, int len) {
     if (w < len && f.zc.kind == 2)
         w += snprintf(out + w, len - w,
                       "\"C_z_nonlinear\": {\"kernel\": \"register-resident\", \"E\": %d, "
-                      "\"warps_per_cta\": %d, \"park_ux\": %s}}",
-                      f.zc.pl.E, f.zc.ct & (ZR_PARK - 1), (f.zc.ct & ZR_PARK) ? "true" : "false");
+                      "\"warps_per_cta\": %d, \"parked_fields\": %d}}",
+                      f.zc.pl.E, f.zc.ct % ZR_PARK, f.zc.ct / ZR_PARK);
     else if (w < len && f.zc.kind == 1)
         w += snprintf(out + w, len - w,
                       "\"C_z_nonlinear\": {\"kernel\": \"compile-time length\", \"E\": %d, "

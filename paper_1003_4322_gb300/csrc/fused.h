@@ -28,8 +28,8 @@ struct ZctKernel {
 // was compiled (E in {16, 8} or {12, 6}; wpb in {1, 2, 4}).
 bool zct_lookup(int N, int E, int wpb, ZctKernel *out);
 // Register-resident pass-C kernel (fused_zr.cuh, fused_zr2.cu, fused_zr3.cu):
-// tile = warps per CTA (1 or 2) plus ZR_PARK when u_x is parked in shared
-// memory.
+// tile = warps per CTA (1 or 2) + ZR_PARK x the number of fields parked in
+// shared memory (0, 1: u_x, 2: u_x and u_y).
 constexpr int ZR_PARK = 8;
 bool zr_lookup(int N, int E, int tile, ZctKernel *out);
 

@@ -16,8 +16,8 @@
 //    E - 1 - j: it arrives by warp shuffle;
 //  * the cross product is taken in registers, with the fields transformed in
 //    the order u_x, w_y, u_y, w_x, u_z, w_z so that at most five field arrays
-//    are live (u_x, the longest-lived, optionally parked in thread-private
-//    shared memory).
+//    are live; PARK of them (u_x, then u_y: the longest-lived) can be parked
+//    in thread-private shared memory to leave room for longer lines.
 // With N fixed at compile time the kept range kz < (N-1)/3 + 1 is a constant
 // too, so the registers that only ever hold dealiased zeros fold away.
 #pragma once
@@ -95,7 +95,7 @@ NSK_DEV float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-template <int N, int E, int WPB, bool PARK>
+template <int N, int E, int WPB, int PARK>
 __global__ void __launch_bounds__(32 * WPB)
 k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restrict__ tw) {
     typedef ZrShape<N, E> Z;
@@ -109,7 +109,8 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     const long line = ((long)blockIdx.x * WPB + warp) * LPW + ll;
     const bool valid = line < nlines;
     float2 *L = sm + (long)(warp * LPW + ll) * LS;
-    float2 *park = sm + (long)WPB * LPW * LS + (long)warp * E * 32 + lane;
+    float2 *park0 = sm + (long)WPB * LPW * LS + (long)warp * PARK * E * 32 + lane;   // u_x
+    float2 *park1 = park0 + E * 32;                                                   // u_y
     auto sl = [&](int e) -> float2 { return L[ct_skew(e)]; };
     auto ss = [&](int e, float2 v) { L[ct_skew(e)] = v; };
 
@@ -178,18 +179,22 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     float2 A[E], B[E], C[E], D[E], P[E];
     fetch(0);
     inverse(A, 4);   // u_x
-    if constexpr (PARK) {
+    if constexpr (PARK >= 1) {
 #pragma unroll
-        for (int j = 0; j < E; j++) park[j * 32] = A[j];
+        for (int j = 0; j < E; j++) park0[j * 32] = A[j];
     }
     inverse(B, 1);   // w_y
 #pragma unroll
-    for (int j = 0; j < E; j++) P[j] = pmul(PARK ? park[j * 32] : A[j], B[j]);   // u_x w_y
+    for (int j = 0; j < E; j++) P[j] = pmul(PARK >= 1 ? park0[j * 32] : A[j], B[j]);   // u_x w_y
     inverse(C, 3);   // u_y
+    if constexpr (PARK >= 2) {
+#pragma unroll
+        for (int j = 0; j < E; j++) park1[j * 32] = C[j];
+    }
     inverse(D, 2);   // w_x
 #pragma unroll
     for (int j = 0; j < E; j++) {
-        const float2 t = pmul(C[j], D[j]);   // u_y w_x
+        const float2 t = pmul(PARK >= 2 ? park1[j * 32] : C[j], D[j]);   // u_y w_x
         P[j] = make_float2(P[j].x - t.x, P[j].y - t.y);
     }
     forward_store(P, 2);
@@ -203,8 +208,8 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     inverse(B, -1);  // w_z
 #pragma unroll
     for (int j = 0; j < E; j++) {
-        const float2 a = PARK ? park[j * 32] : A[j];
-        const float2 s = pmul(C[j], B[j]);   // u_y w_z
+        const float2 a = PARK >= 1 ? park0[j * 32] : A[j];
+        const float2 s = pmul(PARK >= 2 ? park1[j * 32] : C[j], B[j]);   // u_y w_z
         const float2 t = pmul(a, B[j]);      // u_x w_z
         px[j] = make_float2(s.x - px[j].x, s.y - px[j].y);
         py[j] = make_float2(py[j].x - t.x, py[j].y - t.y);
@@ -213,24 +218,23 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     forward_store(py, 1);
 }
 
-template <int N, int E, int WPB, bool PARK> bool zr_entry(ZctKernel *o) {
+template <int N, int E, int WPB, int PARK> bool zr_entry(ZctKernel *o) {
     typedef ZrShape<N, E> Z;
     if constexpr (!Z::ok) {
         return false;
     } else {
         o->k = (const void *)k_fused_zr<N, E, WPB, PARK>;
-        o->smem = (size_t)WPB * (Z::LPW * Z::LS + (PARK ? E * 32 : 0)) * sizeof(float2);
+        o->smem = (size_t)WPB * (Z::LPW * Z::LS + PARK * E * 32) * sizeof(float2);
         o->lines_per_block = WPB * Z::LPW;
         o->threads = 32 * WPB;
         return true;
     }
 }
 
-// tile = warps per CTA (1 or 2), plus ZR_PARK to park u_x in shared memory.
-template <int N, int E, bool PARK> bool zr_by_tile(int tile, ZctKernel *o) {
-    const bool park = (tile & ZR_PARK) != 0;
-    if (park != PARK) return false;
-    switch (tile & (ZR_PARK - 1)) {
+// tile = warps per CTA (1 or 2) + ZR_PARK x the number of parked fields.
+template <int N, int E, int PARK> bool zr_by_tile(int tile, ZctKernel *o) {
+    if (tile / ZR_PARK != PARK) return false;
+    switch (tile % ZR_PARK) {
     case 1: return zr_entry<N, E, 1, PARK>(o);
     case 2: return zr_entry<N, E, 2, PARK>(o);
     }

@@ -1,19 +1,19 @@
 // fused_zr2.cu -- register-resident pass C for power-of-two grid sizes:
-// E = 8 or 4 elements per thread; E = 16 with u_x parked at N = 256 and 512
-// (a two-stage plan) and at N = 1024 (where E = 8 would need two warps per
-// line).
+// E = 8 or 4 elements per thread; E = 16 with one or two fields parked at
+// N = 256 and 512 (a two-stage plan) and at N = 1024 (where E = 8 would need
+// two warps per line).
 #include "fused_zr.cuh"
 
 namespace nsk {
 
 template <int N> static bool zr_pow2(int E, int tile, ZctKernel *o) {
     if constexpr (N == 1024) {
-        return E == 16 && zr_by_tile<N, 16, true>(tile, o);
+        return E == 16 && (zr_by_tile<N, 16, 1>(tile, o) || zr_by_tile<N, 16, 2>(tile, o));
     } else {
-        if (E == 8) return zr_by_tile<N, 8, false>(tile, o);
-        if (E == 4) return zr_by_tile<N, 4, false>(tile, o);
+        if (E == 8) return zr_by_tile<N, 8, 0>(tile, o);
+        if (E == 4) return zr_by_tile<N, 4, 0>(tile, o);
         if constexpr (N == 256 || N == 512)
-            if (E == 16) return zr_by_tile<N, 16, true>(tile, o);
+            if (E == 16) return zr_by_tile<N, 16, 1>(tile, o) || zr_by_tile<N, 16, 2>(tile, o);
         return false;
     }
 }

@@ -1,12 +1,12 @@
 // fused_zr3.cu -- register-resident pass C for grid sizes with a factor 3:
-// E = 12 with u_x parked in shared memory, or E = 6.
+// E = 12 with one or two fields parked in shared memory, or E = 6.
 #include "fused_zr.cuh"
 
 namespace nsk {
 
 template <int N> static bool zr_three(int E, int tile, ZctKernel *o) {
-    if (E == 12) return zr_by_tile<N, 12, true>(tile, o);
-    if (E == 6) return zr_by_tile<N, 6, false>(tile, o);
+    if (E == 12) return zr_by_tile<N, 12, 1>(tile, o) || zr_by_tile<N, 12, 2>(tile, o);
+    if (E == 6) return zr_by_tile<N, 6, 0>(tile, o);
     return false;
 }
 

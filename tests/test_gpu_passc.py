@@ -12,9 +12,9 @@ from tests.spectral_ref import rel_l2
 pytestmark = pytest.mark.gpu
 
 # (kind, E, tile) triples as the plan cache writes them: kind 2 =
-# register-resident (tile = warps per CTA, + 8 with u_x parked), kind 1 =
+# register-resident (tile = warps per CTA + 8 x parked fields), kind 1 =
 # shared-memory line kernel (tile = warps per CTA).
-CANDIDATES = ([(2, E, t) for E in (16, 12, 8, 6, 4) for t in (1, 2, 9, 10)]
+CANDIDATES = ([(2, E, t) for E in (16, 12, 8, 6, 4) for t in (1, 2, 9, 10, 17, 18)]
               + [(1, E, w) for E in (16, 12, 8, 6) for w in (1, 2, 4)])
 
 
@@ -24,7 +24,7 @@ def _matches(desc, kind, E, tile):
         return False
     if kind == 2:
         return (c.get("kernel") == "register-resident" and c["warps_per_cta"] == tile % 8
-                and c["park_ux"] == (tile >= 8))
+                and c["parked_fields"] == tile // 8)
     return c.get("kernel") == "compile-time length" and c["warps_per_cta"] == tile
 
 
