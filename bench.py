@@ -65,23 +65,37 @@ def load_peaks():
     return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
 
 
+# Kernel sources of each form, for telling whether a committed ncu capture
+# still describes the kernels that run.
+KERNEL_SOURCES = {
+    "fp64": ("fft_core.cuh", "fft_passes.cu", "plain.cu", "plain.h", "reduce.cuh"),
+    "fp32": ("fft_core.cuh", "fft_ct.cuh", "reduce.cuh", "fused.cu", "fused.h", "fused_access.cuh",
+             "fused_s.cuh", "fused_k.cuh", "fused_kA.cu", "fused_kB.cu", "fused_kD.cu",
+             "fused_kE.cu", "fused_sA.cu", "fused_sB.cu", "fused_sDE.cu", "fused_z.cu",
+             "fused_zr.cuh", "fused_zr2.cu", "fused_zr3.cu"),
+}
+
+
+def source_hash(prec):
+    import hashlib
+    h = hashlib.sha256()
+    for fn in KERNEL_SOURCES[prec]:
+        with open(os.path.join(ROOT, "paper_1003_4322_gb300", "csrc", fn), "rb") as g:
+            h.update(g.read())
+    return h.hexdigest()
+
+
 def captured_traffic(workload, prec, kernel):
     """DRAM bytes per launch of a kernel from the committed ncu summary of this
-    workload, if the kernel sources are unchanged since the capture."""
-    import glob
-    import hashlib
+    workload, if that form's kernel sources are unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
-        t = json.load(f)
-    h = hashlib.sha256()
-    for fn in sorted(glob.glob(os.path.join(ROOT, "paper_1003_4322_gb300", "csrc", "*"))):
-        with open(fn, "rb") as g:
-            h.update(g.read())
-    if h.hexdigest() != t.get("source_sha256"):
+        t = json.load(f).get(prec, {})
+    if t.get("source_sha256") != source_hash(prec):
         return None
-    return t.get(prec, {}).get(kernel)
+    return t.get("kernels", {}).get(kernel)
 
 
 # FP64 FMA pipes: GB300 lists 1.25 TFLOP/s FP64 at its 2070 MHz maximum SM
@@ -264,12 +278,13 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
     total = sum(t for _, _, t in census)
     name, launches, tms = max(census, key=lambda r: r[2])
     per_launch_ms = tms / launches
-    # one launch covers every run of a group; launches per step = groups x passes
+    # fused form: one launch covers every run of a group (runs of equal N);
+    # plain form: one launch per run
     sizes = sizes or [w["n"]]
     per_size = [kernel_model(name, n, prec) for n in sizes]
-    groups = len(set(sizes))
-    bytes_ = sum(b for b, _ in per_size) / groups
-    flops = sum(f for _, f in per_size) / groups
+    launches_per_pass = len(sizes) if prec == "fp64" else len(set(sizes))
+    bytes_ = sum(b for b, _ in per_size) / launches_per_pass
+    flops = sum(f for _, f in per_size) / launches_per_pass
     gbs = bytes_ / (per_launch_ms * 1e-3) / 1e9
     hbm_frac = gbs / peaks["hbm_gbs"]
     roof = {"kernel": name, "launches_per_step": launches / census_steps,
@@ -326,9 +341,43 @@ def fft_stage(n, prec, reps=5):
     half = n * n * (n // 2 + 1) * 2 * es
     real = n ** 3 * es
     model = 3 * ((real + half) + 2 * half + 2 * half)   # z, y, x passes (read + write)
-    return {"n": n, "ncomp": 3, "prec": prec, "r2c_ms": r2c_ms, "c2r_ms": c2r_ms,
-            "r2c_gbs": model / (r2c_ms * 1e-3) / 1e9, "c2r_gbs": model / (c2r_ms * 1e-3) / 1e9,
-            "bytes_model": model}
+    out = {"n": n, "ncomp": 3, "prec": prec, "r2c_ms": r2c_ms, "c2r_ms": c2r_ms,
+           "r2c_gbs": model / (r2c_ms * 1e-3) / 1e9, "c2r_gbs": model / (c2r_ms * 1e-3) / 1e9,
+           "bytes_model": model}
+    out["cufft_reference"] = cufft_reference(u, uh, back, reps, model)
+    return out
+
+
+def cufft_reference(u, uh, back, reps, model):
+    """cuFFT (through torch.fft) on the same arrays, unnormalised both ways,
+    timed the same way: a reference point only, never on the product path."""
+    import torch
+    n = u.shape[-1]
+    dims = (-3, -2, -1)
+    ours = uh.clone()
+    ref_h = torch.empty_like(uh)
+    ref_b = torch.empty_like(back)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        torch.fft.rfftn(u, dim=dims, norm="backward", out=ref_h)
+        torch.fft.irfftn(ref_h, s=(n, n, n), dim=dims, norm="forward", out=ref_b)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    evs[0].record(stream)
+    for _ in range(reps):
+        torch.fft.rfftn(u, dim=dims, norm="backward", out=ref_h)
+    evs[1].record(stream)
+    for _ in range(reps):
+        torch.fft.irfftn(ref_h, s=(n, n, n), dim=dims, norm="forward", out=ref_b)
+    evs[2].record(stream)
+    torch.cuda.synchronize()
+    r2c = evs[0].elapsed_time(evs[1]) / reps
+    c2r = evs[1].elapsed_time(evs[2]) / reps
+    diff = float(torch.linalg.vector_norm(ours - ref_h) / torch.linalg.vector_norm(ref_h))
+    return {"library": "cuFFT via torch.fft.rfftn / irfftn", "r2c_ms": r2c, "c2r_ms": c2r,
+            "r2c_gbs_by_same_model": model / (r2c * 1e-3) / 1e9,
+            "c2r_gbs_by_same_model": model / (c2r * 1e-3) / 1e9,
+            "rel_diff_r2c_vs_ours": diff}
 
 
 def e2e(w, prec, mem, steps):

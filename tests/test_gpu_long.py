@@ -1,0 +1,47 @@
+"""Long parity runs, opt-in (NS_LONG_TESTS=1): the oracle needs minutes of
+host time for them.
+
+256^3 decaying Taylor-Green vortex (nu = 1/1600, dt = 2e-3), 200 RK2 steps
+of the plain FP64 GPU form against the FP64 CPU oracle (Sec. 2, Eqs. 1-2):
+relative L2 distance of the velocity on the 64^3 sub-lattice (every 4th grid
+point), of the spectral state, and of E and Omega after 50, 100, 150 and 200
+steps."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1003_4322_gb300 import inputs
+from tests.spectral_ref import rel_l2
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not os.environ.get("NS_LONG_TESTS"),
+                                 reason="long oracle run; set NS_LONG_TESTS=1")]
+
+
+def test_tg256_200_steps_against_oracle(ns):
+    from paper_1003_4322_gb300.solver import Solver
+    n, nu, dt = 256, 1 / 1600, 2e-3
+    oracle.set_threads(os.cpu_count() or 1)
+    p = oracle.Params(n=n, nu=nu, dt=dt)
+    a0 = inputs.taylor_green_state(n)
+    ref = a0
+    rows = []
+    with Solver([dict(n=n, nu=nu, dt=dt)], prec="fp64") as s:
+        s.set_state(a0)
+        for k in range(4):
+            s.step(50)
+            got = s.get_state()
+            ref = oracle.step(ref, p, 50)
+            ug = oracle.fft3_c2r(got)[:, ::4, ::4, ::4]
+            ur = oracle.fft3_c2r(ref)[:, ::4, ::4, ::4]
+            sub = math.sqrt(float(np.sum((ug - ur) ** 2)) / float(np.sum(ur ** 2)))
+            Eg, Og, _ = s.energy_spectrum()
+            Er, Or, _ = oracle.diagnostics(ref)
+            rows.append((50 * (k + 1), sub, rel_l2(got, ref), abs(Eg - Er) / Er, abs(Og - Or) / Or))
+    for step, sub, spec, dE, dO in rows:
+        print(f"step {step}: sub-lattice rel-L2 {sub:.3e}, spectral rel-L2 {spec:.3e}, "
+              f"dE/E {dE:.3e}, dOmega/Omega {dO:.3e}")
+        assert sub < 1e-12 and spec < 1e-12 and dE < 1e-12 and dO < 1e-12
