@@ -42,7 +42,8 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nu", ctypes.c_double),
                 ("dt", ctypes.c_double), ("force_amp", ctypes.c_double),
-                ("force_k", ctypes.c_int), ("dealias", ctypes.c_int)]
+                ("force_k", ctypes.c_int), ("dealias", ctypes.c_int),
+                ("rot", ctypes.c_double)]
 
 
 @dataclass
@@ -53,10 +54,11 @@ class Params:
     force_amp: float = 0.0
     force_k: int = 0
     dealias: int = 0
+    rot: float = 0.0
 
     def c(self) -> _Params:
         return _Params(self.n, self.nu, self.dt, self.force_amp,
-                       self.force_k, self.dealias)
+                       self.force_k, self.dealias, self.rot)
 
 
 _lib = None
@@ -140,7 +142,7 @@ def forcing(p: Params) -> np.ndarray:
 
 
 def nonlinear(a: np.ndarray, p: Params) -> np.ndarray:
-    """N(a) = P Pi FFT(u x w)/N^3 + f_hat."""
+    """N(a) = P Pi [FFT(u x w)/N^3 + 2 rot (a_y, -a_x, 0)] + f_hat."""
     a = np.ascontiguousarray(a, dtype=np.complex128)
     out = np.empty_like(a)
     cp = p.c()

@@ -32,6 +32,10 @@
  *   P           P(k) v = v - k (k.v)/|k|^2, and N(k=0) = 0;
  *   forcing     ABC: f = F (sin kf z + cos kf y, sin kf x + cos kf z,
  *               sin kf y + cos kf x), constant in time, added inside N;
+ *   rotation    frame rotating at rate rot about z (the rotating equations the
+ *               same code integrates, Sec. 5): the Coriolis force -2 rot z x u
+ *               = 2 rot (u_y, -u_x, 0) joins u x w before the projection,
+ *               N(a) = P Pi [FFT(u x w)/N^3 + 2 rot (a_y, -a_x, 0)] + f_hat;
  *   time step   integrating-factor Heun (RK2), E(k) = exp(-nu |k|^2 dt):
  *               a1 = E (a + dt N(a)),  a' = E a / 2 + (a1 + dt N(a1)) / 2;
  *   diagnostics E = 1/2 sum |a|^2, Omega = 1/2 sum |k|^2 |a|^2 over the full
@@ -62,13 +66,14 @@ typedef double complex cplx;
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_OOM = 3 };
 
 /* Same field list as the run parameters of the boundary (problem statement
- * of Sec. 2: N, nu, dt, forcing, dealiasing rule). */
+ * of Sec. 2: N, nu, dt, forcing, dealiasing rule; rotation rate, Sec. 5). */
 typedef struct {
     int n;
     double nu, dt;
     double force_amp;
     int force_k;
     int dealias;
+    double rot;
 } or_params;
 
 static const double OR_TWO_PI = 6.283185307179586476925286766559;
@@ -371,6 +376,10 @@ int or_nonlinear(const or_params *p, const cplx *a_in, cplx *out)
     }
     if ((e = or_fft3_r2c(n, 3, c, out))) goto done;
     for (long i = 0; i < 3 * M; i++) out[i] /= (double)V;
+    for (long i = 0; i < M; i++) {                   /* Coriolis -2 rot z x u */
+        out[i] += 2.0 * p->rot * a[M + i];
+        out[M + i] -= 2.0 * p->rot * a[i];
+    }
     if ((e = or_project(n, p->dealias, out))) goto done;   /* Pi, then P */
     if ((e = or_forcing(p, fh))) goto done;
     for (long i = 0; i < 3 * M; i++) out[i] += fh[i];

@@ -111,3 +111,17 @@ def rel_l2(test: np.ndarray, ref: np.ndarray) -> float:
     num = np.sum(w * np.abs(test - ref) ** 2)
     den = np.sum(w * np.abs(ref) ** 2)
     return math.sqrt(num / den)
+
+
+def helical_mode(n, k, s, amp=0.3):
+    """Half-layout state with one helical mode at wavevector k (kz > 0): the
+    eigenvector of the curl symbol i k x with eigenvalue s |k|, found by
+    numpy's eig, so that w = s |k| u and u x w vanishes."""
+    kv = np.array(k, dtype=float)
+    cross = np.array([[0.0, -kv[2], kv[1]], [kv[2], 0.0, -kv[0]], [-kv[1], kv[0], 0.0]])
+    w, V = np.linalg.eig(1j * cross)
+    h = V[:, np.argmin(abs(w - s * np.linalg.norm(kv)))]
+    h = h / np.linalg.norm(h)
+    a = np.zeros((3, n, n, n // 2 + 1), dtype=np.complex128)
+    a[:, k[0] % n, k[1] % n, k[2]] = amp * h
+    return a

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from paper_1003_4322_gb300 import inputs
-from tests.spectral_ref import rel_l2, triad_nonlinear
+from tests.spectral_ref import helical_mode, rel_l2, triad_nonlinear
 
 SRC = open(os.path.join(os.path.dirname(oracle.__file__), "ns_oracle.c")).read()
 
@@ -48,6 +48,18 @@ MUTATIONS = {
         ("double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;", "double w = 2.0;"),
     "shell binning by truncation":
         ("long K = (long)floor(sqrt(k2) + 0.5);", "long K = (long)floor(sqrt(k2));"),
+    "Coriolis sign of one component":
+        ("out[i] += 2.0 * p->rot * a[M + i];", "out[i] -= 2.0 * p->rot * a[M + i];"),
+    "Coriolis without the factor 2":
+        ("out[i] += 2.0 * p->rot * a[M + i];\n        out[M + i] -= 2.0 * p->rot * a[i];",
+         "out[i] += p->rot * a[M + i];\n        out[M + i] -= p->rot * a[i];"),
+    "Coriolis added after the projection":
+        ("    if ((e = or_project(n, p->dealias, out))) goto done;   /* Pi, then P */\n",
+         "    for (long i = 0; i < M; i++) {\n        out[i] -= 2.0 * p->rot * a[M + i];\n"
+         "        out[M + i] += 2.0 * p->rot * a[i];\n    }\n"
+         "    if ((e = or_project(n, p->dealias, out))) goto done;\n"
+         "    for (long i = 0; i < M; i++) {\n        out[i] += 2.0 * p->rot * a[M + i];\n"
+         "        out[M + i] -= 2.0 * p->rot * a[i];\n    }\n"),
 }
 
 
@@ -89,6 +101,19 @@ def _pins():
         failed.append("shell")
     if abs(oracle.diagnostics(inputs.taylor_green_state(8))[2][2] - 0.125) > 1e-15:
         failed.append("shell-round")     # |k| = sqrt3 rounds to shell 2
+    # rotation: one helical mode is an inertial wave of frequency 2 rot kz/|k|
+    h = helical_mode(8, (1, 1, 2), 1)
+    z = 2j * 2.0 * 2 / math.sqrt(6) * 0.02
+    g = math.exp(-0.01 * 6 * 0.02) * (1 + z + z * z / 2)
+    if np.abs(oracle.step(h, oracle.Params(n=8, nu=0.01, dt=0.02, rot=2.0), 5) - h * g ** 5).max() > 1e-14:
+        failed.append("inertial")
+    # rotation leaves z-independent flows alone (Taylor-Proudman)
+    q = inputs.random_solenoidal_state(8, 1.0, 3.0, 0.5, seed=5)
+    q[..., 1:] = 0.0
+    q0 = oracle.step(q, oracle.Params(n=8, nu=0.01, dt=0.02), 3)
+    q1 = oracle.step(q, oracle.Params(n=8, nu=0.01, dt=0.02, rot=3.0), 3)
+    if np.abs(q1 - q0).max() > 1e-13 * np.abs(q0).max():
+        failed.append("taylor-proudman")
     return failed
 
 

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_1003_4322_gb300 import inputs
-from tests.spectral_ref import (energy_half, half_to_full, kept_modes, rel_l2,
+from tests.spectral_ref import (energy_half, half_to_full, helical_mode, kept_modes, rel_l2,
                                 triad_nonlinear, wavenumbers)
 
 
@@ -259,3 +259,47 @@ def test_helicity_matches_grid_average():
     b = np.conj(a) * -1.0   # coefficients of -u(-x)
     Hb, _ = oracle.helicity(b)
     assert abs(Hb + H) < 1e-14
+
+
+@pytest.mark.parametrize("k", [(2, 1, 3), (1, -2, 1), (-3, 0, 2)])
+@pytest.mark.parametrize("s", [1, -1])
+def test_rotation_inertial_wave_is_exact(k, s):
+    """A single helical mode in a frame rotating about z is an inertial wave
+    (Sec. 5 lists rotation among the equations of the same code): u x w = 0,
+    and the projected Coriolis force turns the mode at the inertial frequency
+    2 rot kz/|k|, positive sense for positive helicity.  The nonlinear term
+    is then linear, N = lam a with lam = 2 i s rot kz/|k|, and IF-Heun
+    multiplies the mode by exp(-nu k^2 dt) (1 + z + z^2/2), z = lam dt, per
+    step exactly."""
+    n, nu, dt, rot, steps = 16, 0.01, 0.01, 2.5, 20
+    a0 = helical_mode(n, k, s)
+    kk = np.linalg.norm(k)
+    z = 2j * s * rot * k[2] / kk * dt
+    g = np.exp(-nu * kk ** 2 * dt) * (1 + z + z * z / 2)
+    b = oracle.step(a0, oracle.Params(n=n, nu=nu, dt=dt, rot=rot), steps)
+    assert np.abs(b - a0 * g ** steps).max() < 1e-14
+    # and the continuous solution a0 exp((lam - nu k^2) t) to second order in dt
+    lam = 2j * s * rot * k[2] / kk
+    T = 0.2
+    errs = []
+    for m in (20, 40):
+        b = oracle.step(a0, oracle.Params(n=n, nu=nu, dt=T / m, rot=rot), m)
+        errs.append(np.abs(b - a0 * np.exp((lam - nu * kk ** 2) * T)).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_rotation_leaves_z_independent_flows_alone():
+    """Taylor-Proudman: for kz = 0 the projected Coriolis force vanishes
+    (z x u is a gradient there), so a z-independent flow evolves the same
+    with and without rotation."""
+    n = 16
+    a = inputs.random_solenoidal_state(n, lo=1, hi=5, rms=0.5, seed=21, dealias=0)
+    a[..., 1:] = 0.0
+    b0 = oracle.step(a, oracle.Params(n=n, nu=0.01, dt=0.01), 5)
+    b1 = oracle.step(a, oracle.Params(n=n, nu=0.01, dt=0.01, rot=4.0), 5)
+    assert np.abs(b1 - b0).max() < 1e-13 * np.abs(b0).max()
+    # while a 3D flow does feel it
+    c = inputs.random_solenoidal_state(n, lo=1, hi=5, rms=0.5, seed=21, dealias=0)
+    d0 = oracle.step(c, oracle.Params(n=n, nu=0.01, dt=0.01), 5)
+    d1 = oracle.step(c, oracle.Params(n=n, nu=0.01, dt=0.01, rot=4.0), 5)
+    assert np.abs(d1 - d0).max() > 1e-3 * np.abs(d0).max()
