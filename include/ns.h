@@ -81,6 +81,10 @@ typedef struct {
     double force_amp;  /* ABC forcing amplitude F (0 = unforced) */
     int force_k;       /* ABC forcing wavenumber kf (0 = unforced) */
     int dealias;       /* 0 = cubic 2/3 rule, 1 = spherical 2/3 rule */
+    double rot;        /* rotation rate about z (0 = inertial frame): the
+                          Coriolis force -2 rot z x u of the rotating
+                          equations (Sec. 5) joins u x w before the
+                          projection; any finite value */
 } ns_run_params;
 
 /* Create a context for nruns independent runs (an ensemble when nruns > 1;

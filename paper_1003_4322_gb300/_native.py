@@ -36,7 +36,7 @@ class NsError(RuntimeError):
 class ns_run_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nu", ctypes.c_double), ("dt", ctypes.c_double),
                 ("force_amp", ctypes.c_double), ("force_k", ctypes.c_int),
-                ("dealias", ctypes.c_int)]
+                ("dealias", ctypes.c_int), ("rot", ctypes.c_double)]
 
 
 class ns_kernel_time(ctypes.Structure):
@@ -130,7 +130,7 @@ def ns_init(runs, prec: int, stream=None):
         else:
             arr[i] = ns_run_params(int(r["n"]), float(r.get("nu", 0.0)), float(r["dt"]),
                                    float(r.get("force_amp", 0.0)), int(r.get("force_k", 0)),
-                                   int(r.get("dealias", 0)))
+                                   int(r.get("dealias", 0)), float(r.get("rot", 0.0)))
     if stream is None:
         s = None
     elif hasattr(stream, "cuda_stream"):

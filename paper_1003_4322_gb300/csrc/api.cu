@@ -300,7 +300,7 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
         NS_CK(c2r_batch<T>((C *)r.wn, (C *)r.work, phys + 3 * r.V, r.n, 3, *f, ct, s, tr));
         NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, r.n, s)));
         NS_CK(r2c_batch<T>(phys, (C *)r.wn, r.n, 3, *f, ct, s, tr));
-        UpdateArgs ua{stage, r.p.dt, r.p.force_amp, r.p.force_k, r.p.dealias};
+        UpdateArgs ua{stage, r.p.dt, r.p.force_amp, r.p.force_k, r.p.dealias, r.p.rot};
         NS_CK(NSK_TIMED(tr, "update",
                         plain_update<T>((C *)r.un, (C *)r.u1, (const C *)r.wn, (const T *)r.etab, r.n, ua, s)));
     }
@@ -432,7 +432,8 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
     for (int i = 0; i < nruns; i++) {
         const ns_run_params &p = runs[i];
         if (!(p.nu >= 0.0) || !(p.dt > 0.0) || (p.dealias != 0 && p.dealias != 1) ||
-            p.force_k < 0 || !isfinite(p.force_amp) || !isfinite(p.nu) || !isfinite(p.dt))
+            p.force_k < 0 || !isfinite(p.force_amp) || !isfinite(p.nu) || !isfinite(p.dt) ||
+            !isfinite(p.rot))
             return NS_ERR_ARG;
         if (!supported_n(p.n) || p.n > (prec == NS_FP32 ? 1024 : 768)) return NS_ERR_UNSUPPORTED_N;
     }

@@ -239,6 +239,12 @@ __device__ __forceinline__ FzMode fz_update_mode(long m, const FzUpdate &u, cons
         vx = cscale(vx, inv);
         vy = cscale(vy, inv);
         vz = cscale(vz, inv);
+        if (q.rot != 0.f) {   // Coriolis -2 rot z x u of the stage's state, before P
+            const float r2 = 2.f * q.rot;
+            const float2 cx = u.stage == 1 ? b0 : c0, cy = u.stage == 1 ? b1 : c1;
+            vx = cadd(vx, cscale(cy, r2));
+            vy = csub(vy, cscale(cx, r2));
+        }
         const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz, ik2 = 1.f / (float)r.k2;
         const float2 kv = cadd(cadd(cscale(vx, fkx), cscale(vy, fky)), cscale(vz, fkz));
         vx = csub(vx, cscale(kv, fkx * ik2));
@@ -914,7 +920,7 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     for (long r = 0; r < nr; r++) {
         const ns_run_params &q = runs[r];
         for (int k2 = 0; k2 < f.nk2; k2++) h[r * f.nk2 + k2] = (float)exp(-q.nu * (double)k2 * q.dt);
-        hp[r] = FzRunParams{(float)q.dt, (float)q.force_amp, q.force_k, q.dealias};
+        hp[r] = FzRunParams{(float)q.dt, (float)q.force_amp, q.force_k, q.dealias, (float)q.rot};
     }
     if ((e = cudaMalloc(&f.etab, h.size() * sizeof(float))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(f.etab, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)

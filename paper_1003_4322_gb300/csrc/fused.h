@@ -59,6 +59,7 @@ bool std_c2r_fp32(const float2 *in, float2 *tmp, float *out, int N, const float2
 struct FzRunParams {
     float dt, force_amp;
     int force_k, dealias;
+    float rot;   // rotation rate about z (Coriolis -2 rot z x u)
 };
 
 // A group of nr runs of the fused form that share the grid size N; their

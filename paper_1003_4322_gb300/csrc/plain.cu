@@ -96,6 +96,12 @@ __global__ void k_update(typename Cx<T>::type *__restrict__ a, typename Cx<T>::t
         C o0 = czero<C>(), o1 = czero<C>(), o2 = czero<C>();
         if (kept(kx, ky, kz, n, ua.dealias) && k2 > 0) {
             C vx = cscale(nl[m], inv), vy = cscale(nl[M + m], inv), vz = cscale(nl[2 * M + m], inv);
+            if (ua.rot != 0.0) {   // Coriolis -2 rot z x u of the stage's state, before P
+                const C *cur = ua.stage == 1 ? a : a1;
+                const T r2 = (T)(2.0 * ua.rot);
+                vx = cadd(vx, cscale(cur[M + m], r2));
+                vy = csub(vy, cscale(cur[m], r2));
+            }
             const T fkx = (T)kx, fky = (T)ky, fkz = (T)kz, ik2 = (T)1 / (T)k2;
             const C kv = cadd(cadd(cscale(vx, fkx), cscale(vy, fky)), cscale(vz, fkz));
             vx = csub(vx, cscale(kv, fkx * ik2));

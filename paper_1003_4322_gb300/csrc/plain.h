@@ -10,6 +10,7 @@ struct UpdateArgs {
     double force_amp;
     int force_k;
     int dealias;
+    double rot;       // rotation rate about z (Coriolis -2 rot z x u)
 };
 
 template <typename T>

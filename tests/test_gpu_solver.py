@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_1003_4322_gb300 import inputs
-from tests.spectral_ref import rel_l2, wavenumbers
+from tests.spectral_ref import helical_mode, rel_l2, wavenumbers
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +25,8 @@ def _oracle_run(a0, run, steps):
     return oracle.step(a0, oracle.Params(n=run["n"], nu=run.get("nu", 0.0), dt=run["dt"],
                                          force_amp=run.get("force_amp", 0.0),
                                          force_k=run.get("force_k", 0),
-                                         dealias=run.get("dealias", 0)), steps)
+                                         dealias=run.get("dealias", 0),
+                                         rot=run.get("rot", 0.0)), steps)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -255,3 +256,53 @@ def test_fused_series_accumulation_is_fp64_quality(ns, n):
     if st is not None:
         rE, rO, _ = oracle.diagnostics(st)
         assert abs(Es[-1] - rE) < 1e-12 * rE and abs(Os[-1] - rO) < 1e-12 * rO
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [32, 48])
+def test_rotating_turbulence_matches_oracle(ns, prec, n):
+    """Forced turbulence in a frame rotating about z (Coriolis -2 rot z x u
+    inside the projected nonlinear term), both forms against the oracle."""
+    run = dict(n=n, nu=0.01, dt=1e-3, force_amp=0.5, force_k=3, rot=3.0)
+    a0 = inputs.turbulence_state(n, seed=17)
+    ref = _oracle_run(a0, run, 4)
+    with _solver(ns, prec, **run) as s:
+        s.set_state(a0)
+        s.step(4)
+        got = s.get_state()
+    assert rel_l2(got, ref) < TOL[prec]
+    assert rel_l2(ref, _oracle_run(a0, dict(run, rot=0.0), 4)) > 100 * TOL["fp32"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_inertial_wave_exact_on_gpu(ns, prec):
+    """One helical mode turns at the inertial frequency 2 rot kz/|k| with the
+    exact discrete IF-Heun amplification (the oracle's pin, on the GPU)."""
+    n, nu, dt, rot, steps = 32, 0.01, 0.01, 2.5, 20
+    k = (2, 1, 3)
+    a0 = helical_mode(n, k, 1)
+    kk = np.linalg.norm(k)
+    z = 2j * rot * k[2] / kk * dt
+    g = np.exp(-nu * kk ** 2 * dt) * (1 + z + z * z / 2)
+    with _solver(ns, prec, n=n, nu=nu, dt=dt, rot=rot) as s:
+        s.set_state(a0)
+        s.step(steps)
+        got = s.get_state()
+    want = a0 * g ** steps
+    assert np.abs(got - want).max() < (1e-14 if prec == "fp64" else 1e-6)
+
+
+def test_rotation_is_per_run_in_a_group(ns):
+    """Two runs of one size in one fused group, rotating and not: one launch
+    per pass advances both, each with its own rotation rate."""
+    from paper_1003_4322_gb300.solver import Solver
+    n = 32
+    runs = [dict(n=n, nu=0.01, dt=1e-3, rot=4.0), dict(n=n, nu=0.01, dt=1e-3)]
+    a0 = inputs.turbulence_state(n, seed=23)
+    with Solver(runs, prec="fp32") as s:
+        for r in range(2):
+            s.set_state(a0, run=r)
+        s.step(3)
+        got = [s.get_state(run=r) for r in range(2)]
+    for r in range(2):
+        assert rel_l2(got[r], _oracle_run(a0, runs[r], 3)) < TOL["fp32"]
