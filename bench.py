@@ -164,6 +164,8 @@ def kernel_model(name, n, prec):
         return (3 * Ax + 3 * S) * cb, 3 * Mx * Mz * f_line
     if name == "fused_update":
         return 10.5 * S * cb, 3 * S * 30   # reads N, a (and a1 at stage 2), writes 3
+    if name == "fused_E_x_forward_update":   # reads D, a (and a1 at stage 2), writes 3
+        return (3 * Ax + 7.5 * S) * cb, 3 * Mx * Mz * f_line + 3 * S * 30
     return 0, 0
 
 

@@ -268,4 +268,59 @@ NSK_DEV void ct_fft_block(int slot, const float2 *__restrict__ tw, GL gl, SL sl,
     }
 }
 
+// As ct_fft_block, but the last stage leaves the line in v instead of storing
+// it: v[j] holds position slot + j T (T = n/E) afterwards, the same positions
+// whatever the plan (the last stage's butterfly b writes output q at
+// slot + T (b + q E/R)).  The caller separates two calls that share the
+// shared-memory tile with a block barrier.
+template <int n, int E, int DIR, int NTAB, int S = 0, class GL, class SL, class SS>
+NSK_DEV void ct_fft_block_reg(float2 (&v)[E], int slot, const float2 *__restrict__ tw, GL gl, SL sl,
+                              SS ss) {
+    constexpr int NST = ct_nst(n, E);
+    constexpr int R = ct_radix(n, E, S), p = ct_span(n, E, S), T = n / E, nR = n / R;
+    constexpr bool first = S == 0, last = S == NST - 1;
+#pragma unroll
+    for (int b = 0; b < E / R; b++) {
+        const int i = slot + b * T;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            if constexpr (first) v[b * R + q] = gl(i + q * nR);
+            else v[b * R + q] = sl(i + q * nR);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < E / R; b++) {
+        if constexpr (p > 1) {
+            const int k = (slot + b * T) % p;
+#pragma unroll
+            for (int q = 1; q < R; q++) {
+                const float2 w = __ldg(tw + q * k * (NTAB / (p * R)));
+                v[b * R + q] = DIR < 0 ? cmul(v[b * R + q], w) : cmulc(v[b * R + q], w);
+            }
+        }
+        Dft<R, DIR, float2>::run(&v[b * R]);
+    }
+    if constexpr (!last) {
+        if constexpr (!first) __syncthreads();
+#pragma unroll
+        for (int b = 0; b < E / R; b++) {
+            const int i = slot + b * T;
+            const int k = i % p;
+            const int j = (i - k) * R + k;
+#pragma unroll
+            for (int q = 0; q < R; q++) ss(j + q * p, v[b * R + q]);
+        }
+        __syncthreads();
+        ct_fft_block_reg<n, E, DIR, NTAB, S + 1>(v, slot, tw, gl, sl, ss);
+    } else {
+        float2 t[E];
+#pragma unroll
+        for (int b = 0; b < E / R; b++)
+#pragma unroll
+            for (int q = 0; q < R; q++) t[b + q * (E / R)] = v[b * R + q];
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = t[j];
+    }
+}
+
 }  // namespace nsk

@@ -95,8 +95,14 @@ cudaError_t allow_smem(const void *kernel, size_t bytes) {
     int maxopt = 0;
     e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    if (bytes > (size_t)maxopt) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt);
+    // the opt-in maximum covers static and dynamic shared memory together
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if (fa.sharedSizeBytes >= (size_t)maxopt) return cudaErrorInvalidValue;
+    const int maxdyn = maxopt - (int)fa.sharedSizeBytes;
+    if (bytes > (size_t)maxdyn) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn);
     if (e == cudaSuccess) done.insert(key);
     return e;
 }

@@ -28,6 +28,7 @@
 
 #include "fused.h"
 #include "fused_k.cuh"
+#include "fused_update.cuh"
 #include "plain.h"
 #include "fused_access.cuh"
 #include "reduce.cuh"
@@ -146,126 +147,6 @@ k_fused_z(float2 *buf, long fs, int N, int Mz, long nlines, int L, long brun, Pl
     }
 }
 
-// 1/N^3, projection, forcing and the RK2 stage on the compact state; at
-// stage 2 also the per-block energy and enstrophy partial sums of the new
-// state, FP64 quality (grid-stride with a fixed grid: deterministic).  Grid y is the
-// run of the group; each run has its own parameters and factor table.
-struct FzUpdate {
-    int n, K, Mx, Mz;
-    int stage;
-    long M;          // compact modes per component
-    int nk2;         // entries of one run's factor table
-    int nparts;      // partial sums per run
-};
-
-__device__ __forceinline__ void fz_forcing(int kx, int ky, int kz, int kf, float F, float2 &fx,
-                                           float2 &fy, float2 &fz) {
-    const float h = 0.5f * F;
-    if (kf <= 0) return;
-    if (kx == 0 && ky == 0 && kz == kf) {
-        fx = cadd(fx, make_float2(0.f, -h));
-        fy = cadd(fy, make_float2(h, 0.f));
-    }
-    if (kx == 0 && kz == 0 && (ky == kf || ky == -kf)) {
-        fx = cadd(fx, make_float2(h, 0.f));
-        fz = cadd(fz, make_float2(0.f, ky > 0 ? -h : h));
-    }
-    if (ky == 0 && kz == 0 && (kx == kf || kx == -kf)) {
-        fy = cadd(fy, make_float2(0.f, kx > 0 ? -h : h));
-        fz = cadd(fz, make_float2(h, 0.f));
-    }
-}
-
-// Compensated FP32 accumulator (value hi + lo) for the energy partials of
-// the update.  A square of an FP32 value splits exactly into p + e with
-// e = fma(x, x, -p), each addition keeps its rounding error (Knuth's TwoSum)
-// and the pair is renormalised once per mode (Dekker's Fast2Sum), so a
-// thread's few hundred terms sum to within a few units of 2^-48 relative --
-// FP64-quality accumulation without FP64 instructions, which this GPU issues
-// at 1/64 of the FP32 rate.  Block and final sums are FP64.
-// The _rn intrinsics keep each rounding where it is written (no contraction
-// into FMA), which the error terms rely on.
-struct DfAcc {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add(float b) {
-        const float s = __fadd_rn(hi, b), bb = __fsub_rn(s, hi);
-        lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-        hi = s;
-    }
-    __device__ __forceinline__ void add_sq(float x) {
-        const float p = __fmul_rn(x, x);
-        add(p);
-        lo += fmaf(x, x, -p);
-    }
-    __device__ __forceinline__ void renorm() {
-        const float s = __fadd_rn(hi, lo);
-        lo = __fsub_rn(lo, __fsub_rn(s, hi));
-        hi = s;
-    }
-    // += c * v for an exactly representable weight c (c * v.hi split exactly)
-    __device__ __forceinline__ void add_scaled(const DfAcc &v, float c) {
-        const float q = __fmul_rn(c, v.hi);
-        add(q);
-        lo += fmaf(c, v.hi, -q) + c * v.lo;
-        renorm();
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
-// One mode of the update: N = P Pi (transform of u x w)/N^3 + f, then the
-// IF-RK2 stage, from operands already loaded (b = a, c = a1, v = nl).
-struct FzMode {
-    float2 o0, o1, o2;
-    int k2, kz;
-};
-
-__device__ __forceinline__ FzMode fz_update_mode(long m, const FzUpdate &u, const FzRunParams &q,
-                                                 const float *__restrict__ etab, float inv, float2 vx,
-                                                 float2 vy, float2 vz, float2 b0, float2 b1, float2 b2,
-                                                 float2 c0, float2 c1, float2 c2) {
-    const unsigned Mz = (unsigned)u.Mz, Mx = (unsigned)u.Mx;   // M < 2^31 for every supported N
-    const unsigned row = (unsigned)m / Mz;
-    FzMode r;
-    r.kz = (int)((unsigned)m - row * Mz);
-    const int iky = (int)(row % Mx);
-    const int ikx = (int)(row / Mx);
-    const int kx = fz_compact_signed(ikx, u.Mx, u.K), ky = fz_compact_signed(iky, u.Mx, u.K);
-    const int kz = r.kz;
-    r.k2 = kx * kx + ky * ky + kz * kz;
-    bool keep = r.k2 > 0;
-    if (q.dealias == 1 && 9L * r.k2 >= (long)u.n * u.n) keep = false;
-    r.o0 = r.o1 = r.o2 = make_float2(0.f, 0.f);
-    if (keep) {
-        vx = cscale(vx, inv);
-        vy = cscale(vy, inv);
-        vz = cscale(vz, inv);
-        if (q.rot != 0.f) {   // Coriolis -2 rot z x u of the stage's state, before P
-            const float r2 = 2.f * q.rot;
-            const float2 cx = u.stage == 1 ? b0 : c0, cy = u.stage == 1 ? b1 : c1;
-            vx = cadd(vx, cscale(cy, r2));
-            vy = csub(vy, cscale(cx, r2));
-        }
-        const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz, ik2 = 1.f / (float)r.k2;
-        const float2 kv = cadd(cadd(cscale(vx, fkx), cscale(vy, fky)), cscale(vz, fkz));
-        vx = csub(vx, cscale(kv, fkx * ik2));
-        vy = csub(vy, cscale(kv, fky * ik2));
-        vz = csub(vz, cscale(kv, fkz * ik2));
-        fz_forcing(kx, ky, kz, q.force_k, q.force_amp, vx, vy, vz);
-        const float e = etab[r.k2];
-        if (u.stage == 1) {
-            r.o0 = cscale(cadd(b0, cscale(vx, q.dt)), e);
-            r.o1 = cscale(cadd(b1, cscale(vy, q.dt)), e);
-            r.o2 = cscale(cadd(b2, cscale(vz, q.dt)), e);
-        } else {
-            const float he = 0.5f * e;
-            r.o0 = cadd(cscale(b0, he), cscale(cadd(c0, cscale(vx, q.dt)), 0.5f));
-            r.o1 = cadd(cscale(b1, he), cscale(cadd(c1, cscale(vy, q.dt)), 0.5f));
-            r.o2 = cadd(cscale(b2, he), cscale(cadd(c2, cscale(vz, q.dt)), 0.5f));
-        }
-    }
-    return r;
-}
-
 // Two modes per thread and iteration, every operand load issued before any
 // arithmetic, so that enough bytes are in flight to stream HBM.
 __global__ void __launch_bounds__(256)
@@ -310,19 +191,7 @@ k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__
             dst[m] = r.o0;
             dst[M + m] = r.o1;
             dst[2 * M + m] = r.o2;
-            if (two) {
-                DfAcc me;   // |a(k)|^2 of this mode, exact up to the pair's rounding
-                me.add_sq(r.o0.x);
-                me.add_sq(r.o0.y);
-                me.add_sq(r.o1.x);
-                me.add_sq(r.o1.y);
-                me.add_sq(r.o2.x);
-                me.add_sq(r.o2.y);
-                me.renorm();
-                const float w = r.kz == 0 ? 0.5f : 1.0f;   // half-layout weight / 2
-                e_acc.add_scaled(me, w);
-                o_acc.add_scaled(me, w * (float)r.k2);   // k2 <= 3 K^2 < 2^24: exact
-            }
+            if (two) fz_accumulate(r, e_acc, o_acc);
         }
     }
     if (two) {
@@ -526,9 +395,9 @@ cudaError_t prepare_fused_kernels() {
                         if (e != cudaSuccess) return e;
                     }
                 }
-                for (int pass = 0; pass < 4; pass++) {
+                for (int pass = 0; pass < 5; pass++) {
                     FzsKernel z;
-                    if (fzk_lookup(pass, N, E, ct, &z)) {
+                    if (pass < 4 ? fzk_lookup(pass, N, E, ct, &z) : fzeu_lookup(N, E, ct, &z)) {
                         cudaError_t e = allow_smem(z.k, 48 * 1024 + 1);
                         if (e != cudaSuccess) return e;
                     }
@@ -672,6 +541,34 @@ static cudaError_t run_pass(FusedRun &f, int pass, const PassCfg &cfg, const FzP
     return launch_strided(k, ps, cfg.pl, f.tw, cfg.ct, f.nr, s);
 }
 
+// The separate update kernel, u.nparts blocks (partials) per run.
+static cudaError_t launch_update_n(FusedRun &f, const FzUpdate &u, cudaStream_t s) {
+    k_fused_update<<<dim3(u.nparts, f.nr), 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, f.rp, u, f.part);
+    return cudaGetLastError();
+}
+
+// Column tiles (and energy partials per run) of pass E fused with the update.
+static long eu_tiles(const FusedRun &f, int ct) { return ((long)f.Mx * f.Mz + ct - 1) / ct; }
+
+// Pass E fused with the update at RK2 stage `stage`: reads pass D's output,
+// updates the state in place (a1 at stage 1, a at stage 2).
+static cudaError_t launch_eu(FusedRun &f, int E, int ct, int stage, cudaStream_t s) {
+    FzsKernel z;
+    if (!fzeu_lookup(f.n, E, ct, &z)) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(z.k, z.smem);
+    if (e != cudaSuccess) return e;
+    const long tiles = eu_tiles(f, ct);
+    FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.M, f.nk2, (int)tiles};
+    const float2 *din = f.abuf, *tw = f.tw;
+    float2 *a = f.a, *a1 = f.a1;
+    const float *etab = f.etab;
+    const FzRunParams *rp = f.rp;
+    double *part = f.part;
+    void *args[] = {(void *)&din, (void *)&a, (void *)&a1, (void *)&etab, (void *)&rp,
+                    (void *)&u, (void *)&tw, (void *)&part};
+    return cudaLaunchKernel(z.k, dim3((unsigned)tiles, (unsigned)f.nr), dim3(z.threads), args, z.smem, s);
+}
+
 // ---------------------------------------------------------------- autotuner
 
 // Candidate radix splits (elements per thread) for a line of length n.
@@ -688,6 +585,7 @@ static std::vector<Plan> plan_candidates(int n) {
 struct TunedCfgs {
     PassCfg s[4];   // A, B, D, E
     PassCfg c;      // pass C (ct = lines per CTA)
+    int eu_E = 0, eu_ct = 0;   // pass E fused with the update, 0: separate
 };
 
 // Time `launch` (after one warm-up) over `reps` launches; returns ms per launch
@@ -743,14 +641,27 @@ static void plan_cache_read(std::map<int, TunedCfgs> &cache) {
     fclose(fp);
     size_t pos = 0;
     while ((pos = txt.find('"', pos)) != std::string::npos) {
-        int n = 0, v[15], used = 0;
-        if (sscanf(txt.c_str() + pos, "\"%d\": [[%d, %d, %d], [%d, %d, %d], [%d, %d, %d], [%d, %d, %d], [%d, %d, %d]]%n",
-                   &n, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &v[10],
-                   &v[11], &v[12], &v[13], &v[14], &used) == 16 && used > 0) {
+        int n = 0, v[18] = {0}, used = 0;
+        const char *at = txt.c_str() + pos;
+        bool six = sscanf(at, "\"%d\": [[%d, %d, %d], [%d, %d, %d], [%d, %d, %d], [%d, %d, %d], [%d, %d, %d], [%d, %d, %d]]%n",
+                          &n, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &v[10],
+                          &v[11], &v[12], &v[13], &v[14], &v[15], &v[16], &v[17], &used) == 19 && used > 0;
+        if (!six) {
+            used = 0;
+            v[15] = v[16] = v[17] = 0;
+        }
+        if (six || (sscanf(at, "\"%d\": [[%d, %d, %d], [%d, %d, %d], [%d, %d, %d], [%d, %d, %d], [%d, %d, %d]]%n",
+                           &n, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &v[10],
+                           &v[11], &v[12], &v[13], &v[14], &used) == 16 && used > 0)) {
             TunedCfgs t;
             bool ok = true;
             for (int i = 0; i < 4 && ok; i++) ok = cfg_from_triple(n, v[3 * i], v[3 * i + 1], v[3 * i + 2], false, t.s[i]);
             ok = ok && cfg_from_triple(n, v[12], v[13], v[14], true, t.c);
+            FzsKernel z;
+            if (v[15] == 3 && fzeu_lookup(n, v[16], v[17], &z)) {
+                t.eu_E = v[16];
+                t.eu_ct = v[17];
+            }
             if (ok) cache[n] = t;
             pos += used;
         } else {
@@ -771,7 +682,8 @@ static void plan_cache_write(const std::map<int, TunedCfgs> &cache) {
         fprintf(fp, "%s\n  \"%d\": [", first ? "" : ",", kv.first);
         for (int i = 0; i < 4; i++)
             fprintf(fp, "[%d, %d, %d], ", t.s[i].kind, t.s[i].pl.E, t.s[i].ct);
-        fprintf(fp, "[%d, %d, %d]]", t.c.kind, t.c.pl.E, t.c.ct);
+        fprintf(fp, "[%d, %d, %d], [%d, %d, %d]]", t.c.kind, t.c.pl.E, t.c.ct, t.eu_E ? 3 : 0, t.eu_E,
+                t.eu_ct);
         first = false;
     }
     fprintf(fp, "\n}\n");
@@ -796,6 +708,8 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
         if (it != cache.end()) {
             for (int i = 0; i < 4; i++) f.sp[i] = it->second.s[i];
             f.zc = it->second.c;
+            f.eu_E = it->second.eu_E;
+            f.eu_ct = it->second.eu_ct;
             return cudaSuccess;
         }
     }
@@ -878,10 +792,32 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
         }
         if (best < 0.f) return cudaErrorInvalidValue;
     }
+    // pass E then the update, against pass E fused with the update (stage 2)
+    {
+        FzUpdate u{f.n, f.K, f.Mx, f.Mz, 2, f.M, f.nk2, f.nparts_upd};
+        const float sep = time_launch([&]() { return run_pass(f, 3, f.sp[3], P[3], s); }, s, reps) +
+                          time_launch([&]() { return launch_update_n(f, u, s); }, s, reps);
+        float best = sep > 0.f ? sep : -1.f;
+        f.eu_E = f.eu_ct = 0;
+        const int Es[] = {8, 12, 16, 32};
+        for (int E : Es)
+            for (int ct = 8; ct <= 16; ct *= 2) {
+                FzsKernel z;
+                if (!fzeu_lookup(f.n, E, ct, &z)) continue;
+                const float ms = time_launch([&]() { return launch_eu(f, E, ct, 2, s); }, s, reps);
+                if (ms > 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    f.eu_E = E;
+                    f.eu_ct = ct;
+                }
+            }
+    }
     std::lock_guard<std::mutex> g(mu);
     TunedCfgs t;
     for (int i = 0; i < 4; i++) t.s[i] = f.sp[i];
     t.c = f.zc;
+    t.eu_E = f.eu_E;
+    t.eu_ct = f.eu_ct;
     cache[f.n] = t;
     plan_cache_write(cache);
     return cudaSuccess;
@@ -928,8 +864,12 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     if ((e = cudaMalloc(&f.rp, nr * sizeof(FzRunParams))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(f.rp, hp.data(), nr * sizeof(FzRunParams), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
-    f.nparts = (int)std::min<long>(1024, std::max<long>(1, (f.M + 4095) / 4096));
-    if ((e = cudaMalloc(&f.part, nr * f.nparts * 2 * sizeof(double))) != cudaSuccess) return e;
+    // partials per run: the separate update's blocks, or one per column tile of
+    // pass E fused with the update (at most eu_tiles(f, 8))
+    f.nparts_upd = (int)std::min<long>(1024, std::max<long>(1, (f.M + 4095) / 4096));
+    f.nparts = f.nparts_upd;
+    const long parts_max = std::max<long>(f.nparts_upd, eu_tiles(f, 8));
+    if ((e = cudaMalloc(&f.part, nr * parts_max * 2 * sizeof(double))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&f.series, nr * (long)f.cap * 2 * sizeof(double))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&f.counter, nr * sizeof(unsigned long long))) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(f.counter, 0, nr * sizeof(unsigned long long), s)) != cudaSuccess) return e;
@@ -939,6 +879,18 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     f.zc = PassCfg{f.plH, std::max(1, 192 / (6 * (f.n / 2 / f.plH.E)))};
     cudaError_t e2 = fused_autotune(f, s);
     if (e2 != cudaSuccess) return e2;
+    // Diagnostic override of pass E + update: NS_FORCE_EU="off" (separate
+    // kernels) or "E,ct" (that fused kernel, if compiled for N).
+    if (const char *fe = getenv("NS_FORCE_EU")) {
+        int E = 0, ct = 0;
+        FzsKernel z;
+        if (strcmp(fe, "off") == 0) f.eu_E = f.eu_ct = 0;
+        else if (sscanf(fe, "%d,%d", &E, &ct) == 2 && fzeu_lookup(f.n, E, ct, &z)) {
+            f.eu_E = E;
+            f.eu_ct = ct;
+        }
+    }
+    f.nparts = f.eu_E ? (int)eu_tiles(f, f.eu_ct) : f.nparts_upd;
     // Diagnostic override of the pass-C kernel, NS_FORCE_PASS_C="kind,E,tile"
     // (the plan-cache triple); ignored when no such kernel is compiled for N.
     if (const char *fz = getenv("NS_FORCE_PASS_C")) {
@@ -1004,6 +956,11 @@ cudaError_t fused_step(FusedRun &f, int *flags, cudaStream_t s, Tracer *tr) {
         if (e != cudaSuccess) return e;
         e = NSK_TIMED(tr, "fused_D_y_forward", run_pass(f, 2, f.sp[2], D, s));
         if (e != cudaSuccess) return e;
+        if (f.eu_E) {
+            e = NSK_TIMED(tr, "fused_E_x_forward_update", launch_eu(f, f.eu_E, f.eu_ct, stage, s));
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         e = NSK_TIMED(tr, "fused_E_x_forward", run_pass(f, 3, f.sp[3], Ep, s));
         if (e != cudaSuccess) return e;
         FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.M, f.nk2, f.nparts};
@@ -1024,6 +981,11 @@ int fused_describe(const FusedRun &f, char *out, int len) {
                                           : "runtime length",
                       f.sp[i].pl.E,
                       f.sp[i].ct);
+    if (w < len && f.eu_E)
+        w += snprintf(out + w, len - w, "\"E_fused_with_update\": {\"E\": %d, \"cols_per_cta\": %d}, ",
+                      f.eu_E, f.eu_ct);
+    else if (w < len)
+        w += snprintf(out + w, len - w, "\"E_fused_with_update\": null, ");
     if (w < len && f.zc.kind == 2)
         w += snprintf(out + w, len - w,
                       "\"C_z_nonlinear\": {\"kernel\": \"register-resident\", \"E\": %d, "

@@ -75,6 +75,8 @@ struct FusedRun {
     Plan plN{}, plH{};           // default plans of length n (x, y) and n/2 (z)
     PassCfg sp[4];               // passes A, B, D, E (chosen by the autotuner)
     PassCfg zc;                  // pass C
+    int eu_E = 0, eu_ct = 0;     // pass E fused with the update (fused_keu.cu); 0: separate kernels
+    int nparts_upd = 0;          // energy partials per run of the separate update kernel
     const float2 *tw = nullptr;  // exp(-2 pi i t / n), t < n (owned by the context)
     float2 *a = nullptr;         // state                       [nr][3][M]
     float2 *a1 = nullptr;        // first-stage state           [nr][3][M]

@@ -119,5 +119,8 @@ bool fzk_lookup_A(int N, int E, int CT, FzsKernel *o);
 bool fzk_lookup_B(int N, int E, int CT, FzsKernel *o);
 bool fzk_lookup_D(int N, int E, int CT, FzsKernel *o);
 bool fzk_lookup_E(int N, int E, int CT, FzsKernel *o);
+// Pass E fused with the update (fused_keu.cu); grid x = ceil(Mx Mz / CT)
+// column tiles, one energy partial per CTA.
+bool fzeu_lookup(int N, int E, int CT, FzsKernel *o);
 
 }  // namespace nsk

@@ -101,3 +101,41 @@ def test_every_strided_pass_kernel(ns, n, monkeypatch):
         assert err < 2e-5, (kind, E, ct, forced, err)
         tried.append((kind, E, ct))
     assert any(t[0] == 2 for t in tried) and any(t[0] == 1 for t in tried), tried
+
+
+EU = [(E, ct) for E in (8, 12, 16, 32) for ct in (8, 16)]
+
+
+@pytest.mark.parametrize("n", [64, 96, 128, 256])
+def test_pass_e_fused_with_update(ns, n, monkeypatch):
+    """Pass E fused with the update (x forward FFT, then 1/N^3, Coriolis,
+    projection, forcing, IF-RK2 and the energy partials per mode in
+    registers), forced through NS_FORCE_EU for every compiled shape and off,
+    against the plain FP64 form; the per-step (E, Omega) from its partials
+    agree with an FP64 sum over the stored state."""
+    from paper_1003_4322_gb300 import _native as nat
+    from paper_1003_4322_gb300.solver import Solver
+    run = dict(n=n, nu=2e-3, dt=1e-3, force_amp=0.5, force_k=3, rot=1.5)
+    a0 = inputs.turbulence_state(n, seed=6)
+    with Solver([run], prec="fp64") as s:
+        s.set_state(a0)
+        s.step(2)
+        ref = s.get_state()
+    tried = []
+    for cfg in ["off"] + [f"{E},{ct}" for E, ct in EU]:
+        monkeypatch.setenv("NS_FORCE_EU", cfg)
+        with Solver([run], prec="fp32") as s:
+            eu = _find_c(nat.ns_describe_run(s.ctx, 0))["E_fused_with_update"]
+            if cfg == "off":
+                assert eu is None
+            elif eu is None or f"{eu['E']},{eu['cols_per_cta']}" != cfg:
+                continue
+            s.set_state(a0)
+            s.step(2)
+            got = s.get_state()
+            Es, Os = s.series(count=4)
+            E, Om, _ = s.energy_spectrum()
+        assert rel_l2(got, ref) < 2e-5, cfg
+        assert abs(Es[-1] - E) < 1e-12 * E and abs(Os[-1] - Om) < 1e-12 * Om, cfg
+        tried.append(cfg)
+    assert len(tried) >= 2, tried
