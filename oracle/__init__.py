@@ -43,7 +43,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nu", ctypes.c_double),
                 ("dt", ctypes.c_double), ("force_amp", ctypes.c_double),
                 ("force_k", ctypes.c_int), ("dealias", ctypes.c_int),
-                ("rot", ctypes.c_double)]
+                ("rot", ctypes.c_double), ("eta", ctypes.c_double),
+                ("mhd", ctypes.c_int)]
 
 
 @dataclass
@@ -55,10 +56,15 @@ class Params:
     force_k: int = 0
     dealias: int = 0
     rot: float = 0.0
+    eta: float = 0.0
+    mhd: int = 0
 
     def c(self) -> _Params:
         return _Params(self.n, self.nu, self.dt, self.force_amp,
-                       self.force_k, self.dealias, self.rot)
+                       self.force_k, self.dealias, self.rot, self.eta, self.mhd)
+
+    def ncomp(self) -> int:
+        return 6 if self.mhd else 3
 
 
 _lib = None
@@ -142,8 +148,11 @@ def forcing(p: Params) -> np.ndarray:
 
 
 def nonlinear(a: np.ndarray, p: Params) -> np.ndarray:
-    """N(a) = P Pi [FFT(u x w)/N^3 + 2 rot (a_y, -a_x, 0)] + f_hat."""
+    """N(a) = P Pi [FFT(u x w)/N^3 + 2 rot (a_y, -a_x, 0)] + f_hat; with
+    p.mhd the six-component [N_u; N_b] of the state [u; b]."""
     a = np.ascontiguousarray(a, dtype=np.complex128)
+    if a.shape[0] != p.ncomp():
+        raise ValueError("state has %d components, parameters want %d" % (a.shape[0], p.ncomp()))
     out = np.empty_like(a)
     cp = p.c()
     _check(lib().or_nonlinear(ctypes.byref(cp), _ptr(a), _ptr(out)), "nonlinear")
@@ -153,6 +162,8 @@ def nonlinear(a: np.ndarray, p: Params) -> np.ndarray:
 def step(a: np.ndarray, p: Params, nsteps: int) -> np.ndarray:
     """nsteps integrating-factor RK2 steps; returns the new state (a copy)."""
     v = np.array(a, dtype=np.complex128, order="C", copy=True)
+    if v.shape[0] != p.ncomp():
+        raise ValueError("state has %d components, parameters want %d" % (v.shape[0], p.ncomp()))
     cp = p.c()
     _check(lib().or_step(ctypes.byref(cp), _ptr(v), int(nsteps)), "step")
     return v

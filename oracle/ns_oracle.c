@@ -36,6 +36,12 @@
  *               same code integrates, Sec. 5): the Coriolis force -2 rot z x u
  *               = 2 rot (u_y, -u_x, 0) joins u x w before the projection,
  *               N(a) = P Pi [FFT(u x w)/N^3 + 2 rot (a_y, -a_x, 0)] + f_hat;
+ *   MHD         (mhd = 1; the magnetohydrodynamic equations of the same code,
+ *               Sec. 5) in Alfven units, state [u; b] of six components,
+ *               j = curl b:  N_u = P Pi [FFT(u x w + j x b)/N^3 + Coriolis]
+ *               + f_hat,  N_b = Pi [i k x FFT(u x b)/N^3];  b has its own
+ *               factor exp(-eta |k|^2 dt), and its mean b(k = 0) is a
+ *               constant of the motion;
  *   time step   integrating-factor Heun (RK2), E(k) = exp(-nu |k|^2 dt):
  *               a1 = E (a + dt N(a)),  a' = E a / 2 + (a1 + dt N(a1)) / 2;
  *   diagnostics E = 1/2 sum |a|^2, Omega = 1/2 sum |k|^2 |a|^2 over the full
@@ -74,6 +80,8 @@ typedef struct {
     int force_k;
     int dealias;
     double rot;
+    double eta;     /* magnetic diffusivity (MHD) */
+    int mhd;        /* 1: state [u; b], 6 components */
 } or_params;
 
 static const double OR_TWO_PI = 6.283185307179586476925286766559;
@@ -349,19 +357,42 @@ int or_forcing(const or_params *p, cplx *fh)
 }
 
 /* Nonlinear term N(a) = P Pi FFT(u x w)/N^3 + f_hat (Sec. 2, Eqs. 1-2). */
+static int nonlinear_mhd(const or_params *p, const cplx *a_in, cplx *out);
+
+/* Velocity part of N from the transformed product already divided by N^3
+ * (in out): the Coriolis force of the state a, then Pi and P, then f_hat. */
+static int finish_velocity(const or_params *p, const cplx *a, cplx *out)
+{
+    const int n = p->n;
+    const long M = (long)n * n * (n / 2 + 1);
+    for (long i = 0; i < M; i++) {                   /* Coriolis -2 rot z x u */
+        out[i] += 2.0 * p->rot * a[M + i];
+        out[M + i] -= 2.0 * p->rot * a[i];
+    }
+    int e = or_project(n, p->dealias, out);          /* Pi, then P */
+    if (e) return e;
+    cplx *fh = malloc(sizeof(cplx) * 3 * (size_t)M);
+    if (!fh) return OR_ERR_OOM;
+    e = or_forcing(p, fh);
+    if (!e)
+        for (long i = 0; i < 3 * M; i++) out[i] += fh[i];
+    free(fh);
+    return e;
+}
+
 int or_nonlinear(const or_params *p, const cplx *a_in, cplx *out)
 {
     if (!p || !a_in || !out || p->n < 2) return OR_ERR_ARG;
+    if (p->mhd) return nonlinear_mhd(p, a_in, out);
     const int n = p->n;
     const long V = (long)n * n * n, nh = n / 2 + 1, M = (long)n * n * nh;
     int e = OR_ERR_OOM;
     cplx *a = malloc(sizeof(cplx) * 3 * (size_t)M);
     cplx *wh = malloc(sizeof(cplx) * 3 * (size_t)M);
-    cplx *fh = malloc(sizeof(cplx) * 3 * (size_t)M);
     double *u = malloc(sizeof(double) * 3 * (size_t)V);
     double *w = malloc(sizeof(double) * 3 * (size_t)V);
     double *c = malloc(sizeof(double) * 3 * (size_t)V);
-    if (!a || !wh || !fh || !u || !w || !c) goto done;
+    if (!a || !wh || !u || !w || !c) goto done;
 
     memcpy(a, a_in, sizeof(cplx) * 3 * (size_t)M);
     apply_mask(n, p->dealias, 3, a);                 /* Galerkin truncation */
@@ -376,47 +407,100 @@ int or_nonlinear(const or_params *p, const cplx *a_in, cplx *out)
     }
     if ((e = or_fft3_r2c(n, 3, c, out))) goto done;
     for (long i = 0; i < 3 * M; i++) out[i] /= (double)V;
-    for (long i = 0; i < M; i++) {                   /* Coriolis -2 rot z x u */
-        out[i] += 2.0 * p->rot * a[M + i];
-        out[M + i] -= 2.0 * p->rot * a[i];
-    }
-    if ((e = or_project(n, p->dealias, out))) goto done;   /* Pi, then P */
-    if ((e = or_forcing(p, fh))) goto done;
-    for (long i = 0; i < 3 * M; i++) out[i] += fh[i];
+    if ((e = finish_velocity(p, a, out))) goto done;
     e = OR_OK;
 done:
-    free(a); free(wh); free(fh); free(u); free(w); free(c);
+    free(a); free(wh); free(u); free(w); free(c);
     return e;
 }
 
-/* nsteps integrating-factor RK2 (Heun) steps of the state a, in place.
+/* MHD nonlinear terms of the six-component state [u; b]. */
+static int nonlinear_mhd(const or_params *p, const cplx *a_in, cplx *out)
+{
+    const int n = p->n;
+    const long V = (long)n * n * n, nh = n / 2 + 1, M = (long)n * n * nh;
+    int e = OR_ERR_OOM;
+    cplx *a = malloc(sizeof(cplx) * 6 * (size_t)M);
+    cplx *cw = malloc(sizeof(cplx) * 6 * (size_t)M);     /* curl u, curl b */
+    cplx *tb = malloc(sizeof(cplx) * 3 * (size_t)M);
+    double *g = malloc(sizeof(double) * 12 * (size_t)V);  /* u, w, b, j on the grid */
+    double *c = malloc(sizeof(double) * 6 * (size_t)V);   /* u x w + j x b, u x b */
+    if (!a || !cw || !tb || !g || !c) goto done;
+
+    memcpy(a, a_in, sizeof(cplx) * 6 * (size_t)M);
+    apply_mask(n, p->dealias, 6, a);                      /* Galerkin truncation */
+    if ((e = or_curl(n, a, cw))) goto done;               /* w_hat = i k x u_hat */
+    if ((e = or_curl(n, a + 3 * M, cw + 3 * M))) goto done;   /* j_hat = i k x b_hat */
+    if ((e = or_fft3_c2r(n, 3, a, g))) goto done;
+    if ((e = or_fft3_c2r(n, 3, cw, g + 3 * V))) goto done;
+    if ((e = or_fft3_c2r(n, 3, a + 3 * M, g + 6 * V))) goto done;
+    if ((e = or_fft3_c2r(n, 3, cw + 3 * M, g + 9 * V))) goto done;
+    const double *u = g, *w = g + 3 * V, *b = g + 6 * V, *j = g + 9 * V;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < V; i++) {
+        /* u x w + j x b */
+        c[i] = u[V + i] * w[2 * V + i] - u[2 * V + i] * w[V + i]
+             + j[V + i] * b[2 * V + i] - j[2 * V + i] * b[V + i];
+        c[V + i] = u[2 * V + i] * w[i] - u[i] * w[2 * V + i]
+                 + j[2 * V + i] * b[i] - j[i] * b[2 * V + i];
+        c[2 * V + i] = u[i] * w[V + i] - u[V + i] * w[i]
+                     + j[i] * b[V + i] - j[V + i] * b[i];
+        /* u x b */
+        c[3 * V + i] = u[V + i] * b[2 * V + i] - u[2 * V + i] * b[V + i];
+        c[4 * V + i] = u[2 * V + i] * b[i] - u[i] * b[2 * V + i];
+        c[5 * V + i] = u[i] * b[V + i] - u[V + i] * b[i];
+    }
+    if ((e = or_fft3_r2c(n, 3, c, out))) goto done;
+    if ((e = or_fft3_r2c(n, 3, c + 3 * V, tb))) goto done;
+    for (long i = 0; i < 3 * M; i++) {
+        out[i] /= (double)V;
+        tb[i] /= (double)V;
+    }
+    if ((e = finish_velocity(p, a, out))) goto done;
+    if ((e = or_curl(n, tb, out + 3 * M))) goto done;    /* N_b = i k x FFT(u x b) */
+    apply_mask(n, p->dealias, 3, out + 3 * M);
+    e = OR_OK;
+done:
+    free(a); free(cw); free(tb); free(g); free(c);
+    return e;
+}
+
+/* nsteps integrating-factor RK2 (Heun) steps of the state a, in place
+ * (three components, or six [u; b] with mhd, b with the factor of eta).
  * The state is first restricted to Pi (the Galerkin space). */
 int or_step(const or_params *p, cplx *a, int nsteps)
 {
     if (!p || !a || p->n < 2 || nsteps < 0) return OR_ERR_ARG;
-    const int n = p->n;
+    const int n = p->n, nc = p->mhd ? 6 : 3;
     const long nh = n / 2 + 1, M = (long)n * n * nh;
     int e = OR_ERR_OOM;
-    double *E = malloc(sizeof(double) * (size_t)M);
-    cplx *N0 = malloc(sizeof(cplx) * 3 * (size_t)M);
-    cplx *a1 = malloc(sizeof(cplx) * 3 * (size_t)M);
+    double *E = malloc(sizeof(double) * 2 * (size_t)M);   /* nu, then eta */
+    cplx *N0 = malloc(sizeof(cplx) * nc * (size_t)M);
+    cplx *a1 = malloc(sizeof(cplx) * nc * (size_t)M);
     if (!E || !N0 || !a1) goto done;
     for (long ix = 0; ix < n; ix++) {
         double kx = wavenumber((int)ix, n);
         for (long iy = 0; iy < n; iy++) {
             double ky = wavenumber((int)iy, n);
-            for (long kz = 0; kz < nh; kz++)
-                E[(ix * n + iy) * nh + kz] =
-                    exp(-p->nu * (kx * kx + ky * ky + (double)kz * kz) * p->dt);
+            for (long kz = 0; kz < nh; kz++) {
+                const double k2 = kx * kx + ky * ky + (double)kz * kz;
+                E[(ix * n + iy) * nh + kz] = exp(-p->nu * k2 * p->dt);
+                E[M + (ix * n + iy) * nh + kz] = exp(-p->eta * k2 * p->dt);
+            }
         }
     }
-    apply_mask(n, p->dealias, 3, a);
+    apply_mask(n, p->dealias, nc, a);
     for (int s = 0; s < nsteps; s++) {
         if ((e = or_nonlinear(p, a, N0))) goto done;
-        for (long i = 0; i < 3 * M; i++) a1[i] = E[i % M] * (a[i] + p->dt * N0[i]);
+        for (long i = 0; i < nc * M; i++) {
+            const double Ei = E[(i >= 3 * M ? M : 0) + i % M];
+            a1[i] = Ei * (a[i] + p->dt * N0[i]);
+        }
         if ((e = or_nonlinear(p, a1, N0))) goto done;
-        for (long i = 0; i < 3 * M; i++)
-            a[i] = 0.5 * E[i % M] * a[i] + 0.5 * (a1[i] + p->dt * N0[i]);
+        for (long i = 0; i < nc * M; i++) {
+            const double Ei = E[(i >= 3 * M ? M : 0) + i % M];
+            a[i] = 0.5 * Ei * a[i] + 0.5 * (a1[i] + p->dt * N0[i]);
+        }
     }
     e = OR_OK;
 done:

@@ -125,3 +125,49 @@ def helical_mode(n, k, s, amp=0.3):
     a = np.zeros((3, n, n, n // 2 + 1), dtype=np.complex128)
     a[:, k[0] % n, k[1] % n, k[2]] = amp * h
     return a
+
+
+def _triad_cross(A, B, K, n):
+    """sum_{p+q=k; p,q,k kept} A(p) x B(q) for every kept k (rows of K)."""
+    M = len(K)
+    off = n
+    lut = -np.ones((3 * n, 3 * n, 3 * n), dtype=np.int64)
+    lut[K[:, 0] + off, K[:, 1] + off, K[:, 2] + off] = np.arange(M)
+    out = np.zeros((M, 3), dtype=np.complex128)
+    for i in range(M):
+        s = K[i] + K
+        tgt = lut[s[:, 0] + off, s[:, 1] + off, s[:, 2] + off]
+        ok = tgt >= 0
+        np.add.at(out, tgt[ok], np.cross(np.broadcast_to(A[i], (M, 3))[ok], B[ok]))
+    return out
+
+
+def _to_half(out, K, like):
+    n = like.shape[1]
+    res = np.zeros_like(like)
+    sel = K[:, 2] >= 0
+    for c in range(3):
+        res[c, K[sel, 0] % n, K[sel, 1] % n, K[sel, 2]] = out[sel, c]
+    return res
+
+
+def triad_mhd(a_half: np.ndarray, dealias: int = 0):
+    """Exact convolutions of the MHD nonlinear terms of a six-component
+    half-layout state [u; b] (Alfven units, j = i k x b):
+    N_u(k) = P(k) sum_{p+q=k} [u(p) x (i q x u(q)) + (i p x b(p)) x b(q)],
+    N_b(k) = i k x sum_{p+q=k} u(p) x b(q);  no transform, no aliasing."""
+    n = a_half.shape[1]
+    K = kept_modes(n, dealias)
+    Kf = K.astype(np.float64)
+    U = full_coeffs(a_half[:3], K)
+    B = full_coeffs(a_half[3:], K)
+    W = 1j * np.cross(Kf, U)
+    J = 1j * np.cross(Kf, B)
+    nu = _triad_cross(U, W, K, n) + _triad_cross(J, B, K, n)
+    k2 = np.sum(Kf * Kf, axis=1)
+    kv = np.sum(Kf * nu, axis=1)
+    nz = k2 > 0
+    nu[nz] -= Kf[nz] * (kv[nz] / k2[nz])[:, None]
+    nu[~nz] = 0
+    nb = 1j * np.cross(Kf, _triad_cross(U, B, K, n))
+    return np.concatenate([_to_half(nu, K, a_half[:3]), _to_half(nb, K, a_half[3:])])

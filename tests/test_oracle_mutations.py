@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from paper_1003_4322_gb300 import inputs
-from tests.spectral_ref import helical_mode, rel_l2, triad_nonlinear
+from tests.spectral_ref import helical_mode, rel_l2, triad_mhd, triad_nonlinear
 
 SRC = open(os.path.join(os.path.dirname(oracle.__file__), "ns_oracle.c")).read()
 
@@ -30,13 +30,12 @@ MUTATIONS = {
     "missing 1/N^3 on the nonlinear term":
         ("for (long i = 0; i < 3 * M; i++) out[i] /= (double)V;", ""),
     "Heun second-stage weight dropped":
-        ("a[i] = 0.5 * E[i % M] * a[i] + 0.5 * (a1[i] + p->dt * N0[i]);",
-         "a[i] = 0.5 * E[i % M] * a[i] + (a1[i] + p->dt * N0[i]);"),
+        ("a[i] = 0.5 * Ei * a[i] + 0.5 * (a1[i] + p->dt * N0[i]);",
+         "a[i] = 0.5 * Ei * a[i] + (a1[i] + p->dt * N0[i]);"),
     "integrating factor outside the Euler stage":
-        ("a1[i] = E[i % M] * (a[i] + p->dt * N0[i]);", "a1[i] = E[i % M] * a[i] + p->dt * N0[i];"),
+        ("a1[i] = Ei * (a[i] + p->dt * N0[i]);", "a1[i] = Ei * a[i] + p->dt * N0[i];"),
     "half viscous factor":
-        ("exp(-p->nu * (kx * kx + ky * ky + (double)kz * kz) * p->dt);",
-         "exp(-0.5 * p->nu * (kx * kx + ky * ky + (double)kz * kz) * p->dt);"),
+        ("exp(-p->nu * k2 * p->dt);", "exp(-0.5 * p->nu * k2 * p->dt);"),
     "forcing sin/cos swapped":
         ("f[i] = F * (sin(kf * z) + cos(kf * y));", "f[i] = F * (cos(kf * z) + sin(kf * y));"),
     "twiddle sign":
@@ -53,11 +52,23 @@ MUTATIONS = {
     "Coriolis without the factor 2":
         ("out[i] += 2.0 * p->rot * a[M + i];\n        out[M + i] -= 2.0 * p->rot * a[i];",
          "out[i] += p->rot * a[M + i];\n        out[M + i] -= p->rot * a[i];"),
+    "Lorentz force j x b written b x j (x component)":
+        ("+ j[V + i] * b[2 * V + i] - j[2 * V + i] * b[V + i];",
+         "+ b[V + i] * j[2 * V + i] - b[2 * V + i] * j[V + i];"),
+    "electromotive force written b x u (x component)":
+        ("c[3 * V + i] = u[V + i] * b[2 * V + i] - u[2 * V + i] * b[V + i];",
+         "c[3 * V + i] = b[V + i] * u[2 * V + i] - b[2 * V + i] * u[V + i];"),
+    "induction term without the curl":
+        ("if ((e = or_curl(n, tb, out + 3 * M))) goto done;",
+         "memcpy(out + 3 * M, tb, sizeof(cplx) * 3 * (size_t)M);"),
+    "magnetic field diffused with nu":
+        ("E[M + (ix * n + iy) * nh + kz] = exp(-p->eta * k2 * p->dt);",
+         "E[M + (ix * n + iy) * nh + kz] = exp(-p->nu * k2 * p->dt);"),
     "Coriolis added after the projection":
-        ("    if ((e = or_project(n, p->dealias, out))) goto done;   /* Pi, then P */\n",
+        ("    int e = or_project(n, p->dealias, out);          /* Pi, then P */\n",
          "    for (long i = 0; i < M; i++) {\n        out[i] -= 2.0 * p->rot * a[M + i];\n"
          "        out[M + i] += 2.0 * p->rot * a[i];\n    }\n"
-         "    if ((e = or_project(n, p->dealias, out))) goto done;\n"
+         "    int e = or_project(n, p->dealias, out);\n"
          "    for (long i = 0; i < M; i++) {\n        out[i] += 2.0 * p->rot * a[M + i];\n"
          "        out[M + i] -= 2.0 * p->rot * a[i];\n    }\n"),
 }
@@ -114,6 +125,15 @@ def _pins():
     q1 = oracle.step(q, oracle.Params(n=8, nu=0.01, dt=0.02, rot=3.0), 3)
     if np.abs(q1 - q0).max() > 1e-13 * np.abs(q0).max():
         failed.append("taylor-proudman")
+    # MHD: exact triad sums, and the force-free field's decay with eta
+    mh = np.concatenate([inputs.random_solenoidal_state(8, 1.0, 2.7, 0.6, seed=31),
+                         inputs.random_solenoidal_state(8, 1.0, 2.7, 0.5, seed=32)])
+    if np.abs(oracle.nonlinear(mh, oracle.Params(n=8, mhd=1)) - triad_mhd(mh)).max() > 1e-12:
+        failed.append("mhd-triad")
+    ff = np.concatenate([np.zeros_like(inputs.abc_state(8)), inputs.abc_state(8)])
+    fb = oracle.step(ff, oracle.Params(n=8, nu=0.01, eta=0.03, dt=0.05, mhd=1), 4)
+    if np.abs(fb[3:] - ff[3:] * math.exp(-0.03 * 0.2)).max() > 1e-14:
+        failed.append("force-free")
     return failed
 
 
