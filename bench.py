@@ -49,6 +49,10 @@ WORKLOADS = {
                             "nu_r = 5e-3 + 1.5e-2 U(4999, r), dt=1e-3, seeded k^-2 starts on "
                             "1<=|k|<=4 (seeds 4000+r); FP64 plain ensemble alongside",
                        n=128, ensemble=48, dt=1e-3, prec="fp32", companion="fp64"),
+    "mhd256": dict(desc="256^3 forced MHD (Alfven units), nu=eta=2e-3, dt=1e-3, ABC forcing k=3 "
+                        "F=0.5 on u, seeded k^-2 starts for u (seed 7) and b (seed 57), plain FP64 "
+                        "(plain FP32 alongside)", n=256, nu=2e-3, eta=2e-3, dt=1e-3, force_amp=0.5,
+                   force_k=3, ic=("mhd", 7), mhd=1, prec="fp64", companion="fp32"),
     "plain768": dict(desc="768^3 forced turbulence, ABC forcing k=3 F=0.5, nu=5e-4, dt=5e-4, "
                           "seeded k^-2 start (seed 5), plain FP64", n=768, nu=5e-4, dt=5e-4,
                      force_amp=0.5, force_k=3, ic=("turb", 5), prec="fp64", companion=None),
@@ -106,6 +110,8 @@ N_SM = 152
 
 def members(w):
     """(run parameters, initial states) of every run of the workload."""
+    import numpy as np
+
     from paper_1003_4322_gb300 import inputs
     if w.get("ensemble"):
         runs, ics = [], []
@@ -119,7 +125,25 @@ def members(w):
     if w["ic"] == "tg":
         return [run], [inputs.taylor_green_state(w["n"])]
     kind, seed = w["ic"]
+    if kind == "mhd":   # state [u; b]
+        run.update(eta=w["eta"], mhd=1)
+        u = inputs.turbulence_state(w["n"], seed)
+        b = inputs.random_solenoidal_state(w["n"], 1.0, 4.0, 0.7, seed=seed + 50)
+        return [run], [np.concatenate([u, b])]
     return [run], [inputs.turbulence_state(w["n"], seed)]
+
+
+def load_state(s, a0, run):
+    """Velocity (and, for a six-component MHD state, the magnetic field)."""
+    s.set_field(0, a0[:3], run=run)
+    if a0.shape[0] == 6:
+        s.set_field(1, a0[3:], run=run)
+
+
+def read_state(s, runs, run):
+    import numpy as np
+    u = s.get_field(0, run=run)
+    return np.concatenate([u, s.get_field(1, run=run)]) if runs[run].get("mhd") else u
 
 
 # ---------------------------------------------------------------- kernel model
@@ -143,6 +167,10 @@ def kernel_model(name, n, prec):
         return 2 * 3 * M * 2 * es, 3 * M * 6
     if name == "cross":
         return 9 * V * es, 9 * V
+    if name == "cross_mhd":     # reads u, w, b, j; writes u x w + j x b and u x b
+        return 18 * V * es, 30 * V
+    if name == "update_b":
+        return 7.5 * 3 * M * 2 * es, 3 * M * 20
     if name == "update":
         return 7.5 * 3 * M * 2 * es, 3 * M * 20
     # fused form (FP32 complex = 8 bytes; only the kept modes move)
@@ -247,7 +275,7 @@ def time_form(w, prec, mem, steps, warmup, census_steps, dist):
     runs, ics = mem
     s = Solver(runs, prec=prec, stream=stream)
     for i, a0 in enumerate(ics):
-        s.set_state(a0, run=i)
+        load_state(s, a0, i)
     s.step(warmup)
     s.sync()
     clocks = ClockSampler(torch.cuda.current_device())
@@ -268,7 +296,7 @@ def time_form(w, prec, mem, steps, warmup, census_steps, dist):
     E, O = s.series(count=steps)
     census = nat.ns_kernel_census(s.ctx, census_steps) if census_steps > 0 else []
     desc = nat.ns_describe_run(s.ctx, 0)
-    states = [s.get_state(run=i) for i in range(len(runs))]
+    states = [read_state(s, runs, i) for i in range(len(runs))]
     return dict(solver=s, ms=ms, clocks=clk, census=census, states=states, E=E, O=O, desc=desc)
 
 
@@ -284,7 +312,8 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
     # plain form: one launch per run
     sizes = sizes or [w["n"]]
     per_size = [kernel_model(name, n, prec) for n in sizes]
-    launches_per_pass = len(sizes) if prec == "fp64" else len(set(sizes))
+    plain = prec == "fp64" or w.get("mhd")
+    launches_per_pass = len(sizes) if plain else len(set(sizes))
     bytes_ = sum(b for b, _ in per_size) / launches_per_pass
     flops = sum(f for _, f in per_size) / launches_per_pass
     gbs = bytes_ / (per_launch_ms * 1e-3) / 1e9
@@ -402,7 +431,7 @@ def e2e(w, prec, mem, steps):
 
     def one_step():
         for i, h in enumerate(hosts):
-            s.set_state(h, run=i)
+            load_state(s, h, i)
         s.step(1)
         return [s.energy_spectrum(run=i)[2] for i in range(nr)]
     try:
@@ -434,7 +463,7 @@ def oracle_steps(mem, budget_s, max_steps):
         i = steps % len(runs)
         r = runs[i]
         p = oracle.Params(n=r["n"], nu=r["nu"], dt=r["dt"], force_amp=r.get("force_amp", 0.0),
-                          force_k=r.get("force_k", 0))
+                          force_k=r.get("force_k", 0), eta=r.get("eta", 0.0), mhd=r.get("mhd", 0))
         states[i] = oracle.step(states[i], p, 1)
         steps += 1
         if time.perf_counter() - t0 > budget_s:

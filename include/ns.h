@@ -85,6 +85,14 @@ typedef struct {
                           Coriolis force -2 rot z x u of the rotating
                           equations (Sec. 5) joins u x w before the
                           projection; any finite value */
+    double eta;        /* magnetic diffusivity, >= 0 (used when mhd = 1) */
+    int mhd;           /* 1: the magnetohydrodynamic equations of the same
+                          code (Sec. 5), Alfven units: a magnetic field b
+                          joins the state, j = curl b, the Lorentz force
+                          j x b joins u x w, and db/dt = curl(u x b) +
+                          eta lap b; b(k = 0) is a constant mean field.
+                          A context with an MHD run uses the plain form in
+                          either precision.  0: Navier-Stokes. */
 } ns_run_params;
 
 /* Create a context for nruns independent runs (an ensemble when nruns > 1;
@@ -92,7 +100,8 @@ typedef struct {
  * cuda_stream (a cudaStream_t, or NULL).  Allocates every device buffer the
  * runs need; states start at zero.  *out receives the context, or NULL on
  * error.  Errors: NS_ERR_ARG (null pointer, nruns < 1, nu < 0, dt <= 0,
- * dealias not 0/1, force_k < 0), NS_ERR_UNSUPPORTED_N, NS_ERR_OOM,
+ * dealias not 0/1, force_k < 0, mhd not 0/1, eta < 0, a non-finite
+ * parameter), NS_ERR_UNSUPPORTED_N, NS_ERR_OOM,
  * NS_ERR_CUDA. */
 ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec,
                   void *cuda_stream, ns_ctx **out);
@@ -110,6 +119,13 @@ ns_status ns_set_state(ns_ctx *ctx, int run, const void *uhat, int on_device);
  * are written as zero.  Synchronises the context's stream.  Errors:
  * NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_NONFINITE. */
 ns_status ns_get_state(ns_ctx *ctx, int run, void *uhat, int on_device);
+
+/* ns_set_state / ns_get_state for one field of the state: field 0 is the
+ * velocity (the same as those calls), field 1 the magnetic field of an MHD
+ * run (same layout; its k = 0 mode is the mean field).  Errors as theirs,
+ * and NS_ERR_ARG for field 1 of a Navier-Stokes run. */
+ns_status ns_set_field(ns_ctx *ctx, int run, int field, const void *uhat, int on_device);
+ns_status ns_get_field(ns_ctx *ctx, int run, int field, void *uhat, int on_device);
 
 /* Advance every run by nsteps integrating-factor RK2 steps (Sec. 2,
  * Eqs. 1-2), queued asynchronously; each step also records the run's energy
@@ -161,6 +177,13 @@ ns_status ns_fft_c2r_noalloc(int n, int ncomp, const void *in, void *out, void *
  * min(nbins, ns_nbins(N)) shells (spec may be NULL when nbins = 0); energy
  * and enstrophy may be NULL.  Host outputs; synchronises the stream.
  * Errors: NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_NONFINITE. */
+/* ns_energy_spectrum of one field (0: velocity, as ns_energy_spectrum; 1:
+ * the magnetic field of an MHD run, E_b = 1/2 sum |b|^2 and 1/2 sum |k|^2
+ * |b|^2 = 1/2 <|j|^2>).  Errors as ns_energy_spectrum, and NS_ERR_ARG for
+ * field 1 of a Navier-Stokes run. */
+ns_status ns_field_spectrum(ns_ctx *ctx, int run, int field, double *spec, int nbins,
+                            double *energy, double *enstrophy);
+
 ns_status ns_energy_spectrum(ns_ctx *ctx, int run, double *spec, int nbins,
                              double *energy, double *enstrophy);
 

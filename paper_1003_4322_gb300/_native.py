@@ -23,7 +23,8 @@ NS_FP64, NS_FP32 = 0, 1
 SYMBOLS = ("ns_init", "ns_set_state", "ns_get_state", "ns_step", "ns_fft_r2c", "ns_fft_c2r",
            "ns_energy_spectrum", "ns_nbins", "ns_series", "ns_series_capacity",
            "ns_kernel_census", "ns_sync", "ns_last_error", "ns_status_str", "ns_destroy",
-           "ns_fft_c2r_noalloc", "ns_describe_run", "ns_helicity")
+           "ns_fft_c2r_noalloc", "ns_describe_run", "ns_helicity", "ns_set_field",
+           "ns_get_field", "ns_field_spectrum")
 
 
 class NsError(RuntimeError):
@@ -36,7 +37,8 @@ class NsError(RuntimeError):
 class ns_run_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nu", ctypes.c_double), ("dt", ctypes.c_double),
                 ("force_amp", ctypes.c_double), ("force_k", ctypes.c_int),
-                ("dealias", ctypes.c_int), ("rot", ctypes.c_double)]
+                ("dealias", ctypes.c_int), ("rot", ctypes.c_double), ("eta", ctypes.c_double),
+                ("mhd", ctypes.c_int)]
 
 
 class ns_kernel_time(ctypes.Structure):
@@ -60,6 +62,9 @@ def load(path: str = LIB_PATH):
     sig = {
         "ns_init": ([ctypes.POINTER(ns_run_params), I, I, P, ctypes.POINTER(P)], I),
         "ns_set_state": ([P, I, P, I], I),
+        "ns_set_field": ([P, I, I, P, I], I),
+        "ns_get_field": ([P, I, I, P, I], I),
+        "ns_field_spectrum": ([P, I, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D)], I),
         "ns_get_state": ([P, I, P, I], I),
         "ns_step": ([P, I], I),
         "ns_fft_r2c": ([P, I, I, P, P], I),
@@ -130,7 +135,8 @@ def ns_init(runs, prec: int, stream=None):
         else:
             arr[i] = ns_run_params(int(r["n"]), float(r.get("nu", 0.0)), float(r["dt"]),
                                    float(r.get("force_amp", 0.0)), int(r.get("force_k", 0)),
-                                   int(r.get("dealias", 0)), float(r.get("rot", 0.0)))
+                                   int(r.get("dealias", 0)), float(r.get("rot", 0.0)),
+                                   float(r.get("eta", 0.0)), int(r.get("mhd", 0)))
     if stream is None:
         s = None
     elif hasattr(stream, "cuda_stream"):
@@ -153,6 +159,25 @@ def ns_set_state(ctx, run: int, uhat) -> None:
 
 def ns_get_state(ctx, run: int, out) -> None:
     _check(load().ns_get_state(ctx, run, _ptr(out), _on_device(out)), "ns_get_state", ctx)
+
+
+def ns_set_field(ctx, run: int, field: int, uhat) -> None:
+    """field 0: velocity, 1: magnetic field (MHD runs); layout as ns_set_state."""
+    _check(load().ns_set_field(ctx, run, field, _ptr(uhat), _on_device(uhat)), "ns_set_field", ctx)
+
+
+def ns_get_field(ctx, run: int, field: int, out) -> None:
+    _check(load().ns_get_field(ctx, run, field, _ptr(out), _on_device(out)), "ns_get_field", ctx)
+
+
+def ns_field_spectrum(ctx, run: int, field: int, n: int):
+    """Returns (E, Omega, spectrum) of field 0 (velocity) or 1 (magnetic)."""
+    nb = ns_nbins(n)
+    spec = np.zeros(nb, dtype=np.float64)
+    e, om = ctypes.c_double(), ctypes.c_double()
+    _check(load().ns_field_spectrum(ctx, run, field, _ptr(spec), nb, ctypes.byref(e),
+                                    ctypes.byref(om)), "ns_field_spectrum", ctx)
+    return e.value, om.value, spec
 
 
 def ns_step(ctx, nsteps: int) -> None:

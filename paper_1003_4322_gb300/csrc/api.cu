@@ -38,6 +38,7 @@ struct Run {
     // plain form (full half layout)
     void *un = nullptr, *u1 = nullptr, *wn = nullptr, *work = nullptr, *phys = nullptr;
     void *etab = nullptr;   // exp(-nu k^2 dt) by integer k^2
+    void *etab_b = nullptr; // MHD: exp(-eta k^2 dt); un, u1, wn then hold [u; b] (6 components)
     // fused form: the run is member gidx of group `group` of the context
     int group = -1, gidx = 0;
     // diagnostics (plain form owns them; fused runs point into their group)
@@ -63,6 +64,7 @@ struct ns_ctx {
     int spec_cap = 0;
     void *staging = nullptr;
     size_t staging_bytes = 0;
+    bool any_mhd = false;            // an MHD run puts the context on the plain form
     cudaGraphExec_t graph = nullptr;
     char last_error[256] = {0};
 };
@@ -207,9 +209,9 @@ ns_status ensure_staging(ns_ctx *c, size_t bytes) {
 const size_t kStageChunk = 64u << 20;   // bytes of FP64 complex per host transfer
 
 template <typename T>
-ns_status plain_set_state(ns_ctx *c, Run &r, const double2 *src, int on_device) {
+ns_status plain_set_state(ns_ctx *c, Run &r, const double2 *src, int on_device, int field = 0) {
     typedef typename Cx<T>::type C;
-    C *dst = (C *)r.un;
+    C *dst = (C *)r.un + (long)field * 3 * r.M;
     const long total = 3 * r.M;
     const long chunk = on_device ? total : (long)(kStageChunk / sizeof(double2));
     if (!on_device) {
@@ -242,9 +244,9 @@ ns_status plain_set_state(ns_ctx *c, Run &r, const double2 *src, int on_device) 
 }
 
 template <typename T>
-ns_status plain_get_state(ns_ctx *c, Run &r, double2 *dst, int on_device) {
+ns_status plain_get_state(ns_ctx *c, Run &r, double2 *dst, int on_device, int field = 0) {
     typedef typename Cx<T>::type C;
-    const C *src = (const C *)r.un;
+    const C *src = (const C *)r.un + (long)field * 3 * r.M;
     const long total = 3 * r.M;
     const long chunk = on_device ? total : (long)(kStageChunk / sizeof(double2));
     if (!on_device) {
@@ -271,18 +273,24 @@ ns_status plain_get_state(ns_ctx *c, Run &r, double2 *dst, int on_device) {
 template <typename T> ns_status plain_alloc(ns_ctx *c, Run &r) {
     typedef typename Cx<T>::type C;
     const size_t half = (size_t)r.M * sizeof(C), real = (size_t)r.V * sizeof(T);
-    NS_CK(dalloc(&r.un, 3 * half));
-    NS_CK(dalloc(&r.u1, 3 * half));
-    NS_CK(dalloc(&r.wn, 3 * half));
+    const int nc = r.p.mhd ? 6 : 3;   // state components: u, or u and b
+    NS_CK(dalloc(&r.un, nc * half));
+    NS_CK(dalloc(&r.u1, nc * half));
+    NS_CK(dalloc(&r.wn, nc * half));
     NS_CK(dalloc(&r.work, 3 * half));
-    NS_CK(dalloc(&r.phys, 6 * real));
-    NS_CK(cudaMemsetAsync(r.un, 0, 3 * half, c->stream));
-    NS_CK(cudaMemsetAsync(r.u1, 0, 3 * half, c->stream));
+    NS_CK(dalloc(&r.phys, 2 * nc * real));
+    NS_CK(cudaMemsetAsync(r.un, 0, nc * half, c->stream));
+    NS_CK(cudaMemsetAsync(r.u1, 0, nc * half, c->stream));
     const int nk2 = 3 * (r.n / 2) * (r.n / 2) + 1;
     std::vector<T> h(nk2);
     for (int k2 = 0; k2 < nk2; k2++) h[k2] = (T)exp(-r.p.nu * (double)k2 * r.p.dt);
     NS_CK(dalloc(&r.etab, nk2 * sizeof(T)));
     NS_CK(cudaMemcpy(r.etab, h.data(), nk2 * sizeof(T), cudaMemcpyHostToDevice));
+    if (r.p.mhd) {
+        for (int k2 = 0; k2 < nk2; k2++) h[k2] = (T)exp(-r.p.eta * (double)k2 * r.p.dt);
+        NS_CK(dalloc(&r.etab_b, nk2 * sizeof(T)));
+        NS_CK(cudaMemcpy(r.etab_b, h.data(), nk2 * sizeof(T), cudaMemcpyHostToDevice));
+    }
     return NS_OK;
 }
 
@@ -293,7 +301,29 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
     if (st != NS_OK) return st;
     const int ct = default_ct(sizeof(C), r.n);
     T *phys = (T *)r.phys;
-    for (int stage = 1; stage <= 2; stage++) {
+    const long M3 = 3 * r.M, V3 = 3 * r.V;
+    for (int stage = 1; stage <= 2 && r.p.mhd; stage++) {
+        // MHD (Alfven units): [u; b] -> w = curl u, j = curl b -> u, w, b, j on the
+        // grid -> u x w + j x b, u x b -> their transforms -> the two updates
+        C *src = (C *)(stage == 1 ? r.un : r.u1);
+        C *wj = (C *)r.wn;
+        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, wj, r.n, s)));
+        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src + M3, wj + M3, r.n, s)));
+        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, r.n, 3, *f, ct, s, tr));
+        NS_CK(c2r_batch<T>(wj, (C *)r.work, phys + V3, r.n, 3, *f, ct, s, tr));
+        NS_CK(c2r_batch<T>(src + M3, (C *)r.work, phys + 2 * V3, r.n, 3, *f, ct, s, tr));
+        NS_CK(c2r_batch<T>(wj + M3, (C *)r.work, phys + 3 * V3, r.n, 3, *f, ct, s, tr));
+        NS_CK(NSK_TIMED(tr, "cross_mhd", plain_cross_mhd<T>(phys, r.n, s)));
+        NS_CK(r2c_batch<T>(phys, wj, r.n, 3, *f, ct, s, tr));
+        NS_CK(r2c_batch<T>(phys + V3, wj + M3, r.n, 3, *f, ct, s, tr));
+        UpdateArgs ua{stage, r.p.dt, r.p.force_amp, r.p.force_k, r.p.dealias, r.p.rot};
+        NS_CK(NSK_TIMED(tr, "update",
+                        plain_update<T>((C *)r.un, (C *)r.u1, (const C *)wj, (const T *)r.etab, r.n, ua, s)));
+        NS_CK(NSK_TIMED(tr, "update_b",
+                        plain_update_b<T>((C *)r.un + M3, (C *)r.u1 + M3, (const C *)wj + M3,
+                                          (const T *)r.etab_b, r.n, stage, r.p.dt, r.p.dealias, s)));
+    }
+    for (int stage = 1; stage <= 2 && !r.p.mhd; stage++) {
         C *src = (C *)(stage == 1 ? r.un : r.u1);
         NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, (C *)r.wn, r.n, s)));
         NS_CK(c2r_batch<T>(src, (C *)r.work, phys, r.n, 3, *f, ct, s, tr));
@@ -310,7 +340,7 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
     return NS_OK;
 }
 
-bool use_fused(const ns_ctx *c) { return c->prec == NS_FP32 && fused_enabled(); }
+bool use_fused(const ns_ctx *c) { return c->prec == NS_FP32 && fused_enabled() && !c->any_mhd; }
 
 // One RK2 step of every run of the context: one batched sequence of launches
 // per group of the fused form, or the plain sequence per run.
@@ -353,7 +383,7 @@ ns_status build_graph(ns_ctx *c) {
 }
 
 void free_run(Run &r) {
-    void *ps[] = {r.un, r.u1, r.wn, r.work, r.phys, r.etab};
+    void *ps[] = {r.un, r.u1, r.wn, r.work, r.phys, r.etab, r.etab_b};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (r.owns_diag) {
@@ -417,8 +447,8 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
                  "\"runs_in_group\": %d, \"passes\": %s}",
                  r.n, g.K, 3 * g.M, g.nr, tune);
     } else {
-        snprintf(out, len, "{\"form\": \"plain %s\", \"n\": %d, \"cols_per_cta\": %d}",
-                 c->prec == NS_FP64 ? "FP64" : "FP32", r.n,
+        snprintf(out, len, "{\"form\": \"plain %s\", \"equations\": \"%s\", \"n\": %d, \"cols_per_cta\": %d}",
+                 c->prec == NS_FP64 ? "FP64" : "FP32", r.p.mhd ? "MHD" : "Navier-Stokes", r.n,
                  default_ct(c->prec == NS_FP64 ? 16 : 8, r.n));
     }
     return NS_OK;
@@ -433,7 +463,7 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
         const ns_run_params &p = runs[i];
         if (!(p.nu >= 0.0) || !(p.dt > 0.0) || (p.dealias != 0 && p.dealias != 1) ||
             p.force_k < 0 || !isfinite(p.force_amp) || !isfinite(p.nu) || !isfinite(p.dt) ||
-            !isfinite(p.rot))
+            !isfinite(p.rot) || (p.mhd != 0 && p.mhd != 1) || !(p.eta >= 0.0) || !isfinite(p.eta))
             return NS_ERR_ARG;
         if (!supported_n(p.n) || p.n > (prec == NS_FP32 ? 1024 : 768)) return NS_ERR_UNSUPPORTED_N;
     }
@@ -441,6 +471,7 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
     if (!c) return NS_ERR_OOM;
     c->prec = prec;
     c->stream = (cudaStream_t)cuda_stream;
+    for (int i = 0; i < nruns; i++) c->any_mhd = c->any_mhd || runs[i].mhd;
     ns_status st = NS_OK;
     auto bail = [&](ns_status s) {
         ns_destroy(c);
@@ -528,11 +559,12 @@ void ns_destroy(ns_ctx *c) {
     delete c;
 }
 
-ns_status ns_set_state(ns_ctx *c, int run, const void *uhat, int on_device) {
+ns_status ns_set_field(ns_ctx *c, int run, int field, const void *uhat, int on_device) {
     ns_status st = check_ctx(c);
     if (st != NS_OK) return st;
     if (run < 0 || run >= (int)c->runs.size() || !uhat) return NS_ERR_ARG;
     Run &r = c->runs[run];
+    if (field != 0 && !(field == 1 && r.p.mhd)) return NS_ERR_ARG;
     if (use_fused(c)) {
         if (!on_device) {
             ns_status s2 = ensure_staging(c, kStageChunk);
@@ -543,15 +575,20 @@ ns_status ns_set_state(ns_ctx *c, int run, const void *uhat, int on_device) {
         if (e != cudaSuccess) return fail_cuda(c, e);
         return NS_OK;
     }
-    return c->prec == NS_FP64 ? plain_set_state<double>(c, r, (const double2 *)uhat, on_device)
-                              : plain_set_state<float>(c, r, (const double2 *)uhat, on_device);
+    return c->prec == NS_FP64 ? plain_set_state<double>(c, r, (const double2 *)uhat, on_device, field)
+                              : plain_set_state<float>(c, r, (const double2 *)uhat, on_device, field);
 }
 
-ns_status ns_get_state(ns_ctx *c, int run, void *uhat, int on_device) {
+ns_status ns_set_state(ns_ctx *c, int run, const void *uhat, int on_device) {
+    return ns_set_field(c, run, 0, uhat, on_device);
+}
+
+ns_status ns_get_field(ns_ctx *c, int run, int field, void *uhat, int on_device) {
     ns_status st = check_ctx(c);
     if (st != NS_OK) return st;
     if (run < 0 || run >= (int)c->runs.size() || !uhat) return NS_ERR_ARG;
     Run &r = c->runs[run];
+    if (field != 0 && !(field == 1 && r.p.mhd)) return NS_ERR_ARG;
     if (use_fused(c)) {
         if (!on_device) {
             ns_status s2 = ensure_staging(c, kStageChunk);
@@ -561,12 +598,16 @@ ns_status ns_get_state(ns_ctx *c, int run, void *uhat, int on_device) {
                                         c->staging, kStageChunk, c->stream);
         if (e != cudaSuccess) return fail_cuda(c, e);
     } else {
-        st = c->prec == NS_FP64 ? plain_get_state<double>(c, r, (double2 *)uhat, on_device)
-                                : plain_get_state<float>(c, r, (double2 *)uhat, on_device);
+        st = c->prec == NS_FP64 ? plain_get_state<double>(c, r, (double2 *)uhat, on_device, field)
+                                : plain_get_state<float>(c, r, (double2 *)uhat, on_device, field);
         if (st != NS_OK) return st;
     }
     NS_CK(cudaStreamSynchronize(c->stream));
     return check_flags(c);
+}
+
+ns_status ns_get_state(ns_ctx *c, int run, void *uhat, int on_device) {
+    return ns_get_field(c, run, 0, uhat, on_device);
 }
 
 ns_status ns_step(ns_ctx *c, int nsteps) {
@@ -628,20 +669,22 @@ ns_status ns_fft_c2r(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
     return NS_OK;
 }
 
-ns_status ns_energy_spectrum(ns_ctx *c, int run, double *spec, int nbins, double *energy,
-                             double *enstrophy) {
+ns_status ns_field_spectrum(ns_ctx *c, int run, int field, double *spec, int nbins, double *energy,
+                            double *enstrophy) {
     ns_status st = check_ctx(c);
     if (st != NS_OK) return st;
     if (run < 0 || run >= (int)c->runs.size() || nbins < 0 || (nbins > 0 && !spec))
         return NS_ERR_ARG;
     Run &r = c->runs[run];
+    if (field != 0 && !(field == 1 && r.p.mhd)) return NS_ERR_ARG;
     const int nb = ns_nbins(r.n);
+    const long off = (long)field * 3 * r.M;
     if (use_fused(c))
         NS_CK(fused_spectrum(c->groups[r.group], r.gidx, nb, c->spec, c->ens, c->stream));
     else if (c->prec == NS_FP64)
-        NS_CK(plain_spectrum<double>((const double2 *)r.un, r.n, nb, c->spec, c->ens, c->stream));
+        NS_CK(plain_spectrum<double>((const double2 *)r.un + off, r.n, nb, c->spec, c->ens, c->stream));
     else
-        NS_CK(plain_spectrum<float>((const float2 *)r.un, r.n, nb, c->spec, c->ens, c->stream));
+        NS_CK(plain_spectrum<float>((const float2 *)r.un + off, r.n, nb, c->spec, c->ens, c->stream));
     std::vector<double> hs(nb), he(nb);
     NS_CK(cudaMemcpyAsync(hs.data(), c->spec, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     NS_CK(cudaMemcpyAsync(he.data(), c->ens, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -656,6 +699,11 @@ ns_status ns_energy_spectrum(ns_ctx *c, int run, double *spec, int nbins, double
     if (enstrophy) *enstrophy = om;
     if (!isfinite(e)) return NS_ERR_NONFINITE;
     return check_flags(c);
+}
+
+ns_status ns_energy_spectrum(ns_ctx *c, int run, double *spec, int nbins, double *energy,
+                             double *enstrophy) {
+    return ns_field_spectrum(c, run, 0, spec, nbins, energy, enstrophy);
 }
 
 ns_status ns_helicity(ns_ctx *c, int run, double *spec, int nbins, double *helicity) {

@@ -46,6 +46,24 @@ __global__ void k_cross(T *u, const T *__restrict__ w, long V) {
     }
 }
 
+// MHD products on the grid: g = [u, w, b, j] (3 components each, V points
+// per component); on return g[0..3V) = u x w + j x b and g[3V..6V) = u x b.
+template <typename T>
+__global__ void k_cross_mhd(T *g, long V) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x) {
+        const T ux = g[i], uy = g[V + i], uz = g[2 * V + i];
+        const T wx = g[3 * V + i], wy = g[4 * V + i], wz = g[5 * V + i];
+        const T bx = g[6 * V + i], by = g[7 * V + i], bz = g[8 * V + i];
+        const T jx = g[9 * V + i], jy = g[10 * V + i], jz = g[11 * V + i];
+        g[i] = uy * wz - uz * wy + (jy * bz - jz * by);
+        g[V + i] = uz * wx - ux * wz + (jz * bx - jx * bz);
+        g[2 * V + i] = ux * wy - uy * wx + (jx * by - jy * bx);
+        g[3 * V + i] = uy * bz - uz * by;
+        g[4 * V + i] = uz * bx - ux * bz;
+        g[5 * V + i] = ux * by - uy * bx;
+    }
+}
+
 // ---------------------------------------------------------------- update
 
 // ABC forcing coefficients at signed k (closed form of
@@ -121,6 +139,50 @@ __global__ void k_update(typename Cx<T>::type *__restrict__ a, typename Cx<T>::t
             }
         }
         C *dst = ua.stage == 1 ? a1 : a;
+        dst[m] = o0;
+        dst[M + m] = o1;
+        dst[2 * M + m] = o2;
+    }
+}
+
+// Induction update of the magnetic field: N_b = Pi (i k x nb / N^3) with nb
+// the transform of u x b, then the IF-RK2 stage with the factor of eta.  The
+// mean field b(k = 0) has N_b = 0 and factor 1, so it is carried unchanged.
+template <typename T>
+__global__ void k_update_b(typename Cx<T>::type *__restrict__ b, typename Cx<T>::type *__restrict__ b1,
+                           const typename Cx<T>::type *__restrict__ nb, const T *__restrict__ etab,
+                           int n, long M, int stage, double dt_, int dealias) {
+    typedef typename Cx<T>::type C;
+    const int nh = n / 2 + 1;
+    const T inv = (T)(1.0 / ((double)n * n * n));
+    const T dt = (T)dt_;
+    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(m % nh);
+        const int iy = (int)((m / nh) % n);
+        const int ix = (int)(m / ((long)nh * n));
+        const int kx = wavenum(ix, n), ky = wavenum(iy, n);
+        const int k2 = kx * kx + ky * ky + kz * kz;
+        C o0 = czero<C>(), o1 = czero<C>(), o2 = czero<C>();
+        if (kept(kx, ky, kz, n, dealias)) {
+            const C vx = cscale(nb[m], inv), vy = cscale(nb[M + m], inv), vz = cscale(nb[2 * M + m], inv);
+            const T fkx = (T)kx, fky = (T)ky, fkz = (T)kz;
+            // i k x v
+            const C nx = cmul_i<1>(csub(cscale(vz, fky), cscale(vy, fkz)));
+            const C ny = cmul_i<1>(csub(cscale(vx, fkz), cscale(vz, fkx)));
+            const C nz = cmul_i<1>(csub(cscale(vy, fkx), cscale(vx, fky)));
+            const T e = etab[k2];
+            if (stage == 1) {
+                o0 = cscale(cadd(b[m], cscale(nx, dt)), e);
+                o1 = cscale(cadd(b[M + m], cscale(ny, dt)), e);
+                o2 = cscale(cadd(b[2 * M + m], cscale(nz, dt)), e);
+            } else {
+                const T he = (T)0.5 * e, h = (T)0.5;
+                o0 = cadd(cscale(b[m], he), cscale(cadd(b1[m], cscale(nx, dt)), h));
+                o1 = cadd(cscale(b[M + m], he), cscale(cadd(b1[M + m], cscale(ny, dt)), h));
+                o2 = cadd(cscale(b[2 * M + m], he), cscale(cadd(b1[2 * M + m], cscale(nz, dt)), h));
+            }
+        }
+        C *dst = stage == 1 ? b1 : b;
         dst[m] = o0;
         dst[M + m] = o1;
         dst[2 * M + m] = o2;
@@ -232,6 +294,22 @@ cudaError_t plain_cross(T *u, const T *w, int n, cudaStream_t s) {
 }
 
 template <typename T>
+cudaError_t plain_cross_mhd(T *g, int n, cudaStream_t s) {
+    const long V = (long)n * n * n;
+    k_cross_mhd<T><<<grid_for(V, 256), 256, 0, s>>>(g, V);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t plain_update_b(typename Cx<T>::type *b, typename Cx<T>::type *b1,
+                           const typename Cx<T>::type *nb, const T *etab, int n, int stage, double dt,
+                           int dealias, cudaStream_t s) {
+    const long M = (long)n * n * (n / 2 + 1);
+    k_update_b<T><<<grid_for(M, 256), 256, 0, s>>>(b, b1, nb, etab, n, M, stage, dt, dealias);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t plain_update(typename Cx<T>::type *a, typename Cx<T>::type *a1,
                          const typename Cx<T>::type *nl, const T *etab, int n, const UpdateArgs &ua,
                          cudaStream_t s) {
@@ -281,6 +359,9 @@ cudaError_t energy_final(const double *part, int nparts, double *series, int cap
 #define NSK_INST(T)                                                                                \
     template cudaError_t plain_curl<T>(const Cx<T>::type *, Cx<T>::type *, int, cudaStream_t);    \
     template cudaError_t plain_cross<T>(T *, const T *, int, cudaStream_t);                       \
+    template cudaError_t plain_cross_mhd<T>(T *, int, cudaStream_t);                              \
+    template cudaError_t plain_update_b<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,     \
+                                           const T *, int, int, double, int, cudaStream_t);       \
     template cudaError_t plain_update<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,       \
                                          const T *, int, const UpdateArgs &, cudaStream_t);       \
     template cudaError_t plain_energy_partials<T>(const Cx<T>::type *, int, double *, cudaStream_t); \

@@ -16,6 +16,14 @@ struct UpdateArgs {
 template <typename T>
 cudaError_t plain_curl(const typename Cx<T>::type *a, typename Cx<T>::type *w, int n, cudaStream_t s);
 template <typename T> cudaError_t plain_cross(T *u, const T *w, int n, cudaStream_t s);
+// MHD: g = [u, w, b, j] on the grid -> g[0..3) = u x w + j x b, g[3..6) = u x b.
+template <typename T> cudaError_t plain_cross_mhd(T *g, int n, cudaStream_t s);
+// MHD induction update of b (stage 1: b1 = E (b + dt N_b); stage 2: b = E b/2 +
+// (b1 + dt N_b)/2) from nb = transform of u x b; etab = exp(-eta k^2 dt).
+template <typename T>
+cudaError_t plain_update_b(typename Cx<T>::type *b, typename Cx<T>::type *b1,
+                           const typename Cx<T>::type *nb, const T *etab, int n, int stage, double dt,
+                           int dealias, cudaStream_t s);
 template <typename T>
 cudaError_t plain_update(typename Cx<T>::type *a, typename Cx<T>::type *a1,
                          const typename Cx<T>::type *nl, const T *etab, int n, const UpdateArgs &ua,

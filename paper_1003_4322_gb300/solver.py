@@ -12,7 +12,9 @@ class Solver:
     """Integrating-factor RK2 pseudospectral solver for one or more runs.
 
     runs: list of dicts with keys n, nu, dt and optionally force_amp,
-    force_k, dealias.  prec: "fp64" (plain form) or "fp32" (fused form).
+    force_k, dealias, rot, and eta with mhd = 1 for MHD runs.
+    prec: "fp64" (plain form) or "fp32" (fused form; plain form when a run
+    is MHD).
     """
 
     def __init__(self, runs, prec: str = "fp32", stream=None):
@@ -52,6 +54,22 @@ class Solver:
             out = np.empty((3, n, n, n // 2 + 1), dtype=np.complex128)
         nat.ns_get_state(self.ctx, run, out)
         return out
+
+    def set_field(self, field: int, uhat, run: int = 0) -> None:
+        """field 0: velocity, 1: magnetic field of an MHD run."""
+        if isinstance(uhat, np.ndarray):
+            uhat = np.ascontiguousarray(uhat, dtype=np.complex128)
+        nat.ns_set_field(self.ctx, run, field, uhat)
+
+    def get_field(self, field: int, run: int = 0, out=None):
+        n = self.n(run)
+        if out is None:
+            out = np.empty((3, n, n, n // 2 + 1), dtype=np.complex128)
+        nat.ns_get_field(self.ctx, run, field, out)
+        return out
+
+    def field_spectrum(self, field: int, run: int = 0):
+        return nat.ns_field_spectrum(self.ctx, run, field, self.n(run))
 
     def step(self, nsteps: int = 1) -> None:
         nat.ns_step(self.ctx, nsteps)
