@@ -91,8 +91,12 @@ typedef struct {
                           joins the state, j = curl b, the Lorentz force
                           j x b joins u x w, and db/dt = curl(u x b) +
                           eta lap b; b(k = 0) is a constant mean field.
-                          A context with an MHD run uses the plain form in
-                          either precision.  0: Navier-Stokes. */
+                          FP32 MHD runs use the fused form, unless one of
+                          the context's MHD runs has an N without a
+                          compiled fused MHD kernel (N other than 32, 64,
+                          96, 128, 192, 256, 384, 512, 768, 1024): then the
+                          context uses the plain FP32 form.  0:
+                          Navier-Stokes. */
 } ns_run_params;
 
 /* Create a context for nruns independent runs (an ensemble when nruns > 1;

@@ -64,7 +64,7 @@ struct ns_ctx {
     int spec_cap = 0;
     void *staging = nullptr;
     size_t staging_bytes = 0;
-    bool any_mhd = false;            // an MHD run puts the context on the plain form
+    bool mhd_plain = false;          // an MHD run of a size without a compiled fused MHD kernel
     cudaGraphExec_t graph = nullptr;
     char last_error[256] = {0};
 };
@@ -340,7 +340,7 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
     return NS_OK;
 }
 
-bool use_fused(const ns_ctx *c) { return c->prec == NS_FP32 && fused_enabled() && !c->any_mhd; }
+bool use_fused(const ns_ctx *c) { return c->prec == NS_FP32 && fused_enabled() && !c->mhd_plain; }
 
 // One RK2 step of every run of the context: one batched sequence of launches
 // per group of the fused form, or the plain sequence per run.
@@ -443,9 +443,9 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
         char tune[512];
         fused_describe(g, tune, sizeof(tune));
         snprintf(out, len,
-                 "{\"form\": \"fused FP32\", \"n\": %d, \"K\": %d, \"state_modes\": %ld, "
-                 "\"runs_in_group\": %d, \"passes\": %s}",
-                 r.n, g.K, 3 * g.M, g.nr, tune);
+                 "{\"form\": \"fused FP32\", \"equations\": \"%s\", \"n\": %d, \"K\": %d, "
+                 "\"state_modes\": %ld, \"runs_in_group\": %d, \"passes\": %s}",
+                 g.mhd ? "MHD" : "Navier-Stokes", r.n, g.K, (g.mhd ? 6 : 3) * g.M, g.nr, tune);
     } else {
         snprintf(out, len, "{\"form\": \"plain %s\", \"equations\": \"%s\", \"n\": %d, \"cols_per_cta\": %d}",
                  c->prec == NS_FP64 ? "FP64" : "FP32", r.p.mhd ? "MHD" : "Navier-Stokes", r.n,
@@ -471,7 +471,8 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
     if (!c) return NS_ERR_OOM;
     c->prec = prec;
     c->stream = (cudaStream_t)cuda_stream;
-    for (int i = 0; i < nruns; i++) c->any_mhd = c->any_mhd || runs[i].mhd;
+    for (int i = 0; i < nruns; i++)
+        if (runs[i].mhd && !fused_mhd_supported(runs[i].n)) c->mhd_plain = true;
     ns_status st = NS_OK;
     auto bail = [&](ns_status s) {
         ns_destroy(c);
@@ -505,19 +506,21 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
         cudaMemset(r.counter, 0, sizeof(unsigned long long));
     }
     if (use_fused(c)) {
-        // runs of the same N form one group (in order of first appearance)
-        std::vector<int> order;
-        std::map<int, std::vector<int>> members;
+        // runs of the same N and equations form one group (in order of first
+        // appearance); an MHD group carries a magnetic block beside the velocity
+        std::vector<std::pair<int, int>> order;
+        std::map<std::pair<int, int>, std::vector<int>> members;
         for (int i = 0; i < nruns; i++) {
-            if (!members.count(c->runs[i].n)) order.push_back(c->runs[i].n);
-            members[c->runs[i].n].push_back(i);
+            const std::pair<int, int> key(c->runs[i].n, c->runs[i].p.mhd);
+            if (!members.count(key)) order.push_back(key);
+            members[key].push_back(i);
         }
         c->groups.resize(order.size());
         for (size_t gi = 0; gi < order.size(); gi++) {
             std::vector<ns_run_params> ps;
             for (int i : members[order[gi]]) ps.push_back(c->runs[i].p);
             FftRes *f;
-            if ((st = get_fft(c, order[gi], &f)) != NS_OK) return bail(st);
+            if ((st = get_fft(c, order[gi].first, &f)) != NS_OK) return bail(st);
             e = fused_alloc(c->groups[gi], ps, (const float2 *)f->tw, kSeriesCap, c->stream);
             if (e != cudaSuccess) return bail(fail_cuda(nullptr, e));
             const std::vector<int> &mem = members[order[gi]];
@@ -570,7 +573,7 @@ ns_status ns_set_field(ns_ctx *c, int run, int field, const void *uhat, int on_d
             ns_status s2 = ensure_staging(c, kStageChunk);
             if (s2 != NS_OK) return s2;
         }
-        cudaError_t e = fused_set_state(c->groups[r.group], r.gidx, (const double2 *)uhat, on_device,
+        cudaError_t e = fused_set_state(c->groups[r.group], r.gidx, field, (const double2 *)uhat, on_device,
                                         c->staging, kStageChunk, c->stream);
         if (e != cudaSuccess) return fail_cuda(c, e);
         return NS_OK;
@@ -594,7 +597,7 @@ ns_status ns_get_field(ns_ctx *c, int run, int field, void *uhat, int on_device)
             ns_status s2 = ensure_staging(c, kStageChunk);
             if (s2 != NS_OK) return s2;
         }
-        cudaError_t e = fused_get_state(c->groups[r.group], r.gidx, (double2 *)uhat, on_device,
+        cudaError_t e = fused_get_state(c->groups[r.group], r.gidx, field, (double2 *)uhat, on_device,
                                         c->staging, kStageChunk, c->stream);
         if (e != cudaSuccess) return fail_cuda(c, e);
     } else {
@@ -680,7 +683,7 @@ ns_status ns_field_spectrum(ns_ctx *c, int run, int field, double *spec, int nbi
     const int nb = ns_nbins(r.n);
     const long off = (long)field * 3 * r.M;
     if (use_fused(c))
-        NS_CK(fused_spectrum(c->groups[r.group], r.gidx, nb, c->spec, c->ens, c->stream));
+        NS_CK(fused_spectrum(c->groups[r.group], r.gidx, field, nb, c->spec, c->ens, c->stream));
     else if (c->prec == NS_FP64)
         NS_CK(plain_spectrum<double>((const double2 *)r.un + off, r.n, nb, c->spec, c->ens, c->stream));
     else

@@ -541,6 +541,75 @@ static cudaError_t run_pass(FusedRun &f, int pass, const PassCfg &cfg, const FzP
     return launch_strided(k, ps, cfg.pl, f.tw, cfg.ct, f.nr, s);
 }
 
+// Induction update of the MHD form's magnetic block: N_b = i k x nb / N^3
+// (nb the transform of u x b; the cubic rule is the compact layout, the
+// spherical one a mask), then the IF-RK2 stage with exp(-eta k^2 dt); the
+// mean field b(k = 0) has N_b = 0 and factor 1.
+__global__ void __launch_bounds__(256)
+k_fused_update_b(float2 *__restrict__ b, float2 *__restrict__ b1, const float2 *__restrict__ nb,
+                 const float *__restrict__ etab, const FzRunParams *__restrict__ rp, FzUpdate u) {
+    const long M = u.M;
+    const int run = blockIdx.y;
+    b += run * 3 * M;
+    b1 += run * 3 * M;
+    nb += run * 3 * M;
+    etab += (long)run * u.nk2;
+    const FzRunParams q = rp[run];
+    const float inv = (float)(1.0 / ((double)u.n * u.n * u.n));
+    const bool two = u.stage == 2;
+    float2 *dst = two ? b : b1;
+    const unsigned Mz = (unsigned)u.Mz, Mx = (unsigned)u.Mx;
+    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+        const float2 v0 = nb[m], v1 = nb[M + m], v2 = nb[2 * M + m];
+        const float2 c0 = b[m], c1 = b[M + m], c2 = b[2 * M + m];
+        const float2 z = make_float2(0.f, 0.f);
+        const float2 d0 = two ? b1[m] : z, d1 = two ? b1[M + m] : z, d2 = two ? b1[2 * M + m] : z;
+        const unsigned row = (unsigned)m / Mz;
+        const int kz = (int)((unsigned)m - row * Mz);
+        const int ky = fz_compact_signed((int)(row % Mx), u.Mx, u.K);
+        const int kx = fz_compact_signed((int)(row / Mx), u.Mx, u.K);
+        const int k2 = kx * kx + ky * ky + kz * kz;
+        float2 o0 = z, o1 = z, o2 = z;
+        if (!(q.dealias == 1 && 9L * k2 >= (long)u.n * u.n)) {
+            const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz;
+            const float2 vx = cscale(v0, inv), vy = cscale(v1, inv), vz = cscale(v2, inv);
+            const float2 nx = cmul_i<1>(csub(cscale(vz, fky), cscale(vy, fkz)));   // i k x v
+            const float2 ny = cmul_i<1>(csub(cscale(vx, fkz), cscale(vz, fkx)));
+            const float2 nz = cmul_i<1>(csub(cscale(vy, fkx), cscale(vx, fky)));
+            const float e = etab[k2];
+            if (!two) {
+                o0 = cscale(cadd(c0, cscale(nx, q.dt)), e);
+                o1 = cscale(cadd(c1, cscale(ny, q.dt)), e);
+                o2 = cscale(cadd(c2, cscale(nz, q.dt)), e);
+            } else {
+                const float he = 0.5f * e;
+                o0 = cadd(cscale(c0, he), cscale(cadd(d0, cscale(nx, q.dt)), 0.5f));
+                o1 = cadd(cscale(c1, he), cscale(cadd(d1, cscale(ny, q.dt)), 0.5f));
+                o2 = cadd(cscale(c2, he), cscale(cadd(d2, cscale(nz, q.dt)), 0.5f));
+            }
+        }
+        dst[m] = o0;
+        dst[M + m] = o1;
+        dst[2 * M + m] = o2;
+    }
+}
+
+// MHD pass C: E elements per thread, wpb warps per CTA.
+static cudaError_t launch_zm(FusedRun &f, int E, int wpb, cudaStream_t s) {
+    ZctKernel z;
+    if (!zrm_lookup(f.n, E, wpb, &z) || f.Mz != (f.n - 1) / 3 + 1) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(z.k, z.smem);
+    if (e != cudaSuccess) return e;
+    long nlines = (long)f.n * f.n;
+    const long blocks = (nlines + z.lines_per_block - 1) / z.lines_per_block;
+    float2 *bu = f.bbuf, *bb = f.bbuf + f.blk_B;
+    long fs = (long)f.n * f.n * f.Mz;
+    long brun = f.sB;
+    const float2 *tw = f.tw;
+    void *args[] = {(void *)&bu, (void *)&bb, (void *)&fs, (void *)&nlines, (void *)&brun, (void *)&tw};
+    return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem, s);
+}
+
 // The separate update kernel, u.nparts blocks (partials) per run.
 static cudaError_t launch_update_n(FusedRun &f, const FzUpdate &u, cudaStream_t s) {
     k_fused_update<<<dim3(u.nparts, f.nr), 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, f.rp, u, f.part);
@@ -567,6 +636,26 @@ static cudaError_t launch_eu(FusedRun &f, int E, int ct, int stage, cudaStream_t
     void *args[] = {(void *)&din, (void *)&a, (void *)&a1, (void *)&etab, (void *)&rp,
                     (void *)&u, (void *)&tw, (void *)&part};
     return cudaLaunchKernel(z.k, dim3((unsigned)tiles, (unsigned)f.nr), dim3(z.threads), args, z.smem, s);
+}
+
+template <class F> static float time_launch(F launch, cudaStream_t s, int reps);
+
+// Fastest compiled MHD pass-C kernel for the group, timed on its own buffers.
+static cudaError_t tune_zm(FusedRun &f, cudaStream_t s) {
+    float best = -1.f;
+    const int Es[] = {16, 12, 8, 6};
+    for (int E : Es)
+        for (int wpb = 1; wpb <= 2; wpb++) {
+            ZctKernel z;
+            if (!zrm_lookup(f.n, E, wpb, &z)) continue;
+            const float ms = time_launch([&]() { return launch_zm(f, E, wpb, s); }, s, 3);
+            if (ms > 0.f && (best < 0.f || ms < best)) {
+                best = ms;
+                f.zm_E = E;
+                f.zm_wpb = wpb;
+            }
+        }
+    return best < 0.f ? cudaErrorInvalidValue : cudaSuccess;
 }
 
 // ---------------------------------------------------------------- autotuner
@@ -841,14 +930,21 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     f.sA = 6L * f.Mx * f.n * f.Mz;          // also holds D (3 fields)
     f.sB = 6L * f.n * f.n * f.Mz;           // also holds C (3 fields)
     const long S3 = 3 * f.M, nr = f.nr;
+    f.mhd = runs[0].mhd != 0;
+    for (const ns_run_params &q : runs)
+        if ((q.mhd != 0) != f.mhd) return cudaErrorInvalidValue;
+    const int nb = f.mhd ? 2 : 1;            // blocks: velocity (and magnetic)
+    f.blk_s = nr * S3;
+    f.blk_A = nr * f.sA;
+    f.blk_B = nr * f.sB;
     cudaError_t e;
-    if ((e = cudaMalloc(&f.a, nr * S3 * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.a1, nr * S3 * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.nl, nr * S3 * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.abuf, nr * f.sA * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.bbuf, nr * f.sB * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(f.a, 0, nr * S3 * sizeof(float2), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(f.a1, 0, nr * S3 * sizeof(float2), s)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.a, nb * nr * S3 * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.a1, nb * nr * S3 * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.nl, nb * nr * S3 * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.abuf, nb * nr * f.sA * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&f.bbuf, nb * nr * f.sB * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(f.a, 0, nb * nr * S3 * sizeof(float2), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(f.a1, 0, nb * nr * S3 * sizeof(float2), s)) != cudaSuccess) return e;
     // factor tables exp(-nu k^2 dt) in FP64, rounded once, and per-run parameters
     f.nk2 = 3 * f.K * f.K + 1;
     std::vector<float> h((size_t)nr * f.nk2);
@@ -861,6 +957,15 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     if ((e = cudaMalloc(&f.etab, h.size() * sizeof(float))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(f.etab, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
+    if (f.mhd) {   // exp(-eta k^2 dt) per run
+        for (long r = 0; r < nr; r++)
+            for (int k2 = 0; k2 < f.nk2; k2++)
+                h[r * f.nk2 + k2] = (float)exp(-runs[r].eta * (double)k2 * runs[r].dt);
+        if ((e = cudaMalloc(&f.etab_b, h.size() * sizeof(float))) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(f.etab_b, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return e;
+    }
     if ((e = cudaMalloc(&f.rp, nr * sizeof(FzRunParams))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(f.rp, hp.data(), nr * sizeof(FzRunParams), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
@@ -889,6 +994,11 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
             f.eu_E = E;
             f.eu_ct = ct;
         }
+    }
+    if (f.mhd) {
+        f.eu_E = f.eu_ct = 0;   // the magnetic block has its own update
+        cudaError_t e3 = tune_zm(f, s);
+        if (e3 != cudaSuccess) return e3;
     }
     f.nparts = f.eu_E ? (int)eu_tiles(f, f.eu_ct) : f.nparts_upd;
     // Diagnostic override of the pass-C kernel, NS_FORCE_PASS_C="kind,E,tile"
@@ -923,11 +1033,11 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
 }
 
 void fused_free(FusedRun &f) {
-    void *ps[] = {f.a, f.a1, f.nl, f.abuf, f.bbuf, f.etab, f.rp, f.part, f.series, f.counter};
+    void *ps[] = {f.a, f.a1, f.nl, f.abuf, f.bbuf, f.etab, f.etab_b, f.rp, f.part, f.series, f.counter};
     for (void *p : ps)
         if (p) cudaFree(p);
     f.a = f.a1 = f.nl = f.abuf = f.bbuf = nullptr;
-    f.etab = nullptr;
+    f.etab = f.etab_b = nullptr;
     f.rp = nullptr;
     f.part = f.series = nullptr;
     f.counter = nullptr;
@@ -943,7 +1053,46 @@ static cudaError_t launch_energy_final(FusedRun &f, int *flags, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+// The same pass on the magnetic block: input and output pointers shifted by
+// the blocks' offsets.
+static FzPass mag(FzPass p, long in_off, long out_off) {
+    p.in += in_off;
+    p.out += out_off;
+    return p;
+}
+
+// One RK2 step of an MHD group: passes A, B on both blocks (u, w and b, j),
+// the MHD pass C, passes D, E on both blocks, then the velocity update (with
+// its energy partials) and the induction update.
+static cudaError_t fused_step_mhd(FusedRun &f, int *flags, cudaStream_t s, Tracer *tr) {
+    cudaError_t e;
+    for (int stage = 1; stage <= 2; stage++) {
+        FzPass A, B, D, Ep;
+        pass_descs(f, stage == 1 ? f.a : f.a1, A, B, D, Ep);
+        const FzPass Am = mag(A, f.blk_s, f.blk_A), Bm = mag(B, f.blk_A, f.blk_B),
+                     Dm = mag(D, f.blk_B, f.blk_A), Em = mag(Ep, f.blk_A, f.blk_s);
+        if ((e = NSK_TIMED(tr, "fused_A_x_inverse_curl", run_pass(f, 0, f.sp[0], A, s))) != cudaSuccess) return e;
+        if ((e = NSK_TIMED(tr, "fused_A_x_inverse_curl", run_pass(f, 0, f.sp[0], Am, s))) != cudaSuccess) return e;
+        if ((e = NSK_TIMED(tr, "fused_B_y_inverse", run_pass(f, 1, f.sp[1], B, s))) != cudaSuccess) return e;
+        if ((e = NSK_TIMED(tr, "fused_B_y_inverse", run_pass(f, 1, f.sp[1], Bm, s))) != cudaSuccess) return e;
+        if ((e = NSK_TIMED(tr, "fused_C_z_mhd", launch_zm(f, f.zm_E, f.zm_wpb, s))) != cudaSuccess) return e;
+        if ((e = NSK_TIMED(tr, "fused_D_y_forward", run_pass(f, 2, f.sp[2], D, s))) != cudaSuccess) return e;
+        if ((e = NSK_TIMED(tr, "fused_D_y_forward", run_pass(f, 2, f.sp[2], Dm, s))) != cudaSuccess) return e;
+        if ((e = NSK_TIMED(tr, "fused_E_x_forward", run_pass(f, 3, f.sp[3], Ep, s))) != cudaSuccess) return e;
+        if ((e = NSK_TIMED(tr, "fused_E_x_forward", run_pass(f, 3, f.sp[3], Em, s))) != cudaSuccess) return e;
+        FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.M, f.nk2, f.nparts};
+        if ((e = NSK_TIMED(tr, "fused_update", launch_update(f, u, s))) != cudaSuccess) return e;
+        e = NSK_TIMED(tr, "fused_update_b",
+                      (k_fused_update_b<<<dim3(f.nparts_upd, f.nr), 256, 0, s>>>(
+                           f.a + f.blk_s, f.a1 + f.blk_s, f.nl + f.blk_s, f.etab_b, f.rp, u),
+                       cudaGetLastError()));
+        if (e != cudaSuccess) return e;
+    }
+    return NSK_TIMED(tr, "energy_final", launch_energy_final(f, flags, s));
+}
+
 cudaError_t fused_step(FusedRun &f, int *flags, cudaStream_t s, Tracer *tr) {
+    if (f.mhd) return fused_step_mhd(f, flags, s, tr);
     cudaError_t e;
     for (int stage = 1; stage <= 2; stage++) {
         FzPass A, B, D, Ep;
@@ -981,6 +1130,9 @@ int fused_describe(const FusedRun &f, char *out, int len) {
                                           : "runtime length",
                       f.sp[i].pl.E,
                       f.sp[i].ct);
+    if (w < len && f.mhd)
+        w += snprintf(out + w, len - w, "\"C_z_mhd\": {\"E\": %d, \"warps_per_cta\": %d}, ", f.zm_E,
+                      f.zm_wpb);
     if (w < len && f.eu_E)
         w += snprintf(out + w, len - w, "\"E_fused_with_update\": {\"E\": %d, \"cols_per_cta\": %d}, ",
                       f.eu_E, f.eu_ct);
@@ -1003,12 +1155,13 @@ int fused_describe(const FusedRun &f, char *out, int len) {
     return w;
 }
 
-cudaError_t fused_set_state(FusedRun &f, int run, const double2 *src, int on_device, void *staging,
+cudaError_t fused_set_state(FusedRun &f, int run, int field, const double2 *src, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s) {
     const int n = f.n, nh = n / 2 + 1;
     const long plane = (long)n * nh, M = (long)n * plane;
     const int pc = on_device ? n : (int)std::max<size_t>(1, staging_bytes / (plane * sizeof(double2)));
-    float2 *a = f.a + (long)run * 3 * f.M;
+    if (field != 0 && !(field == 1 && f.mhd)) return cudaErrorInvalidValue;
+    float2 *a = f.a + field * f.blk_s + (long)run * 3 * f.M;
     const int dealias = f.p[run].dealias;
     cudaError_t e;
     if ((e = cudaMemsetAsync(a, 0, 3 * f.M * sizeof(float2), s)) != cudaSuccess) return e;
@@ -1035,12 +1188,13 @@ cudaError_t fused_set_state(FusedRun &f, int run, const double2 *src, int on_dev
     return cudaSuccess;
 }
 
-cudaError_t fused_get_state(FusedRun &f, int run, double2 *dst, int on_device, void *staging,
+cudaError_t fused_get_state(FusedRun &f, int run, int field, double2 *dst, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s) {
     const int n = f.n, nh = n / 2 + 1;
     const long plane = (long)n * nh, M = (long)n * plane;
     const int pc = on_device ? n : (int)std::max<size_t>(1, staging_bytes / (plane * sizeof(double2)));
-    const float2 *a = f.a + (long)run * 3 * f.M;
+    if (field != 0 && !(field == 1 && f.mhd)) return cudaErrorInvalidValue;
+    const float2 *a = f.a + field * f.blk_s + (long)run * 3 * f.M;
     cudaError_t e;
     for (int c = 0; c < 3; c++) {
         for (int kx0 = 0; kx0 < n; kx0 += pc) {
@@ -1062,8 +1216,10 @@ cudaError_t fused_get_state(FusedRun &f, int run, double2 *dst, int on_device, v
     return cudaSuccess;
 }
 
-cudaError_t fused_spectrum(FusedRun &f, int run, int nbins, double *spec, double *ens, cudaStream_t s) {
-    CompactAcc acc{f.a + (long)run * 3 * f.M, f.K, f.Mx, f.Mz, f.M};
+cudaError_t fused_spectrum(FusedRun &f, int run, int field, int nbins, double *spec, double *ens,
+                           cudaStream_t s) {
+    if (field != 0 && !(field == 1 && f.mhd)) return cudaErrorInvalidValue;
+    CompactAcc acc{f.a + field * f.blk_s + (long)run * 3 * f.M, f.K, f.Mx, f.Mz, f.M};
     k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, f.n, nbins, spec, ens);
     return cudaGetLastError();
 }

@@ -32,6 +32,10 @@ bool zct_lookup(int N, int E, int wpb, ZctKernel *out);
 // shared memory (0, 1: u_x, 2: u_x and u_y).
 constexpr int ZR_PARK = 8;
 bool zr_lookup(int N, int E, int tile, ZctKernel *out);
+// Pass C of the MHD form (fused_zm.cu): E elements per thread, wpb warps per CTA.
+bool zrm_lookup(int N, int E, int wpb, ZctKernel *out);
+// Whether grid size N has a compiled MHD pass C (else MHD runs use the plain form).
+bool fused_mhd_supported(int N);
 
 // A strided-pass kernel specialised for one (N, E, CT) shape (fused_s*.cu).
 struct FzsKernel {
@@ -76,6 +80,13 @@ struct FusedRun {
     PassCfg sp[4];               // passes A, B, D, E (chosen by the autotuner)
     PassCfg zc;                  // pass C
     int eu_E = 0, eu_ct = 0;     // pass E fused with the update (fused_keu.cu); 0: separate kernels
+    // MHD group: a, a1, nl, abuf and bbuf each hold a velocity block (u, w =
+    // curl u) and then a magnetic block (b, j = curl b), both with the
+    // per-run layout of the Navier-Stokes form; blk_* are the block offsets.
+    bool mhd = false;
+    long blk_s = 0, blk_A = 0, blk_B = 0;
+    float *etab_b = nullptr;     // exp(-eta k^2 dt) by integer k^2       [nr][nk2]
+    int zm_E = 0, zm_wpb = 0;    // MHD pass C (fused_zm.cu)
     int nparts_upd = 0;          // energy partials per run of the separate update kernel
     const float2 *tw = nullptr;  // exp(-2 pi i t / n), t < n (owned by the context)
     float2 *a = nullptr;         // state                       [nr][3][M]
@@ -99,15 +110,16 @@ bool fused_enabled();
 cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, const float2 *tw,
                         int series_cap, cudaStream_t s);
 void fused_free(FusedRun &f);
-cudaError_t fused_set_state(FusedRun &f, int run, const double2 *src, int on_device, void *staging,
+cudaError_t fused_set_state(FusedRun &f, int run, int field, const double2 *src, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s);
-cudaError_t fused_get_state(FusedRun &f, int run, double2 *dst, int on_device, void *staging,
+cudaError_t fused_get_state(FusedRun &f, int run, int field, double2 *dst, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s);
 // One RK2 step of every run of the group.
 cudaError_t fused_step(FusedRun &f, int *flags, cudaStream_t s, Tracer *tr);
 // JSON text describing the chosen per-pass configuration; returns its length.
 int fused_describe(const FusedRun &f, char *out, int len);
-cudaError_t fused_spectrum(FusedRun &f, int run, int nbins, double *spec, double *ens, cudaStream_t s);
+cudaError_t fused_spectrum(FusedRun &f, int run, int field, int nbins, double *spec, double *ens,
+                           cudaStream_t s);
 cudaError_t fused_helicity(FusedRun &f, int run, int nbins, double *spec, double *aux, cudaStream_t s);
 
 }  // namespace nsk

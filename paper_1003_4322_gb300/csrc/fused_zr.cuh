@@ -218,6 +218,165 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     forward_store(py, 1);
 }
 
+// Pass C of the MHD form (Alfven units): the group's B buffers form two
+// blocks, bu = (u, w = curl u) and bb = (b, j = curl b), six fields each.
+// Per (y, x) line: the c2r of the twelve fields, u x b written over b's
+// slots (the induction term) and u x w + j x b over u's slots (the velocity
+// term), as r2c of the kept kz.  u and b wait in thread-private shared
+// memory; the products accumulate in registers while w and j stream through.
+template <int N, int E, int WPB>
+__global__ void __launch_bounds__(32 * WPB)
+k_fused_zr_mhd(float2 *bu, float2 *bb, long fs, long nlines, long brun, const float2 *__restrict__ tw) {
+    typedef ZrShape<N, E> Z;
+    constexpr int n = Z::n, T = Z::T, LPW = Z::LPW, LS = Z::LS, Mz = Z::Mz;
+    bu += blockIdx.y * brun;   // run of the group
+    bb += blockIdx.y * brun;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ll = lane / T, slot = lane % T;
+    const int partner = ll * T + (T - slot) % T;
+    const long line = ((long)blockIdx.x * WPB + warp) * LPW + ll;
+    const bool valid = line < nlines;
+    float2 *L = sm + (long)(warp * LPW + ll) * LS;
+    float2 *park = sm + (long)WPB * LPW * LS + (long)warp * 6 * E * 32 + lane;   // u, then b
+    auto pk = [&](int c, int j) -> float2 & { return park[(c * E + j) * 32]; };
+    auto sl = [&](int e) -> float2 { return L[ct_skew(e)]; };
+    auto ss = [&](int e, float2 v) { L[ct_skew(e)] = v; };
+
+    CtTwiddles<n, E, N> twr;
+    twr.load(slot, tw);
+    float2 wk[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) wk[j] = __ldg(tw + slot + j * T);
+
+    float2 x[E];
+    auto fetch = [&](const float2 *field) {
+        const float2 *src = field + line * Mz;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            x[j] = make_float2(0.f, 0.f);
+            if (j * T < Mz && valid && k < Mz) x[j] = src[k];
+        }
+    };
+    auto inverse = [&](float2 (&v)[E], const float2 *next) {
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            float2 a0 = x[j];
+            float2 am = make_float2(0.f, 0.f);
+            if ((E - 1 - j) * T < Mz) am = shfl2(x[E - 1 - j], partner);
+            if (slot == 0) am = (j > 0 && (E - j) * T < Mz) ? x[(E - j) % E] : make_float2(0.f, 0.f);
+            if (k == 0) {
+                a0.y = 0.f;
+                am.y = 0.f;
+            }
+            const float2 xc = cconj(am);
+            const float2 wb = cmulc(csub(a0, xc), wk[j]);
+            v[j] = cadd(cadd(a0, xc), cmul_i<1>(wb));
+        }
+        if (next) fetch(next);
+        ct_fft_reg<n, E, +1, N>(v, slot, twr, sl, ss);
+    };
+    auto forward_store = [&](float2 (&v)[E], float2 *field) {
+        ct_fft_reg<n, E, -1, N>(v, slot, twr, sl, ss);
+        float2 *dst = field + line * Mz;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            if (j * T < Mz) {
+                const int k = slot + j * T;
+                float2 zm = shfl2(v[E - 1 - j], partner);
+                if (slot == 0) zm = v[(E - j) % E];
+                const float2 zk = v[j], zc = cconj(zm);
+                const float2 ev = cscale(cadd(zk, zc), 0.5f);
+                const float2 od = cmul_i<-1>(cscale(csub(zk, zc), 0.5f));
+                if (valid && k < Mz) dst[k] = cadd(ev, cmul(od, wk[j]));
+            }
+        }
+    };
+    auto acc = [&](float2 &p, float2 a, float2 b, float sgn) {
+        p = make_float2(p.x + sgn * a.x * b.x, p.y + sgn * a.y * b.y);
+    };
+
+    // the twelve fields in transform order: u, b, w, j
+    const float2 *seq[12] = {bu, bu + fs, bu + 2 * fs, bb, bb + fs, bb + 2 * fs,
+                             bu + 3 * fs, bu + 4 * fs, bu + 5 * fs, bb + 3 * fs, bb + 4 * fs, bb + 5 * fs};
+    float2 V[E];
+    fetch(seq[0]);
+    for (int c = 0; c < 6; c++) {   // u_x, u_y, u_z, b_x, b_y, b_z -> parked
+        inverse(V, seq[c + 1]);
+#pragma unroll
+        for (int j = 0; j < E; j++) pk(c, j) = V[j];
+    }
+    // u x b, component by component, over b's slots
+    for (int c = 0; c < 3; c++) {
+        const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const float2 u1 = pk(c1, j), u2 = pk(c2, j), b1 = pk(3 + c1, j), b2 = pk(3 + c2, j);
+            V[j] = make_float2(u1.x * b2.x - u2.x * b1.x, u1.y * b2.y - u2.y * b1.y);
+        }
+        forward_store(V, bb + c * fs);
+    }
+    // u x w + j x b, with w and j one component at a time
+    float2 P0[E], P1[E], P2[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) P0[j] = P1[j] = P2[j] = make_float2(0.f, 0.f);
+    inverse(V, seq[7]);   // w_x: (u x w)_y += u_z w_x, (u x w)_z -= u_y w_x
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        acc(P1[j], pk(2, j), V[j], 1.f);
+        acc(P2[j], pk(1, j), V[j], -1.f);
+    }
+    inverse(V, seq[8]);   // w_y: (u x w)_z += u_x w_y, (u x w)_x -= u_z w_y
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        acc(P2[j], pk(0, j), V[j], 1.f);
+        acc(P0[j], pk(2, j), V[j], -1.f);
+    }
+    inverse(V, seq[9]);   // w_z: (u x w)_x += u_y w_z, (u x w)_y -= u_x w_z
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        acc(P0[j], pk(1, j), V[j], 1.f);
+        acc(P1[j], pk(0, j), V[j], -1.f);
+    }
+    inverse(V, seq[10]);  // j_x: (j x b)_y -= j_x b_z, (j x b)_z += j_x b_y
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        acc(P1[j], V[j], pk(5, j), -1.f);
+        acc(P2[j], V[j], pk(4, j), 1.f);
+    }
+    inverse(V, seq[11]);  // j_y: (j x b)_x += j_y b_z, (j x b)_z -= j_y b_x
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        acc(P0[j], V[j], pk(5, j), 1.f);
+        acc(P2[j], V[j], pk(3, j), -1.f);
+    }
+    inverse(V, nullptr);  // j_z: (j x b)_x -= j_z b_y, (j x b)_y += j_z b_x
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        acc(P0[j], V[j], pk(4, j), -1.f);
+        acc(P1[j], V[j], pk(3, j), 1.f);
+    }
+    forward_store(P0, bu);
+    forward_store(P1, bu + fs);
+    forward_store(P2, bu + 2 * fs);
+}
+
+template <int N, int E, int WPB> bool zrm_entry(ZctKernel *o) {
+    typedef ZrShape<N, E> Z;
+    if constexpr (!Z::ok) {
+        return false;
+    } else {
+        o->k = (const void *)k_fused_zr_mhd<N, E, WPB>;
+        o->smem = (size_t)WPB * (Z::LPW * Z::LS + 6 * E * 32) * sizeof(float2);
+        o->lines_per_block = WPB * Z::LPW;
+        o->threads = 32 * WPB;
+        return true;
+    }
+}
+
 template <int N, int E, int WPB, int PARK> bool zr_entry(ZctKernel *o) {
     typedef ZrShape<N, E> Z;
     if constexpr (!Z::ok) {

@@ -1,4 +1,4 @@
-"""MHD in the plain form (both precisions), through the C ABI, against the
+"""MHD in the plain FP64 and the fused FP32 form, through the C ABI, against the
 oracle (the magnetohydrodynamic equations of the same code, Sec. 5; Alfven
 units, state [u; b]) and against exact solutions."""
 import math
@@ -81,8 +81,9 @@ def test_alfven_wave_exact_on_gpu(ns, prec):
 
 
 def test_force_free_field_and_form(ns):
-    """u = 0, b = ABC: exact decay exp(-eta t); an FP32 MHD context runs the
-    plain FP32 form; field 1 of a Navier-Stokes run is an argument error."""
+    """u = 0, b = ABC: exact decay exp(-eta t); FP64 runs the plain form and
+    FP32 the fused form (velocity and magnetic blocks); field 1 of a
+    Navier-Stokes run is an argument error."""
     from paper_1003_4322_gb300 import _native as nat
     from paper_1003_4322_gb300.solver import Solver
     n, eta, dt, steps = 32, 0.02, 0.05, 6
@@ -91,7 +92,8 @@ def test_force_free_field_and_form(ns):
     for prec, tol, utol in (("fp64", 1e-14, 1e-28), ("fp32", 1e-6, 1e-14)):
         with Solver([dict(n=n, nu=0.01, eta=eta, dt=dt, mhd=1)], prec=prec) as s:
             d = nat.ns_describe_run(s.ctx, 0)
-            assert d["equations"] == "MHD" and d["form"].startswith("plain")
+            assert d["equations"] == "MHD"
+            assert d["form"] == ("plain FP64" if prec == "fp64" else "fused FP32")
             s.set_field(1, inputs.abc_state(n))
             s.step(steps)
             Eb, _, _ = s.field_spectrum(1)
@@ -103,3 +105,27 @@ def test_force_free_field_and_form(ns):
         assert e.value.status == nat.NS_ERR_ARG
         with pytest.raises(nat.NsError):
             s.field_spectrum(1)
+
+
+def test_mhd_group_with_navier_stokes_run(ns):
+    """One fused context: two MHD runs of one size with different eta (one
+    group, one launch per pass on both blocks) and a Navier-Stokes run of the
+    same size (its own group); every member matches its oracle run."""
+    from paper_1003_4322_gb300.solver import Solver
+    n = 32
+    runs = [dict(n=n, nu=0.01, eta=0.01, dt=1e-3, mhd=1),
+            dict(n=n, nu=0.01, eta=0.03, dt=1e-3, force_amp=0.5, force_k=3, mhd=1),
+            dict(n=n, nu=0.01, dt=1e-3)]
+    u0, b0 = _mhd_state(n, 61)
+    with Solver(runs, prec="fp32") as s:
+        for r in range(3):
+            s.set_field(0, u0, run=r)
+        for r in range(2):
+            s.set_field(1, b0, run=r)
+        s.step(3)
+        got = [(s.get_field(0, run=r), s.get_field(1, run=r) if r < 2 else None) for r in range(3)]
+    for r in range(2):
+        ru, rb = _oracle(runs[r], u0, b0, 3)
+        assert rel_l2(got[r][0], ru) < TOL["fp32"] and rel_l2(got[r][1], rb) < TOL["fp32"]
+    ref = oracle.step(u0, oracle.Params(n=n, nu=0.01, dt=1e-3), 3)
+    assert rel_l2(got[2][0], ref) < TOL["fp32"]
