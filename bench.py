@@ -192,6 +192,10 @@ def kernel_model(name, n, prec):
         return (3 * Ax + 3 * S) * cb, 3 * Mx * Mz * f_line
     if name == "fused_update":
         return 10.5 * S * cb, 3 * S * 30   # reads N, a (and a1 at stage 2), writes 3
+    if name == "fused_C_z_mhd":               # reads u, w, b, j; writes u x w + j x b, u x b
+        return (12 * Bx + 6 * Bx) * cb, n * n * (18 * f_zline + 30 * n)
+    if name == "fused_update_b":              # reads N_b, b (and b1 at stage 2), writes 3
+        return 10.5 * S * cb, 3 * S * 25
     if name == "fused_E_x_forward_update":   # reads D, a (and a1 at stage 2), writes 3
         return (3 * Ax + 7.5 * S) * cb, 3 * Mx * Mz * f_line + 3 * S * 30
     return 0, 0
@@ -312,8 +316,7 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
     # plain form: one launch per run
     sizes = sizes or [w["n"]]
     per_size = [kernel_model(name, n, prec) for n in sizes]
-    plain = prec == "fp64" or w.get("mhd")
-    launches_per_pass = len(sizes) if plain else len(set(sizes))
+    launches_per_pass = len(sizes) if prec == "fp64" else len(set(sizes))
     bytes_ = sum(b for b, _ in per_size) / launches_per_pass
     flops = sum(f for _, f in per_size) / launches_per_pass
     gbs = bytes_ / (per_launch_ms * 1e-3) / 1e9
