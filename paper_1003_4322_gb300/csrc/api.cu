@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <new>
 #include <vector>
@@ -23,9 +24,20 @@ namespace {
 
 const int kSeriesCap = 4096;
 
+// Launch shapes of the plain form's transforms: radix splits of the x/y
+// passes (inverse, forward) and of the z passes, columns per CTA of the x/y
+// passes.  Defaults from make_plan / default_ct, replaced by the plain-form
+// autotuner's choice (tune_plain) once per (N, precision) in the process.
+struct PlainPlans {
+    Plan inv{}, fwd{}, zc{}, zr{};
+    int ct_inv = 0, ct_fwd = 0;
+    bool tuned = false;
+};
+
 struct FftRes {
     int n = 0;
     Plan plN{}, plH{};
+    PlainPlans pp;
     void *tw = nullptr;       // Cx<T>[n], exp(-2 pi i t / n)
     void *scratch = nullptr;  // one half-layout field (c2r)
 };
@@ -108,6 +120,9 @@ ns_status get_fft(ns_ctx *c, int n, FftRes **out) {
     FftRes f;
     f.n = n;
     if (!make_plan(n, &f.plN) || !make_plan(n / 2, &f.plH)) return NS_ERR_UNSUPPORTED_N;
+    f.pp.inv = f.pp.fwd = f.plN;
+    f.pp.zc = f.pp.zr = f.plH;
+    f.pp.ct_inv = f.pp.ct_fwd = default_ct(c->prec == NS_FP64 ? 16 : 8, n);
     cudaError_t e;
     if (c->prec == NS_FP64) f.tw = make_twiddles<double>(n, &e);
     else f.tw = make_twiddles<float>(n, &e);
@@ -130,31 +145,33 @@ ns_status ensure_scratch(ns_ctx *c, FftRes *f) {
 // (tmp -> out).  tmp holds ncomp_tmp fields; components go in batches.
 template <typename T>
 cudaError_t c2r_batch(const typename Cx<T>::type *in, typename Cx<T>::type *tmp, T *out, int n,
-                      int ncomp, const FftRes &f, int ct, cudaStream_t s, Tracer *tr = nullptr) {
+                      int ncomp, const FftRes &f, cudaStream_t s, Tracer *tr = nullptr) {
     const long nh = n / 2 + 1, plane = (long)n * nh, M = (long)n * plane;
     const typename Cx<T>::type *tw = (const typename Cx<T>::type *)f.tw;
+    const PlainPlans &q = f.pp;
     cudaError_t e = NSK_TIMED(tr, "fft_x_inverse",
-                              fft_strided<T>(in, tmp, plane, plane, M, M, ncomp, +1, f.plN, tw, n, ct, s));
+                              fft_strided<T>(in, tmp, plane, plane, M, M, ncomp, +1, q.inv, tw, n, q.ct_inv, s));
     if (e != cudaSuccess) return e;
     e = NSK_TIMED(tr, "fft_y_inverse",
-                  fft_strided<T>(tmp, tmp, nh, nh, plane, plane, ncomp * n, +1, f.plN, tw, n, ct, s));
+                  fft_strided<T>(tmp, tmp, nh, nh, plane, plane, ncomp * n, +1, q.inv, tw, n, q.ct_inv, s));
     if (e != cudaSuccess) return e;
-    return NSK_TIMED(tr, "fft_z_c2r", fft_z_c2r<T>(tmp, out, n, (long)ncomp * n * n, f.plH, tw, s));
+    return NSK_TIMED(tr, "fft_z_c2r", fft_z_c2r<T>(tmp, out, n, (long)ncomp * n * n, q.zc, tw, s));
 }
 
 // r2c of ncomp real fields: z pass (in -> out), y and x passes in place.
 template <typename T>
 cudaError_t r2c_batch(const T *in, typename Cx<T>::type *out, int n, int ncomp, const FftRes &f,
-                      int ct, cudaStream_t s, Tracer *tr = nullptr) {
+                      cudaStream_t s, Tracer *tr = nullptr) {
     const long nh = n / 2 + 1, plane = (long)n * nh, M = (long)n * plane;
     const typename Cx<T>::type *tw = (const typename Cx<T>::type *)f.tw;
-    cudaError_t e = NSK_TIMED(tr, "fft_z_r2c", fft_z_r2c<T>(in, out, n, (long)ncomp * n * n, f.plH, tw, s));
+    const PlainPlans &q = f.pp;
+    cudaError_t e = NSK_TIMED(tr, "fft_z_r2c", fft_z_r2c<T>(in, out, n, (long)ncomp * n * n, q.zr, tw, s));
     if (e != cudaSuccess) return e;
     e = NSK_TIMED(tr, "fft_y_forward",
-                  fft_strided<T>(out, out, nh, nh, plane, plane, ncomp * n, -1, f.plN, tw, n, ct, s));
+                  fft_strided<T>(out, out, nh, nh, plane, plane, ncomp * n, -1, q.fwd, tw, n, q.ct_fwd, s));
     if (e != cudaSuccess) return e;
     return NSK_TIMED(tr, "fft_x_forward",
-                     fft_strided<T>(out, out, plane, plane, M, M, ncomp, -1, f.plN, tw, n, ct, s));
+                     fft_strided<T>(out, out, plane, plane, M, M, ncomp, -1, q.fwd, tw, n, q.ct_fwd, s));
 }
 
 // ---------------------------------------------------------------- state transfer
@@ -270,6 +287,91 @@ ns_status plain_get_state(ns_ctx *c, Run &r, double2 *dst, int on_device, int fi
 
 // ---------------------------------------------------------------- plain step
 
+// Time `launch` after one warm-up: ms per launch over three, or -1.
+template <class F> static float plain_time(F launch, cudaStream_t s) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1.f;
+    }
+    float ms = -1.f;
+    if (launch() == cudaSuccess && cudaEventRecord(a, s) == cudaSuccess) {
+        bool ok = true;
+        for (int i = 0; i < 3 && ok; i++) ok = launch() == cudaSuccess;
+        if (ok && cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+            ms /= 3;
+        else
+            ms = -1.f;
+    }
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+// Plain-form autotuner: for the x/y inverse and forward passes and the z c2r
+// and r2c passes, every radix split with at most four stages (and, for x/y,
+// 2 to 32 columns per CTA within the kernel's thread bound) runs on the run's
+// own buffers; the fastest is kept per (N, precision) for the life of the
+// process.  Where nothing runs, the defaults stay.
+template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
+    typedef typename Cx<T>::type C;
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, PlainPlans> cache;
+    const std::pair<int, int> key(r.n, (int)sizeof(T));
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            f->pp = it->second;
+            return NS_OK;
+        }
+    }
+    if (f->pp.tuned) return NS_OK;
+    const int n = r.n;
+    const long nh = n / 2 + 1, plane = (long)n * nh, M = (long)n * plane, lines = 3L * n * n;
+    const C *tw = (const C *)f->tw;
+    cudaStream_t s = c->stream;
+    C *in = (C *)r.un, *tmp = (C *)r.work, *half = (C *)r.wn;
+    T *phys = (T *)r.phys;
+    const int bound = sizeof(T) == 8 ? 384 : 512;
+    PlainPlans best = f->pp;
+    float bi = -1.f, bf = -1.f, bc = -1.f, br = -1.f;
+    const int Es[] = {16, 12, 9, 8, 6, 4};
+    for (int E : Es) {
+        Plan pl;
+        if (make_plan_e(n, E, &pl) && pl.nst <= 4) {
+            const int Tn = n / E;
+            for (int ct = 2; ct <= 32; ct *= 2) {
+                if (ct * Tn > bound || ct * Tn < 32) continue;
+                const float ti = plain_time([&]() {
+                    return fft_strided<T>(in, tmp, plane, plane, M, M, 3, +1, pl, tw, n, ct, s);
+                }, s);
+                if (ti > 0.f && (bi < 0.f || ti < bi)) { bi = ti; best.inv = pl; best.ct_inv = ct; }
+                const float tf = plain_time([&]() {
+                    return fft_strided<T>(half, half, plane, plane, M, M, 3, -1, pl, tw, n, ct, s);
+                }, s);
+                if (tf > 0.f && (bf < 0.f || tf < bf)) { bf = tf; best.fwd = pl; best.ct_fwd = ct; }
+            }
+        }
+        Plan ph;
+        if (make_plan_e(n / 2, E, &ph) && ph.nst <= 4) {
+            const float tc = plain_time([&]() { return fft_z_c2r<T>(tmp, phys, n, lines, ph, tw, s); }, s);
+            if (tc > 0.f && (bc < 0.f || tc < bc)) { bc = tc; best.zc = ph; }
+            const float tr = plain_time([&]() { return fft_z_r2c<T>(phys, half, n, lines, ph, tw, s); }, s);
+            if (tr > 0.f && (br < 0.f || tr < br)) { br = tr; best.zr = ph; }
+        }
+    }
+    NS_CK(cudaStreamSynchronize(s));
+    best.tuned = true;
+    f->pp = best;
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = best;
+    return NS_OK;
+}
+
 template <typename T> ns_status plain_alloc(ns_ctx *c, Run &r) {
     typedef typename Cx<T>::type C;
     const size_t half = (size_t)r.M * sizeof(C), real = (size_t)r.V * sizeof(T);
@@ -291,7 +393,10 @@ template <typename T> ns_status plain_alloc(ns_ctx *c, Run &r) {
         NS_CK(dalloc(&r.etab_b, nk2 * sizeof(T)));
         NS_CK(cudaMemcpy(r.etab_b, h.data(), nk2 * sizeof(T), cudaMemcpyHostToDevice));
     }
-    return NS_OK;
+    FftRes *f;
+    ns_status st = get_fft(c, r.n, &f);
+    if (st != NS_OK) return st;
+    return tune_plain<T>(c, r, f);
 }
 
 template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tracer *tr) {
@@ -299,7 +404,6 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
     FftRes *f;
     ns_status st = get_fft(c, r.n, &f);
     if (st != NS_OK) return st;
-    const int ct = default_ct(sizeof(C), r.n);
     T *phys = (T *)r.phys;
     const long M3 = 3 * r.M, V3 = 3 * r.V;
     for (int stage = 1; stage <= 2 && r.p.mhd; stage++) {
@@ -309,13 +413,13 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
         C *wj = (C *)r.wn;
         NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, wj, r.n, s)));
         NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src + M3, wj + M3, r.n, s)));
-        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, r.n, 3, *f, ct, s, tr));
-        NS_CK(c2r_batch<T>(wj, (C *)r.work, phys + V3, r.n, 3, *f, ct, s, tr));
-        NS_CK(c2r_batch<T>(src + M3, (C *)r.work, phys + 2 * V3, r.n, 3, *f, ct, s, tr));
-        NS_CK(c2r_batch<T>(wj + M3, (C *)r.work, phys + 3 * V3, r.n, 3, *f, ct, s, tr));
+        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, r.n, 3, *f, s, tr));
+        NS_CK(c2r_batch<T>(wj, (C *)r.work, phys + V3, r.n, 3, *f, s, tr));
+        NS_CK(c2r_batch<T>(src + M3, (C *)r.work, phys + 2 * V3, r.n, 3, *f, s, tr));
+        NS_CK(c2r_batch<T>(wj + M3, (C *)r.work, phys + 3 * V3, r.n, 3, *f, s, tr));
         NS_CK(NSK_TIMED(tr, "cross_mhd", plain_cross_mhd<T>(phys, r.n, s)));
-        NS_CK(r2c_batch<T>(phys, wj, r.n, 3, *f, ct, s, tr));
-        NS_CK(r2c_batch<T>(phys + V3, wj + M3, r.n, 3, *f, ct, s, tr));
+        NS_CK(r2c_batch<T>(phys, wj, r.n, 3, *f, s, tr));
+        NS_CK(r2c_batch<T>(phys + V3, wj + M3, r.n, 3, *f, s, tr));
         UpdateArgs ua{stage, r.p.dt, r.p.force_amp, r.p.force_k, r.p.dealias, r.p.rot};
         NS_CK(NSK_TIMED(tr, "update",
                         plain_update<T>((C *)r.un, (C *)r.u1, (const C *)wj, (const T *)r.etab, r.n, ua, s)));
@@ -326,10 +430,10 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
     for (int stage = 1; stage <= 2 && !r.p.mhd; stage++) {
         C *src = (C *)(stage == 1 ? r.un : r.u1);
         NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, (C *)r.wn, r.n, s)));
-        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, r.n, 3, *f, ct, s, tr));
-        NS_CK(c2r_batch<T>((C *)r.wn, (C *)r.work, phys + 3 * r.V, r.n, 3, *f, ct, s, tr));
+        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, r.n, 3, *f, s, tr));
+        NS_CK(c2r_batch<T>((C *)r.wn, (C *)r.work, phys + 3 * r.V, r.n, 3, *f, s, tr));
         NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, r.n, s)));
-        NS_CK(r2c_batch<T>(phys, (C *)r.wn, r.n, 3, *f, ct, s, tr));
+        NS_CK(r2c_batch<T>(phys, (C *)r.wn, r.n, 3, *f, s, tr));
         UpdateArgs ua{stage, r.p.dt, r.p.force_amp, r.p.force_k, r.p.dealias, r.p.rot};
         NS_CK(NSK_TIMED(tr, "update",
                         plain_update<T>((C *)r.un, (C *)r.u1, (const C *)r.wn, (const T *)r.etab, r.n, ua, s)));
@@ -447,9 +551,14 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
                  "\"state_modes\": %ld, \"runs_in_group\": %d, \"passes\": %s}",
                  g.mhd ? "MHD" : "Navier-Stokes", r.n, g.K, (g.mhd ? 6 : 3) * g.M, g.nr, tune);
     } else {
-        snprintf(out, len, "{\"form\": \"plain %s\", \"equations\": \"%s\", \"n\": %d, \"cols_per_cta\": %d}",
+        const auto it = c->fft.find(r.n);
+        const PlainPlans q = it != c->fft.end() ? it->second.pp : PlainPlans{};
+        snprintf(out, len,
+                 "{\"form\": \"plain %s\", \"equations\": \"%s\", \"n\": %d, \"tuned\": %s, "
+                 "\"xy_inverse\": {\"E\": %d, \"cols_per_cta\": %d}, \"xy_forward\": {\"E\": %d, "
+                 "\"cols_per_cta\": %d}, \"z_c2r\": {\"E\": %d}, \"z_r2c\": {\"E\": %d}}",
                  c->prec == NS_FP64 ? "FP64" : "FP32", r.p.mhd ? "MHD" : "Navier-Stokes", r.n,
-                 default_ct(c->prec == NS_FP64 ? 16 : 8, r.n));
+                 q.tuned ? "true" : "false", q.inv.E, q.ct_inv, q.fwd.E, q.ct_fwd, q.zc.E, q.zr.E);
     }
     return NS_OK;
 }
@@ -631,15 +740,13 @@ ns_status ns_fft_r2c(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
     FftRes *f;
     if ((st = get_fft(c, n, &f)) != NS_OK) return st;
     if (c->prec == NS_FP64) {
-        NS_CK(r2c_batch<double>((const double *)in, (double2 *)out, n, ncomp, *f,
-                                default_ct(sizeof(double2), n), c->stream));
+        NS_CK(r2c_batch<double>((const double *)in, (double2 *)out, n, ncomp, *f, c->stream));
     } else {
         cudaError_t e = cudaSuccess;
         if (std_r2c_fp32((const float *)in, (float2 *)out, n, ncomp, (const float2 *)f->tw, c->stream, &e))
             NS_CK(e);
         else
-            NS_CK(r2c_batch<float>((const float *)in, (float2 *)out, n, ncomp, *f,
-                                   default_ct(sizeof(float2), n), c->stream));
+            NS_CK(r2c_batch<float>((const float *)in, (float2 *)out, n, ncomp, *f, c->stream));
     }
     return NS_OK;
 }
@@ -656,8 +763,7 @@ ns_status ns_fft_c2r(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
     for (int k = 0; k < ncomp; k++) {
         if (c->prec == NS_FP64)
             NS_CK(c2r_batch<double>((const double2 *)in + k * M, (double2 *)f->scratch,
-                                    (double *)out + k * V, n, 1, *f,
-                                    default_ct(sizeof(double2), n), c->stream));
+                                    (double *)out + k * V, n, 1, *f, c->stream));
         else {
             cudaError_t e = cudaSuccess;
             if (std_c2r_fp32((const float2 *)in + k * M, (float2 *)f->scratch, (float *)out + k * V, n,
@@ -665,8 +771,7 @@ ns_status ns_fft_c2r(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
                 NS_CK(e);
             else
                 NS_CK(c2r_batch<float>((const float2 *)in + k * M, (float2 *)f->scratch,
-                                       (float *)out + k * V, n, 1, *f, default_ct(sizeof(float2), n),
-                                       c->stream));
+                                       (float *)out + k * V, n, 1, *f, c->stream));
         }
     }
     return NS_OK;
