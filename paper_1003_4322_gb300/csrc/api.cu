@@ -67,6 +67,11 @@ struct ns_ctx {
     ns_prec prec = NS_FP64;
     cudaStream_t stream = nullptr;   // caller's stream
     cudaStream_t cap = nullptr;      // private stream for graph capture
+    // independent units of a step (fused groups, or plain runs) are captured
+    // on these streams, forked from and joined back to `cap`, so that the
+    // graph runs them concurrently
+    std::vector<cudaStream_t> par;
+    std::vector<cudaEvent_t> fork_join;   // [0]: fork; [1 + i]: join of par[i]
     std::vector<Run> runs;
     std::vector<FusedRun> groups;   // fused form: runs grouped by N
     std::map<int, FftRes> fft;
@@ -463,6 +468,35 @@ ns_status step_all(ns_ctx *c, cudaStream_t s, Tracer *tr) {
     return NS_OK;
 }
 
+// The step with its independent units (fused groups, or plain runs) on the
+// streams of c->par, forked from c->cap and joined back to it: captured, the
+// units become parallel branches of the graph.  Unit u goes to stream
+// u % par.size() (units on one stream stay in order).
+ns_status step_all_forked(ns_ctx *c) {
+    const int P = (int)c->par.size();
+    NS_CK(cudaEventRecord(c->fork_join[0], c->cap));
+    for (int q = 0; q < P; q++) NS_CK(cudaStreamWaitEvent(c->par[q], c->fork_join[0], 0));
+    if (use_fused(c)) {
+        for (size_t g = 0; g < c->groups.size(); g++) {
+            cudaError_t e = fused_step(c->groups[g], c->flags, c->par[g % P], nullptr);
+            if (e != cudaSuccess) return fail_cuda(c, e);
+        }
+    } else {
+        for (size_t i = 0; i < c->runs.size(); i++) {
+            Run &r = c->runs[i];
+            cudaStream_t q = c->par[i % P];
+            ns_status st = c->prec == NS_FP64 ? plain_step<double>(c, r, q, nullptr)
+                                              : plain_step<float>(c, r, q, nullptr);
+            if (st != NS_OK) return st;
+        }
+    }
+    for (int q = 0; q < P; q++) {
+        NS_CK(cudaEventRecord(c->fork_join[1 + q], c->par[q]));
+        NS_CK(cudaStreamWaitEvent(c->cap, c->fork_join[1 + q], 0));
+    }
+    return NS_OK;
+}
+
 ns_status build_graph(ns_ctx *c) {
     if (c->graph) return NS_OK;
     // Resources the step needs must exist before capture (no allocation inside).
@@ -472,7 +506,7 @@ ns_status build_graph(ns_ctx *c) {
         if (st != NS_OK) return st;
     }
     NS_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    ns_status st = step_all(c, c->cap, nullptr);
+    ns_status st = c->par.empty() ? step_all(c, c->cap, nullptr) : step_all_forked(c);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap, &g);
     if (st != NS_OK) {
@@ -648,6 +682,19 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
         (e = dalloc(&c->ens, sizeof(double) * maxbins)) != cudaSuccess)
         return bail(fail_cuda(nullptr, e));
     c->spec_cap = maxbins;
+    // streams for concurrent units of the step graph (ensembles)
+    const size_t units = use_fused(c) ? c->groups.size() : c->runs.size();
+    if (units > 1) {
+        const int P = (int)std::min<size_t>(units, 8);
+        c->par.resize(P, nullptr);
+        c->fork_join.resize(P + 1, nullptr);
+        for (int q = 0; q < P; q++)
+            if ((e = cudaStreamCreateWithFlags(&c->par[q], cudaStreamNonBlocking)) != cudaSuccess)
+                return bail(fail_cuda(nullptr, e));
+        for (int q = 0; q <= P; q++)
+            if ((e = cudaEventCreateWithFlags(&c->fork_join[q], cudaEventDisableTiming)) != cudaSuccess)
+                return bail(fail_cuda(nullptr, e));
+    }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(fail_cuda(nullptr, e));
     *out = c;
     return NS_OK;
@@ -668,6 +715,8 @@ void ns_destroy(ns_ctx *c) {
     if (c->ens) cudaFree(c->ens);
     if (c->staging) cudaFree(c->staging);
     if (c->cap) cudaStreamDestroy(c->cap);
+    for (cudaStream_t q : c->par) cudaStreamDestroy(q);
+    for (cudaEvent_t ev : c->fork_join) cudaEventDestroy(ev);
     delete c;
 }
 
