@@ -24,7 +24,7 @@ SYMBOLS = ("ns_init", "ns_set_state", "ns_get_state", "ns_step", "ns_fft_r2c", "
            "ns_energy_spectrum", "ns_nbins", "ns_series", "ns_series_capacity",
            "ns_kernel_census", "ns_sync", "ns_last_error", "ns_status_str", "ns_destroy",
            "ns_fft_c2r_noalloc", "ns_describe_run", "ns_helicity", "ns_set_field",
-           "ns_get_field", "ns_field_spectrum")
+           "ns_get_field", "ns_field_spectrum", "ns_guard_check", "ns_guard_selftest")
 
 
 class NsError(RuntimeError):
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH):
         "ns_last_error": ([P], ctypes.c_char_p),
         "ns_describe_run": ([P, I, ctypes.c_char_p, I], I),
         "ns_destroy": ([P], None),
+        "ns_guard_check": ([ctypes.POINTER(ctypes.c_longlong)], I),
+        "ns_guard_selftest": ([ctypes.POINTER(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -178,6 +180,19 @@ def ns_field_spectrum(ctx, run: int, field: int, n: int):
     _check(load().ns_field_spectrum(ctx, run, field, _ptr(spec), nb, ctypes.byref(e),
                                     ctypes.byref(om)), "ns_field_spectrum", ctx)
     return e.value, om.value, spec
+
+
+def ns_guard_check() -> int:
+    """Corrupted guard bytes of all live library buffers (-1: guards off)."""
+    v = ctypes.c_longlong()
+    _check(load().ns_guard_check(ctypes.byref(v)), "ns_guard_check")
+    return v.value
+
+
+def ns_guard_selftest() -> int:
+    v = ctypes.c_longlong()
+    _check(load().ns_guard_selftest(ctypes.byref(v)), "ns_guard_selftest")
+    return v.value
 
 
 def ns_step(ctx, nsteps: int) -> None:

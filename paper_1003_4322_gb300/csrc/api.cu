@@ -112,7 +112,7 @@ ns_status fail_cuda_at(ns_ctx *c, cudaError_t e, int line) {
 template <typename P> cudaError_t dalloc(P **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return cudaSuccess;
-    return cudaMalloc((void **)p, bytes);
+    return dev_malloc((void **)p, bytes);
 }
 
 // Per-n transform resources (plans, twiddles, c2r scratch), created once.
@@ -220,7 +220,7 @@ __global__ void k_store_half(const typename Cx<T>::type *__restrict__ src, doubl
 
 ns_status ensure_staging(ns_ctx *c, size_t bytes) {
     if (c->staging_bytes >= bytes) return NS_OK;
-    if (c->staging) cudaFree(c->staging);
+    if (c->staging) dev_free(c->staging);
     c->staging = nullptr;
     c->staging_bytes = 0;
     NS_CK(dalloc(&c->staging, bytes));
@@ -523,11 +523,11 @@ ns_status build_graph(ns_ctx *c) {
 void free_run(Run &r) {
     void *ps[] = {r.un, r.u1, r.wn, r.work, r.phys, r.etab, r.etab_b};
     for (void *p : ps)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     if (r.owns_diag) {
         void *qs[] = {r.part, r.series, r.counter};
         for (void *p : qs)
-            if (p) cudaFree(p);
+            if (p) dev_free(p);
     }
 }
 
@@ -707,13 +707,13 @@ void ns_destroy(ns_ctx *c) {
     for (Run &r : c->runs) free_run(r);
     for (FusedRun &g : c->groups) fused_free(g);
     for (auto &kv : c->fft) {
-        if (kv.second.tw) cudaFree(kv.second.tw);
-        if (kv.second.scratch) cudaFree(kv.second.scratch);
+        if (kv.second.tw) dev_free(kv.second.tw);
+        if (kv.second.scratch) dev_free(kv.second.scratch);
     }
-    if (c->flags) cudaFree(c->flags);
-    if (c->spec) cudaFree(c->spec);
-    if (c->ens) cudaFree(c->ens);
-    if (c->staging) cudaFree(c->staging);
+    if (c->flags) dev_free(c->flags);
+    if (c->spec) dev_free(c->spec);
+    if (c->ens) dev_free(c->ens);
+    if (c->staging) dev_free(c->staging);
     if (c->cap) cudaStreamDestroy(c->cap);
     for (cudaStream_t q : c->par) cudaStreamDestroy(q);
     for (cudaEvent_t ev : c->fork_join) cudaEventDestroy(ev);

@@ -117,11 +117,11 @@ template <typename T> typename Cx<T>::type *make_twiddles(int n, cudaError_t *er
         h[t].y = (T)(-sin(a));
     }
     C *d = nullptr;
-    *err = cudaMalloc(&d, sizeof(C) * n);
+    *err = dev_malloc((void **)&d, sizeof(C) * n);
     if (*err != cudaSuccess) return nullptr;
     *err = cudaMemcpy(d, h.data(), sizeof(C) * n, cudaMemcpyHostToDevice);
     if (*err != cudaSuccess) {
-        cudaFree(d);
+        dev_free(d);
         return nullptr;
     }
     return d;

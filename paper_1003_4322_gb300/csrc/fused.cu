@@ -938,11 +938,11 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     f.blk_A = nr * f.sA;
     f.blk_B = nr * f.sB;
     cudaError_t e;
-    if ((e = cudaMalloc(&f.a, nb * nr * S3 * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.a1, nb * nr * S3 * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.nl, nb * nr * S3 * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.abuf, nb * nr * f.sA * sizeof(float2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.bbuf, nb * nr * f.sB * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&f.a, nb * nr * S3 * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&f.a1, nb * nr * S3 * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&f.nl, nb * nr * S3 * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&f.abuf, nb * nr * f.sA * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&f.bbuf, nb * nr * f.sB * sizeof(float2))) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(f.a, 0, nb * nr * S3 * sizeof(float2), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(f.a1, 0, nb * nr * S3 * sizeof(float2), s)) != cudaSuccess) return e;
     // factor tables exp(-nu k^2 dt) in FP64, rounded once, and per-run parameters
@@ -954,19 +954,19 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
         for (int k2 = 0; k2 < f.nk2; k2++) h[r * f.nk2 + k2] = (float)exp(-q.nu * (double)k2 * q.dt);
         hp[r] = FzRunParams{(float)q.dt, (float)q.force_amp, q.force_k, q.dealias, (float)q.rot};
     }
-    if ((e = cudaMalloc(&f.etab, h.size() * sizeof(float))) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&f.etab, h.size() * sizeof(float))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(f.etab, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
     if (f.mhd) {   // exp(-eta k^2 dt) per run
         for (long r = 0; r < nr; r++)
             for (int k2 = 0; k2 < f.nk2; k2++)
                 h[r * f.nk2 + k2] = (float)exp(-runs[r].eta * (double)k2 * runs[r].dt);
-        if ((e = cudaMalloc(&f.etab_b, h.size() * sizeof(float))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void **)&f.etab_b, h.size() * sizeof(float))) != cudaSuccess) return e;
         if ((e = cudaMemcpy(f.etab_b, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
             cudaSuccess)
             return e;
     }
-    if ((e = cudaMalloc(&f.rp, nr * sizeof(FzRunParams))) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&f.rp, nr * sizeof(FzRunParams))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(f.rp, hp.data(), nr * sizeof(FzRunParams), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
     // partials per run: the separate update's blocks, or one per column tile of
@@ -974,9 +974,9 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     f.nparts_upd = (int)std::min<long>(1024, std::max<long>(1, (f.M + 4095) / 4096));
     f.nparts = f.nparts_upd;
     const long parts_max = std::max<long>(f.nparts_upd, eu_tiles(f, 8));
-    if ((e = cudaMalloc(&f.part, nr * parts_max * 2 * sizeof(double))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.series, nr * (long)f.cap * 2 * sizeof(double))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&f.counter, nr * sizeof(unsigned long long))) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&f.part, nr * parts_max * 2 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&f.series, nr * (long)f.cap * 2 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&f.counter, nr * sizeof(unsigned long long))) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(f.counter, 0, nr * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if ((e = prepare_fused_kernels()) != cudaSuccess) return e;
     const int ct = default_ct(sizeof(float2), f.n);
@@ -1035,7 +1035,7 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
 void fused_free(FusedRun &f) {
     void *ps[] = {f.a, f.a1, f.nl, f.abuf, f.bbuf, f.etab, f.etab_b, f.rp, f.part, f.series, f.counter};
     for (void *p : ps)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     f.a = f.a1 = f.nl = f.abuf = f.bbuf = nullptr;
     f.etab = f.etab_b = nullptr;
     f.rp = nullptr;

@@ -100,6 +100,10 @@ int default_ct(int elem_bytes, int n);
 // Opt a kernel into more than 48 KB of dynamic shared memory (once per
 // device); fails if bytes exceeds the device's opt-in maximum.
 cudaError_t allow_smem(const void *kernel, size_t bytes);
+// The library's device allocations (devmem.cu): plain cudaMalloc, or with
+// guard bands when NS_GUARD=1.
+cudaError_t dev_malloc(void **p, size_t bytes);
+void dev_free(void *p);
 
 // Opt every transform kernel in up front (called by ns_init, so that nothing
 // of the kind happens while a step is being captured into a graph).
