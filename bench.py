@@ -287,21 +287,25 @@ def time_form(w, prec, mem, steps, warmup, census_steps, dist):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    s.step(steps)
-    ev1.record(stream)
+    # one event between consecutive steps (graph launches) on the launching
+    # stream: the total, and the median and best single step
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for i in range(steps):
+        s.step(1)
+        evs[i + 1].record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms = evs[0].elapsed_time(evs[-1])
+    per = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(steps))
     clk = clocks.stop()
     E, O = s.series(count=steps)
     census = nat.ns_kernel_census(s.ctx, census_steps) if census_steps > 0 else []
     desc = nat.ns_describe_run(s.ctx, 0)
     states = [read_state(s, runs, i) for i in range(len(runs))]
-    return dict(solver=s, ms=ms, clocks=clk, census=census, states=states, E=E, O=O, desc=desc)
+    return dict(solver=s, ms=ms, clocks=clk, census=census, states=states, E=E, O=O, desc=desc,
+                step_ms_median=statistics.median(per), step_ms_min=per[0])
 
 
 def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
@@ -562,6 +566,7 @@ def ours(args, w):
         "metric": METRIC, "value": value, "unit": "run-steps/s" if nr > 1 else "steps/s",
         "n_gpus": world, "runs": nr, "grid_point_steps_per_s": value * points / nr,
         "steps": args.steps, "warmup": warmup, "ms_per_step": ms / args.steps,
+        "ms_per_step_median": main["step_ms_median"], "ms_per_step_min": main["step_ms_min"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if w["prec"] == "fp64" else "f32",
         "data": "synthetic (analytic / seeded initial condition, no dataset)",
