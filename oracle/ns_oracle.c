@@ -29,6 +29,14 @@
  *   Pi          cubic 2/3 rule: keep iff 3 max|k_i| < N (dealias = 0), or the
  *               sphere 9|k|^2 < N^2 (dealias = 1);  the Nyquist index is
  *               never kept;
+ *   phase shift (dealias = 2, Navier-Stokes only; the dealiasing the
+ *               paper's Sec. 2 leaves open, in its phase-shift variant) the
+ *               product is evaluated on the grid and on the grid shifted by
+ *               D = (pi/N)(1,1,1), i.e. from a(k) e^{i k.D}, the second
+ *               transform multiplied by e^{-i k.D}, and the two averaged:
+ *               aliases k + N m with odd m_x + m_y + m_z cancel, and with
+ *               Pi the sphere 9|k|^2 < 2 N^2 no other alias reaches a kept
+ *               mode, so N equals the exact convolution on that sphere;
  *   P           P(k) v = v - k (k.v)/|k|^2, and N(k=0) = 0;
  *   forcing     ABC: f = F (sin kf z + cos kf y, sin kf x + cos kf z,
  *               sin kf y + cos kf x), constant in time, added inside N;
@@ -261,6 +269,7 @@ static int keep(int kx, int ky, int kz, int n, int dealias)
     int m = abs(kx);
     if (abs(ky) > m) m = abs(ky);
     if (abs(kz) > m) m = abs(kz);
+    if (dealias == 2) return 2 * m < n && 9L * (kx * kx + ky * ky + kz * kz) < 2L * n * n;
     if (3 * m >= n) return 0;
     if (dealias == 1 && 9L * (kx * kx + ky * ky + kz * kz) >= (long)n * n) return 0;
     return 1;
@@ -380,22 +389,61 @@ static int finish_velocity(const or_params *p, const cplx *a, cplx *out)
     return e;
 }
 
+/* Multiply a half-layout vector field by exp(i sign k.D), D = (pi/N)(1,1,1):
+ * its values on the grid shifted by D (sign +1), or back (sign -1). */
+static void phase_shift(int n, int sign, cplx *v)
+{
+    const long nh = n / 2 + 1, M = (long)n * n * nh;
+    for (long ix = 0; ix < n; ix++)
+        for (long iy = 0; iy < n; iy++)
+            for (long kz = 0; kz < nh; kz++) {
+                const double t = sign * OR_TWO_PI * 0.5 *
+                                 (wavenumber((int)ix, n) + wavenumber((int)iy, n) + (double)kz) / n;
+                const cplx ph = cos(t) + I * sin(t);
+                for (int c = 0; c < 3; c++) v[c * M + (ix * n + iy) * nh + kz] *= ph;
+            }
+}
+
+static int product_ns(int n, const cplx *a, cplx *out);
+
 int or_nonlinear(const or_params *p, const cplx *a_in, cplx *out)
 {
     if (!p || !a_in || !out || p->n < 2) return OR_ERR_ARG;
-    if (p->mhd) return nonlinear_mhd(p, a_in, out);
+    if (p->mhd) return p->dealias == 2 ? OR_ERR_ARG : nonlinear_mhd(p, a_in, out);
     const int n = p->n;
-    const long V = (long)n * n * n, nh = n / 2 + 1, M = (long)n * n * nh;
+    const long M = (long)n * n * (n / 2 + 1);
     int e = OR_ERR_OOM;
     cplx *a = malloc(sizeof(cplx) * 3 * (size_t)M);
+    cplx *as = malloc(sizeof(cplx) * 3 * (size_t)M);
+    cplx *o2 = malloc(sizeof(cplx) * 3 * (size_t)M);
+    if (!a || !as || !o2) goto done;
+    memcpy(a, a_in, sizeof(cplx) * 3 * (size_t)M);
+    apply_mask(n, p->dealias, 3, a);                 /* Galerkin truncation */
+    if ((e = product_ns(n, a, out))) goto done;      /* FFT(u x w)/N^3 */
+    if (p->dealias == 2) {                           /* and on the shifted grid */
+        memcpy(as, a, sizeof(cplx) * 3 * (size_t)M);
+        phase_shift(n, +1, as);
+        if ((e = product_ns(n, as, o2))) goto done;
+        phase_shift(n, -1, o2);
+        for (long i = 0; i < 3 * M; i++) out[i] = 0.5 * (out[i] + o2[i]);
+    }
+    e = finish_velocity(p, a, out);
+done:
+    free(a); free(as); free(o2);
+    return e;
+}
+
+/* FFT(u x w)/N^3 of a (truncated) half-layout velocity a. */
+static int product_ns(int n, const cplx *a, cplx *out)
+{
+    const long V = (long)n * n * n, nh = n / 2 + 1, M = (long)n * n * nh;
+    int e = OR_ERR_OOM;
     cplx *wh = malloc(sizeof(cplx) * 3 * (size_t)M);
     double *u = malloc(sizeof(double) * 3 * (size_t)V);
     double *w = malloc(sizeof(double) * 3 * (size_t)V);
     double *c = malloc(sizeof(double) * 3 * (size_t)V);
-    if (!a || !wh || !u || !w || !c) goto done;
+    if (!wh || !u || !w || !c) goto done;
 
-    memcpy(a, a_in, sizeof(cplx) * 3 * (size_t)M);
-    apply_mask(n, p->dealias, 3, a);                 /* Galerkin truncation */
     if ((e = or_curl(n, a, wh))) goto done;          /* w_hat = i k x a */
     if ((e = or_fft3_c2r(n, 3, a, u))) goto done;    /* u on the grid */
     if ((e = or_fft3_c2r(n, 3, wh, w))) goto done;   /* w on the grid */
@@ -407,10 +455,9 @@ int or_nonlinear(const or_params *p, const cplx *a_in, cplx *out)
     }
     if ((e = or_fft3_r2c(n, 3, c, out))) goto done;
     for (long i = 0; i < 3 * M; i++) out[i] /= (double)V;
-    if ((e = finish_velocity(p, a, out))) goto done;
     e = OR_OK;
 done:
-    free(a); free(wh); free(u); free(w); free(c);
+    free(wh); free(u); free(w); free(c);
     return e;
 }
 

@@ -110,8 +110,11 @@ def taylor_green_state(n: int) -> np.ndarray:
 
 def _in_box(k: tuple, n: int, dealias: int) -> bool:
     """Modes the generator may populate: strictly inside the 2/3-rule cube
-    (and sphere, for dealias=1) so that the field is representable."""
+    (and sphere, for dealias=1), or the sphere 9|k|^2 < 2 n^2 without the
+    Nyquist index (dealias=2), so that the field is representable."""
     kx, ky, kz = k
+    if dealias == 2:
+        return 2 * max(abs(kx), abs(ky), abs(kz)) < n and 9 * (kx * kx + ky * ky + kz * kz) < 2 * n * n
     if 3 * max(abs(kx), abs(ky), abs(kz)) >= n:
         return False
     if dealias == 1 and 9 * (kx * kx + ky * ky + kz * kz) >= n * n:

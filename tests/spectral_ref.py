@@ -40,8 +40,11 @@ def half_to_full(a: np.ndarray) -> np.ndarray:
 
 
 def keep(k: np.ndarray, n: int, dealias: int = 0) -> np.ndarray:
-    """2/3-rule mask: cube 3 max|k_i| < n, sphere 9|k|^2 < n^2 in addition."""
+    """2/3-rule mask: cube 3 max|k_i| < n, sphere 9|k|^2 < n^2 in addition;
+    dealias=2: the sphere 9|k|^2 < 2 n^2 without the Nyquist index."""
     m = np.max(np.abs(k), axis=-1)
+    if dealias == 2:
+        return (2 * m < n) & (9 * np.sum(k * k, axis=-1) < 2 * n * n)
     ok = 3 * m < n
     if dealias == 1:
         ok &= 9 * np.sum(k * k, axis=-1) < n * n

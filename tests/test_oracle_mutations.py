@@ -64,6 +64,11 @@ MUTATIONS = {
     "magnetic field diffused with nu":
         ("E[M + (ix * n + iy) * nh + kz] = exp(-p->eta * k2 * p->dt);",
          "E[M + (ix * n + iy) * nh + kz] = exp(-p->nu * k2 * p->dt);"),
+    "phase shift: shifted evaluation dropped":
+        ("    if (p->dealias == 2) {                           /* and on the shifted grid */",
+         "    if (0) {"),
+    "phase shift: shifted back with the same sign":
+        ("        phase_shift(n, -1, o2);", "        phase_shift(n, +1, o2);"),
     "Coriolis added after the projection":
         ("    int e = or_project(n, p->dealias, out);          /* Pi, then P */\n",
          "    for (long i = 0; i < M; i++) {\n        out[i] -= 2.0 * p->rot * a[M + i];\n"
@@ -125,6 +130,10 @@ def _pins():
     q1 = oracle.step(q, oracle.Params(n=8, nu=0.01, dt=0.02, rot=3.0), 3)
     if np.abs(q1 - q0).max() > 1e-13 * np.abs(q0).max():
         failed.append("taylor-proudman")
+    # phase-shift dealiasing: exact triad sum on the sphere 9|k|^2 < 2 n^2
+    ps = inputs.random_solenoidal_state(8, 1.0, 3.7, 0.7, seed=12, dealias=2)
+    if np.abs(oracle.nonlinear(ps, oracle.Params(n=8, dealias=2)) - triad_nonlinear(ps, 2)).max() > 1e-12:
+        failed.append("phase-shift-triad")
     # MHD: exact triad sums, and the force-free field's decay with eta
     mh = np.concatenate([inputs.random_solenoidal_state(8, 1.0, 2.7, 0.6, seed=31),
                          inputs.random_solenoidal_state(8, 1.0, 2.7, 0.5, seed=32)])

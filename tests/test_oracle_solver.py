@@ -303,3 +303,36 @@ def test_rotation_leaves_z_independent_flows_alone():
     d0 = oracle.step(c, oracle.Params(n=n, nu=0.01, dt=0.01), 5)
     d1 = oracle.step(c, oracle.Params(n=n, nu=0.01, dt=0.01, rot=4.0), 5)
     assert np.abs(d1 - d0).max() > 1e-3 * np.abs(d0).max()
+
+
+@pytest.mark.parametrize("n", [8, 12, 16])
+def test_phase_shift_dealiasing_equals_exact_triad_sum(n):
+    """Phase-shift dealiasing (dealias = 2): the product on the grid and on
+    the grid shifted by (pi/N)(1,1,1), averaged, with the sphere
+    9|k|^2 < 2 N^2, equals the exact convolution over that sphere, which
+    holds modes beyond the 2/3 cube (|k| up to 0.47 N)."""
+    a = inputs.random_solenoidal_state(n, 1.0, 0.47 * n, 0.7, seed=n, dealias=2)
+    k = np.array(np.meshgrid(*[np.fft.fftfreq(n, 1.0 / n)] * 2, np.arange(n // 2 + 1),
+                             indexing="ij"))
+    outside_cube = 3 * np.max(np.abs(k), axis=0) >= n
+    assert np.abs(a[:, outside_cube]).max() > 0      # the input uses the larger sphere
+    got = oracle.nonlinear(a, oracle.Params(n=n, dealias=2))
+    want = triad_nonlinear(a, 2)
+    assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+
+
+def test_phase_shift_run_keeps_beltrami_decay_and_energy_budget():
+    n, nu, dt = 16, 0.02, 0.01
+    b = oracle.step(inputs.abc_state(n), oracle.Params(n=n, nu=nu, dt=dt, dealias=2), 5)
+    assert abs(oracle.diagnostics(b)[0] - 1.5 * math.exp(-2 * nu * dt * 5)) < 1e-13
+    # inviscid and unforced, the phase-shifted N conserves energy, so one Heun
+    # step changes |a|^2 by exactly (dt^2/4) |N(a) - N(a1)|^2, a1 = a + dt N(a)
+    a0 = inputs.random_solenoidal_state(n, 1.0, 7.0, 0.6, seed=5, dealias=2)
+    h = 1e-2
+    p = oracle.Params(n=n, dt=h, dealias=2)
+    N0 = oracle.nonlinear(a0, p)
+    N1 = oracle.nonlinear(a0 + h * N0, p)
+    want = h * h / 4 * energy_half(N0 - N1)
+    e0 = oracle.diagnostics(a0)[0]
+    got = oracle.diagnostics(oracle.step(a0, p, 1))[0] - e0
+    assert want > 0 and abs(got - want) < 1e-5 * want + 4e-15 * e0
