@@ -80,7 +80,13 @@ typedef struct {
     double dt;         /* time step, > 0 */
     double force_amp;  /* ABC forcing amplitude F (0 = unforced) */
     int force_k;       /* ABC forcing wavenumber kf (0 = unforced) */
-    int dealias;       /* 0 = cubic 2/3 rule, 1 = spherical 2/3 rule */
+    int dealias;       /* 0 = cubic 2/3 rule, 1 = spherical 2/3 rule,
+                          2 = phase shift: the product also on the grid
+                          shifted by (pi/N)(1,1,1), the two averaged, with
+                          the sphere 9|k|^2 < 2 N^2 (Navier-Stokes only;
+                          twice the transforms; the dealiasing left open in
+                          Sec. 2).  A context with a dealias = 2 run uses
+                          the plain form in either precision. */
     double rot;        /* rotation rate about z (0 = inertial frame): the
                           Coriolis force -2 rot z x u of the rotating
                           equations (Sec. 5) joins u x w before the
@@ -104,8 +110,8 @@ typedef struct {
  * cuda_stream (a cudaStream_t, or NULL).  Allocates every device buffer the
  * runs need; states start at zero.  *out receives the context, or NULL on
  * error.  Errors: NS_ERR_ARG (null pointer, nruns < 1, nu < 0, dt <= 0,
- * dealias not 0/1, force_k < 0, mhd not 0/1, eta < 0, a non-finite
- * parameter), NS_ERR_UNSUPPORTED_N, NS_ERR_OOM,
+ * dealias not 0/1/2, force_k < 0, mhd not 0/1, mhd with dealias 2, eta < 0,
+ * a non-finite parameter), NS_ERR_UNSUPPORTED_N, NS_ERR_OOM,
  * NS_ERR_CUDA. */
 ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec,
                   void *cuda_stream, ns_ctx **out);

@@ -49,6 +49,7 @@ struct Run {
     long V = 0;   // grid points per component
     // plain form (full half layout)
     void *un = nullptr, *u1 = nullptr, *wn = nullptr, *work = nullptr, *phys = nullptr;
+    void *sh = nullptr, *sh2 = nullptr;   // phase-shift dealiasing: shifted state, its product
     void *etab = nullptr;   // exp(-nu k^2 dt) by integer k^2
     void *etab_b = nullptr; // MHD: exp(-eta k^2 dt); un, u1, wn then hold [u; b] (6 components)
     // fused form: the run is member gidx of group `group` of the context
@@ -81,7 +82,8 @@ struct ns_ctx {
     int spec_cap = 0;
     void *staging = nullptr;
     size_t staging_bytes = 0;
-    bool mhd_plain = false;          // an MHD run of a size without a compiled fused MHD kernel
+    bool mhd_plain = false;          // a run the fused form does not cover (MHD at a size
+                                     // without a compiled kernel, or phase-shift dealiasing)
     cudaGraphExec_t graph = nullptr;
     char last_error[256] = {0};
 };
@@ -185,6 +187,7 @@ __device__ __forceinline__ int wn_(int i, int n) { return 2 * i < n ? i : i - n;
 
 __device__ __forceinline__ bool kept_(int kx, int ky, int kz, int n, int dealias) {
     int m = max(abs(kx), max(abs(ky), abs(kz)));
+    if (dealias == 2) return 2 * m < n && 9L * (kx * kx + ky * ky + kz * kz) < 2L * n * n;
     if (3 * m >= n) return false;
     if (dealias == 1 && 9L * (kx * kx + ky * ky + kz * kz) >= (long)n * n) return false;
     return true;
@@ -386,6 +389,10 @@ template <typename T> ns_status plain_alloc(ns_ctx *c, Run &r) {
     NS_CK(dalloc(&r.wn, nc * half));
     NS_CK(dalloc(&r.work, 3 * half));
     NS_CK(dalloc(&r.phys, 2 * nc * real));
+    if (r.p.dealias == 2) {
+        NS_CK(dalloc(&r.sh, 3 * half));
+        NS_CK(dalloc(&r.sh2, 3 * half));
+    }
     NS_CK(cudaMemsetAsync(r.un, 0, nc * half, c->stream));
     NS_CK(cudaMemsetAsync(r.u1, 0, nc * half, c->stream));
     const int nk2 = 3 * (r.n / 2) * (r.n / 2) + 1;
@@ -439,6 +446,16 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
         NS_CK(c2r_batch<T>((C *)r.wn, (C *)r.work, phys + 3 * r.V, r.n, 3, *f, s, tr));
         NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, r.n, s)));
         NS_CK(r2c_batch<T>(phys, (C *)r.wn, r.n, 3, *f, s, tr));
+        if (r.p.dealias == 2) {   // the same on the grid shifted by (pi/N)(1,1,1), averaged
+            C *sh = (C *)r.sh, *sh2 = (C *)r.sh2;
+            NS_CK(NSK_TIMED(tr, "phase", plain_phase<T>(src, sh, r.n, s)));
+            NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(sh, sh2, r.n, s)));
+            NS_CK(c2r_batch<T>(sh, (C *)r.work, phys, r.n, 3, *f, s, tr));
+            NS_CK(c2r_batch<T>(sh2, (C *)r.work, phys + 3 * r.V, r.n, 3, *f, s, tr));
+            NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, r.n, s)));
+            NS_CK(r2c_batch<T>(phys, sh2, r.n, 3, *f, s, tr));
+            NS_CK(NSK_TIMED(tr, "phase", plain_phase_avg<T>((C *)r.wn, sh2, r.n, s)));
+        }
         UpdateArgs ua{stage, r.p.dt, r.p.force_amp, r.p.force_k, r.p.dealias, r.p.rot};
         NS_CK(NSK_TIMED(tr, "update",
                         plain_update<T>((C *)r.un, (C *)r.u1, (const C *)r.wn, (const T *)r.etab, r.n, ua, s)));
@@ -521,7 +538,7 @@ ns_status build_graph(ns_ctx *c) {
 }
 
 void free_run(Run &r) {
-    void *ps[] = {r.un, r.u1, r.wn, r.work, r.phys, r.etab, r.etab_b};
+    void *ps[] = {r.un, r.u1, r.wn, r.work, r.phys, r.etab, r.etab_b, r.sh, r.sh2};
     for (void *p : ps)
         if (p) dev_free(p);
     if (r.owns_diag) {
@@ -604,9 +621,10 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
     if (!runs || nruns < 1 || (prec != NS_FP64 && prec != NS_FP32)) return NS_ERR_ARG;
     for (int i = 0; i < nruns; i++) {
         const ns_run_params &p = runs[i];
-        if (!(p.nu >= 0.0) || !(p.dt > 0.0) || (p.dealias != 0 && p.dealias != 1) ||
+        if (!(p.nu >= 0.0) || !(p.dt > 0.0) || p.dealias < 0 || p.dealias > 2 ||
             p.force_k < 0 || !isfinite(p.force_amp) || !isfinite(p.nu) || !isfinite(p.dt) ||
-            !isfinite(p.rot) || (p.mhd != 0 && p.mhd != 1) || !(p.eta >= 0.0) || !isfinite(p.eta))
+            !isfinite(p.rot) || (p.mhd != 0 && p.mhd != 1) || !(p.eta >= 0.0) || !isfinite(p.eta) ||
+            (p.dealias == 2 && p.mhd))
             return NS_ERR_ARG;
         if (!supported_n(p.n) || p.n > (prec == NS_FP32 ? 1024 : 768)) return NS_ERR_UNSUPPORTED_N;
     }
@@ -615,7 +633,7 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
     c->prec = prec;
     c->stream = (cudaStream_t)cuda_stream;
     for (int i = 0; i < nruns; i++)
-        if (runs[i].mhd && !fused_mhd_supported(runs[i].n)) c->mhd_plain = true;
+        if ((runs[i].mhd && !fused_mhd_supported(runs[i].n)) || runs[i].dealias == 2) c->mhd_plain = true;
     ns_status st = NS_OK;
     auto bail = [&](ns_status s) {
         ns_destroy(c);

@@ -90,6 +90,7 @@ __device__ __forceinline__ bool kept(int kx, int ky, int kz, int n, int dealias)
     int m = abs(kx);
     m = max(m, abs(ky));
     m = max(m, abs(kz));
+    if (dealias == 2) return 2 * m < n && 9L * (kx * kx + ky * ky + kz * kz) < 2L * n * n;
     if (3 * m >= n) return false;
     if (dealias == 1 && 9L * (kx * kx + ky * ky + kz * kz) >= (long)n * n) return false;
     return true;
@@ -186,6 +187,41 @@ __global__ void k_update_b(typename Cx<T>::type *__restrict__ b, typename Cx<T>:
         dst[m] = o0;
         dst[M + m] = o1;
         dst[2 * M + m] = o2;
+    }
+}
+
+// Phase-shift dealiasing: dst = src exp(i k.D), D = (pi/N)(1,1,1), the
+// coefficients of the field on the shifted grid (three components).
+template <typename T>
+__global__ void k_phase(const typename Cx<T>::type *__restrict__ src, typename Cx<T>::type *__restrict__ dst,
+                        int n, long M) {
+    typedef typename Cx<T>::type C;
+    const int nh = n / 2 + 1;
+    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(m % nh), iy = (int)((m / nh) % n), ix = (int)(m / ((long)nh * n));
+        double s, c;
+        sincospi((double)(wavenum(ix, n) + wavenum(iy, n) + kz) / n, &s, &c);
+        const C ph = mkc((T)c, (T)s);
+#pragma unroll
+        for (int d = 0; d < 3; d++) dst[d * M + m] = cmul(src[d * M + m], ph);
+    }
+}
+
+// acc = (acc + sh exp(-i k.D)) / 2: the product on the grid and, shifted
+// back, on the shifted grid, averaged (three components).
+template <typename T>
+__global__ void k_phase_avg(typename Cx<T>::type *__restrict__ acc, const typename Cx<T>::type *__restrict__ sh,
+                            int n, long M) {
+    typedef typename Cx<T>::type C;
+    const int nh = n / 2 + 1;
+    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+        const int kz = (int)(m % nh), iy = (int)((m / nh) % n), ix = (int)(m / ((long)nh * n));
+        double s, c;
+        sincospi((double)(wavenum(ix, n) + wavenum(iy, n) + kz) / n, &s, &c);
+        const C ph = mkc((T)c, (T)-s);
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+            acc[d * M + m] = cscale(cadd(acc[d * M + m], cmul(sh[d * M + m], ph)), (T)0.5);
     }
 }
 
@@ -310,6 +346,20 @@ cudaError_t plain_update_b(typename Cx<T>::type *b, typename Cx<T>::type *b1,
 }
 
 template <typename T>
+cudaError_t plain_phase(const typename Cx<T>::type *src, typename Cx<T>::type *dst, int n, cudaStream_t s) {
+    const long M = (long)n * n * (n / 2 + 1);
+    k_phase<T><<<grid_for(M, 256), 256, 0, s>>>(src, dst, n, M);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t plain_phase_avg(typename Cx<T>::type *acc, const typename Cx<T>::type *sh, int n, cudaStream_t s) {
+    const long M = (long)n * n * (n / 2 + 1);
+    k_phase_avg<T><<<grid_for(M, 256), 256, 0, s>>>(acc, sh, n, M);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t plain_update(typename Cx<T>::type *a, typename Cx<T>::type *a1,
                          const typename Cx<T>::type *nl, const T *etab, int n, const UpdateArgs &ua,
                          cudaStream_t s) {
@@ -360,6 +410,8 @@ cudaError_t energy_final(const double *part, int nparts, double *series, int cap
     template cudaError_t plain_curl<T>(const Cx<T>::type *, Cx<T>::type *, int, cudaStream_t);    \
     template cudaError_t plain_cross<T>(T *, const T *, int, cudaStream_t);                       \
     template cudaError_t plain_cross_mhd<T>(T *, int, cudaStream_t);                              \
+    template cudaError_t plain_phase<T>(const Cx<T>::type *, Cx<T>::type *, int, cudaStream_t);   \
+    template cudaError_t plain_phase_avg<T>(Cx<T>::type *, const Cx<T>::type *, int, cudaStream_t); \
     template cudaError_t plain_update_b<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,     \
                                            const T *, int, int, double, int, cudaStream_t);       \
     template cudaError_t plain_update<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,       \

@@ -18,6 +18,12 @@ cudaError_t plain_curl(const typename Cx<T>::type *a, typename Cx<T>::type *w, i
 template <typename T> cudaError_t plain_cross(T *u, const T *w, int n, cudaStream_t s);
 // MHD: g = [u, w, b, j] on the grid -> g[0..3) = u x w + j x b, g[3..6) = u x b.
 template <typename T> cudaError_t plain_cross_mhd(T *g, int n, cudaStream_t s);
+// Phase-shift dealiasing: dst = src exp(i k.D) (the shifted grid's coefficients), and
+// acc = (acc + sh exp(-i k.D)) / 2; D = (pi/N)(1,1,1), three components.
+template <typename T>
+cudaError_t plain_phase(const typename Cx<T>::type *src, typename Cx<T>::type *dst, int n, cudaStream_t s);
+template <typename T>
+cudaError_t plain_phase_avg(typename Cx<T>::type *acc, const typename Cx<T>::type *sh, int n, cudaStream_t s);
 // MHD induction update of b (stage 1: b1 = E (b + dt N_b); stage 2: b = E b/2 +
 // (b1 + dt N_b)/2) from nb = transform of u x b; etab = exp(-eta k^2 dt).
 template <typename T>

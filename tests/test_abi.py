@@ -58,8 +58,9 @@ def test_unsupported_sizes_rejected_before_any_device_call(lib, bad):
     assert ei.value.status == nat.NS_ERR_UNSUPPORTED_N
 
 
-@pytest.mark.parametrize("bad", [dict(dt=0.0), dict(nu=-1.0), dict(dealias=2), dict(force_k=-1),
-                                 dict(dt=float("nan"))])
+@pytest.mark.parametrize("bad", [dict(dt=0.0), dict(nu=-1.0), dict(dealias=3), dict(force_k=-1),
+                                 dict(dt=float("nan")), dict(mhd=2), dict(mhd=1, eta=-1.0),
+                                 dict(mhd=1, dealias=2), dict(rot=float("inf"))])
 def test_bad_parameters_rejected(lib, bad):
     from paper_1003_4322_gb300 import _native as nat
     p = dict(n=32, dt=1e-3, nu=0.01)

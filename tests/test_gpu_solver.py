@@ -306,3 +306,31 @@ def test_rotation_is_per_run_in_a_group(ns):
         got = [s.get_state(run=r) for r in range(2)]
     for r in range(2):
         assert rel_l2(got[r], _oracle_run(a0, runs[r], 3)) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [16, 24, 48])
+def test_phase_shift_dealiasing_matches_oracle(ns, prec, n):
+    """dealias = 2: the product on the grid and on the grid shifted by
+    (pi/N)(1,1,1), averaged, sphere 9|k|^2 < 2 N^2 (the plain form in both
+    precisions), against the oracle, with a start that fills that sphere."""
+    from paper_1003_4322_gb300 import _native as nat
+    run = dict(n=n, nu=0.01, dt=1e-3, force_amp=0.5, force_k=3, dealias=2)
+    a0 = inputs.random_solenoidal_state(n, 1.0, 0.47 * n, 0.7, seed=n + 1, dealias=2)
+    ref = _oracle_run(a0, run, 3)
+    with _solver(ns, prec, **run) as s:
+        assert nat.ns_describe_run(s.ctx, 0)["form"].startswith("plain")
+        s.set_state(a0)
+        s.step(3)
+        got = s.get_state()
+    assert rel_l2(got, ref) < TOL[prec]
+    # and it differs from the cubic 2/3 rule on the same start
+    assert rel_l2(ref, _oracle_run(a0, dict(run, dealias=0), 3)) > 100 * TOL["fp32"]
+
+
+def test_phase_shift_with_mhd_is_rejected(ns):
+    from paper_1003_4322_gb300 import _native as nat
+    from paper_1003_4322_gb300.solver import Solver
+    with pytest.raises(nat.NsError) as e:
+        Solver([dict(n=16, nu=0.01, eta=0.01, dt=1e-3, mhd=1, dealias=2)], prec="fp64")
+    assert e.value.status == nat.NS_ERR_ARG
