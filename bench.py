@@ -121,7 +121,7 @@ def members(w):
             ics.append(inputs.turbulence_state(n, 4000 + r))
         return runs, ics
     run = dict(n=w["n"], nu=w["nu"], dt=w["dt"], force_amp=w.get("force_amp", 0.0),
-               force_k=w.get("force_k", 0))
+               force_k=w.get("force_k", 0), dealias=w.get("dealias", 0))
     if w["ic"] == "tg":
         return [run], [inputs.taylor_green_state(w["n"])]
     kind, seed = w["ic"]
@@ -571,6 +571,7 @@ def ours(args, w):
         "dtype": "f64" if w["prec"] == "fp64" else "f32",
         "data": "synthetic (analytic / seeded initial condition, no dataset)",
         "config": {"workload": args.workload, "description": w["desc"], "n": w["n"],
+                   "dealias": w.get("dealias", 0),
                    "nu": w.get("nu"), "dt": w["dt"], "form": "plain FP64" if w["prec"] == "fp64"
                    else "fused FP32", "parallelism": f"replicas x{world}",
                    "l2": "working set above 129 MB L2 (no flush needed)",
@@ -628,12 +629,18 @@ def main():
     ap.add_argument("--fft-prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--prec", default=None, choices=["fp32", "fp64"],
                     help="override the workload's headline form")
+    ap.add_argument("--dealias", type=int, default=None, choices=[0, 1, 2],
+                    help="override the dealiasing rule (0 cubic 2/3, 1 spherical 2/3, "
+                         "2 phase shift with the sphere 9|k|^2 < 2N^2; Navier-Stokes runs)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     w["name"] = args.workload
     if args.prec and args.prec != w["prec"]:
         w["prec"] = args.prec
         w["companion"] = None
+    if args.dealias is not None:
+        w["dealias"] = args.dealias
+        w["desc"] += f", dealias rule {args.dealias}"
     if args.mode == "fft":
         import torch
 
