@@ -75,8 +75,9 @@ KERNEL_SOURCES = {
     "fp64": ("fft_core.cuh", "fft_passes.cu", "plain.cu", "plain.h", "reduce.cuh"),
     "fp32": ("fft_core.cuh", "fft_ct.cuh", "reduce.cuh", "fused.cu", "fused.h", "fused_access.cuh",
              "fused_s.cuh", "fused_k.cuh", "fused_kA.cu", "fused_kB.cu", "fused_kD.cu",
-             "fused_kE.cu", "fused_sA.cu", "fused_sB.cu", "fused_sDE.cu", "fused_z.cu",
-             "fused_zr.cuh", "fused_zr2.cu", "fused_zr3.cu"),
+             "fused_kE.cu", "fused_keu.cu", "fused_update.cuh", "fused_sA.cu", "fused_sB.cu",
+             "fused_sDE.cu", "fused_z.cu", "fused_zr.cuh", "fused_zr2.cu", "fused_zr3.cu",
+             "fused_zm.cu"),
 }
 
 
