@@ -324,13 +324,52 @@ template <class F> static float plain_time(F launch, cudaStream_t s) {
 // 2 to 32 columns per CTA within the kernel's thread bound) runs on the run's
 // own buffers; the fastest is kept per (N, precision) for the life of the
 // process.  Where nothing runs, the defaults stay.
+// Plain-form plan cache file (environment variable NS_PLAIN_CACHE): one line
+// per (N, bytes of the real type): "N bytes E_inv ct_inv E_fwd ct_fwd E_zc2r
+// E_zr2c".  Entries found there are used as they are; newly tuned ones are
+// written back, so that profiled runs execute the same kernels as plain ones.
+static void plain_cache_read(std::map<std::pair<int, int>, PlainPlans> &cache) {
+    const char *path = getenv("NS_PLAIN_CACHE");
+    FILE *fp = path ? fopen(path, "r") : nullptr;
+    if (!fp) return;
+    int n, b, ei, ci, ef, cf, ec, er;
+    while (fscanf(fp, "%d %d %d %d %d %d %d %d", &n, &b, &ei, &ci, &ef, &cf, &ec, &er) == 8) {
+        PlainPlans q;
+        if (make_plan_e(n, ei, &q.inv) && make_plan_e(n, ef, &q.fwd) && make_plan_e(n / 2, ec, &q.zc) &&
+            make_plan_e(n / 2, er, &q.zr) && ci > 0 && cf > 0) {
+            q.ct_inv = ci;
+            q.ct_fwd = cf;
+            q.tuned = true;
+            cache[std::make_pair(n, b)] = q;
+        }
+    }
+    fclose(fp);
+}
+
+static void plain_cache_write(const std::map<std::pair<int, int>, PlainPlans> &cache) {
+    const char *path = getenv("NS_PLAIN_CACHE");
+    FILE *fp = path ? fopen(path, "w") : nullptr;
+    if (!fp) return;
+    for (const auto &kv : cache) {
+        const PlainPlans &q = kv.second;
+        fprintf(fp, "%d %d %d %d %d %d %d %d\n", kv.first.first, kv.first.second, q.inv.E, q.ct_inv,
+                q.fwd.E, q.ct_fwd, q.zc.E, q.zr.E);
+    }
+    fclose(fp);
+}
+
 template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
     typedef typename Cx<T>::type C;
     static std::mutex mu;
     static std::map<std::pair<int, int>, PlainPlans> cache;
+    static bool loaded = false;
     const std::pair<int, int> key(r.n, (int)sizeof(T));
     {
         std::lock_guard<std::mutex> g(mu);
+        if (!loaded) {
+            plain_cache_read(cache);
+            loaded = true;
+        }
         auto it = cache.find(key);
         if (it != cache.end()) {
             f->pp = it->second;
@@ -377,6 +416,7 @@ template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
     f->pp = best;
     std::lock_guard<std::mutex> g(mu);
     cache[key] = best;
+    plain_cache_write(cache);
     return NS_OK;
 }
 
