@@ -255,14 +255,14 @@ const char *ns_status_str(ns_status s);
 void ns_destroy(ns_ctx *ctx);
 
 /* Debug guard bands (no counterpart in the paper; a stand-in for a device
- * memory checker).  With NS_GUARD=1 in the environment when the library
+ * memory-error detector).  With NS_GUARD=1 in the environment when the library
  * makes its first allocation, every device buffer it allocates carries 4 KiB
  * of a fixed byte pattern on each side.  ns_guard_check synchronises the
  * device and stores in *bad_bytes how many guard bytes of all live buffers
  * no longer hold the pattern (a kernel wrote outside its buffer), or -1 when
  * guards are off.  ns_guard_selftest writes one byte into the guard of a
  * buffer of its own and stores the count ns_guard_check then reports for it
- * (1 when the checker works; -1 when guards are off).  Errors: NS_ERR_ARG
+ * (1 when the scan detects it; -1 when guards are off).  Errors: NS_ERR_ARG
  * (null pointer), NS_ERR_OOM, NS_ERR_CUDA. */
 ns_status ns_guard_check(long long *bad_bytes);
 ns_status ns_guard_selftest(long long *detected);

@@ -5,7 +5,8 @@
 // side; ns_guard_check scans every live guard band on the GPU and reports how
 // many bytes no longer hold the pattern, so that a kernel writing outside its
 // buffers shows up as a nonzero count in the tests (a debug stand-in for a
-// memory checker).  Without NS_GUARD the allocator is plain cudaMalloc.
+// device memory-error detector).  Without NS_GUARD the allocator is plain
+// cudaMalloc.
 #include <stdlib.h>
 
 #include <map>
