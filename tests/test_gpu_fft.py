@@ -157,3 +157,42 @@ def test_sizes_in_any_order_fp64(ns):
         finally:
             ns.ns_destroy(ctx)
         assert _rel(out.cpu().numpy(), oracle.fft3_c2r(a)) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("n,prec", [(512, "fp32"), (1024, "fp32"), (512, "fp64"), (768, "fp64")])
+def test_full_size_random_input_sampled_dft(ns, n, prec):
+    """At the benchmark sizes, a random input: sampled output modes against
+    the DFT written out on the host in FP64 (the sum over z for two kz in one
+    pass, then the sums over y and x per mode).  Tolerance relative to the
+    RMS coefficient magnitude sqrt(N^3) * rms(u)."""
+    import torch
+    rt, ct = _types(prec)
+    g = torch.Generator(device="cuda").manual_seed(n + 11)
+    u = (torch.rand((n, n, n), device="cuda", dtype=torch.float32, generator=g) - 0.5).to(rt)
+    out = torch.empty((1, n, n, n // 2 + 1), dtype=ct, device="cuda")
+    ctx = _ctx(ns, prec)
+    try:
+        ns.ns_fft_r2c(ctx, n, 1, u, out)
+        ns.ns_sync(ctx)
+    finally:
+        ns.ns_destroy(ctx)
+    host = u.double().cpu().numpy().reshape(n * n, n)
+    del u
+    kzs = (1, n // 2 - 3)
+    z = np.arange(n)
+    # phases from k x mod N, so that the exponentials see arguments below 2 pi
+    Ez = np.stack([np.exp(-2j * np.pi * ((kz * z) % n) / n) for kz in kzs], axis=1)   # (n, 2)
+    S = host @ np.concatenate([Ez.real, Ez.imag], axis=1)                          # one pass
+    S = (S[:, :2] + 1j * S[:, 2:]).reshape(n, n, 2)                                # [x, y, kz]
+    scale = math.sqrt(n ** 3) * float(np.sqrt(np.mean(host ** 2)))
+    del host
+    rng = np.random.default_rng(n)
+    x = np.arange(n)
+    tol = (2e-6 if prec == "fp32" else 1e-13) * scale
+    for i, kz in enumerate(kzs):
+        for _ in range(4):
+            kx, ky = (int(v) for v in rng.integers(0, n, size=2))
+            want = (np.exp(-2j * np.pi * ((kx * x) % n) / n) @ S[:, :, i]
+                    @ np.exp(-2j * np.pi * ((ky * x) % n) / n))
+            got = complex(out[0, kx, ky, kz].cpu())
+            assert abs(got - want) < tol, (kx, ky, kz, got, want, tol)
