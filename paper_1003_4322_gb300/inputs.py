@@ -13,7 +13,11 @@ Conventions (shared by both sides through the data only):
   u(x) = sum_k a(k) exp(i k.x), in the r2c half layout
   ``[3][N][N][N//2+1]`` complex128, index ``[c][kx mod N][ky mod N][kz]``
   with kz in [0, N/2] (the half storage of Sec. 2, Fig. 1);
-* the kz = 0 and kz = N/2 planes hold both k and -k, with a(-k) = conj(a(k)).
+* the kz = 0 and kz = N/2 planes hold both k and -k, with a(-k) = conj(a(k));
+* on a grid of N_x x N_y x N_z points and a box of sides 2*pi*l_i (the boxes
+  of aspect ratio other than one of Sec. 5) the layout is
+  ``[3][N_x][N_y][N_z//2+1]`` and index m along axis i stands for the
+  wavenumber m / l_i.
 
 Counter-based generator: SplitMix64 (Steele, Lea and Flood, "Fast splittable
 pseudorandom number generators", OOPSLA 2014), used as a pure function of
@@ -24,6 +28,7 @@ the same low-wavenumber field at every grid size.
 from __future__ import annotations
 
 import math
+from fractions import Fraction
 
 import numpy as np
 
@@ -54,10 +59,11 @@ def half_shape(n: int, ncomp: int = 3) -> tuple:
 
 
 class _Spectrum:
-    """Accumulates the full-space coefficient list of a real vector field."""
+    """Accumulates the full-space coefficient list of a real vector field
+    (n: N of the cube, or the grid (N_x, N_y, N_z))."""
 
-    def __init__(self, n: int):
-        self.n = n
+    def __init__(self, n):
+        self.dims = (n, n, n) if isinstance(n, int) else tuple(n)
         self.terms: dict = {}
 
     def add_real_term(self, c: int, k: tuple, a: complex) -> None:
@@ -71,12 +77,12 @@ class _Spectrum:
         return float(sum(abs(v) ** 2 for v in self.terms.values()))
 
     def to_half(self, scale: float = 1.0) -> np.ndarray:
-        n = self.n
-        out = np.zeros(half_shape(n), dtype=np.complex128)
+        nx, ny, nz = self.dims
+        out = np.zeros((3, nx, ny, nz // 2 + 1), dtype=np.complex128)
         for (c, kx, ky, kz), v in self.terms.items():
             if kz < 0:
                 continue  # its partner -k (kz > 0) carries the same information
-            out[c, kx % n, ky % n, kz] += scale * v
+            out[c, kx % nx, ky % ny, kz] += scale * v
         return out
 
 
@@ -158,6 +164,78 @@ def random_solenoidal_spectrum(n: int, lo: float, hi: float, rms: float,
     e_target = 1.5 * rms * rms
     s.scale = math.sqrt(e_target / e_now) if e_now > 0 else 0.0
     return s
+
+
+def _in_grid(m: tuple, dims: tuple, dealias: int) -> bool:
+    """Index vectors the grid generator may populate: inside the 2/3 rule of
+    every axis, 3 |m_i| < N_i (and the ellipsoid sum_i (3 m_i / N_i)^2 < 1,
+    for dealias=1), or the ellipsoid sum_i (3 m_i / N_i)^2 < 2 without the
+    Nyquist index (dealias=2); the ellipsoid in exact rationals."""
+    s = sum(Fraction(3 * abs(mi), ni) ** 2 for mi, ni in zip(m, dims))
+    if dealias == 2:
+        return all(2 * abs(mi) < ni for mi, ni in zip(m, dims)) and s < 2
+    if not all(3 * abs(mi) < ni for mi, ni in zip(m, dims)):
+        return False
+    return not (dealias == 1 and s >= 1)
+
+
+def random_solenoidal_grid(dims: tuple, box: tuple, lo: float, hi: float, rms: float,
+                           seed: int, dealias: int = 0) -> np.ndarray:
+    """The random solenoidal field of ``random_solenoidal_spectrum`` on an
+    N_x x N_y x N_z grid of the box of sides 2*pi*l_i: index vector m stands
+    for k = m / l, per-mode amplitude |k|^-2 on lo <= |k| <= hi, the same
+    draws per index vector (mode_id of m), per-component rms ``rms``.
+    Returns the half layout [3][N_x][N_y][N_z//2+1]."""
+    dims = tuple(int(d) for d in dims)
+    box = tuple(float(b) for b in box)
+    s = _Spectrum(dims)
+    lim = [int(math.floor(hi * b)) for b in box]
+    for mx in range(-lim[0], lim[0] + 1):
+        for my in range(-lim[1], lim[1] + 1):
+            for mz in range(0, lim[2] + 1):
+                if mz == 0 and not (my > 0 or (my == 0 and mx > 0)):
+                    continue
+                if not _in_grid((mx, my, mz), dims, dealias):
+                    continue
+                kv = np.array([mx / box[0], my / box[1], mz / box[2]])
+                kmag = float(np.linalg.norm(kv))
+                if kmag < lo or kmag > hi:
+                    continue
+                e1 = np.cross(kv, np.array([0.0, 0.0, 1.0]))
+                if np.linalg.norm(e1) == 0.0:
+                    e1 = np.cross(kv, np.array([1.0, 0.0, 0.0]))
+                e1 /= np.linalg.norm(e1)
+                e2 = np.cross(kv / kmag, e1)
+                mid = mode_id(mx, my, mz)
+                r1, r2, r3 = (uniform(seed, mid, d) for d in range(3))
+                vec = kmag ** -2 * (e1 * np.exp(2j * math.pi * r1) * math.cos(2 * math.pi * r3)
+                                    + e2 * np.exp(2j * math.pi * r2) * math.sin(2 * math.pi * r3))
+                for c in range(3):
+                    s.add_real_term(c, (mx, my, mz), vec[c])
+    e_now = 0.5 * s.sum_sq()
+    scale = math.sqrt(1.5 * rms * rms / e_now) if e_now > 0 else 0.0
+    return s.to_half(scale)
+
+
+def random_real_grid(dims: tuple, ncomp: int, seed: int) -> np.ndarray:
+    """Gaussian real fields, shape [ncomp][N_x][N_y][N_z] (z fastest)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((ncomp,) + tuple(dims))
+
+
+def random_hermitian_half_grid(dims: tuple, ncomp: int, seed: int) -> np.ndarray:
+    """Random half-layout array [ncomp][N_x][N_y][N_z/2+1] whose kz = 0 and
+    kz = N_z/2 planes satisfy a(-k) = conj(a(k))."""
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    nh = nz // 2 + 1
+    a = rng.standard_normal((ncomp, nx, ny, nh)) + 1j * rng.standard_normal((ncomp, nx, ny, nh))
+    negx, negy = (-np.arange(nx)) % nx, (-np.arange(ny)) % ny
+    for p in (0, nz // 2):
+        plane = a[:, :, :, p]
+        partner = np.conj(plane[:, negx][:, :, negy])
+        a[:, :, :, p] = 0.5 * (plane + partner)
+    return a
 
 
 def random_solenoidal_state(n: int, lo: float, hi: float, rms: float,

@@ -1,9 +1,14 @@
 """Independent references used to pin the oracle: brute-force sums written
 from the definitions (O(N^6) DFT, the triad convolution of the nonlinear
-term), half-layout <-> full-spectrum bookkeeping and the error metric."""
+term), half-layout <-> full-spectrum bookkeeping and the error metric.
+
+Grids may have N_x x N_y x N_z points and the box sides 2 pi l_i (the boxes
+of aspect ratio other than one of Sec. 5): index m along axis i stands for
+the wavenumber m / l_i; the dealiasing rules hold in grid indices per axis."""
 from __future__ import annotations
 
 import math
+from fractions import Fraction
 
 import numpy as np
 
@@ -15,68 +20,88 @@ def wavenumbers(n: int) -> np.ndarray:
 
 
 def brute_dft3(u: np.ndarray, sign: int = -1) -> np.ndarray:
-    """X(k) = sum_x u(x) exp(sign i k.x) for every k of the n^3 grid, by one
-    dense phase matrix (the definition, O(N^6))."""
-    n = u.shape[0]
-    g = np.arange(n)
-    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    """X(k) = sum_x u(x) exp(sign i k.x) for every k of the N_x x N_y x N_z
+    grid, by one dense phase matrix (the definition, O(N^6))."""
+    nx, ny, nz = u.shape
+    X, Y, Z = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
     pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float64)
-    phase = np.exp(sign * 2j * math.pi * (pos @ pos.T) / n)  # k and x share index sets
-    return (phase @ u.ravel().astype(np.complex128)).reshape(n, n, n)
+    scaled = pos / np.array([nx, ny, nz], dtype=np.float64)
+    phase = np.exp(sign * 2j * math.pi * (pos @ scaled.T))  # k and x share index sets
+    return (phase @ u.ravel().astype(np.complex128)).reshape(nx, ny, nz)
 
 
 def half_to_full(a: np.ndarray) -> np.ndarray:
-    """Complete a half-layout array [..][n][n][n/2+1] to the full n^3
-    spectrum with a(-k) = conj(a(k))."""
-    n = a.shape[-3]
-    nh = n // 2 + 1
-    full = np.zeros(a.shape[:-1] + (n,), dtype=np.complex128)
-    full[..., :nh] = a
-    neg = (-np.arange(n)) % n
-    for z in range(nh, n):
-        b = a[..., n - z]
-        full[..., z] = np.conj(b[..., neg, :][..., :, neg])
+    """Complete a half-layout array [..][N_x][N_y][N_z/2+1] (N_z even) to the
+    full spectrum with a(-k) = conj(a(k))."""
+    nx, ny, nzh = a.shape[-3:]
+    nz = 2 * (nzh - 1)
+    full = np.zeros(a.shape[:-1] + (nz,), dtype=np.complex128)
+    full[..., :nzh] = a
+    negx, negy = (-np.arange(nx)) % nx, (-np.arange(ny)) % ny
+    for z in range(nzh, nz):
+        b = a[..., nz - z]
+        full[..., z] = np.conj(b[..., negx, :][..., :, negy])
     return full
 
 
-def keep(k: np.ndarray, n: int, dealias: int = 0) -> np.ndarray:
-    """2/3-rule mask: cube 3 max|k_i| < n, sphere 9|k|^2 < n^2 in addition;
-    dealias=2: the sphere 9|k|^2 < 2 n^2 without the Nyquist index."""
-    m = np.max(np.abs(k), axis=-1)
-    if dealias == 2:
-        return (2 * m < n) & (9 * np.sum(k * k, axis=-1) < 2 * n * n)
-    ok = 3 * m < n
-    if dealias == 1:
-        ok &= 9 * np.sum(k * k, axis=-1) < n * n
-    return ok
+def keep(k: np.ndarray, n, dealias: int = 0) -> np.ndarray:
+    """2/3-rule mask of signed grid indices k (rows): cube 3 |k_i| < N_i,
+    the ellipsoid sum_i (3 k_i / N_i)^2 < 1 in addition (dealias=1); dealias=2:
+    the ellipsoid sum_i (3 k_i / N_i)^2 < 2 without the Nyquist index.  n is
+    N (cube) or (N_x, N_y, N_z); the ellipsoid is tested in exact rationals."""
+    dims = (n, n, n) if np.isscalar(n) else tuple(n)
+    k = np.asarray(k)
+    m = np.abs(k)
+    out = np.empty(k.shape[0], dtype=bool)
+    for r in range(k.shape[0]):
+        s = sum(Fraction(3 * int(m[r, i]), dims[i]) ** 2 for i in range(3))
+        if dealias == 2:
+            out[r] = all(2 * m[r, i] < dims[i] for i in range(3)) and s < 2
+            continue
+        ok = all(3 * m[r, i] < dims[i] for i in range(3))
+        if dealias == 1:
+            ok = ok and s < 1
+        out[r] = ok
+    return out
 
 
-def kept_modes(n: int, dealias: int = 0):
-    """All kept wavevectors of the full spectrum, as an (M, 3) int array."""
-    kk = wavenumbers(n)
-    KX, KY, KZ = np.meshgrid(kk, kk, kk, indexing="ij")
+def kept_modes(n, dealias: int = 0):
+    """All kept signed index vectors of the full spectrum, as an (M, 3) int
+    array (n: N or (N_x, N_y, N_z))."""
+    dims = (n, n, n) if np.isscalar(n) else tuple(n)
+    KX, KY, KZ = np.meshgrid(*(wavenumbers(d) for d in dims), indexing="ij")
     K = np.stack([KX.ravel(), KY.ravel(), KZ.ravel()], axis=1)
-    return K[keep(K, n, dealias)]
+    if dealias == 0:   # the plain cube rule, vectorised
+        return K[np.all(3 * np.abs(K) < np.array(dims), axis=1)]
+    return K[keep(K, dims, dealias)]
+
+
+def _dims(a_half: np.ndarray) -> tuple:
+    nx, ny, nzh = a_half.shape[-3:]
+    return (nx, ny, 2 * (nzh - 1))
 
 
 def full_coeffs(a_half: np.ndarray, K: np.ndarray) -> np.ndarray:
-    """Coefficients (M, 3) of a half-layout vector field at wavevectors K."""
-    n = a_half.shape[1]
+    """Coefficients (M, 3) of a half-layout vector field at index vectors K."""
+    nx, ny, nz = _dims(a_half)
     full = half_to_full(a_half)
-    return full[:, K[:, 0] % n, K[:, 1] % n, K[:, 2] % n].T
+    return full[:, K[:, 0] % nx, K[:, 1] % ny, K[:, 2] % nz].T
 
 
-def triad_nonlinear(a_half: np.ndarray, dealias: int = 0) -> np.ndarray:
+def triad_nonlinear(a_half: np.ndarray, dealias: int = 0, l=(1.0, 1.0, 1.0)) -> np.ndarray:
     """N(k) = P(k) sum_{p+q=k; p,q,k kept} a(p) x (i q x a(q)) for every kept
     k, written into a half-layout array (no forcing).  Exact convolution:
-    no transform, hence no aliasing."""
-    n = a_half.shape[1]
-    K = kept_modes(n, dealias)
+    no transform, hence no aliasing.  On a box of sides 2 pi l_i the
+    wavevector of index m is m / l (the convolution runs over indices)."""
+    dims = _dims(a_half)
+    K = kept_modes(dims, dealias)
+    Kf = K.astype(np.float64) / np.array(l, dtype=np.float64)
     A = full_coeffs(a_half, K)                       # (M, 3)
-    W = 1j * np.cross(K.astype(np.float64), A)       # vorticity coefficients i q x a(q)
+    W = 1j * np.cross(Kf, A)                         # vorticity coefficients i q x a(q)
     M = len(K)
-    off = n
-    lut = -np.ones((3 * n, 3 * n, 3 * n), dtype=np.int64)
+    off = max(dims)
+    span = 3 * off
+    lut = -np.ones((span, span, span), dtype=np.int64)
     lut[K[:, 0] + off, K[:, 1] + off, K[:, 2] + off] = np.arange(M)
     out = np.zeros((M, 3), dtype=np.complex128)
     for i in range(M):                               # p = K[i]
@@ -85,20 +110,16 @@ def triad_nonlinear(a_half: np.ndarray, dealias: int = 0) -> np.ndarray:
         ok = tgt >= 0
         contrib = np.cross(np.broadcast_to(A[i], (M, 3))[ok], W[ok])
         np.add.at(out, tgt[ok], contrib)
-    Kf = K.astype(np.float64)
     k2 = np.sum(Kf * Kf, axis=1)
     kv = np.sum(Kf * out, axis=1)
     nz = k2 > 0
     out[nz] -= Kf[nz] * (kv[nz] / k2[nz])[:, None]
     out[~nz] = 0
-    res = np.zeros_like(a_half)
-    sel = K[:, 2] >= 0
-    for c in range(3):
-        res[c, K[sel, 0] % n, K[sel, 1] % n, K[sel, 2]] = out[sel, c]
-    return res
+    return _to_half(out, K, a_half)
 
 
 def half_weights(n: int) -> np.ndarray:
+    """Multiplicity weights of the kz planes 0..N_z/2 (n = N_z)."""
     w = np.full(n // 2 + 1, 2.0)
     w[0] = 1.0
     w[n // 2] = 1.0
@@ -106,11 +127,11 @@ def half_weights(n: int) -> np.ndarray:
 
 
 def energy_half(a: np.ndarray) -> float:
-    return float(0.5 * np.sum(half_weights(a.shape[1]) * np.abs(a) ** 2))
+    return float(0.5 * np.sum(half_weights(_dims(a)[2]) * np.abs(a) ** 2))
 
 
 def rel_l2(test: np.ndarray, ref: np.ndarray) -> float:
-    w = half_weights(ref.shape[1])
+    w = half_weights(_dims(ref)[2])
     num = np.sum(w * np.abs(test - ref) ** 2)
     den = np.sum(w * np.abs(ref) ** 2)
     return math.sqrt(num / den)
@@ -146,11 +167,11 @@ def _triad_cross(A, B, K, n):
 
 
 def _to_half(out, K, like):
-    n = like.shape[1]
+    nx, ny, _ = _dims(like)
     res = np.zeros_like(like)
     sel = K[:, 2] >= 0
     for c in range(3):
-        res[c, K[sel, 0] % n, K[sel, 1] % n, K[sel, 2]] = out[sel, c]
+        res[c, K[sel, 0] % nx, K[sel, 1] % ny, K[sel, 2]] = out[sel, c]
     return res
 
 

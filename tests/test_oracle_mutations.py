@@ -22,11 +22,11 @@ MUTATIONS = {
         ("c[i] = u[V + i] * w[2 * V + i] - u[2 * V + i] * w[V + i];",
          "c[i] = w[V + i] * u[2 * V + i] - w[2 * V + i] * u[V + i];"),
     "curl sign":
-        ("w[m] = I * (ky * az - (double)kz * ay);", "w[m] = I * ((double)kz * ay - ky * az);"),
+        ("w[m] = I * (ky * az - kz * ay);", "w[m] = I * (kz * ay - ky * az);"),
     "projection sign":
         ("v[m] -= kx * kv / k2;", "v[m] += kx * kv / k2;"),
     "2/3 rule replaced by 1/2 rule":
-        ("if (3 * m >= n) return 0;", "if (2 * m >= n) return 0;"),
+        ("if (3 * mm >= g->n[i]) cube_ok = 0;", "if (2 * mm >= g->n[i]) cube_ok = 0;"),
     "missing 1/N^3 on the nonlinear term":
         ("for (long i = 0; i < 3 * M; i++) out[i] /= (double)V;", ""),
     "Heun second-stage weight dropped":
@@ -41,12 +41,12 @@ MUTATIONS = {
     "twiddle sign":
         ("w[t] = cos(a) + I * (sign * sin(a));", "w[t] = cos(a) - I * (sign * sin(a));"),
     "Hermitian completion without conjugate":
-        ("v = conj(h[(((n - x) % n) * n + (n - y) % n) * nh + (n - z)]);",
-         "v = h[(((n - x) % n) * n + (n - y) % n) * nh + (n - z)];"),
+        ("v = conj(h[(((nx - x) % nx) * ny + (ny - y) % ny) * nh + (nz - z)]);",
+         "v = h[(((nx - x) % nx) * ny + (ny - y) % ny) * nh + (nz - z)];"),
     "energy weight 2 on every plane":
-        ("double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;", "double w = 2.0;"),
+        ("double w = (mi[2] == 0 || 2 * mi[2] == g->n[2]) ? 1.0 : 2.0;", "double w = 2.0;"),
     "shell binning by truncation":
-        ("long K = (long)floor(sqrt(k2) + 0.5);", "long K = (long)floor(sqrt(k2));"),
+        ("long K = (long)floor(sqrt(k2) * lmax + 0.5);", "long K = (long)floor(sqrt(k2) * lmax);"),
     "Coriolis sign of one component":
         ("out[i] += 2.0 * p->rot * a[M + i];", "out[i] -= 2.0 * p->rot * a[M + i];"),
     "Coriolis without the factor 2":
@@ -59,23 +59,39 @@ MUTATIONS = {
         ("c[3 * V + i] = u[V + i] * b[2 * V + i] - u[2 * V + i] * b[V + i];",
          "c[3 * V + i] = b[V + i] * u[2 * V + i] - b[2 * V + i] * u[V + i];"),
     "induction term without the curl":
-        ("if ((e = or_curl(n, tb, out + 3 * M))) goto done;",
-         "memcpy(out + 3 * M, tb, sizeof(cplx) * 3 * (size_t)M);"),
+        ("curl_g(&g, tb, out + 3 * M);", "memcpy(out + 3 * M, tb, sizeof(cplx) * 3 * (size_t)M);"),
     "magnetic field diffused with nu":
-        ("E[M + (ix * n + iy) * nh + kz] = exp(-p->eta * k2 * p->dt);",
-         "E[M + (ix * n + iy) * nh + kz] = exp(-p->nu * k2 * p->dt);"),
+        ("E[M + m] = exp(-p->eta * k2 * p->dt);", "E[M + m] = exp(-p->nu * k2 * p->dt);"),
     "phase shift: shifted evaluation dropped":
         ("    if (p->dealias == 2) {                           /* and on the shifted grid */",
          "    if (0) {"),
     "phase shift: shifted back with the same sign":
-        ("        phase_shift(n, -1, o2);", "        phase_shift(n, +1, o2);"),
+        ("        phase_shift(&g, -1, o2);", "        phase_shift(&g, +1, o2);"),
     "Coriolis added after the projection":
-        ("    int e = or_project(n, p->dealias, out);          /* Pi, then P */\n",
+        ("    project_g(&g, p->dealias, out);                  /* Pi, then P */\n",
          "    for (long i = 0; i < M; i++) {\n        out[i] -= 2.0 * p->rot * a[M + i];\n"
          "        out[M + i] += 2.0 * p->rot * a[i];\n    }\n"
-         "    int e = or_project(n, p->dealias, out);\n"
+         "    project_g(&g, p->dealias, out);\n"
          "    for (long i = 0; i < M; i++) {\n        out[i] += 2.0 * p->rot * a[M + i];\n"
          "        out[M + i] -= 2.0 * p->rot * a[i];\n    }\n"),
+    # grids of N_x x N_y x N_z points on boxes of sides 2 pi l_i
+    "wavenumber m * l instead of m / l":
+        ("for (int i = 0; i < 3; i++) k[i] = mi[i] / g->l[i];",
+         "for (int i = 0; i < 3; i++) k[i] = mi[i] * g->l[i];"),
+    "forcing sampled without the box side along z":
+        ("z = OR_TWO_PI * g.l[2] * iz / nz;", "z = OR_TWO_PI * iz / nz;"),
+    "2/3 rule of N_x applied to every axis":
+        ("if (3 * mm >= g->n[i]) cube_ok = 0;", "if (3 * mm >= g->n[0]) cube_ok = 0;"),
+    "ellipsoid scaled by N_x on every axis":
+        ("const long q = mm * (D / g->n[i]);", "const long q = mm * (D / g->n[0]);"),
+    "phase shift with the x spacing along z":
+        ("(double)mi[2] / g->n[2]", "(double)mi[2] / g->n[0]"),
+    "shells one unit wide on every box":
+        ("    const double lmax = 1.0 / kmin_of(g);\n    double e = 0.0, om = 0.0;",
+         "    const double lmax = 1.0;\n    double e = 0.0, om = 0.0;"),
+    "Nyquist plane weight from N_x":
+        ("double w = (mi[2] == 0 || 2 * mi[2] == g->n[2]) ? 1.0 : 2.0;",
+         "double w = (mi[2] == 0 || 2 * mi[2] == g->n[0]) ? 1.0 : 2.0;"),
 }
 
 
@@ -143,6 +159,35 @@ def _pins():
     fb = oracle.step(ff, oracle.Params(n=8, nu=0.01, eta=0.03, dt=0.05, mhd=1), 4)
     if np.abs(fb[3:] - ff[3:] * math.exp(-0.03 * 0.2)).max() > 1e-14:
         failed.append("force-free")
+    # grids and boxes of other aspect ratios
+    gp = dict(n=8, ny=12, nz=6, lx=1.0, ly=1.5, lz=0.75)
+    ug = inputs.random_real_grid((6, 8, 4), 1, 3)[0]
+    if np.abs(oracle.fft3_r2c(ug) - np.fft.rfftn(ug)).max() > 1e-9:
+        failed.append("r2c-grid")
+    for d in (0, 1, 2):
+        ag = inputs.random_solenoidal_grid((8, 12, 6), (1.0, 1.5, 0.75), 0.5, 6.0, 0.8, seed=17, dealias=d)
+        if np.abs(oracle.nonlinear(ag, oracle.Params(dealias=d, **gp)) - triad_nonlinear(ag, d, (1.0, 1.5, 0.75))).max() > 1e-12:
+            failed.append(f"triad-grid-{d}")
+    fg = oracle.forcing(oracle.Params(n=8, ny=16, nz=8, lx=1.0, ly=2.0, lz=0.5, force_amp=0.5, force_k=2))
+    if abs(fg[0, 0, 0, 1] - 0.5 / 2j) > 1e-14 or abs(fg[0, 0, 4, 0] - 0.25) > 1e-14:
+        failed.append("forcing-grid")
+    pb = oracle.Params(n=8, ny=8, nz=16, lz=2.0)
+    sg = np.zeros(pb.half_shape(), dtype=np.complex128)
+    sg[0, 1, 0, 1] = 0.5
+    sg[2, 0, 0, 4] = 1.0
+    eg, _, spg = oracle.diagnostics(sg, pb)
+    if abs(spg[2] - 0.25) > 1e-16 or abs(spg[4] - 1.0) > 1e-16 or abs(eg - 1.25) > 1e-16:
+        failed.append("shell-grid")
+    ce = inputs.random_solenoidal_state(12, 1.0, 3.5, 0.8, seed=23)
+    kw = dict(nu=0.02, dt=0.01, force_amp=0.4, force_k=2, rot=0.7)
+    ref = oracle.step(ce, oracle.Params(n=12, **kw), 2)
+    emb = np.zeros((3, 24, 12, 19), dtype=np.complex128)
+    m = np.fft.fftfreq(12, 1.0 / 12).astype(int)
+    ix, iy, iz = (2 * m) % 24, m % 12, 3 * np.arange(7)
+    emb[:, ix[:, None, None], iy[None, :, None], iz[None, None, :]] = ce
+    got = oracle.step(emb, oracle.Params(n=24, ny=12, nz=36, lx=2.0, ly=1.0, lz=3.0, **kw), 2)
+    if rel_l2(got[:, ix[:, None, None], iy[None, :, None], iz[None, None, :]], ref) > 1e-14:
+        failed.append("embedding")
     return failed
 
 
