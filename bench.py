@@ -56,7 +56,19 @@ WORKLOADS = {
     "plain768": dict(desc="768^3 forced turbulence, ABC forcing k=3 F=0.5, nu=5e-4, dt=5e-4, "
                           "seeded k^-2 start (seed 5), plain FP64", n=768, nu=5e-4, dt=5e-4,
                      force_amp=0.5, force_k=3, ic=("turb", 5), prec="fp64", companion=None),
+    "box512x512x256": dict(desc="512x512x256 grid on the box of sides (2pi, 2pi, pi) (aspect ratio "
+                                "2, the spacing of 512^3), forced turbulence, ABC forcing k=2 F=0.5, "
+                                "nu=2e-3, dt=1e-3, seeded k^-2 start on 1<=|k|<=4 (seed 3), plain "
+                                "FP64 (plain FP32 alongside)", n=512, ny=512, nz=256, lz=0.5,
+                           nu=2e-3, dt=1e-3, force_amp=0.5, force_k=2, ic=("grid", 3),
+                           prec="fp64", companion="fp32"),
 }
+
+
+def dims_of(r):
+    """Grid points (N_x, N_y, N_z) of a run (dict with n and optionally ny, nz)."""
+    n = r["n"]
+    return (n, r.get("ny", 0) or n, r.get("nz", 0) or n)
 
 
 def load_peaks():
@@ -72,7 +84,7 @@ def load_peaks():
 # Kernel sources of each form, for telling whether a committed ncu capture
 # still describes the kernels that run.
 KERNEL_SOURCES = {
-    "fp64": ("fft_core.cuh", "fft_passes.cu", "plain.cu", "plain.h", "reduce.cuh"),
+    "fp64": ("fft_core.cuh", "fft_passes.cu", "plain.cu", "plain.h", "grid.cuh", "reduce.cuh"),
     "fp32": ("fft_core.cuh", "fft_ct.cuh", "reduce.cuh", "fused.cu", "fused.h", "fused_access.cuh",
              "fused_s.cuh", "fused_k.cuh", "fused_kA.cu", "fused_kB.cu", "fused_kD.cu",
              "fused_kE.cu", "fused_keu.cu", "fused_update.cuh", "fused_sA.cu", "fused_sB.cu",
@@ -123,6 +135,9 @@ def members(w):
         return runs, ics
     run = dict(n=w["n"], nu=w["nu"], dt=w["dt"], force_amp=w.get("force_amp", 0.0),
                force_k=w.get("force_k", 0), dealias=w.get("dealias", 0))
+    for k in ("ny", "nz", "lx", "ly", "lz"):
+        if k in w:
+            run[k] = w[k]
     if w["ic"] == "tg":
         return [run], [inputs.taylor_green_state(w["n"])]
     kind, seed = w["ic"]
@@ -131,6 +146,9 @@ def members(w):
         u = inputs.turbulence_state(w["n"], seed)
         b = inputs.random_solenoidal_state(w["n"], 1.0, 4.0, 0.7, seed=seed + 50)
         return [run], [np.concatenate([u, b])]
+    if kind == "grid":
+        box = tuple(run.get(k, 1.0) for k in ("lx", "ly", "lz"))
+        return [run], [inputs.random_solenoidal_grid(dims_of(run), box, 1.0, 4.0, 1.0, seed)]
     return [run], [inputs.turbulence_state(w["n"], seed)]
 
 
@@ -151,19 +169,22 @@ def read_state(s, runs, run):
 
 def kernel_model(name, n, prec):
     """Algorithmic (bytes, flops) of one launch of a kernel of the step (three
-    vector components per launch).  FFT flops use 5 n log2 n per complex
-    line of length n."""
+    vector components per launch) on the grid n (N of a cube, or (N_x, N_y,
+    N_z) for the plain kernels).  FFT flops use 5 n log2 n per complex line
+    of length n."""
     es = 8 if prec == "fp64" else 4
-    nh = n // 2 + 1
-    M = n * n * nh          # half-layout modes per component
-    V = n ** 3
-    lines_strided = n * nh
-    f_line = 5 * n * math.log2(n)
-    f_zline = 5 * (n // 2) * math.log2(n // 2) + 10 * (n // 2)
-    if name in ("fft_x_inverse", "fft_y_inverse", "fft_x_forward", "fft_y_forward"):
-        return 2 * 3 * M * 2 * es, 3 * lines_strided * f_line
+    nx, ny, nz = (n, n, n) if isinstance(n, int) else n
+    n = nx
+    nh = nz // 2 + 1
+    M = nx * ny * nh        # half-layout modes per component
+    V = nx * ny * nz
+    f_zline = 5 * (nz // 2) * math.log2(nz // 2) + 10 * (nz // 2)
+    if name in ("fft_x_inverse", "fft_x_forward"):
+        return 2 * 3 * M * 2 * es, 3 * ny * nh * 5 * nx * math.log2(nx)
+    if name in ("fft_y_inverse", "fft_y_forward"):
+        return 2 * 3 * M * 2 * es, 3 * nx * nh * 5 * ny * math.log2(ny)
     if name in ("fft_z_c2r", "fft_z_r2c"):
-        return 3 * (M * 2 * es + V * es), 3 * n * n * f_zline
+        return 3 * (M * 2 * es + V * es), 3 * nx * ny * f_zline
     if name == "curl":
         return 2 * 3 * M * 2 * es, 3 * M * 6
     if name == "cross":
@@ -174,7 +195,8 @@ def kernel_model(name, n, prec):
         return 7.5 * 3 * M * 2 * es, 3 * M * 20
     if name == "update":
         return 7.5 * 3 * M * 2 * es, 3 * M * 20
-    # fused form (FP32 complex = 8 bytes; only the kept modes move)
+    # fused form (cubes only; FP32 complex = 8 bytes; only the kept modes move)
+    f_line = 5 * n * math.log2(n)
     K = (n - 1) // 3
     Mx, Mz = 2 * K + 1, K + 1
     S = Mx * Mx * Mz            # compact modes per component
@@ -319,7 +341,7 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
     per_launch_ms = tms / launches
     # fused form: one launch covers every run of a group (runs of equal N);
     # plain form: one launch per run
-    sizes = sizes or [w["n"]]
+    sizes = sizes or [dims_of(w)]
     per_size = [kernel_model(name, n, prec) for n in sizes]
     launches_per_pass = len(sizes) if prec == "fp64" else len(set(sizes))
     bytes_ = sum(b for b, _ in per_size) / launches_per_pass
@@ -344,32 +366,47 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
 
 
 def fft_stage(n, prec, reps=5):
-    """Standalone ns_fft_r2c + ns_fft_c2r of 3 components: HBM GB/s by the
-    algorithmic model (each of the 3 passes reads and writes the array)."""
+    """Standalone ns_fft_r2c + ns_fft_c2r of 3 components (ns_fft_*_grid on a
+    grid (N_x, N_y, N_z) that is not a cube): HBM GB/s by the algorithmic
+    model (each of the 3 passes reads and writes the array)."""
     import torch
 
     from paper_1003_4322_gb300 import _native as nat
+    nx, ny, nz = (n, n, n) if isinstance(n, int) else n
+    cube = nx == ny == nz
     rt = torch.float32 if prec == "fp32" else torch.float64
     ct = torch.complex64 if prec == "fp32" else torch.complex128
     g = torch.Generator(device="cuda").manual_seed(1)
-    u = torch.randn((3, n, n, n), device="cuda", dtype=rt, generator=g)
-    uh = torch.empty((3, n, n, n // 2 + 1), device="cuda", dtype=ct)
+    u = torch.randn((3, nx, ny, nz), device="cuda", dtype=rt, generator=g)
+    uh = torch.empty((3, nx, ny, nz // 2 + 1), device="cuda", dtype=ct)
     back = torch.empty_like(u)
     stream = torch.cuda.current_stream()
     ctx = nat.ns_init([dict(n=8, dt=1e-3)], nat.NS_FP32 if prec == "fp32" else nat.NS_FP64,
                       stream)
+
+    def fwd():
+        if cube:
+            nat.ns_fft_r2c(ctx, nx, 3, u, uh)
+        else:
+            nat.ns_fft_r2c_grid(ctx, nx, ny, nz, 3, u, uh)
+
+    def inv():
+        if cube:
+            nat.ns_fft_c2r(ctx, nx, 3, uh, back)
+        else:
+            nat.ns_fft_c2r_grid(ctx, nx, ny, nz, 3, uh, back)
     try:
         for _ in range(2):
-            nat.ns_fft_r2c(ctx, n, 3, u, uh)
-            nat.ns_fft_c2r(ctx, n, 3, uh, back)
+            fwd()
+            inv()
         torch.cuda.synchronize()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         evs[0].record(stream)
         for _ in range(reps):
-            nat.ns_fft_r2c(ctx, n, 3, u, uh)
+            fwd()
         evs[1].record(stream)
         for _ in range(reps):
-            nat.ns_fft_c2r(ctx, n, 3, uh, back)
+            inv()
         evs[2].record(stream)
         torch.cuda.synchronize()
         r2c_ms = evs[0].elapsed_time(evs[1]) / reps
@@ -377,10 +414,11 @@ def fft_stage(n, prec, reps=5):
     finally:
         nat.ns_destroy(ctx)
     es = 4 if prec == "fp32" else 8
-    half = n * n * (n // 2 + 1) * 2 * es
-    real = n ** 3 * es
+    half = nx * ny * (nz // 2 + 1) * 2 * es
+    real = nx * ny * nz * es
     model = 3 * ((real + half) + 2 * half + 2 * half)   # z, y, x passes (read + write)
-    out = {"n": n, "ncomp": 3, "prec": prec, "r2c_ms": r2c_ms, "c2r_ms": c2r_ms,
+    out = {"n": nx if cube else [nx, ny, nz], "ncomp": 3, "prec": prec, "r2c_ms": r2c_ms,
+           "c2r_ms": c2r_ms,
            "r2c_gbs": model / (r2c_ms * 1e-3) / 1e9, "c2r_gbs": model / (c2r_ms * 1e-3) / 1e9,
            "bytes_model": model}
     out["cufft_reference"] = cufft_reference(u, uh, back, reps, model)
@@ -391,7 +429,7 @@ def cufft_reference(u, uh, back, reps, model):
     """cuFFT (through torch.fft) on the same arrays, unnormalised both ways,
     timed the same way: a reference point only, never on the product path."""
     import torch
-    n = u.shape[-1]
+    shape = tuple(u.shape[-3:])
     dims = (-3, -2, -1)
     ours = uh.clone()
     ref_h = torch.empty_like(uh)
@@ -399,7 +437,7 @@ def cufft_reference(u, uh, back, reps, model):
     stream = torch.cuda.current_stream()
     for _ in range(2):
         torch.fft.rfftn(u, dim=dims, norm="backward", out=ref_h)
-        torch.fft.irfftn(ref_h, s=(n, n, n), dim=dims, norm="forward", out=ref_b)
+        torch.fft.irfftn(ref_h, s=shape, dim=dims, norm="forward", out=ref_b)
     torch.cuda.synchronize()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     evs[0].record(stream)
@@ -407,7 +445,7 @@ def cufft_reference(u, uh, back, reps, model):
         torch.fft.rfftn(u, dim=dims, norm="backward", out=ref_h)
     evs[1].record(stream)
     for _ in range(reps):
-        torch.fft.irfftn(ref_h, s=(n, n, n), dim=dims, norm="forward", out=ref_b)
+        torch.fft.irfftn(ref_h, s=shape, dim=dims, norm="forward", out=ref_b)
     evs[2].record(stream)
     torch.cuda.synchronize()
     r2c = evs[0].elapsed_time(evs[1]) / reps
@@ -471,7 +509,10 @@ def oracle_steps(mem, budget_s, max_steps):
         i = steps % len(runs)
         r = runs[i]
         p = oracle.Params(n=r["n"], nu=r["nu"], dt=r["dt"], force_amp=r.get("force_amp", 0.0),
-                          force_k=r.get("force_k", 0), eta=r.get("eta", 0.0), mhd=r.get("mhd", 0))
+                          force_k=r.get("force_k", 0), dealias=r.get("dealias", 0),
+                          eta=r.get("eta", 0.0), mhd=r.get("mhd", 0), ny=r.get("ny", 0),
+                          nz=r.get("nz", 0), lx=r.get("lx", 0.0), ly=r.get("ly", 0.0),
+                          lz=r.get("lz", 0.0))
         states[i] = oracle.step(states[i], p, 1)
         steps += 1
         if time.perf_counter() - t0 > budget_s:
@@ -530,9 +571,9 @@ def ours(args, w):
     main = time_form(w, w["prec"], mem, args.steps, warmup, census_steps, dist)
     ms = max_over_ranks(main["ms"], dist, "cuda")
     value = job_rate(nr * args.steps, world, ms)
-    points = sum(r["n"] ** 3 for r in mem[0])
+    points = sum(math.prod(dims_of(r)) for r in mem[0])
     clk = main["clocks"] or {}
-    sizes = [r["n"] for r in mem[0]]
+    sizes = [dims_of(r) for r in mem[0]]
     roof, census_total = roofline_of(main["census"], w, w["prec"], census_steps, peaks,
                                      clk.get("sm_mhz"), sizes)
     launches_per_step = sum(l for _, l, _ in main["census"]) / census_steps if main["census"] else 0
@@ -553,7 +594,7 @@ def ours(args, w):
                 "kernels": [{"name": n, "launches": l, "ms": t} for n, l, t in c["census"]]}
         c["solver"].close()
 
-    fft = fft_stage(w["n"], "fp32") if not args.no_fft else None
+    fft = fft_stage(dims_of(w) if "ny" in w else w["n"], "fp32") if not args.no_fft else None
     ee = e2e(w, w["prec"], mem, min(args.steps, 20))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -572,9 +613,10 @@ def ours(args, w):
         "dtype": "f64" if w["prec"] == "fp64" else "f32",
         "data": "synthetic (analytic / seeded initial condition, no dataset)",
         "config": {"workload": args.workload, "description": w["desc"], "n": w["n"],
+                   "grid": list(dims_of(w)), "box_over_2pi": [w.get(k, 1.0) for k in ("lx", "ly", "lz")],
                    "dealias": w.get("dealias", 0),
-                   "nu": w.get("nu"), "dt": w["dt"], "form": "plain FP64" if w["prec"] == "fp64"
-                   else "fused FP32", "parallelism": f"replicas x{world}",
+                   "nu": w.get("nu"), "dt": w["dt"], "form": main["desc"]["form"],
+                   "parallelism": f"replicas x{world}",
                    "l2": "working set above 129 MB L2 (no flush needed)",
                    "execution": main["desc"]},
         "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -606,8 +648,9 @@ def reference(args, w):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": w["desc"], "n": w["n"]},
             "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
-                             "sample": f"{steps} of {args.steps} RK2 steps of the {w['n']}^3 "
-                                       f"workload (bounded to {args.cpu_budget * 4:.0f} s)"},
+                             "sample": f"{steps} of {args.steps} RK2 steps of the "
+                                       f"{'x'.join(str(d) for d in dims_of(w))} workload "
+                                       f"(bounded to {args.cpu_budget * 4:.0f} s)"},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -8,7 +8,14 @@
  * ---------------------------------------
  * Box and grid: the (2 pi)^3 periodic box sampled on N^3 points
  *   x_j = 2 pi j / N (Sec. 2).  Physical fields are [ncomp][N][N][N]
- *   (C order, z fastest).
+ *   (C order, z fastest).  A run may instead have N_x x N_y x N_z points on
+ *   a box of sides 2 pi l_x, 2 pi l_y, 2 pi l_z (the domains of aspect ratio
+ *   other than one that Sec. 5 says the scheme handles; fields
+ *   [ncomp][N_x][N_y][N_z], spectra [ncomp][N_x][N_y][N_z/2+1]); index m
+ *   along axis i then stands for the wavenumber m / l_i, and every rule
+ *   below that names N holds per axis in grid indices (3 |m_i| < N_i; the
+ *   spheres become the ellipsoids sum_i (3 m_i / N_i)^2 < 1 or < 2; the
+ *   phase shift is half a grid spacing along every axis).
  * Spectral fields: the r2c half layout [ncomp][N][N][N/2+1] (kx, ky, kz with
  *   kz in [0, N/2] fastest), the C-order mirror of the (N/2+1) x N x M
  *   arrays of Sec. 2, Fig. 1.  Full index i stands for the wavenumber
@@ -103,6 +110,13 @@ typedef struct {
                           96, 128, 192, 256, 384, 512, 768, 1024): then the
                           context uses the plain FP32 form.  0:
                           Navier-Stokes. */
+    int ny, nz;        /* grid points along y and z (0: n), each 2^a 3^b,
+                          even, >= 8; a grid other than n^3, or a box side
+                          other than 2 pi, makes the context use the plain
+                          form in either precision */
+    double lx, ly, lz; /* box sides in units of 2 pi (0: 1); with forcing,
+                          every force_k * l_i must be an integer (the ABC
+                          field periodic on the box) */
 } ns_run_params;
 
 /* Create a context for nruns independent runs (an ensemble when nruns > 1;
@@ -111,13 +125,16 @@ typedef struct {
  * runs need; states start at zero.  *out receives the context, or NULL on
  * error.  Errors: NS_ERR_ARG (null pointer, nruns < 1, nu < 0, dt <= 0,
  * dealias not 0/1/2, force_k < 0, mhd not 0/1, mhd with dealias 2, eta < 0,
- * a non-finite parameter), NS_ERR_UNSUPPORTED_N, NS_ERR_OOM,
- * NS_ERR_CUDA. */
+ * ny or nz < 0, a box side < 0 or > 1e6, forcing not periodic on the box,
+ * a non-finite parameter), NS_ERR_UNSUPPORTED_N (an axis not supported, or
+ * above 1024 points for NS_FP32 / 768 for NS_FP64, or more points than
+ * that cube), NS_ERR_OOM, NS_ERR_CUDA. */
 ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec,
                   void *cuda_stream, ns_ctx **out);
 
 /* Load the state of one run from a full half-layout FP64 complex array
- * [3][N][N][N/2+1] (host memory if on_device = 0, device memory if 1).
+ * [3][N][N][N/2+1], [3][N_x][N_y][N_z/2+1] on other grids (host memory
+ * if on_device = 0, device memory if 1).
  * Modes outside Pi are dropped (the Galerkin truncation of Sec. 2); the
  * context converts to its precision and layout.  Synchronous with respect to
  * the host buffer: it may be reused when the call returns.  Errors:
@@ -125,7 +142,8 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec,
 ns_status ns_set_state(ns_ctx *ctx, int run, const void *uhat, int on_device);
 
 /* Store the state of one run into a full half-layout FP64 complex array
- * [3][N][N][N/2+1] (host if on_device = 0, device if 1); modes outside Pi
+ * [3][N][N][N/2+1] ([3][N_x][N_y][N_z/2+1] on other grids; host if
+ * on_device = 0, device if 1); modes outside Pi
  * are written as zero.  Synchronises the context's stream.  Errors:
  * NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_NONFINITE. */
 ns_status ns_get_state(ns_ctx *ctx, int run, void *uhat, int on_device);
@@ -158,6 +176,16 @@ ns_status ns_fft_r2c(ns_ctx *ctx, int n, int ncomp, const void *in, void *out);
  * (allocated on the first call for that n).  Errors as ns_fft_r2c. */
 ns_status ns_fft_c2r(ns_ctx *ctx, int n, int ncomp, const void *in, void *out);
 
+/* ns_fft_r2c / ns_fft_c2r on a grid of nx x ny x nz points (each 2^a 3^b,
+ * even, >= 8): real fields [ncomp][nx][ny][nz] <-> half-layout complex
+ * fields [ncomp][nx][ny][nz/2+1], device pointers, unnormalised, the
+ * exponent sum_i 2 pi m_i j_i / n_i (the transform of a field on any box
+ * does not depend on its sides).  ncomp * nx <= 65535.  ns_fft_c2r_grid
+ * keeps one field of complex scratch (grown to the largest grid asked for)
+ * and synchronises the stream when it grows it.  Errors as ns_fft_r2c. */
+ns_status ns_fft_r2c_grid(ns_ctx *ctx, int nx, int ny, int nz, int ncomp, const void *in, void *out);
+ns_status ns_fft_c2r_grid(ns_ctx *ctx, int nx, int ny, int nz, int ncomp, const void *in, void *out);
+
 /* FP32 inverse c2r transform, as ns_fft_c2r for a context of precision
  * NS_FP32, that allocates nothing.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc, such as applications
@@ -184,7 +212,8 @@ ns_status ns_fft_c2r_noalloc(int n, int ncomp, const void *in, void *out, void *
  * over the full spectrum) and the shell spectrum E(K), K = round-half-up
  * |k|, of one run's current state, accumulated in FP64 (the reductions for
  * global quantities and spectra of Sec. 3).  spec receives
- * min(nbins, ns_nbins(N)) shells (spec may be NULL when nbins = 0); energy
+ * min(nbins, ns_run_nbins(run)) shells (spec may be NULL when nbins = 0);
+ * on other boxes the shells are round-half-up(|k| / k_min); energy
  * and enstrophy may be NULL.  Host outputs; synchronises the stream.
  * Errors: NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_NONFINITE. */
 /* ns_energy_spectrum of one field (0: velocity, as ns_energy_spectrum; 1:
@@ -203,13 +232,19 @@ ns_status ns_energy_spectrum(ns_ctx *ctx, int run, double *spec, int nbins,
  * it: it is one more global quantity and spectrum of the kind Sec. 3 reduces,
  * the standard invariant of ideal 3D flow; a Beltrami (ABC) field with
  * w = k u has H = k E.  spec
- * receives min(nbins, ns_nbins(N)) shells; helicity may be NULL.  Host
+ * receives min(nbins, ns_run_nbins(run)) shells; helicity may be NULL.  Host
  * outputs; synchronises the stream.  Errors: NS_ERR_ARG, NS_ERR_CUDA,
  * NS_ERR_NONFINITE (H is not finite). */
 ns_status ns_helicity(ns_ctx *ctx, int run, double *spec, int nbins, double *helicity);
 
 /* Number of shells of an N^3 grid: ceil(sqrt(3) N / 2) + 1. */
 int ns_nbins(int n);
+
+/* Number of shells of a run's grid and box: shell K = round-half-up(|k| /
+ * k_min) with k_min = 1 / max_i l_i, K = 0 .. ceil(|k_corner| / k_min),
+ * k_corner = (N_x / 2l_x, N_y / 2l_y, N_z / 2l_z); ns_nbins(N) on the
+ * (2 pi)^3 cube.  0 for a null pointer or n < 2. */
+int ns_run_nbins(const ns_run_params *p);
 
 /* Energy and enstrophy recorded by the last `count` steps of one run
  * (oldest first, at most the ring size ns_series_capacity()); fewer are

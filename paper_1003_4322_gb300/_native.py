@@ -24,7 +24,8 @@ SYMBOLS = ("ns_init", "ns_set_state", "ns_get_state", "ns_step", "ns_fft_r2c", "
            "ns_energy_spectrum", "ns_nbins", "ns_series", "ns_series_capacity",
            "ns_kernel_census", "ns_sync", "ns_last_error", "ns_status_str", "ns_destroy",
            "ns_fft_c2r_noalloc", "ns_describe_run", "ns_helicity", "ns_set_field",
-           "ns_get_field", "ns_field_spectrum", "ns_guard_check", "ns_guard_selftest")
+           "ns_get_field", "ns_field_spectrum", "ns_guard_check", "ns_guard_selftest",
+           "ns_fft_r2c_grid", "ns_fft_c2r_grid", "ns_run_nbins")
 
 
 class NsError(RuntimeError):
@@ -38,7 +39,8 @@ class ns_run_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nu", ctypes.c_double), ("dt", ctypes.c_double),
                 ("force_amp", ctypes.c_double), ("force_k", ctypes.c_int),
                 ("dealias", ctypes.c_int), ("rot", ctypes.c_double), ("eta", ctypes.c_double),
-                ("mhd", ctypes.c_int)]
+                ("mhd", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
 
 
 class ns_kernel_time(ctypes.Structure):
@@ -70,6 +72,9 @@ def load(path: str = LIB_PATH):
         "ns_fft_r2c": ([P, I, I, P, P], I),
         "ns_fft_c2r": ([P, I, I, P, P], I),
         "ns_fft_c2r_noalloc": ([I, I, P, P, P], I),
+        "ns_fft_r2c_grid": ([P, I, I, I, I, P, P], I),
+        "ns_fft_c2r_grid": ([P, I, I, I, I, P, P], I),
+        "ns_run_nbins": ([ctypes.POINTER(ns_run_params)], I),
         "ns_energy_spectrum": ([P, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D)], I),
         "ns_nbins": ([I], I),
         "ns_helicity": ([P, I, P, I, ctypes.POINTER(D)], I),
@@ -123,6 +128,24 @@ def ns_nbins(n: int) -> int:
     return load().ns_nbins(n)
 
 
+def run_params(r) -> ns_run_params:
+    """ns_run_params from a dict with keys n, dt and optionally nu,
+    force_amp, force_k, dealias, rot, eta, mhd, ny, nz, lx, ly, lz."""
+    if isinstance(r, ns_run_params):
+        return r
+    return ns_run_params(int(r["n"]), float(r.get("nu", 0.0)), float(r["dt"]),
+                         float(r.get("force_amp", 0.0)), int(r.get("force_k", 0)),
+                         int(r.get("dealias", 0)), float(r.get("rot", 0.0)),
+                         float(r.get("eta", 0.0)), int(r.get("mhd", 0)), int(r.get("ny", 0)),
+                         int(r.get("nz", 0)), float(r.get("lx", 0.0)), float(r.get("ly", 0.0)),
+                         float(r.get("lz", 0.0)))
+
+
+def ns_run_nbins(r) -> int:
+    p = run_params(r)
+    return load().ns_run_nbins(ctypes.byref(p))
+
+
 def ns_series_capacity() -> int:
     return load().ns_series_capacity()
 
@@ -132,13 +155,7 @@ def ns_init(runs, prec: int, stream=None):
     cudaStream_t integer, or None (legacy default stream)."""
     arr = (ns_run_params * len(runs))()
     for i, r in enumerate(runs):
-        if isinstance(r, ns_run_params):
-            arr[i] = r
-        else:
-            arr[i] = ns_run_params(int(r["n"]), float(r.get("nu", 0.0)), float(r["dt"]),
-                                   float(r.get("force_amp", 0.0)), int(r.get("force_k", 0)),
-                                   int(r.get("dealias", 0)), float(r.get("rot", 0.0)),
-                                   float(r.get("eta", 0.0)), int(r.get("mhd", 0)))
+        arr[i] = run_params(r)
     if stream is None:
         s = None
     elif hasattr(stream, "cuda_stream"):
@@ -172,9 +189,15 @@ def ns_get_field(ctx, run: int, field: int, out) -> None:
     _check(load().ns_get_field(ctx, run, field, _ptr(out), _on_device(out)), "ns_get_field", ctx)
 
 
-def ns_field_spectrum(ctx, run: int, field: int, n: int):
-    """Returns (E, Omega, spectrum) of field 0 (velocity) or 1 (magnetic)."""
-    nb = ns_nbins(n)
+def _shells(n) -> int:
+    """Shell count of N (an int: the cube) or of a run (dict or ns_run_params)."""
+    return ns_nbins(n) if isinstance(n, int) else ns_run_nbins(n)
+
+
+def ns_field_spectrum(ctx, run: int, field: int, n):
+    """Returns (E, Omega, spectrum) of field 0 (velocity) or 1 (magnetic);
+    n is N of a cubic run, or the run's parameters."""
+    nb = _shells(n)
     spec = np.zeros(nb, dtype=np.float64)
     e, om = ctypes.c_double(), ctypes.c_double()
     _check(load().ns_field_spectrum(ctx, run, field, _ptr(spec), nb, ctypes.byref(e),
@@ -207,6 +230,14 @@ def ns_fft_c2r(ctx, n: int, ncomp: int, inp, out) -> None:
     _check(load().ns_fft_c2r(ctx, n, ncomp, _ptr(inp), _ptr(out)), "ns_fft_c2r", ctx)
 
 
+def ns_fft_r2c_grid(ctx, nx: int, ny: int, nz: int, ncomp: int, inp, out) -> None:
+    _check(load().ns_fft_r2c_grid(ctx, nx, ny, nz, ncomp, _ptr(inp), _ptr(out)), "ns_fft_r2c_grid", ctx)
+
+
+def ns_fft_c2r_grid(ctx, nx: int, ny: int, nz: int, ncomp: int, inp, out) -> None:
+    _check(load().ns_fft_c2r_grid(ctx, nx, ny, nz, ncomp, _ptr(inp), _ptr(out)), "ns_fft_c2r_grid", ctx)
+
+
 def ns_fft_c2r_noalloc(n: int, ncomp: int, inp, out, stream=None) -> None:
     """FP32 c2r that allocates nothing (fixed in-library scratch, n <= 128)."""
     if stream is None:
@@ -218,9 +249,10 @@ def ns_fft_c2r_noalloc(n: int, ncomp: int, inp, out, stream=None) -> None:
     _check(load().ns_fft_c2r_noalloc(n, ncomp, _ptr(inp), _ptr(out), s), "ns_fft_c2r_noalloc")
 
 
-def ns_energy_spectrum(ctx, run: int, n: int):
-    """Returns (E, Omega, spectrum as a numpy array of ns_nbins(n) shells)."""
-    nb = ns_nbins(n)
+def ns_energy_spectrum(ctx, run: int, n):
+    """Returns (E, Omega, spectrum as a numpy array of the run's shells); n is
+    N of a cubic run, or the run's parameters."""
+    nb = _shells(n)
     spec = np.zeros(nb, dtype=np.float64)
     e, om = ctypes.c_double(), ctypes.c_double()
     _check(load().ns_energy_spectrum(ctx, run, _ptr(spec), nb, ctypes.byref(e), ctypes.byref(om)),
@@ -228,9 +260,9 @@ def ns_energy_spectrum(ctx, run: int, n: int):
     return e.value, om.value, spec
 
 
-def ns_helicity(ctx, run: int, n: int):
-    """Returns (H, helicity spectrum as a numpy array of ns_nbins(n) shells)."""
-    nb = ns_nbins(n)
+def ns_helicity(ctx, run: int, n):
+    """Returns (H, helicity spectrum as a numpy array of the run's shells)."""
+    nb = _shells(n)
     spec = np.zeros(nb, dtype=np.float64)
     h = ctypes.c_double()
     _check(load().ns_helicity(ctx, run, _ptr(spec), nb, ctypes.byref(h)), "ns_helicity", ctx)

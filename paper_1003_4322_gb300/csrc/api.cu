@@ -44,13 +44,14 @@ struct FftRes {
 
 struct Run {
     ns_run_params p{};
-    int n = 0, nh = 0;
+    int n = 0;    // N_x (the N of a cubic run)
+    Grid g;       // grid and box
     long M = 0;   // modes per component, half layout
     long V = 0;   // grid points per component
     // plain form (full half layout)
     void *un = nullptr, *u1 = nullptr, *wn = nullptr, *work = nullptr, *phys = nullptr;
     void *sh = nullptr, *sh2 = nullptr;   // phase-shift dealiasing: shifted state, its product
-    void *etab = nullptr;   // exp(-nu k^2 dt) by integer k^2
+    void *etab = nullptr;   // exp(-nu k^2 dt) by integer k^2 (unit boxes)
     void *etab_b = nullptr; // MHD: exp(-eta k^2 dt); un, u1, wn then hold [u; b] (6 components)
     // fused form: the run is member gidx of group `group` of the context
     int group = -1, gidx = 0;
@@ -82,8 +83,11 @@ struct ns_ctx {
     int spec_cap = 0;
     void *staging = nullptr;
     size_t staging_bytes = 0;
-    bool mhd_plain = false;          // a run the fused form does not cover (MHD at a size
-                                     // without a compiled kernel, or phase-shift dealiasing)
+    bool plain_only = false;         // a run the fused form does not cover (MHD at a size
+                                     // without a compiled kernel, phase-shift dealiasing,
+                                     // or a grid or box other than the cube)
+    void *gscratch = nullptr;        // c2r scratch of the grid transforms
+    size_t gscratch_bytes = 0;
     cudaGraphExec_t graph = nullptr;
     char last_error[256] = {0};
 };
@@ -91,6 +95,12 @@ struct ns_ctx {
 namespace {
 
 size_t elem_bytes(ns_prec p) { return p == NS_FP64 ? sizeof(double) : sizeof(float); }
+
+// Grid and box of a run: ny, nz = 0 mean N; box sides 0 mean 2 pi.
+Grid run_grid(const ns_run_params &p) {
+    return make_grid(p.n, p.ny > 0 ? p.ny : p.n, p.nz > 0 ? p.nz : p.n, p.lx > 0 ? p.lx : 1.0,
+                     p.ly > 0 ? p.ly : 1.0, p.lz > 0 ? p.lz : 1.0);
+}
 
 ns_status fail_cuda_at(ns_ctx *c, cudaError_t e, int line) {
     if (c)
@@ -139,6 +149,17 @@ ns_status get_fft(ns_ctx *c, int n, FftRes **out) {
     return NS_OK;
 }
 
+// Transform resources of the three axes of a grid (the same entry thrice on
+// the cube).
+ns_status get_fft3(ns_ctx *c, const Grid &g, FftRes *f[3]) {
+    const int n[3] = {g.nx, g.ny, g.nz};
+    for (int i = 0; i < 3; i++) {
+        ns_status st = get_fft(c, n[i], &f[i]);
+        if (st != NS_OK) return st;
+    }
+    return NS_OK;
+}
+
 ns_status ensure_scratch(ns_ctx *c, FftRes *f) {
     if (f->scratch) return NS_OK;
     const size_t bytes = (size_t)f->n * f->n * (f->n / 2 + 1) * 2 * elem_bytes(c->prec);
@@ -148,62 +169,69 @@ ns_status ensure_scratch(ns_ctx *c, FftRes *f) {
 
 // ---------------------------------------------------------------- transforms
 
-// c2r of ncomp half fields: x pass (in -> tmp), y pass (tmp in place), z pass
-// (tmp -> out).  tmp holds ncomp_tmp fields; components go in batches.
+// Per-axis transform resources of a grid: x, y and z (all the same on the cube).
+struct Fft3 {
+    const FftRes *x, *y, *z;
+};
+
+// c2r of ncomp half fields [ncomp][N_x][N_y][N_z/2+1]: x pass (in -> tmp), y
+// pass (tmp in place), z pass (tmp -> out [ncomp][N_x][N_y][N_z]).
 template <typename T>
-cudaError_t c2r_batch(const typename Cx<T>::type *in, typename Cx<T>::type *tmp, T *out, int n,
-                      int ncomp, const FftRes &f, cudaStream_t s, Tracer *tr = nullptr) {
-    const long nh = n / 2 + 1, plane = (long)n * nh, M = (long)n * plane;
-    const typename Cx<T>::type *tw = (const typename Cx<T>::type *)f.tw;
-    const PlainPlans &q = f.pp;
+cudaError_t c2r_batch(const typename Cx<T>::type *in, typename Cx<T>::type *tmp, T *out, const Grid &g,
+                      int ncomp, const Fft3 &f, cudaStream_t s, Tracer *tr = nullptr) {
+    typedef typename Cx<T>::type C;
+    const long nh = g.nzh(), plane = (long)g.ny * nh, M = (long)g.nx * plane;
+    const PlainPlans &qx = f.x->pp, &qy = f.y->pp, &qz = f.z->pp;
     cudaError_t e = NSK_TIMED(tr, "fft_x_inverse",
-                              fft_strided<T>(in, tmp, plane, plane, M, M, ncomp, +1, q.inv, tw, n, q.ct_inv, s));
+                              fft_strided<T>(in, tmp, plane, plane, M, M, ncomp, +1, qx.inv, (const C *)f.x->tw,
+                                             g.nx, qx.ct_inv, s));
     if (e != cudaSuccess) return e;
     e = NSK_TIMED(tr, "fft_y_inverse",
-                  fft_strided<T>(tmp, tmp, nh, nh, plane, plane, ncomp * n, +1, q.inv, tw, n, q.ct_inv, s));
+                  fft_strided<T>(tmp, tmp, nh, nh, plane, plane, ncomp * g.nx, +1, qy.inv, (const C *)f.y->tw,
+                                 g.ny, qy.ct_inv, s));
     if (e != cudaSuccess) return e;
-    return NSK_TIMED(tr, "fft_z_c2r", fft_z_c2r<T>(tmp, out, n, (long)ncomp * n * n, q.zc, tw, s));
+    return NSK_TIMED(tr, "fft_z_c2r",
+                     fft_z_c2r<T>(tmp, out, g.nz, (long)ncomp * g.nx * g.ny, qz.zc, (const C *)f.z->tw, s));
 }
 
 // r2c of ncomp real fields: z pass (in -> out), y and x passes in place.
 template <typename T>
-cudaError_t r2c_batch(const T *in, typename Cx<T>::type *out, int n, int ncomp, const FftRes &f,
+cudaError_t r2c_batch(const T *in, typename Cx<T>::type *out, const Grid &g, int ncomp, const Fft3 &f,
                       cudaStream_t s, Tracer *tr = nullptr) {
-    const long nh = n / 2 + 1, plane = (long)n * nh, M = (long)n * plane;
-    const typename Cx<T>::type *tw = (const typename Cx<T>::type *)f.tw;
-    const PlainPlans &q = f.pp;
-    cudaError_t e = NSK_TIMED(tr, "fft_z_r2c", fft_z_r2c<T>(in, out, n, (long)ncomp * n * n, q.zr, tw, s));
+    typedef typename Cx<T>::type C;
+    const long nh = g.nzh(), plane = (long)g.ny * nh, M = (long)g.nx * plane;
+    const PlainPlans &qx = f.x->pp, &qy = f.y->pp, &qz = f.z->pp;
+    cudaError_t e = NSK_TIMED(tr, "fft_z_r2c",
+                              fft_z_r2c<T>(in, out, g.nz, (long)ncomp * g.nx * g.ny, qz.zr, (const C *)f.z->tw, s));
     if (e != cudaSuccess) return e;
     e = NSK_TIMED(tr, "fft_y_forward",
-                  fft_strided<T>(out, out, nh, nh, plane, plane, ncomp * n, -1, q.fwd, tw, n, q.ct_fwd, s));
+                  fft_strided<T>(out, out, nh, nh, plane, plane, ncomp * g.nx, -1, qy.fwd, (const C *)f.y->tw,
+                                 g.ny, qy.ct_fwd, s));
     if (e != cudaSuccess) return e;
     return NSK_TIMED(tr, "fft_x_forward",
-                     fft_strided<T>(out, out, plane, plane, M, M, ncomp, -1, q.fwd, tw, n, q.ct_fwd, s));
+                     fft_strided<T>(out, out, plane, plane, M, M, ncomp, -1, qx.fwd, (const C *)f.x->tw, g.nx,
+                                    qx.ct_fwd, s));
+}
+
+ns_status fft3_of(ns_ctx *c, const Grid &g, Fft3 *out) {
+    FftRes *f[3];
+    ns_status st = get_fft3(c, g, f);
+    if (st != NS_OK) return st;
+    *out = Fft3{f[0], f[1], f[2]};
+    return NS_OK;
 }
 
 // ---------------------------------------------------------------- state transfer
-
-__device__ __forceinline__ int wn_(int i, int n) { return 2 * i < n ? i : i - n; }
-
-__device__ __forceinline__ bool kept_(int kx, int ky, int kz, int n, int dealias) {
-    int m = max(abs(kx), max(abs(ky), abs(kz)));
-    if (dealias == 2) return 2 * m < n && 9L * (kx * kx + ky * ky + kz * kz) < 2L * n * n;
-    if (3 * m >= n) return false;
-    if (dealias == 1 && 9L * (kx * kx + ky * ky + kz * kz) >= (long)n * n) return false;
-    return true;
-}
 
 // dst (half layout, precision T) <- src (FP64 half layout) for modes
 // [m0, m0 + cnt) of one component, zeroing modes outside Pi.
 template <typename T>
 __global__ void k_load_half(const double2 *__restrict__ src, typename Cx<T>::type *__restrict__ dst,
-                            int n, long m0, long cnt, int dealias) {
-    const int nh = n / 2 + 1;
+                            Grid g, long m0, long cnt, int dealias) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < cnt; i += (long)gridDim.x * blockDim.x) {
         const long m = m0 + i;
-        const int kz = (int)(m % nh), iy = (int)((m / nh) % n), ix = (int)(m / ((long)nh * n));
         typename Cx<T>::type v;
-        if (kept_(wn_(ix, n), wn_(iy, n), kz, n, dealias)) {
+        if (kept(mode_at(m, g), g, dealias)) {
             v.x = (T)src[i].x;
             v.y = (T)src[i].y;
         } else {
@@ -259,7 +287,7 @@ ns_status plain_set_state(ns_ctx *c, Run &r, const double2 *src, int on_device, 
             const long mm = g % r.M;
             const long seg = std::min(cnt - done, r.M - mm);
             k_load_half<T><<<(unsigned)std::min<long>((seg + 255) / 256, 152 * 16), 256, 0, c->stream>>>(
-                s + done, dst + (long)comp * r.M, r.n, mm, seg, r.p.dealias);
+                s + done, dst + (long)comp * r.M, r.g, mm, seg, r.p.dealias);
             NS_CK(cudaGetLastError());
             done += seg;
         }
@@ -360,6 +388,7 @@ static void plain_cache_write(const std::map<std::pair<int, int>, PlainPlans> &c
 
 template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
     typedef typename Cx<T>::type C;
+    if (!r.g.cube) return NS_OK;   // other grids use the plans of their axis lengths as they stand
     static std::mutex mu;
     static std::map<std::pair<int, int>, PlainPlans> cache;
     static bool loaded = false;
@@ -435,27 +464,46 @@ template <typename T> ns_status plain_alloc(ns_ctx *c, Run &r) {
     }
     NS_CK(cudaMemsetAsync(r.un, 0, nc * half, c->stream));
     NS_CK(cudaMemsetAsync(r.u1, 0, nc * half, c->stream));
-    const int nk2 = 3 * (r.n / 2) * (r.n / 2) + 1;
-    std::vector<T> h(nk2);
-    for (int k2 = 0; k2 < nk2; k2++) h[k2] = (T)exp(-r.p.nu * (double)k2 * r.p.dt);
-    NS_CK(dalloc(&r.etab, nk2 * sizeof(T)));
-    NS_CK(cudaMemcpy(r.etab, h.data(), nk2 * sizeof(T), cudaMemcpyHostToDevice));
-    if (r.p.mhd) {
-        for (int k2 = 0; k2 < nk2; k2++) h[k2] = (T)exp(-r.p.eta * (double)k2 * r.p.dt);
-        NS_CK(dalloc(&r.etab_b, nk2 * sizeof(T)));
-        NS_CK(cudaMemcpy(r.etab_b, h.data(), nk2 * sizeof(T), cudaMemcpyHostToDevice));
+    if (r.g.unit) {   // factor tables by integer |k|^2 (other boxes form the factor per mode)
+        const long nk2 = grid_max_k2(r.g) + 1;
+        std::vector<T> h(nk2);
+        for (long k2 = 0; k2 < nk2; k2++) h[k2] = (T)exp(-r.p.nu * (double)k2 * r.p.dt);
+        NS_CK(dalloc(&r.etab, nk2 * sizeof(T)));
+        NS_CK(cudaMemcpy(r.etab, h.data(), nk2 * sizeof(T), cudaMemcpyHostToDevice));
+        if (r.p.mhd) {
+            for (long k2 = 0; k2 < nk2; k2++) h[k2] = (T)exp(-r.p.eta * (double)k2 * r.p.dt);
+            NS_CK(dalloc(&r.etab_b, nk2 * sizeof(T)));
+            NS_CK(cudaMemcpy(r.etab_b, h.data(), nk2 * sizeof(T), cudaMemcpyHostToDevice));
+        }
     }
-    FftRes *f;
-    ns_status st = get_fft(c, r.n, &f);
+    FftRes *f[3];
+    ns_status st = get_fft3(c, r.g, f);
     if (st != NS_OK) return st;
-    return tune_plain<T>(c, r, f);
+    return tune_plain<T>(c, r, f[0]);
+}
+
+// Update arguments of a stage: forcing index kf l_i along every axis.
+UpdateArgs update_args(const Run &r, int stage) {
+    UpdateArgs ua{};
+    ua.stage = stage;
+    ua.dt = r.p.dt;
+    ua.force_amp = r.p.force_amp;
+    ua.force_k = r.p.force_k;
+    ua.mfx = (int)lround(r.p.force_k * r.g.lx);
+    ua.mfy = (int)lround(r.p.force_k * r.g.ly);
+    ua.mfz = (int)lround(r.p.force_k * r.g.lz);
+    ua.dealias = r.p.dealias;
+    ua.rot = r.p.rot;
+    ua.nu_dt = r.p.nu * r.p.dt;
+    return ua;
 }
 
 template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tracer *tr) {
     typedef typename Cx<T>::type C;
-    FftRes *f;
-    ns_status st = get_fft(c, r.n, &f);
+    Fft3 f;
+    ns_status st = fft3_of(c, r.g, &f);
     if (st != NS_OK) return st;
+    const Grid &g = r.g;
     T *phys = (T *)r.phys;
     const long M3 = 3 * r.M, V3 = 3 * r.V;
     for (int stage = 1; stage <= 2 && r.p.mhd; stage++) {
@@ -463,50 +511,51 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
         // grid -> u x w + j x b, u x b -> their transforms -> the two updates
         C *src = (C *)(stage == 1 ? r.un : r.u1);
         C *wj = (C *)r.wn;
-        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, wj, r.n, s)));
-        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src + M3, wj + M3, r.n, s)));
-        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, r.n, 3, *f, s, tr));
-        NS_CK(c2r_batch<T>(wj, (C *)r.work, phys + V3, r.n, 3, *f, s, tr));
-        NS_CK(c2r_batch<T>(src + M3, (C *)r.work, phys + 2 * V3, r.n, 3, *f, s, tr));
-        NS_CK(c2r_batch<T>(wj + M3, (C *)r.work, phys + 3 * V3, r.n, 3, *f, s, tr));
-        NS_CK(NSK_TIMED(tr, "cross_mhd", plain_cross_mhd<T>(phys, r.n, s)));
-        NS_CK(r2c_batch<T>(phys, wj, r.n, 3, *f, s, tr));
-        NS_CK(r2c_batch<T>(phys + V3, wj + M3, r.n, 3, *f, s, tr));
-        UpdateArgs ua{stage, r.p.dt, r.p.force_amp, r.p.force_k, r.p.dealias, r.p.rot};
+        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, wj, g, s)));
+        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src + M3, wj + M3, g, s)));
+        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, g, 3, f, s, tr));
+        NS_CK(c2r_batch<T>(wj, (C *)r.work, phys + V3, g, 3, f, s, tr));
+        NS_CK(c2r_batch<T>(src + M3, (C *)r.work, phys + 2 * V3, g, 3, f, s, tr));
+        NS_CK(c2r_batch<T>(wj + M3, (C *)r.work, phys + 3 * V3, g, 3, f, s, tr));
+        NS_CK(NSK_TIMED(tr, "cross_mhd", plain_cross_mhd<T>(phys, g, s)));
+        NS_CK(r2c_batch<T>(phys, wj, g, 3, f, s, tr));
+        NS_CK(r2c_batch<T>(phys + V3, wj + M3, g, 3, f, s, tr));
+        const UpdateArgs ua = update_args(r, stage);
         NS_CK(NSK_TIMED(tr, "update",
-                        plain_update<T>((C *)r.un, (C *)r.u1, (const C *)wj, (const T *)r.etab, r.n, ua, s)));
+                        plain_update<T>((C *)r.un, (C *)r.u1, (const C *)wj, (const T *)r.etab, g, ua, s)));
         NS_CK(NSK_TIMED(tr, "update_b",
                         plain_update_b<T>((C *)r.un + M3, (C *)r.u1 + M3, (const C *)wj + M3,
-                                          (const T *)r.etab_b, r.n, stage, r.p.dt, r.p.dealias, s)));
+                                          (const T *)r.etab_b, g, stage, r.p.dt,
+                                          r.p.eta * r.p.dt, r.p.dealias, s)));
     }
     for (int stage = 1; stage <= 2 && !r.p.mhd; stage++) {
         C *src = (C *)(stage == 1 ? r.un : r.u1);
-        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, (C *)r.wn, r.n, s)));
-        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, r.n, 3, *f, s, tr));
-        NS_CK(c2r_batch<T>((C *)r.wn, (C *)r.work, phys + 3 * r.V, r.n, 3, *f, s, tr));
-        NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, r.n, s)));
-        NS_CK(r2c_batch<T>(phys, (C *)r.wn, r.n, 3, *f, s, tr));
-        if (r.p.dealias == 2) {   // the same on the grid shifted by (pi/N)(1,1,1), averaged
+        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, (C *)r.wn, g, s)));
+        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, g, 3, f, s, tr));
+        NS_CK(c2r_batch<T>((C *)r.wn, (C *)r.work, phys + 3 * r.V, g, 3, f, s, tr));
+        NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, g, s)));
+        NS_CK(r2c_batch<T>(phys, (C *)r.wn, g, 3, f, s, tr));
+        if (r.p.dealias == 2) {   // the same on the grid shifted by half a spacing, averaged
             C *sh = (C *)r.sh, *sh2 = (C *)r.sh2;
-            NS_CK(NSK_TIMED(tr, "phase", plain_phase<T>(src, sh, r.n, s)));
-            NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(sh, sh2, r.n, s)));
-            NS_CK(c2r_batch<T>(sh, (C *)r.work, phys, r.n, 3, *f, s, tr));
-            NS_CK(c2r_batch<T>(sh2, (C *)r.work, phys + 3 * r.V, r.n, 3, *f, s, tr));
-            NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, r.n, s)));
-            NS_CK(r2c_batch<T>(phys, sh2, r.n, 3, *f, s, tr));
-            NS_CK(NSK_TIMED(tr, "phase", plain_phase_avg<T>((C *)r.wn, sh2, r.n, s)));
+            NS_CK(NSK_TIMED(tr, "phase", plain_phase<T>(src, sh, g, s)));
+            NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(sh, sh2, g, s)));
+            NS_CK(c2r_batch<T>(sh, (C *)r.work, phys, g, 3, f, s, tr));
+            NS_CK(c2r_batch<T>(sh2, (C *)r.work, phys + 3 * r.V, g, 3, f, s, tr));
+            NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, g, s)));
+            NS_CK(r2c_batch<T>(phys, sh2, g, 3, f, s, tr));
+            NS_CK(NSK_TIMED(tr, "phase", plain_phase_avg<T>((C *)r.wn, sh2, g, s)));
         }
-        UpdateArgs ua{stage, r.p.dt, r.p.force_amp, r.p.force_k, r.p.dealias, r.p.rot};
+        const UpdateArgs ua = update_args(r, stage);
         NS_CK(NSK_TIMED(tr, "update",
-                        plain_update<T>((C *)r.un, (C *)r.u1, (const C *)r.wn, (const T *)r.etab, r.n, ua, s)));
+                        plain_update<T>((C *)r.un, (C *)r.u1, (const C *)r.wn, (const T *)r.etab, g, ua, s)));
     }
-    NS_CK(NSK_TIMED(tr, "energy_partials", plain_energy_partials<T>((const C *)r.un, r.n, r.part, s)));
+    NS_CK(NSK_TIMED(tr, "energy_partials", plain_energy_partials<T>((const C *)r.un, g, r.part, s)));
     NS_CK(NSK_TIMED(tr, "energy_final",
                     energy_final(r.part, r.nparts, r.series, kSeriesCap, r.counter, c->flags, s)));
     return NS_OK;
 }
 
-bool use_fused(const ns_ctx *c) { return c->prec == NS_FP32 && fused_enabled() && !c->mhd_plain; }
+bool use_fused(const ns_ctx *c) { return c->prec == NS_FP32 && fused_enabled() && !c->plain_only; }
 
 // One RK2 step of every run of the context: one batched sequence of launches
 // per group of the fused form, or the plain sequence per run.
@@ -558,8 +607,8 @@ ns_status build_graph(ns_ctx *c) {
     if (c->graph) return NS_OK;
     // Resources the step needs must exist before capture (no allocation inside).
     for (Run &r : c->runs) {
-        FftRes *f;
-        ns_status st = get_fft(c, r.n, &f);
+        FftRes *f[3];
+        ns_status st = get_fft3(c, r.g, f);
         if (st != NS_OK) return st;
     }
     NS_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -645,11 +694,13 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
         const auto it = c->fft.find(r.n);
         const PlainPlans q = it != c->fft.end() ? it->second.pp : PlainPlans{};
         snprintf(out, len,
-                 "{\"form\": \"plain %s\", \"equations\": \"%s\", \"n\": %d, \"tuned\": %s, "
+                 "{\"form\": \"plain %s\", \"equations\": \"%s\", \"n\": %d, \"grid\": [%d, %d, %d], "
+                 "\"box\": [%.17g, %.17g, %.17g], \"tuned\": %s, "
                  "\"xy_inverse\": {\"E\": %d, \"cols_per_cta\": %d}, \"xy_forward\": {\"E\": %d, "
                  "\"cols_per_cta\": %d}, \"z_c2r\": {\"E\": %d}, \"z_r2c\": {\"E\": %d}}",
-                 c->prec == NS_FP64 ? "FP64" : "FP32", r.p.mhd ? "MHD" : "Navier-Stokes", r.n,
-                 q.tuned ? "true" : "false", q.inv.E, q.ct_inv, q.fwd.E, q.ct_fwd, q.zc.E, q.zr.E);
+                 c->prec == NS_FP64 ? "FP64" : "FP32", r.p.mhd ? "MHD" : "Navier-Stokes", r.n, r.g.nx, r.g.ny,
+                 r.g.nz, r.g.lx, r.g.ly, r.g.lz, q.tuned ? "true" : "false", q.inv.E, q.ct_inv, q.fwd.E, q.ct_fwd,
+                 q.zc.E, q.zr.E);
     }
     return NS_OK;
 }
@@ -664,16 +715,32 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
         if (!(p.nu >= 0.0) || !(p.dt > 0.0) || p.dealias < 0 || p.dealias > 2 ||
             p.force_k < 0 || !isfinite(p.force_amp) || !isfinite(p.nu) || !isfinite(p.dt) ||
             !isfinite(p.rot) || (p.mhd != 0 && p.mhd != 1) || !(p.eta >= 0.0) || !isfinite(p.eta) ||
-            (p.dealias == 2 && p.mhd))
+            (p.dealias == 2 && p.mhd) || p.ny < 0 || p.nz < 0)
             return NS_ERR_ARG;
-        if (!supported_n(p.n) || p.n > (prec == NS_FP32 ? 1024 : 768)) return NS_ERR_UNSUPPORTED_N;
+        const double l[3] = {p.lx, p.ly, p.lz};
+        for (double li : l)
+            if (!(li >= 0.0) || !(li <= 1e6)) return NS_ERR_ARG;
+        const Grid g = run_grid(p);
+        if (p.force_k > 0 && p.force_amp != 0.0) {   // the ABC field must be periodic on the box
+            const double lg[3] = {g.lx, g.ly, g.lz};
+            for (double li : lg) {
+                const double t = p.force_k * li;
+                if (fabs(t - nearbyint(t)) > 1e-9 * t) return NS_ERR_ARG;
+            }
+        }
+        const int cap = prec == NS_FP32 ? 1024 : 768;
+        const int ns[3] = {g.nx, g.ny, g.nz};
+        for (int n : ns)
+            if (!supported_n(n) || n > cap) return NS_ERR_UNSUPPORTED_N;
+        if ((double)g.nx * g.ny * g.nz > (double)cap * cap * cap) return NS_ERR_UNSUPPORTED_N;
     }
     ns_ctx *c = new (std::nothrow) ns_ctx;
     if (!c) return NS_ERR_OOM;
     c->prec = prec;
     c->stream = (cudaStream_t)cuda_stream;
     for (int i = 0; i < nruns; i++)
-        if ((runs[i].mhd && !fused_mhd_supported(runs[i].n)) || runs[i].dealias == 2) c->mhd_plain = true;
+        if ((runs[i].mhd && !fused_mhd_supported(runs[i].n)) || runs[i].dealias == 2 || !run_grid(runs[i]).cube)
+            c->plain_only = true;
     ns_status st = NS_OK;
     auto bail = [&](ns_status s) {
         ns_destroy(c);
@@ -690,13 +757,13 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
         Run &r = c->runs[i];
         r.p = runs[i];
         r.n = r.p.n;
-        r.nh = r.n / 2 + 1;
-        r.M = (long)r.n * r.n * r.nh;
-        r.V = (long)r.n * r.n * r.n;
-        r.nparts = energy_nparts(r.n);
-        maxbins = std::max(maxbins, ns_nbins(r.n));
-        FftRes *f;
-        if ((st = get_fft(c, r.n, &f)) != NS_OK) return bail(st);
+        r.g = run_grid(r.p);
+        r.M = r.g.M();
+        r.V = r.g.V();
+        r.nparts = energy_nparts(r.M);
+        maxbins = std::max(maxbins, grid_nbins(r.g));
+        FftRes *f[3];
+        if ((st = get_fft3(c, r.g, f)) != NS_OK) return bail(st);
         if (use_fused(c)) continue;   // grouped below
         st = prec == NS_FP64 ? plain_alloc<double>(c, r) : plain_alloc<float>(c, r);
         if (st != NS_OK) return bail(st);
@@ -772,6 +839,7 @@ void ns_destroy(ns_ctx *c) {
     if (c->spec) dev_free(c->spec);
     if (c->ens) dev_free(c->ens);
     if (c->staging) dev_free(c->staging);
+    if (c->gscratch) dev_free(c->gscratch);
     if (c->cap) cudaStreamDestroy(c->cap);
     for (cudaStream_t q : c->par) cudaStreamDestroy(q);
     for (cudaEvent_t ev : c->fork_join) cudaEventDestroy(ev);
@@ -846,14 +914,16 @@ ns_status ns_fft_r2c(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
     if (!supported_n(n)) return NS_ERR_UNSUPPORTED_N;
     FftRes *f;
     if ((st = get_fft(c, n, &f)) != NS_OK) return st;
+    const Grid g = make_grid(n, n, n, 1.0, 1.0, 1.0);
+    const Fft3 f3{f, f, f};
     if (c->prec == NS_FP64) {
-        NS_CK(r2c_batch<double>((const double *)in, (double2 *)out, n, ncomp, *f, c->stream));
+        NS_CK(r2c_batch<double>((const double *)in, (double2 *)out, g, ncomp, f3, c->stream));
     } else {
         cudaError_t e = cudaSuccess;
         if (std_r2c_fp32((const float *)in, (float2 *)out, n, ncomp, (const float2 *)f->tw, c->stream, &e))
             NS_CK(e);
         else
-            NS_CK(r2c_batch<float>((const float *)in, (float2 *)out, n, ncomp, *f, c->stream));
+            NS_CK(r2c_batch<float>((const float *)in, (float2 *)out, g, ncomp, f3, c->stream));
     }
     return NS_OK;
 }
@@ -866,11 +936,13 @@ ns_status ns_fft_c2r(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
     FftRes *f;
     if ((st = get_fft(c, n, &f)) != NS_OK) return st;
     if ((st = ensure_scratch(c, f)) != NS_OK) return st;
-    const long M = (long)n * n * (n / 2 + 1), V = (long)n * n * n;
+    const Grid g = make_grid(n, n, n, 1.0, 1.0, 1.0);
+    const Fft3 f3{f, f, f};
+    const long M = g.M(), V = g.V();
     for (int k = 0; k < ncomp; k++) {
         if (c->prec == NS_FP64)
             NS_CK(c2r_batch<double>((const double2 *)in + k * M, (double2 *)f->scratch,
-                                    (double *)out + k * V, n, 1, *f, c->stream));
+                                    (double *)out + k * V, g, 1, f3, c->stream));
         else {
             cudaError_t e = cudaSuccess;
             if (std_c2r_fp32((const float2 *)in + k * M, (float2 *)f->scratch, (float *)out + k * V, n,
@@ -878,10 +950,78 @@ ns_status ns_fft_c2r(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
                 NS_CK(e);
             else
                 NS_CK(c2r_batch<float>((const float2 *)in + k * M, (float2 *)f->scratch,
-                                       (float *)out + k * V, n, 1, *f, c->stream));
+                                       (float *)out + k * V, g, 1, f3, c->stream));
         }
     }
     return NS_OK;
+}
+
+// The transforms of N_x x N_y x N_z grids (the three axes may differ).
+static ns_status grid_fft_args(ns_ctx *c, int nx, int ny, int nz, int ncomp, const void *in, void *out,
+                               Grid *g, Fft3 *f3) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (!in || !out || ncomp < 1 || ncomp > 65535 / (nx > 0 ? nx : 1)) return NS_ERR_ARG;
+    if (!supported_n(nx) || !supported_n(ny) || !supported_n(nz)) return NS_ERR_UNSUPPORTED_N;
+    *g = make_grid(nx, ny, nz, 1.0, 1.0, 1.0);
+    return fft3_of(c, *g, f3);
+}
+
+ns_status ns_fft_r2c_grid(ns_ctx *c, int nx, int ny, int nz, int ncomp, const void *in, void *out) {
+    Grid g;
+    Fft3 f3;
+    ns_status st = grid_fft_args(c, nx, ny, nz, ncomp, in, out, &g, &f3);
+    if (st != NS_OK) return st;
+    if (c->prec == NS_FP64) {
+        NS_CK(r2c_batch<double>((const double *)in, (double2 *)out, g, ncomp, f3, c->stream));
+    } else {
+        const StdGrid sg{nx, ny, nz, (const float2 *)f3.x->tw, (const float2 *)f3.y->tw,
+                         (const float2 *)f3.z->tw};
+        cudaError_t e = cudaSuccess;
+        if (std_r2c_fp32_grid((const float *)in, (float2 *)out, sg, ncomp, c->stream, &e))
+            NS_CK(e);
+        else
+            NS_CK(r2c_batch<float>((const float *)in, (float2 *)out, g, ncomp, f3, c->stream));
+    }
+    return NS_OK;
+}
+
+ns_status ns_fft_c2r_grid(ns_ctx *c, int nx, int ny, int nz, int ncomp, const void *in, void *out) {
+    Grid g;
+    Fft3 f3;
+    ns_status st = grid_fft_args(c, nx, ny, nz, ncomp, in, out, &g, &f3);
+    if (st != NS_OK) return st;
+    const size_t bytes = (size_t)g.M() * 2 * elem_bytes(c->prec);
+    if (c->gscratch_bytes < bytes) {
+        NS_CK(cudaStreamSynchronize(c->stream));
+        if (c->gscratch) dev_free(c->gscratch);
+        c->gscratch = nullptr;
+        c->gscratch_bytes = 0;
+        NS_CK(dalloc(&c->gscratch, bytes));
+        c->gscratch_bytes = bytes;
+    }
+    const long M = g.M(), V = g.V();
+    const StdGrid sg{nx, ny, nz, (const float2 *)f3.x->tw, (const float2 *)f3.y->tw, (const float2 *)f3.z->tw};
+    for (int k = 0; k < ncomp; k++) {
+        if (c->prec == NS_FP64) {
+            NS_CK(c2r_batch<double>((const double2 *)in + k * M, (double2 *)c->gscratch, (double *)out + k * V,
+                                    g, 1, f3, c->stream));
+        } else {
+            cudaError_t e = cudaSuccess;
+            if (std_c2r_fp32_grid((const float2 *)in + k * M, (float2 *)c->gscratch, (float *)out + k * V, sg,
+                                  c->stream, &e))
+                NS_CK(e);
+            else
+                NS_CK(c2r_batch<float>((const float2 *)in + k * M, (float2 *)c->gscratch, (float *)out + k * V,
+                                       g, 1, f3, c->stream));
+        }
+    }
+    return NS_OK;
+}
+
+int ns_run_nbins(const ns_run_params *p) {
+    if (!p || p->n < 2) return 0;
+    return grid_nbins(run_grid(*p));
 }
 
 ns_status ns_field_spectrum(ns_ctx *c, int run, int field, double *spec, int nbins, double *energy,
@@ -892,14 +1032,14 @@ ns_status ns_field_spectrum(ns_ctx *c, int run, int field, double *spec, int nbi
         return NS_ERR_ARG;
     Run &r = c->runs[run];
     if (field != 0 && !(field == 1 && r.p.mhd)) return NS_ERR_ARG;
-    const int nb = ns_nbins(r.n);
+    const int nb = grid_nbins(r.g);
     const long off = (long)field * 3 * r.M;
     if (use_fused(c))
         NS_CK(fused_spectrum(c->groups[r.group], r.gidx, field, nb, c->spec, c->ens, c->stream));
     else if (c->prec == NS_FP64)
-        NS_CK(plain_spectrum<double>((const double2 *)r.un + off, r.n, nb, c->spec, c->ens, c->stream));
+        NS_CK(plain_spectrum<double>((const double2 *)r.un + off, r.g, nb, c->spec, c->ens, c->stream));
     else
-        NS_CK(plain_spectrum<float>((const float2 *)r.un + off, r.n, nb, c->spec, c->ens, c->stream));
+        NS_CK(plain_spectrum<float>((const float2 *)r.un + off, r.g, nb, c->spec, c->ens, c->stream));
     std::vector<double> hs(nb), he(nb);
     NS_CK(cudaMemcpyAsync(hs.data(), c->spec, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     NS_CK(cudaMemcpyAsync(he.data(), c->ens, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -927,13 +1067,13 @@ ns_status ns_helicity(ns_ctx *c, int run, double *spec, int nbins, double *helic
     if (run < 0 || run >= (int)c->runs.size() || nbins < 0 || (nbins > 0 && !spec))
         return NS_ERR_ARG;
     Run &r = c->runs[run];
-    const int nb = ns_nbins(r.n);
+    const int nb = grid_nbins(r.g);
     if (use_fused(c))
         NS_CK(fused_helicity(c->groups[r.group], r.gidx, nb, c->spec, c->ens, c->stream));
     else if (c->prec == NS_FP64)
-        NS_CK(plain_helicity<double>((const double2 *)r.un, r.n, nb, c->spec, c->ens, c->stream));
+        NS_CK(plain_helicity<double>((const double2 *)r.un, r.g, nb, c->spec, c->ens, c->stream));
     else
-        NS_CK(plain_helicity<float>((const float2 *)r.un, r.n, nb, c->spec, c->ens, c->stream));
+        NS_CK(plain_helicity<float>((const float2 *)r.un, r.g, nb, c->spec, c->ens, c->stream));
     std::vector<double> hs(nb);
     NS_CK(cudaMemcpyAsync(hs.data(), c->spec, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     NS_CK(cudaStreamSynchronize(c->stream));
@@ -975,8 +1115,8 @@ ns_status ns_kernel_census(ns_ctx *c, int nsteps, ns_kernel_time *out, int max, 
     if (st != NS_OK) return st;
     if (nsteps < 1 || max < 0 || !count || (max > 0 && !out)) return NS_ERR_ARG;
     for (Run &r : c->runs) {
-        FftRes *f;
-        if ((st = get_fft(c, r.n, &f)) != NS_OK) return st;
+        FftRes *f[3];
+        if ((st = get_fft3(c, r.g, f)) != NS_OK) return st;
     }
     Tracer tr;
     tr.s = c->stream;

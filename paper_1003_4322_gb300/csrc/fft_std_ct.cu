@@ -1,14 +1,17 @@
-// fft_std_ct.cu -- the standalone FP32 3D transforms (ns_fft_r2c, ns_fft_c2r;
-// Sec. 2, Fig. 1) on compile-time-length kernels: the strided x and y passes
+// fft_std_ct.cu -- the standalone FP32 3D transforms (ns_fft_r2c, ns_fft_c2r,
+// and their grid forms; Sec. 2, Fig. 1) on compile-time-length kernels, one
+// length per axis: the strided x and y passes
 // reuse the column machinery of the fused form with every row present (the y
 // pass flattens (x, kz) into columns, so no tile is ragged), and the z pass is
 // a warp-level r2c / c2r with the line in shared memory.
 #include <map>
 #include <mutex>
+#include <tuple>
 
 #include "fft_ct.cuh"
 #include "fused.h"
 #include "fused_access.cuh"
+#include "ns_internal.h"
 
 namespace nsk {
 
@@ -199,24 +202,26 @@ template <class F> static float std_time(F launch, cudaStream_t s) {
 }
 
 // Column descriptors of the y and x passes over ncomp half-layout fields
-// [c][x][y][kz] (kz < Nh): y pass columns (x, kz), x pass columns (y, kz).
-static void std_descs(const float2 *in, float2 *out, int N, int ncomp, FzPass &py, FzPass &px) {
-    const long Nh = N / 2 + 1, plane = (long)N * Nh, M = (long)N * plane;
-    py = FzPass{in, out, plane, M, Nh, M, Nh, plane, ncomp, (int)Nh, 0, 0, 0, 0, plane};
+// [c][x][y][kz] of an nx x ny x nz grid (kz < Nh = nz/2 + 1): y pass columns
+// (x, kz), x pass columns (y, kz).
+static void std_descs(const float2 *in, float2 *out, const StdGrid &g, int ncomp, FzPass &py, FzPass &px) {
+    const long Nh = g.nz / 2 + 1, plane = (long)g.ny * Nh, M = (long)g.nx * plane;
+    py = FzPass{in, out, (long)g.nx * Nh, M, Nh, M, Nh, plane, ncomp, (int)Nh, 0, 0, 0, 0, plane};
     px = FzPass{in, out, plane, M, plane, M, plane, Nh, ncomp, (int)Nh, 0, 0, 0, 0, Nh};
 }
 
-// Choose the shapes on the first call for (N, direction), timing every
+// Choose the shapes on the first call for (grid, direction), timing every
 // compiled candidate on the call's own buffers (the passes run in place on
 // `work`, whose contents the real transform then overwrites); kept for the
 // life of the process.
-static bool std_shapes(int N, bool fwd, const void *zin, void *zout, float2 *work, int ncomp,
-                       const float2 *tw, cudaStream_t s, StdShapes *out) {
+static bool std_shapes(const StdGrid &g, bool fwd, const void *zin, void *zout, float2 *work, int ncomp,
+                       cudaStream_t s, StdShapes *out) {
     static std::mutex mu;
-    static std::map<std::pair<int, bool>, StdShapes> cache;
+    static std::map<std::tuple<int, int, int, bool>, StdShapes> cache;
+    const auto key = std::make_tuple(g.nx, g.ny, g.nz, fwd);
     {
-        std::lock_guard<std::mutex> g(mu);
-        auto it = cache.find({N, fwd});
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
         if (it != cache.end()) {
             *out = it->second;
             return true;
@@ -228,67 +233,80 @@ static bool std_shapes(int N, bool fwd, const void *zin, void *zout, float2 *wor
     StdShapes best;
     float bx = -1.f, by = -1.f, bz = -1.f;
     FzPass py, px;
-    std_descs(work, work, N, ncomp, py, px);
+    std_descs(work, work, g, ncomp, py, px);
     for (int E : Es)
         for (int ct = 8; ct <= 16; ct *= 2) {
-            if (!std_lookup_col(fwd, N, E, ct, &k)) continue;
-            const float ty = std_time([&]() { return launch_col(k, py, ct, tw, s); }, s);
-            if (ty > 0.f && (by < 0.f || ty < by)) { by = ty; best.ey = E; best.cy = ct; }
-            const float tx = std_time([&]() { return launch_col(k, px, ct, tw, s); }, s);
-            if (tx > 0.f && (bx < 0.f || tx < bx)) { bx = tx; best.ex = E; best.cx = ct; }
+            if (std_lookup_col(fwd, g.ny, E, ct, &k)) {
+                const float ty = std_time([&]() { return launch_col(k, py, ct, g.twy, s); }, s);
+                if (ty > 0.f && (by < 0.f || ty < by)) { by = ty; best.ey = E; best.cy = ct; }
+            }
+            if (std_lookup_col(fwd, g.nx, E, ct, &k)) {
+                const float tx = std_time([&]() { return launch_col(k, px, ct, g.twx, s); }, s);
+                if (tx > 0.f && (bx < 0.f || tx < bx)) { bx = tx; best.ex = E; best.cx = ct; }
+            }
         }
     const int Ezs[] = {16, 12, 8, 6};
-    const long nlines = (long)(fwd ? ncomp : 1) * N * N;
+    const long nlines = (long)(fwd ? ncomp : 1) * g.nx * g.ny;
     for (int E : Ezs)
         for (int w = 2; w <= 4; w *= 2) {
-            if (!zstd_lookup(N, fwd, E, w, &z)) continue;
-            const float t = std_time([&]() { return launch_zstd(z, zin, zout, nlines, tw, s); }, s);
+            if (!zstd_lookup(g.nz, fwd, E, w, &z)) continue;
+            const float t = std_time([&]() { return launch_zstd(z, zin, zout, nlines, g.twz, s); }, s);
             if (t > 0.f && (bz < 0.f || t < bz)) { bz = t; best.ez = E; best.wz = w; }
         }
     if (bx < 0.f || by < 0.f || bz < 0.f) return false;
-    std::lock_guard<std::mutex> g(mu);
-    cache[{N, fwd}] = best;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = best;
     *out = best;
+    return true;
+}
+
+bool std_r2c_fp32_grid(const float *in, float2 *out, const StdGrid &g, int ncomp, cudaStream_t s,
+                       cudaError_t *err) {
+    StdShapes sh;
+    if (!std_shapes(g, true, in, out, out, ncomp, s, &sh)) return false;
+    FzsKernel kx, ky;
+    ZctKernel kz;
+    if (!std_lookup_col(true, g.nx, sh.ex, sh.cx, &kx) || !std_lookup_col(true, g.ny, sh.ey, sh.cy, &ky) ||
+        !zstd_lookup(g.nz, true, sh.ez, sh.wz, &kz))
+        return false;
+    *err = launch_zstd(kz, in, out, (long)ncomp * g.nx * g.ny, g.twz, s);
+    if (*err != cudaSuccess) return true;
+    FzPass py, px;
+    std_descs(out, out, g, ncomp, py, px);
+    *err = launch_col(ky, py, sh.cy, g.twy, s);
+    if (*err != cudaSuccess) return true;
+    *err = launch_col(kx, px, sh.cx, g.twx, s);
+    return true;
+}
+
+bool std_c2r_fp32_grid(const float2 *in, float2 *tmp, float *out, const StdGrid &g, cudaStream_t s,
+                       cudaError_t *err) {
+    StdShapes sh;
+    if (!std_shapes(g, false, tmp, out, tmp, 1, s, &sh)) return false;
+    FzsKernel kx, ky;
+    ZctKernel kz;
+    if (!std_lookup_col(false, g.nx, sh.ex, sh.cx, &kx) || !std_lookup_col(false, g.ny, sh.ey, sh.cy, &ky) ||
+        !zstd_lookup(g.nz, false, sh.ez, sh.wz, &kz))
+        return false;
+    FzPass py, px;
+    std_descs(in, tmp, g, 1, py, px);
+    *err = launch_col(kx, px, sh.cx, g.twx, s);
+    if (*err != cudaSuccess) return true;
+    std_descs(tmp, tmp, g, 1, py, px);
+    *err = launch_col(ky, py, sh.cy, g.twy, s);
+    if (*err != cudaSuccess) return true;
+    *err = launch_zstd(kz, tmp, out, (long)g.nx * g.ny, g.twz, s);
     return true;
 }
 
 bool std_r2c_fp32(const float *in, float2 *out, int N, int ncomp, const float2 *tw, cudaStream_t s,
                   cudaError_t *err) {
-    StdShapes sh;
-    if (!std_shapes(N, true, in, out, out, ncomp, tw, s, &sh)) return false;
-    FzsKernel kx, ky;
-    ZctKernel kz;
-    if (!std_lookup_col(true, N, sh.ex, sh.cx, &kx) || !std_lookup_col(true, N, sh.ey, sh.cy, &ky) ||
-        !zstd_lookup(N, true, sh.ez, sh.wz, &kz))
-        return false;
-    *err = launch_zstd(kz, in, out, (long)ncomp * N * N, tw, s);
-    if (*err != cudaSuccess) return true;
-    FzPass py, px;
-    std_descs(out, out, N, ncomp, py, px);
-    *err = launch_col(ky, py, sh.cy, tw, s);
-    if (*err != cudaSuccess) return true;
-    *err = launch_col(kx, px, sh.cx, tw, s);
-    return true;
+    return std_r2c_fp32_grid(in, out, StdGrid{N, N, N, tw, tw, tw}, ncomp, s, err);
 }
 
 bool std_c2r_fp32(const float2 *in, float2 *tmp, float *out, int N, const float2 *tw, cudaStream_t s,
                   cudaError_t *err) {
-    StdShapes sh;
-    if (!std_shapes(N, false, tmp, out, tmp, 1, tw, s, &sh)) return false;
-    FzsKernel kx, ky;
-    ZctKernel kz;
-    if (!std_lookup_col(false, N, sh.ex, sh.cx, &kx) || !std_lookup_col(false, N, sh.ey, sh.cy, &ky) ||
-        !zstd_lookup(N, false, sh.ez, sh.wz, &kz))
-        return false;
-    FzPass py, px;
-    std_descs(in, tmp, N, 1, py, px);
-    *err = launch_col(kx, px, sh.cx, tw, s);
-    if (*err != cudaSuccess) return true;
-    std_descs(tmp, tmp, N, 1, py, px);
-    *err = launch_col(ky, py, sh.cy, tw, s);
-    if (*err != cudaSuccess) return true;
-    *err = launch_zstd(kz, tmp, out, (long)N * N, tw, s);
-    return true;
+    return std_c2r_fp32_grid(in, tmp, out, StdGrid{N, N, N, tw, tw, tw}, s, err);
 }
 
 }  // namespace nsk

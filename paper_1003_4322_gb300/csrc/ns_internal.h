@@ -58,6 +58,21 @@ struct Tracer {
         return _te;                                       \
     }())
 
+// Standalone FP32 transforms of an nx x ny x nz grid on the compile-time
+// kernels (axis lengths 64 ... 1024 of the compiled set), with the twiddle
+// table exp(-2 pi i t / n_i) of every axis: r2c of ncomp real fields into the
+// half layout, c2r of one half field through tmp (one half field).  False
+// when a length has no compiled kernel (nothing launched); else *err holds
+// the launch status.
+struct StdGrid {
+    int nx, ny, nz;
+    const float2 *twx, *twy, *twz;
+};
+bool std_r2c_fp32_grid(const float *in, float2 *out, const StdGrid &g, int ncomp, cudaStream_t s,
+                       cudaError_t *err);
+bool std_c2r_fp32_grid(const float2 *in, float2 *tmp, float *out, const StdGrid &g, cudaStream_t s,
+                       cudaError_t *err);
+
 // Radix plan for a line of length n = 2^a 3^b (false if n has another factor).
 bool make_plan(int n, Plan *pl);
 

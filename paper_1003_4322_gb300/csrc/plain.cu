@@ -1,29 +1,98 @@
 // plain.cu -- the unfused, unpruned ("plain") form of the solver's pointwise
-// steps on full half-layout arrays [3][N][N][N/2+1] (Sec. 2, Eqs. 1-2): the
-// vorticity i k x a, the cross product u x w on the grid, and the projected,
-// dealiased, forced integrating-factor RK2 update; plus the deterministic
-// FP64 reductions for energy, enstrophy and the shell spectrum (the global
-// quantities and spectra of Sec. 3).
+// steps on full half-layout arrays [3][N_x][N_y][N_z/2+1] (Sec. 2, Eqs. 1-2):
+// the vorticity i k x a, the cross product u x w on the grid, and the
+// projected, dealiased, forced integrating-factor RK2 update; plus the
+// deterministic FP64 reductions for energy, enstrophy and the shell spectrum
+// (the global quantities and spectra of Sec. 3).  Grids of N_x x N_y x N_z
+// points on boxes of sides 2 pi l_i (the domains of aspect ratio other than
+// one of Sec. 5) go through the same kernels: index m along axis i is the
+// wavenumber m / l_i, and the 2/3 rule holds per axis in grid indices.
+#include <math.h>
+
 #include "ns_internal.h"
 #include "plain.h"
 #include "reduce.cuh"
 
 namespace nsk {
 
-__device__ __forceinline__ int wavenum(int i, int n) { return 2 * i < n ? i : i - n; }
+static long gcd_l(long a, long b) { return b ? gcd_l(b, a % b) : a; }
+
+Grid make_grid(int nx, int ny, int nz, double lx, double ly, double lz) {
+    Grid g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.lx = lx;
+    g.ly = ly;
+    g.lz = lz;
+    g.ilx = 1.0 / lx;
+    g.ily = 1.0 / ly;
+    g.ilz = 1.0 / lz;
+    long D = nx;
+    D = D / gcd_l(D, ny) * ny;
+    D = D / gcd_l(D, nz) * nz;
+    g.D = D;
+    g.qx = D / nx;
+    g.qy = D / ny;
+    g.qz = D / nz;
+    g.unit = lx == 1.0 && ly == 1.0 && lz == 1.0;
+    g.cube = g.unit && nx == ny && ny == nz;
+    const double lm = fmax(lx, fmax(ly, lz));
+    g.lmax = 1.0 / (1.0 / lm);   // as the shell width 1 / k_min, k_min = 1 / max l
+    return g;
+}
+
+int grid_nbins(const Grid &g) {
+    if (g.cube) return (int)ceil(sqrt(3.0) * g.nx / 2.0) + 1;
+    const double cx = g.nx / 2 / g.lx, cy = g.ny / 2 / g.ly, cz = g.nz / 2 / g.lz;
+    const double kmin = 1.0 / fmax(g.lx, fmax(g.ly, g.lz));
+    return (int)ceil(sqrt(cx * cx + cy * cy + cz * cz) / kmin) + 1;
+}
+
+long grid_max_k2(const Grid &g) {
+    const long hx = g.nx / 2, hy = g.ny / 2, hz = g.nz / 2;
+    return hx * hx + hy * hy + hz * hz;
+}
+
+// Wavevector of a mode in precision T and |k|^2.  On the unit box (UNIT) the
+// wavenumbers are the integer indices and |k|^2 an integer (the index of the
+// factor tables); elsewhere k = m / l is formed from the reciprocals in FP64.
+template <typename T, bool UNIT> struct Wave {
+    T kx, ky, kz;
+    double k2;     // |k|^2
+    long i2;       // |k|^2 as an integer (UNIT only)
+    __device__ __forceinline__ Wave(const Idx &q, const Grid &g) {
+        if constexpr (UNIT) {
+            i2 = (long)q.x * q.x + (long)q.y * q.y + (long)q.z * q.z;
+            kx = (T)q.x;
+            ky = (T)q.y;
+            kz = (T)q.z;
+            k2 = (double)i2;
+        } else {
+            const double dx = kmul(q.x, g.ilx), dy = kmul(q.y, g.ily), dz = kmul(q.z, g.ilz);
+            i2 = 0;
+            kx = (T)dx;
+            ky = (T)dy;
+            kz = (T)dz;
+            k2 = dx * dx + dy * dy + dz * dz;
+        }
+    }
+    // exp(-c |k|^2): the table entry by integer |k|^2 on the unit box, else in FP64
+    __device__ __forceinline__ T factor(const T *etab, double c) const {
+        if constexpr (UNIT) return etab[i2];
+        else return (T)exp(-c * k2);
+    }
+};
 
 // ---------------------------------------------------------------- curl
 
-template <typename T>
+template <typename T, bool UNIT>
 __global__ void k_curl(const typename Cx<T>::type *__restrict__ a, typename Cx<T>::type *__restrict__ w,
-                       int n, long M) {
+                       Grid g, long M) {
     typedef typename Cx<T>::type C;
-    const int nh = n / 2 + 1;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        const int kz = (int)(m % nh);
-        const int iy = (int)((m / nh) % n);
-        const int ix = (int)(m / ((long)nh * n));
-        const T kx = (T)wavenum(ix, n), ky = (T)wavenum(iy, n), kzz = (T)kz;
+        const Wave<T, UNIT> k(mode_at(m, g), g);
+        const T kx = k.kx, ky = k.ky, kzz = k.kz;
         const C ax = a[m], ay = a[M + m], az = a[2 * M + m];
         // w = i k x a
         w[m] = cmul_i<1>(csub(cscale(az, ky), cscale(ay, kzz)));
@@ -66,54 +135,42 @@ __global__ void k_cross_mhd(T *g, long V) {
 
 // ---------------------------------------------------------------- update
 
-// ABC forcing coefficients at signed k (closed form of
-// f = F (sin kf z + cos kf y, sin kf x + cos kf z, sin kf y + cos kf x)).
+// ABC forcing coefficients at signed grid index k (closed form of
+// f = F (sin kf z + cos kf y, sin kf x + cos kf z, sin kf y + cos kf x));
+// kf sits at grid index kf l_i along axis i (mfx, mfy, mfz).
 template <typename C, typename T>
-__device__ __forceinline__ void abc_forcing(int kx, int ky, int kz, int kf, T F, C &fx, C &fy, C &fz) {
+__device__ __forceinline__ void abc_forcing(const Idx &k, const UpdateArgs &ua, T F, C &fx, C &fy, C &fz) {
     const T h = F * (T)0.5;
-    if (kf <= 0) return;
-    if (kx == 0 && ky == 0 && kz == kf) {          // e^{i kf z}: sin -> -i/2, cos -> 1/2
+    if (ua.force_k <= 0) return;
+    if (k.x == 0 && k.y == 0 && k.z == ua.mfz) {   // e^{i kf z}: sin -> -i/2, cos -> 1/2
         fx = cadd(fx, mkc((T)0, -h));
         fy = cadd(fy, mkc(h, (T)0));
     }
-    if (kx == 0 && kz == 0 && (ky == kf || ky == -kf)) {
+    if (k.x == 0 && k.z == 0 && (k.y == ua.mfy || k.y == -ua.mfy)) {
         fx = cadd(fx, mkc(h, (T)0));
-        fz = cadd(fz, mkc((T)0, ky > 0 ? -h : h));
+        fz = cadd(fz, mkc((T)0, k.y > 0 ? -h : h));
     }
-    if (ky == 0 && kz == 0 && (kx == kf || kx == -kf)) {
-        fy = cadd(fy, mkc((T)0, kx > 0 ? -h : h));
+    if (k.y == 0 && k.z == 0 && (k.x == ua.mfx || k.x == -ua.mfx)) {
+        fy = cadd(fy, mkc((T)0, k.x > 0 ? -h : h));
         fz = cadd(fz, mkc(h, (T)0));
     }
 }
 
-__device__ __forceinline__ bool kept(int kx, int ky, int kz, int n, int dealias) {
-    int m = abs(kx);
-    m = max(m, abs(ky));
-    m = max(m, abs(kz));
-    if (dealias == 2) return 2 * m < n && 9L * (kx * kx + ky * ky + kz * kz) < 2L * n * n;
-    if (3 * m >= n) return false;
-    if (dealias == 1 && 9L * (kx * kx + ky * ky + kz * kz) >= (long)n * n) return false;
-    return true;
-}
 
 // Stage 1: a1 = E (a + dt N);  stage 2: a = E a / 2 + (a1 + dt N) / 2, with
 // N = P Pi (nl / N^3) + f_hat; every mode outside Pi (and k = 0) set to 0.
-template <typename T>
+template <typename T, bool UNIT>
 __global__ void k_update(typename Cx<T>::type *__restrict__ a, typename Cx<T>::type *__restrict__ a1,
                          const typename Cx<T>::type *__restrict__ nl, const T *__restrict__ etab,
-                         int n, long M, UpdateArgs ua) {
+                         Grid g, long M, UpdateArgs ua) {
     typedef typename Cx<T>::type C;
-    const int nh = n / 2 + 1;
-    const T inv = (T)(1.0 / ((double)n * n * n));
+    const T inv = (T)(1.0 / ((double)g.nx * g.ny * g.nz));
     const T dt = (T)ua.dt, F = (T)ua.force_amp;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        const int kz = (int)(m % nh);
-        const int iy = (int)((m / nh) % n);
-        const int ix = (int)(m / ((long)nh * n));
-        const int kx = wavenum(ix, n), ky = wavenum(iy, n);
-        const int k2 = kx * kx + ky * ky + kz * kz;
+        const Idx q = mode_at(m, g);
+        const Wave<T, UNIT> k(q, g);
         C o0 = czero<C>(), o1 = czero<C>(), o2 = czero<C>();
-        if (kept(kx, ky, kz, n, ua.dealias) && k2 > 0) {
+        if (kept(q, g, ua.dealias) && k.k2 > 0) {
             C vx = cscale(nl[m], inv), vy = cscale(nl[M + m], inv), vz = cscale(nl[2 * M + m], inv);
             if (ua.rot != 0.0) {   // Coriolis -2 rot z x u of the stage's state, before P
                 const C *cur = ua.stage == 1 ? a : a1;
@@ -121,13 +178,13 @@ __global__ void k_update(typename Cx<T>::type *__restrict__ a, typename Cx<T>::t
                 vx = cadd(vx, cscale(cur[M + m], r2));
                 vy = csub(vy, cscale(cur[m], r2));
             }
-            const T fkx = (T)kx, fky = (T)ky, fkz = (T)kz, ik2 = (T)1 / (T)k2;
+            const T fkx = k.kx, fky = k.ky, fkz = k.kz, ik2 = (T)1 / (T)k.k2;
             const C kv = cadd(cadd(cscale(vx, fkx), cscale(vy, fky)), cscale(vz, fkz));
             vx = csub(vx, cscale(kv, fkx * ik2));
             vy = csub(vy, cscale(kv, fky * ik2));
             vz = csub(vz, cscale(kv, fkz * ik2));
-            abc_forcing(kx, ky, kz, ua.force_k, F, vx, vy, vz);
-            const T e = etab[k2];
+            abc_forcing(q, ua, F, vx, vy, vz);
+            const T e = k.factor(etab, ua.nu_dt);
             if (ua.stage == 1) {
                 o0 = cscale(cadd(a[m], cscale(vx, dt)), e);
                 o1 = cscale(cadd(a[M + m], cscale(vy, dt)), e);
@@ -149,29 +206,25 @@ __global__ void k_update(typename Cx<T>::type *__restrict__ a, typename Cx<T>::t
 // Induction update of the magnetic field: N_b = Pi (i k x nb / N^3) with nb
 // the transform of u x b, then the IF-RK2 stage with the factor of eta.  The
 // mean field b(k = 0) has N_b = 0 and factor 1, so it is carried unchanged.
-template <typename T>
+template <typename T, bool UNIT>
 __global__ void k_update_b(typename Cx<T>::type *__restrict__ b, typename Cx<T>::type *__restrict__ b1,
                            const typename Cx<T>::type *__restrict__ nb, const T *__restrict__ etab,
-                           int n, long M, int stage, double dt_, int dealias) {
+                           Grid g, long M, int stage, double dt_, double eta_dt, int dealias) {
     typedef typename Cx<T>::type C;
-    const int nh = n / 2 + 1;
-    const T inv = (T)(1.0 / ((double)n * n * n));
+    const T inv = (T)(1.0 / ((double)g.nx * g.ny * g.nz));
     const T dt = (T)dt_;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        const int kz = (int)(m % nh);
-        const int iy = (int)((m / nh) % n);
-        const int ix = (int)(m / ((long)nh * n));
-        const int kx = wavenum(ix, n), ky = wavenum(iy, n);
-        const int k2 = kx * kx + ky * ky + kz * kz;
+        const Idx q = mode_at(m, g);
+        const Wave<T, UNIT> k(q, g);
         C o0 = czero<C>(), o1 = czero<C>(), o2 = czero<C>();
-        if (kept(kx, ky, kz, n, dealias)) {
+        if (kept(q, g, dealias)) {
             const C vx = cscale(nb[m], inv), vy = cscale(nb[M + m], inv), vz = cscale(nb[2 * M + m], inv);
-            const T fkx = (T)kx, fky = (T)ky, fkz = (T)kz;
+            const T fkx = k.kx, fky = k.ky, fkz = k.kz;
             // i k x v
             const C nx = cmul_i<1>(csub(cscale(vz, fky), cscale(vy, fkz)));
             const C ny = cmul_i<1>(csub(cscale(vx, fkz), cscale(vz, fkx)));
             const C nz = cmul_i<1>(csub(cscale(vy, fkx), cscale(vx, fky)));
-            const T e = etab[k2];
+            const T e = k.factor(etab, eta_dt);
             if (stage == 1) {
                 o0 = cscale(cadd(b[m], cscale(nx, dt)), e);
                 o1 = cscale(cadd(b[M + m], cscale(ny, dt)), e);
@@ -190,17 +243,22 @@ __global__ void k_update_b(typename Cx<T>::type *__restrict__ b, typename Cx<T>:
     }
 }
 
-// Phase-shift dealiasing: dst = src exp(i k.D), D = (pi/N)(1,1,1), the
-// coefficients of the field on the shifted grid (three components).
+// k.D / pi for the shift by half a grid spacing along every axis:
+// sum_i m_i / N_i = (sum_i m_i q_i) / D, (m_x + m_y + m_z) / N on the cube.
+__device__ __forceinline__ double shift_phase(const Idx &q, const Grid &g) {
+    return (double)(q.x * g.qx + q.y * g.qy + q.z * g.qz) / (double)g.D;
+}
+
+// Phase-shift dealiasing: dst = src exp(i k.D), D half a grid spacing along
+// every axis, the coefficients of the field on the shifted grid (three
+// components).
 template <typename T>
 __global__ void k_phase(const typename Cx<T>::type *__restrict__ src, typename Cx<T>::type *__restrict__ dst,
-                        int n, long M) {
+                        Grid g, long M) {
     typedef typename Cx<T>::type C;
-    const int nh = n / 2 + 1;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        const int kz = (int)(m % nh), iy = (int)((m / nh) % n), ix = (int)(m / ((long)nh * n));
         double s, c;
-        sincospi((double)(wavenum(ix, n) + wavenum(iy, n) + kz) / n, &s, &c);
+        sincospi(shift_phase(mode_at(m, g), g), &s, &c);
         const C ph = mkc((T)c, (T)s);
 #pragma unroll
         for (int d = 0; d < 3; d++) dst[d * M + m] = cmul(src[d * M + m], ph);
@@ -211,13 +269,11 @@ __global__ void k_phase(const typename Cx<T>::type *__restrict__ src, typename C
 // back, on the shifted grid, averaged (three components).
 template <typename T>
 __global__ void k_phase_avg(typename Cx<T>::type *__restrict__ acc, const typename Cx<T>::type *__restrict__ sh,
-                            int n, long M) {
+                            Grid g, long M) {
     typedef typename Cx<T>::type C;
-    const int nh = n / 2 + 1;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        const int kz = (int)(m % nh), iy = (int)((m / nh) % n), ix = (int)(m / ((long)nh * n));
         double s, c;
-        sincospi((double)(wavenum(ix, n) + wavenum(iy, n) + kz) / n, &s, &c);
+        sincospi(shift_phase(mode_at(m, g), g), &s, &c);
         const C ph = mkc((T)c, (T)-s);
 #pragma unroll
         for (int d = 0; d < 3; d++)
@@ -229,19 +285,16 @@ __global__ void k_phase_avg(typename Cx<T>::type *__restrict__ acc, const typena
 
 // Per-block partial energy and enstrophy of a half-layout state.  Block b
 // owns the contiguous chunk [b*chunk, (b+1)*chunk) of modes.
-template <typename T>
+template <typename T, bool UNIT>
 __global__ void __launch_bounds__(256)
-k_energy_partials(const typename Cx<T>::type *__restrict__ a, int n, long M, long chunk, double *part) {
+k_energy_partials(const typename Cx<T>::type *__restrict__ a, Grid g, long M, long chunk, double *part) {
     __shared__ double sh[512];
-    const int nh = n / 2 + 1;
     double e = 0.0, om = 0.0;
     const long beg = blockIdx.x * chunk, end = min(M, beg + chunk);
     for (long m = beg + threadIdx.x; m < end; m += blockDim.x) {
-        const int kz = (int)(m % nh);
-        const int iy = (int)((m / nh) % n);
-        const int ix = (int)(m / ((long)nh * n));
-        const double kx = wavenum(ix, n), ky = wavenum(iy, n);
-        const double w = (kz == 0 || 2 * kz == n) ? 0.5 : 1.0;   // 1/2 * multiplicity
+        const Idx q = mode_at(m, g);
+        const Wave<double, UNIT> k(q, g);
+        const double w = (q.z == 0 || 2 * q.z == g.nz) ? 0.5 : 1.0;   // 1/2 * multiplicity
         double a2 = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -249,7 +302,7 @@ k_energy_partials(const typename Cx<T>::type *__restrict__ a, int n, long M, lon
             a2 += re * re + im * im;
         }
         e += w * a2;
-        om += w * a2 * (kx * kx + ky * ky + (double)kz * kz);
+        om += w * a2 * k.k2;
     }
     block_sum2(e, om, sh);
     if (threadIdx.x == 0) {
@@ -307,6 +360,80 @@ template <typename T> struct HalfHelAcc {
     }
 };
 
+// Per-mode sums for grids other than the cube: signed indices and their
+// wavenumbers -> |a|^2 summed over components, or the helicity density.
+template <typename T> struct GridAcc {
+    const typename Cx<T>::type *a;
+    Grid g;
+    __device__ double operator()(int mx, int my, int mz, double, double, double) const {
+        const long m = ((long)((mx + g.nx) % g.nx) * g.ny + (my + g.ny) % g.ny) * g.nzh() + mz;
+        const long M = g.M();
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const double re = (double)a[c * M + m].x, im = (double)a[c * M + m].y;
+            s += re * re + im * im;
+        }
+        return s;
+    }
+};
+
+template <typename T> struct GridHelAcc {
+    const typename Cx<T>::type *a;
+    Grid g;
+    __device__ double operator()(int mx, int my, int mz, double kx, double ky, double kz) const {
+        const long m = ((long)((mx + g.nx) % g.nx) * g.ny + (my + g.ny) % g.ny) * g.nzh() + mz;
+        const long M = g.M();
+        return helicity_density(kx, ky, kz, a[m].x, a[m].y, a[M + m].x, a[M + m].y, a[2 * M + m].x,
+                                a[2 * M + m].y);
+    }
+};
+
+// Shell spectrum on any grid and box: block K sums the modes whose shell
+// round-half-up(|k| lmax) is K.  Threads take the (m_x, m_y) pairs that can
+// reach the shell; for each, every m_z of a slightly widened interval is
+// tested with the shell formula itself, in FP64 with each operation rounded
+// as written (no contraction), so that the binning is the definition's.
+// Fixed per-thread order and a fixed tree: deterministic.
+template <class Acc>
+__global__ void __launch_bounds__(256)
+k_grid_spectrum(Acc acc, Grid g, int nbins, double *spec, double *aux) {
+    __shared__ double sh[512];
+    const int K = blockIdx.x;
+    if (K >= nbins) return;
+    const double hi = (K + 0.5) / g.lmax, lo = (K - 0.5) / g.lmax;
+    const int bx = (int)(hi * g.lx) + 1, by = (int)(hi * g.ly) + 1;
+    const int x0 = max(-bx, -g.nx / 2), x1 = min(bx, g.nx / 2 - 1);
+    const int y0 = max(-by, -g.ny / 2), y1 = min(by, g.ny / 2 - 1);
+    const long sy = y1 - y0 + 1, pairs = (long)(x1 - x0 + 1) * sy;
+    const double hi2 = hi * hi * (1.0 + 1e-9) + 1e-12;
+    double e = 0.0, om = 0.0;
+    for (long p = threadIdx.x; p < pairs; p += blockDim.x) {
+        const int mx = x0 + (int)(p / sy), my = y0 + (int)(p % sy);
+        const double kx = kof(mx, g.lx), ky = kof(my, g.ly);
+        const double r2 = __dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky));
+        if (r2 > hi2) continue;
+        const double zlo = lo > 0.0 && lo * lo > r2 ? sqrt(lo * lo - r2) : 0.0;
+        const double zhi = sqrt(fmax(0.0, hi2 - r2));
+        const int z0 = max(0, (int)floor(zlo * g.lz) - 1);
+        const int z1 = min(g.nz / 2, (int)ceil(zhi * g.lz) + 1);
+        for (int mz = z0; mz <= z1; mz++) {
+            const double kz = kof(mz, g.lz);
+            const double k2 = __dadd_rn(r2, __dmul_rn(kz, kz));
+            if ((long)floor(__dadd_rn(__dmul_rn(__dsqrt_rn(k2), g.lmax), 0.5)) != K) continue;
+            const double w = (mz == 0 || 2 * mz == g.nz) ? 0.5 : 1.0;
+            const double de = w * acc(mx, my, mz, kx, ky, kz);
+            e += de;
+            om += de * k2;
+        }
+    }
+    block_sum2(e, om, sh);
+    if (threadIdx.x == 0) {
+        spec[K] = e;
+        aux[K] = om;
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 
 static unsigned grid_for(long work, int threads) {
@@ -316,87 +443,105 @@ static unsigned grid_for(long work, int threads) {
 }
 
 template <typename T>
-cudaError_t plain_curl(const typename Cx<T>::type *a, typename Cx<T>::type *w, int n, cudaStream_t s) {
-    const long M = (long)n * n * (n / 2 + 1);
-    k_curl<T><<<grid_for(M, 256), 256, 0, s>>>(a, w, n, M);
+cudaError_t plain_curl(const typename Cx<T>::type *a, typename Cx<T>::type *w, const Grid &g, cudaStream_t s) {
+    const long M = g.M();
+    if (g.unit) k_curl<T, true><<<grid_for(M, 256), 256, 0, s>>>(a, w, g, M);
+    else k_curl<T, false><<<grid_for(M, 256), 256, 0, s>>>(a, w, g, M);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t plain_cross(T *u, const T *w, int n, cudaStream_t s) {
-    const long V = (long)n * n * n;
+cudaError_t plain_cross(T *u, const T *w, const Grid &g, cudaStream_t s) {
+    const long V = g.V();
     k_cross<T><<<grid_for(V, 256), 256, 0, s>>>(u, w, V);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t plain_cross_mhd(T *g, int n, cudaStream_t s) {
-    const long V = (long)n * n * n;
-    k_cross_mhd<T><<<grid_for(V, 256), 256, 0, s>>>(g, V);
+cudaError_t plain_cross_mhd(T *f, const Grid &g, cudaStream_t s) {
+    const long V = g.V();
+    k_cross_mhd<T><<<grid_for(V, 256), 256, 0, s>>>(f, V);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t plain_update_b(typename Cx<T>::type *b, typename Cx<T>::type *b1,
-                           const typename Cx<T>::type *nb, const T *etab, int n, int stage, double dt,
-                           int dealias, cudaStream_t s) {
-    const long M = (long)n * n * (n / 2 + 1);
-    k_update_b<T><<<grid_for(M, 256), 256, 0, s>>>(b, b1, nb, etab, n, M, stage, dt, dealias);
+                           const typename Cx<T>::type *nb, const T *etab, const Grid &g, int stage,
+                           double dt, double eta_dt, int dealias, cudaStream_t s) {
+    const long M = g.M();
+    if (g.unit)
+        k_update_b<T, true><<<grid_for(M, 256), 256, 0, s>>>(b, b1, nb, etab, g, M, stage, dt, eta_dt, dealias);
+    else
+        k_update_b<T, false><<<grid_for(M, 256), 256, 0, s>>>(b, b1, nb, etab, g, M, stage, dt, eta_dt, dealias);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t plain_phase(const typename Cx<T>::type *src, typename Cx<T>::type *dst, int n, cudaStream_t s) {
-    const long M = (long)n * n * (n / 2 + 1);
-    k_phase<T><<<grid_for(M, 256), 256, 0, s>>>(src, dst, n, M);
+cudaError_t plain_phase(const typename Cx<T>::type *src, typename Cx<T>::type *dst, const Grid &g,
+                        cudaStream_t s) {
+    const long M = g.M();
+    k_phase<T><<<grid_for(M, 256), 256, 0, s>>>(src, dst, g, M);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t plain_phase_avg(typename Cx<T>::type *acc, const typename Cx<T>::type *sh, int n, cudaStream_t s) {
-    const long M = (long)n * n * (n / 2 + 1);
-    k_phase_avg<T><<<grid_for(M, 256), 256, 0, s>>>(acc, sh, n, M);
+cudaError_t plain_phase_avg(typename Cx<T>::type *acc, const typename Cx<T>::type *sh, const Grid &g,
+                            cudaStream_t s) {
+    const long M = g.M();
+    k_phase_avg<T><<<grid_for(M, 256), 256, 0, s>>>(acc, sh, g, M);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t plain_update(typename Cx<T>::type *a, typename Cx<T>::type *a1,
-                         const typename Cx<T>::type *nl, const T *etab, int n, const UpdateArgs &ua,
-                         cudaStream_t s) {
-    const long M = (long)n * n * (n / 2 + 1);
-    k_update<T><<<grid_for(M, 256), 256, 0, s>>>(a, a1, nl, etab, n, M, ua);
+                         const typename Cx<T>::type *nl, const T *etab, const Grid &g,
+                         const UpdateArgs &ua, cudaStream_t s) {
+    const long M = g.M();
+    if (g.unit) k_update<T, true><<<grid_for(M, 256), 256, 0, s>>>(a, a1, nl, etab, g, M, ua);
+    else k_update<T, false><<<grid_for(M, 256), 256, 0, s>>>(a, a1, nl, etab, g, M, ua);
     return cudaGetLastError();
 }
 
-int energy_nparts(int n) {
-    const long M = (long)n * n * (n / 2 + 1);
+int energy_nparts(long M) {
     long np = (M + 4095) / 4096;
     if (np > 1024) np = 1024;
     return (int)(np < 1 ? 1 : np);
 }
 
 template <typename T>
-cudaError_t plain_energy_partials(const typename Cx<T>::type *a, int n, double *part, cudaStream_t s) {
-    const long M = (long)n * n * (n / 2 + 1);
-    const int np = energy_nparts(n);
+cudaError_t plain_energy_partials(const typename Cx<T>::type *a, const Grid &g, double *part,
+                                  cudaStream_t s) {
+    const long M = g.M();
+    const int np = energy_nparts(M);
     const long chunk = (M + np - 1) / np;
-    k_energy_partials<T><<<np, 256, 0, s>>>(a, n, M, chunk, part);
+    if (g.unit) k_energy_partials<T, true><<<np, 256, 0, s>>>(a, g, M, chunk, part);
+    else k_energy_partials<T, false><<<np, 256, 0, s>>>(a, g, M, chunk, part);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t plain_spectrum(const typename Cx<T>::type *a, int n, int nbins, double *spec, double *ens,
-                           cudaStream_t s) {
-    HalfAcc<T> acc{a, n, (long)n * n * (n / 2 + 1)};
-    k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, n, nbins, spec, ens);
+cudaError_t plain_spectrum(const typename Cx<T>::type *a, const Grid &g, int nbins, double *spec,
+                           double *ens, cudaStream_t s) {
+    if (g.cube) {
+        HalfAcc<T> acc{a, g.nx, g.M()};
+        k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, g.nx, nbins, spec, ens);
+    } else {
+        GridAcc<T> acc{a, g};
+        k_grid_spectrum<<<nbins, 256, 0, s>>>(acc, g, nbins, spec, ens);
+    }
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t plain_helicity(const typename Cx<T>::type *a, int n, int nbins, double *spec, double *aux,
-                           cudaStream_t s) {
-    HalfHelAcc<T> acc{a, n, (long)n * n * (n / 2 + 1)};
-    k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, n, nbins, spec, aux);
+cudaError_t plain_helicity(const typename Cx<T>::type *a, const Grid &g, int nbins, double *spec,
+                           double *aux, cudaStream_t s) {
+    if (g.cube) {
+        HalfHelAcc<T> acc{a, g.nx, g.M()};
+        k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, g.nx, nbins, spec, aux);
+    } else {
+        GridHelAcc<T> acc{a, g};
+        k_grid_spectrum<<<nbins, 256, 0, s>>>(acc, g, nbins, spec, aux);
+    }
     return cudaGetLastError();
 }
 
@@ -407,19 +552,22 @@ cudaError_t energy_final(const double *part, int nparts, double *series, int cap
 }
 
 #define NSK_INST(T)                                                                                \
-    template cudaError_t plain_curl<T>(const Cx<T>::type *, Cx<T>::type *, int, cudaStream_t);    \
-    template cudaError_t plain_cross<T>(T *, const T *, int, cudaStream_t);                       \
-    template cudaError_t plain_cross_mhd<T>(T *, int, cudaStream_t);                              \
-    template cudaError_t plain_phase<T>(const Cx<T>::type *, Cx<T>::type *, int, cudaStream_t);   \
-    template cudaError_t plain_phase_avg<T>(Cx<T>::type *, const Cx<T>::type *, int, cudaStream_t); \
+    template cudaError_t plain_curl<T>(const Cx<T>::type *, Cx<T>::type *, const Grid &, cudaStream_t); \
+    template cudaError_t plain_cross<T>(T *, const T *, const Grid &, cudaStream_t);              \
+    template cudaError_t plain_cross_mhd<T>(T *, const Grid &, cudaStream_t);                     \
+    template cudaError_t plain_phase<T>(const Cx<T>::type *, Cx<T>::type *, const Grid &, cudaStream_t); \
+    template cudaError_t plain_phase_avg<T>(Cx<T>::type *, const Cx<T>::type *, const Grid &,     \
+                                            cudaStream_t);                                        \
     template cudaError_t plain_update_b<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,     \
-                                           const T *, int, int, double, int, cudaStream_t);       \
-    template cudaError_t plain_update<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,       \
-                                         const T *, int, const UpdateArgs &, cudaStream_t);       \
-    template cudaError_t plain_energy_partials<T>(const Cx<T>::type *, int, double *, cudaStream_t); \
-    template cudaError_t plain_spectrum<T>(const Cx<T>::type *, int, int, double *, double *,     \
+                                           const T *, const Grid &, int, double, double, int,     \
                                            cudaStream_t);                                         \
-    template cudaError_t plain_helicity<T>(const Cx<T>::type *, int, int, double *, double *,     \
+    template cudaError_t plain_update<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,       \
+                                         const T *, const Grid &, const UpdateArgs &, cudaStream_t); \
+    template cudaError_t plain_energy_partials<T>(const Cx<T>::type *, const Grid &, double *,    \
+                                                  cudaStream_t);                                  \
+    template cudaError_t plain_spectrum<T>(const Cx<T>::type *, const Grid &, int, double *, double *, \
+                                           cudaStream_t);                                         \
+    template cudaError_t plain_helicity<T>(const Cx<T>::type *, const Grid &, int, double *, double *, \
                                            cudaStream_t);
 NSK_INST(float)
 NSK_INST(double)

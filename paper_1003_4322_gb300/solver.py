@@ -12,9 +12,12 @@ class Solver:
     """Integrating-factor RK2 pseudospectral solver for one or more runs.
 
     runs: list of dicts with keys n, nu, dt and optionally force_amp,
-    force_k, dealias, rot, and eta with mhd = 1 for MHD runs.
-    prec: "fp64" (plain form) or "fp32" (fused form; plain form when a run
-    is MHD).
+    force_k, dealias, rot, eta with mhd = 1 for MHD runs, and ny, nz, lx,
+    ly, lz for a grid of n x ny x nz points on the box of sides
+    2 pi (lx, ly, lz).
+    prec: "fp64" (plain form) or "fp32" (fused form; plain FP32 form when a
+    run is MHD at a size without a fused kernel, uses phase shifts, or is not
+    the (2 pi)^3 cube).
     """
 
     def __init__(self, runs, prec: str = "fp32", stream=None):
@@ -42,43 +45,62 @@ class Solver:
     def n(self, run: int = 0) -> int:
         return int(self.runs[run]["n"])
 
+    def dims(self, run: int = 0) -> tuple:
+        """Grid points (N_x, N_y, N_z) of a run."""
+        r = self.runs[run]
+        n = int(r["n"])
+        return (n, int(r.get("ny", 0)) or n, int(r.get("nz", 0)) or n)
+
+    def half_shape(self, run: int = 0, ncomp: int = 3) -> tuple:
+        nx, ny, nz = self.dims(run)
+        return (ncomp, nx, ny, nz // 2 + 1)
+
+    def _checked(self, a, run: int, out: bool = False):
+        """The buffer must hold exactly the run's half layout in complex128
+        (an output buffer as it is: it is written in place)."""
+        if isinstance(a, np.ndarray):
+            if out and (a.dtype != np.complex128 or not a.flags["C_CONTIGUOUS"]):
+                raise TypeError("output buffers are C-contiguous complex128")
+            a = np.ascontiguousarray(a, dtype=np.complex128)
+        elif str(getattr(a, "dtype", "")) != "torch.complex128":
+            raise TypeError("state buffers are complex128")
+        if tuple(a.shape) != self.half_shape(run):
+            raise ValueError(f"state has shape {tuple(a.shape)}, run {run} wants {self.half_shape(run)}")
+        return a
+
     def set_state(self, uhat, run: int = 0) -> None:
-        """uhat: complex128 half layout [3][N][N][N/2+1] (numpy or torch)."""
-        if isinstance(uhat, np.ndarray):
-            uhat = np.ascontiguousarray(uhat, dtype=np.complex128)
-        nat.ns_set_state(self.ctx, run, uhat)
+        """uhat: complex128 half layout [3][N_x][N_y][N_z/2+1] (numpy or torch)."""
+        nat.ns_set_state(self.ctx, run, self._checked(uhat, run))
 
     def get_state(self, run: int = 0, out=None):
-        n = self.n(run)
         if out is None:
-            out = np.empty((3, n, n, n // 2 + 1), dtype=np.complex128)
+            out = np.empty(self.half_shape(run), dtype=np.complex128)
+        out = self._checked(out, run, out=True)
         nat.ns_get_state(self.ctx, run, out)
         return out
 
     def set_field(self, field: int, uhat, run: int = 0) -> None:
         """field 0: velocity, 1: magnetic field of an MHD run."""
-        if isinstance(uhat, np.ndarray):
-            uhat = np.ascontiguousarray(uhat, dtype=np.complex128)
-        nat.ns_set_field(self.ctx, run, field, uhat)
+        nat.ns_set_field(self.ctx, run, field, self._checked(uhat, run))
 
     def get_field(self, field: int, run: int = 0, out=None):
-        n = self.n(run)
         if out is None:
-            out = np.empty((3, n, n, n // 2 + 1), dtype=np.complex128)
+            out = np.empty(self.half_shape(run), dtype=np.complex128)
+        out = self._checked(out, run, out=True)
         nat.ns_get_field(self.ctx, run, field, out)
         return out
 
     def field_spectrum(self, field: int, run: int = 0):
-        return nat.ns_field_spectrum(self.ctx, run, field, self.n(run))
+        return nat.ns_field_spectrum(self.ctx, run, field, self.runs[run])
 
     def step(self, nsteps: int = 1) -> None:
         nat.ns_step(self.ctx, nsteps)
 
     def energy_spectrum(self, run: int = 0):
-        return nat.ns_energy_spectrum(self.ctx, run, self.n(run))
+        return nat.ns_energy_spectrum(self.ctx, run, self.runs[run])
 
     def helicity(self, run: int = 0):
-        return nat.ns_helicity(self.ctx, run, self.n(run))
+        return nat.ns_helicity(self.ctx, run, self.runs[run])
 
     def series(self, run: int = 0, count: int = 4096):
         return nat.ns_series(self.ctx, run, count)
@@ -93,3 +115,19 @@ class Solver:
     def fft_c2r(self, uh, out) -> None:
         n = uh.shape[-2]
         nat.ns_fft_c2r(self.ctx, n, out.numel() // n ** 3, uh, out)
+
+    def fft_r2c_grid(self, u, out) -> None:
+        """r2c of device fields [ncomp][N_x][N_y][N_z] into [ncomp][N_x][N_y][N_z/2+1]."""
+        nx, ny, nz = u.shape[-3:]
+        nc = u.numel() // (nx * ny * nz)
+        if tuple(out.shape[-3:]) != (nx, ny, nz // 2 + 1) or out.numel() != nc * nx * ny * (nz // 2 + 1):
+            raise ValueError("output shape does not match the input grid")
+        nat.ns_fft_r2c_grid(self.ctx, nx, ny, nz, nc, u, out)
+
+    def fft_c2r_grid(self, uh, out) -> None:
+        """c2r of device fields [ncomp][N_x][N_y][N_z/2+1] into [ncomp][N_x][N_y][N_z]."""
+        nx, ny, nz = out.shape[-3:]
+        nc = out.numel() // (nx * ny * nz)
+        if tuple(uh.shape[-3:]) != (nx, ny, nz // 2 + 1) or uh.numel() != nc * nx * ny * (nz // 2 + 1):
+            raise ValueError("input shape does not match the output grid")
+        nat.ns_fft_c2r_grid(self.ctx, nx, ny, nz, nc, uh, out)

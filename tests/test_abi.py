@@ -46,9 +46,17 @@ def test_status_strings_and_bins(lib):
     assert nat.ns_nbins(32) == 29          # ceil(sqrt3 * 16) + 1
     assert nat.ns_nbins(1024) == 888
     assert nat.ns_series_capacity() >= 1000
+    # shells of other grids and boxes agree with the oracle's count
+    import oracle
+    for kw in (dict(n=32), dict(n=32, ny=64, nz=16), dict(n=32, nz=64, lz=2.0),
+               dict(n=24, ny=36, nz=48, lx=1.0, ly=1.5, lz=0.75)):
+        want = oracle.nbins(oracle.Params(**kw))
+        assert nat.ns_run_nbins(dict(dt=1e-3, **kw)) == want, kw
 
 
-@pytest.mark.parametrize("bad", [dict(n=30), dict(n=14), dict(n=7), dict(n=2048), dict(n=1536)])
+@pytest.mark.parametrize("bad", [dict(n=30), dict(n=14), dict(n=7), dict(n=2048), dict(n=1536),
+                                 dict(n=32, ny=30), dict(n=32, nz=2048), dict(n=1024, ny=1024, nz=1536),
+                                 dict(n=1024, ny=1024, nz=1024 * 3 // 2 // 3 * 3)])
 def test_unsupported_sizes_rejected_before_any_device_call(lib, bad):
     from paper_1003_4322_gb300 import _native as nat
     p = dict(dt=1e-3, nu=0.01)
@@ -60,7 +68,10 @@ def test_unsupported_sizes_rejected_before_any_device_call(lib, bad):
 
 @pytest.mark.parametrize("bad", [dict(dt=0.0), dict(nu=-1.0), dict(dealias=3), dict(force_k=-1),
                                  dict(dt=float("nan")), dict(mhd=2), dict(mhd=1, eta=-1.0),
-                                 dict(mhd=1, dealias=2), dict(rot=float("inf"))])
+                                 dict(mhd=1, dealias=2), dict(rot=float("inf")), dict(ny=-8),
+                                 dict(lz=-1.0), dict(lx=float("nan")), dict(ly=1e7),
+                                 dict(lz=0.5, force_k=3, force_amp=0.5),
+                                 dict(ly=1.25, force_k=2, force_amp=0.5)])
 def test_bad_parameters_rejected(lib, bad):
     from paper_1003_4322_gb300 import _native as nat
     p = dict(n=32, dt=1e-3, nu=0.01)

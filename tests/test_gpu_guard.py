@@ -1,7 +1,8 @@
 """Guard bands around every device buffer of the library (NS_GUARD=1): after
 steps of both forms (Navier-Stokes, rotation, MHD, ensembles of uneven
-sizes, a size with no compiled fused MHD kernel) and the standalone
-transforms, no kernel has written outside its buffers.  Runs in a child
+sizes, a size with no compiled fused MHD kernel, grids and boxes other than
+the cube) and the standalone transforms, no kernel has written outside its
+buffers.  Runs in a child
 process, since the guard mode is fixed at the library's first allocation."""
 import os
 import subprocess
@@ -37,6 +38,27 @@ SCRIPT = textwrap.dedent("""
             for r, q in enumerate(runs):
                 s.set_state(inputs.turbulence_state(q["n"], seed=4 + r), run=r)
             s.step(2)
+        for grid in (dict(n=16, ny=24, nz=36, lx=1.0, ly=1.5, lz=3.0, dealias=2),
+                     dict(n=24, ny=16, nz=8, lz=0.5, force_amp=0.5, force_k=2, dealias=1, rot=1.0)):
+            dims = (grid["n"], grid["ny"], grid["nz"])
+            box = tuple(grid.get(k, 1.0) for k in ("lx", "ly", "lz"))
+            with Solver([dict(nu=0.01, dt=1e-3, **grid)], prec=prec) as s:
+                s.set_state(inputs.random_solenoidal_grid(dims, box, 0.5, 3.0, 1.0, 6, grid["dealias"]))
+                s.step(2)
+                s.get_state(); s.energy_spectrum(); s.helicity()
+            with Solver([dict(nu=0.01, eta=0.02, dt=1e-3, mhd=1, n=16, ny=12, nz=24, ly=0.75)],
+                        prec=prec) as s:
+                s.set_field(1, inputs.random_solenoidal_grid((16, 12, 24), (1, 0.75, 1), 0.5, 3.0, 1.0, 7))
+                s.step(2)
+                s.field_spectrum(1)
+            rt = torch.float64 if prec == "fp64" else torch.float32
+            ct = torch.complex128 if prec == "fp64" else torch.complex64
+            for d in (dims, (64, 96, 128)):
+                u = torch.randn((3,) + d, device="cuda", dtype=rt)
+                uh = torch.empty((3, d[0], d[1], d[2] // 2 + 1), device="cuda", dtype=ct)
+                with Solver([dict(n=8, dt=1e-3)], prec=prec) as s:
+                    s.fft_r2c_grid(u, uh)
+                    s.fft_c2r_grid(uh, u)
         for n in (48, 64):
             rt = torch.float64 if prec == "fp64" else torch.float32
             ct = torch.complex128 if prec == "fp64" else torch.complex64
