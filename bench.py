@@ -191,10 +191,12 @@ def kernel_model(name, n, prec):
         return 9 * V * es, 9 * V
     if name == "cross_mhd":     # reads u, w, b, j; writes u x w + j x b and u x b
         return 18 * V * es, 30 * V
-    if name == "update_b":
-        return 7.5 * 3 * M * 2 * es, 3 * M * 20
-    if name == "update":
-        return 7.5 * 3 * M * 2 * es, 3 * M * 20
+    if name in ("update", "update_b"):
+        # writes three components of every mode; reads the transformed product,
+        # the state (and the stage-1 state at stage 2: 7.5 components on
+        # average) of the kept modes only
+        kept = (2 * ((nx - 1) // 3) + 1) * (2 * ((ny - 1) // 3) + 1) * ((nz - 1) // 3 + 1)
+        return (3 * M + 7.5 * kept) * 2 * es, 3 * kept * 20
     # fused form (cubes only; FP32 complex = 8 bytes; only the kept modes move)
     f_line = 5 * n * math.log2(n)
     K = (n - 1) // 3
