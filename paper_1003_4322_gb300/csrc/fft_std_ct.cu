@@ -4,6 +4,9 @@
 // reuse the column machinery of the fused form with every row present (the y
 // pass flattens (x, kz) into columns, so no tile is ragged), and the z pass is
 // a warp-level r2c / c2r with the line in shared memory.
+#include <stdlib.h>
+#include <string.h>
+
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -172,7 +175,15 @@ static cudaError_t launch_col(const FzsKernel &k, const FzPass &ps, int ct, cons
 // and y passes' (E, columns per CTA) and the z pass's (E, warps per CTA).
 struct StdShapes {
     int ex = 0, cx = 0, ey = 0, cy = 0, ez = 0, wz = 0;
+    int zreg = 0;   // z pass: 0 line in shared memory (zstd), 1 register-resident (zreg)
 };
+
+// Register-resident z-pass candidates (fft_std_reg.cu).
+bool zreg_lookup(int N, bool r2c, int E, ZctKernel *o);
+
+static bool z_kernel(const StdShapes &sh, int N, bool r2c, ZctKernel *z) {
+    return sh.zreg ? zreg_lookup(N, r2c, sh.ez, z) : zstd_lookup(N, r2c, sh.ez, sh.wz, z);
+}
 
 static bool std_lookup_col(bool fwd, int N, int E, int CT, FzsKernel *k) {
     return fwd ? fzs_lookup_PF(N, E, CT, k) : fzs_lookup_PI(N, E, CT, k);
@@ -213,12 +224,15 @@ static void std_descs(const float2 *in, float2 *out, const StdGrid &g, int ncomp
 // Choose the shapes on the first call for (grid, direction), timing every
 // compiled candidate on the call's own buffers (the passes run in place on
 // `work`, whose contents the real transform then overwrites); kept for the
-// life of the process.
+// life of the process.  NS_FORCE_STD_Z=smem or =reg restricts the z pass to
+// one kernel family (so that tests can run both).
 static bool std_shapes(const StdGrid &g, bool fwd, const void *zin, void *zout, float2 *work, int ncomp,
                        cudaStream_t s, StdShapes *out) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, bool>, StdShapes> cache;
-    const auto key = std::make_tuple(g.nx, g.ny, g.nz, fwd);
+    static std::map<std::tuple<int, int, int, bool, int>, StdShapes> cache;
+    const char *fz = getenv("NS_FORCE_STD_Z");
+    const bool try_smem = !fz || strcmp(fz, "reg") != 0, try_reg = !fz || strcmp(fz, "smem") != 0;
+    const auto key = std::make_tuple(g.nx, g.ny, g.nz, fwd, (int)try_smem + 2 * (int)try_reg);
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
@@ -248,11 +262,16 @@ static bool std_shapes(const StdGrid &g, bool fwd, const void *zin, void *zout, 
     const int Ezs[] = {16, 12, 8, 6};
     const long nlines = (long)(fwd ? ncomp : 1) * g.nx * g.ny;
     for (int E : Ezs)
-        for (int w = 2; w <= 4; w *= 2) {
+        for (int w = 2; w <= 4 && try_smem; w *= 2) {
             if (!zstd_lookup(g.nz, fwd, E, w, &z)) continue;
             const float t = std_time([&]() { return launch_zstd(z, zin, zout, nlines, g.twz, s); }, s);
-            if (t > 0.f && (bz < 0.f || t < bz)) { bz = t; best.ez = E; best.wz = w; }
+            if (t > 0.f && (bz < 0.f || t < bz)) { bz = t; best.ez = E; best.wz = w; best.zreg = 0; }
         }
+    for (int E : Ezs) {
+        if (!try_reg || !zreg_lookup(g.nz, fwd, E, &z)) continue;
+        const float t = std_time([&]() { return launch_zstd(z, zin, zout, nlines, g.twz, s); }, s);
+        if (t > 0.f && (bz < 0.f || t < bz)) { bz = t; best.ez = E; best.wz = 4; best.zreg = 1; }
+    }
     if (bx < 0.f || by < 0.f || bz < 0.f) return false;
     std::lock_guard<std::mutex> lk(mu);
     cache[key] = best;
@@ -267,7 +286,7 @@ bool std_r2c_fp32_grid(const float *in, float2 *out, const StdGrid &g, int ncomp
     FzsKernel kx, ky;
     ZctKernel kz;
     if (!std_lookup_col(true, g.nx, sh.ex, sh.cx, &kx) || !std_lookup_col(true, g.ny, sh.ey, sh.cy, &ky) ||
-        !zstd_lookup(g.nz, true, sh.ez, sh.wz, &kz))
+        !z_kernel(sh, g.nz, true, &kz))
         return false;
     *err = launch_zstd(kz, in, out, (long)ncomp * g.nx * g.ny, g.twz, s);
     if (*err != cudaSuccess) return true;
@@ -286,7 +305,7 @@ bool std_c2r_fp32_grid(const float2 *in, float2 *tmp, float *out, const StdGrid 
     FzsKernel kx, ky;
     ZctKernel kz;
     if (!std_lookup_col(false, g.nx, sh.ex, sh.cx, &kx) || !std_lookup_col(false, g.ny, sh.ey, sh.cy, &ky) ||
-        !zstd_lookup(g.nz, false, sh.ez, sh.wz, &kz))
+        !z_kernel(sh, g.nz, false, &kz))
         return false;
     FzPass py, px;
     std_descs(in, tmp, g, 1, py, px);

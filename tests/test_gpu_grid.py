@@ -191,3 +191,31 @@ def test_shape_checks_refuse_wrong_buffers(ns):
         with pytest.raises(TypeError):
             s.get_state(out=np.zeros((3, 16, 24, 5), dtype=np.complex64))
         assert s.get_state().shape == (3, 16, 24, 5)
+
+
+@pytest.mark.parametrize("family", ["smem", "reg"])
+@pytest.mark.parametrize("dims", [(64, 64, 512), (64, 96, 384), (32, 64, 1024), (64, 32, 768),
+                                  (96, 64, 256)])
+def test_std_z_kernel_families_against_oracle(ns, dims, family, monkeypatch):
+    """The compile-time FP32 transforms with the z pass restricted to one
+    kernel family (shared-memory lines, or register-resident lines with the
+    even/odd packing through warp shuffles), NS_FORCE_STD_Z, against the
+    oracle on grids whose z lengths have register candidates."""
+    import torch
+    from paper_1003_4322_gb300.solver import Solver
+    monkeypatch.setenv("NS_FORCE_STD_Z", family)
+    nx, ny, nz = dims
+    u = inputs.random_real_grid(dims, 2, seed=nz)
+    ref = oracle.fft3_r2c(u)
+    a = inputs.random_hermitian_half_grid(dims, 2, seed=nz + 1)
+    a[:, :, :, -1] += 0.5   # a real Nyquist plane of its own
+    back = oracle.fft3_c2r(a)
+    with Solver([dict(n=8, dt=1e-3)], prec="fp32") as s:
+        out = torch.empty((2, nx, ny, nz // 2 + 1), dtype=torch.complex64, device="cuda")
+        s.fft_r2c_grid(torch.from_numpy(u).to("cuda", torch.float32), out)
+        phys = torch.empty((2, nx, ny, nz), dtype=torch.float32, device="cuda")
+        s.fft_c2r_grid(torch.from_numpy(a).to("cuda", torch.complex64), phys)
+        s.sync()
+        got, gotp = out.cpu().numpy(), phys.cpu().numpy()
+    assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
+    assert np.abs(gotp - back).max() < 1e-5 * np.abs(back).max()
