@@ -367,10 +367,12 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
     return roof, total
 
 
-def fft_stage(n, prec, reps=5):
-    """Standalone ns_fft_r2c + ns_fft_c2r of 3 components (ns_fft_*_grid on a
-    grid (N_x, N_y, N_z) that is not a cube): HBM GB/s by the algorithmic
-    model (each of the 3 passes reads and writes the array)."""
+def fft_stage(n, prec, reps=5, ncomp=3, window=False):
+    """Standalone ns_fft_r2c + ns_fft_c2r of ncomp components (ns_fft_*_grid
+    on a grid (N_x, N_y, N_z) that is not a cube): HBM GB/s by the
+    algorithmic model (each of the 3 passes reads and writes the array).
+    window: bracket one more r2c and c2r with cudaProfilerStart/Stop, for a
+    profiler started with its capture off (ncu --profile-from-start off)."""
     import torch
 
     from paper_1003_4322_gb300 import _native as nat
@@ -379,8 +381,8 @@ def fft_stage(n, prec, reps=5):
     rt = torch.float32 if prec == "fp32" else torch.float64
     ct = torch.complex64 if prec == "fp32" else torch.complex128
     g = torch.Generator(device="cuda").manual_seed(1)
-    u = torch.randn((3, nx, ny, nz), device="cuda", dtype=rt, generator=g)
-    uh = torch.empty((3, nx, ny, nz // 2 + 1), device="cuda", dtype=ct)
+    u = torch.randn((ncomp, nx, ny, nz), device="cuda", dtype=rt, generator=g)
+    uh = torch.empty((ncomp, nx, ny, nz // 2 + 1), device="cuda", dtype=ct)
     back = torch.empty_like(u)
     stream = torch.cuda.current_stream()
     ctx = nat.ns_init([dict(n=8, dt=1e-3)], nat.NS_FP32 if prec == "fp32" else nat.NS_FP64,
@@ -388,15 +390,15 @@ def fft_stage(n, prec, reps=5):
 
     def fwd():
         if cube:
-            nat.ns_fft_r2c(ctx, nx, 3, u, uh)
+            nat.ns_fft_r2c(ctx, nx, ncomp, u, uh)
         else:
-            nat.ns_fft_r2c_grid(ctx, nx, ny, nz, 3, u, uh)
+            nat.ns_fft_r2c_grid(ctx, nx, ny, nz, ncomp, u, uh)
 
     def inv():
         if cube:
-            nat.ns_fft_c2r(ctx, nx, 3, uh, back)
+            nat.ns_fft_c2r(ctx, nx, ncomp, uh, back)
         else:
-            nat.ns_fft_c2r_grid(ctx, nx, ny, nz, 3, uh, back)
+            nat.ns_fft_c2r_grid(ctx, nx, ny, nz, ncomp, uh, back)
     try:
         for _ in range(2):
             fwd()
@@ -413,13 +415,19 @@ def fft_stage(n, prec, reps=5):
         torch.cuda.synchronize()
         r2c_ms = evs[0].elapsed_time(evs[1]) / reps
         c2r_ms = evs[1].elapsed_time(evs[2]) / reps
+        if window:
+            torch.cuda.profiler.start()
+            fwd()
+            inv()
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
     finally:
         nat.ns_destroy(ctx)
     es = 4 if prec == "fp32" else 8
     half = nx * ny * (nz // 2 + 1) * 2 * es
     real = nx * ny * nz * es
-    model = 3 * ((real + half) + 2 * half + 2 * half)   # z, y, x passes (read + write)
-    out = {"n": nx if cube else [nx, ny, nz], "ncomp": 3, "prec": prec, "r2c_ms": r2c_ms,
+    model = ncomp * ((real + half) + 2 * half + 2 * half)   # z, y, x passes (read + write)
+    out = {"n": nx if cube else [nx, ny, nz], "ncomp": ncomp, "prec": prec, "r2c_ms": r2c_ms,
            "c2r_ms": c2r_ms,
            "r2c_gbs": model / (r2c_ms * 1e-3) / 1e9, "c2r_gbs": model / (c2r_ms * 1e-3) / 1e9,
            "bytes_model": model}
@@ -673,6 +681,11 @@ def main():
                     help="fft: only the standalone 3-component r2c/c2r stage")
     ap.add_argument("--fft-n", type=int, default=256)
     ap.add_argument("--fft-prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fft-dims", default=None,
+                    help="NX,NY,NZ: the stage on that grid instead of --fft-n cubed")
+    ap.add_argument("--fft-ncomp", type=int, default=3)
+    ap.add_argument("--fft-window", action="store_true",
+                    help="bracket one more r2c + c2r with cudaProfilerStart/Stop")
     ap.add_argument("--prec", default=None, choices=["fp32", "fp64"],
                     help="override the workload's headline form")
     ap.add_argument("--dealias", type=int, default=None, choices=[0, 1, 2],
@@ -693,7 +706,8 @@ def main():
         from paper_1003_4322_gb300 import _native as nat
         nat.load()
         peaks = load_peaks()
-        r = fft_stage(args.fft_n, args.fft_prec)
+        size = tuple(int(x) for x in args.fft_dims.split(",")) if args.fft_dims else args.fft_n
+        r = fft_stage(size, args.fft_prec, ncomp=args.fft_ncomp, window=args.fft_window)
         r["r2c_frac"] = r["r2c_gbs"] / peaks["hbm_gbs"]
         r["c2r_frac"] = r["c2r_gbs"] / peaks["hbm_gbs"]
         print(json.dumps(r), flush=True)
