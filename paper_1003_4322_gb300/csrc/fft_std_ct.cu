@@ -224,15 +224,16 @@ static void std_descs(const float2 *in, float2 *out, const StdGrid &g, int ncomp
 // Choose the shapes on the first call for (grid, direction), timing every
 // compiled candidate on the call's own buffers (the passes run in place on
 // `work`, whose contents the real transform then overwrites); kept for the
-// life of the process.  NS_FORCE_STD_Z=smem or =reg restricts the z pass to
-// one kernel family (so that tests can run both).
+// life of the process.  NS_FORCE_STD_Z=smem, =reg or =pf restricts the z pass
+// to one kernel family (so that tests can run each).
 static bool std_shapes(const StdGrid &g, bool fwd, const void *zin, void *zout, float2 *work, int ncomp,
                        cudaStream_t s, StdShapes *out) {
     static std::mutex mu;
     static std::map<std::tuple<int, int, int, bool, int>, StdShapes> cache;
     const char *fz = getenv("NS_FORCE_STD_Z");
-    const bool try_smem = !fz || strcmp(fz, "reg") != 0, try_reg = !fz || strcmp(fz, "smem") != 0;
-    const auto key = std::make_tuple(g.nx, g.ny, g.nz, fwd, (int)try_smem + 2 * (int)try_reg);
+    const bool try_smem = !fz || strcmp(fz, "smem") == 0, try_reg = !fz || strcmp(fz, "reg") == 0,
+               try_pf = !fz || strcmp(fz, "pf") == 0;
+    const auto key = std::make_tuple(g.nx, g.ny, g.nz, fwd, (int)try_smem + 2 * (int)try_reg + 4 * (int)try_pf);
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
@@ -267,8 +268,9 @@ static bool std_shapes(const StdGrid &g, bool fwd, const void *zin, void *zout, 
             const float t = std_time([&]() { return launch_zstd(z, zin, zout, nlines, g.twz, s); }, s);
             if (t > 0.f && (bz < 0.f || t < bz)) { bz = t; best.ez = E; best.wz = w; best.zreg = 0; }
         }
-    for (int E : Ezs) {
-        if (!try_reg || !zreg_lookup(g.nz, fwd, E, &z)) continue;
+    const int Eregs[] = {16, 12, 8, 6, 116, 112, 108, 106};   // E + 100: prefetching form
+    for (int E : Eregs) {
+        if (!(E < 100 ? try_reg : try_pf) || !zreg_lookup(g.nz, fwd, E, &z)) continue;
         const float t = std_time([&]() { return launch_zstd(z, zin, zout, nlines, g.twz, s); }, s);
         if (t > 0.f && (bz < 0.f || t < bz)) { bz = t; best.ez = E; best.wz = 4; best.zreg = 1; }
     }

@@ -117,6 +117,133 @@ k_z_c2r_reg(const float2 *__restrict__ in, float *__restrict__ out, long nlines,
     for (int j = 0; j < E; j++) dst[slot + j * T] = v[j];
 }
 
+// The same two transforms with IT consecutive line groups per warp: the
+// input of group i + 1 is loaded into registers while group i is
+// transformed, so a warp keeps a line's loads in flight through its FFT, and
+// the stage twiddles are loaded once per IT groups.
+template <int N, int E, int WPB, int IT>
+__global__ void __launch_bounds__(32 * WPB)
+k_z_r2c_pf(const float *__restrict__ in, float2 *__restrict__ out, long nlines,
+           const float2 *__restrict__ tw) {
+    typedef ZRegShape<N, E> Z;
+    constexpr int n = Z::n, T = Z::T, LPW = Z::LPW, LS = Z::LS;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ll = lane / T, slot = lane % T;
+    const int partner = ll * T + (T - slot) % T;
+    const long g0 = ((long)blockIdx.x * WPB + warp) * IT;   // first line group of the warp
+    float2 *L = sm + (long)(warp * LPW + ll) * LS;
+    auto sl = [&](int e) -> float2 { return L[ct_skew(e)]; };
+    auto ss = [&](int e, float2 v) { L[ct_skew(e)] = v; };
+    CtTwiddles<n, E, N> twr;
+    twr.load(slot, tw);
+    float2 nx[E];
+    auto fetch = [&](long grp) {
+        const long line = grp * LPW + ll;
+        const bool ok = line < nlines;
+        const float2 *src = reinterpret_cast<const float2 *>(in + (ok ? line : 0) * N);
+#pragma unroll
+        for (int j = 0; j < E; j++) nx[j] = ok ? src[slot + j * T] : make_float2(0.f, 0.f);
+    };
+    fetch(g0);
+#pragma unroll 1
+    for (int it = 0; it < IT; it++) {
+        const long line = (g0 + it) * LPW + ll;
+        const bool valid = line < nlines;
+        float2 v[E];
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = nx[j];
+        if (it + 1 < IT) fetch(g0 + it + 1);
+        ct_fft_reg<n, E, -1, N>(v, slot, twr, sl, ss);
+        float2 *dst = out + (valid ? line : 0) * (n + 1);
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            float2 zm = zreg_shfl(v[E - 1 - j], partner);
+            if (slot == 0) zm = v[(E - j) % E];
+            const float2 zk = v[j], zc = cconj(zm);
+            const float2 ev = cscale(cadd(zk, zc), 0.5f);
+            const float2 od = cmul_i<-1>(cscale(csub(zk, zc), 0.5f));
+            if (valid) dst[k] = cadd(ev, cmul(od, __ldg(tw + k)));
+        }
+        if (valid && slot == 0) dst[n] = make_float2(v[0].x - v[0].y, 0.f);
+    }
+}
+
+template <int N, int E, int WPB, int IT>
+__global__ void __launch_bounds__(32 * WPB)
+k_z_c2r_pf(const float2 *__restrict__ in, float *__restrict__ out, long nlines,
+           const float2 *__restrict__ tw) {
+    typedef ZRegShape<N, E> Z;
+    constexpr int n = Z::n, T = Z::T, LPW = Z::LPW, LS = Z::LS;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ll = lane / T, slot = lane % T;
+    const int partner = ll * T + (T - slot) % T;
+    const long g0 = ((long)blockIdx.x * WPB + warp) * IT;
+    float2 *L = sm + (long)(warp * LPW + ll) * LS;
+    auto sl = [&](int e) -> float2 { return L[ct_skew(e)]; };
+    auto ss = [&](int e, float2 v) { L[ct_skew(e)] = v; };
+    CtTwiddles<n, E, N> twr;
+    twr.load(slot, tw);
+    float2 nx[E], nn;
+    auto fetch = [&](long grp) {
+        const long line = grp * LPW + ll;
+        const bool ok = line < nlines;
+        const float2 *src = in + (ok ? line : 0) * (n + 1);
+#pragma unroll
+        for (int j = 0; j < E; j++) nx[j] = ok ? src[slot + j * T] : make_float2(0.f, 0.f);
+        nn = ok && slot == 0 ? src[n] : make_float2(0.f, 0.f);
+    };
+    fetch(g0);
+#pragma unroll 1
+    for (int it = 0; it < IT; it++) {
+        const long line = (g0 + it) * LPW + ll;
+        const bool valid = line < nlines;
+        float2 x[E];
+#pragma unroll
+        for (int j = 0; j < E; j++) x[j] = nx[j];
+        const float2 xn = nn;
+        if (it + 1 < IT) fetch(g0 + it + 1);
+        float2 v[E];
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            float2 a0 = x[j];
+            float2 am = zreg_shfl(x[E - 1 - j], partner);
+            if (slot == 0) am = j > 0 ? x[(E - j) % E] : xn;
+            if (k == 0) {
+                a0.y = 0.f;
+                am.y = 0.f;
+            }
+            const float2 xc = cconj(am);
+            const float2 wb = cmulc(csub(a0, xc), __ldg(tw + k));
+            v[j] = cadd(cadd(a0, xc), cmul_i<1>(wb));
+        }
+        ct_fft_reg<n, E, +1, N>(v, slot, twr, sl, ss);
+        if (valid) {
+            float2 *dst = reinterpret_cast<float2 *>(out + line * N);
+#pragma unroll
+            for (int j = 0; j < E; j++) dst[slot + j * T] = v[j];
+        }
+    }
+}
+
+template <int N, int E, int WPB, int IT> bool zpf_entry(bool r2c, ZctKernel *o) {
+    typedef ZRegShape<N, E> Z;
+    if constexpr (!Z::ok) {
+        return false;
+    } else {
+        o->k = r2c ? (const void *)k_z_r2c_pf<N, E, WPB, IT> : (const void *)k_z_c2r_pf<N, E, WPB, IT>;
+        o->smem = (size_t)WPB * Z::LPW * (Z::LS > 0 ? Z::LS : 1) * sizeof(float2);
+        o->lines_per_block = WPB * Z::LPW * IT;
+        o->threads = 32 * WPB;
+        return true;
+    }
+}
+
 template <int N, int E, int WPB> bool zreg_entry(bool r2c, ZctKernel *o) {
     typedef ZRegShape<N, E> Z;
     if constexpr (!Z::ok) {

@@ -193,14 +193,16 @@ def test_shape_checks_refuse_wrong_buffers(ns):
         assert s.get_state().shape == (3, 16, 24, 5)
 
 
-@pytest.mark.parametrize("family", ["smem", "reg"])
+@pytest.mark.parametrize("family", ["smem", "reg", "pf"])
 @pytest.mark.parametrize("dims", [(64, 64, 512), (64, 96, 384), (32, 64, 1024), (64, 32, 768),
                                   (96, 64, 256)])
 def test_std_z_kernel_families_against_oracle(ns, dims, family, monkeypatch):
     """The compile-time FP32 transforms with the z pass restricted to one
-    kernel family (shared-memory lines, or register-resident lines with the
-    even/odd packing through warp shuffles), NS_FORCE_STD_Z, against the
-    oracle on grids whose z lengths have register candidates."""
+    kernel family (shared-memory lines; register-resident lines with the
+    even/odd packing through warp shuffles; the same with four line groups
+    per warp and the next group's input prefetched), NS_FORCE_STD_Z, against
+    the oracle on grids whose z lengths have register candidates (the line
+    counts leave the last warp's groups partly empty)."""
     import torch
     from paper_1003_4322_gb300.solver import Solver
     monkeypatch.setenv("NS_FORCE_STD_Z", family)
