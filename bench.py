@@ -185,6 +185,9 @@ def kernel_model(name, n, prec):
         return 2 * 3 * M * 2 * es, 3 * nx * nh * 5 * ny * math.log2(ny)
     if name in ("fft_z_c2r", "fft_z_r2c"):
         return 3 * (M * 2 * es + V * es), 3 * nx * ny * f_zline
+    if name in ("fft_c2r_std", "fft_r2c_std"):   # all three passes of three components
+        flops = 3 * (ny * nh * 5 * nx * math.log2(nx) + nx * nh * 5 * ny * math.log2(ny) + nx * ny * f_zline)
+        return 3 * (M * 2 * es + V * es) + 2 * (2 * 3 * M * 2 * es), flops
     if name == "curl":
         return 2 * 3 * M * 2 * es, 3 * M * 6
     if name == "cross":

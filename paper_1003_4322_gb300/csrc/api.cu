@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <map>
 #include <mutex>
 #include <memory>
@@ -51,6 +52,7 @@ struct Run {
     // plain form (full half layout)
     void *un = nullptr, *u1 = nullptr, *wn = nullptr, *work = nullptr, *phys = nullptr;
     void *sh = nullptr, *sh2 = nullptr;   // phase-shift dealiasing: shifted state, its product
+    void *phtab = nullptr;                // per-axis shift factors exp(i pi m / N_i)
     void *etab = nullptr;   // exp(-nu k^2 dt) by integer k^2 (unit boxes)
     void *etab_b = nullptr; // MHD: exp(-eta k^2 dt); un, u1, wn then hold [u; b] (6 components)
     // fused form: the run is member gidx of group `group` of the context
@@ -174,12 +176,31 @@ struct Fft3 {
     const FftRes *x, *y, *z;
 };
 
+// FP32 transforms of a grid whose axis lengths have compile-time kernels go
+// through the tuned standalone path (fft_std_ct.cu); its shapes are chosen on
+// the first call, which the plain form makes before any graph capture.
+inline StdGrid std_grid(const Grid &g, const Fft3 &f) {
+    return StdGrid{g.nx, g.ny, g.nz, (const float2 *)f.x->tw, (const float2 *)f.y->tw,
+                   (const float2 *)f.z->tw};
+}
+
 // c2r of ncomp half fields [ncomp][N_x][N_y][N_z/2+1]: x pass (in -> tmp), y
-// pass (tmp in place), z pass (tmp -> out [ncomp][N_x][N_y][N_z]).
+// pass (tmp in place), z pass (tmp -> out [ncomp][N_x][N_y][N_z]).  FP32 on
+// compiled lengths: the standalone kernels, one field at a time through tmp.
 template <typename T>
 cudaError_t c2r_batch(const typename Cx<T>::type *in, typename Cx<T>::type *tmp, T *out, const Grid &g,
                       int ncomp, const Fft3 &f, cudaStream_t s, Tracer *tr = nullptr) {
     typedef typename Cx<T>::type C;
+    if constexpr (std::is_same<T, float>::value) {
+        const StdGrid sg = std_grid(g, f);
+        cudaError_t e = cudaSuccess;
+        bool done = true;
+        if (tr) tr->begin("fft_c2r_std");
+        for (int k = 0; k < ncomp && done && e == cudaSuccess; k++)
+            done = std_c2r_fp32_grid(in + k * g.M(), tmp, out + k * g.V(), sg, s, &e);
+        if (tr) tr->end();
+        if (done) return e;
+    }
     const long nh = g.nzh(), plane = (long)g.ny * nh, M = (long)g.nx * plane;
     const PlainPlans &qx = f.x->pp, &qy = f.y->pp, &qz = f.z->pp;
     cudaError_t e = NSK_TIMED(tr, "fft_x_inverse",
@@ -199,6 +220,13 @@ template <typename T>
 cudaError_t r2c_batch(const T *in, typename Cx<T>::type *out, const Grid &g, int ncomp, const Fft3 &f,
                       cudaStream_t s, Tracer *tr = nullptr) {
     typedef typename Cx<T>::type C;
+    if constexpr (std::is_same<T, float>::value) {
+        cudaError_t e = cudaSuccess;
+        if (tr) tr->begin("fft_r2c_std");
+        const bool done = std_r2c_fp32_grid(in, out, std_grid(g, f), ncomp, s, &e);
+        if (tr) tr->end();
+        if (done) return e;
+    }
     const long nh = g.nzh(), plane = (long)g.ny * nh, M = (long)g.nx * plane;
     const PlainPlans &qx = f.x->pp, &qy = f.y->pp, &qz = f.z->pp;
     cudaError_t e = NSK_TIMED(tr, "fft_z_r2c",
@@ -464,22 +492,65 @@ template <typename T> ns_status plain_alloc(ns_ctx *c, Run &r) {
     }
     NS_CK(cudaMemsetAsync(r.un, 0, nc * half, c->stream));
     NS_CK(cudaMemsetAsync(r.u1, 0, nc * half, c->stream));
-    if (r.g.unit) {   // factor tables by integer |k|^2 (other boxes form the factor per mode)
-        const long nk2 = grid_max_k2(r.g) + 1;
-        std::vector<T> h(nk2);
-        for (long k2 = 0; k2 < nk2; k2++) h[k2] = (T)exp(-r.p.nu * (double)k2 * r.p.dt);
-        NS_CK(dalloc(&r.etab, nk2 * sizeof(T)));
-        NS_CK(cudaMemcpy(r.etab, h.data(), nk2 * sizeof(T), cudaMemcpyHostToDevice));
-        if (r.p.mhd) {
-            for (long k2 = 0; k2 < nk2; k2++) h[k2] = (T)exp(-r.p.eta * (double)k2 * r.p.dt);
-            NS_CK(dalloc(&r.etab_b, nk2 * sizeof(T)));
-            NS_CK(cudaMemcpy(r.etab_b, h.data(), nk2 * sizeof(T), cudaMemcpyHostToDevice));
+    // factor tables, computed in FP64 and rounded once: by integer |k|^2 on a
+    // unit box; elsewhere per axis by array position [N_x | N_y | N_z/2+1]
+    auto factors = [&](double c, std::vector<T> &h) {
+        if (r.g.unit) {
+            h.resize(grid_max_k2(r.g) + 1);
+            for (size_t k2 = 0; k2 < h.size(); k2++) h[k2] = (T)exp(-c * (double)k2 * r.p.dt);
+            return;
         }
+        const int n[3] = {r.g.nx, r.g.ny, r.g.nz};
+        const double l[3] = {r.g.lx, r.g.ly, r.g.lz};
+        h.clear();
+        for (int a = 0; a < 3; a++) {
+            const int cnt = a < 2 ? n[a] : n[a] / 2 + 1;
+            for (int i = 0; i < cnt; i++) {
+                const int m = a < 2 && 2 * i >= n[a] ? i - n[a] : i;
+                const double k = (double)m / l[a];
+                h.push_back((T)exp(-c * k * k * r.p.dt));
+            }
+        }
+    };
+    std::vector<T> h;
+    factors(r.p.nu, h);
+    NS_CK(dalloc(&r.etab, h.size() * sizeof(T)));
+    NS_CK(cudaMemcpy(r.etab, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (r.p.mhd) {
+        factors(r.p.eta, h);
+        NS_CK(dalloc(&r.etab_b, h.size() * sizeof(T)));
+        NS_CK(cudaMemcpy(r.etab_b, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    if (r.p.dealias == 2) {   // per-axis shift factors exp(i pi m / N_i), FP64 rounded once
+        const int n[3] = {r.g.nx, r.g.ny, r.g.nz};
+        std::vector<C> ph;
+        for (int a = 0; a < 3; a++) {
+            const int cnt = a < 2 ? n[a] : n[a] / 2 + 1;
+            for (int i = 0; i < cnt; i++) {
+                const int m = a < 2 && 2 * i >= n[a] ? i - n[a] : i;
+                const double t = M_PI * (double)m / (double)n[a];
+                C v;
+                v.x = (T)cos(t);
+                v.y = (T)sin(t);
+                ph.push_back(v);
+            }
+        }
+        NS_CK(dalloc(&r.phtab, ph.size() * sizeof(C)));
+        NS_CK(cudaMemcpy(r.phtab, ph.data(), ph.size() * sizeof(C), cudaMemcpyHostToDevice));
     }
     FftRes *f[3];
     ns_status st = get_fft3(c, r.g, f);
     if (st != NS_OK) return st;
-    return tune_plain<T>(c, r, f[0]);
+    if ((st = tune_plain<T>(c, r, f[0])) != NS_OK) return st;
+    if constexpr (std::is_same<T, float>::value) {
+        // choose the standalone kernels' shapes now, outside any graph capture
+        // (on the run's own buffers, whose contents the first step overwrites)
+        const Fft3 f3{f[0], f[1], f[2]};
+        NS_CK(r2c_batch<T>((const T *)r.phys, (C *)r.wn, r.g, 3, f3, c->stream));
+        NS_CK(c2r_batch<T>((const C *)r.wn, (C *)r.work, (T *)r.phys, r.g, 3, f3, c->stream));
+        NS_CK(cudaStreamSynchronize(c->stream));
+    }
+    return NS_OK;
 }
 
 // Update arguments of a stage: forcing index kf l_i along every axis.
@@ -494,7 +565,6 @@ UpdateArgs update_args(const Run &r, int stage) {
     ua.mfz = (int)lround(r.p.force_k * r.g.lz);
     ua.dealias = r.p.dealias;
     ua.rot = r.p.rot;
-    ua.nu_dt = r.p.nu * r.p.dt;
     return ua;
 }
 
@@ -526,7 +596,7 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
         NS_CK(NSK_TIMED(tr, "update_b",
                         plain_update_b<T>((C *)r.un + M3, (C *)r.u1 + M3, (const C *)wj + M3,
                                           (const T *)r.etab_b, g, stage, r.p.dt,
-                                          r.p.eta * r.p.dt, r.p.dealias, s)));
+                                          r.p.dealias, s)));
     }
     for (int stage = 1; stage <= 2 && !r.p.mhd; stage++) {
         C *src = (C *)(stage == 1 ? r.un : r.u1);
@@ -537,13 +607,13 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
         NS_CK(r2c_batch<T>(phys, (C *)r.wn, g, 3, f, s, tr));
         if (r.p.dealias == 2) {   // the same on the grid shifted by half a spacing, averaged
             C *sh = (C *)r.sh, *sh2 = (C *)r.sh2;
-            NS_CK(NSK_TIMED(tr, "phase", plain_phase<T>(src, sh, g, s)));
+            NS_CK(NSK_TIMED(tr, "phase", plain_phase<T>(src, sh, (const C *)r.phtab, g, s)));
             NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(sh, sh2, g, s)));
             NS_CK(c2r_batch<T>(sh, (C *)r.work, phys, g, 3, f, s, tr));
             NS_CK(c2r_batch<T>(sh2, (C *)r.work, phys + 3 * r.V, g, 3, f, s, tr));
             NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, g, s)));
             NS_CK(r2c_batch<T>(phys, sh2, g, 3, f, s, tr));
-            NS_CK(NSK_TIMED(tr, "phase", plain_phase_avg<T>((C *)r.wn, sh2, g, s)));
+            NS_CK(NSK_TIMED(tr, "phase", plain_phase_avg<T>((C *)r.wn, sh2, (const C *)r.phtab, g, s)));
         }
         const UpdateArgs ua = update_args(r, stage);
         NS_CK(NSK_TIMED(tr, "update",
@@ -627,7 +697,7 @@ ns_status build_graph(ns_ctx *c) {
 }
 
 void free_run(Run &r) {
-    void *ps[] = {r.un, r.u1, r.wn, r.work, r.phys, r.etab, r.etab_b, r.sh, r.sh2};
+    void *ps[] = {r.un, r.u1, r.wn, r.work, r.phys, r.etab, r.etab_b, r.sh, r.sh2, r.phtab};
     for (void *p : ps)
         if (p) dev_free(p);
     if (r.owns_diag) {

@@ -175,7 +175,8 @@ static cudaError_t launch_col(const FzsKernel &k, const FzPass &ps, int ct, cons
 // and y passes' (E, columns per CTA) and the z pass's (E, warps per CTA).
 struct StdShapes {
     int ex = 0, cx = 0, ey = 0, cy = 0, ez = 0, wz = 0;
-    int zreg = 0;   // z pass: 0 line in shared memory (zstd), 1 register-resident (zreg)
+    int zreg = 0;      // z pass: 0 line in shared memory (zstd), 1 register-resident (zreg)
+    bool ok = false;   // false: no compiled kernel for some axis (the caller falls back)
 };
 
 // Register-resident z-pass candidates (fft_std_reg.cu).
@@ -239,11 +240,30 @@ static bool std_shapes(const StdGrid &g, bool fwd, const void *zin, void *zout, 
         auto it = cache.find(key);
         if (it != cache.end()) {
             *out = it->second;
-            return true;
+            return out->ok;
         }
     }
     FzsKernel k;
     ZctKernel z;
+    // every axis needs a compiled kernel before anything is launched (a miss is
+    // remembered, so later calls, possibly inside a graph capture, launch nothing)
+    {
+        bool hx = false, hy = false, hz = false;
+        const int Ec[] = {6, 8, 12, 16, 32, 106, 108, 112, 116};
+        for (int E : Ec)
+            for (int ct = 8; ct <= 16; ct *= 2) {
+                hx = hx || std_lookup_col(fwd, g.nx, E, ct, &k);
+                hy = hy || std_lookup_col(fwd, g.ny, E, ct, &k);
+            }
+        for (int E : Ec)
+            for (int w = 2; w <= 4; w *= 2) hz = hz || zstd_lookup(g.nz, fwd, E, w, &z);
+        for (int E : Ec) hz = hz || zreg_lookup(g.nz, fwd, E, &z);
+        if (!hx || !hy || !hz) {
+            std::lock_guard<std::mutex> lk(mu);
+            cache[key] = StdShapes{};
+            return false;
+        }
+    }
     const int Es[] = {8, 12, 16, 32};
     StdShapes best;
     float bx = -1.f, by = -1.f, bz = -1.f;
@@ -274,11 +294,11 @@ static bool std_shapes(const StdGrid &g, bool fwd, const void *zin, void *zout, 
         const float t = std_time([&]() { return launch_zstd(z, zin, zout, nlines, g.twz, s); }, s);
         if (t > 0.f && (bz < 0.f || t < bz)) { bz = t; best.ez = E; best.wz = 4; best.zreg = 1; }
     }
-    if (bx < 0.f || by < 0.f || bz < 0.f) return false;
+    best.ok = bx >= 0.f && by >= 0.f && bz >= 0.f;
     std::lock_guard<std::mutex> lk(mu);
     cache[key] = best;
     *out = best;
-    return true;
+    return best.ok;
 }
 
 bool std_r2c_fp32_grid(const float *in, float2 *out, const StdGrid &g, int ncomp, cudaStream_t s,

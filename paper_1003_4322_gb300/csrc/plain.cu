@@ -56,12 +56,16 @@ long grid_max_k2(const Grid &g) {
 
 // Wavevector of a mode in precision T and |k|^2.  On the unit box (UNIT) the
 // wavenumbers are the integer indices and |k|^2 an integer (the index of the
-// factor tables); elsewhere k = m / l is formed from the reciprocals in FP64.
+// factor table); elsewhere k = m / l is formed from the reciprocals in FP64.
 template <typename T, bool UNIT> struct Wave {
     T kx, ky, kz;
     double k2;     // |k|^2
     long i2;       // |k|^2 as an integer (UNIT only)
+    int px, py, pz;   // array positions of the mode along x, y, z
     __device__ __forceinline__ Wave(const Idx &q, const Grid &g) {
+        px = q.x < 0 ? q.x + g.nx : q.x;
+        py = q.y < 0 ? q.y + g.ny : q.y;
+        pz = q.z;
         if constexpr (UNIT) {
             i2 = (long)q.x * q.x + (long)q.y * q.y + (long)q.z * q.z;
             kx = (T)q.x;
@@ -77,10 +81,12 @@ template <typename T, bool UNIT> struct Wave {
             k2 = dx * dx + dy * dy + dz * dz;
         }
     }
-    // exp(-c |k|^2): the table entry by integer |k|^2 on the unit box, else in FP64
-    __device__ __forceinline__ T factor(const T *etab, double c) const {
+    // exp(-c |k|^2) from the run's table: by integer |k|^2 on the unit box;
+    // elsewhere the product of the per-axis factors exp(-c k_x^2) exp(-c k_y^2)
+    // exp(-c k_z^2), tabulated by array position ([N_x | N_y | N_z/2+1]).
+    __device__ __forceinline__ T factor(const T *etab, const Grid &g) const {
         if constexpr (UNIT) return etab[i2];
-        else return (T)exp(-c * k2);
+        else return etab[px] * etab[g.nx + py] * etab[g.nx + g.ny + pz];
     }
 };
 
@@ -184,7 +190,7 @@ __global__ void k_update(typename Cx<T>::type *__restrict__ a, typename Cx<T>::t
             vy = csub(vy, cscale(kv, fky * ik2));
             vz = csub(vz, cscale(kv, fkz * ik2));
             abc_forcing(q, ua, F, vx, vy, vz);
-            const T e = k.factor(etab, ua.nu_dt);
+            const T e = k.factor(etab, g);
             if (ua.stage == 1) {
                 o0 = cscale(cadd(a[m], cscale(vx, dt)), e);
                 o1 = cscale(cadd(a[M + m], cscale(vy, dt)), e);
@@ -209,7 +215,7 @@ __global__ void k_update(typename Cx<T>::type *__restrict__ a, typename Cx<T>::t
 template <typename T, bool UNIT>
 __global__ void k_update_b(typename Cx<T>::type *__restrict__ b, typename Cx<T>::type *__restrict__ b1,
                            const typename Cx<T>::type *__restrict__ nb, const T *__restrict__ etab,
-                           Grid g, long M, int stage, double dt_, double eta_dt, int dealias) {
+                           Grid g, long M, int stage, double dt_, int dealias) {
     typedef typename Cx<T>::type C;
     const T inv = (T)(1.0 / ((double)g.nx * g.ny * g.nz));
     const T dt = (T)dt_;
@@ -224,7 +230,7 @@ __global__ void k_update_b(typename Cx<T>::type *__restrict__ b, typename Cx<T>:
             const C nx = cmul_i<1>(csub(cscale(vz, fky), cscale(vy, fkz)));
             const C ny = cmul_i<1>(csub(cscale(vx, fkz), cscale(vz, fkx)));
             const C nz = cmul_i<1>(csub(cscale(vy, fkx), cscale(vx, fky)));
-            const T e = k.factor(etab, eta_dt);
+            const T e = k.factor(etab, g);
             if (stage == 1) {
                 o0 = cscale(cadd(b[m], cscale(nx, dt)), e);
                 o1 = cscale(cadd(b[M + m], cscale(ny, dt)), e);
@@ -243,25 +249,27 @@ __global__ void k_update_b(typename Cx<T>::type *__restrict__ b, typename Cx<T>:
     }
 }
 
-// k.D / pi for the shift by half a grid spacing along every axis:
-// sum_i m_i / N_i = (sum_i m_i q_i) / D, (m_x + m_y + m_z) / N on the cube.
-__device__ __forceinline__ double shift_phase(const Idx &q, const Grid &g) {
-    return (double)(q.x * g.qx + q.y * g.qy + q.z * g.qz) / (double)g.D;
+// Phase-shift dealiasing: dst = src exp(i k.D), D half a grid spacing along
+// every axis (k.D = pi sum_i m_i / N_i), the coefficients of the field on the
+// shifted grid (three components).  The factor is the product of the per-axis
+// factors exp(i pi m_i / N_i), tabulated in FP64 by array position
+// ([N_x | N_y | N_z/2+1], rounded once to T).
+template <typename T>
+__device__ __forceinline__ typename Cx<T>::type shift_factor(long m, const Grid &g,
+                                                             const typename Cx<T>::type *__restrict__ ph) {
+    const long nh = g.nzh();
+    const int pz = (int)(m % nh), py = (int)((m / nh) % g.ny), px = (int)(m / (nh * g.ny));
+    return cmul(cmul(ph[px], ph[g.nx + py]), ph[g.nx + g.ny + pz]);
 }
 
-// Phase-shift dealiasing: dst = src exp(i k.D), D half a grid spacing along
-// every axis, the coefficients of the field on the shifted grid (three
-// components).
 template <typename T>
 __global__ void k_phase(const typename Cx<T>::type *__restrict__ src, typename Cx<T>::type *__restrict__ dst,
-                        Grid g, long M) {
+                        const typename Cx<T>::type *__restrict__ ph, Grid g, long M) {
     typedef typename Cx<T>::type C;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        double s, c;
-        sincospi(shift_phase(mode_at(m, g), g), &s, &c);
-        const C ph = mkc((T)c, (T)s);
+        const C f = shift_factor<T>(m, g, ph);
 #pragma unroll
-        for (int d = 0; d < 3; d++) dst[d * M + m] = cmul(src[d * M + m], ph);
+        for (int d = 0; d < 3; d++) dst[d * M + m] = cmul(src[d * M + m], f);
     }
 }
 
@@ -269,15 +277,13 @@ __global__ void k_phase(const typename Cx<T>::type *__restrict__ src, typename C
 // back, on the shifted grid, averaged (three components).
 template <typename T>
 __global__ void k_phase_avg(typename Cx<T>::type *__restrict__ acc, const typename Cx<T>::type *__restrict__ sh,
-                            Grid g, long M) {
+                            const typename Cx<T>::type *__restrict__ ph, Grid g, long M) {
     typedef typename Cx<T>::type C;
     for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
-        double s, c;
-        sincospi(shift_phase(mode_at(m, g), g), &s, &c);
-        const C ph = mkc((T)c, (T)-s);
+        const C f = cconj(shift_factor<T>(m, g, ph));
 #pragma unroll
         for (int d = 0; d < 3; d++)
-            acc[d * M + m] = cscale(cadd(acc[d * M + m], cmul(sh[d * M + m], ph)), (T)0.5);
+            acc[d * M + m] = cscale(cadd(acc[d * M + m], cmul(sh[d * M + m], f)), (T)0.5);
     }
 }
 
@@ -467,28 +473,28 @@ cudaError_t plain_cross_mhd(T *f, const Grid &g, cudaStream_t s) {
 template <typename T>
 cudaError_t plain_update_b(typename Cx<T>::type *b, typename Cx<T>::type *b1,
                            const typename Cx<T>::type *nb, const T *etab, const Grid &g, int stage,
-                           double dt, double eta_dt, int dealias, cudaStream_t s) {
+                           double dt, int dealias, cudaStream_t s) {
     const long M = g.M();
     if (g.unit)
-        k_update_b<T, true><<<grid_for(M, 256), 256, 0, s>>>(b, b1, nb, etab, g, M, stage, dt, eta_dt, dealias);
+        k_update_b<T, true><<<grid_for(M, 256), 256, 0, s>>>(b, b1, nb, etab, g, M, stage, dt, dealias);
     else
-        k_update_b<T, false><<<grid_for(M, 256), 256, 0, s>>>(b, b1, nb, etab, g, M, stage, dt, eta_dt, dealias);
+        k_update_b<T, false><<<grid_for(M, 256), 256, 0, s>>>(b, b1, nb, etab, g, M, stage, dt, dealias);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t plain_phase(const typename Cx<T>::type *src, typename Cx<T>::type *dst, const Grid &g,
-                        cudaStream_t s) {
+cudaError_t plain_phase(const typename Cx<T>::type *src, typename Cx<T>::type *dst,
+                        const typename Cx<T>::type *ph, const Grid &g, cudaStream_t s) {
     const long M = g.M();
-    k_phase<T><<<grid_for(M, 256), 256, 0, s>>>(src, dst, g, M);
+    k_phase<T><<<grid_for(M, 256), 256, 0, s>>>(src, dst, ph, g, M);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t plain_phase_avg(typename Cx<T>::type *acc, const typename Cx<T>::type *sh, const Grid &g,
-                            cudaStream_t s) {
+cudaError_t plain_phase_avg(typename Cx<T>::type *acc, const typename Cx<T>::type *sh,
+                            const typename Cx<T>::type *ph, const Grid &g, cudaStream_t s) {
     const long M = g.M();
-    k_phase_avg<T><<<grid_for(M, 256), 256, 0, s>>>(acc, sh, g, M);
+    k_phase_avg<T><<<grid_for(M, 256), 256, 0, s>>>(acc, sh, ph, g, M);
     return cudaGetLastError();
 }
 
@@ -555,12 +561,12 @@ cudaError_t energy_final(const double *part, int nparts, double *series, int cap
     template cudaError_t plain_curl<T>(const Cx<T>::type *, Cx<T>::type *, const Grid &, cudaStream_t); \
     template cudaError_t plain_cross<T>(T *, const T *, const Grid &, cudaStream_t);              \
     template cudaError_t plain_cross_mhd<T>(T *, const Grid &, cudaStream_t);                     \
-    template cudaError_t plain_phase<T>(const Cx<T>::type *, Cx<T>::type *, const Grid &, cudaStream_t); \
-    template cudaError_t plain_phase_avg<T>(Cx<T>::type *, const Cx<T>::type *, const Grid &,     \
-                                            cudaStream_t);                                        \
+    template cudaError_t plain_phase<T>(const Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,  \
+                                        const Grid &, cudaStream_t);                              \
+    template cudaError_t plain_phase_avg<T>(Cx<T>::type *, const Cx<T>::type *, const Cx<T>::type *, \
+                                            const Grid &, cudaStream_t);                          \
     template cudaError_t plain_update_b<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,     \
-                                           const T *, const Grid &, int, double, double, int,     \
-                                           cudaStream_t);                                         \
+                                           const T *, const Grid &, int, double, int, cudaStream_t); \
     template cudaError_t plain_update<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,       \
                                          const T *, const Grid &, const UpdateArgs &, cudaStream_t); \
     template cudaError_t plain_energy_partials<T>(const Cx<T>::type *, const Grid &, double *,    \

@@ -19,7 +19,6 @@ struct UpdateArgs {
     int mfx, mfy, mfz;   // grid index of kf along each axis (kf l_i)
     int dealias;
     double rot;       // rotation rate about z (Coriolis -2 rot z x u)
-    double nu_dt;     // nu dt: the factor exp(-nu |k|^2 dt) where no table applies
 };
 
 template <typename T>
@@ -29,20 +28,22 @@ template <typename T> cudaError_t plain_cross(T *u, const T *w, const Grid &g, c
 template <typename T> cudaError_t plain_cross_mhd(T *f, const Grid &g, cudaStream_t s);
 // Phase-shift dealiasing: dst = src exp(i k.D) (the shifted grid's coefficients), and
 // acc = (acc + sh exp(-i k.D)) / 2; D half a grid spacing along every axis,
-// k.D = pi sum_i m_i / N_i, three components.
+// k.D = pi sum_i m_i / N_i, three components; ph = the per-axis factors
+// exp(i pi m / N_i) by array position, [N_x | N_y | N_z/2+1].
 template <typename T>
-cudaError_t plain_phase(const typename Cx<T>::type *src, typename Cx<T>::type *dst, const Grid &g,
-                        cudaStream_t s);
+cudaError_t plain_phase(const typename Cx<T>::type *src, typename Cx<T>::type *dst,
+                        const typename Cx<T>::type *ph, const Grid &g, cudaStream_t s);
 template <typename T>
-cudaError_t plain_phase_avg(typename Cx<T>::type *acc, const typename Cx<T>::type *sh, const Grid &g,
-                            cudaStream_t s);
+cudaError_t plain_phase_avg(typename Cx<T>::type *acc, const typename Cx<T>::type *sh,
+                            const typename Cx<T>::type *ph, const Grid &g, cudaStream_t s);
 // MHD induction update of b (stage 1: b1 = E (b + dt N_b); stage 2: b = E b/2 +
-// (b1 + dt N_b)/2) from nb = transform of u x b; etab = exp(-eta k^2 dt) by
-// integer |k|^2 on a unit box (else the factor is formed per mode from eta_dt).
+// (b1 + dt N_b)/2) from nb = transform of u x b.  Factor tables (etab here,
+// and the update's): exp(-c k^2 dt) by integer |k|^2 on a unit box, else the
+// per-axis factors exp(-c k_i^2 dt) by array position, [N_x | N_y | N_z/2+1].
 template <typename T>
 cudaError_t plain_update_b(typename Cx<T>::type *b, typename Cx<T>::type *b1,
                            const typename Cx<T>::type *nb, const T *etab, const Grid &g, int stage,
-                           double dt, double eta_dt, int dealias, cudaStream_t s);
+                           double dt, int dealias, cudaStream_t s);
 template <typename T>
 cudaError_t plain_update(typename Cx<T>::type *a, typename Cx<T>::type *a1,
                          const typename Cx<T>::type *nl, const T *etab, const Grid &g,
