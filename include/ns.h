@@ -137,14 +137,18 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec,
  * if on_device = 0, device memory if 1).
  * Modes outside Pi are dropped (the Galerkin truncation of Sec. 2); the
  * context converts to its precision and layout.  Synchronous with respect to
- * the host buffer: it may be reused when the call returns.  Errors:
- * NS_ERR_ARG (bad run index or null pointer), NS_ERR_CUDA. */
+ * the host buffer: it may be reused when the call returns.  A page-locked
+ * host buffer (cudaHostAlloc'd or registered, 16-byte aligned) is read by the
+ * conversion kernels directly; pageable memory is copied through a device
+ * staging buffer.  Errors: NS_ERR_ARG (bad run index or null pointer),
+ * NS_ERR_CUDA. */
 ns_status ns_set_state(ns_ctx *ctx, int run, const void *uhat, int on_device);
 
 /* Store the state of one run into a full half-layout FP64 complex array
  * [3][N][N][N/2+1] ([3][N_x][N_y][N_z/2+1] on other grids; host if
  * on_device = 0, device if 1); modes outside Pi
- * are written as zero.  Synchronises the context's stream.  Errors:
+ * are written as zero (directly into a page-locked host buffer, else through
+ * a device staging buffer).  Synchronises the context's stream.  Errors:
  * NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_NONFINITE. */
 ns_status ns_get_state(ns_ctx *ctx, int run, void *uhat, int on_device);
 

@@ -18,6 +18,7 @@
 #include "fused.h"
 #include "ns_internal.h"
 #include "plain.h"
+#include "reduce.cuh"
 
 using namespace nsk;
 
@@ -873,8 +874,9 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
             }
         }
     }
-    if ((e = dalloc(&c->spec, sizeof(double) * maxbins)) != cudaSuccess ||
-        (e = dalloc(&c->ens, sizeof(double) * maxbins)) != cudaSuccess)
+    // nbins results, then kShellParts partials per shell
+    if ((e = dalloc(&c->spec, sizeof(double) * maxbins * (1 + kShellParts))) != cudaSuccess ||
+        (e = dalloc(&c->ens, sizeof(double) * maxbins * (1 + kShellParts))) != cudaSuccess)
         return bail(fail_cuda(nullptr, e));
     c->spec_cap = maxbins;
     // streams for concurrent units of the step graph (ensembles)
@@ -916,12 +918,34 @@ void ns_destroy(ns_ctx *c) {
     delete c;
 }
 
+// Device address of a host buffer the GPU can reach directly (page-locked
+// memory: cudaHostAlloc'd or registered), 16-byte aligned, else null.  Such
+// buffers are read and written by the conversion kernels themselves (over
+// NVLink-C2C on Grace-Blackwell), without staging copies; pageable memory
+// goes through the staging buffer.
+static const void *mapped_host(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || ((uintptr_t)a.devicePointer & 15)) return nullptr;
+    return a.devicePointer;
+}
+
 ns_status ns_set_field(ns_ctx *c, int run, int field, const void *uhat, int on_device) {
     ns_status st = check_ctx(c);
     if (st != NS_OK) return st;
     if (run < 0 || run >= (int)c->runs.size() || !uhat) return NS_ERR_ARG;
     Run &r = c->runs[run];
     if (field != 0 && !(field == 1 && r.p.mhd)) return NS_ERR_ARG;
+    if (!on_device) {
+        if (const void *d = mapped_host(uhat)) {   // page-locked: no staging
+            if ((st = ns_set_field(c, run, field, d, 1)) != NS_OK) return st;
+            NS_CK(cudaStreamSynchronize(c->stream));   // the caller may reuse its buffer
+            return NS_OK;
+        }
+    }
     if (use_fused(c)) {
         if (!on_device) {
             ns_status s2 = ensure_staging(c, kStageChunk);
@@ -946,6 +970,9 @@ ns_status ns_get_field(ns_ctx *c, int run, int field, void *uhat, int on_device)
     if (run < 0 || run >= (int)c->runs.size() || !uhat) return NS_ERR_ARG;
     Run &r = c->runs[run];
     if (field != 0 && !(field == 1 && r.p.mhd)) return NS_ERR_ARG;
+    if (!on_device) {
+        if (const void *d = mapped_host(uhat)) return ns_get_field(c, run, field, (void *)d, 1);
+    }
     if (use_fused(c)) {
         if (!on_device) {
             ns_status s2 = ensure_staging(c, kStageChunk);

@@ -1220,14 +1220,12 @@ cudaError_t fused_spectrum(FusedRun &f, int run, int field, int nbins, double *s
                            cudaStream_t s) {
     if (field != 0 && !(field == 1 && f.mhd)) return cudaErrorInvalidValue;
     CompactAcc acc{f.a + field * f.blk_s + (long)run * 3 * f.M, f.K, f.Mx, f.Mz, f.M};
-    k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, f.n, nbins, spec, ens);
-    return cudaGetLastError();
+    return shell_launch(k_shell_spectrum<CompactAcc>, nbins, spec, ens, s, acc, f.n, nbins);
 }
 
 cudaError_t fused_helicity(FusedRun &f, int run, int nbins, double *spec, double *aux, cudaStream_t s) {
     CompactHelAcc acc{f.a + (long)run * 3 * f.M, f.K, f.Mx, f.Mz, f.M};
-    k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, f.n, nbins, spec, aux);
-    return cudaGetLastError();
+    return shell_launch(k_shell_spectrum<CompactHelAcc>, nbins, spec, aux, s, acc, f.n, nbins);
 }
 
 }  // namespace nsk

@@ -405,7 +405,7 @@ template <class Acc>
 __global__ void __launch_bounds__(256)
 k_grid_spectrum(Acc acc, Grid g, int nbins, double *spec, double *aux) {
     __shared__ double sh[512];
-    const int K = blockIdx.x;
+    const int K = blockIdx.x, part = blockIdx.y;   // pairs part, part + kShellParts, ... (blocks)
     if (K >= nbins) return;
     const double hi = (K + 0.5) / g.lmax, lo = (K - 0.5) / g.lmax;
     const int bx = (int)(hi * g.lx) + 1, by = (int)(hi * g.ly) + 1;
@@ -414,7 +414,7 @@ k_grid_spectrum(Acc acc, Grid g, int nbins, double *spec, double *aux) {
     const long sy = y1 - y0 + 1, pairs = (long)(x1 - x0 + 1) * sy;
     const double hi2 = hi * hi * (1.0 + 1e-9) + 1e-12;
     double e = 0.0, om = 0.0;
-    for (long p = threadIdx.x; p < pairs; p += blockDim.x) {
+    for (long p = (long)part * blockDim.x + threadIdx.x; p < pairs; p += (long)blockDim.x * gridDim.y) {
         const int mx = x0 + (int)(p / sy), my = y0 + (int)(p % sy);
         const double kx = kof(mx, g.lx), ky = kof(my, g.ly);
         const double r2 = __dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky));
@@ -435,8 +435,8 @@ k_grid_spectrum(Acc acc, Grid g, int nbins, double *spec, double *aux) {
     }
     block_sum2(e, om, sh);
     if (threadIdx.x == 0) {
-        spec[K] = e;
-        aux[K] = om;
+        spec[nbins + K * kShellParts + part] = e;
+        aux[nbins + K * kShellParts + part] = om;
     }
 }
 
@@ -528,27 +528,19 @@ cudaError_t plain_energy_partials(const typename Cx<T>::type *a, const Grid &g, 
 template <typename T>
 cudaError_t plain_spectrum(const typename Cx<T>::type *a, const Grid &g, int nbins, double *spec,
                            double *ens, cudaStream_t s) {
-    if (g.cube) {
-        HalfAcc<T> acc{a, g.nx, g.M()};
-        k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, g.nx, nbins, spec, ens);
-    } else {
-        GridAcc<T> acc{a, g};
-        k_grid_spectrum<<<nbins, 256, 0, s>>>(acc, g, nbins, spec, ens);
-    }
-    return cudaGetLastError();
+    if (g.cube)
+        return shell_launch(k_shell_spectrum<HalfAcc<T>>, nbins, spec, ens, s, HalfAcc<T>{a, g.nx, g.M()}, g.nx,
+                            nbins);
+    return shell_launch(k_grid_spectrum<GridAcc<T>>, nbins, spec, ens, s, GridAcc<T>{a, g}, g, nbins);
 }
 
 template <typename T>
 cudaError_t plain_helicity(const typename Cx<T>::type *a, const Grid &g, int nbins, double *spec,
                            double *aux, cudaStream_t s) {
-    if (g.cube) {
-        HalfHelAcc<T> acc{a, g.nx, g.M()};
-        k_shell_spectrum<<<nbins, 256, 0, s>>>(acc, g.nx, nbins, spec, aux);
-    } else {
-        GridHelAcc<T> acc{a, g};
-        k_grid_spectrum<<<nbins, 256, 0, s>>>(acc, g, nbins, spec, aux);
-    }
-    return cudaGetLastError();
+    if (g.cube)
+        return shell_launch(k_shell_spectrum<HalfHelAcc<T>>, nbins, spec, aux, s, HalfHelAcc<T>{a, g.nx, g.M()},
+                            g.nx, nbins);
+    return shell_launch(k_grid_spectrum<GridHelAcc<T>>, nbins, spec, aux, s, GridHelAcc<T>{a, g}, g, nbins);
 }
 
 cudaError_t energy_final(const double *part, int nparts, double *series, int cap,

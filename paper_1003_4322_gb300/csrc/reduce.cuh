@@ -24,16 +24,22 @@ __device__ __forceinline__ void block_sum2(double &s0, double &s1, double *sh) {
     s1 = sh[1];
 }
 
-// Shell spectrum: block K sums the modes with round-half-up(|k|) = K, i.e.
-// K^2 - K + 1 <= |k|^2 <= K^2 + K (|k|^2 = 0 for K = 0), enumerating (kx, ky)
-// pairs and the kz interval they allow.  Per-thread sums in a fixed order and
-// a fixed tree make the result deterministic.  Acc maps signed (kx, ky, kz)
-// with kz >= 0 to the squared magnitude of the 3-vector coefficient, or 0.
+// Blocks per shell of the spectrum kernels (grid y).  Their partial sums sit
+// after the nbins results in spec and ens, which hold nbins (1 + kShellParts)
+// doubles each; k_shell_finish adds them in a fixed order.
+constexpr int kShellParts = 8;
+
+// Shell spectrum: blocks (K, p) sum the modes with round-half-up(|k|) = K,
+// i.e. K^2 - K + 1 <= |k|^2 <= K^2 + K (|k|^2 = 0 for K = 0), enumerating
+// the (kx, ky) pairs p, p + kShellParts, ... (in units of the block size) and
+// the kz interval each allows.  Per-thread sums in a fixed order and a fixed
+// tree make the result deterministic.  Acc maps signed (kx, ky, kz) with
+// kz >= 0 to the squared magnitude of the 3-vector coefficient, or 0.
 template <class Acc>
 __global__ void __launch_bounds__(256)
 k_shell_spectrum(Acc acc, int n, int nbins, double *spec, double *ens) {
     __shared__ double sh[512];
-    const int K = blockIdx.x;
+    const int K = blockIdx.x, part = blockIdx.y;
     if (K >= nbins) return;
     const long lo = K == 0 ? 0 : (long)K * K - K + 1, hi = (long)K * K + K;
     const int kmin = -n / 2, kmax = n / 2 - 1;
@@ -41,7 +47,8 @@ k_shell_spectrum(Acc acc, int n, int nbins, double *spec, double *ens) {
     const int a0 = max(kmin, -lim), a1 = min(kmax, lim);
     const long side = a1 - a0 + 1;
     double e = 0.0, om = 0.0;
-    for (long pidx = threadIdx.x; pidx < side * side; pidx += blockDim.x) {
+    for (long pidx = (long)part * blockDim.x + threadIdx.x; pidx < side * side;
+         pidx += (long)blockDim.x * gridDim.y) {
         const int kx = a0 + (int)(pidx / side), ky = a0 + (int)(pidx % side);
         const long r2 = (long)kx * kx + (long)ky * ky;
         if (r2 > hi) continue;
@@ -65,9 +72,31 @@ k_shell_spectrum(Acc acc, int n, int nbins, double *spec, double *ens) {
     }
     block_sum2(e, om, sh);
     if (threadIdx.x == 0) {
-        spec[K] = e;
-        ens[K] = om;
+        spec[nbins + K * kShellParts + part] = e;
+        ens[nbins + K * kShellParts + part] = om;
     }
+}
+
+// spec[K] = the sum of the shell's kShellParts partials, in order (and ens).
+static __global__ void k_shell_finish(double *spec, double *ens, int nbins) {
+    const int K = blockIdx.x * blockDim.x + threadIdx.x;
+    if (K >= nbins) return;
+    double e = 0.0, om = 0.0;
+    for (int p = 0; p < kShellParts; p++) {
+        e += spec[nbins + K * kShellParts + p];
+        om += ens[nbins + K * kShellParts + p];
+    }
+    spec[K] = e;
+    ens[K] = om;
+}
+
+// Launch a shell-spectrum kernel over nbins x kShellParts blocks, then the
+// ordered sum of the partials.
+template <class Kernel, class... Args>
+static cudaError_t shell_launch(Kernel k, int nbins, double *spec, double *ens, cudaStream_t s, Args... args) {
+    k<<<dim3(nbins, kShellParts), 256, 0, s>>>(args..., spec, ens);
+    k_shell_finish<<<(nbins + 255) / 256, 256, 0, s>>>(spec, ens, nbins);
+    return cudaGetLastError();
 }
 
 // Re(a . conj(w)) with w = i k x a, for the helicity 1/2 <u . w>.
