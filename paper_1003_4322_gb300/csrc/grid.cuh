@@ -16,6 +16,7 @@ struct Grid {
     long D = 0;                  // lcm(N_x, N_y, N_z): the ellipsoid masks in integers
     long qx = 0, qy = 0, qz = 0; // D / N_i
     int unit = 1;                // every l_i = 1: integer wavenumbers, factor table by |k|^2
+    int m32 = 1;                 // half-layout positions fit 32 bits (index decoding in 32 bits)
     int cube = 1;                // unit and N_x = N_y = N_z
     double lmax = 1.0;           // 1 / k_min with k_min = 1 / max l_i: shell K = [|k| lmax]
     __host__ __device__ long nzh() const { return nz / 2 + 1; }
@@ -30,8 +31,17 @@ struct Idx {
     int x, y, z;
 };
 __device__ __forceinline__ Idx mode_at(long m, const Grid &g) {
-    const long nh = g.nzh();
     Idx r;
+    if (g.m32) {   // 32-bit divisions (the 64-bit ones are emulated)
+        const unsigned um = (unsigned)m, nh = (unsigned)(g.nz / 2 + 1), ny = (unsigned)g.ny;
+        const unsigned q = um / nh;
+        r.z = (int)(um - q * nh);
+        const unsigned x = q / ny;
+        r.y = wavenum((int)(q - x * ny), g.ny);
+        r.x = wavenum((int)x, g.nx);
+        return r;
+    }
+    const long nh = g.nzh();
     r.z = (int)(m % nh);
     r.y = wavenum((int)((m / nh) % g.ny), g.ny);
     r.x = wavenum((int)(m / (nh * g.ny)), g.nx);

@@ -36,6 +36,7 @@ Grid make_grid(int nx, int ny, int nz, double lx, double ly, double lz) {
     g.qy = D / ny;
     g.qz = D / nz;
     g.unit = lx == 1.0 && ly == 1.0 && lz == 1.0;
+    g.m32 = g.M() < (1L << 31);
     g.cube = g.unit && nx == ny && ny == nz;
     const double lm = fmax(lx, fmax(ly, lz));
     g.lmax = 1.0 / (1.0 / lm);   // as the shell width 1 / k_min, k_min = 1 / max l
@@ -257,9 +258,9 @@ __global__ void k_update_b(typename Cx<T>::type *__restrict__ b, typename Cx<T>:
 template <typename T>
 __device__ __forceinline__ typename Cx<T>::type shift_factor(long m, const Grid &g,
                                                              const typename Cx<T>::type *__restrict__ ph) {
-    const long nh = g.nzh();
-    const int pz = (int)(m % nh), py = (int)((m / nh) % g.ny), px = (int)(m / (nh * g.ny));
-    return cmul(cmul(ph[px], ph[g.nx + py]), ph[g.nx + g.ny + pz]);
+    const Idx q = mode_at(m, g);
+    const int px = q.x < 0 ? q.x + g.nx : q.x, py = q.y < 0 ? q.y + g.ny : q.y;
+    return cmul(cmul(ph[px], ph[g.nx + py]), ph[g.nx + g.ny + q.z]);
 }
 
 template <typename T>
