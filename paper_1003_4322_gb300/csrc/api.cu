@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <tuple>
 #include <type_traits>
 #include <map>
 #include <mutex>
@@ -48,6 +49,7 @@ struct Run {
     ns_run_params p{};
     int n = 0;    // N_x (the N of a cubic run)
     Grid g;       // grid and box
+    PlainPlans gp[3];   // grid runs: the run's own plans for the x, y and z passes
     long M = 0;   // modes per component, half layout
     long V = 0;   // grid points per component
     // plain form (full half layout)
@@ -172,9 +174,16 @@ ns_status ensure_scratch(ns_ctx *c, FftRes *f) {
 
 // ---------------------------------------------------------------- transforms
 
-// Per-axis transform resources of a grid: x, y and z (all the same on the cube).
+// Per-axis transform resources of a grid: x, y and z (all the same on the
+// cube), and the plans of the x, y and z passes (those of the resources, or
+// a grid run's own).
 struct Fft3 {
-    const FftRes *x, *y, *z;
+    const FftRes *x = nullptr, *y = nullptr, *z = nullptr;
+    const PlainPlans *px = nullptr, *py = nullptr, *pz = nullptr;
+    Fft3() = default;
+    Fft3(const FftRes *x_, const FftRes *y_, const FftRes *z_, const PlainPlans *px_, const PlainPlans *py_,
+         const PlainPlans *pz_)
+        : x(x_), y(y_), z(z_), px(px_), py(py_), pz(pz_) {}
 };
 
 // FP32 transforms of a grid whose axis lengths have compile-time kernels go
@@ -203,7 +212,7 @@ cudaError_t c2r_batch(const typename Cx<T>::type *in, typename Cx<T>::type *tmp,
         if (done) return e;
     }
     const long nh = g.nzh(), plane = (long)g.ny * nh, M = (long)g.nx * plane;
-    const PlainPlans &qx = f.x->pp, &qy = f.y->pp, &qz = f.z->pp;
+    const PlainPlans &qx = *f.px, &qy = *f.py, &qz = *f.pz;
     cudaError_t e = NSK_TIMED(tr, "fft_x_inverse",
                               fft_strided<T>(in, tmp, plane, plane, M, M, ncomp, +1, qx.inv, (const C *)f.x->tw,
                                              g.nx, qx.ct_inv, s));
@@ -229,7 +238,7 @@ cudaError_t r2c_batch(const T *in, typename Cx<T>::type *out, const Grid &g, int
         if (done) return e;
     }
     const long nh = g.nzh(), plane = (long)g.ny * nh, M = (long)g.nx * plane;
-    const PlainPlans &qx = f.x->pp, &qy = f.y->pp, &qz = f.z->pp;
+    const PlainPlans &qx = *f.px, &qy = *f.py, &qz = *f.pz;
     cudaError_t e = NSK_TIMED(tr, "fft_z_r2c",
                               fft_z_r2c<T>(in, out, g.nz, (long)ncomp * g.nx * g.ny, qz.zr, (const C *)f.z->tw, s));
     if (e != cudaSuccess) return e;
@@ -242,11 +251,18 @@ cudaError_t r2c_batch(const T *in, typename Cx<T>::type *out, const Grid &g, int
                                     qx.ct_fwd, s));
 }
 
+// The transforms of a run: the resources of its axis lengths with their plans
+// (a cubic run), or with the run's own tuned plans (a grid run).
+Fft3 run_fft3(const Run &r, FftRes *const f[3]) {
+    if (r.g.cube) return Fft3{f[0], f[1], f[2], &f[0]->pp, &f[1]->pp, &f[2]->pp};
+    return Fft3{f[0], f[1], f[2], &r.gp[0], &r.gp[1], &r.gp[2]};
+}
+
 ns_status fft3_of(ns_ctx *c, const Grid &g, Fft3 *out) {
     FftRes *f[3];
     ns_status st = get_fft3(c, g, f);
     if (st != NS_OK) return st;
-    *out = Fft3{f[0], f[1], f[2]};
+    *out = Fft3{f[0], f[1], f[2], &f[0]->pp, &f[1]->pp, &f[2]->pp};
     return NS_OK;
 }
 
@@ -417,7 +433,6 @@ static void plain_cache_write(const std::map<std::pair<int, int>, PlainPlans> &c
 
 template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
     typedef typename Cx<T>::type C;
-    if (!r.g.cube) return NS_OK;   // other grids use the plans of their axis lengths as they stand
     static std::mutex mu;
     static std::map<std::pair<int, int>, PlainPlans> cache;
     static bool loaded = false;
@@ -475,6 +490,74 @@ template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
     std::lock_guard<std::mutex> g(mu);
     cache[key] = best;
     plain_cache_write(cache);
+    return NS_OK;
+}
+
+// Grid runs: the same search per axis on the run's own geometry (the x, y
+// and z passes of its grid), into the run's own plans, so that a run's
+// transforms do not depend on the other runs of its context.  Kept per
+// (grid, precision) for the life of the process; the cubic runs' plan cache
+// is neither read nor written.
+template <typename T> ns_status tune_plain_grid(ns_ctx *c, Run &r, FftRes *f[3]) {
+    typedef typename Cx<T>::type C;
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int>, std::vector<PlainPlans>> cache;
+    const Grid &g = r.g;
+    const auto key = std::make_tuple(g.nx, g.ny, g.nz, (int)sizeof(T));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            for (int a = 0; a < 3; a++) r.gp[a] = it->second[a];
+            return NS_OK;
+        }
+    }
+    const long nh = g.nzh(), plane = (long)g.ny * nh, M = (long)g.nx * plane, lines = 3L * g.nx * g.ny;
+    cudaStream_t s = c->stream;
+    C *in = (C *)r.un, *tmp = (C *)r.work, *half = (C *)r.wn;
+    T *phys = (T *)r.phys;
+    const int bound = sizeof(T) == 8 ? 384 : 512;
+    const int Es[] = {16, 12, 9, 8, 6, 4};
+    for (int a = 0; a < 3; a++) r.gp[a] = f[a]->pp;
+    for (int a = 0; a < 2; a++) {   // x pass, y pass
+        const int n = a == 0 ? g.nx : g.ny;
+        const C *tw = (const C *)f[a]->tw;
+        auto pass = [&](const C *src, C *dst, int dir, const Plan &pl, int ct) {
+            return a == 0 ? fft_strided<T>(src, dst, plane, plane, M, M, 3, dir, pl, tw, n, ct, s)
+                          : fft_strided<T>(src, dst, nh, nh, plane, plane, 3 * g.nx, dir, pl, tw, n, ct, s);
+        };
+        PlainPlans &best = r.gp[a];
+        float bi = -1.f, bf = -1.f;
+        for (int E : Es) {
+            Plan pl;
+            if (!make_plan_e(n, E, &pl) || pl.nst > 4) continue;
+            const int Tn = n / E;
+            for (int ct = 2; ct <= 32; ct *= 2) {
+                if (ct * Tn > bound || ct * Tn < 32) continue;
+                const float ti = plain_time([&]() { return pass(a == 0 ? in : tmp, tmp, +1, pl, ct); }, s);
+                if (ti > 0.f && (bi < 0.f || ti < bi)) { bi = ti; best.inv = pl; best.ct_inv = ct; }
+                const float tf = plain_time([&]() { return pass(half, half, -1, pl, ct); }, s);
+                if (tf > 0.f && (bf < 0.f || tf < bf)) { bf = tf; best.fwd = pl; best.ct_fwd = ct; }
+            }
+        }
+    }
+    {   // z passes
+        const C *tw = (const C *)f[2]->tw;
+        PlainPlans &best = r.gp[2];
+        float bc = -1.f, br = -1.f;
+        for (int E : Es) {
+            Plan ph;
+            if (!make_plan_e(g.nz / 2, E, &ph) || ph.nst > 4) continue;
+            const float tc = plain_time([&]() { return fft_z_c2r<T>(tmp, phys, g.nz, lines, ph, tw, s); }, s);
+            if (tc > 0.f && (bc < 0.f || tc < bc)) { bc = tc; best.zc = ph; }
+            const float tr = plain_time([&]() { return fft_z_r2c<T>(phys, half, g.nz, lines, ph, tw, s); }, s);
+            if (tr > 0.f && (br < 0.f || tr < br)) { br = tr; best.zr = ph; }
+        }
+    }
+    NS_CK(cudaStreamSynchronize(s));
+    for (int a = 0; a < 3; a++) r.gp[a].tuned = true;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = std::vector<PlainPlans>(r.gp, r.gp + 3);
     return NS_OK;
 }
 
@@ -542,11 +625,11 @@ template <typename T> ns_status plain_alloc(ns_ctx *c, Run &r) {
     FftRes *f[3];
     ns_status st = get_fft3(c, r.g, f);
     if (st != NS_OK) return st;
-    if ((st = tune_plain<T>(c, r, f[0])) != NS_OK) return st;
+    if ((st = r.g.cube ? tune_plain<T>(c, r, f[0]) : tune_plain_grid<T>(c, r, f)) != NS_OK) return st;
     if constexpr (std::is_same<T, float>::value) {
         // choose the standalone kernels' shapes now, outside any graph capture
         // (on the run's own buffers, whose contents the first step overwrites)
-        const Fft3 f3{f[0], f[1], f[2]};
+        const Fft3 f3 = run_fft3(r, f);
         NS_CK(r2c_batch<T>((const T *)r.phys, (C *)r.wn, r.g, 3, f3, c->stream));
         NS_CK(c2r_batch<T>((const C *)r.wn, (C *)r.work, (T *)r.phys, r.g, 3, f3, c->stream));
         NS_CK(cudaStreamSynchronize(c->stream));
@@ -571,9 +654,10 @@ UpdateArgs update_args(const Run &r, int stage) {
 
 template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tracer *tr) {
     typedef typename Cx<T>::type C;
-    Fft3 f;
-    ns_status st = fft3_of(c, r.g, &f);
+    FftRes *fr[3];
+    ns_status st = get_fft3(c, r.g, fr);
     if (st != NS_OK) return st;
+    const Fft3 f = run_fft3(r, fr);
     const Grid &g = r.g;
     T *phys = (T *)r.phys;
     const long M3 = 3 * r.M, V3 = 3 * r.V;
@@ -762,8 +846,10 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
                  "\"state_modes\": %ld, \"runs_in_group\": %d, \"passes\": %s}",
                  g.mhd ? "MHD" : "Navier-Stokes", r.n, g.K, (g.mhd ? 6 : 3) * g.M, g.nr, tune);
     } else {
+        // plans of the x pass (and the y pass of a cube) and of the z passes
         const auto it = c->fft.find(r.n);
-        const PlainPlans q = it != c->fft.end() ? it->second.pp : PlainPlans{};
+        const PlainPlans qc = it != c->fft.end() ? it->second.pp : PlainPlans{};
+        const PlainPlans &q = r.g.cube ? qc : r.gp[0], &qz = r.g.cube ? qc : r.gp[2];
         snprintf(out, len,
                  "{\"form\": \"plain %s\", \"equations\": \"%s\", \"n\": %d, \"grid\": [%d, %d, %d], "
                  "\"box\": [%.17g, %.17g, %.17g], \"tuned\": %s, "
@@ -771,7 +857,7 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
                  "\"cols_per_cta\": %d}, \"z_c2r\": {\"E\": %d}, \"z_r2c\": {\"E\": %d}}",
                  c->prec == NS_FP64 ? "FP64" : "FP32", r.p.mhd ? "MHD" : "Navier-Stokes", r.n, r.g.nx, r.g.ny,
                  r.g.nz, r.g.lx, r.g.ly, r.g.lz, q.tuned ? "true" : "false", q.inv.E, q.ct_inv, q.fwd.E, q.ct_fwd,
-                 q.zc.E, q.zr.E);
+                 qz.zc.E, qz.zr.E);
     }
     return NS_OK;
 }
@@ -1012,7 +1098,7 @@ ns_status ns_fft_r2c(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
     FftRes *f;
     if ((st = get_fft(c, n, &f)) != NS_OK) return st;
     const Grid g = make_grid(n, n, n, 1.0, 1.0, 1.0);
-    const Fft3 f3{f, f, f};
+    const Fft3 f3{f, f, f, &f->pp, &f->pp, &f->pp};
     if (c->prec == NS_FP64) {
         NS_CK(r2c_batch<double>((const double *)in, (double2 *)out, g, ncomp, f3, c->stream));
     } else {
@@ -1034,7 +1120,7 @@ ns_status ns_fft_c2r(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
     if ((st = get_fft(c, n, &f)) != NS_OK) return st;
     if ((st = ensure_scratch(c, f)) != NS_OK) return st;
     const Grid g = make_grid(n, n, n, 1.0, 1.0, 1.0);
-    const Fft3 f3{f, f, f};
+    const Fft3 f3{f, f, f, &f->pp, &f->pp, &f->pp};
     const long M = g.M(), V = g.V();
     for (int k = 0; k < ncomp; k++) {
         if (c->prec == NS_FP64)
