@@ -28,9 +28,49 @@ NSK_DEV float2 zreg_shfl(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-// r2c of nlines lines of N reals into N/2 + 1 complex values each:
-// X[k] = (Z[k] + conj Z[n-k])/2 - i W^k (Z[k] - conj Z[n-k])/2, W = e^{-2 pi i/N},
-// k = 0..n-1, and X[n] = Re Z[0] - Im Z[0].
+// r2c output of a transformed line Z (positions slot + jT in v):
+// X[k] = (Z[k] + conj Z[n-k])/2 - i W^k (Z[k] - conj Z[n-k])/2 for k < n, and
+// X[n] = Re Z[0] - Im Z[0]; Z[n-k] comes from the partner lane (register
+// E-1-j), or from this lane's register (E-j) mod E when slot = 0.
+template <int n, int E, int T>
+NSK_DEV void zreg_r2c_store(const float2 (&v)[E], int slot, int partner, bool valid, float2 *dst,
+                            const float2 *__restrict__ tw) {
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        const int k = slot + j * T;
+        float2 zm = zreg_shfl(v[E - 1 - j], partner);
+        if (slot == 0) zm = v[(E - j) % E];   // n - jT = (E - j) T, and Z[n] = Z[0]
+        const float2 zk = v[j], zc = cconj(zm);
+        const float2 ev = cscale(cadd(zk, zc), 0.5f);
+        const float2 od = cmul_i<-1>(cscale(csub(zk, zc), 0.5f));
+        if (valid) dst[k] = cadd(ev, cmul(od, __ldg(tw + k)));
+    }
+    if (valid && slot == 0) dst[n] = make_float2(v[0].x - v[0].y, 0.f);
+}
+
+// c2r input of a line from X (positions slot + jT in x, X[n] in xn on slot 0):
+// Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]), the imaginary
+// parts of X[0] and X[n] dropped.
+template <int n, int E, int T>
+NSK_DEV void zreg_c2r_pack(const float2 (&x)[E], float2 xn, int slot, int partner, float2 (&v)[E],
+                           const float2 *__restrict__ tw) {
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        const int k = slot + j * T;
+        float2 a0 = x[j];
+        float2 am = zreg_shfl(x[E - 1 - j], partner);
+        if (slot == 0) am = j > 0 ? x[(E - j) % E] : xn;
+        if (k == 0) {
+            a0.y = 0.f;
+            am.y = 0.f;
+        }
+        const float2 xc = cconj(am);
+        const float2 wb = cmulc(csub(a0, xc), __ldg(tw + k));
+        v[j] = cadd(cadd(a0, xc), cmul_i<1>(wb));
+    }
+}
+
+// r2c of nlines lines of N reals into N/2 + 1 complex values each (W = e^{-2 pi i/N}).
 template <int N, int E, int WPB>
 __global__ void __launch_bounds__(32 * WPB)
 k_z_r2c_reg(const float *__restrict__ in, float2 *__restrict__ out, long nlines,
@@ -54,24 +94,11 @@ k_z_r2c_reg(const float *__restrict__ in, float2 *__restrict__ out, long nlines,
 #pragma unroll
     for (int j = 0; j < E; j++) v[j] = valid ? src[slot + j * T] : make_float2(0.f, 0.f);
     ct_fft_reg<n, E, -1, N>(v, slot, twr, sl, ss);
-    float2 *dst = out + (valid ? line : 0) * (n + 1);
-#pragma unroll
-    for (int j = 0; j < E; j++) {
-        const int k = slot + j * T;
-        float2 zm = zreg_shfl(v[E - 1 - j], partner);
-        if (slot == 0) zm = v[(E - j) % E];   // n - jT = (E - j) T, and Z[n] = Z[0]
-        const float2 zk = v[j], zc = cconj(zm);
-        const float2 ev = cscale(cadd(zk, zc), 0.5f);
-        const float2 od = cmul_i<-1>(cscale(csub(zk, zc), 0.5f));
-        if (valid) dst[k] = cadd(ev, cmul(od, __ldg(tw + k)));
-    }
-    if (valid && slot == 0) dst[n] = make_float2(v[0].x - v[0].y, 0.f);
+    zreg_r2c_store<n, E, T>(v, slot, partner, valid, out + (valid ? line : 0) * (n + 1), tw);
 }
 
-// c2r of nlines lines of N/2 + 1 complex values into N reals each (the
-// imaginary parts of X[0] and X[n] dropped):
-// Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]), inverse
-// length-n FFT, complex element m holding the reals 2m and 2m + 1.
+// c2r of nlines lines of N/2 + 1 complex values into N reals each: the packed
+// line, its inverse length-n FFT, complex element m holding the reals 2m, 2m + 1.
 template <int N, int E, int WPB>
 __global__ void __launch_bounds__(32 * WPB)
 k_z_c2r_reg(const float2 *__restrict__ in, float *__restrict__ out, long nlines,
@@ -96,20 +123,7 @@ k_z_c2r_reg(const float2 *__restrict__ in, float *__restrict__ out, long nlines,
     for (int j = 0; j < E; j++) x[j] = valid ? src[slot + j * T] : make_float2(0.f, 0.f);
     const float2 xn = valid && slot == 0 ? src[n] : make_float2(0.f, 0.f);
     float2 v[E];
-#pragma unroll
-    for (int j = 0; j < E; j++) {
-        const int k = slot + j * T;
-        float2 a0 = x[j];
-        float2 am = zreg_shfl(x[E - 1 - j], partner);
-        if (slot == 0) am = j > 0 ? x[(E - j) % E] : xn;
-        if (k == 0) {
-            a0.y = 0.f;
-            am.y = 0.f;
-        }
-        const float2 xc = cconj(am);
-        const float2 wb = cmulc(csub(a0, xc), __ldg(tw + k));
-        v[j] = cadd(cadd(a0, xc), cmul_i<1>(wb));
-    }
+    zreg_c2r_pack<n, E, T>(x, xn, slot, partner, v, tw);
     ct_fft_reg<n, E, +1, N>(v, slot, twr, sl, ss);
     if (!valid) return;
     float2 *dst = reinterpret_cast<float2 *>(out + line * N);
@@ -156,18 +170,7 @@ k_z_r2c_pf(const float *__restrict__ in, float2 *__restrict__ out, long nlines,
         for (int j = 0; j < E; j++) v[j] = nx[j];
         if (it + 1 < IT) fetch(g0 + it + 1);
         ct_fft_reg<n, E, -1, N>(v, slot, twr, sl, ss);
-        float2 *dst = out + (valid ? line : 0) * (n + 1);
-#pragma unroll
-        for (int j = 0; j < E; j++) {
-            const int k = slot + j * T;
-            float2 zm = zreg_shfl(v[E - 1 - j], partner);
-            if (slot == 0) zm = v[(E - j) % E];
-            const float2 zk = v[j], zc = cconj(zm);
-            const float2 ev = cscale(cadd(zk, zc), 0.5f);
-            const float2 od = cmul_i<-1>(cscale(csub(zk, zc), 0.5f));
-            if (valid) dst[k] = cadd(ev, cmul(od, __ldg(tw + k)));
-        }
-        if (valid && slot == 0) dst[n] = make_float2(v[0].x - v[0].y, 0.f);
+        zreg_r2c_store<n, E, T>(v, slot, partner, valid, out + (valid ? line : 0) * (n + 1), tw);
     }
 }
 
@@ -208,20 +211,7 @@ k_z_c2r_pf(const float2 *__restrict__ in, float *__restrict__ out, long nlines,
         const float2 xn = nn;
         if (it + 1 < IT) fetch(g0 + it + 1);
         float2 v[E];
-#pragma unroll
-        for (int j = 0; j < E; j++) {
-            const int k = slot + j * T;
-            float2 a0 = x[j];
-            float2 am = zreg_shfl(x[E - 1 - j], partner);
-            if (slot == 0) am = j > 0 ? x[(E - j) % E] : xn;
-            if (k == 0) {
-                a0.y = 0.f;
-                am.y = 0.f;
-            }
-            const float2 xc = cconj(am);
-            const float2 wb = cmulc(csub(a0, xc), __ldg(tw + k));
-            v[j] = cadd(cadd(a0, xc), cmul_i<1>(wb));
-        }
+        zreg_c2r_pack<n, E, T>(x, xn, slot, partner, v, tw);
         ct_fft_reg<n, E, +1, N>(v, slot, twr, sl, ss);
         if (valid) {
             float2 *dst = reinterpret_cast<float2 *>(out + line * N);
