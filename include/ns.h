@@ -144,6 +144,12 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec,
  * NS_ERR_CUDA. */
 ns_status ns_set_state(ns_ctx *ctx, int run, const void *uhat, int on_device);
 
+/* ns_set_state of runs first .. first + count - 1 from uhats[0 .. count-1]
+ * (all host or all device buffers, as on_device says), synchronising once at
+ * the end for page-locked or device buffers: every buffer may be reused when
+ * the call returns.  Errors as ns_set_state. */
+ns_status ns_set_states(ns_ctx *ctx, int first, int count, const void *const *uhats, int on_device);
+
 /* Store the state of one run into a full half-layout FP64 complex array
  * [3][N][N][N/2+1] ([3][N_x][N_y][N_z/2+1] on other grids; host if
  * on_device = 0, device if 1); modes outside Pi
@@ -229,6 +235,16 @@ ns_status ns_field_spectrum(ns_ctx *ctx, int run, int field, double *spec, int n
 
 ns_status ns_energy_spectrum(ns_ctx *ctx, int run, double *spec, int nbins,
                              double *energy, double *enstrophy);
+
+/* ns_energy_spectrum of runs first .. first + count - 1 with one
+ * synchronisation (an ensemble's diagnostics in one round trip): spec
+ * receives count rows of nbins doubles (row i: run first + i, its
+ * ns_run_nbins shells, the rest of the row zeroed; spec may be NULL when
+ * nbins = 0); energy and enstrophy receive count values each and may be
+ * NULL.  Errors: NS_ERR_ARG (range, null pointer), NS_ERR_CUDA, NS_ERR_OOM,
+ * NS_ERR_NONFINITE (some run's energy is not finite). */
+ns_status ns_energy_spectra(ns_ctx *ctx, int first, int count, double *spec, int nbins,
+                            double *energy, double *enstrophy);
 
 /* Helicity H = 1/2 <u . w> = 1/2 sum Re(a . conj(i k x a)) over the full
  * spectrum and its shell spectrum H(K) (same shells and FP64 accumulation as

@@ -25,7 +25,8 @@ SYMBOLS = ("ns_init", "ns_set_state", "ns_get_state", "ns_step", "ns_fft_r2c", "
            "ns_kernel_census", "ns_sync", "ns_last_error", "ns_status_str", "ns_destroy",
            "ns_fft_c2r_noalloc", "ns_describe_run", "ns_helicity", "ns_set_field",
            "ns_get_field", "ns_field_spectrum", "ns_guard_check", "ns_guard_selftest",
-           "ns_fft_r2c_grid", "ns_fft_c2r_grid", "ns_run_nbins")
+           "ns_fft_r2c_grid", "ns_fft_c2r_grid", "ns_run_nbins", "ns_set_states",
+           "ns_energy_spectra")
 
 
 class NsError(RuntimeError):
@@ -75,6 +76,8 @@ def load(path: str = LIB_PATH):
         "ns_fft_r2c_grid": ([P, I, I, I, I, P, P], I),
         "ns_fft_c2r_grid": ([P, I, I, I, I, P, P], I),
         "ns_run_nbins": ([ctypes.POINTER(ns_run_params)], I),
+        "ns_set_states": ([P, I, I, ctypes.POINTER(P), I], I),
+        "ns_energy_spectra": ([P, I, I, P, I, P, P], I),
         "ns_energy_spectrum": ([P, I, P, I, ctypes.POINTER(D), ctypes.POINTER(D)], I),
         "ns_nbins": ([I], I),
         "ns_helicity": ([P, I, P, I, ctypes.POINTER(D)], I),
@@ -178,6 +181,28 @@ def ns_set_state(ctx, run: int, uhat) -> None:
 
 def ns_get_state(ctx, run: int, out) -> None:
     _check(load().ns_get_state(ctx, run, _ptr(out), _on_device(out)), "ns_get_state", ctx)
+
+
+def ns_set_states(ctx, first: int, uhats) -> None:
+    """uhats: complex128 half-layout states of runs first, first + 1, ...
+    (all numpy / host torch, or all device torch)."""
+    n = len(uhats)
+    ptrs = (ctypes.c_void_p * n)(*[_ptr(u).value for u in uhats])
+    dev = {_on_device(u) for u in uhats}
+    if len(dev) != 1:
+        raise ValueError("the buffers must all be on the host or all on the device")
+    _check(load().ns_set_states(ctx, first, n, ptrs, dev.pop()), "ns_set_states", ctx)
+
+
+def ns_energy_spectra(ctx, first: int, count: int, nbins: int):
+    """Returns (E[count], Omega[count], spectra[count][nbins]) of runs first ..
+    first + count - 1 (rows zero-padded past each run's shells)."""
+    spec = np.zeros((count, max(nbins, 0)), dtype=np.float64)
+    e = np.zeros(count, dtype=np.float64)
+    om = np.zeros(count, dtype=np.float64)
+    _check(load().ns_energy_spectra(ctx, first, count, _ptr(spec), nbins, _ptr(e), _ptr(om)),
+           "ns_energy_spectra", ctx)
+    return e, om, spec
 
 
 def ns_set_field(ctx, run: int, field: int, uhat) -> None:

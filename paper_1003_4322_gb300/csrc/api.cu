@@ -93,6 +93,8 @@ struct ns_ctx {
                                      // or a grid or box other than the cube)
     void *gscratch = nullptr;        // c2r scratch of the grid transforms
     size_t gscratch_bytes = 0;
+    double *bspec = nullptr;         // batched spectra: per run nbins results + partials, twice
+    size_t bspec_runs = 0;
     cudaGraphExec_t graph = nullptr;
     char last_error[256] = {0};
 };
@@ -998,6 +1000,7 @@ void ns_destroy(ns_ctx *c) {
     if (c->ens) dev_free(c->ens);
     if (c->staging) dev_free(c->staging);
     if (c->gscratch) dev_free(c->gscratch);
+    if (c->bspec) dev_free(c->bspec);
     if (c->cap) cudaStreamDestroy(c->cap);
     for (cudaStream_t q : c->par) cudaStreamDestroy(q);
     for (cudaEvent_t ev : c->fork_join) cudaEventDestroy(ev);
@@ -1242,6 +1245,80 @@ ns_status ns_field_spectrum(ns_ctx *c, int run, int field, double *spec, int nbi
 ns_status ns_energy_spectrum(ns_ctx *c, int run, double *spec, int nbins, double *energy,
                              double *enstrophy) {
     return ns_field_spectrum(c, run, 0, spec, nbins, energy, enstrophy);
+}
+
+ns_status ns_energy_spectra(ns_ctx *c, int first, int count, double *spec, int nbins, double *energy,
+                            double *enstrophy) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (first < 0 || count < 1 || first + count > (int)c->runs.size() || nbins < 0 || (nbins > 0 && !spec))
+        return NS_ERR_ARG;
+    // one device slice per run: spec_cap results then partials, for spec and ens
+    const size_t slice = (size_t)c->spec_cap * (1 + kShellParts);
+    if (c->bspec_runs < (size_t)count) {
+        NS_CK(cudaStreamSynchronize(c->stream));
+        if (c->bspec) dev_free(c->bspec);
+        c->bspec = nullptr;
+        c->bspec_runs = 0;
+        NS_CK(dalloc(&c->bspec, sizeof(double) * 2 * slice * count));
+        c->bspec_runs = count;
+    }
+    for (int i = 0; i < count; i++) {
+        Run &r = c->runs[first + i];
+        const int nb = grid_nbins(r.g);
+        double *sp = c->bspec + 2 * slice * i, *en = sp + slice;
+        if (use_fused(c))
+            NS_CK(fused_spectrum(c->groups[r.group], r.gidx, 0, nb, sp, en, c->stream));
+        else if (c->prec == NS_FP64)
+            NS_CK(plain_spectrum<double>((const double2 *)r.un, r.g, nb, sp, en, c->stream));
+        else
+            NS_CK(plain_spectrum<float>((const float2 *)r.un, r.g, nb, sp, en, c->stream));
+    }
+    // the results of every run (spec, then ens, of each slice) in one copy
+    std::vector<double> h((size_t)2 * count * c->spec_cap);
+    NS_CK(cudaMemcpy2DAsync(h.data(), sizeof(double) * c->spec_cap, c->bspec, sizeof(double) * slice,
+                            sizeof(double) * c->spec_cap, (size_t)2 * count, cudaMemcpyDeviceToHost,
+                            c->stream));
+    NS_CK(cudaStreamSynchronize(c->stream));
+    bool finite = true;
+    for (int i = 0; i < count; i++) {
+        const int nb = grid_nbins(c->runs[first + i].g);
+        const double *hs = h.data() + (size_t)2 * i * c->spec_cap, *he = hs + c->spec_cap;
+        double e = 0.0, om = 0.0;
+        for (int k = 0; k < nb; k++) {
+            e += hs[k];
+            om += he[k];
+        }
+        for (int k = 0; k < nbins; k++) spec[(size_t)i * nbins + k] = k < nb ? hs[k] : 0.0;
+        if (energy) energy[i] = e;
+        if (enstrophy) enstrophy[i] = om;
+        finite = finite && isfinite(e);
+    }
+    if (!finite) return NS_ERR_NONFINITE;
+    return check_flags(c);
+}
+
+ns_status ns_set_states(ns_ctx *c, int first, int count, const void *const *uhats, int on_device) {
+    ns_status st = check_ctx(c);
+    if (st != NS_OK) return st;
+    if (first < 0 || count < 1 || first + count > (int)c->runs.size() || !uhats) return NS_ERR_ARG;
+    for (int i = 0; i < count; i++)
+        if (!uhats[i]) return NS_ERR_ARG;
+    bool mapped = false;
+    for (int i = 0; i < count; i++) {
+        const void *p = uhats[i];
+        int dev = on_device;
+        if (!on_device) {
+            if (const void *d = mapped_host(p)) {   // page-locked: read by the kernels, no staging
+                p = d;
+                dev = 1;
+                mapped = true;
+            }
+        }
+        if ((st = ns_set_field(c, first + i, 0, p, dev)) != NS_OK) return st;
+    }
+    if (mapped) NS_CK(cudaStreamSynchronize(c->stream));   // the caller may reuse its buffers
+    return NS_OK;
 }
 
 ns_status ns_helicity(ns_ctx *c, int run, double *spec, int nbins, double *helicity) {

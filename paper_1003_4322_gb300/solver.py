@@ -79,6 +79,18 @@ class Solver:
         nat.ns_get_state(self.ctx, run, out)
         return out
 
+    def set_states(self, uhats, first: int = 0) -> None:
+        """The velocity states of runs first, first + 1, ... in one call (one
+        synchronisation for page-locked host or device buffers)."""
+        nat.ns_set_states(self.ctx, first, [self._checked(u, first + i) for i, u in enumerate(uhats)])
+
+    def energy_spectra(self, first: int = 0, count: int | None = None):
+        """(E, Omega, spectra) of runs first .. first + count - 1 in one round
+        trip; spectra rows are zero-padded to the widest run's shells."""
+        count = len(self.runs) - first if count is None else count
+        nb = max(nat.ns_run_nbins(self.runs[first + i]) for i in range(count))
+        return nat.ns_energy_spectra(self.ctx, first, count, nb)
+
     def set_field(self, field: int, uhat, run: int = 0) -> None:
         """field 0: velocity, 1: magnetic field of an MHD run."""
         nat.ns_set_field(self.ctx, run, field, self._checked(uhat, run))

@@ -70,3 +70,40 @@ def test_config4_ensemble_shapes(ns):
             s1.set_state(ics[i])
             s1.step(2)
             assert np.array_equal(st, s1.get_state())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batched_state_and_spectra_calls_match_per_run_calls(ns, prec):
+    """ns_set_states and ns_energy_spectra (one synchronisation for all runs)
+    give bit for bit what ns_set_state and ns_energy_spectrum give run by run,
+    from page-locked and from pageable host buffers."""
+    import torch
+    from paper_1003_4322_gb300.solver import Solver
+    runs = [dict(n=n, nu=0.01, dt=1e-3) for n in (32, 48, 32, 64)]
+    starts = [inputs.turbulence_state(r["n"], seed=70 + i) for i, r in enumerate(runs)]
+    with Solver(runs, prec=prec) as s:
+        for i, a in enumerate(starts):
+            s.set_state(a, run=i)
+        s.step(2)
+        one = [s.get_state(run=i) for i in range(len(runs))]
+        diag = [s.energy_spectrum(run=i) for i in range(len(runs))]
+    for pinned in (False, True):
+        if pinned:
+            hosts = []
+            for a in starts:
+                t = torch.empty(a.shape, dtype=torch.complex128, pin_memory=True)
+                t.numpy()[...] = a
+                hosts.append(t.numpy())
+        else:
+            hosts = [a.copy() for a in starts]
+        with Solver(runs, prec=prec) as s:
+            s.set_states(hosts)
+            for h in hosts:
+                h[...] = 0
+            s.step(2)
+            E, O, spec = s.energy_spectra()
+            for i in range(len(runs)):
+                assert np.array_equal(s.get_state(run=i), one[i])
+        for i, (e, om, sp) in enumerate(diag):
+            assert E[i] == e and O[i] == om
+            assert np.array_equal(spec[i, :len(sp)], sp) and not spec[i, len(sp):].any()
