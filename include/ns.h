@@ -147,7 +147,9 @@ ns_status ns_set_state(ns_ctx *ctx, int run, const void *uhat, int on_device);
 /* ns_set_state of runs first .. first + count - 1 from uhats[0 .. count-1]
  * (all host or all device buffers, as on_device says), synchronising once at
  * the end for page-locked or device buffers: every buffer may be reused when
- * the call returns.  Errors as ns_set_state. */
+ * the call returns, after an error too.  Sets the velocity (field 0) of each
+ * run; an MHD run's magnetic field is loaded with ns_set_field.  On an error
+ * the runs before the failing one are loaded.  Errors as ns_set_state. */
 ns_status ns_set_states(ns_ctx *ctx, int first, int count, const void *const *uhats, int on_device);
 
 /* Store the state of one run into a full half-layout FP64 complex array
@@ -226,15 +228,15 @@ ns_status ns_fft_c2r_noalloc(int n, int ncomp, const void *in, void *out, void *
  * on other boxes the shells are round-half-up(|k| / k_min); energy
  * and enstrophy may be NULL.  Host outputs; synchronises the stream.
  * Errors: NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_NONFINITE. */
+ns_status ns_energy_spectrum(ns_ctx *ctx, int run, double *spec, int nbins,
+                             double *energy, double *enstrophy);
+
 /* ns_energy_spectrum of one field (0: velocity, as ns_energy_spectrum; 1:
  * the magnetic field of an MHD run, E_b = 1/2 sum |b|^2 and 1/2 sum |k|^2
  * |b|^2 = 1/2 <|j|^2>).  Errors as ns_energy_spectrum, and NS_ERR_ARG for
  * field 1 of a Navier-Stokes run. */
 ns_status ns_field_spectrum(ns_ctx *ctx, int run, int field, double *spec, int nbins,
                             double *energy, double *enstrophy);
-
-ns_status ns_energy_spectrum(ns_ctx *ctx, int run, double *spec, int nbins,
-                             double *energy, double *enstrophy);
 
 /* ns_energy_spectrum of runs first .. first + count - 1 with one
  * synchronisation (an ensemble's diagnostics in one round trip): spec

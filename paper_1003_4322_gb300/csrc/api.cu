@@ -1315,10 +1315,15 @@ ns_status ns_set_states(ns_ctx *c, int first, int count, const void *const *uhat
                 mapped = true;
             }
         }
-        if ((st = ns_set_field(c, first + i, 0, p, dev)) != NS_OK) return st;
+        if ((st = ns_set_field(c, first + i, 0, p, dev)) != NS_OK) break;
     }
-    if (mapped) NS_CK(cudaStreamSynchronize(c->stream));   // the caller may reuse its buffers
-    return NS_OK;
+    // the caller may reuse (or free) its buffers when the call returns, on
+    // an error too: wait for the kernels that read the page-locked ones
+    if (mapped) {
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (st == NS_OK && e != cudaSuccess) return fail_cuda(c, e);
+    }
+    return st;
 }
 
 ns_status ns_helicity(ns_ctx *c, int run, double *spec, int nbins, double *helicity) {

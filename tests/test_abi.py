@@ -88,4 +88,6 @@ def test_null_arguments_rejected(lib):
     assert lib.ns_step(None, 1) == nat.NS_ERR_ARG
     assert lib.ns_sync(None) == nat.NS_ERR_ARG
     assert lib.ns_fft_r2c(None, 32, 1, None, None) == nat.NS_ERR_ARG
+    assert lib.ns_set_states(None, 0, 1, None, 0) == nat.NS_ERR_ARG
+    assert lib.ns_energy_spectra(None, 0, 1, None, 0, None, None) == nat.NS_ERR_ARG
     lib.ns_destroy(None)
