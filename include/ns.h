@@ -37,8 +37,8 @@
  *   f = F (sin kf z + cos kf y, sin kf x + cos kf z, sin kf y + cos kf x).
  *   Time step: integrating-factor Heun (RK2), E = exp(-nu |k|^2 dt):
  *   a1 = E (a + dt N(a)),  a_next = E a / 2 + (a1 + dt N(a1)) / 2.
- * Supported N: 2^a 3^b with N >= 8 and N even (N <= 1024 for NS_FP32,
- *   N <= 768 for NS_FP64); other N give NS_ERR_UNSUPPORTED_N.
+ * Supported N: 2^a 3^b with N >= 8, N even and N <= 1024; other N give
+ *   NS_ERR_UNSUPPORTED_N.
  * Precision: NS_FP64 is the plain form (unfused, unpruned, FP64
  *   throughout).  NS_FP32 is the fused form (pruned FP32 transforms and
  *   nonlinear term); its twiddle and integrating-factor tables are generated
@@ -127,8 +127,9 @@ typedef struct {
  * dealias not 0/1/2, force_k < 0, mhd not 0/1, mhd with dealias 2, eta < 0,
  * ny or nz < 0, a box side < 0 or > 1e6, forcing not periodic on the box,
  * a non-finite parameter), NS_ERR_UNSUPPORTED_N (an axis not supported, or
- * above 1024 points for NS_FP32 / 768 for NS_FP64, or more points than
- * that cube), NS_ERR_OOM, NS_ERR_CUDA. */
+ * above 1024 points, or more points than 1024^3), NS_ERR_OOM (a plain FP64
+ * 1024^3 run needs about 155 GB, an MHD one more than the GPU has),
+ * NS_ERR_CUDA. */
 ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec,
                   void *cuda_stream, ns_ctx **out);
 

@@ -887,7 +887,7 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
                 if (fabs(t - nearbyint(t)) > 1e-9 * t) return NS_ERR_ARG;
             }
         }
-        const int cap = prec == NS_FP32 ? 1024 : 768;
+        const int cap = 1024;
         const int ns[3] = {g.nx, g.ny, g.nz};
         for (int n : ns)
             if (!supported_n(n) || n > cap) return NS_ERR_UNSUPPORTED_N;

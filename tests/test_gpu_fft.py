@@ -104,7 +104,8 @@ def _plane_waves(n, waves, dtype):
     return u.to(dtype)
 
 
-@pytest.mark.parametrize("n,prec", [(512, "fp32"), (1024, "fp32"), (512, "fp64"), (768, "fp64")])
+@pytest.mark.parametrize("n,prec", [(512, "fp32"), (1024, "fp32"), (512, "fp64"), (768, "fp64"),
+                                    (1024, "fp64")])
 def test_full_size_plane_waves_and_round_trip(ns, n, prec):
     """At the benchmark sizes: exact peaks of known plane waves, zero
     elsewhere, and c2r(r2c(u)) = N^3 u (properties that hold at any size)."""
@@ -159,7 +160,8 @@ def test_sizes_in_any_order_fp64(ns):
         assert _rel(out.cpu().numpy(), oracle.fft3_c2r(a)) < TOL["fp64"]
 
 
-@pytest.mark.parametrize("n,prec", [(512, "fp32"), (1024, "fp32"), (512, "fp64"), (768, "fp64")])
+@pytest.mark.parametrize("n,prec", [(512, "fp32"), (1024, "fp32"), (512, "fp64"), (768, "fp64"),
+                                    (1024, "fp64")])
 def test_full_size_random_input_sampled_dft(ns, n, prec):
     """At the benchmark sizes, a random input: sampled output modes against
     the DFT written out on the host in FP64 (the sum over z for two kz in one
