@@ -516,39 +516,52 @@ def e2e(w, prec, mem, steps):
             "d2h_bytes_per_step": int(sum(x.nbytes for x in specs)), "steps": steps}
 
 
-def oracle_steps(mem, budget_s, max_steps):
+def oracle_steps(mem, budget_s, max_steps, warmup=0):
     """Whole RK2 steps of the oracle (as it stands) over the workload's runs,
-    cycling through the members, until the time budget is used."""
+    cycling through the members: `warmup` untimed steps (fewer if they use
+    the time budget), then timed steps until max_steps or the budget.
+    Returns (timed steps, their seconds, threads, warm-up steps done)."""
     import oracle
     cores = oracle.set_threads(os.cpu_count() or 1)
     runs, ics = mem
     states = list(ics)
+    params = [oracle.Params(n=r["n"], nu=r["nu"], dt=r["dt"], force_amp=r.get("force_amp", 0.0),
+                            force_k=r.get("force_k", 0), dealias=r.get("dealias", 0),
+                            eta=r.get("eta", 0.0), mhd=r.get("mhd", 0), ny=r.get("ny", 0),
+                            nz=r.get("nz", 0), lx=r.get("lx", 0.0), ly=r.get("ly", 0.0),
+                            lz=r.get("lz", 0.0)) for r in runs]
+    done = 0
+
+    def one():
+        nonlocal done
+        i = done % len(runs)
+        states[i] = oracle.step(states[i], params[i], 1)
+        done += 1
+
+    tw = time.perf_counter()
+    warm = 0
+    while warm < warmup and time.perf_counter() - tw <= budget_s:
+        one()
+        warm += 1
     t0 = time.perf_counter()
     steps = 0
     while steps < max_steps:
-        i = steps % len(runs)
-        r = runs[i]
-        p = oracle.Params(n=r["n"], nu=r["nu"], dt=r["dt"], force_amp=r.get("force_amp", 0.0),
-                          force_k=r.get("force_k", 0), dealias=r.get("dealias", 0),
-                          eta=r.get("eta", 0.0), mhd=r.get("mhd", 0), ny=r.get("ny", 0),
-                          nz=r.get("nz", 0), lx=r.get("lx", 0.0), ly=r.get("ly", 0.0),
-                          lz=r.get("lz", 0.0))
-        states[i] = oracle.step(states[i], p, 1)
+        one()
         steps += 1
         if time.perf_counter() - t0 > budget_s:
             break
-    return steps, time.perf_counter() - t0, cores
+    return steps, time.perf_counter() - t0, cores, warm
 
 
 def cpu_baseline(w, mem, budget_s=30.0):
     """The FP64 oracle (test infrastructure, as it stands) on the host cores:
     whole RK2 steps of the same workload until the time budget is used."""
-    steps, dt, cores = oracle_steps(mem, budget_s, 1000)
+    steps, dt, cores, warm = oracle_steps(mem, budget_s, 1000, warmup=1)
     nr = len(mem[0])
     unit = "run-steps/s" if nr > 1 else "steps/s"
     return {"value": steps / dt, "unit": unit, "cores": cores, "kind": "oracle",
             "sample": f"{steps} whole RK2 step(s) of {'members of ' if nr > 1 else ''}the "
-                      f"workload on {cores} host threads ({dt:.1f} s)"}
+                      f"workload on {cores} host threads ({dt:.1f} s), after {warm} untimed"}
 
 
 def max_over_ranks(ms, dist, device=None):
@@ -659,18 +672,20 @@ def reference(args, w):
     if rank != 0:
         return
     mem = members(w)
-    steps, dt, cores = oracle_steps(mem, args.cpu_budget * 4, args.steps)
+    steps, dt, cores, warm = oracle_steps(mem, args.cpu_budget * 4, args.steps, args.warmup)
     v = steps / dt
     unit = "run-steps/s" if len(mem[0]) > 1 else "steps/s"
+    what = (f"members of the {len(mem[0])}-run ensemble (in turn)" if len(mem[0]) > 1 else
+            f"the {'x'.join(str(d) for d in dims_of(w))} workload")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit,
-            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": steps, "warmup": 0,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": steps, "warmup": warm,
             "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": w["desc"], "n": w["n"]},
             "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
-                             "sample": f"{steps} of {args.steps} RK2 steps of the "
-                                       f"{'x'.join(str(d) for d in dims_of(w))} workload "
-                                       f"(bounded to {args.cpu_budget * 4:.0f} s)"},
+                             "sample": f"{steps} of {args.steps} RK2 steps of {what} "
+                                       f"after {warm} untimed (each phase bounded to "
+                                       f"{args.cpu_budget * 4:.0f} s)"},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
