@@ -1,0 +1,102 @@
+"""The benchmark's algorithmic byte model, against the arrays each kernel
+reads and writes (sized here with numpy, independently of the model's
+formulas), and the roofline arithmetic on a synthetic census."""
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _sizes(dims, prec):
+    nx, ny, nz = dims
+    ct = np.complex128 if prec == "fp64" else np.complex64
+    rt = np.float64 if prec == "fp64" else np.float32
+    half = np.empty((3, nx, ny, nz // 2 + 1), dtype=ct).nbytes   # one 3-vector, half layout
+    real = np.empty((3, nx, ny, nz), dtype=rt).nbytes           # one 3-vector on the grid
+    return half, real
+
+
+def _kept_cubic(dims):
+    """Modes of the half layout inside the cubic 2/3 rule, counted one by one."""
+    nx, ny, nz = dims
+    mx = [m if 2 * m < nx else m - nx for m in range(nx)]
+    my = [m if 2 * m < ny else m - ny for m in range(ny)]
+    cx = sum(1 for m in mx if 3 * abs(m) < nx)
+    cy = sum(1 for m in my if 3 * abs(m) < ny)
+    cz = sum(1 for m in range(nz // 2 + 1) if 3 * m < nz)
+    return cx * cy * cz
+
+
+@pytest.mark.parametrize("dims", [(64, 64, 64), (96, 96, 96), (256, 256, 256), (48, 64, 96)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_plain_kernel_bytes_are_the_arrays_they_move(dims, prec):
+    half, real = _sizes(dims, prec)
+    n = dims if len(set(dims)) > 1 else dims[0]
+    want = {
+        "fft_x_inverse": 2 * half, "fft_x_forward": 2 * half,     # read and write in place
+        "fft_y_inverse": 2 * half, "fft_y_forward": 2 * half,
+        "fft_z_c2r": half + real, "fft_z_r2c": half + real,
+        "fft_c2r_std": (half + real) + 4 * half, "fft_r2c_std": (half + real) + 4 * half,
+        "curl": 2 * half,                                          # read a, write w
+        "cross": 3 * real,                                         # read u, w; write u x w
+        "cross_mhd": 6 * real,                                     # read u, w, b, j; write 2
+    }
+    for name, b in want.items():
+        got, flops = bench.kernel_model(name, n, prec)
+        assert got == b, (name, got, b)
+        assert flops > 0
+    # the update writes every mode of three components and reads the
+    # product, the state and (at stage 2) the stage-1 state at the kept modes
+    cb = half // (3 * dims[0] * dims[1] * (dims[2] // 2 + 1))
+    got, _ = bench.kernel_model("update", n, prec)
+    assert got == (3 * dims[0] * dims[1] * (dims[2] // 2 + 1) + 7.5 * _kept_cubic(dims)) * cb
+
+
+@pytest.mark.parametrize("n", [64, 96, 128, 256, 512])
+def test_fused_pass_bytes_follow_the_pruned_shapes(n):
+    """Passes of the fused FP32 form move complex64 fields of the pruned
+    shapes: the compact state [3][2K+1][2K+1][K+1], pass A/D fields
+    [.][2K+1][N][K+1], pass B/C fields [.][N][N][K+1], K the largest kept
+    wavenumber (3K < N)."""
+    K = max(k for k in range(n) if 3 * k < n)
+    c64 = np.dtype(np.complex64).itemsize
+    S = (2 * K + 1) ** 2 * (K + 1)
+    Ax = (2 * K + 1) * n * (K + 1)
+    Bx = n * n * (K + 1)
+    want = {
+        "fused_A_x_inverse_curl": 3 * S + 6 * Ax,   # reads a, writes u and w
+        "fused_B_y_inverse": 6 * Ax + 6 * Bx,
+        "fused_C_z_nonlinear": 6 * Bx + 3 * Bx,     # reads u, w; writes u x w transformed
+        "fused_D_y_forward": 3 * Bx + 3 * Ax,
+        "fused_E_x_forward": 3 * Ax + 3 * S,
+    }
+    for name, modes in want.items():
+        got, _ = bench.kernel_model(name, n, "fp32")
+        assert got == modes * c64, (name, got, modes * c64)
+
+
+def test_roofline_arithmetic_on_a_synthetic_census():
+    peaks = {"hbm_gbs": 6000.0, "sm_max_mhz": 2000.0, "source": "measured"}
+    w = {"n": 256, "name": "none"}
+    # FP64 z c2r: flop-bound by its model; achieved = flops / time, frac = achieved / peak
+    census = [("fft_z_c2r", 4, 8.0), ("curl", 2, 1.0)]
+    roof, total = bench.roofline_of(census, w, "fp64", 2, peaks, None)
+    assert total == 9.0 and roof["kernel"] == "fft_z_c2r" and roof["launches_per_step"] == 2
+    _, flops = bench.kernel_model("fft_z_c2r", 256, "fp64")
+    assert roof["bound"] == "alu"
+    assert math.isclose(roof["achieved"], flops / 2e-3 / 1e12)
+    assert math.isclose(roof["peak"], 152 * 4.0 * 2000e6 / 1e12)
+    assert math.isclose(roof["frac"], roof["achieved"] / roof["peak"])
+    # FP32 fused pass: HBM-bound; achieved = bytes / time against the HBM peak
+    census = [("fused_C_z_nonlinear", 2, 1.0)]
+    roof, _ = bench.roofline_of(census, w, "fp32", 1, peaks, None)
+    b, _ = bench.kernel_model("fused_C_z_nonlinear", 256, "fp32")
+    assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    assert math.isclose(roof["achieved"], b / 0.5e-3 / 1e9)
+    assert math.isclose(roof["frac"], roof["achieved"] / 6000.0)
