@@ -107,3 +107,37 @@ def test_batched_state_and_spectra_calls_match_per_run_calls(ns, prec):
         for i, (e, om, sp) in enumerate(diag):
             assert E[i] == e and O[i] == om
             assert np.array_equal(spec[i, :len(sp)], sp) and not spec[i, len(sp):].any()
+
+
+def test_batched_calls_reject_bad_ranges_and_null_buffers(ns):
+    """Argument errors of ns_set_states / ns_energy_spectra come back as
+    NS_ERR_ARG before any device work, and leave the context usable."""
+    import ctypes
+
+    from paper_1003_4322_gb300 import _native as nat
+    from paper_1003_4322_gb300.solver import Solver
+    runs = [dict(n=16, nu=0.01, dt=1e-3), dict(n=24, nu=0.02, dt=1e-3)]
+    starts = [inputs.turbulence_state(r["n"], seed=90 + i) for i, r in enumerate(runs)]
+    lib = nat.load()
+    with Solver(runs, prec="fp64") as s:
+        good = [a.ctypes.data for a in starts]
+        P2 = ctypes.c_void_p * 2
+        assert lib.ns_set_states(s.ctx, 1, 2, P2(*good), 0) == nat.NS_ERR_ARG     # past the last run
+        assert lib.ns_set_states(s.ctx, -1, 1, P2(*good), 0) == nat.NS_ERR_ARG
+        assert lib.ns_set_states(s.ctx, 0, 0, P2(*good), 0) == nat.NS_ERR_ARG
+        assert lib.ns_set_states(s.ctx, 0, 2, P2(good[0], None), 0) == nat.NS_ERR_ARG
+        assert lib.ns_set_states(s.ctx, 0, 2, None, 0) == nat.NS_ERR_ARG
+        spec = np.zeros((3, 40))
+        sp = spec.ctypes.data_as(ctypes.c_void_p)
+        assert lib.ns_energy_spectra(s.ctx, 0, 3, sp, 40, None, None) == nat.NS_ERR_ARG
+        assert lib.ns_energy_spectra(s.ctx, 2, 1, sp, 40, None, None) == nat.NS_ERR_ARG
+        assert lib.ns_energy_spectra(s.ctx, 0, 1, None, 40, None, None) == nat.NS_ERR_ARG
+        # the context still works, and nbins = 0 with no spectrum buffer is allowed
+        s.set_states(starts)
+        s.step(1)
+        E, O, _ = s.energy_spectra()
+        e0, o0, _ = s.energy_spectrum(run=0)
+        assert E[0] == e0 and O[0] == o0 and np.all(np.isfinite(E))
+        E2 = (ctypes.c_double * 2)()
+        assert lib.ns_energy_spectra(s.ctx, 0, 2, None, 0, E2, None) == nat.NS_OK
+        assert list(E2) == list(E)
