@@ -1093,11 +1093,15 @@ ns_status ns_step(ns_ctx *c, int nsteps) {
     return NS_OK;
 }
 
+// Axis lengths of every entry point: those with transform plans, up to 1024
+// points (the range the transforms are built, tuned and tested for).
+static bool axis_ok(int n) { return n <= 1024 && supported_n(n); }
+
 ns_status ns_fft_r2c(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
     ns_status st = check_ctx(c);
     if (st != NS_OK) return st;
     if (!in || !out || ncomp < 1 || ncomp > 65535 / (n > 0 ? n : 1)) return NS_ERR_ARG;
-    if (!supported_n(n)) return NS_ERR_UNSUPPORTED_N;
+    if (!axis_ok(n)) return NS_ERR_UNSUPPORTED_N;
     FftRes *f;
     if ((st = get_fft(c, n, &f)) != NS_OK) return st;
     const Grid g = make_grid(n, n, n, 1.0, 1.0, 1.0);
@@ -1118,7 +1122,7 @@ ns_status ns_fft_c2r(ns_ctx *c, int n, int ncomp, const void *in, void *out) {
     ns_status st = check_ctx(c);
     if (st != NS_OK) return st;
     if (!in || !out || ncomp < 1) return NS_ERR_ARG;
-    if (!supported_n(n)) return NS_ERR_UNSUPPORTED_N;
+    if (!axis_ok(n)) return NS_ERR_UNSUPPORTED_N;
     FftRes *f;
     if ((st = get_fft(c, n, &f)) != NS_OK) return st;
     if ((st = ensure_scratch(c, f)) != NS_OK) return st;
@@ -1148,7 +1152,7 @@ static ns_status grid_fft_args(ns_ctx *c, int nx, int ny, int nz, int ncomp, con
     ns_status st = check_ctx(c);
     if (st != NS_OK) return st;
     if (!in || !out || ncomp < 1 || ncomp > 65535 / (nx > 0 ? nx : 1)) return NS_ERR_ARG;
-    if (!supported_n(nx) || !supported_n(ny) || !supported_n(nz)) return NS_ERR_UNSUPPORTED_N;
+    if (!axis_ok(nx) || !axis_ok(ny) || !axis_ok(nz)) return NS_ERR_UNSUPPORTED_N;
     *g = make_grid(nx, ny, nz, 1.0, 1.0, 1.0);
     return fft3_of(c, *g, f3);
 }

@@ -60,11 +60,8 @@ bool make_plan_e(int n, int E, Plan *pl) {
     return true;
 }
 
-// The axis lengths of the library: 2^a 3^b, even, 8 <= N <= 1024, the range
-// its transforms are built, tuned and tested for (the documented range of
-// every entry point, standalone transforms included).
 bool supported_n(int n) {
-    if (n < 8 || n % 2 || n > 1024) return false;
+    if (n < 8 || n % 2) return false;
     Plan p;
     return make_plan(n, &p) && make_plan(n / 2, &p);
 }
