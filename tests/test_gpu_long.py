@@ -1,11 +1,14 @@
-"""Long parity runs, opt-in (NS_LONG_TESTS=1): the oracle needs minutes of
-host time for them.
+"""Long parity runs, opt-in (NS_LONG_TESTS=1): minutes of oracle time on the
+host, or a GPU run of about 155 GB.
 
-256^3 decaying Taylor-Green vortex (nu = 1/1600, dt = 2e-3), 200 RK2 steps
-of the plain FP64 GPU form against the FP64 CPU oracle (Sec. 2, Eqs. 1-2):
-relative L2 distance of the velocity on the 64^3 sub-lattice (every 4th grid
-point), of the spectral state, and of E and Omega after 50, 100, 150 and 200
-steps."""
+* 256^3 decaying Taylor-Green vortex (nu = 1/1600, dt = 2e-3), 200 RK2 steps
+  of the plain FP64 GPU form against the FP64 CPU oracle (Sec. 2, Eqs. 1-2):
+  relative L2 distance of the velocity on the 64^3 sub-lattice (every 4th
+  grid point), of the spectral state, and of E and Omega after 50, 100, 150
+  and 200 steps;
+* 512^3 forced turbulence, one RK2 step of both forms against the oracle;
+* 1024^3 forced turbulence, 20 steps of the fused FP32 form against the
+  plain FP64 form."""
 import math
 import os
 
