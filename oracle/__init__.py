@@ -112,6 +112,7 @@ def lib():
         L.or_forcing.argtypes = [ctypes.POINTER(_Params), P]
         L.or_nonlinear.argtypes = [ctypes.POINTER(_Params), P, P]
         L.or_step.argtypes = [ctypes.POINTER(_Params), P, ctypes.c_int]
+        L.or_step_with.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, P, ctypes.c_int]
         L.or_nbins.argtypes = [ctypes.c_int]
         L.or_diagnostics.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int]
         L.or_helicity.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int]
@@ -205,12 +206,23 @@ def nonlinear(a: np.ndarray, p: Params) -> np.ndarray:
     return out
 
 
-def step(a: np.ndarray, p: Params, nsteps: int) -> np.ndarray:
-    """nsteps integrating-factor RK2 steps; returns the new state (a copy)."""
+INTEGRATORS = {"if-heun": 0, "if-midpoint": 1, "rk2": 2}
+
+
+def step(a: np.ndarray, p: Params, nsteps: int, integrator: str = "if-heun") -> np.ndarray:
+    """nsteps RK2 steps; returns the new state (a copy).  integrator:
+    "if-heun" (integrating-factor Heun, the reading of the unnamed integrator
+    that the solver uses), or for comparison only "if-midpoint"
+    (integrating factor with the midpoint rule) and "rk2" (Heun with the
+    viscous term explicit)."""
     v = np.array(a, dtype=np.complex128, order="C", copy=True)
     _check_shape(v, p)
     cp = p.c()
-    _check(lib().or_step(ctypes.byref(cp), _ptr(v), int(nsteps)), "step")
+    if integrator == "if-heun":
+        _check(lib().or_step(ctypes.byref(cp), _ptr(v), int(nsteps)), "step")
+    else:
+        _check(lib().or_step_with(ctypes.byref(cp), INTEGRATORS[integrator], _ptr(v), int(nsteps)),
+               "step")
     return v
 
 

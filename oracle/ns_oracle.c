@@ -642,6 +642,67 @@ done:
 /* nsteps integrating-factor RK2 (Heun) steps of the state a, in place
  * (three components, or six [u; b] with mhd, b with the factor of eta).
  * The state is first restricted to Pi (the Galerkin space). */
+/* Time integrators.  The paper names none (Sec. 3 speaks only of the time
+ * advance); OR_IF_HEUN is the reading every other part of the oracle and the
+ * product use.  The other two are for comparison only:
+ *   OR_IF_MIDPOINT  integrating factor with the midpoint rule, E_h =
+ *                   exp(-nu |k|^2 dt / 2):  a_h = E_h (a + dt/2 N(a)),
+ *                   a' = E a + dt E_h N(a_h);
+ *   OR_RK2          Heun on da/dt = N(a) - nu |k|^2 a with the viscous
+ *                   (and resistive) term explicit:  L(a) = N(a) - nu k^2 a,
+ *                   a1 = a + dt L(a),  a' = a + dt/2 (L(a) + L(a1)). */
+enum { OR_IF_HEUN = 0, OR_IF_MIDPOINT = 1, OR_RK2 = 2 };
+
+int or_step_with(const or_params *p, int integrator, cplx *a, int nsteps)
+{
+    if (!p || !a || nsteps < 0 || integrator < OR_IF_HEUN || integrator > OR_RK2) return OR_ERR_ARG;
+    const grid g = grid_of(p);
+    if (!grid_ok(&g)) return OR_ERR_ARG;
+    const int nc = p->mhd ? 6 : 3;
+    const long M = g.M;
+    int e = OR_ERR_OOM;
+    double *E = malloc(sizeof(double) * 2 * (size_t)M);    /* full step: nu, then eta */
+    double *Eh = malloc(sizeof(double) * 2 * (size_t)M);   /* half step */
+    double *lam = malloc(sizeof(double) * 2 * (size_t)M);  /* nu |k|^2, then eta |k|^2 */
+    cplx *N0 = malloc(sizeof(cplx) * nc * (size_t)M);
+    cplx *N1 = malloc(sizeof(cplx) * nc * (size_t)M);
+    cplx *a1 = malloc(sizeof(cplx) * nc * (size_t)M);
+    if (!E || !Eh || !lam || !N0 || !N1 || !a1) goto done;
+    for (long m = 0; m < M; m++) {
+        int mi[3];
+        double k[3];
+        mode_of(&g, m, mi, k);
+        const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        lam[m] = p->nu * k2;
+        lam[M + m] = p->eta * k2;
+        E[m] = exp(-lam[m] * p->dt);
+        E[M + m] = exp(-lam[M + m] * p->dt);
+        Eh[m] = exp(-lam[m] * p->dt / 2);
+        Eh[M + m] = exp(-lam[M + m] * p->dt / 2);
+    }
+    apply_mask(&g, p->dealias, nc, a);
+    for (int s = 0; s < nsteps; s++) {
+        if ((e = or_nonlinear(p, a, N0))) goto done;
+        for (long i = 0; i < nc * M; i++) {
+            const long t = (i >= 3 * M ? M : 0) + i % M;
+            if (integrator == OR_IF_HEUN) a1[i] = E[t] * (a[i] + p->dt * N0[i]);
+            else if (integrator == OR_IF_MIDPOINT) a1[i] = Eh[t] * (a[i] + 0.5 * p->dt * N0[i]);
+            else a1[i] = a[i] + p->dt * (N0[i] - lam[t] * a[i]);
+        }
+        if ((e = or_nonlinear(p, a1, N1))) goto done;
+        for (long i = 0; i < nc * M; i++) {
+            const long t = (i >= 3 * M ? M : 0) + i % M;
+            if (integrator == OR_IF_HEUN) a[i] = 0.5 * E[t] * a[i] + 0.5 * (a1[i] + p->dt * N1[i]);
+            else if (integrator == OR_IF_MIDPOINT) a[i] = E[t] * a[i] + p->dt * Eh[t] * N1[i];
+            else a[i] = a[i] + 0.5 * p->dt * ((N0[i] - lam[t] * a[i]) + (N1[i] - lam[t] * a1[i]));
+        }
+    }
+    e = OR_OK;
+done:
+    free(E); free(Eh); free(lam); free(N0); free(N1); free(a1);
+    return e;
+}
+
 int or_step(const or_params *p, cplx *a, int nsteps)
 {
     if (!p || !a || nsteps < 0) return OR_ERR_ARG;
