@@ -209,16 +209,24 @@ ns_status ns_fft_c2r_grid(ns_ctx *ctx, int nx, int ny, int nz, int ncomp, const 
  *   out: device pointer, ncomp float fields [ncomp][n][n][n];
  *   cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
  * Scratch space (one complex field of 128^3 half layout, 8,519,680 bytes)
- * and a 128-entry twiddle table sit in fixed device arrays inside the library,
- * which every GPU that loads libns holds until the process exits; n above 128
- * (or an unsupported n) returns NS_ERR_UNSUPPORTED_N.  The first call on a
- * device looks up the arrays' device addresses for that device; make that
- * first call before any stream capture.  Every call shares the same arrays and
- * overwrites them: calls whose work overlaps on the GPU (other streams, other
- * threads) race and give wrong results, so serialise them.  The function
- * calls no cudaMalloc, cudaFree or allocating library routine.  Asynchronous
- * on cuda_stream.  Errors: NS_ERR_ARG (null pointer, ncomp < 1),
- * NS_ERR_UNSUPPORTED_N, NS_ERR_CUDA. */
+ * and the twiddle tables of every supported n up to 128 (716 complex64
+ * entries) sit in fixed device arrays inside the library, which every GPU
+ * that loads libns holds until the process exits; n above 128 (or an
+ * unsupported n) returns NS_ERR_UNSUPPORTED_N.  The first call on a device
+ * sets that device up: it looks up the arrays' device addresses, fills the
+ * twiddle tables from host memory on cuda_stream and waits for that stream;
+ * later calls only launch the transform kernels.  Make the first call on each
+ * device before any stream capture, and at start-up, before a pool allocator
+ * reserves its memory: loading the library's kernels onto the device (which
+ * the CUDA driver may defer to first use) takes device memory, including the
+ * fixed arrays.  Every call shares the same arrays and overwrites them: calls
+ * whose work overlaps on the GPU (other streams, other threads) race and
+ * give wrong results, so serialise them.  The function calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Asynchronous on cuda_stream after
+ * the first call.  Errors: NS_ERR_ARG (null pointer, ncomp < 1),
+ * NS_ERR_UNSUPPORTED_N, NS_ERR_CUDA.  It does not reset the CUDA runtime's
+ * last-error state: an error raised by the caller's earlier work stays there
+ * for the caller to read. */
 ns_status ns_fft_c2r_noalloc(int n, int ncomp, const void *in, void *out, void *cuda_stream);
 
 /* Energy E = 1/2 sum |a|^2, enstrophy Omega = 1/2 sum |k|^2 |a|^2 (sums

@@ -7,11 +7,12 @@
 // forbid any allocation after start-up.  ns_fft_c2r needs a context, and the
 // context allocates its tables and a one-field scratch buffer; this entry
 // point needs neither.  Its scratch (one complex half-layout field) and its
-// twiddle table live in file-scope __device__ arrays of fixed size, which
+// twiddle tables live in file-scope __device__ arrays of fixed size, which
 // every GPU that loads libns holds until the process exits.
 #include <math.h>
 
 #include <mutex>
+#include <vector>
 
 #include "../../include/ns.h"
 #include "ns_internal.h"
@@ -19,12 +20,16 @@
 namespace {
 
 // Largest supported grid: one FP32 complex half-layout field of 128^3
-// (128 * 128 * 65 * 8 bytes = 8,519,680 bytes) plus a 128-entry table.
+// (128 * 128 * 65 * 8 bytes = 8,519,680 bytes).
 constexpr int kNoAllocMaxN = 128;
 constexpr long kNoAllocScratch = (long)kNoAllocMaxN * kNoAllocMaxN * (kNoAllocMaxN / 2 + 1);
+// The twiddle tables exp(-2 pi i t / n), t < n, of every supported n up to
+// 128 (8, 12, 16, 18, 24, 32, 36, 48, 54, 64, 72, 96, 108, 128: 716
+// entries), one after another in increasing n.
+constexpr int kNoAllocTwiddles = 1024;
 
 static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocScratch];
-static __device__ __align__(256) float2 g_noalloc_twiddles[kNoAllocMaxN];
+static __device__ __align__(256) float2 g_noalloc_twiddles[kNoAllocTwiddles];
 
 constexpr int kMaxDevices = 64;
 
@@ -37,24 +42,54 @@ struct DeviceSlot {
 std::mutex g_mu;
 DeviceSlot g_slots[kMaxDevices];
 
-// In host code the arrays' names stand for host-side shadows, not device
-// addresses; the addresses come from cudaGetSymbolAddress, taken once per
-// device with that device current.
-ns_status setup_current_device(DeviceSlot *out) {
+// Offset of the table of length n inside g_noalloc_twiddles (-1 if n is not
+// a supported size up to the maximum).
+int table_offset(int n) {
+    int off = 0;
+    for (int m = 8; m <= kNoAllocMaxN; m += 2) {
+        if (!nsk::supported_n(m)) continue;
+        if (m == n) return off;
+        off += m;
+    }
+    return -1;
+}
+
+// Once per device, with that device current: look up the arrays' device
+// addresses (in host code their names stand for host-side shadows, not device
+// addresses) and fill every twiddle table, computed in FP64 on the host and
+// rounded once to float.  The copy is ordered on the caller's stream and
+// waited for, so that the tables are in place before any later call on any
+// stream; later calls copy nothing.
+ns_status setup_current_device(cudaStream_t s, DeviceSlot *out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return NS_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return NS_ERR_CUDA;
     std::lock_guard<std::mutex> g(g_mu);
-    DeviceSlot &s = g_slots[dev];
-    if (!s.ready) {
+    DeviceSlot &slot = g_slots[dev];
+    if (!slot.ready) {
         void *p = nullptr, *q = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return NS_ERR_CUDA;
         if (cudaGetSymbolAddress(&q, g_noalloc_twiddles) != cudaSuccess) return NS_ERR_CUDA;
-        s.scratch = (float2 *)p;
-        s.twiddles = (float2 *)q;
-        s.ready = true;
+        std::vector<float2> tw;
+        tw.reserve(kNoAllocTwiddles);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int n = 8; n <= kNoAllocMaxN; n += 2) {
+            if (!nsk::supported_n(n)) continue;
+            for (int t = 0; t < n; t++) {
+                const double a = two_pi * (double)t / (double)n;
+                tw.push_back(make_float2((float)cos(a), (float)(-sin(a))));
+            }
+        }
+        if (tw.size() > (size_t)kNoAllocTwiddles) return NS_ERR_UNSUPPORTED_N;
+        if (cudaMemcpyAsync(q, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                            s) != cudaSuccess)
+            return NS_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return NS_ERR_CUDA;
+        slot.scratch = (float2 *)p;
+        slot.twiddles = (float2 *)q;
+        slot.ready = true;
     }
-    *out = s;
+    *out = slot;
     return NS_OK;
 }
 
@@ -65,39 +100,27 @@ extern "C" ns_status ns_fft_c2r_noalloc(int n, int ncomp, const void *in, void *
     using namespace nsk;
     if (!in || !out || ncomp < 1) return NS_ERR_ARG;
     if (!supported_n(n) || n > kNoAllocMaxN) return NS_ERR_UNSUPPORTED_N;
+    const int off = table_offset(n);
     Plan plN, plH;
-    if (!make_plan(n, &plN) || !make_plan(n / 2, &plH)) return NS_ERR_UNSUPPORTED_N;
-    DeviceSlot dev;
-    ns_status st = setup_current_device(&dev);
-    if (st != NS_OK) return st;
+    if (off < 0 || !make_plan(n, &plN) || !make_plan(n / 2, &plH)) return NS_ERR_UNSUPPORTED_N;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    (void)cudaGetLastError();
-
-    // exp(-2 pi i t / n) in FP64 on the host, rounded once to float; the copy
-    // is staged out of this stack buffer before cudaMemcpyToSymbolAsync returns.
-    float2 tw[kNoAllocMaxN];
-    const double two_pi = 6.283185307179586476925286766559;
-    for (int t = 0; t < n; t++) {
-        const double a = two_pi * (double)t / (double)n;
-        tw[t] = make_float2((float)cos(a), (float)(-sin(a)));
-    }
-    if (cudaMemcpyToSymbolAsync(g_noalloc_twiddles, tw, sizeof(float2) * n, 0,
-                                cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return NS_ERR_CUDA;
+    DeviceSlot dev;
+    ns_status st = setup_current_device(s, &dev);
+    if (st != NS_OK) return st;
+    const float2 *tw = dev.twiddles + off;
 
     const long nh = n / 2 + 1, plane = (long)n * nh, M = (long)n * plane, V = (long)n * n * n;
     const int ct = default_ct(sizeof(float2), n);
     const float2 *src = (const float2 *)in;
     float *dst = (float *)out;
     for (int c = 0; c < ncomp; c++) {
-        if (fft_strided<float>(src + c * M, dev.scratch, plane, plane, M, M, 1, +1, plN,
-                               dev.twiddles, n, ct, s) != cudaSuccess)
+        if (fft_strided<float>(src + c * M, dev.scratch, plane, plane, M, M, 1, +1, plN, tw, n,
+                               ct, s) != cudaSuccess)
             return NS_ERR_CUDA;
-        if (fft_strided<float>(dev.scratch, dev.scratch, nh, nh, plane, plane, n, +1, plN,
-                               dev.twiddles, n, ct, s) != cudaSuccess)
+        if (fft_strided<float>(dev.scratch, dev.scratch, nh, nh, plane, plane, n, +1, plN, tw, n,
+                               ct, s) != cudaSuccess)
             return NS_ERR_CUDA;
-        if (fft_z_c2r<float>(dev.scratch, dst + c * V, n, (long)n * n, plH, dev.twiddles, s) !=
-            cudaSuccess)
+        if (fft_z_c2r<float>(dev.scratch, dst + c * V, n, (long)n * n, plH, tw, s) != cudaSuccess)
             return NS_ERR_CUDA;
     }
     return NS_OK;
