@@ -639,9 +639,6 @@ done:
     return e;
 }
 
-/* nsteps integrating-factor RK2 (Heun) steps of the state a, in place
- * (three components, or six [u; b] with mhd, b with the factor of eta).
- * The state is first restricted to Pi (the Galerkin space). */
 /* Time integrators.  The paper names none (Sec. 3 speaks only of the time
  * advance); OR_IF_HEUN is the reading every other part of the oracle and the
  * product use.  The other two are for comparison only:
@@ -703,6 +700,9 @@ done:
     return e;
 }
 
+/* nsteps integrating-factor RK2 (Heun) steps of the state a, in place
+ * (three components, or six [u; b] with mhd, b with the factor of eta).
+ * The state is first restricted to Pi (the Galerkin space). */
 int or_step(const or_params *p, cplx *a, int nsteps)
 {
     if (!p || !a || nsteps < 0) return OR_ERR_ARG;
