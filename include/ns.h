@@ -299,6 +299,19 @@ typedef struct {
 } ns_kernel_time;
 ns_status ns_kernel_census(ns_ctx *ctx, int nsteps, ns_kernel_time *out, int max, int *count);
 
+/* Measured FMA rate of the current device, the ALU roof of the transforms
+ * (the paper's timings are per step; a roofline needs the device's own
+ * arithmetic peak, which for FP64 the specification sheet only estimates).
+ * prec NS_FP64 times fma() on doubles, NS_FP32 fmaf() on floats: every thread
+ * of a grid that fills each SM to its occupancy limit runs eight independent
+ * chains x <- x a + b.  One calibration launch sizes the run to about ms
+ * milliseconds per launch; the best of three timed launches (CUDA events on
+ * cuda_stream, NULL for the legacy default stream) gives *flops_per_s, at two
+ * flops per FMA, at whatever SM clock the device runs.  Synchronises the
+ * stream.  Errors: NS_ERR_ARG (null pointer, unknown prec, ms outside
+ * (0, 10000]), NS_ERR_CUDA. */
+ns_status ns_alu_peak(int prec, double ms, double *flops_per_s, void *cuda_stream);
+
 /* Wait for all queued work and report any sticky or device-side error. */
 ns_status ns_sync(ns_ctx *ctx);
 

@@ -26,7 +26,7 @@ SYMBOLS = ("ns_init", "ns_set_state", "ns_get_state", "ns_step", "ns_fft_r2c", "
            "ns_fft_c2r_noalloc", "ns_describe_run", "ns_helicity", "ns_set_field",
            "ns_get_field", "ns_field_spectrum", "ns_guard_check", "ns_guard_selftest",
            "ns_fft_r2c_grid", "ns_fft_c2r_grid", "ns_run_nbins", "ns_set_states",
-           "ns_energy_spectra")
+           "ns_energy_spectra", "ns_alu_peak")
 
 
 class NsError(RuntimeError):
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         "ns_fft_r2c": ([P, I, I, P, P], I),
         "ns_fft_c2r": ([P, I, I, P, P], I),
         "ns_fft_c2r_noalloc": ([I, I, P, P, P], I),
+        "ns_alu_peak": ([I, D, ctypes.POINTER(D), P], I),
         "ns_fft_r2c_grid": ([P, I, I, I, I, P, P], I),
         "ns_fft_c2r_grid": ([P, I, I, I, I, P, P], I),
         "ns_run_nbins": ([ctypes.POINTER(ns_run_params)], I),
@@ -310,6 +311,23 @@ def ns_kernel_census(ctx, nsteps: int):
     _check(load().ns_kernel_census(ctx, nsteps, arr, 64, ctypes.byref(cnt)), "ns_kernel_census", ctx)
     return [(arr[i].name.decode(), arr[i].launches, arr[i].total_ms)
             for i in range(min(cnt.value, 64))]
+
+
+def _stream_ptr(stream):
+    """cudaStream_t of a torch.cuda.Stream, a raw integer, or None."""
+    if stream is None:
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def ns_alu_peak(prec: int, ms: float = 200.0, stream=None) -> float:
+    """Measured FMA rate of the current device in flop/s (NS_FP64 or NS_FP32)."""
+    out = ctypes.c_double()
+    _check(load().ns_alu_peak(prec, float(ms), ctypes.byref(out), _stream_ptr(stream)),
+           "ns_alu_peak")
+    return out.value
 
 
 def ns_describe_run(ctx, run: int = 0) -> dict:

@@ -1,0 +1,107 @@
+// probe.cu -- ns_alu_peak: the measured FMA rate of the device, the ALU roof
+// against which the plain FP64 form's transforms are judged.
+//
+// Every thread runs CH independent FMA chains x <- x a + b for a given number
+// of iterations, so that issue, not latency, bounds the kernel; the grid fills
+// every SM to its occupancy limit.  The rate is timed with CUDA events on the
+// caller's stream after one calibration launch that sizes the run.
+#include <cuda_runtime.h>
+
+#include "../../include/ns.h"
+
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kThreads = 256;
+
+template <typename T> __device__ __forceinline__ T fma_t(T x, T a, T b);
+template <> __device__ __forceinline__ double fma_t<double>(double x, double a, double b) {
+    return fma(x, a, b);
+}
+template <> __device__ __forceinline__ float fma_t<float>(float x, float a, float b) {
+    return fmaf(x, a, b);
+}
+
+// Where a chain's sum would go if it ever reached an impossible value.
+__device__ double g_probe_sink;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fma_rate(T a, T b, int iters) {
+    T x[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; i++) x[i] = (T)(threadIdx.x + 7 * i) * (T)1e-3;
+#pragma unroll 4
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < kChains; i++) x[i] = fma_t<T>(x[i], a, b);
+    }
+    T s = (T)0;
+#pragma unroll
+    for (int i = 0; i < kChains; i++) s += x[i];
+    // never true (the chains stay in [0, 1] for these a and b, from
+    // non-negative starts); it keeps every chain's result live
+    if (s == (T)-1.25) g_probe_sink = (double)s;
+}
+
+template <typename T>
+ns_status run_probe(double ms_target, double *flops_per_s, cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NS_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return NS_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_rate<T>, kThreads, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return NS_ERR_CUDA;
+    const int blocks = sms * per_sm;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return NS_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return NS_ERR_CUDA;
+    }
+    ns_status st = NS_OK;
+    const T a = (T)0.999999, b = (T)1e-6;
+    int iters = 1 << 12;
+    double best = 0.0;
+    for (int rep = 0; rep < 4 && st == NS_OK; rep++) {
+        float ms = 0.f;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = NS_ERR_CUDA; break; }
+        T av = a, bv = b;
+        int itv = iters;
+        void *args[] = {(void *)&av, (void *)&bv, (void *)&itv};
+        if (cudaLaunchKernel((const void *)k_fma_rate<T>, dim3(blocks), dim3(kThreads), args, 0,
+                             s) != cudaSuccess) {
+            st = NS_ERR_CUDA;
+            break;
+        }
+        if (cudaEventRecord(e1, s) != cudaSuccess) { st = NS_ERR_CUDA; break; }
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = NS_ERR_CUDA; break; }
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { st = NS_ERR_CUDA; break; }
+        if (rep == 0) {   // calibration: size the timed launches to about ms_target
+            const double scale = ms > 0.f ? ms_target / (double)ms : 1.0;
+            double it = (double)iters * scale;
+            if (it < 1024.0) it = 1024.0;
+            if (it > 1.0e8) it = 1.0e8;
+            iters = (int)it;
+            continue;
+        }
+        const double flops = 2.0 * kChains * (double)iters * (double)blocks * kThreads;
+        const double rate = flops / ((double)ms * 1e-3);
+        if (rate > best) best = rate;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == NS_OK) *flops_per_s = best;
+    return st;
+}
+
+}  // namespace
+
+extern "C" ns_status ns_alu_peak(int prec, double ms, double *flops_per_s, void *cuda_stream) {
+    if (!flops_per_s || !(ms > 0.0) || ms > 10000.0) return NS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (prec == NS_FP64) return run_probe<double>(ms, flops_per_s, s);
+    if (prec == NS_FP32) return run_probe<float>(ms, flops_per_s, s);
+    return NS_ERR_ARG;
+}

@@ -91,3 +91,12 @@ def test_null_arguments_rejected(lib):
     assert lib.ns_set_states(None, 0, 1, None, 0) == nat.NS_ERR_ARG
     assert lib.ns_energy_spectra(None, 0, 1, None, 0, None, None) == nat.NS_ERR_ARG
     lib.ns_destroy(None)
+
+
+def test_alu_peak_rejects_bad_arguments_before_any_device_call(lib):
+    from paper_1003_4322_gb300 import _native as nat
+    out = ctypes.c_double()
+    assert lib.ns_alu_peak(nat.NS_FP64, 100.0, None, None) == nat.NS_ERR_ARG
+    assert lib.ns_alu_peak(nat.NS_FP64, 0.0, ctypes.byref(out), None) == nat.NS_ERR_ARG
+    assert lib.ns_alu_peak(nat.NS_FP64, 2e4, ctypes.byref(out), None) == nat.NS_ERR_ARG
+    assert lib.ns_alu_peak(7, 100.0, ctypes.byref(out), None) == nat.NS_ERR_ARG
