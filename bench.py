@@ -6,10 +6,15 @@ evaluations: 6 inverse + 3 forward 3D transforms each, the cross product,
 projection, dealiasing and update) plus the per-step FP64 energy/enstrophy
 reduction, over the whole grid.
 
-Default workload (the configuration the headline metric is quoted on):
-256^3 decaying Taylor-Green vortex, nu = 1/1600, dt = 2e-3, in the plain FP64
-form, timed over 200 RK2 steps; the FP32 form runs the same workload beside it
-and its relative L2 distance to the FP64 state is reported.
+Default workload (the configuration the headline metric is quoted on, the
+precision form): 512^3 forced turbulence (ABC forcing k = 3, F = 0.5,
+nu = 2e-3, dt = 1e-3, seeded k^-2 start), in the plain FP64 form (the
+paper's precision), timed over K RK2 steps; the fused FP32 form runs the same
+workload beside it and its relative L2 distance to the FP64 state is
+reported.  The large form rides along in the same line: 1024^3 forced
+turbulence in the fused FP32 form, and the plain FP64 form at 768^3 for
+comparison.  The standalone 3-component FFT stage is timed at 512^3 and
+1024^3, and the device's FP64 FMA rate is measured for the FP64 roofline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference      # the FP64 CPU oracle on the host cores
@@ -39,9 +44,10 @@ WORKLOADS = {
                        "(FP32 form alongside)", n=256, nu=1 / 1600, dt=2e-3, ic="tg",
                   prec="fp64", companion="fp32"),
     "forced512": dict(desc="512^3 forced turbulence, ABC forcing k=3 F=0.5, nu=2e-3, dt=1e-3, "
-                           "seeded k^-2 start on 1<=|k|<=4 (seed 3), FP32 (plain FP64 alongside)",
+                           "seeded k^-2 start on 1<=|k|<=4 (seed 3), plain FP64 (fused FP32 "
+                           "alongside)",
                       n=512, nu=2e-3, dt=1e-3, force_amp=0.5, force_k=3, ic=("turb", 3),
-                      prec="fp32", companion="fp64"),
+                      prec="fp64", companion="fp32", large=("forced1024", "plain768")),
     "forced1024": dict(desc="1024^3 forced turbulence, ABC forcing k=3 F=0.5, nu=5e-4, dt=5e-4, "
                             "seeded k^-2 start (seed 5), FP32", n=1024, nu=5e-4, dt=5e-4,
                        force_amp=0.5, force_k=3, ic=("turb", 5), prec="fp32", companion=None),
@@ -295,10 +301,10 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- GPU arm
 
-def time_form(w, prec, mem, steps, warmup, census_steps, dist):
+def time_form(w, prec, mem, steps, warmup, census_steps, dist, keep_states=True):
     """Advance one solver (all runs of the workload) through warm-up, K timed
-    steps and a kernel census; returns timing, census, final states and the
-    energy series of run 0."""
+    steps and a kernel census; returns timing, census, final states (host
+    copies, unless keep_states is false) and the energy series of run 0."""
     import torch
 
     from paper_1003_4322_gb300 import _native as nat
@@ -331,7 +337,7 @@ def time_form(w, prec, mem, steps, warmup, census_steps, dist):
     E, O = s.series(count=steps)
     census = nat.ns_kernel_census(s.ctx, census_steps) if census_steps > 0 else []
     desc = nat.ns_describe_run(s.ctx, 0)
-    states = [read_state(s, runs, i) for i in range(len(runs))]
+    states = [read_state(s, runs, i) for i in range(len(runs))] if keep_states else None
     return dict(solver=s, ms=ms, clocks=clk, census=census, states=states, E=E, O=O, desc=desc,
                 step_ms_median=statistics.median(per), step_ms_min=per[0])
 
@@ -357,13 +363,18 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
             "share": tms / total, "avg_launch_ms": per_launch_ms,
             "traffic": captured_traffic(w.get("name", ""), prec, name), "algorithmic_bytes": bytes_}
     if prec == "fp64":
-        peak_flops = N_SM * FP64_FLOP_PER_SM_CLK * peaks["sm_max_mhz"] * 1e6
+        if peaks.get("fp64_flops"):
+            peak_flops = peaks["fp64_flops"]
+            src = ("measured: ns_alu_peak, independent FP64 FMA chains on every SM, CUDA events, "
+                   "in this run")
+        else:
+            peak_flops = N_SM * FP64_FLOP_PER_SM_CLK * peaks["sm_max_mhz"] * 1e6
+            src = "FP64 FMA pipes x max SM clock (derived)"
         tflops = flops / (per_launch_ms * 1e-3) / 1e12
         alu_frac = tflops * 1e12 / peak_flops
         if alu_frac >= hbm_frac:
             roof.update(bound="alu", achieved=tflops, peak=peak_flops / 1e12, unit="TFLOP/s",
-                        frac=alu_frac, peak_source="FP64 FMA pipes x max SM clock (derived)",
-                        hbm_frac=hbm_frac)
+                        frac=alu_frac, peak_source=src, hbm_frac=hbm_frac)
             return roof, total
     roof.update(bound="hbm", achieved=gbs, peak=peaks["hbm_gbs"], unit="GB/s", frac=hbm_frac,
                 peak_source=peaks["source"])
@@ -473,19 +484,21 @@ def cufft_reference(u, uh, back, reps, model):
 def e2e(w, prec, mem, steps):
     """Through the public API with host buffers: every step uploads every
     run's input state from pinned host memory (ns_set_states; ns_set_field per
-    run for MHD states), advances one RK2 step (ns_step) and reads every run's
-    energy, enstrophy and spectrum back (ns_energy_spectra)."""
+    run for MHD states), advances one RK2 step (ns_step), reads every run's
+    energy, enstrophy and spectrum back (ns_energy_spectra) and reads every
+    run's advanced state back into pinned host memory (ns_get_state, or
+    ns_get_field per field for MHD states)."""
     import numpy as np
     import torch
 
-    from paper_1003_4322_gb300 import _native as nat
     from paper_1003_4322_gb300.solver import Solver
     runs, ics = mem
-    hosts = []
+    hosts, outs = [], []
     for a0 in ics:
         pinned = torch.empty(a0.shape, dtype=torch.complex128, pin_memory=True)
         pinned.numpy()[...] = a0
         hosts.append(pinned.numpy())
+        outs.append(torch.empty(a0.shape, dtype=torch.complex128, pin_memory=True).numpy())
     s = Solver(runs, prec=prec, stream=torch.cuda.current_stream())
     nr = len(runs)
 
@@ -499,6 +512,10 @@ def e2e(w, prec, mem, steps):
             s.set_states(hosts)
         s.step(1)
         E, O, spec = s.energy_spectra()   # every run's diagnostics in one round trip
+        for i, o in enumerate(outs):
+            s.get_field(0, run=i, out=o[:3])
+            if o.shape[0] == 6:
+                s.get_field(1, run=i, out=o[3:])
         return [E, O, spec]
     try:
         for _ in range(2):
@@ -511,15 +528,19 @@ def e2e(w, prec, mem, steps):
         dt = time.perf_counter() - t0
     finally:
         s.close()
+    if not all(np.isfinite(o).all() for o in outs[:1]):
+        raise RuntimeError("e2e: the state read back is not finite")
     return {"value": nr * steps / dt, "unit": "run-steps/s" if nr > 1 else "steps/s",
             "h2d_bytes_per_step": int(sum(h.nbytes for h in hosts)),
-            "d2h_bytes_per_step": int(sum(x.nbytes for x in specs)), "steps": steps}
+            "d2h_bytes_per_step": int(sum(x.nbytes for x in specs) + sum(o.nbytes for o in outs)),
+            "steps": steps}
 
 
-def oracle_steps(mem, budget_s, max_steps, warmup=0):
+def oracle_steps(mem, budget_s, max_steps, warmup=0, warm_budget_s=None):
     """Whole RK2 steps of the oracle (as it stands) over the workload's runs,
     cycling through the members: `warmup` untimed steps (fewer if they use
-    the time budget), then timed steps until max_steps or the budget.
+    warm_budget_s, by default budget_s), then timed steps until max_steps or
+    the budget (at least one of each kind asked for).
     Returns (timed steps, their seconds, threads, warm-up steps done)."""
     import oracle
     cores = oracle.set_threads(os.cpu_count() or 1)
@@ -540,7 +561,8 @@ def oracle_steps(mem, budget_s, max_steps, warmup=0):
 
     tw = time.perf_counter()
     warm = 0
-    while warm < warmup and time.perf_counter() - tw <= budget_s:
+    wb = budget_s if warm_budget_s is None else warm_budget_s
+    while warm < warmup and time.perf_counter() - tw <= wb:
         one()
         warm += 1
     t0 = time.perf_counter()
@@ -555,8 +577,11 @@ def oracle_steps(mem, budget_s, max_steps, warmup=0):
 
 def cpu_baseline(w, mem, budget_s=30.0):
     """The FP64 oracle (test infrastructure, as it stands) on the host cores:
-    whole RK2 steps of the same workload until the time budget is used."""
-    steps, dt, cores, warm = oracle_steps(mem, budget_s, 1000, warmup=1)
+    whole RK2 steps of the same workload until the time budget is used (at
+    least one; after one untimed step when the grid is small enough that a
+    step takes well under the budget)."""
+    big = max(math.prod(dims_of(r)) for r in mem[0]) >= 256 ** 3
+    steps, dt, cores, warm = oracle_steps(mem, budget_s, 1000, warmup=0 if big else 1)
     nr = len(mem[0])
     unit = "run-steps/s" if nr > 1 else "steps/s"
     return {"value": steps / dt, "unit": unit, "cores": cores, "kind": "oracle",
@@ -580,6 +605,66 @@ def job_rate(units_per_rank, world, ms):
     return world * units_per_rank / (ms * 1e-3)
 
 
+def config_of(args, w, world):
+    """The workload block both arms print, identical for the same command."""
+    return {"workload": args.workload, "description": w["desc"], "n": w["n"],
+            "grid": list(dims_of(w)), "box_over_2pi": [w.get(k, 1.0) for k in ("lx", "ly", "lz")],
+            "dealias": w.get("dealias", 0), "nu": w.get("nu"), "dt": w["dt"],
+            "runs": w.get("ensemble", 1), "parallelism": f"replicas x{world}",
+            "l2": "working set above 129 MB L2 (no flush needed)"}
+
+
+def measure_alu_peaks(peaks):
+    """FP64 (and FP32) FMA rate of this device, with the SM clock sampled
+    while the FP64 probe runs; the FP64 rate becomes the plain form's roof."""
+    import torch
+
+    from paper_1003_4322_gb300 import _native as nat
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    fp64 = nat.ns_alu_peak(nat.NS_FP64, 400.0, torch.cuda.current_stream())
+    clk = clocks.stop()
+    fp32 = nat.ns_alu_peak(nat.NS_FP32, 200.0, torch.cuda.current_stream())
+    peaks["fp64_flops"] = fp64
+    sm = (clk or {}).get("sm_mhz")
+    return {"fp64_tflops": fp64 / 1e12, "fp32_tflops": fp32 / 1e12,
+            "fp64_fma_per_sm_per_clk": fp64 / 2 / (N_SM * sm * 1e6) if sm else None,
+            "clocks": clk, "how": "ns_alu_peak: 8 independent FMA chains per thread, every SM "
+                                  "filled to its occupancy limit, best of 3 launches (CUDA events)"}
+
+
+def large_form(args, peaks, dist):
+    """The large configuration beside the headline: 1024^3 forced turbulence
+    in the fused FP32 form (steps/s, roofline, e2e, FFT stage at 1024^3) and
+    the plain FP64 form at 768^3 for comparison."""
+    out = {}
+    w = dict(WORKLOADS["forced1024"], name="forced1024")
+    mem = members(w)
+    steps = min(args.steps, 20)
+    t = time_form(w, "fp32", mem, steps, 3, 2, dist, keep_states=False)
+    roof, _ = roofline_of(t["census"], w, "fp32", 2, peaks, None, [dims_of(w)])
+    t["solver"].close()
+    out["forced1024_fp32"] = {
+        "description": w["desc"], "value": steps / (t["ms"] * 1e-3), "unit": "steps/s",
+        "ms_per_step": t["ms"] / steps, "steps": steps, "warmup": 3, "roofline": roof,
+        "execution": t["desc"], "clocks": t["clocks"],
+        "kernels": [{"name": n, "launches": l, "ms": ms} for n, l, ms in t["census"]],
+        "e2e": e2e(w, "fp32", mem, min(steps, 10))}
+    if not args.no_fft:
+        out["fft_1024"] = fft_stage(1024, "fp32")
+    del mem
+    w = dict(WORKLOADS["plain768"], name="plain768")
+    mem = members(w)
+    steps = min(args.steps, 5)
+    t = time_form(w, "fp64", mem, steps, 3, 1, dist, keep_states=False)
+    roof, _ = roofline_of(t["census"], w, "fp64", 1, peaks, None, [dims_of(w)])
+    t["solver"].close()
+    out["plain768_fp64"] = {"description": w["desc"], "value": steps / (t["ms"] * 1e-3),
+                            "unit": "steps/s", "ms_per_step": t["ms"] / steps, "steps": steps,
+                            "warmup": 3, "roofline": roof, "clocks": t["clocks"]}
+    return out
+
+
 def ours(args, w):
     import numpy as np
     import torch
@@ -596,6 +681,7 @@ def ours(args, w):
     torch.cuda.set_device(local)
     nat.load()
     peaks = load_peaks()
+    alu = measure_alu_peaks(peaks)
     mem = members(w)
     nr = len(mem[0])
     warmup = max(args.warmup, 3)
@@ -623,12 +709,14 @@ def ours(args, w):
                 "unit": "run-steps/s" if nr > 1 else "steps/s", "ms_per_step": c["ms"] / args.steps,
                 "rel_l2_fp32_vs_fp64": max(rel_l2(a, b) for a, b in zip(fp32, fp64)),
                 "after_steps": warmup + args.steps + census_steps, "roofline": croof,
-                "execution": c["desc"],
+                "execution": c["desc"], "clocks": c["clocks"],
                 "kernels": [{"name": n, "launches": l, "ms": t} for n, l, t in c["census"]]}
         c["solver"].close()
+    main["states"] = None
 
     fft = fft_stage(dims_of(w) if "ny" in w else w["n"], "fp32") if not args.no_fft else None
     ee = e2e(w, w["prec"], mem, min(args.steps, 20))
+    large = large_form(args, peaks, dist) if w.get("large") and not args.no_large else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, mem, args.cpu_budget)
@@ -645,20 +733,15 @@ def ours(args, w):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if w["prec"] == "fp64" else "f32",
         "data": "synthetic (analytic / seeded initial condition, no dataset)",
-        "config": {"workload": args.workload, "description": w["desc"], "n": w["n"],
-                   "grid": list(dims_of(w)), "box_over_2pi": [w.get(k, 1.0) for k in ("lx", "ly", "lz")],
-                   "dealias": w.get("dealias", 0),
-                   "nu": w.get("nu"), "dt": w["dt"], "form": main["desc"]["form"],
-                   "parallelism": f"replicas x{world}",
-                   "l2": "working set above 129 MB L2 (no flush needed)",
-                   "execution": main["desc"]},
+        "config": config_of(args, w, world),
+        "form": main["desc"]["form"], "execution": main["desc"],
         "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
-        "e2e": ee, "cpu_baseline": cpu, "clocks": clk or None,
+        "e2e": ee, "cpu_baseline": cpu, "clocks": clk or None, "alu_peaks": alu,
         "kernels": [{"name": n, "launches": l, "ms": t} for n, l, t in main["census"]],
         "series": {"at_step": [i + 1 + warmup for i in step_idx],
                    "energy": [float(main["E"][i]) for i in step_idx],
                    "enstrophy": [float(main["O"][i]) for i in step_idx]},
-        "companion": comp, "fft": fft,
+        "companion": comp, "fft": fft, "large": large,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -672,7 +755,8 @@ def reference(args, w):
     if rank != 0:
         return
     mem = members(w)
-    steps, dt, cores, warm = oracle_steps(mem, args.cpu_budget * 4, args.steps, args.warmup)
+    steps, dt, cores, warm = oracle_steps(mem, args.cpu_budget * 4, args.steps, args.warmup,
+                                          warm_budget_s=args.cpu_budget)
     v = steps / dt
     unit = "run-steps/s" if len(mem[0]) > 1 else "steps/s"
     what = (f"members of the {len(mem[0])}-run ensemble (in turn)" if len(mem[0]) > 1 else
@@ -681,11 +765,12 @@ def reference(args, w):
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": steps, "warmup": warm,
             "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": w["desc"], "n": w["n"]},
+            "config": config_of(args, w, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
                              "sample": f"{steps} of {args.steps} RK2 steps of {what} "
-                                       f"after {warm} untimed (each phase bounded to "
-                                       f"{args.cpu_budget * 4:.0f} s)"},
+                                       f"after {warm} untimed (warm-up bounded to "
+                                       f"{args.cpu_budget:.0f} s, timed steps to "
+                                       f"{args.cpu_budget * 4:.0f} s; at least one of each)"},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -694,9 +779,11 @@ def reference(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="tg256", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="forced512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 1024^3 / 768^3 forms that ride along with forced512")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-companion", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
