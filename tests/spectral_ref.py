@@ -195,3 +195,76 @@ def triad_mhd(a_half: np.ndarray, dealias: int = 0):
     nu[~nz] = 0
     nb = 1j * np.cross(Kf, _triad_cross(U, B, K, n))
     return np.concatenate([_to_half(nu, K, a_half[:3]), _to_half(nb, K, a_half[3:])])
+
+
+def _shell_of_half(nx: int, ny: int, nz: int):
+    """Shell index round-half-up(|k|) and the cube-rule kept mask of every
+    half-layout mode, (N_x, N_y, N_z/2+1) arrays."""
+    kx = wavenumbers(nx)[:, None, None].astype(np.float64)
+    ky = wavenumbers(ny)[None, :, None].astype(np.float64)
+    kz = np.arange(nz // 2 + 1, dtype=np.float64)[None, None, :]
+    shell = np.floor(np.sqrt(kx * kx + ky * ky + kz * kz) + 0.5).astype(np.int64)
+    keep = (3 * np.abs(kx) < nx) & (3 * np.abs(ky) < ny) & (3 * kz < nz)
+    return shell, keep
+
+
+def shell_error_ratios(test: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    """Per-shell error bound of an FP32 state against its FP64 reference:
+    for every shell K (round-half-up |k|) with kept modes,
+        err_K / sqrt(E_K + (n_K / n) E),
+    where err_K^2 and E_K are the weighted sums of |test - ref|^2 and |ref|^2
+    over the shell, E the sum over all modes, and n_K / n the shell's share of
+    the kept modes (multiplicity-weighted).  A bound tol on every ratio admits
+    the two errors FP32 arithmetic makes -- rounding proportional to each
+    mode's own amplitude, and transform noise spread evenly over the modes --
+    but not an error confined to a few shells, which the global relative L2
+    distance misses when those shells hold little energy."""
+    nx, ny, nz = _dims(ref)
+    shell, keep = _shell_of_half(nx, ny, nz)
+    w = np.broadcast_to(half_weights(nz)[None, None, :], shell.shape)
+    d2 = (w * np.sum(np.abs(test - ref) ** 2, axis=0))[keep]
+    r2 = (w * np.sum(np.abs(ref) ** 2, axis=0))[keep]
+    s = shell[keep]
+    nb = int(s.max()) + 1
+    err = np.bincount(s, weights=d2, minlength=nb)
+    ek = np.bincount(s, weights=r2, minlength=nb)
+    nk = np.bincount(s, weights=w[keep], minlength=nb)
+    has = nk > 0
+    return np.sqrt(err[has] / (ek[has] + nk[has] / nk.sum() * ek.sum()))
+
+
+def shell_error_ratios_device(got, ref, planes: int = 32):
+    """shell_error_ratios of two device half-layout states (torch complex
+    tensors [3][N_x][N_y][N_z/2+1]), accumulated in FP64 over slabs of x
+    planes, so that 1024^3 states need no host copy."""
+    import torch
+    nx, ny, nzh = ref.shape[-3:]
+    nz = 2 * (nzh - 1)
+    dev = ref.device
+    ky = torch.as_tensor(wavenumbers(ny), dtype=torch.float64, device=dev)[None, :, None]
+    kz = torch.arange(nzh, dtype=torch.float64, device=dev)[None, None, :]
+    wz = torch.as_tensor(half_weights(nz), dtype=torch.float64, device=dev)[None, None, :]
+    kxs = torch.as_tensor(wavenumbers(nx), dtype=torch.float64, device=dev)
+    nb = int(math.floor(math.sqrt(3) * (nx // 2) + 0.5)) + 2
+    err = torch.zeros(nb, dtype=torch.float64, device=dev)
+    ek = torch.zeros_like(err)
+    nk = torch.zeros_like(err)
+    for x0 in range(0, nx, planes):
+        kx = kxs[x0:x0 + planes][:, None, None]
+        k2 = kx * kx + ky * ky + kz * kz
+        shell = torch.floor(torch.sqrt(k2) + 0.5).long()
+        keep = (3 * kx.abs() < nx) & (3 * ky.abs() < ny) & (3 * kz < nz)
+        w = wz.expand(shell.shape)
+        d2 = torch.zeros(shell.shape, dtype=torch.float64, device=dev)
+        r2 = torch.zeros_like(d2)
+        for c in range(ref.shape[0]):
+            d2 += (got[c, x0:x0 + planes].to(torch.complex128)
+                   - ref[c, x0:x0 + planes].to(torch.complex128)).abs().square()
+            r2 += ref[c, x0:x0 + planes].to(torch.complex128).abs().square()
+        s = shell[keep]
+        err += torch.bincount(s, weights=(w * d2)[keep], minlength=nb)[:nb]
+        ek += torch.bincount(s, weights=(w * r2)[keep], minlength=nb)[:nb]
+        nk += torch.bincount(s, weights=w[keep], minlength=nb)[:nb]
+    has = nk > 0
+    r = torch.sqrt(err[has] / (ek[has] + nk[has] / nk.sum() * ek.sum()))
+    return r.cpu().numpy()

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_1003_4322_gb300 import inputs
-from tests.spectral_ref import helical_mode, rel_l2, wavenumbers
+from tests.spectral_ref import helical_mode, rel_l2, shell_error_ratios, wavenumbers
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +41,8 @@ def test_config1_32cubed_ten_steps(ns, prec):
         s.step(10)
         got = s.get_state()
     assert rel_l2(got, ref) < TOL[prec]
+    if prec == "fp32":
+        assert shell_error_ratios(got, ref).max() < TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -58,6 +60,8 @@ def test_sizes_dealias_forcing(ns, prec, n, dealias, forced):
         s.step(steps)
         got = s.get_state()
     assert rel_l2(got, ref) < TOL[prec]
+    if prec == "fp32":
+        assert shell_error_ratios(got, ref).max() < TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
