@@ -43,6 +43,31 @@ template <typename C> NSK_DEV C cmulc(C a, C b) {
 template <int S, typename C> NSK_DEV C cmul_i(C a) {
     return S > 0 ? mkc(-a.y, a.x) : mkc(a.y, -a.x);
 }
+// a + S i b for S = +1 / -1 (one addition per part, no separate swap).
+template <int S, typename C> NSK_DEV C cadd_i(C a, C b) {
+    return S > 0 ? mkc(a.x - b.y, a.y + b.x) : mkc(a.x + b.y, a.y - b.x);
+}
+
+// Even/odd packing of a real transform of N points as a complex one of
+// n = N/2 (w = W^k = exp(-2 pi i k / N)).  With f = a + b and g = a - b of
+// the two modes k and n - k (four additions for both formulas):
+//  c2r: Z[k] = (X[k] + conj X[n-k]) + i conj(w) (X[k] - conj X[n-k])
+//       = (f.x, g.y) + i conj(w) (g.x, f.y);
+//  r2c: X[k] = (Z[k] + conj Z[n-k]) / 2 - i w (Z[k] - conj Z[n-k]) / 2
+//       = ((f.x, g.y) + w (f.y, -g.x)) / 2,
+// ten arithmetic instructions per mode for r2c where the expanded form takes
+// fourteen.  The plain form's z passes use them; the FP32 kernels of the
+// fused form keep their own expressions, which suit their register budgets.
+template <typename C> NSK_DEV C c2r_pack(C xk, C xm, C w) {
+    const C f = cadd(xk, xm), g = csub(xk, xm);
+    const auto bx = g.x * w.x + f.y * w.y, by = f.y * w.x - g.x * w.y;
+    return mkc(f.x - by, g.y + bx);
+}
+template <typename C> NSK_DEV C r2c_unpack(C zk, C zm, C w) {
+    typedef decltype(zk.x) T;
+    const C f = cadd(zk, zm), g = csub(zk, zm);
+    return cscale(mkc(f.x + f.y * w.x + g.x * w.y, g.y + f.y * w.y - g.x * w.x), (T)0.5);
+}
 template <typename C> NSK_DEV C czero() { C z; z.x = 0; z.y = 0; return z; }
 
 // cos and sin of 2 pi key / 288 for the angles the register butterflies use
@@ -130,22 +155,22 @@ template <int DIR, typename C> struct Dft<3, DIR, C> {
         typedef decltype(a[0].x) T;
         const T h = (T)0.8660254037844386;  // sqrt(3)/2
         C t1 = cadd(a[1], a[2]);
-        C t2 = csub(a[0], cscale(t1, (T)0.5));
-        C t3 = cmul_i<DIR>(cscale(csub(a[1], a[2]), h));
+        C t2 = csub(a[0], cscale(t1, (T)0.5));   // 0.5 t1 is exact
+        C t3 = cscale(csub(a[1], a[2]), h);
         a[0] = cadd(a[0], t1);
-        a[1] = cadd(t2, t3);
-        a[2] = csub(t2, t3);
+        a[1] = cadd_i<DIR>(t2, t3);
+        a[2] = cadd_i<-DIR>(t2, t3);
     }
 };
 
 template <int DIR, typename C> struct Dft<4, DIR, C> {
     static NSK_DEV void run(C *a) {
         C s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
-        C s13 = cadd(a[1], a[3]), d13 = cmul_i<DIR>(csub(a[1], a[3]));
+        C s13 = cadd(a[1], a[3]), d13 = csub(a[1], a[3]);
         a[0] = cadd(s02, s13);
         a[2] = csub(s02, s13);
-        a[1] = cadd(d02, d13);
-        a[3] = csub(d02, d13);
+        a[1] = cadd_i<DIR>(d02, d13);
+        a[3] = cadd_i<-DIR>(d02, d13);
     }
 };
 

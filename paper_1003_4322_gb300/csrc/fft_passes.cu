@@ -234,13 +234,8 @@ k_fft_z_r2c(const T *__restrict__ in, typename Cx<T>::type *__restrict__ out, in
     fft_line<E, -1, false, true, false>(pl, slot, tw, N, gl, sl, ss, ss);
     if (!valid) return;
     C *dst = out + line * (n + 1);
-    const T half = (T)0.5;
     for (int k = slot; k <= n; k += Tn) {
-        const C zk = sl(k == n ? 0 : k);
-        const C zc = cconj(sl(k == 0 ? 0 : n - k));
-        const C ev = cscale(cadd(zk, zc), half);
-        const C od = cmul_i<-1>(cscale(csub(zk, zc), half));  // (zk - zc) / (2i)
-        dst[k] = cadd(ev, cmul(od, ldg_c(tw + k)));
+        dst[k] = r2c_unpack(sl(k == n ? 0 : k), sl(k == 0 ? 0 : n - k), ldg_c(tw + k));
     }
 }
 
@@ -264,18 +259,16 @@ k_fft_z_c2r(const typename Cx<T>::type *__restrict__ in, T *__restrict__ out, in
     auto ss = [&](int e, C v) { ls[e + (e >> sh)] = v; };
     const C *src = in + line * (n + 1);
     for (int k = slot; k < n; k += Tn) {
-        C xk = czero<C>(), xc = czero<C>();
+        C xk = czero<C>(), xm = czero<C>();
         if (valid) {
             xk = src[k];
-            xc = cconj(src[n - k]);
+            xm = src[n - k];
             if (k == 0) {
                 xk.y = 0;
-                xc.y = 0;
+                xm.y = 0;
             }
         }
-        const C a = cadd(xk, xc);
-        const C wb = cmulc(csub(xk, xc), ldg_c(tw + k));  // W^{-k} (X[k] - conj X[n-k])
-        ss(k, cadd(a, cmul_i<1>(wb)));
+        ss(k, c2r_pack(xk, xm, ldg_c(tw + k)));
     }
     __syncthreads();
     C *dst = reinterpret_cast<C *>(out + line * N);
