@@ -95,6 +95,11 @@ NSK_DEV float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
+// A warp owns a group of LPW lines at a time and walks the groups
+// warp * WPB * gridDim.x apart (the launch sizes the grid to what is
+// resident at once); the first field of its next group is loaded while the
+// current group's last three transforms run, so only a warp's first group
+// waits for its loads.
 template <int N, int E, int WPB, int PARK>
 __global__ void __launch_bounds__(32 * WPB)
 k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restrict__ tw) {
@@ -106,8 +111,11 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ll = lane / T, slot = lane % T;
     const int partner = ll * T + (T - slot) % T;   // holds position n - k of this line
-    const long line = ((long)blockIdx.x * WPB + warp) * LPW + ll;
-    const bool valid = line < nlines;
+    const long ngroups = (nlines + LPW - 1) / LPW;
+    const long gstride = (long)gridDim.x * WPB;
+    long group = (long)blockIdx.x * WPB + warp;   // warp-uniform
+    long line = group * LPW + ll;
+    bool valid = line < nlines;
     float2 *L = sm + (long)(warp * LPW + ll) * LS;
     float2 *park0 = sm + (long)WPB * LPW * LS + (long)warp * PARK * E * 32 + lane;   // u_x
     float2 *park1 = park0 + E * 32;                                                   // u_y
@@ -121,18 +129,20 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     for (int j = 0; j < E; j++) wk[j] = __ldg(tw + slot + j * T);
 
     float2 x[E];   // X[k], k = slot + j T, of the field being loaded
-    auto fetch = [&](int f) {
-        const float2 *src = buf + f * fs + line * Mz;
+    auto fetch_at = [&](int f, long ln, bool ok) {
+        const float2 *src = buf + f * fs + ln * Mz;
 #pragma unroll
         for (int j = 0; j < E; j++) {
             const int k = slot + j * T;
             x[j] = make_float2(0.f, 0.f);
-            if (j * T < Mz && valid && k < Mz) x[j] = src[k];
+            if (j * T < Mz && ok && k < Mz) x[j] = src[k];
         }
     };
+    auto fetch = [&](int f) { fetch_at(f, line, valid); };
     // c2r: Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]) with
     // the imaginary parts of X[0] and X[n] dropped, then the inverse length-n
     // FFT; complex element m of the result holds the real points 2m, 2m + 1.
+    // fnext: the field to load next (-1 none, -2 field 0 of the next group).
     auto inverse = [&](float2 (&v)[E], int fnext) {
 #pragma unroll
         for (int j = 0; j < E; j++) {
@@ -150,6 +160,10 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
             v[j] = cadd(cadd(a0, xc), cmul_i<1>(wb));
         }
         if (fnext >= 0) fetch(fnext);
+        if (fnext == -2) {
+            const long nl = (group + gstride) * LPW + ll;
+            fetch_at(0, nl, group + gstride < ngroups && nl < nlines);
+        }
         ct_fft_reg<n, E, +1, N>(v, slot, twr, sl, ss);
     };
     // r2c of a product held as Z[m] = x[2m] + i x[2m+1]: forward length-n FFT,
@@ -178,6 +192,7 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     // loaded itself, and its loads of a field precede its stores to it.
     float2 A[E], B[E], C[E], D[E], P[E];
     fetch(0);
+    for (; group < ngroups; group += gstride) {
     inverse(A, 4);   // u_x
     if constexpr (PARK >= 1) {
 #pragma unroll
@@ -205,7 +220,7 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
         px[j] = pmul(P[j], B[j]);   // u_z w_y (subtracted below)
         py[j] = pmul(P[j], D[j]);   // u_z w_x
     }
-    inverse(B, -1);  // w_z
+    inverse(B, -2);  // w_z; the next group's u_x starts loading
 #pragma unroll
     for (int j = 0; j < E; j++) {
         const float2 a = PARK >= 1 ? park0[j * 32] : A[j];
@@ -216,6 +231,9 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     }
     forward_store(px, 0);
     forward_store(py, 1);
+    line += gstride * LPW;
+    valid = line < nlines;
+    }
 }
 
 // Pass C of the MHD form (Alfven units): the group's B buffers form two
