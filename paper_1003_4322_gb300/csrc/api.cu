@@ -410,8 +410,12 @@ static void plain_cache_read(std::map<std::pair<int, int>, PlainPlans> &cache) {
     int n, b, ei, ci, ef, cf, ec, er;
     while (fscanf(fp, "%d %d %d %d %d %d %d %d", &n, &b, &ei, &ci, &ef, &cf, &ec, &er) == 8) {
         PlainPlans q;
-        if (make_plan_e(n, ei, &q.inv) && make_plan_e(n, ef, &q.fwd) && make_plan_e(n / 2, ec, &q.zc) &&
-            make_plan_e(n / 2, er, &q.zr) && ci > 0 && cf > 0) {
+        // z plans: E, or E + 100 for a plan of length n (two lines per transform)
+        auto zplan = [&](int code, Plan *pl) {
+            return code >= 100 ? make_plan_e(n, code - 100, pl) : make_plan_e(n / 2, code, pl);
+        };
+        if (make_plan_e(n, ei, &q.inv) && make_plan_e(n, ef, &q.fwd) && zplan(ec, &q.zc) &&
+            zplan(er, &q.zr) && ci > 0 && cf > 0) {
             q.ct_inv = ci;
             q.ct_fwd = cf;
             q.tuned = true;
@@ -427,10 +431,19 @@ static void plain_cache_write(const std::map<std::pair<int, int>, PlainPlans> &c
     if (!fp) return;
     for (const auto &kv : cache) {
         const PlainPlans &q = kv.second;
-        fprintf(fp, "%d %d %d %d %d %d %d %d\n", kv.first.first, kv.first.second, q.inv.E, q.ct_inv,
-                q.fwd.E, q.ct_fwd, q.zc.E, q.zr.E);
+        const int n = kv.first.first;
+        fprintf(fp, "%d %d %d %d %d %d %d %d\n", n, kv.first.second, q.inv.E, q.ct_inv, q.fwd.E, q.ct_fwd,
+                q.zc.E + (q.zc.n == n ? 100 : 0), q.zr.E + (q.zr.n == n ? 100 : 0));
     }
     fclose(fp);
+}
+
+// Diagnostic restriction of the plain form's z-pass candidates,
+// NS_PLAIN_Z=1 (one line per transform) or 2 (two lines per transform); with
+// it set, tuning bypasses the plan caches.
+static int plain_z_mode() {
+    const char *v = getenv("NS_PLAIN_Z");
+    return v && (v[0] == '1' || v[0] == '2') ? v[0] - '0' : 0;
 }
 
 template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
@@ -439,7 +452,8 @@ template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
     static std::map<std::pair<int, int>, PlainPlans> cache;
     static bool loaded = false;
     const std::pair<int, int> key(r.n, (int)sizeof(T));
-    {
+    const int zmode = plain_z_mode();
+    if (!zmode) {
         std::lock_guard<std::mutex> g(mu);
         if (!loaded) {
             plain_cache_read(cache);
@@ -451,7 +465,7 @@ template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
             return NS_OK;
         }
     }
-    if (f->pp.tuned) return NS_OK;
+    if (f->pp.tuned && !zmode) return NS_OK;
     const int n = r.n;
     const long nh = n / 2 + 1, plane = (long)n * nh, M = (long)n * plane, lines = 3L * n * n;
     const C *tw = (const C *)f->tw;
@@ -478,8 +492,12 @@ template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
                 if (tf > 0.f && (bf < 0.f || tf < bf)) { bf = tf; best.fwd = pl; best.ct_fwd = ct; }
             }
         }
-        Plan ph;
-        if (make_plan_e(n / 2, E, &ph) && ph.nst <= 4) {
+        // z passes: one line per transform of length n/2 (even/odd packing), or
+        // two lines per transform of length n
+        for (int len : {n / 2, n}) {
+            Plan ph;
+            if ((zmode == 1 && len == n) || (zmode == 2 && len != n)) continue;
+            if (!make_plan_e(len, E, &ph) || ph.nst > 4) continue;
             const float tc = plain_time([&]() { return fft_z_c2r<T>(tmp, phys, n, lines, ph, tw, s); }, s);
             if (tc > 0.f && (bc < 0.f || tc < bc)) { bc = tc; best.zc = ph; }
             const float tr = plain_time([&]() { return fft_z_r2c<T>(phys, half, n, lines, ph, tw, s); }, s);
@@ -489,6 +507,7 @@ template <typename T> ns_status tune_plain(ns_ctx *c, Run &r, FftRes *f) {
     NS_CK(cudaStreamSynchronize(s));
     best.tuned = true;
     f->pp = best;
+    if (zmode) return NS_OK;
     std::lock_guard<std::mutex> g(mu);
     cache[key] = best;
     plain_cache_write(cache);
@@ -506,7 +525,8 @@ template <typename T> ns_status tune_plain_grid(ns_ctx *c, Run &r, FftRes *f[3])
     static std::map<std::tuple<int, int, int, int>, std::vector<PlainPlans>> cache;
     const Grid &g = r.g;
     const auto key = std::make_tuple(g.nx, g.ny, g.nz, (int)sizeof(T));
-    {
+    const int zmode = plain_z_mode();
+    if (!zmode) {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
         if (it != cache.end()) {
@@ -547,17 +567,20 @@ template <typename T> ns_status tune_plain_grid(ns_ctx *c, Run &r, FftRes *f[3])
         const C *tw = (const C *)f[2]->tw;
         PlainPlans &best = r.gp[2];
         float bc = -1.f, br = -1.f;
-        for (int E : Es) {
-            Plan ph;
-            if (!make_plan_e(g.nz / 2, E, &ph) || ph.nst > 4) continue;
-            const float tc = plain_time([&]() { return fft_z_c2r<T>(tmp, phys, g.nz, lines, ph, tw, s); }, s);
-            if (tc > 0.f && (bc < 0.f || tc < bc)) { bc = tc; best.zc = ph; }
-            const float tr = plain_time([&]() { return fft_z_r2c<T>(phys, half, g.nz, lines, ph, tw, s); }, s);
-            if (tr > 0.f && (br < 0.f || tr < br)) { br = tr; best.zr = ph; }
-        }
+        for (int E : Es)
+            for (int len : {g.nz / 2, g.nz}) {
+                Plan ph;
+                if ((zmode == 1 && len == g.nz) || (zmode == 2 && len != g.nz)) continue;
+                if (!make_plan_e(len, E, &ph) || ph.nst > 4) continue;
+                const float tc = plain_time([&]() { return fft_z_c2r<T>(tmp, phys, g.nz, lines, ph, tw, s); }, s);
+                if (tc > 0.f && (bc < 0.f || tc < bc)) { bc = tc; best.zc = ph; }
+                const float tr = plain_time([&]() { return fft_z_r2c<T>(phys, half, g.nz, lines, ph, tw, s); }, s);
+                if (tr > 0.f && (br < 0.f || tr < br)) { br = tr; best.zr = ph; }
+            }
     }
     NS_CK(cudaStreamSynchronize(s));
     for (int a = 0; a < 3; a++) r.gp[a].tuned = true;
+    if (zmode) return NS_OK;
     std::lock_guard<std::mutex> lk(mu);
     cache[key] = std::vector<PlainPlans>(r.gp, r.gp + 3);
     return NS_OK;
@@ -856,10 +879,11 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
                  "{\"form\": \"plain %s\", \"equations\": \"%s\", \"n\": %d, \"grid\": [%d, %d, %d], "
                  "\"box\": [%.17g, %.17g, %.17g], \"tuned\": %s, "
                  "\"xy_inverse\": {\"E\": %d, \"cols_per_cta\": %d}, \"xy_forward\": {\"E\": %d, "
-                 "\"cols_per_cta\": %d}, \"z_c2r\": {\"E\": %d}, \"z_r2c\": {\"E\": %d}}",
+                 "\"cols_per_cta\": %d}, \"z_c2r\": {\"E\": %d, \"lines_per_transform\": %d}, "
+                 "\"z_r2c\": {\"E\": %d, \"lines_per_transform\": %d}}",
                  c->prec == NS_FP64 ? "FP64" : "FP32", r.p.mhd ? "MHD" : "Navier-Stokes", r.n, r.g.nx, r.g.ny,
                  r.g.nz, r.g.lx, r.g.ly, r.g.lz, q.tuned ? "true" : "false", q.inv.E, q.ct_inv, q.fwd.E, q.ct_fwd,
-                 qz.zc.E, qz.zr.E);
+                 qz.zc.E, qz.zc.n == r.g.nz ? 2 : 1, qz.zr.E, qz.zr.n == r.g.nz ? 2 : 1);
     }
     return NS_OK;
 }

@@ -278,6 +278,95 @@ k_fft_z_c2r(const typename Cx<T>::type *__restrict__ in, T *__restrict__ out, in
     fft_line<E, +1, true, false, false>(pl, slot, tw, N, sl, sl, ss, gs);
 }
 
+// Two real lines through one complex transform of length N (the plan of
+// length N selects this form; one of length N/2 the packed form above).  Per
+// line pair the length-N transform costs 5N flops more than two of length
+// N/2 but needs no even/odd packing, which saves about 14 % of the
+// arithmetic instructions of c2r and 8 % of r2c.
+//  c2r: the spectra X1, X2 of lines 2p and 2p + 1 (the imaginary parts of
+//       X[0] and X[N/2] dropped) form Z[k] = X1[k] + i X2[k] for k <= N/2 and
+//       Z[k] = conj X1[N-k] + i conj X2[N-k] above, a Hermitian pair; the
+//       inverse transform of Z is x1 + i x2.
+//  r2c: the forward transform Z of x1 + i x2 gives
+//       X1[k] = (Z[k] + conj Z[N-k]) / 2 and X2[k] = (Z[k] - conj Z[N-k]) / 2i.
+// A missing second line (odd line count) reads as zero and is not written.
+template <typename T, int E>
+__global__ void __launch_bounds__(256)
+k_fft_z_r2c2(const T *__restrict__ in, typename Cx<T>::type *__restrict__ out, int N, long nlines,
+             Plan pl, const typename Cx<T>::type *__restrict__ tw) {
+    typedef typename Cx<T>::type C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nh = N / 2, Tn = N / E;
+    const int slot = threadIdx.x % Tn, li = threadIdx.x / Tn;
+    const int lb = blockDim.x / Tn;
+    const long l1 = 2 * ((long)blockIdx.x * lb + li), l2 = l1 + 1;
+    const bool v1 = l1 < nlines, v2 = l2 < nlines;
+    C *ls = reinterpret_cast<C *>(smraw) + li * skew_len<C>(N);
+    const int sh = Skew<C>::shift;
+    const T *s1 = in + l1 * N, *s2 = in + l2 * N;
+    auto gl = [&](int e) -> C { return mkc(v1 ? s1[e] : (T)0, v2 ? s2[e] : (T)0); };
+    auto sl = [&](int e) -> C { return ls[e + (e >> sh)]; };
+    auto ss = [&](int e, C v) { ls[e + (e >> sh)] = v; };
+    fft_line<E, -1, false, true, false>(pl, slot, tw, N, gl, sl, ss, ss);
+    C *d1 = out + l1 * (nh + 1), *d2 = out + l2 * (nh + 1);
+    const T half = (T)0.5;
+    for (int k = slot; k <= nh; k += Tn) {
+        const C a = sl(k), b = sl(k == 0 ? 0 : N - k);
+        if (v1) d1[k] = mkc((a.x + b.x) * half, (a.y - b.y) * half);
+        if (v2) d2[k] = mkc((a.y + b.y) * half, (b.x - a.x) * half);
+    }
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(256)
+k_fft_z_c2r2(const typename Cx<T>::type *__restrict__ in, T *__restrict__ out, int N, long nlines,
+             Plan pl, const typename Cx<T>::type *__restrict__ tw) {
+    typedef typename Cx<T>::type C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nh = N / 2, Tn = N / E;
+    const int slot = threadIdx.x % Tn, li = threadIdx.x / Tn;
+    const int lb = blockDim.x / Tn;
+    const long l1 = 2 * ((long)blockIdx.x * lb + li), l2 = l1 + 1;
+    const bool v1 = l1 < nlines, v2 = l2 < nlines;
+    C *ls = reinterpret_cast<C *>(smraw) + li * skew_len<C>(N);
+    const int sh = Skew<C>::shift;
+    auto sl = [&](int e) -> C { return ls[e + (e >> sh)]; };
+    auto ss = [&](int e, C v) { ls[e + (e >> sh)] = v; };
+    const C *s1 = in + l1 * (nh + 1), *s2 = in + l2 * (nh + 1);
+    for (int k = slot; k < N; k += Tn) {
+        const int m = k <= nh ? k : N - k;
+        C a = v1 ? s1[m] : czero<C>(), b = v2 ? s2[m] : czero<C>();
+        if (m == 0 || m == nh) {
+            a.y = 0;
+            b.y = 0;
+        }
+        ss(k, k <= nh ? mkc(a.x - b.y, a.y + b.x) : mkc(a.x + b.y, b.x - a.y));
+    }
+    __syncthreads();
+    T *d1 = out + l1 * N, *d2 = out + l2 * N;
+    auto gs = [&](int e, C v) {
+        if (v1) d1[e] = v.x;
+        if (v2) d2[e] = v.y;
+    };
+    fft_line<E, +1, true, false, false>(pl, slot, tw, N, sl, sl, ss, gs);
+}
+
+template <typename T, bool R2C>
+static const void *z_kernel2(int E) {
+#define NSK_ZK2(EE) \
+    return R2C ? (const void *)k_fft_z_r2c2<T, EE> : (const void *)k_fft_z_c2r2<T, EE>
+    switch (E) {
+    case 4: NSK_ZK2(4);
+    case 6: NSK_ZK2(6);
+    case 8: NSK_ZK2(8);
+    case 9: NSK_ZK2(9);
+    case 12: NSK_ZK2(12);
+    case 16: NSK_ZK2(16);
+    }
+#undef NSK_ZK2
+    return nullptr;
+}
+
 template <typename T, bool R2C>
 static const void *z_kernel(int E) {
 #define NSK_ZK(EE) \
@@ -294,19 +383,23 @@ static const void *z_kernel(int E) {
     return nullptr;
 }
 
+// pl.n == N / 2: one line per complex transform (even/odd packing);
+// pl.n == N: two lines per complex transform.
 template <typename T, bool R2C>
 static cudaError_t launch_z(const void *in, void *out, int N, long nlines, const Plan &pl,
                             const typename Cx<T>::type *tw, cudaStream_t s) {
     typedef typename Cx<T>::type C;
-    const void *k = z_kernel<T, R2C>(pl.E);
-    if (!k || pl.n * 2 != N || nlines < 1) return cudaErrorInvalidValue;
+    const bool paired = pl.n == N;
+    const void *k = paired ? z_kernel2<T, R2C>(pl.E) : z_kernel<T, R2C>(pl.E);
+    if (!k || (!paired && pl.n * 2 != N) || nlines < 1) return cudaErrorInvalidValue;
     const int Tn = pl.n / pl.E;
     int lb = 256 / Tn;
     if (lb < 1) return cudaErrorInvalidValue;
     const size_t smem = (size_t)lb * skew_len<C>(pl.n) * sizeof(C);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
-    const long blocks = (nlines + lb - 1) / lb;
+    const long units = paired ? (nlines + 1) / 2 : nlines;   // transforms
+    const long blocks = (units + lb - 1) / lb;
     if (blocks > 0x7fffffffL) return cudaErrorInvalidValue;
     Plan p = pl;
     void *args[] = {(void *)&in, (void *)&out, (void *)&N, (void *)&nlines, (void *)&p,
@@ -331,7 +424,9 @@ cudaError_t prepare_fft_kernels() {
         const void *ks[] = {strided_kernel<float, -1>(E), strided_kernel<float, 1>(E),
                             strided_kernel<double, -1>(E), strided_kernel<double, 1>(E),
                             z_kernel<float, true>(E), z_kernel<float, false>(E),
-                            z_kernel<double, true>(E), z_kernel<double, false>(E)};
+                            z_kernel<double, true>(E), z_kernel<double, false>(E),
+                            z_kernel2<float, true>(E), z_kernel2<float, false>(E),
+                            z_kernel2<double, true>(E), z_kernel2<double, false>(E)};
         for (const void *k : ks) {
             cudaError_t e = allow_smem(k, big);
             if (e != cudaSuccess) return e;
