@@ -7,6 +7,9 @@ runs; the long ones are opt-in in test_gpu_long.py):
   grid point), and in E and Omega;
 * the 48-run ensemble (16 runs each at 64^3, 96^3 and 128^3): two members of
   each size against the oracle, in both precisions;
+* 512^3 forced turbulence (the benchmark's headline configuration): one RK2
+  step of both forms against the oracle on the whole state (about a minute
+  of oracle time on the host cores);
 * 1024^3 forced turbulence: the fused FP32 form (its N = 1024 pass kernels)
   against the plain FP64 form after a few steps, on the whole state.
 
@@ -79,6 +82,29 @@ def test_config4_members_against_oracle(ns, prec):
         assert err < TOL[prec]
         if prec == "fp32":
             assert shell_error_ratios(got[i], ref).max() < TOL[prec]
+
+
+def test_forced512_one_step_against_oracle(ns):
+    """The 512^3 forced-turbulence configuration (nu = 2e-3, dt = 1e-3, ABC
+    forcing k = 3, F = 0.5, seeded k^-2 start on 1 <= |k| <= 4), one RK2 step
+    of the plain FP64 and the fused FP32 form against the oracle on the whole
+    state (about a minute of oracle time on the host cores)."""
+    from paper_1003_4322_gb300.solver import Solver
+    n = 512
+    run = dict(n=n, nu=2e-3, dt=1e-3, force_amp=0.5, force_k=3)
+    oracle.set_threads(os.cpu_count() or 1)
+    a0 = inputs.turbulence_state(n, seed=3)
+    ref = oracle.step(a0, oracle.Params(n=n, nu=2e-3, dt=1e-3, force_amp=0.5, force_k=3), 1)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-5)):
+        with Solver([run], prec=prec) as s:
+            s.set_state(a0)
+            s.step(1)
+            got = s.get_state()
+        err = rel_l2(got, ref)
+        print(f"512^3 {prec}: rel-L2 vs oracle after one step {err:.3e}")
+        assert err < tol
+        if prec == "fp32":
+            assert shell_error_ratios(got, ref).max() < tol
 
 
 def test_forced1024_fused_fp32_against_plain_fp64_short(ns):
