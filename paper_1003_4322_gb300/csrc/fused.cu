@@ -374,7 +374,10 @@ cudaError_t prepare_fused_kernels() {
                 }
             }
     const int zrEs[] = {16, 12, 8, 6, 4};
-    const int zrTiles[] = {1, 2, ZR_PARK + 1, ZR_PARK + 2, 2 * ZR_PARK + 1, 2 * ZR_PARK + 2};
+    int zrTiles[2 * 6];
+    for (int d = 0, k = 0; d < 2; d++)
+        for (int t : {1, 2, ZR_PARK + 1, ZR_PARK + 2, 2 * ZR_PARK + 1, 2 * ZR_PARK + 2})
+            zrTiles[k++] = d * ZR_ASYNC + t;   // depth 0 (registers), 2
     for (int N : Ns)
         for (int zE : zrEs)
             for (int tile : zrTiles) {
@@ -904,7 +907,10 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
             if (ms > 0.f) cands.push_back({ms, cfg});
         }
         const int zrEs[] = {16, 12, 8, 6, 4};
-        const int zrTiles[] = {1, 2, ZR_PARK + 1, ZR_PARK + 2, 2 * ZR_PARK + 1, 2 * ZR_PARK + 2};
+        int zrTiles[2 * 6];
+        for (int d = 0, k = 0; d < 2; d++)
+            for (int t : {1, 2, ZR_PARK + 1, ZR_PARK + 2, 2 * ZR_PARK + 1, 2 * ZR_PARK + 2})
+                zrTiles[k++] = d * ZR_ASYNC + t;   // depth 0 (registers), 2
         for (int zE : zrEs)
             for (int tile : zrTiles) {
                 ZctKernel z;
@@ -1184,8 +1190,9 @@ int fused_describe(const FusedRun &f, char *out, int len) {
     if (w < len && f.zc.kind == 2)
         w += snprintf(out + w, len - w,
                       "\"C_z_nonlinear\": {\"kernel\": \"register-resident\", \"E\": %d, "
-                      "\"warps_per_cta\": %d, \"parked_fields\": %d}}",
-                      f.zc.pl.E, f.zc.ct % ZR_PARK, f.zc.ct / ZR_PARK);
+                      "\"warps_per_cta\": %d, \"parked_fields\": %d, \"async_depth\": %d}}",
+                      f.zc.pl.E, (f.zc.ct % ZR_ASYNC) % ZR_PARK, (f.zc.ct % ZR_ASYNC) / ZR_PARK,
+                      f.zc.ct >= ZR_ASYNC ? f.zc.ct / ZR_ASYNC + 1 : 0);
     else if (w < len && f.zc.kind == 1)
         w += snprintf(out + w, len - w,
                       "\"C_z_nonlinear\": {\"kernel\": \"compile-time length\", \"E\": %d, "

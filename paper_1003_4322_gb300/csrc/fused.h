@@ -27,10 +27,13 @@ struct ZctKernel {
 // Kernel for grid size N, E elements per thread and wpb warps per CTA, if one
 // was compiled (E in {16, 8} or {12, 6}; wpb in {1, 2, 4}).
 bool zct_lookup(int N, int E, int wpb, ZctKernel *out);
-// Register-resident pass-C kernel (fused_zr.cuh, fused_zr2.cu, fused_zr3.cu):
-// tile = warps per CTA (1 or 2) + ZR_PARK x the number of fields parked in
-// shared memory (0, 1: u_x, 2: u_x and u_y).
+// Register-resident pass-C kernel (fused_zr.cuh, fused_zr2.cu, fused_zr3.cu,
+// fused_zr4.cu): tile = warps per CTA (1 or 2) + ZR_PARK x the number of
+// fields parked in shared memory (0, 1: u_x, 2: u_x and u_y), + ZR_ASYNC x
+// (depth - 1) for the form whose field loads are asynchronous copies depth
+// fields ahead (depth 2 is compiled).
 constexpr int ZR_PARK = 8;
+constexpr int ZR_ASYNC = 32;
 bool zr_lookup(int N, int E, int tile, ZctKernel *out);
 // Pass C of the MHD form (fused_zm.cu): E elements per thread, wpb warps per CTA.
 bool zrm_lookup(int N, int E, int wpb, ZctKernel *out);

@@ -91,6 +91,18 @@ template <int N, int E_> struct ZrShape {
 };
 
 NSK_DEV float2 pmul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+
+// Asynchronous 8-byte copy global -> shared (zero-filled when ok is false;
+// src is then not read), and the group commit / wait of such copies.
+NSK_DEV void cp_async8(float2 *dst, const float2 *src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 8 : 0)
+                 : "memory");
+}
+NSK_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING> NSK_DEV void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
 NSK_DEV float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
@@ -100,9 +112,17 @@ NSK_DEV float2 shfl2(float2 v, int src) {
 // resident at once); the first field of its next group is loaded while the
 // current group's last three transforms run, so only a warp's first group
 // waits for its loads.
-template <int N, int E, int WPB, int PARK>
+// DEPTH > 0: the fields are copied into DEPTH per-warp shared buffers by
+// asynchronous copies issued DEPTH fields ahead (the field order continues
+// into the next group), so a load has DEPTH transforms' time to land instead
+// of one, with no more registers; each thread copies and reads back only its
+// own elements.  DEPTH divides the six fields of a group (2 or 3), so a
+// field keeps its buffer from group to group.
+template <int N, int E, int WPB, int PARK, int DEPTH = 0>
 __global__ void __launch_bounds__(32 * WPB)
 k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restrict__ tw) {
+    static_assert(DEPTH == 0 || DEPTH == 2 || DEPTH == 3, "DEPTH divides 6");
+    constexpr bool ASYNC = DEPTH > 0;
     typedef ZrShape<N, E> Z;
     constexpr int n = Z::n, T = Z::T, LPW = Z::LPW, LS = Z::LS, Mz = Z::Mz;
     buf += blockIdx.y * brun;   // run of the group
@@ -119,6 +139,8 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     float2 *L = sm + (long)(warp * LPW + ll) * LS;
     float2 *park0 = sm + (long)WPB * LPW * LS + (long)warp * PARK * E * 32 + lane;   // u_x
     float2 *park1 = park0 + E * 32;                                                   // u_y
+    // ASYNC: [warp][DEPTH buffers][E][32 lanes] after the parked fields
+    float2 *pfb = sm + (long)WPB * LPW * LS + (long)WPB * PARK * E * 32 + (long)warp * DEPTH * E * 32 + lane;
     auto sl = [&](int e) -> float2 { return L[ct_skew(e)]; };
     auto ss = [&](int e, float2 v) { L[ct_skew(e)] = v; };
 
@@ -139,11 +161,41 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
         }
     };
     auto fetch = [&](int f) { fetch_at(f, line, valid); };
+    // ASYNC: field f of line ln into buffer b (one commit group), and the
+    // buffer's contents into x once all but the latest group have landed
+    auto issue_at = [&](int f, long ln, bool ok, int b) {
+        const float2 *src = buf + f * fs + (ok ? ln : 0) * Mz;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            if (j * T < Mz) cp_async8(pfb + (b * E + j) * 32, ok && k < Mz ? src + k : buf, ok && k < Mz);
+        }
+        cp_async_commit();
+    };
+    auto take = [&](int b) {
+        cp_async_wait<(DEPTH > 0 ? DEPTH - 1 : 0)>();
+#pragma unroll
+        for (int j = 0; j < E; j++) x[j] = j * T < Mz ? pfb[(b * E + j) * 32] : make_float2(0.f, 0.f);
+    };
+    // the field DEPTH places after position i of the order u_x, w_y, u_y, w_x,
+    // u_z, w_z (the last DEPTH positions reach into the next group), into the
+    // buffer position i has just freed
+    constexpr int kOrder[6] = {0, 4, 1, 3, 2, 5};
+    auto issue_ahead = [&](int i) {
+        if (i + DEPTH < 6) {
+            issue_at(kOrder[i + DEPTH], line, valid, i % DEPTH);
+        } else {
+            const long nl = (group + gstride) * LPW + ll;
+            issue_at(kOrder[i + DEPTH - 6], nl, group + gstride < ngroups && nl < nlines, i % DEPTH);
+        }
+    };
     // c2r: Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]) with
     // the imaginary parts of X[0] and X[n] dropped, then the inverse length-n
     // FFT; complex element m of the result holds the real points 2m, 2m + 1.
-    // fnext: the field to load next (-1 none, -2 field 0 of the next group).
-    auto inverse = [&](float2 (&v)[E], int fnext) {
+    // fnext: the field to load next (-1 none, -2 field 0 of the next group);
+    // ASYNC: pos, the position of this field in the order (buffer pos % DEPTH).
+    auto inverse = [&](float2 (&v)[E], int fnext, int pos) {
+        if constexpr (ASYNC) take(pos % (DEPTH > 0 ? DEPTH : 1));
 #pragma unroll
         for (int j = 0; j < E; j++) {
             const int k = slot + j * T;
@@ -159,10 +211,14 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
             const float2 wb = cmulc(csub(a0, xc), wk[j]);
             v[j] = cadd(cadd(a0, xc), cmul_i<1>(wb));
         }
-        if (fnext >= 0) fetch(fnext);
-        if (fnext == -2) {
-            const long nl = (group + gstride) * LPW + ll;
-            fetch_at(0, nl, group + gstride < ngroups && nl < nlines);
+        if constexpr (ASYNC) {
+            issue_ahead(pos);
+        } else {
+            if (fnext >= 0) fetch(fnext);
+            if (fnext == -2) {
+                const long nl = (group + gstride) * LPW + ll;
+                fetch_at(0, nl, group + gstride < ngroups && nl < nlines);
+            }
         }
         ct_fft_reg<n, E, +1, N>(v, slot, twr, sl, ss);
     };
@@ -191,36 +247,45 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     // most five field arrays are live.  A thread stores only positions it
     // loaded itself, and its loads of a field precede its stores to it.
     float2 A[E], B[E], C[E], D[E], P[E];
-    fetch(0);
+    if constexpr (ASYNC) {
+#pragma unroll
+        for (int i = 0; i < DEPTH; i++) issue_at(kOrder[i], line, valid, i);
+    } else {
+        fetch(0);
+    }
     for (; group < ngroups; group += gstride) {
-    inverse(A, 4);   // u_x
+    inverse(A, 4, 0);   // u_x
     if constexpr (PARK >= 1) {
 #pragma unroll
         for (int j = 0; j < E; j++) park0[j * 32] = A[j];
     }
-    inverse(B, 1);   // w_y
+    inverse(B, 1, 1);   // w_y
 #pragma unroll
     for (int j = 0; j < E; j++) P[j] = pmul(PARK >= 1 ? park0[j * 32] : A[j], B[j]);   // u_x w_y
-    inverse(C, 3);   // u_y
+    inverse(C, 3, 2);   // u_y
     if constexpr (PARK >= 2) {
 #pragma unroll
         for (int j = 0; j < E; j++) park1[j * 32] = C[j];
     }
-    inverse(D, 2);   // w_x
+    inverse(D, 2, 3);   // w_x
 #pragma unroll
     for (int j = 0; j < E; j++) {
         const float2 t = pmul(PARK >= 2 ? park1[j * 32] : C[j], D[j]);   // u_y w_x
         P[j] = make_float2(P[j].x - t.x, P[j].y - t.y);
     }
+    // ASYNC: the store over field 2 must not overtake the copy of u_z (field
+    // 2, position 4); groups complete in order, and the copies issued after it
+    // are those of positions 5 .. 3 + DEPTH
+    if constexpr (ASYNC) cp_async_wait<(DEPTH > 0 ? DEPTH - 2 : 0)>();
     forward_store(P, 2);
     float2 px[E], py[E];
-    inverse(P, 5);   // u_z
+    inverse(P, 5, 4);   // u_z
 #pragma unroll
     for (int j = 0; j < E; j++) {
         px[j] = pmul(P[j], B[j]);   // u_z w_y (subtracted below)
         py[j] = pmul(P[j], D[j]);   // u_z w_x
     }
-    inverse(B, -2);  // w_z; the next group's u_x starts loading
+    inverse(B, -2, 5);  // w_z; the next group's u_x starts loading
 #pragma unroll
     for (int j = 0; j < E; j++) {
         const float2 a = PARK >= 1 ? park0[j * 32] : A[j];
@@ -234,6 +299,7 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     line += gstride * LPW;
     valid = line < nlines;
     }
+    if constexpr (ASYNC) cp_async_wait<0>();   // no copy may land after the CTA exits
 }
 
 // Pass C of the MHD form (Alfven units): the group's B buffers form two
@@ -395,25 +461,29 @@ template <int N, int E, int WPB> bool zrm_entry(ZctKernel *o) {
     }
 }
 
-template <int N, int E, int WPB, int PARK> bool zr_entry(ZctKernel *o) {
+template <int N, int E, int WPB, int PARK, int DEPTH = 0> bool zr_entry(ZctKernel *o) {
     typedef ZrShape<N, E> Z;
     if constexpr (!Z::ok) {
         return false;
     } else {
-        o->k = (const void *)k_fused_zr<N, E, WPB, PARK>;
-        o->smem = (size_t)WPB * (Z::LPW * Z::LS + PARK * E * 32) * sizeof(float2);
+        o->k = (const void *)k_fused_zr<N, E, WPB, PARK, DEPTH>;
+        o->smem = (size_t)WPB * (Z::LPW * Z::LS + PARK * E * 32 + DEPTH * E * 32) * sizeof(float2);
         o->lines_per_block = WPB * Z::LPW;
         o->threads = 32 * WPB;
         return true;
     }
 }
 
-// tile = warps per CTA (1 or 2) + ZR_PARK x the number of parked fields.
-template <int N, int E, int PARK> bool zr_by_tile(int tile, ZctKernel *o) {
+// tile = warps per CTA (1 or 2) + ZR_PARK x the number of parked fields
+// + ZR_ASYNC x (depth - 1) for the asynchronous-copy form of depth 2 or 3.
+template <int N, int E, int PARK, int DEPTH = 0> bool zr_by_tile(int tile, ZctKernel *o) {
+    const int depth = tile / ZR_ASYNC ? tile / ZR_ASYNC + 1 : 0;
+    if (depth != DEPTH) return false;
+    tile %= ZR_ASYNC;
     if (tile / ZR_PARK != PARK) return false;
     switch (tile % ZR_PARK) {
-    case 1: return zr_entry<N, E, 1, PARK>(o);
-    case 2: return zr_entry<N, E, 2, PARK>(o);
+    case 1: return zr_entry<N, E, 1, PARK, DEPTH>(o);
+    case 2: return zr_entry<N, E, 2, PARK, DEPTH>(o);
     }
     return false;
 }
@@ -422,5 +492,7 @@ template <int N, int E, int PARK> bool zr_by_tile(int tile, ZctKernel *o) {
 // with a factor 3).
 bool zr_lookup2(int N, int E, int tile, ZctKernel *o);
 bool zr_lookup3(int N, int E, int tile, ZctKernel *o);
+// The asynchronous-copy form for powers of two (fused_zr4.cu).
+bool zr_lookup4(int N, int E, int tile, ZctKernel *o);
 
 }  // namespace nsk

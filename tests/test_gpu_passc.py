@@ -12,9 +12,11 @@ from tests.spectral_ref import rel_l2
 pytestmark = pytest.mark.gpu
 
 # (kind, E, tile) triples as the plan cache writes them: kind 2 =
-# register-resident (tile = warps per CTA + 8 x parked fields), kind 1 =
-# shared-memory line kernel (tile = warps per CTA).
-CANDIDATES = ([(2, E, t) for E in (16, 12, 8, 6, 4) for t in (1, 2, 9, 10, 17, 18)]
+# register-resident (tile = warps per CTA + 8 x parked fields, + 32 for the
+# form with asynchronous copies two fields ahead), kind 1 = shared-memory line
+# kernel (tile = warps per CTA).
+CANDIDATES = ([(2, E, t + a) for E in (16, 12, 8, 6, 4) for t in (1, 2, 9, 10, 17, 18)
+               for a in (0, 32)]
               + [(1, E, w) for E in (16, 12, 8, 6) for w in (1, 2, 4)])
 
 
@@ -23,8 +25,9 @@ def _matches(desc, kind, E, tile):
     if c.get("E") != E:
         return False
     if kind == 2:
-        return (c.get("kernel") == "register-resident" and c["warps_per_cta"] == tile % 8
-                and c["parked_fields"] == tile // 8)
+        t, depth = tile % 32, (tile // 32 + 1 if tile >= 32 else 0)
+        return (c.get("kernel") == "register-resident" and c["warps_per_cta"] == t % 8
+                and c["parked_fields"] == t // 8 and c["async_depth"] == depth)
     return c.get("kernel") == "compile-time length" and c["warps_per_cta"] == tile
 
 
@@ -63,8 +66,11 @@ def test_every_pass_c_kernel(ns, n, monkeypatch):
         err = rel_l2(got, ref)
         assert err < 2e-5, (kind, E, tile, err)
         tried.append((kind, E, tile))
-    # at least one register-resident and one shared-memory kernel per N
+    # at least one register-resident and one shared-memory kernel per N, and
+    # the asynchronous-copy form where it is compiled
     assert any(t[0] == 2 for t in tried) and any(t[0] == 1 for t in tried), tried
+    if n in (256, 512, 1024):
+        assert any(t[0] == 2 and t[2] >= 32 for t in tried), tried
 
 
 STRIDED = [(k, E, ct) for k in (2, 1) for E in (8, 12, 16, 32) for ct in (8, 16)]
