@@ -45,11 +45,19 @@ struct FftRes {
     void *scratch = nullptr;  // one half-layout field (c2r)
 };
 
+// The largest |m_i| per axis that a run's dealiasing rule keeps: the plain
+// form's transforms skip the lines beyond them (on = false: every line).
+struct PlainPrune {
+    bool on = false;
+    int kx = 0, ky = 0, kz = 0;
+};
+
 struct Run {
     ns_run_params p{};
     int n = 0;    // N_x (the N of a cubic run)
     Grid g;       // grid and box
     PlainPlans gp[3];   // grid runs: the run's own plans for the x, y and z passes
+    PlainPrune prune;   // lines of the step's transforms that are skipped
     long M = 0;   // modes per component, half layout
     long V = 0;   // grid points per component
     // plain form (full half layout)
@@ -196,12 +204,40 @@ inline StdGrid std_grid(const Grid &g, const Fft3 &f) {
                    (const float2 *)f.z->tw};
 }
 
+// The lines of the x and y passes a pruned step transforms.  A field inside
+// Pi is zero on every x line (fixed ky, kz) with |ky| > K_y or kz > K_z and on
+// every y line with kz > K_z, and rows |kx| > K_x (x) and |ky| > K_y (y) of
+// the others are zero; the forward passes need the same lines and rows only,
+// because the update reads the transform inside Pi alone.  x pass: the plane
+// [ky][kz] as N_y rows of N_z/2+1 columns, the kept ky rows and their first
+// K_z + 1 columns, rows kx in the gap; y pass: the plane [kz] (one row), its
+// first K_z + 1 columns, rows ky in the gap.
+static void prune_sels(const Grid &g, const PlainPrune &p, StridedSel *sx, StridedSel *sy) {
+    const long nh = g.nzh();
+    sx->inner = nh;
+    sx->nouter = g.ny;
+    sx->keep = p.kz + 1;
+    sx->o1 = p.ky + 1;
+    sx->o2 = std::max(g.ny - p.ky, sx->o1);
+    sx->gap_lo = p.kx + 1;
+    sx->gap_hi = std::max(g.nx - p.kx, sx->gap_lo);
+    sy->inner = nh;
+    sy->nouter = 1;
+    sy->keep = p.kz + 1;
+    sy->o1 = sy->o2 = 1;
+    sy->gap_lo = p.ky + 1;
+    sy->gap_hi = std::max(g.ny - p.ky, sy->gap_lo);
+}
+
 // c2r of ncomp half fields [ncomp][N_x][N_y][N_z/2+1]: x pass (in -> tmp), y
 // pass (tmp in place), z pass (tmp -> out [ncomp][N_x][N_y][N_z]).  FP32 on
 // compiled lengths: the standalone kernels, one field at a time through tmp.
+// pr (on): the fields lie inside the run's Pi, and only the lines that can be
+// nonzero are transformed (the rest of tmp is neither read nor written).
 template <typename T>
 cudaError_t c2r_batch(const typename Cx<T>::type *in, typename Cx<T>::type *tmp, T *out, const Grid &g,
-                      int ncomp, const Fft3 &f, cudaStream_t s, Tracer *tr = nullptr) {
+                      int ncomp, const Fft3 &f, cudaStream_t s, Tracer *tr = nullptr,
+                      const PlainPrune *pr = nullptr) {
     typedef typename Cx<T>::type C;
     if constexpr (std::is_same<T, float>::value) {
         const StdGrid sg = std_grid(g, f);
@@ -215,22 +251,28 @@ cudaError_t c2r_batch(const typename Cx<T>::type *in, typename Cx<T>::type *tmp,
     }
     const long nh = g.nzh(), plane = (long)g.ny * nh, M = (long)g.nx * plane;
     const PlainPlans &qx = *f.px, &qy = *f.py, &qz = *f.pz;
+    const bool pruned = pr && pr->on;
+    StridedSel sx, sy;
+    if (pruned) prune_sels(g, *pr, &sx, &sy);
     cudaError_t e = NSK_TIMED(tr, "fft_x_inverse",
                               fft_strided<T>(in, tmp, plane, plane, M, M, ncomp, +1, qx.inv, (const C *)f.x->tw,
-                                             g.nx, qx.ct_inv, s));
+                                             g.nx, qx.ct_inv, s, pruned ? &sx : nullptr));
     if (e != cudaSuccess) return e;
     e = NSK_TIMED(tr, "fft_y_inverse",
                   fft_strided<T>(tmp, tmp, nh, nh, plane, plane, ncomp * g.nx, +1, qy.inv, (const C *)f.y->tw,
-                                 g.ny, qy.ct_inv, s));
+                                 g.ny, qy.ct_inv, s, pruned ? &sy : nullptr));
     if (e != cudaSuccess) return e;
     return NSK_TIMED(tr, "fft_z_c2r",
-                     fft_z_c2r<T>(tmp, out, g.nz, (long)ncomp * g.nx * g.ny, qz.zc, (const C *)f.z->tw, s));
+                     fft_z_c2r<T>(tmp, out, g.nz, (long)ncomp * g.nx * g.ny, qz.zc, (const C *)f.z->tw, s,
+                                  pruned ? pr->kz + 1 : -1));
 }
 
 // r2c of ncomp real fields: z pass (in -> out), y and x passes in place.
+// pr (on): only the modes inside the run's Pi are wanted; the others are left
+// partly transformed or untouched.
 template <typename T>
 cudaError_t r2c_batch(const T *in, typename Cx<T>::type *out, const Grid &g, int ncomp, const Fft3 &f,
-                      cudaStream_t s, Tracer *tr = nullptr) {
+                      cudaStream_t s, Tracer *tr = nullptr, const PlainPrune *pr = nullptr) {
     typedef typename Cx<T>::type C;
     if constexpr (std::is_same<T, float>::value) {
         cudaError_t e = cudaSuccess;
@@ -241,16 +283,20 @@ cudaError_t r2c_batch(const T *in, typename Cx<T>::type *out, const Grid &g, int
     }
     const long nh = g.nzh(), plane = (long)g.ny * nh, M = (long)g.nx * plane;
     const PlainPlans &qx = *f.px, &qy = *f.py, &qz = *f.pz;
+    const bool pruned = pr && pr->on;
+    StridedSel sx, sy;
+    if (pruned) prune_sels(g, *pr, &sx, &sy);
     cudaError_t e = NSK_TIMED(tr, "fft_z_r2c",
-                              fft_z_r2c<T>(in, out, g.nz, (long)ncomp * g.nx * g.ny, qz.zr, (const C *)f.z->tw, s));
+                              fft_z_r2c<T>(in, out, g.nz, (long)ncomp * g.nx * g.ny, qz.zr, (const C *)f.z->tw, s,
+                                           pruned ? pr->kz + 1 : -1));
     if (e != cudaSuccess) return e;
     e = NSK_TIMED(tr, "fft_y_forward",
                   fft_strided<T>(out, out, nh, nh, plane, plane, ncomp * g.nx, -1, qy.fwd, (const C *)f.y->tw,
-                                 g.ny, qy.ct_fwd, s));
+                                 g.ny, qy.ct_fwd, s, pruned ? &sy : nullptr));
     if (e != cudaSuccess) return e;
     return NSK_TIMED(tr, "fft_x_forward",
                      fft_strided<T>(out, out, plane, plane, M, M, ncomp, -1, qx.fwd, (const C *)f.x->tw, g.nx,
-                                    qx.ct_fwd, s));
+                                    qx.ct_fwd, s, pruned ? &sx : nullptr));
 }
 
 // The transforms of a run: the resources of its axis lengths with their plans
@@ -586,8 +632,31 @@ template <typename T> ns_status tune_plain_grid(ns_ctx *c, Run &r, FftRes *f[3])
     return NS_OK;
 }
 
+// Largest |m| along one axis that the dealiasing rule keeps.  The rule only
+// loosens as any |m_i| shrinks, so no kept mode reaches beyond it.
+static int axis_keep(const Grid &g, int axis, int dealias) {
+    const int n = axis == 0 ? g.nx : axis == 1 ? g.ny : g.nz;
+    int K = -1;
+    for (int m = 0; 2 * m <= n; m++) {
+        const Idx q{axis == 0 ? m : 0, axis == 1 ? m : 0, axis == 2 ? m : 0};
+        if (kept(q, g, dealias)) K = m;
+    }
+    return K;
+}
+
+// NS_PLAIN_PRUNE=0 makes the plain form transform every line (the results
+// inside Pi are the same bit for bit).
+static bool plain_prune_enabled() {
+    const char *v = getenv("NS_PLAIN_PRUNE");
+    return !(v && v[0] == '0');
+}
+
 template <typename T> ns_status plain_alloc(ns_ctx *c, Run &r) {
     typedef typename Cx<T>::type C;
+    r.prune.kx = axis_keep(r.g, 0, r.p.dealias);
+    r.prune.ky = axis_keep(r.g, 1, r.p.dealias);
+    r.prune.kz = axis_keep(r.g, 2, r.p.dealias);
+    r.prune.on = plain_prune_enabled() && r.prune.kx >= 0 && r.prune.ky >= 0 && r.prune.kz >= 0;
     const size_t half = (size_t)r.M * sizeof(C), real = (size_t)r.V * sizeof(T);
     const int nc = r.p.mhd ? 6 : 3;   // state components: u, or u and b
     NS_CK(dalloc(&r.un, nc * half));
@@ -693,13 +762,13 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
         C *wj = (C *)r.wn;
         NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, wj, g, s)));
         NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src + M3, wj + M3, g, s)));
-        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, g, 3, f, s, tr));
-        NS_CK(c2r_batch<T>(wj, (C *)r.work, phys + V3, g, 3, f, s, tr));
-        NS_CK(c2r_batch<T>(src + M3, (C *)r.work, phys + 2 * V3, g, 3, f, s, tr));
-        NS_CK(c2r_batch<T>(wj + M3, (C *)r.work, phys + 3 * V3, g, 3, f, s, tr));
+        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, g, 3, f, s, tr, &r.prune));
+        NS_CK(c2r_batch<T>(wj, (C *)r.work, phys + V3, g, 3, f, s, tr, &r.prune));
+        NS_CK(c2r_batch<T>(src + M3, (C *)r.work, phys + 2 * V3, g, 3, f, s, tr, &r.prune));
+        NS_CK(c2r_batch<T>(wj + M3, (C *)r.work, phys + 3 * V3, g, 3, f, s, tr, &r.prune));
         NS_CK(NSK_TIMED(tr, "cross_mhd", plain_cross_mhd<T>(phys, g, s)));
-        NS_CK(r2c_batch<T>(phys, wj, g, 3, f, s, tr));
-        NS_CK(r2c_batch<T>(phys + V3, wj + M3, g, 3, f, s, tr));
+        NS_CK(r2c_batch<T>(phys, wj, g, 3, f, s, tr, &r.prune));
+        NS_CK(r2c_batch<T>(phys + V3, wj + M3, g, 3, f, s, tr, &r.prune));
         const UpdateArgs ua = update_args(r, stage);
         NS_CK(NSK_TIMED(tr, "update",
                         plain_update<T>((C *)r.un, (C *)r.u1, (const C *)wj, (const T *)r.etab, g, ua, s)));
@@ -711,18 +780,18 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
     for (int stage = 1; stage <= 2 && !r.p.mhd; stage++) {
         C *src = (C *)(stage == 1 ? r.un : r.u1);
         NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, (C *)r.wn, g, s)));
-        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, g, 3, f, s, tr));
-        NS_CK(c2r_batch<T>((C *)r.wn, (C *)r.work, phys + 3 * r.V, g, 3, f, s, tr));
+        NS_CK(c2r_batch<T>(src, (C *)r.work, phys, g, 3, f, s, tr, &r.prune));
+        NS_CK(c2r_batch<T>((C *)r.wn, (C *)r.work, phys + 3 * r.V, g, 3, f, s, tr, &r.prune));
         NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, g, s)));
-        NS_CK(r2c_batch<T>(phys, (C *)r.wn, g, 3, f, s, tr));
+        NS_CK(r2c_batch<T>(phys, (C *)r.wn, g, 3, f, s, tr, &r.prune));
         if (r.p.dealias == 2) {   // the same on the grid shifted by half a spacing, averaged
             C *sh = (C *)r.sh, *sh2 = (C *)r.sh2;
             NS_CK(NSK_TIMED(tr, "phase", plain_phase<T>(src, sh, (const C *)r.phtab, g, s)));
             NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(sh, sh2, g, s)));
-            NS_CK(c2r_batch<T>(sh, (C *)r.work, phys, g, 3, f, s, tr));
-            NS_CK(c2r_batch<T>(sh2, (C *)r.work, phys + 3 * r.V, g, 3, f, s, tr));
+            NS_CK(c2r_batch<T>(sh, (C *)r.work, phys, g, 3, f, s, tr, &r.prune));
+            NS_CK(c2r_batch<T>(sh2, (C *)r.work, phys + 3 * r.V, g, 3, f, s, tr, &r.prune));
             NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, g, s)));
-            NS_CK(r2c_batch<T>(phys, sh2, g, 3, f, s, tr));
+            NS_CK(r2c_batch<T>(phys, sh2, g, 3, f, s, tr, &r.prune));
             NS_CK(NSK_TIMED(tr, "phase", plain_phase_avg<T>((C *)r.wn, sh2, (const C *)r.phtab, g, s)));
         }
         const UpdateArgs ua = update_args(r, stage);

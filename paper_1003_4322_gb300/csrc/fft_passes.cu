@@ -135,12 +135,22 @@ template <typename T> struct Bounds;
 template <> struct Bounds<float> { enum { threads = 512 }; };
 template <> struct Bounds<double> { enum { threads = 384 }; };
 
+// The columns of a plane a strided launch transforms, as the kernel sees
+// them: the plane is nouter rows of `inner` columns, of which rows [0, o1)
+// and [o2, nouter) and the first `keep` columns of each are done, tpr tiles
+// of ct columns per row; rows e of the transform axis in [gap_lo, gap_hi)
+// read as zero (inverse) or are not written (forward).
+struct SelK {
+    long inner;
+    int keep, tpr, o1, o2, gap_lo, gap_hi;
+};
+
 // One CTA: ct contiguous columns of one plane, T = n/E threads per column,
 // lanes along columns (coalesced rows).  Shared tile: element (e, c) at
 // e * ct + c.
 template <typename T, int E, int DIR>
 __global__ void __launch_bounds__(Bounds<T>::threads)
-k_fft_strided(const typename Cx<T>::type *__restrict__ in, typename Cx<T>::type *out, long ncols,
+k_fft_strided(const typename Cx<T>::type *__restrict__ in, typename Cx<T>::type *out, SelK sel,
               long es, long ps_in, long ps_out, Plan pl, const typename Cx<T>::type *__restrict__ tw,
               int ntab) {
     typedef typename Cx<T>::type C;
@@ -149,13 +159,16 @@ k_fft_strided(const typename Cx<T>::type *__restrict__ in, typename Cx<T>::type 
     const int ct = blockDim.x / (pl.n / E);
     const int c = threadIdx.x % ct;
     const int slot = threadIdx.x / ct;
-    const long col = (long)blockIdx.x * ct + c;
-    const bool valid = col < ncols;
+    const int ro = blockIdx.x / sel.tpr;
+    const long inner = (long)(blockIdx.x - ro * sel.tpr) * ct + c;
+    const long col = (long)(ro < sel.o1 ? ro : ro - sel.o1 + sel.o2) * sel.inner + inner;
+    const bool valid = inner < sel.keep;
     const C *src = in + (long)blockIdx.y * ps_in + col;
     C *dst = out + (long)blockIdx.y * ps_out + col;
-    auto gl = [&](int e) -> C { return valid ? src[e * es] : czero<C>(); };
+    auto in_gap = [&](int e) { return e >= sel.gap_lo && e < sel.gap_hi; };
+    auto gl = [&](int e) -> C { return valid && (DIR < 0 || !in_gap(e)) ? src[e * es] : czero<C>(); };
     auto gs = [&](int e, C v) {
-        if (valid) dst[e * es] = v;
+        if (valid && (DIR > 0 || !in_gap(e))) dst[e * es] = v;
     };
     auto sl = [&](int e) -> C { return sm[e * ct + c]; };
     auto ss = [&](int e, C v) { sm[e * ct + c] = v; };
@@ -178,26 +191,43 @@ static const void *strided_kernel(int E) {
 template <typename T>
 cudaError_t fft_strided(const typename Cx<T>::type *in, typename Cx<T>::type *out, long ncols,
                         long es, long ps_in, long ps_out, int planes, int dir, const Plan &pl,
-                        const typename Cx<T>::type *tw, int ntab, int ct, cudaStream_t s) {
+                        const typename Cx<T>::type *tw, int ntab, int ct, cudaStream_t s,
+                        const StridedSel *sel) {
     typedef typename Cx<T>::type C;
     const void *k = dir < 0 ? strided_kernel<T, -1>(pl.E) : strided_kernel<T, +1>(pl.E);
     if (!k || planes < 1 || planes > 65535) return cudaErrorInvalidValue;
     const int T_ = pl.n / pl.E;
     if (ct < 1 || ct * T_ > (int)Bounds<T>::threads) return cudaErrorInvalidValue;
+    if (ncols < 1 || ncols > 0x7fff0000L) return cudaErrorInvalidValue;
+    SelK sk{ncols, (int)ncols, 0, 1, 1, 0, 0};
+    int nrows = 1;
+    if (sel) {
+        if (sel->nouter < 1 || sel->inner < 1 || sel->keep < 0 || sel->keep > sel->inner ||
+            sel->inner * sel->nouter != ncols || sel->o1 < 0 || sel->o1 > sel->o2 || sel->o2 > sel->nouter ||
+            sel->gap_lo < 0 || sel->gap_lo > sel->gap_hi || sel->gap_hi > pl.n)
+            return cudaErrorInvalidValue;
+        sk = SelK{sel->inner, sel->keep, 0, sel->o1, sel->o2, sel->gap_lo, sel->gap_hi};
+        nrows = sel->o1 + sel->nouter - sel->o2;
+    }
+    if (sk.keep > 0x7fffffffL - ct) return cudaErrorInvalidValue;
+    sk.tpr = (sk.keep + ct - 1) / ct;
+    if (nrows < 1 || sk.tpr < 1) return cudaSuccess;   // nothing selected
+    if ((long)nrows * sk.tpr > 0x7fffffffL) return cudaErrorInvalidValue;
     const size_t smem = (size_t)pl.n * ct * sizeof(C);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((ncols + ct - 1) / ct), (unsigned)planes);
+    dim3 grid((unsigned)(nrows * sk.tpr), (unsigned)planes);
     Plan p = pl;
-    void *args[] = {(void *)&in, (void *)&out, (void *)&ncols, (void *)&es, (void *)&ps_in,
+    void *args[] = {(void *)&in, (void *)&out, (void *)&sk, (void *)&es, (void *)&ps_in,
                     (void *)&ps_out, (void *)&p, (void *)&tw, (void *)&ntab};
     return cudaLaunchKernel(k, grid, dim3(ct * T_), args, smem, s);
 }
 template cudaError_t fft_strided<float>(const float2 *, float2 *, long, long, long, long, int, int,
-                                        const Plan &, const float2 *, int, int, cudaStream_t);
+                                        const Plan &, const float2 *, int, int, cudaStream_t,
+                                        const StridedSel *);
 template cudaError_t fft_strided<double>(const double2 *, double2 *, long, long, long, long, int,
                                          int, const Plan &, const double2 *, int, int,
-                                         cudaStream_t);
+                                         cudaStream_t, const StridedSel *);
 
 // ---------------------------------------------------------------- z passes
 
@@ -213,11 +243,12 @@ template <typename C> __host__ __device__ inline int skew_len(int n) {
 // r2c along z.  The N reals of a line, read as n = N/2 complex values
 // z[m] = x[2m] + i x[2m+1], go through one length-n FFT; then
 // X[k] = (Z[k] + conj Z[n-k])/2 - i W^k (Z[k] - conj Z[n-k])/2, W = e^{-2 pi i/N},
-// for k = 0..n (Z[n] = Z[0]).  One CTA holds lb lines, T = n/E threads each.
+// for k = 0..n (Z[n] = Z[0]), of which those below kzk are written.  One CTA
+// holds lb lines, T = n/E threads each.
 template <typename T, int E>
 __global__ void __launch_bounds__(256)
 k_fft_z_r2c(const T *__restrict__ in, typename Cx<T>::type *__restrict__ out, int N, long nlines,
-            Plan pl, const typename Cx<T>::type *__restrict__ tw) {
+            Plan pl, const typename Cx<T>::type *__restrict__ tw, int kzk) {
     typedef typename Cx<T>::type C;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int n = N / 2, Tn = n / E;
@@ -234,18 +265,18 @@ k_fft_z_r2c(const T *__restrict__ in, typename Cx<T>::type *__restrict__ out, in
     fft_line<E, -1, false, true, false>(pl, slot, tw, N, gl, sl, ss, ss);
     if (!valid) return;
     C *dst = out + line * (n + 1);
-    for (int k = slot; k <= n; k += Tn) {
+    for (int k = slot; k <= n && k < kzk; k += Tn) {
         dst[k] = r2c_unpack(sl(k == n ? 0 : k), sl(k == 0 ? 0 : n - k), ldg_c(tw + k));
     }
 }
 
 // c2r along z: Z[k] = (X[k] + conj X[n-k]) + i W^{-k} (X[k] - conj X[n-k]),
 // k < n, with the real parts of X[0] and X[n]; one inverse length-n FFT gives
-// z[m] = x[2m] + i x[2m+1].
+// z[m] = x[2m] + i x[2m+1].  Entries X[k], k >= kzk, read as zero.
 template <typename T, int E>
 __global__ void __launch_bounds__(256)
 k_fft_z_c2r(const typename Cx<T>::type *__restrict__ in, T *__restrict__ out, int N, long nlines,
-            Plan pl, const typename Cx<T>::type *__restrict__ tw) {
+            Plan pl, const typename Cx<T>::type *__restrict__ tw, int kzk) {
     typedef typename Cx<T>::type C;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int n = N / 2, Tn = n / E;
@@ -261,8 +292,8 @@ k_fft_z_c2r(const typename Cx<T>::type *__restrict__ in, T *__restrict__ out, in
     for (int k = slot; k < n; k += Tn) {
         C xk = czero<C>(), xm = czero<C>();
         if (valid) {
-            xk = src[k];
-            xm = src[n - k];
+            if (k < kzk) xk = src[k];
+            if (n - k < kzk) xm = src[n - k];
             if (k == 0) {
                 xk.y = 0;
                 xm.y = 0;
@@ -290,10 +321,12 @@ k_fft_z_c2r(const typename Cx<T>::type *__restrict__ in, T *__restrict__ out, in
 //  r2c: the forward transform Z of x1 + i x2 gives
 //       X1[k] = (Z[k] + conj Z[N-k]) / 2 and X2[k] = (Z[k] - conj Z[N-k]) / 2i.
 // A missing second line (odd line count) reads as zero and is not written.
+// Only the entries below kzk are read (c2r; the others are zero) or written
+// (r2c).
 template <typename T, int E>
 __global__ void __launch_bounds__(256)
 k_fft_z_r2c2(const T *__restrict__ in, typename Cx<T>::type *__restrict__ out, int N, long nlines,
-             Plan pl, const typename Cx<T>::type *__restrict__ tw) {
+             Plan pl, const typename Cx<T>::type *__restrict__ tw, int kzk) {
     typedef typename Cx<T>::type C;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nh = N / 2, Tn = N / E;
@@ -310,7 +343,7 @@ k_fft_z_r2c2(const T *__restrict__ in, typename Cx<T>::type *__restrict__ out, i
     fft_line<E, -1, false, true, false>(pl, slot, tw, N, gl, sl, ss, ss);
     C *d1 = out + l1 * (nh + 1), *d2 = out + l2 * (nh + 1);
     const T half = (T)0.5;
-    for (int k = slot; k <= nh; k += Tn) {
+    for (int k = slot; k <= nh && k < kzk; k += Tn) {
         const C a = sl(k), b = sl(k == 0 ? 0 : N - k);
         if (v1) d1[k] = mkc((a.x + b.x) * half, (a.y - b.y) * half);
         if (v2) d2[k] = mkc((a.y + b.y) * half, (b.x - a.x) * half);
@@ -320,7 +353,7 @@ k_fft_z_r2c2(const T *__restrict__ in, typename Cx<T>::type *__restrict__ out, i
 template <typename T, int E>
 __global__ void __launch_bounds__(256)
 k_fft_z_c2r2(const typename Cx<T>::type *__restrict__ in, T *__restrict__ out, int N, long nlines,
-             Plan pl, const typename Cx<T>::type *__restrict__ tw) {
+             Plan pl, const typename Cx<T>::type *__restrict__ tw, int kzk) {
     typedef typename Cx<T>::type C;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nh = N / 2, Tn = N / E;
@@ -335,7 +368,7 @@ k_fft_z_c2r2(const typename Cx<T>::type *__restrict__ in, T *__restrict__ out, i
     const C *s1 = in + l1 * (nh + 1), *s2 = in + l2 * (nh + 1);
     for (int k = slot; k < N; k += Tn) {
         const int m = k <= nh ? k : N - k;
-        C a = v1 ? s1[m] : czero<C>(), b = v2 ? s2[m] : czero<C>();
+        C a = v1 && m < kzk ? s1[m] : czero<C>(), b = v2 && m < kzk ? s2[m] : czero<C>();
         if (m == 0 || m == nh) {
             a.y = 0;
             b.y = 0;
@@ -387,11 +420,12 @@ static const void *z_kernel(int E) {
 // pl.n == N: two lines per complex transform.
 template <typename T, bool R2C>
 static cudaError_t launch_z(const void *in, void *out, int N, long nlines, const Plan &pl,
-                            const typename Cx<T>::type *tw, cudaStream_t s) {
+                            const typename Cx<T>::type *tw, cudaStream_t s, int kzk) {
     typedef typename Cx<T>::type C;
     const bool paired = pl.n == N;
     const void *k = paired ? z_kernel2<T, R2C>(pl.E) : z_kernel<T, R2C>(pl.E);
     if (!k || (!paired && pl.n * 2 != N) || nlines < 1) return cudaErrorInvalidValue;
+    if (kzk < 0 || kzk > N / 2 + 1) kzk = N / 2 + 1;   // every entry
     const int Tn = pl.n / pl.E;
     int lb = 256 / Tn;
     if (lb < 1) return cudaErrorInvalidValue;
@@ -403,19 +437,19 @@ static cudaError_t launch_z(const void *in, void *out, int N, long nlines, const
     if (blocks > 0x7fffffffL) return cudaErrorInvalidValue;
     Plan p = pl;
     void *args[] = {(void *)&in, (void *)&out, (void *)&N, (void *)&nlines, (void *)&p,
-                    (void *)&tw};
+                    (void *)&tw, (void *)&kzk};
     return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(lb * Tn), args, smem, s);
 }
 
 template <typename T>
 cudaError_t fft_z_r2c(const T *in, typename Cx<T>::type *out, int N, long nlines, const Plan &pl,
-                      const typename Cx<T>::type *tw, cudaStream_t s) {
-    return launch_z<T, true>(in, out, N, nlines, pl, tw, s);
+                      const typename Cx<T>::type *tw, cudaStream_t s, int kzk) {
+    return launch_z<T, true>(in, out, N, nlines, pl, tw, s, kzk);
 }
 template <typename T>
 cudaError_t fft_z_c2r(const typename Cx<T>::type *in, T *out, int N, long nlines,
-                      const Plan &pl, const typename Cx<T>::type *tw, cudaStream_t s) {
-    return launch_z<T, false>(in, out, N, nlines, pl, tw, s);
+                      const Plan &pl, const typename Cx<T>::type *tw, cudaStream_t s, int kzk) {
+    return launch_z<T, false>(in, out, N, nlines, pl, tw, s, kzk);
 }
 cudaError_t prepare_fft_kernels() {
     const size_t big = 48 * 1024 + 1;
@@ -436,12 +470,12 @@ cudaError_t prepare_fft_kernels() {
 }
 
 template cudaError_t fft_z_r2c<float>(const float *, float2 *, int, long, const Plan &,
-                                      const float2 *, cudaStream_t);
+                                      const float2 *, cudaStream_t, int);
 template cudaError_t fft_z_r2c<double>(const double *, double2 *, int, long, const Plan &,
-                                       const double2 *, cudaStream_t);
+                                       const double2 *, cudaStream_t, int);
 template cudaError_t fft_z_c2r<float>(const float2 *, float *, int, long, const Plan &,
-                                      const float2 *, cudaStream_t);
+                                      const float2 *, cudaStream_t, int);
 template cudaError_t fft_z_c2r<double>(const double2 *, double *, int, long, const Plan &,
-                                       const double2 *, cudaStream_t);
+                                       const double2 *, cudaStream_t, int);
 
 }  // namespace nsk

@@ -61,7 +61,7 @@ __device__ __forceinline__ double kmul(int m, double il) { return (double)m * il
 // ellipsoid sum_i (3 m_i / N_i)^2 < 1 (dealias 1); dealias 2: 2 |m_i| < N_i
 // and the ellipsoid < 2.  The ellipsoid is tested exactly over D = lcm(N_i).
 // On the cube these are 3 max|k_i| < N, 9 |k|^2 < N^2 and 9 |k|^2 < 2 N^2.
-__device__ __forceinline__ bool kept(const Idx &k, const Grid &g, int dealias) {
+__host__ __device__ __forceinline__ bool kept(const Idx &k, const Grid &g, int dealias) {
     const long ax = abs(k.x), ay = abs(k.y), az = abs(k.z);
     const long sx = ax * g.qx, sy = ay * g.qy, sz = az * g.qz;
     const long s = sx * sx + sy * sy + sz * sz;

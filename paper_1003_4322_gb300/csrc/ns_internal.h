@@ -87,27 +87,44 @@ bool supported_n(int n);
 // uploaded (rounded once to float for the FP32 path).
 template <typename T> typename Cx<T>::type *make_twiddles(int n, cudaError_t *err);
 
+// A subset of the columns and rows of a strided pass: the lines that the
+// dealiasing rule leaves zero (inverse) or whose result it discards
+// (forward).  A plane's ncols columns are nouter rows of `inner` columns
+// (inner x nouter = ncols); the pass transforms the first `keep` columns of
+// rows [0, o1) and [o2, nouter), and treats the elements e of the transform
+// axis in [gap_lo, gap_hi) as zero on input (dir +1) or leaves them
+// unwritten (dir -1).  The other columns are neither read nor written.
+struct StridedSel {
+    long inner = 0;
+    int keep = 0, nouter = 1, o1 = 1, o2 = 1;
+    int gap_lo = 0, gap_hi = 0;
+};
+
 // Batched FFT along a strided axis.  Element e (< pl.n) of column c (< ncols)
 // of plane b (< planes) sits at base + b * plane_stride + e * es + c (in
 // complex units); columns are contiguous.  dir = -1 forward, +1 inverse.
-// in == out is allowed (in place).  ct = columns per CTA.
+// in == out is allowed (in place).  ct = columns per CTA.  sel (optional):
+// only the selected columns and rows.
 template <typename T>
 cudaError_t fft_strided(const typename Cx<T>::type *in, typename Cx<T>::type *out, long ncols,
                         long es, long ps_in, long ps_out, int planes, int dir, const Plan &pl,
-                        const typename Cx<T>::type *tw, int ntab, int ct, cudaStream_t s);
+                        const typename Cx<T>::type *tw, int ntab, int ct, cudaStream_t s,
+                        const StridedSel *sel = nullptr);
 
 // Real-to-complex transform along z (contiguous) of nlines lines of N reals
-// into nlines lines of N/2+1 complex values; pl is the plan of length N/2 and
-// tw the table of length N.
+// into nlines lines of N/2+1 complex values; pl is the plan of length N/2 (one
+// line per transform) or N (two), tw the table of length N.  kzk in
+// [0, N/2+1]: only the entries kz < kzk are written (-1: all).
 template <typename T>
 cudaError_t fft_z_r2c(const T *in, typename Cx<T>::type *out, int N, long nlines, const Plan &pl,
-                      const typename Cx<T>::type *tw, cudaStream_t s);
+                      const typename Cx<T>::type *tw, cudaStream_t s, int kzk = -1);
 
 // Complex-to-real transform along z: nlines lines of N/2+1 complex values into
 // nlines lines of N reals (real parts of the kz = 0 and N/2 entries only).
+// kzk: the entries kz >= kzk are taken as zero and not read (-1: all read).
 template <typename T>
 cudaError_t fft_z_c2r(const typename Cx<T>::type *in, T *out, int N, long nlines,
-                      const Plan &pl, const typename Cx<T>::type *tw, cudaStream_t s);
+                      const Plan &pl, const typename Cx<T>::type *tw, cudaStream_t s, int kzk = -1);
 
 // Columns per CTA of the strided pass for a given precision and length.
 int default_ct(int elem_bytes, int n);
