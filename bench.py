@@ -11,7 +11,10 @@ precision form): 512^3 forced turbulence (ABC forcing k = 3, F = 0.5,
 nu = 2e-3, dt = 1e-3, seeded k^-2 start), in the plain FP64 form (the
 paper's precision), timed over K RK2 steps; the fused FP32 form runs the same
 workload beside it and its relative L2 distance to the FP64 state is
-reported.  The large form rides along in the same line: 1024^3 forced
+reported.  The plain form's transforms skip the lines the 2/3 rule zeroes
+or discards; the same form with every line done runs too, and the line
+reports its steps/s and whether its state equals the pruned one bit for bit.
+The large form rides along in the same line: 1024^3 forced
 turbulence in the fused FP32 form, and the plain FP64 form at 768^3 for
 comparison.  The standalone 3-component FFT stage is timed at 512^3 and
 1024^3, and the device's FP64 FMA rate is measured for the FP64 roofline.
@@ -90,12 +93,12 @@ def load_peaks():
 # Kernel sources of each form, for telling whether a committed ncu capture
 # still describes the kernels that run.
 KERNEL_SOURCES = {
-    "fp64": ("fft_core.cuh", "fft_passes.cu", "plain.cu", "plain.h", "grid.cuh", "reduce.cuh"),
+    "fp64": ("fft_core.cuh", "fft_passes.cu", "plain.cu", "plain.h", "grid.cuh", "reduce.cuh", "api.cu"),
     "fp32": ("fft_core.cuh", "fft_ct.cuh", "reduce.cuh", "fused.cu", "fused.h", "fused_access.cuh",
              "fused_s.cuh", "fused_k.cuh", "fused_kA.cu", "fused_kB.cu", "fused_kD.cu",
              "fused_kE.cu", "fused_keu.cu", "fused_update.cuh", "fused_sA.cu", "fused_sB.cu",
              "fused_sDE.cu", "fused_z.cu", "fused_zr.cuh", "fused_zr2.cu", "fused_zr3.cu",
-             "fused_zm.cu"),
+             "fused_zr4.cu", "fused_zm.cu"),
 }
 
 
@@ -665,6 +668,29 @@ def large_form(args, peaks, dist):
     return out
 
 
+def plain_unpruned(w, mem, steps, warmup, census_steps, main, dist):
+    """The plain form with every line of its transforms done (NS_PLAIN_PRUNE=0):
+    the same workload and step counts, its steps/s, and whether its states
+    equal the pruned run's bit for bit (they must: the skipped lines are the
+    ones the 2/3 rule zeroes or discards)."""
+    import numpy as np
+    old = os.environ.get("NS_PLAIN_PRUNE")
+    os.environ["NS_PLAIN_PRUNE"] = "0"
+    try:
+        u = time_form(w, "fp64", mem, steps, warmup, census_steps, dist)
+    finally:
+        if old is None:
+            del os.environ["NS_PLAIN_PRUNE"]
+        else:
+            os.environ["NS_PLAIN_PRUNE"] = old
+    u["solver"].close()
+    nr = len(mem[0])
+    same = all(np.array_equal(a, b) for a, b in zip(u["states"], main["states"]))
+    return {"value": nr * steps / (u["ms"] * 1e-3), "unit": "run-steps/s" if nr > 1 else "steps/s",
+            "ms_per_step": u["ms"] / steps, "states_bitwise_equal_to_pruned": bool(same),
+            "kernels": [{"name": n, "launches": l, "ms": t} for n, l, t in u["census"]]}
+
+
 def ours(args, w):
     import numpy as np
     import torch
@@ -712,6 +738,9 @@ def ours(args, w):
                 "execution": c["desc"], "clocks": c["clocks"],
                 "kernels": [{"name": n, "launches": l, "ms": t} for n, l, t in c["census"]]}
         c["solver"].close()
+    unpruned = None
+    if w["prec"] == "fp64" and not args.no_unpruned:
+        unpruned = plain_unpruned(w, mem, args.steps, warmup, census_steps, main, dist)
     main["states"] = None
 
     fft = fft_stage(dims_of(w) if "ny" in w else w["n"], "fp32") if not args.no_fft else None
@@ -741,7 +770,7 @@ def ours(args, w):
         "series": {"at_step": [i + 1 + warmup for i in step_idx],
                    "energy": [float(main["E"][i]) for i in step_idx],
                    "enstrophy": [float(main["O"][i]) for i in step_idx]},
-        "companion": comp, "fft": fft, "large": large,
+        "companion": comp, "plain_unpruned": unpruned, "fft": fft, "large": large,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -786,6 +815,8 @@ def main():
                     help="skip the 1024^3 / 768^3 forms that ride along with forced512")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-companion", action="store_true")
+    ap.add_argument("--no-unpruned", action="store_true",
+                    help="skip the plain FP64 form with every transform line done")
     ap.add_argument("--no-fft", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
