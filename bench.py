@@ -176,11 +176,32 @@ def read_state(s, runs, run):
 
 # ---------------------------------------------------------------- kernel model
 
-def kernel_model(name, n, prec):
+def plain_keep(dims, dealias=0):
+    """Largest |m_i| per axis that the dealiasing rule keeps (3 |m| < N_i for
+    the cubic and spherical 2/3 rules; 2 |m| < N_i and 9 m^2 < 2 N_i^2 for the
+    phase-shift rule): the plain form's transforms skip the lines beyond it,
+    unless NS_PLAIN_PRUNE=0 (then None)."""
+    if os.environ.get("NS_PLAIN_PRUNE", "1").startswith("0"):
+        return None
+    def k(n):
+        m = n // 2
+        while m >= 0 and not ((2 * m < n and 9 * m * m < 2 * n * n) if dealias == 2 else 3 * m < n):
+            m -= 1
+        return m
+    return tuple(k(d) for d in dims)
+
+
+PLAIN_KERNELS = ("fft_x_inverse", "fft_x_forward", "fft_y_inverse", "fft_y_forward", "fft_z_c2r",
+                 "fft_z_r2c")
+
+
+def kernel_model(name, n, prec, keep=None):
     """Algorithmic (bytes, flops) of one launch of a kernel of the step (three
     vector components per launch) on the grid n (N of a cube, or (N_x, N_y,
     N_z) for the plain kernels).  FFT flops use 5 n log2 n per complex line
-    of length n."""
+    of length n.  keep (plain form): the kept (K_x, K_y, K_z), whose lines
+    alone the transforms do and whose rows alone they read (inverse) or
+    write (forward); None: every line."""
     es = 8 if prec == "fp64" else 4
     nx, ny, nz = (n, n, n) if isinstance(n, int) else n
     n = nx
@@ -188,12 +209,17 @@ def kernel_model(name, n, prec):
     M = nx * ny * nh        # half-layout modes per component
     V = nx * ny * nz
     f_zline = 5 * (nz // 2) * math.log2(nz // 2) + 10 * (nz // 2)
+    kx, ky, kz = keep if keep else (nx, ny, nh - 1)
+    rx, ry = (2 * kx + 1, 2 * ky + 1) if keep else (nx, ny)   # rows along x, y kept
+    cx = (2 * ky + 1) * (kz + 1) if keep else ny * nh          # x lines per component
+    cy = nx * (kz + 1) if keep else nx * nh                    # y lines per component
+    zk = kz + 1 if keep else nh                                # kz entries per z line
     if name in ("fft_x_inverse", "fft_x_forward"):
-        return 2 * 3 * M * 2 * es, 3 * ny * nh * 5 * nx * math.log2(nx)
+        return 3 * cx * (rx + nx) * 2 * es, 3 * cx * 5 * nx * math.log2(nx)
     if name in ("fft_y_inverse", "fft_y_forward"):
-        return 2 * 3 * M * 2 * es, 3 * nx * nh * 5 * ny * math.log2(ny)
+        return 3 * cy * (ry + ny) * 2 * es, 3 * cy * 5 * ny * math.log2(ny)
     if name in ("fft_z_c2r", "fft_z_r2c"):
-        return 3 * (M * 2 * es + V * es), 3 * nx * ny * f_zline
+        return 3 * (nx * ny * zk * 2 * es + V * es), 3 * nx * ny * f_zline
     if name in ("fft_c2r_std", "fft_r2c_std"):   # all three passes of three components
         flops = 3 * (ny * nh * 5 * nx * math.log2(nx) + nx * nh * 5 * ny * math.log2(ny) + nx * ny * f_zline)
         return 3 * (M * 2 * es + V * es) + 2 * (2 * 3 * M * 2 * es), flops
@@ -356,7 +382,10 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
     # fused form: one launch covers every run of a group (runs of equal N);
     # plain form: one launch per run
     sizes = sizes or [dims_of(w)]
-    per_size = [kernel_model(name, n, prec) for n in sizes]
+    plain = name in PLAIN_KERNELS
+    per_size = [kernel_model(name, n, prec, plain_keep(n if not isinstance(n, int) else (n, n, n),
+                                                       w.get("dealias", 0)) if plain else None)
+                for n in sizes]
     launches_per_pass = len(sizes) if prec == "fp64" else len(set(sizes))
     bytes_ = sum(b for b, _ in per_size) / launches_per_pass
     flops = sum(f for _, f in per_size) / launches_per_pass

@@ -100,3 +100,52 @@ def test_roofline_arithmetic_on_a_synthetic_census():
     assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
     assert math.isclose(roof["achieved"], b / 0.5e-3 / 1e9)
     assert math.isclose(roof["frac"], roof["achieved"] / 6000.0)
+
+
+def _kept_rule(m, dims, dealias):
+    """The dealiasing rule on one index vector m (grid indices), written out:
+    3 |m_i| < N_i on every axis (and the sphere sum (3 m_i / N_i)^2 < 1 for
+    rule 1); rule 2: 2 |m_i| < N_i and sum (3 m_i / N_i)^2 < 2."""
+    r = sum((3 * mi / ni) ** 2 for mi, ni in zip(m, dims))
+    if dealias == 2:
+        return all(2 * abs(mi) < ni for mi, ni in zip(m, dims)) and r < 2
+    return all(3 * abs(mi) < ni for mi, ni in zip(m, dims)) and (dealias != 1 or r < 1)
+
+
+@pytest.mark.parametrize("dims,dealias", [((64, 64, 64), 0), ((48, 64, 96), 0), ((96, 96, 96), 1),
+                                          ((64, 64, 64), 2), ((36, 24, 48), 2)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_pruned_plain_transforms_move_the_kept_lines(dims, dealias, prec, monkeypatch):
+    """With the lines beyond the kept indices skipped, the x passes do the
+    (2K_y+1)(K_z+1) lines of every component, the y passes N_x (K_z+1), and
+    each reads or writes only the 2K+1 kept rows of its axis; the z passes
+    read (c2r) or write (r2c) K_z+1 entries per line.  K_i is the largest
+    index the rule keeps on axis i, found here by testing the rule index by
+    index."""
+    monkeypatch.delenv("NS_PLAIN_PRUNE", raising=False)
+    nx, ny, nz = dims
+    K = []
+    for a, n in enumerate(dims):
+        kept = [m for m in range(n // 2 + 1) if _kept_rule(tuple(m if i == a else 0 for i in range(3)), dims, dealias)]
+        K.append(max(kept))
+    assert bench.plain_keep(dims, dealias) == tuple(K)
+    es = 8 if prec == "fp64" else 4
+    cx, cy = (2 * K[1] + 1) * (K[2] + 1), nx * (K[2] + 1)
+    want = {
+        "fft_x_inverse": 3 * cx * ((2 * K[0] + 1) + nx) * 2 * es,
+        "fft_x_forward": 3 * cx * ((2 * K[0] + 1) + nx) * 2 * es,
+        "fft_y_inverse": 3 * cy * ((2 * K[1] + 1) + ny) * 2 * es,
+        "fft_y_forward": 3 * cy * ((2 * K[1] + 1) + ny) * 2 * es,
+        "fft_z_c2r": 3 * nx * ny * ((K[2] + 1) * 2 * es + nz * es),
+        "fft_z_r2c": 3 * nx * ny * ((K[2] + 1) * 2 * es + nz * es),
+    }
+    for name, b in want.items():
+        got, flops = bench.kernel_model(name, dims, prec, bench.plain_keep(dims, dealias))
+        assert got == b, (name, got, b)
+    # every line of the full form is at least as much
+    for name in want:
+        full, ffull = bench.kernel_model(name, dims, prec)
+        got, fl = bench.kernel_model(name, dims, prec, bench.plain_keep(dims, dealias))
+        assert got < full and fl <= ffull
+    monkeypatch.setenv("NS_PLAIN_PRUNE", "0")
+    assert bench.plain_keep(dims, dealias) is None
