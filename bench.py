@@ -98,7 +98,7 @@ KERNEL_SOURCES = {
              "fused_s.cuh", "fused_k.cuh", "fused_kA.cu", "fused_kB.cu", "fused_kD.cu",
              "fused_kE.cu", "fused_keu.cu", "fused_update.cuh", "fused_sA.cu", "fused_sB.cu",
              "fused_sDE.cu", "fused_z.cu", "fused_zr.cuh", "fused_zr2.cu", "fused_zr3.cu",
-             "fused_zr4.cu", "fused_zm.cu"),
+             "fused_zr4.cu", "fused_zr5.cu", "fused_zm.cu"),
 }
 
 

@@ -74,7 +74,11 @@ typedef enum {
     NS_ERR_CUDA = 2,           /* a CUDA runtime call or kernel failed */
     NS_ERR_OOM = 3,            /* device or host allocation failed */
     NS_ERR_UNSUPPORTED_N = 4,  /* N is not 2^a 3^b, even, >= 8, in range */
-    NS_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+    NS_ERR_TIMEOUT = 5,        /* a bounded device wait gave up (the fused
+                                  FP32 pass C waits at most about a second
+                                  for each bulk copy of its input); reported,
+                                  like NS_ERR_NONFINITE, by the next call
+                                  that checks the context's error word */
     NS_ERR_NONFINITE = 6       /* the energy of a run is NaN or infinite */
 } ns_status;
 

@@ -91,7 +91,8 @@ struct ns_ctx {
     std::vector<FusedRun> groups;   // fused form: runs grouped by N
     std::map<int, FftRes> fft;
     ns_status sticky = NS_OK;
-    int *flags = nullptr;            // device error word (bit 0: non-finite energy)
+    int *flags = nullptr;            // device error word (bit 0: non-finite energy, bit 1: a bounded
+                                     // device wait gave up)
     double *spec = nullptr, *ens = nullptr;
     int spec_cap = 0;
     void *staging = nullptr;
@@ -899,6 +900,7 @@ ns_status check_ctx(ns_ctx *c) {
 ns_status check_flags(ns_ctx *c) {
     int h = 0;
     NS_CK(cudaMemcpy(&h, c->flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & 2) return NS_ERR_TIMEOUT;
     if (h & 1) return NS_ERR_NONFINITE;
     return NS_OK;
 }

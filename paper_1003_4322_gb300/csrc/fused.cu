@@ -374,10 +374,10 @@ cudaError_t prepare_fused_kernels() {
                 }
             }
     const int zrEs[] = {16, 12, 8, 6, 4};
-    int zrTiles[2 * 6];
-    for (int d = 0, k = 0; d < 2; d++)
+    int zrTiles[3 * 6];
+    for (int d = 0, k = 0; d < 3; d++)
         for (int t : {1, 2, ZR_PARK + 1, ZR_PARK + 2, 2 * ZR_PARK + 1, 2 * ZR_PARK + 2})
-            zrTiles[k++] = d * ZR_ASYNC + t;   // depth 0 (registers), 2
+            zrTiles[k++] = d * ZR_ASYNC + t;   // loads: registers, per-lane copies, bulk copies
     for (int N : Ns)
         for (int zE : zrEs)
             for (int tile : zrTiles) {
@@ -456,22 +456,41 @@ static long resident_blocks(const void *k, int threads, size_t smem) {
     return r;
 }
 
+// NS_TEST_ZR_SKIP_COPY=1 (tests only): every warp of the bulk-copy pass C
+// leaves its first copy unissued, so that the wait for it runs out (after
+// about a millisecond) and the kernel reports the timeout in the error word.
+static ZrCtl zr_ctl(const FusedRun &f) {
+    const char *v = getenv("NS_TEST_ZR_SKIP_COPY");
+    const bool skip = v && v[0] == '1';
+    return ZrCtl{f.flags, skip ? (1LL << 21) : (1LL << 31), skip ? 1 : 0};   // about 1 ms / 1 s
+}
+
 static cudaError_t launch_zr(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
     ZctKernel z;
     if (!zr_lookup(f.n, cfg.pl.E, cfg.ct, &z) || f.Mz != (f.n - 1) / 3 + 1) return cudaErrorInvalidValue;
+    long nlines = (long)f.n * f.n;
+    long fs = (long)f.n * f.n * f.Mz;
+    long brun = f.sB;
+    if (z.bulk_bytes) {
+        // bulk copies: every copy starts on a 16-byte boundary and moves a
+        // whole number of 16-byte units (the kernel copies the LPW lines of a
+        // group, groups never straddle the end)
+        const int lpw = z.lines_per_block / (z.threads / 32);
+        if (((uintptr_t)f.bbuf & 15) || (fs * 8) % 16 || (brun * 8) % 16 || z.bulk_bytes % 16 ||
+            (long)z.bulk_bytes != (long)lpw * f.Mz * 8 || nlines % lpw)
+            return cudaErrorInvalidValue;
+    }
     cudaError_t e = allow_smem(z.k, z.smem);
     if (e != cudaSuccess) return e;
-    long nlines = (long)f.n * f.n;
     // the kernel walks its line groups (k_fused_zr): one resident wave of
     // CTAs, shared among the runs of the group
     long blocks = (nlines + z.lines_per_block - 1) / z.lines_per_block;
     const long per_run = resident_blocks(z.k, z.threads, z.smem) / f.nr;
     if (per_run >= 1 && blocks > per_run) blocks = per_run;
     float2 *buf = f.bbuf;
-    long fs = (long)f.n * f.n * f.Mz;
-    long brun = f.sB;
     const float2 *tw = f.tw;
-    void *args[] = {(void *)&buf, (void *)&fs, (void *)&nlines, (void *)&brun, (void *)&tw};
+    ZrCtl ctl = zr_ctl(f);
+    void *args[] = {(void *)&buf, (void *)&fs, (void *)&nlines, (void *)&brun, (void *)&tw, (void *)&ctl};
     return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem,
                             s);
 }
@@ -907,10 +926,10 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
             if (ms > 0.f) cands.push_back({ms, cfg});
         }
         const int zrEs[] = {16, 12, 8, 6, 4};
-        int zrTiles[2 * 6];
-        for (int d = 0, k = 0; d < 2; d++)
+        int zrTiles[3 * 6];
+        for (int d = 0, k = 0; d < 3; d++)
             for (int t : {1, 2, ZR_PARK + 1, ZR_PARK + 2, 2 * ZR_PARK + 1, 2 * ZR_PARK + 2})
-                zrTiles[k++] = d * ZR_ASYNC + t;   // depth 0 (registers), 2
+                zrTiles[k++] = d * ZR_ASYNC + t;   // loads: registers, per-lane copies, bulk copies
         for (int zE : zrEs)
             for (int tile : zrTiles) {
                 ZctKernel z;
@@ -1141,6 +1160,7 @@ static cudaError_t fused_step_mhd(FusedRun &f, int *flags, cudaStream_t s, Trace
 }
 
 cudaError_t fused_step(FusedRun &f, int *flags, cudaStream_t s, Tracer *tr) {
+    f.flags = flags;
     if (f.mhd) return fused_step_mhd(f, flags, s, tr);
     cudaError_t e;
     for (int stage = 1; stage <= 2; stage++) {
@@ -1190,9 +1210,11 @@ int fused_describe(const FusedRun &f, char *out, int len) {
     if (w < len && f.zc.kind == 2)
         w += snprintf(out + w, len - w,
                       "\"C_z_nonlinear\": {\"kernel\": \"register-resident\", \"E\": %d, "
-                      "\"warps_per_cta\": %d, \"parked_fields\": %d, \"async_depth\": %d}}",
+                      "\"warps_per_cta\": %d, \"parked_fields\": %d, \"loads\": \"%s\"}}",
                       f.zc.pl.E, (f.zc.ct % ZR_ASYNC) % ZR_PARK, (f.zc.ct % ZR_ASYNC) / ZR_PARK,
-                      f.zc.ct >= ZR_ASYNC ? f.zc.ct / ZR_ASYNC + 1 : 0);
+                      f.zc.ct / ZR_ASYNC == 2   ? "bulk copies, two fields ahead"
+                      : f.zc.ct / ZR_ASYNC == 1 ? "per-lane asynchronous copies, two fields ahead"
+                                                : "registers, one field ahead");
     else if (w < len && f.zc.kind == 1)
         w += snprintf(out + w, len - w,
                       "\"C_z_nonlinear\": {\"kernel\": \"compile-time length\", \"E\": %d, "

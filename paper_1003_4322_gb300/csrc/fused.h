@@ -23,6 +23,17 @@ struct ZctKernel {
     size_t smem = 0;
     int lines_per_block = 0;
     int threads = 0;
+    int bulk_bytes = 0;   // pass C with bulk copies: bytes of one copy (a warp's lines of one field)
+};
+
+// Control block of the register-resident pass C: the context's error word
+// (bit 1 set when a bounded wait gave up), the clock-cycle limit of each
+// wait, and a test switch that leaves a warp's first bulk copy unissued so
+// that the wait for it runs out.
+struct ZrCtl {
+    int *flags;
+    long long wait_cycles;
+    int skip_first_copy;
 };
 // Kernel for grid size N, E elements per thread and wpb warps per CTA, if one
 // was compiled (E in {16, 8} or {12, 6}; wpb in {1, 2, 4}).
@@ -30,8 +41,8 @@ bool zct_lookup(int N, int E, int wpb, ZctKernel *out);
 // Register-resident pass-C kernel (fused_zr.cuh, fused_zr2.cu, fused_zr3.cu,
 // fused_zr4.cu): tile = warps per CTA (1 or 2) + ZR_PARK x the number of
 // fields parked in shared memory (0, 1: u_x, 2: u_x and u_y), + ZR_ASYNC x
-// (depth - 1) for the form whose field loads are asynchronous copies depth
-// fields ahead (depth 2 is compiled).
+// the load mode: 0 registers, 1 per-lane asynchronous copies two fields
+// ahead, 2 one bulk copy per warp and field, two fields ahead.
 constexpr int ZR_PARK = 8;
 constexpr int ZR_ASYNC = 32;
 bool zr_lookup(int N, int E, int tile, ZctKernel *out);
@@ -90,6 +101,7 @@ struct FusedRun {
     long blk_s = 0, blk_A = 0, blk_B = 0;
     float *etab_b = nullptr;     // exp(-eta k^2 dt) by integer k^2       [nr][nk2]
     int zm_E = 0, zm_wpb = 0;    // MHD pass C (fused_zm.cu)
+    int *flags = nullptr;        // the context's device error word (set by fused_step)
     int nparts_upd = 0;          // energy partials per run of the separate update kernel
     const float2 *tw = nullptr;  // exp(-2 pi i t / n), t < n (owned by the context)
     float2 *a = nullptr;         // state                       [nr][3][M]

@@ -103,6 +103,44 @@ NSK_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "me
 template <int PENDING> NSK_DEV void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
 }
+// Bulk copies global -> shared that complete on an mbarrier (the
+// transaction count of the barrier's current phase), and the barrier's
+// bounded wait.
+NSK_DEV unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+NSK_DEV void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+NSK_DEV void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+// Shared memory read by generic loads before an asynchronous-proxy write.
+NSK_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// bytes (a multiple of 16) from src to dst (both 16-byte aligned); one
+// arrival on bar that expects them.
+NSK_DEV void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+NSK_DEV bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// true once the phase of the given parity has completed; false after
+// `cycles` clock cycles without it
+NSK_DEV bool mbar_wait(unsigned long long *bar, unsigned parity, long long cycles) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > cycles) return false;
+    return true;
+}
+
 NSK_DEV float2 shfl2(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
@@ -118,10 +156,18 @@ NSK_DEV float2 shfl2(float2 v, int src) {
 // of one, with no more registers; each thread copies and reads back only its
 // own elements.  DEPTH divides the six fields of a group (2 or 3), so a
 // field keeps its buffer from group to group.
-template <int N, int E, int WPB, int PARK, int DEPTH = 0>
+// BULK (with DEPTH): one lane copies the warp's LPW lines of a field (they are
+// contiguous, LPW Mz 8 bytes, a multiple of 16) with one bulk copy that
+// completes on the buffer's mbarrier, and every lane reads its elements from
+// the natural line layout; the warp syncs before a buffer is refilled.  A
+// wait that runs out of ctl.wait_cycles raises bit 1 of *ctl.flags, the
+// loads that follow read zeros, and the kernel still waits for the copies it
+// issued before it exits.
+template <int N, int E, int WPB, int PARK, int DEPTH = 0, bool BULK = false>
 __global__ void __launch_bounds__(32 * WPB)
-k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restrict__ tw) {
+k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restrict__ tw, ZrCtl ctl) {
     static_assert(DEPTH == 0 || DEPTH == 2 || DEPTH == 3, "DEPTH divides 6");
+    static_assert(!BULK || DEPTH > 0, "bulk copies run ahead");
     constexpr bool ASYNC = DEPTH > 0;
     typedef ZrShape<N, E> Z;
     constexpr int n = Z::n, T = Z::T, LPW = Z::LPW, LS = Z::LS, Mz = Z::Mz;
@@ -141,6 +187,15 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     float2 *park1 = park0 + E * 32;                                                   // u_y
     // ASYNC: [warp][DEPTH buffers][E][32 lanes] after the parked fields
     float2 *pfb = sm + (long)WPB * LPW * LS + (long)WPB * PARK * E * 32 + (long)warp * DEPTH * E * 32 + lane;
+    // BULK: [warp][DEPTH buffers][BL] (16-byte aligned), then the warps'
+    // mbarriers [warp][DEPTH]
+    constexpr int BL = (LPW * Mz + 1) & ~1;
+    constexpr long BB = ((long)WPB * LPW * LS + (long)WPB * PARK * E * 32 + 1) & ~1L;
+    float2 *bb = sm + BB + (long)warp * DEPTH * BL;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(sm + BB + (long)WPB * DEPTH * BL) + warp * DEPTH;
+    unsigned par = 0, pend = 0;   // BULK: phase parity and copy in flight, bit b for buffer b
+    bool bad = false;             // BULK: a wait ran out
+    bool first_copy = true;
     auto sl = [&](int e) -> float2 { return L[ct_skew(e)]; };
     auto ss = [&](int e, float2 v) { L[ct_skew(e)] = v; };
 
@@ -177,12 +232,52 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
 #pragma unroll
         for (int j = 0; j < E; j++) x[j] = j * T < Mz ? pfb[(b * E + j) * 32] : make_float2(0.f, 0.f);
     };
+    // BULK: field f of group g into buffer b (no copy past the last group)
+    auto issue_bulk = [&](int f, long g, int b) {
+        if (g >= ngroups || bad) return;
+        __syncwarp();   // every lane has read buffer b
+        if (lane == 0 && !(ctl.skip_first_copy && first_copy)) {
+            fence_proxy_async_smem();
+            bulk_g2s(bb + b * BL, buf + f * fs + g * LPW * Mz, LPW * Mz * 8, &bars[b]);
+        }
+        first_copy = false;
+        pend |= 1u << b;
+    };
+    // BULK: wait for buffer b's copy (the phase stays current: a second wait
+    // on it returns at once)
+    auto wait_bulk = [&](int b) {
+        if (bad || !(pend & (1u << b))) return;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[b], (par >> b) & 1u, ctl.wait_cycles));
+        if (!ok) {
+            bad = true;
+            pend &= ~(1u << b);
+            if (lane == 0 && ctl.flags) atomicOr(ctl.flags, 2);
+        }
+    };
+    auto take_bulk = [&](int b) {
+        wait_bulk(b);
+        const bool ok = !bad;
+        if (ok && (pend & (1u << b))) {   // else a copy in flight stays pending for the exit
+            par ^= 1u << b;
+            pend &= ~(1u << b);
+        }
+        const float2 *src = bb + b * BL + ll * Mz;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int k = slot + j * T;
+            x[j] = make_float2(0.f, 0.f);
+            if (j * T < Mz && ok && k < Mz) x[j] = src[k];
+        }
+    };
     // the field DEPTH places after position i of the order u_x, w_y, u_y, w_x,
     // u_z, w_z (the last DEPTH positions reach into the next group), into the
     // buffer position i has just freed
     constexpr int kOrder[6] = {0, 4, 1, 3, 2, 5};
     auto issue_ahead = [&](int i) {
-        if (i + DEPTH < 6) {
+        if constexpr (BULK) {
+            if (i + DEPTH < 6) issue_bulk(kOrder[i + DEPTH], group, i % DEPTH);
+            else issue_bulk(kOrder[i + DEPTH - 6], group + gstride, i % DEPTH);
+        } else if (i + DEPTH < 6) {
             issue_at(kOrder[i + DEPTH], line, valid, i % DEPTH);
         } else {
             const long nl = (group + gstride) * LPW + ll;
@@ -195,7 +290,8 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     // fnext: the field to load next (-1 none, -2 field 0 of the next group);
     // ASYNC: pos, the position of this field in the order (buffer pos % DEPTH).
     auto inverse = [&](float2 (&v)[E], int fnext, int pos) {
-        if constexpr (ASYNC) take(pos % (DEPTH > 0 ? DEPTH : 1));
+        if constexpr (BULK) take_bulk(pos % DEPTH);
+        else if constexpr (ASYNC) take(pos % (DEPTH > 0 ? DEPTH : 1));
 #pragma unroll
         for (int j = 0; j < E; j++) {
             const int k = slot + j * T;
@@ -247,7 +343,16 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     // most five field arrays are live.  A thread stores only positions it
     // loaded itself, and its loads of a field precede its stores to it.
     float2 A[E], B[E], C[E], D[E], P[E];
-    if constexpr (ASYNC) {
+    if constexpr (BULK) {
+        if (lane == 0) {
+#pragma unroll
+            for (int b = 0; b < DEPTH; b++) mbar_init(&bars[b], 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < DEPTH; i++) issue_bulk(kOrder[i], group, i);
+    } else if constexpr (ASYNC) {
 #pragma unroll
         for (int i = 0; i < DEPTH; i++) issue_at(kOrder[i], line, valid, i);
     } else {
@@ -275,8 +380,9 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     }
     // ASYNC: the store over field 2 must not overtake the copy of u_z (field
     // 2, position 4); groups complete in order, and the copies issued after it
-    // are those of positions 5 .. 3 + DEPTH
-    if constexpr (ASYNC) cp_async_wait<(DEPTH > 0 ? DEPTH - 2 : 0)>();
+    // are those of positions 5 .. 3 + DEPTH.  BULK: wait for that copy.
+    if constexpr (BULK) wait_bulk(4 % DEPTH);
+    else if constexpr (ASYNC) cp_async_wait<(DEPTH > 0 ? DEPTH - 2 : 0)>();
     forward_store(P, 2);
     float2 px[E], py[E];
     inverse(P, 5, 4);   // u_z
@@ -299,7 +405,13 @@ k_fused_zr(float2 *buf, long fs, long nlines, long brun, const float2 *__restric
     line += gstride * LPW;
     valid = line < nlines;
     }
-    if constexpr (ASYNC) cp_async_wait<0>();   // no copy may land after the CTA exits
+    if constexpr (BULK) {   // no copy may land after the CTA exits
+#pragma unroll
+        for (int b = 0; b < DEPTH; b++)
+            if (pend & (1u << b)) (void)mbar_wait(&bars[b], (par >> b) & 1u, ctl.wait_cycles);
+    } else if constexpr (ASYNC) {
+        cp_async_wait<0>();
+    }
 }
 
 // Pass C of the MHD form (Alfven units): the group's B buffers form two
@@ -461,13 +573,22 @@ template <int N, int E, int WPB> bool zrm_entry(ZctKernel *o) {
     }
 }
 
-template <int N, int E, int WPB, int PARK, int DEPTH = 0> bool zr_entry(ZctKernel *o) {
+template <int N, int E, int WPB, int PARK, int DEPTH = 0, bool BULK = false> bool zr_entry(ZctKernel *o) {
     typedef ZrShape<N, E> Z;
-    if constexpr (!Z::ok) {
+    // a bulk copy moves a warp's LPW lines of a field: a multiple of 16 bytes
+    if constexpr (!Z::ok || (BULK && (Z::LPW * Z::Mz) % 2 != 0)) {
         return false;
     } else {
-        o->k = (const void *)k_fused_zr<N, E, WPB, PARK, DEPTH>;
-        o->smem = (size_t)WPB * (Z::LPW * Z::LS + PARK * E * 32 + DEPTH * E * 32) * sizeof(float2);
+        o->k = (const void *)k_fused_zr<N, E, WPB, PARK, DEPTH, BULK>;
+        if constexpr (BULK) {
+            constexpr long BL = (Z::LPW * Z::Mz + 1) & ~1;
+            constexpr long BB = ((long)WPB * Z::LPW * Z::LS + (long)WPB * PARK * E * 32 + 1) & ~1L;
+            o->smem = (size_t)(BB + WPB * DEPTH * BL) * sizeof(float2) + WPB * DEPTH * sizeof(unsigned long long);
+            o->bulk_bytes = Z::LPW * Z::Mz * (int)sizeof(float2);
+        } else {
+            o->smem = (size_t)WPB * (Z::LPW * Z::LS + PARK * E * 32 + DEPTH * E * 32) * sizeof(float2);
+            o->bulk_bytes = 0;
+        }
         o->lines_per_block = WPB * Z::LPW;
         o->threads = 32 * WPB;
         return true;
@@ -475,15 +596,17 @@ template <int N, int E, int WPB, int PARK, int DEPTH = 0> bool zr_entry(ZctKerne
 }
 
 // tile = warps per CTA (1 or 2) + ZR_PARK x the number of parked fields
-// + ZR_ASYNC x (depth - 1) for the asynchronous-copy form of depth 2 or 3.
-template <int N, int E, int PARK, int DEPTH = 0> bool zr_by_tile(int tile, ZctKernel *o) {
-    const int depth = tile / ZR_ASYNC ? tile / ZR_ASYNC + 1 : 0;
-    if (depth != DEPTH) return false;
+// + ZR_ASYNC x the load mode (0 registers, 1 per-lane asynchronous copies, 2
+// bulk copies; both copy forms two fields ahead).
+template <int N, int E, int PARK, int DEPTH = 0, bool BULK = false> bool zr_by_tile(int tile, ZctKernel *o) {
+    static_assert(DEPTH == 0 || DEPTH == 2, "the copy forms run two fields ahead");
+    const int mode = tile / ZR_ASYNC;
+    if (mode != (BULK ? 2 : DEPTH > 0 ? 1 : 0)) return false;
     tile %= ZR_ASYNC;
     if (tile / ZR_PARK != PARK) return false;
     switch (tile % ZR_PARK) {
-    case 1: return zr_entry<N, E, 1, PARK, DEPTH>(o);
-    case 2: return zr_entry<N, E, 2, PARK, DEPTH>(o);
+    case 1: return zr_entry<N, E, 1, PARK, DEPTH, BULK>(o);
+    case 2: return zr_entry<N, E, 2, PARK, DEPTH, BULK>(o);
     }
     return false;
 }
@@ -492,7 +615,9 @@ template <int N, int E, int PARK, int DEPTH = 0> bool zr_by_tile(int tile, ZctKe
 // with a factor 3).
 bool zr_lookup2(int N, int E, int tile, ZctKernel *o);
 bool zr_lookup3(int N, int E, int tile, ZctKernel *o);
-// The asynchronous-copy form for powers of two (fused_zr4.cu).
+// The asynchronous-copy form for powers of two (fused_zr4.cu), and the
+// bulk-copy form (fused_zr5.cu).
 bool zr_lookup4(int N, int E, int tile, ZctKernel *o);
+bool zr_lookup5(int N, int E, int tile, ZctKernel *o);
 
 }  // namespace nsk

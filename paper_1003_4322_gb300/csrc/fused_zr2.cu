@@ -31,7 +31,8 @@ bool zr_lookup2(int N, int E, int tile, ZctKernel *o) {
 }
 
 bool zr_lookup(int N, int E, int tile, ZctKernel *o) {
-    return zr_lookup2(N, E, tile, o) || zr_lookup3(N, E, tile, o) || zr_lookup4(N, E, tile, o);
+    return zr_lookup2(N, E, tile, o) || zr_lookup3(N, E, tile, o) || zr_lookup4(N, E, tile, o) ||
+           zr_lookup5(N, E, tile, o);
 }
 
 }  // namespace nsk

@@ -13,10 +13,13 @@ pytestmark = pytest.mark.gpu
 
 # (kind, E, tile) triples as the plan cache writes them: kind 2 =
 # register-resident (tile = warps per CTA + 8 x parked fields, + 32 for the
-# form with asynchronous copies two fields ahead), kind 1 = shared-memory line
-# kernel (tile = warps per CTA).
+# form with per-lane asynchronous copies two fields ahead, + 64 for the form
+# with one bulk copy per warp and field), kind 1 = shared-memory line kernel
+# (tile = warps per CTA).
+LOADS = {0: "registers, one field ahead", 1: "per-lane asynchronous copies, two fields ahead",
+         2: "bulk copies, two fields ahead"}
 CANDIDATES = ([(2, E, t + a) for E in (16, 12, 8, 6, 4) for t in (1, 2, 9, 10, 17, 18)
-               for a in (0, 32)]
+               for a in (0, 32, 64)]
               + [(1, E, w) for E in (16, 12, 8, 6) for w in (1, 2, 4)])
 
 
@@ -25,9 +28,9 @@ def _matches(desc, kind, E, tile):
     if c.get("E") != E:
         return False
     if kind == 2:
-        t, depth = tile % 32, (tile // 32 + 1 if tile >= 32 else 0)
+        t = tile % 32
         return (c.get("kernel") == "register-resident" and c["warps_per_cta"] == t % 8
-                and c["parked_fields"] == t // 8 and c["async_depth"] == depth)
+                and c["parked_fields"] == t // 8 and c["loads"] == LOADS[tile // 32])
     return c.get("kernel") == "compile-time length" and c["warps_per_cta"] == tile
 
 
@@ -70,7 +73,8 @@ def test_every_pass_c_kernel(ns, n, monkeypatch):
     # the asynchronous-copy form where it is compiled
     assert any(t[0] == 2 for t in tried) and any(t[0] == 1 for t in tried), tried
     if n in (256, 512, 1024):
-        assert any(t[0] == 2 and t[2] >= 32 for t in tried), tried
+        for mode in (1, 2):
+            assert any(t[0] == 2 and t[2] // 32 == mode for t in tried), tried
 
 
 STRIDED = [(k, E, ct) for k in (2, 1) for E in (8, 12, 16, 32) for ct in (8, 16)]
@@ -145,3 +149,37 @@ def test_pass_e_fused_with_update(ns, n, monkeypatch):
         assert abs(Es[-1] - E) < 1e-12 * E and abs(Os[-1] - Om) < 1e-12 * Om, cfg
         tried.append(cfg)
     assert len(tried) >= 2, tried
+
+
+def test_bulk_copy_wait_runs_out_and_reports(ns, monkeypatch):
+    """The bulk-copy pass C waits for each copy with a bounded mbarrier wait.
+    NS_TEST_ZR_SKIP_COPY=1 leaves every warp's first copy unissued, so that
+    wait runs out (after about a millisecond). The kernel then raises the
+    context's timeout bit and still waits for the copies it did issue before
+    it exits. ns_sync reports NS_ERR_TIMEOUT, and the device stays usable: a
+    fresh context runs the same kernel to the plain FP64 result."""
+    from paper_1003_4322_gb300 import _native as nat
+    from paper_1003_4322_gb300.solver import Solver
+    n = 256
+    run = dict(n=n, nu=2e-3, dt=1e-3, force_amp=0.5, force_k=3)
+    a0 = inputs.turbulence_state(n, seed=8)
+    with Solver([run], prec="fp64") as s:
+        s.set_state(a0)
+        s.step(1)
+        ref = s.get_state()
+    monkeypatch.setenv("NS_FORCE_PASS_C", "2,16,81")   # E = 16, one warp, two fields parked, bulk
+    monkeypatch.setenv("NS_TEST_ZR_SKIP_COPY", "1")
+    with Solver([run], prec="fp32") as s:
+        c = _find_c(nat.ns_describe_run(s.ctx, 0))["C_z_nonlinear"]
+        assert c["loads"] == "bulk copies, two fields ahead", c
+        s.set_state(a0)
+        s.step(1)
+        with pytest.raises(nat.NsError) as err:
+            s.sync()
+        assert err.value.status == 5   # NS_ERR_TIMEOUT
+    monkeypatch.delenv("NS_TEST_ZR_SKIP_COPY")
+    with Solver([run], prec="fp32") as s:
+        s.set_state(a0)
+        s.step(1)
+        got = s.get_state()
+    assert rel_l2(got, ref) < 2e-5
