@@ -343,12 +343,15 @@ def test_phase_shift_with_mhd_is_rejected(ns):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_page_locked_host_buffers_match_pageable(ns, prec):
     """ns_set_state / ns_get_state read and write page-locked host memory
-    directly (no staging copies); the results equal the staged path's bit
-    for bit, for the velocity and the magnetic field of an MHD run, on a cube
-    and on a grid of another shape."""
+    directly (no staging copies), every element of the output (filled with
+    NaN first). The results equal the staged path's bit for bit, for the
+    velocity and the magnetic field of an MHD run, on cubes, every
+    dealiasing rule and a grid of another shape."""
     import torch
     from paper_1003_4322_gb300.solver import Solver
     for run, mhd in ((dict(n=64, nu=0.01, dt=1e-3, force_amp=0.5, force_k=3), False),
+                     (dict(n=192, nu=0.01, dt=1e-3, dealias=1), False),
+                     (dict(n=36, nu=0.01, dt=1e-3, dealias=2), False),
                      (dict(n=32, nu=0.01, eta=0.02, dt=1e-3, mhd=1), True),
                      (dict(n=32, ny=48, nz=24, lz=2.0, nu=0.01, dt=1e-3), False)):
         dims = (run["n"], run.get("ny", run["n"]), run.get("nz", run["n"]))
@@ -372,6 +375,8 @@ def test_page_locked_host_buffers_match_pageable(ns, prec):
                     ob = torch.empty(a0.shape, dtype=torch.complex128, pin_memory=True).numpy()
                 else:
                     o, ob = np.empty_like(a0), np.empty_like(a0)
+                o[...] = np.nan
+                ob[...] = np.nan
                 s.get_state(out=o)
                 if mhd:
                     s.get_field(1, out=ob)
