@@ -323,8 +323,8 @@ ns_status ns_sync(ns_ctx *ctx);
  * fused form, the radix split and tile the autotuner chose for each pass
  * (ns_init runs each pass with a few candidate configurations on the run's
  * own buffers and keeps the fastest, per N, for the life of the process).
- * Writes at most len bytes including the terminating zero.  Errors:
- * NS_ERR_ARG. */
+ * Writes at most len bytes including the terminating zero (2048 always
+ * suffice).  Errors: NS_ERR_ARG (also when the text did not fit in len). */
 ns_status ns_describe_run(ns_ctx *ctx, int run, char *out, int len);
 
 /* Detail of the last CUDA failure the context recorded (CUDA error name,

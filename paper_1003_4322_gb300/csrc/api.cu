@@ -933,11 +933,12 @@ const char *ns_last_error(ns_ctx *c) { return c ? c->last_error : ""; }
 ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
     if (!c || run < 0 || run >= (int)c->runs.size() || !out || len < 1) return NS_ERR_ARG;
     const Run &r = c->runs[run];
+    int w;
     if (use_fused(c)) {
         const FusedRun &g = c->groups[r.group];
-        char tune[512];
-        fused_describe(g, tune, sizeof(tune));
-        snprintf(out, len,
+        char tune[2048];
+        if (fused_describe(g, tune, sizeof(tune)) >= (int)sizeof(tune)) return NS_ERR_ARG;
+        w = snprintf(out, len,
                  "{\"form\": \"fused FP32\", \"equations\": \"%s\", \"n\": %d, \"K\": %d, "
                  "\"state_modes\": %ld, \"runs_in_group\": %d, \"passes\": %s}",
                  g.mhd ? "MHD" : "Navier-Stokes", r.n, g.K, (g.mhd ? 6 : 3) * g.M, g.nr, tune);
@@ -946,7 +947,7 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
         const auto it = c->fft.find(r.n);
         const PlainPlans qc = it != c->fft.end() ? it->second.pp : PlainPlans{};
         const PlainPlans &q = r.g.cube ? qc : r.gp[0], &qz = r.g.cube ? qc : r.gp[2];
-        snprintf(out, len,
+        w = snprintf(out, len,
                  "{\"form\": \"plain %s\", \"equations\": \"%s\", \"n\": %d, \"grid\": [%d, %d, %d], "
                  "\"box\": [%.17g, %.17g, %.17g], \"tuned\": %s, "
                  "\"xy_inverse\": {\"E\": %d, \"cols_per_cta\": %d}, \"xy_forward\": {\"E\": %d, "
@@ -956,7 +957,7 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
                  r.g.nz, r.g.lx, r.g.ly, r.g.lz, q.tuned ? "true" : "false", q.inv.E, q.ct_inv, q.fwd.E, q.ct_fwd,
                  qz.zc.E, qz.zc.n == r.g.nz ? 2 : 1, qz.zr.E, qz.zr.n == r.g.nz ? 2 : 1);
     }
-    return NS_OK;
+    return w < len ? NS_OK : NS_ERR_ARG;   // the text did not fit in len bytes
 }
 
 ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda_stream,

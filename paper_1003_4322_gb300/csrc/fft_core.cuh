@@ -201,7 +201,48 @@ template <int R1, int R2, int DIR, typename C> struct DftComposite {
     }
 };
 template <int DIR, typename C> struct Dft<6, DIR, C> : DftComposite<2, 3, DIR, C> {};
+
+NSK_DEV float fmac(float a, float b, float c) { return fmaf(a, b, c); }
+NSK_DEV double fmac(double a, double b, double c) { return fma(a, b, c); }
+
+// Radix 8 in FP64 as 2 x 4 (j = 4 j1 + j2, k = k1 + 2 k2) like the
+// composite, with the odd outputs k1 = 1 regrouped: their inputs carry W^j2,
+// W = exp(DIR 2 pi i / 8), and W^2 = DIR i, so the length-4 sums pair up as
+// W (b1 +- DIR i b3) and W = (1 + DIR i) / sqrt(2).  The 1/sqrt(2) is applied
+// by the fused multiply-adds of the last additions: 52 arithmetic
+// instructions where the composite takes 56, which pays in the FP64 passes
+// (bound by the FP64 pipe: 2-3 % per pass).  The FP32 passes, bound by
+// memory, keep the composite: the regrouped form changed their register
+// allocation and cost up to 10 % (pass A at 1024^3).
 template <int DIR, typename C> struct Dft<8, DIR, C> : DftComposite<2, 4, DIR, C> {};
+template <int DIR> struct Dft<8, DIR, double2> {
+    typedef double2 C;
+    static NSK_DEV void run(C *a) {
+        typedef double T;
+        const T h = (T)0.7071067811865476;   // 1 / sqrt(2)
+        C b0[4], b1[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            b0[j] = cadd(a[j], a[4 + j]);
+            b1[j] = csub(a[j], a[4 + j]);
+        }
+        Dft<4, DIR, C>::run(b0);
+        a[0] = b0[0];
+        a[2] = b0[1];
+        a[4] = b0[2];
+        a[6] = b0[3];
+        const C s02 = cadd_i<DIR>(b1[0], b1[2]), d02 = cadd_i<-DIR>(b1[0], b1[2]);
+        const C e = cadd_i<DIR>(b1[1], b1[3]), f = cadd_i<-DIR>(b1[1], b1[3]);
+        // W e = h (pe, qe), W f = h (pf, qf)
+        const T pe = DIR > 0 ? e.x - e.y : e.x + e.y, qe = DIR > 0 ? e.y + e.x : e.y - e.x;
+        const T pf = DIR > 0 ? f.x - f.y : f.x + f.y, qf = DIR > 0 ? f.y + f.x : f.y - f.x;
+        const T hd = DIR > 0 ? h : -h;
+        a[1] = mkc(fmac(h, pe, s02.x), fmac(h, qe, s02.y));    // s02 + W e
+        a[5] = mkc(fmac(-h, pe, s02.x), fmac(-h, qe, s02.y));  // s02 - W e
+        a[3] = mkc(fmac(-hd, qf, d02.x), fmac(hd, pf, d02.y)); // d02 + DIR i W f
+        a[7] = mkc(fmac(hd, qf, d02.x), fmac(-hd, pf, d02.y)); // d02 - DIR i W f
+    }
+};
 template <int DIR, typename C> struct Dft<9, DIR, C> : DftComposite<3, 3, DIR, C> {};
 template <int DIR, typename C> struct Dft<12, DIR, C> : DftComposite<4, 3, DIR, C> {};
 template <int DIR, typename C> struct Dft<16, DIR, C> : DftComposite<4, 4, DIR, C> {};
