@@ -671,6 +671,7 @@ template <typename T> ns_status plain_alloc(ns_ctx *c, Run &r) {
     }
     NS_CK(cudaMemsetAsync(r.un, 0, nc * half, c->stream));
     NS_CK(cudaMemsetAsync(r.u1, 0, nc * half, c->stream));
+    NS_CK(cudaMemsetAsync(r.wn, 0, nc * half, c->stream));   // modes a pruned curl never writes
     // factor tables, computed in FP64 and rounded once: by integer |k|^2 on a
     // unit box; elsewhere per axis by array position [N_x | N_y | N_z/2+1]
     auto factors = [&](double c, std::vector<T> &h) {
@@ -756,13 +757,17 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
     const Grid &g = r.g;
     T *phys = (T *)r.phys;
     const long M3 = 3 * r.M, V3 = 3 * r.V;
+    // the pointwise kernels may skip the modes outside the kept rectangle only
+    // where every transform that reads their output is pruned: the FP64 path
+    // (FP32 transforms of compiled lengths read every mode)
+    const Rect rc{r.prune.on && std::is_same<T, double>::value ? 1 : 0, r.prune.kx, r.prune.ky, r.prune.kz};
     for (int stage = 1; stage <= 2 && r.p.mhd; stage++) {
         // MHD (Alfven units): [u; b] -> w = curl u, j = curl b -> u, w, b, j on the
         // grid -> u x w + j x b, u x b -> their transforms -> the two updates
         C *src = (C *)(stage == 1 ? r.un : r.u1);
         C *wj = (C *)r.wn;
-        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, wj, g, s)));
-        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src + M3, wj + M3, g, s)));
+        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, wj, g, rc, s)));
+        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src + M3, wj + M3, g, rc, s)));
         NS_CK(c2r_batch<T>(src, (C *)r.work, phys, g, 3, f, s, tr, &r.prune));
         NS_CK(c2r_batch<T>(wj, (C *)r.work, phys + V3, g, 3, f, s, tr, &r.prune));
         NS_CK(c2r_batch<T>(src + M3, (C *)r.work, phys + 2 * V3, g, 3, f, s, tr, &r.prune));
@@ -772,15 +777,15 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
         NS_CK(r2c_batch<T>(phys + V3, wj + M3, g, 3, f, s, tr, &r.prune));
         const UpdateArgs ua = update_args(r, stage);
         NS_CK(NSK_TIMED(tr, "update",
-                        plain_update<T>((C *)r.un, (C *)r.u1, (const C *)wj, (const T *)r.etab, g, ua, s)));
+                        plain_update<T>((C *)r.un, (C *)r.u1, (const C *)wj, (const T *)r.etab, g, ua, rc, s)));
         NS_CK(NSK_TIMED(tr, "update_b",
                         plain_update_b<T>((C *)r.un + M3, (C *)r.u1 + M3, (const C *)wj + M3,
                                           (const T *)r.etab_b, g, stage, r.p.dt,
-                                          r.p.dealias, s)));
+                                          r.p.dealias, rc, s)));
     }
     for (int stage = 1; stage <= 2 && !r.p.mhd; stage++) {
         C *src = (C *)(stage == 1 ? r.un : r.u1);
-        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, (C *)r.wn, g, s)));
+        NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(src, (C *)r.wn, g, rc, s)));
         NS_CK(c2r_batch<T>(src, (C *)r.work, phys, g, 3, f, s, tr, &r.prune));
         NS_CK(c2r_batch<T>((C *)r.wn, (C *)r.work, phys + 3 * r.V, g, 3, f, s, tr, &r.prune));
         NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, g, s)));
@@ -788,7 +793,7 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
         if (r.p.dealias == 2) {   // the same on the grid shifted by half a spacing, averaged
             C *sh = (C *)r.sh, *sh2 = (C *)r.sh2;
             NS_CK(NSK_TIMED(tr, "phase", plain_phase<T>(src, sh, (const C *)r.phtab, g, s)));
-            NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(sh, sh2, g, s)));
+            NS_CK(NSK_TIMED(tr, "curl", plain_curl<T>(sh, sh2, g, rc, s)));
             NS_CK(c2r_batch<T>(sh, (C *)r.work, phys, g, 3, f, s, tr, &r.prune));
             NS_CK(c2r_batch<T>(sh2, (C *)r.work, phys + 3 * r.V, g, 3, f, s, tr, &r.prune));
             NS_CK(NSK_TIMED(tr, "cross", plain_cross<T>(phys, phys + 3 * r.V, g, s)));
@@ -797,9 +802,9 @@ template <typename T> ns_status plain_step(ns_ctx *c, Run &r, cudaStream_t s, Tr
         }
         const UpdateArgs ua = update_args(r, stage);
         NS_CK(NSK_TIMED(tr, "update",
-                        plain_update<T>((C *)r.un, (C *)r.u1, (const C *)r.wn, (const T *)r.etab, g, ua, s)));
+                        plain_update<T>((C *)r.un, (C *)r.u1, (const C *)r.wn, (const T *)r.etab, g, ua, rc, s)));
     }
-    NS_CK(NSK_TIMED(tr, "energy_partials", plain_energy_partials<T>((const C *)r.un, g, r.part, s)));
+    NS_CK(NSK_TIMED(tr, "energy_partials", plain_energy_partials<T>((const C *)r.un, g, r.part, rc, s)));
     NS_CK(NSK_TIMED(tr, "energy_final",
                     energy_final(r.part, r.nparts, r.series, kSeriesCap, r.counter, c->flags, s)));
     return NS_OK;

@@ -71,4 +71,26 @@ __host__ __device__ __forceinline__ bool kept(const Idx &k, const Grid &g, int d
     return true;
 }
 
+// The rectangle |m_x| <= kx, |m_y| <= ky, m_z <= kz of the half layout that
+// holds every mode a run's rule keeps (on = 0: the whole layout).  Its size
+// stays below 2^31 for every supported grid.
+struct Rect {
+    int on, kx, ky, kz;
+};
+__host__ __device__ __forceinline__ long rect_size(const Rect &r, const Grid &g) {
+    return r.on ? (long)(2 * r.kx + 1) * (2 * r.ky + 1) * (r.kz + 1) : g.M();
+}
+// Half-layout position of entry i of the rectangle (i itself when off).
+__device__ __forceinline__ long rect_at(long i, const Rect &r, const Grid &g) {
+    if (!r.on) return i;
+    const unsigned mz = r.kz + 1, my = 2 * r.ky + 1, ui = (unsigned)i;
+    const unsigned z = ui % mz, t = ui / mz, iy = t % my, ix = t / my;
+    const long x = ix <= (unsigned)r.kx ? (long)ix : (long)ix - (2 * r.kx + 1) + g.nx;
+    const long y = iy <= (unsigned)r.ky ? (long)iy : (long)iy - my + g.ny;
+    return (x * g.ny + y) * g.nzh() + z;
+}
+__device__ __forceinline__ bool in_rect(const Idx &q, const Rect &r) {
+    return !r.on || (abs(q.x) <= r.kx && abs(q.y) <= r.ky && q.z <= r.kz);
+}
+
 }  // namespace nsk

@@ -108,12 +108,15 @@ __device__ __forceinline__ unsigned long long cbits(float2 a, float2 b, float2 c
 // The state is zero outside the kept set (every dealiasing rule); there the
 // curl is written as zeros without arithmetic, which on GB300's slow FP64
 // pipe is most of this kernel's time (about 70 % of the half-layout modes lie
-// outside the 2/3 cube).
+// outside the 2/3 cube).  With the rectangle on, only its modes are read and
+// written (the transforms that follow read no others).
 template <typename T, bool UNIT>
 __global__ void k_curl(const typename Cx<T>::type *__restrict__ a, typename Cx<T>::type *__restrict__ w,
-                       Grid g, long M) {
+                       Grid g, long M, Rect rc) {
     typedef typename Cx<T>::type C;
-    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+    const long cnt = rect_size(rc, g);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < cnt; i += (long)gridDim.x * blockDim.x) {
+        const long m = rect_at(i, rc, g);
         const C ax = a[m], ay = a[M + m], az = a[2 * M + m];
         if (cbits(ax, ay, az) == 0) {
             w[m] = w[M + m] = w[2 * M + m] = czero<C>();
@@ -192,12 +195,14 @@ __device__ __forceinline__ void abc_forcing(const Idx &k, const UpdateArgs &ua, 
 template <typename T, bool UNIT>
 __global__ void k_update(typename Cx<T>::type *__restrict__ a, typename Cx<T>::type *__restrict__ a1,
                          const typename Cx<T>::type *__restrict__ nl, const T *__restrict__ etab,
-                         Grid g, long M, UpdateArgs ua) {
+                         Grid g, long M, UpdateArgs ua, Rect rc) {
     typedef typename Cx<T>::type C;
     const double vol = (double)g.nx * g.ny * g.nz;
     const T gdt = (T)(ua.dt / vol), dt = (T)ua.dt, F = (T)ua.force_amp;
     const T rn = (T)(2.0 * ua.rot * vol);   // the Coriolis factor in the units of nl
-    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+    const long cnt = rect_size(rc, g);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < cnt; i += (long)gridDim.x * blockDim.x) {
+        const long m = rect_at(i, rc, g);
         const Idx q = mode_at(m, g);
         const Wave<T, UNIT> k(q, g);
         C o0 = czero<C>(), o1 = czero<C>(), o2 = czero<C>();
@@ -246,11 +251,13 @@ __global__ void k_update(typename Cx<T>::type *__restrict__ a, typename Cx<T>::t
 template <typename T, bool UNIT>
 __global__ void k_update_b(typename Cx<T>::type *__restrict__ b, typename Cx<T>::type *__restrict__ b1,
                            const typename Cx<T>::type *__restrict__ nb, const T *__restrict__ etab,
-                           Grid g, long M, int stage, double dt_, int dealias) {
+                           Grid g, long M, int stage, double dt_, int dealias, Rect rc) {
     typedef typename Cx<T>::type C;
     const T inv = (T)(1.0 / ((double)g.nx * g.ny * g.nz));
     const T dt = (T)dt_;
-    for (long m = blockIdx.x * (long)blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+    const long cnt = rect_size(rc, g);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < cnt; i += (long)gridDim.x * blockDim.x) {
+        const long m = rect_at(i, rc, g);
         const Idx q = mode_at(m, g);
         const Wave<T, UNIT> k(q, g);
         C o0 = czero<C>(), o1 = czero<C>(), o2 = czero<C>();
@@ -324,12 +331,14 @@ __global__ void k_phase_avg(typename Cx<T>::type *__restrict__ acc, const typena
 // owns the contiguous chunk [b*chunk, (b+1)*chunk) of modes.
 template <typename T, bool UNIT>
 __global__ void __launch_bounds__(256)
-k_energy_partials(const typename Cx<T>::type *__restrict__ a, Grid g, long M, long chunk, double *part) {
+k_energy_partials(const typename Cx<T>::type *__restrict__ a, Grid g, long M, long chunk, double *part,
+                  Rect rc) {
     __shared__ double sh[512];
     double e = 0.0, om = 0.0;
     const long beg = blockIdx.x * chunk, end = min(M, beg + chunk);
     for (long m = beg + threadIdx.x; m < end; m += blockDim.x) {
         const Idx q = mode_at(m, g);
+        if (!in_rect(q, rc)) continue;   // zero there: the sums, in the same order, are unchanged
         const Wave<double, UNIT> k(q, g);
         const double w = (q.z == 0 || 2 * q.z == g.nz) ? 0.5 : 1.0;   // 1/2 * multiplicity
         double a2 = 0.0;
@@ -480,10 +489,12 @@ static unsigned grid_for(long work, int threads) {
 }
 
 template <typename T>
-cudaError_t plain_curl(const typename Cx<T>::type *a, typename Cx<T>::type *w, const Grid &g, cudaStream_t s) {
-    const long M = g.M();
-    if (g.unit) k_curl<T, true><<<grid_for(M, 256), 256, 0, s>>>(a, w, g, M);
-    else k_curl<T, false><<<grid_for(M, 256), 256, 0, s>>>(a, w, g, M);
+cudaError_t plain_curl(const typename Cx<T>::type *a, typename Cx<T>::type *w, const Grid &g, const Rect &rc,
+                       cudaStream_t s) {
+    const long M = g.M(), cnt = rect_size(rc, g);
+    if (cnt > 0x7fffffffL) return cudaErrorInvalidValue;
+    if (g.unit) k_curl<T, true><<<grid_for(cnt, 256), 256, 0, s>>>(a, w, g, M, rc);
+    else k_curl<T, false><<<grid_for(cnt, 256), 256, 0, s>>>(a, w, g, M, rc);
     return cudaGetLastError();
 }
 
@@ -504,12 +515,13 @@ cudaError_t plain_cross_mhd(T *f, const Grid &g, cudaStream_t s) {
 template <typename T>
 cudaError_t plain_update_b(typename Cx<T>::type *b, typename Cx<T>::type *b1,
                            const typename Cx<T>::type *nb, const T *etab, const Grid &g, int stage,
-                           double dt, int dealias, cudaStream_t s) {
-    const long M = g.M();
+                           double dt, int dealias, const Rect &rc, cudaStream_t s) {
+    const long M = g.M(), cnt = rect_size(rc, g);
+    if (cnt > 0x7fffffffL) return cudaErrorInvalidValue;
     if (g.unit)
-        k_update_b<T, true><<<grid_for(M, 256), 256, 0, s>>>(b, b1, nb, etab, g, M, stage, dt, dealias);
+        k_update_b<T, true><<<grid_for(cnt, 256), 256, 0, s>>>(b, b1, nb, etab, g, M, stage, dt, dealias, rc);
     else
-        k_update_b<T, false><<<grid_for(M, 256), 256, 0, s>>>(b, b1, nb, etab, g, M, stage, dt, dealias);
+        k_update_b<T, false><<<grid_for(cnt, 256), 256, 0, s>>>(b, b1, nb, etab, g, M, stage, dt, dealias, rc);
     return cudaGetLastError();
 }
 
@@ -532,10 +544,11 @@ cudaError_t plain_phase_avg(typename Cx<T>::type *acc, const typename Cx<T>::typ
 template <typename T>
 cudaError_t plain_update(typename Cx<T>::type *a, typename Cx<T>::type *a1,
                          const typename Cx<T>::type *nl, const T *etab, const Grid &g,
-                         const UpdateArgs &ua, cudaStream_t s) {
-    const long M = g.M();
-    if (g.unit) k_update<T, true><<<grid_for(M, 256), 256, 0, s>>>(a, a1, nl, etab, g, M, ua);
-    else k_update<T, false><<<grid_for(M, 256), 256, 0, s>>>(a, a1, nl, etab, g, M, ua);
+                         const UpdateArgs &ua, const Rect &rc, cudaStream_t s) {
+    const long M = g.M(), cnt = rect_size(rc, g);
+    if (cnt > 0x7fffffffL) return cudaErrorInvalidValue;
+    if (g.unit) k_update<T, true><<<grid_for(cnt, 256), 256, 0, s>>>(a, a1, nl, etab, g, M, ua, rc);
+    else k_update<T, false><<<grid_for(cnt, 256), 256, 0, s>>>(a, a1, nl, etab, g, M, ua, rc);
     return cudaGetLastError();
 }
 
@@ -546,13 +559,13 @@ int energy_nparts(long M) {
 }
 
 template <typename T>
-cudaError_t plain_energy_partials(const typename Cx<T>::type *a, const Grid &g, double *part,
+cudaError_t plain_energy_partials(const typename Cx<T>::type *a, const Grid &g, double *part, const Rect &rc,
                                   cudaStream_t s) {
     const long M = g.M();
     const int np = energy_nparts(M);
     const long chunk = (M + np - 1) / np;
-    if (g.unit) k_energy_partials<T, true><<<np, 256, 0, s>>>(a, g, M, chunk, part);
-    else k_energy_partials<T, false><<<np, 256, 0, s>>>(a, g, M, chunk, part);
+    if (g.unit) k_energy_partials<T, true><<<np, 256, 0, s>>>(a, g, M, chunk, part, rc);
+    else k_energy_partials<T, false><<<np, 256, 0, s>>>(a, g, M, chunk, part, rc);
     return cudaGetLastError();
 }
 
@@ -581,7 +594,8 @@ cudaError_t energy_final(const double *part, int nparts, double *series, int cap
 }
 
 #define NSK_INST(T)                                                                                \
-    template cudaError_t plain_curl<T>(const Cx<T>::type *, Cx<T>::type *, const Grid &, cudaStream_t); \
+    template cudaError_t plain_curl<T>(const Cx<T>::type *, Cx<T>::type *, const Grid &, const Rect &,   \
+                                       cudaStream_t);                                             \
     template cudaError_t plain_cross<T>(T *, const T *, const Grid &, cudaStream_t);              \
     template cudaError_t plain_cross_mhd<T>(T *, const Grid &, cudaStream_t);                     \
     template cudaError_t plain_phase<T>(const Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,  \
@@ -589,11 +603,13 @@ cudaError_t energy_final(const double *part, int nparts, double *series, int cap
     template cudaError_t plain_phase_avg<T>(Cx<T>::type *, const Cx<T>::type *, const Cx<T>::type *, \
                                             const Grid &, cudaStream_t);                          \
     template cudaError_t plain_update_b<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,     \
-                                           const T *, const Grid &, int, double, int, cudaStream_t); \
+                                           const T *, const Grid &, int, double, int, const Rect &,  \
+                                           cudaStream_t);                                         \
     template cudaError_t plain_update<T>(Cx<T>::type *, Cx<T>::type *, const Cx<T>::type *,       \
-                                         const T *, const Grid &, const UpdateArgs &, cudaStream_t); \
+                                         const T *, const Grid &, const UpdateArgs &, const Rect &, \
+                                         cudaStream_t);                                           \
     template cudaError_t plain_energy_partials<T>(const Cx<T>::type *, const Grid &, double *,    \
-                                                  cudaStream_t);                                  \
+                                                  const Rect &, cudaStream_t);                    \
     template cudaError_t plain_spectrum<T>(const Cx<T>::type *, const Grid &, int, double *, double *, \
                                            cudaStream_t);                                         \
     template cudaError_t plain_helicity<T>(const Cx<T>::type *, const Grid &, int, double *, double *, \

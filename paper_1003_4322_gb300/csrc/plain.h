@@ -21,8 +21,13 @@ struct UpdateArgs {
     double rot;       // rotation rate about z (Coriolis -2 rot z x u)
 };
 
+// rc (the curl, both updates, the energy partials): the rectangle of the
+// half layout outside which the state is zero and which alone the (pruned)
+// transforms read; with rc.on the curl and the updates touch only its modes,
+// and the partials load only its modes (in the same summation order).
 template <typename T>
-cudaError_t plain_curl(const typename Cx<T>::type *a, typename Cx<T>::type *w, const Grid &g, cudaStream_t s);
+cudaError_t plain_curl(const typename Cx<T>::type *a, typename Cx<T>::type *w, const Grid &g, const Rect &rc,
+                       cudaStream_t s);
 template <typename T> cudaError_t plain_cross(T *u, const T *w, const Grid &g, cudaStream_t s);
 // MHD: g = [u, w, b, j] on the grid -> g[0..3) = u x w + j x b, g[3..6) = u x b.
 template <typename T> cudaError_t plain_cross_mhd(T *f, const Grid &g, cudaStream_t s);
@@ -43,14 +48,14 @@ cudaError_t plain_phase_avg(typename Cx<T>::type *acc, const typename Cx<T>::typ
 template <typename T>
 cudaError_t plain_update_b(typename Cx<T>::type *b, typename Cx<T>::type *b1,
                            const typename Cx<T>::type *nb, const T *etab, const Grid &g, int stage,
-                           double dt, int dealias, cudaStream_t s);
+                           double dt, int dealias, const Rect &rc, cudaStream_t s);
 template <typename T>
 cudaError_t plain_update(typename Cx<T>::type *a, typename Cx<T>::type *a1,
                          const typename Cx<T>::type *nl, const T *etab, const Grid &g,
-                         const UpdateArgs &ua, cudaStream_t s);
+                         const UpdateArgs &ua, const Rect &rc, cudaStream_t s);
 int energy_nparts(long M);
 template <typename T>
-cudaError_t plain_energy_partials(const typename Cx<T>::type *a, const Grid &g, double *part,
+cudaError_t plain_energy_partials(const typename Cx<T>::type *a, const Grid &g, double *part, const Rect &rc,
                                   cudaStream_t s);
 template <typename T>
 cudaError_t plain_spectrum(const typename Cx<T>::type *a, const Grid &g, int nbins, double *spec,
