@@ -193,6 +193,7 @@ def plain_keep(dims, dealias=0):
 
 PLAIN_KERNELS = ("fft_x_inverse", "fft_x_forward", "fft_y_inverse", "fft_y_forward", "fft_z_c2r",
                  "fft_z_r2c")
+PLAIN_POINTWISE = ("curl", "update", "update_b", "energy_partials")
 
 
 def kernel_model(name, n, prec, keep=None):
@@ -223,18 +224,21 @@ def kernel_model(name, n, prec, keep=None):
     if name in ("fft_c2r_std", "fft_r2c_std"):   # all three passes of three components
         flops = 3 * (ny * nh * 5 * nx * math.log2(nx) + nx * nh * 5 * ny * math.log2(ny) + nx * ny * f_zline)
         return 3 * (M * 2 * es + V * es) + 2 * (2 * 3 * M * 2 * es), flops
+    rect = (2 * kx + 1) * (2 * ky + 1) * (kz + 1) if keep else M   # modes the pruned FP64 form touches
     if name == "curl":
-        return 2 * 3 * M * 2 * es, 3 * M * 6
+        return 2 * 3 * rect * 2 * es, 3 * rect * 6
+    if name == "energy_partials":   # reads three components (of the rectangle, when pruned)
+        return 3 * rect * 2 * es, 3 * rect * 4
     if name == "cross":
         return 9 * V * es, 9 * V
     if name == "cross_mhd":     # reads u, w, b, j; writes u x w + j x b and u x b
         return 18 * V * es, 30 * V
     if name in ("update", "update_b"):
-        # writes three components of every mode; reads the transformed product,
-        # the state (and the stage-1 state at stage 2: 7.5 components on
-        # average) of the kept modes only
+        # writes three components of every mode (of the rectangle, when
+        # pruned); reads the transformed product, the state (and the stage-1
+        # state at stage 2: 7.5 components on average) of the kept modes only
         kept = (2 * ((nx - 1) // 3) + 1) * (2 * ((ny - 1) // 3) + 1) * ((nz - 1) // 3 + 1)
-        return (3 * M + 7.5 * kept) * 2 * es, 3 * kept * 20
+        return (3 * rect + 7.5 * kept) * 2 * es, 3 * kept * 20
     # fused form (cubes only; FP32 complex = 8 bytes; only the kept modes move)
     f_line = 5 * n * math.log2(n)
     K = (n - 1) // 3
@@ -382,7 +386,9 @@ def roofline_of(census, w, prec, census_steps, peaks, sm_mhz, sizes=None):
     # fused form: one launch covers every run of a group (runs of equal N);
     # plain form: one launch per run
     sizes = sizes or [dims_of(w)]
-    plain = name in PLAIN_KERNELS
+    # the plain transforms skip lines in both precisions; the pointwise
+    # kernels keep to the rectangle in FP64 only
+    plain = name in PLAIN_KERNELS or (prec == "fp64" and name in PLAIN_POINTWISE)
     per_size = [kernel_model(name, n, prec, plain_keep(n if not isinstance(n, int) else (n, n, n),
                                                        w.get("dealias", 0)) if plain else None)
                 for n in sizes]
