@@ -239,24 +239,25 @@ def kernel_model(name, n, prec, keep=None):
         # state at stage 2: 7.5 components on average) of the kept modes only
         kept = (2 * ((nx - 1) // 3) + 1) * (2 * ((ny - 1) // 3) + 1) * ((nz - 1) // 3 + 1)
         return (3 * rect + 7.5 * kept) * 2 * es, 3 * kept * 20
-    # fused form (cubes only; FP32 complex = 8 bytes; only the kept modes move)
-    f_line = 5 * n * math.log2(n)
-    K = (n - 1) // 3
-    Mx, Mz = 2 * K + 1, K + 1
-    S = Mx * Mx * Mz            # compact modes per component
-    Ax = Mx * n * Mz            # pass A / D field size
-    Bx = n * n * Mz             # pass B / C field size
+    # fused form (FP32 complex = 8 bytes; only the kept modes move): compact
+    # state [ikx][iky][kz], A / D fields [iky][x][kz], B / C fields [y][x][kz]
+    f_line, f_yline = 5 * nx * math.log2(nx), 5 * ny * math.log2(ny)
+    K, Ky, Kz = (nx - 1) // 3, (ny - 1) // 3, (nz - 1) // 3
+    Mx, My, Mz = 2 * K + 1, 2 * Ky + 1, Kz + 1
+    S = Mx * My * Mz            # compact modes per component
+    Ax = My * nx * Mz           # pass A / D field size
+    Bx = ny * nx * Mz           # pass B / C field size
     cb = 8
     if name == "fused_A_x_inverse_curl":
-        return (3 * S + 6 * Ax) * cb, 6 * Mx * Mz * f_line
+        return (3 * S + 6 * Ax) * cb, 6 * My * Mz * f_line
     if name == "fused_B_y_inverse":
-        return (6 * Ax + 6 * Bx) * cb, 6 * n * Mz * f_line
+        return (6 * Ax + 6 * Bx) * cb, 6 * nx * Mz * f_yline
     if name == "fused_C_z_nonlinear":
-        return (6 * Bx + 3 * Bx) * cb, n * n * (9 * f_zline + 9 * n)
+        return (6 * Bx + 3 * Bx) * cb, nx * ny * (9 * f_zline + 9 * nz)
     if name == "fused_D_y_forward":
-        return (3 * Bx + 3 * Ax) * cb, 3 * n * Mz * f_line
+        return (3 * Bx + 3 * Ax) * cb, 3 * nx * Mz * f_yline
     if name == "fused_E_x_forward":
-        return (3 * Ax + 3 * S) * cb, 3 * Mx * Mz * f_line
+        return (3 * Ax + 3 * S) * cb, 3 * My * Mz * f_line
     if name == "fused_update":
         return 10.5 * S * cb, 3 * S * 30   # reads N, a (and a1 at stage 2), writes 3
     if name == "fused_C_z_mhd":               # reads u, w, b, j; writes u x w + j x b, u x b

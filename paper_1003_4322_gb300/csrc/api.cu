@@ -902,6 +902,18 @@ ns_status check_ctx(ns_ctx *c) {
     return c->sticky;
 }
 
+// Energy spectrum (or, with hel, helicity spectrum) of a fused run on a grid
+// or box: the compact state expanded into the full FP32 half layout in the
+// group's pass-B buffer (the step is stream-ordered before it), then the
+// plain form's shell kernels on the run's grid.
+cudaError_t fused_grid_spectrum(ns_ctx *c, const Run &r, int field, int nb, double *spec, double *aux, bool hel) {
+    FusedRun &g = c->groups[r.group];
+    cudaError_t e = fused_expand(g, r.gidx, field, g.bbuf, c->stream);
+    if (e != cudaSuccess) return e;
+    return hel ? plain_helicity<float>(g.bbuf, r.g, nb, spec, aux, c->stream)
+               : plain_spectrum<float>(g.bbuf, r.g, nb, spec, aux, c->stream);
+}
+
 ns_status check_flags(ns_ctx *c) {
     int h = 0;
     NS_CK(cudaMemcpy(&h, c->flags, sizeof(int), cudaMemcpyDeviceToHost));
@@ -944,9 +956,11 @@ ns_status ns_describe_run(ns_ctx *c, int run, char *out, int len) {
         char tune[2048];
         if (fused_describe(g, tune, sizeof(tune)) >= (int)sizeof(tune)) return NS_ERR_ARG;
         w = snprintf(out, len,
-                 "{\"form\": \"fused FP32\", \"equations\": \"%s\", \"n\": %d, \"K\": %d, "
+                 "{\"form\": \"fused FP32\", \"equations\": \"%s\", \"n\": %d, \"grid\": [%d, %d, %d], "
+                 "\"box\": [%.17g, %.17g, %.17g], \"K\": %d, \"K_yz\": [%d, %d], "
                  "\"state_modes\": %ld, \"runs_in_group\": %d, \"passes\": %s}",
-                 g.mhd ? "MHD" : "Navier-Stokes", r.n, g.K, (g.mhd ? 6 : 3) * g.M, g.nr, tune);
+                 g.mhd ? "MHD" : "Navier-Stokes", r.n, g.n, g.ny, g.nz, r.g.lx, r.g.ly, r.g.lz, g.K, g.Ky, g.Kz,
+                 (g.mhd ? 6 : 3) * g.M, g.nr, tune);
     } else {
         // plans of the x pass (and the y pass of a cube) and of the z passes
         const auto it = c->fft.find(r.n);
@@ -999,7 +1013,8 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
     c->prec = prec;
     c->stream = (cudaStream_t)cuda_stream;
     for (int i = 0; i < nruns; i++)
-        if ((runs[i].mhd && !fused_mhd_supported(runs[i].n)) || runs[i].dealias == 2 || !run_grid(runs[i]).cube)
+        if ((runs[i].mhd && !fused_mhd_supported(runs[i].n)) || runs[i].dealias == 2 ||
+            !fused_grid_supported(runs[i]))
             c->plain_only = true;
     ns_status st = NS_OK;
     auto bail = [&](ns_status s) {
@@ -1034,12 +1049,15 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
         cudaMemset(r.counter, 0, sizeof(unsigned long long));
     }
     if (use_fused(c)) {
-        // runs of the same N and equations form one group (in order of first
-        // appearance); an MHD group carries a magnetic block beside the velocity
-        std::vector<std::pair<int, int>> order;
-        std::map<std::pair<int, int>, std::vector<int>> members;
+        // runs of the same grid, box and equations form one group (in order of
+        // first appearance); an MHD group carries a magnetic block beside the
+        // velocity
+        typedef std::tuple<int, int, int, double, double, double, int> GKey;
+        std::vector<GKey> order;
+        std::map<GKey, std::vector<int>> members;
         for (int i = 0; i < nruns; i++) {
-            const std::pair<int, int> key(c->runs[i].n, c->runs[i].p.mhd);
+            const Grid &g = c->runs[i].g;
+            const GKey key(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, c->runs[i].p.mhd);
             if (!members.count(key)) order.push_back(key);
             members[key].push_back(i);
         }
@@ -1047,9 +1065,10 @@ ns_status ns_init(const ns_run_params *runs, int nruns, ns_prec prec, void *cuda
         for (size_t gi = 0; gi < order.size(); gi++) {
             std::vector<ns_run_params> ps;
             for (int i : members[order[gi]]) ps.push_back(c->runs[i].p);
-            FftRes *f;
-            if ((st = get_fft(c, order[gi].first, &f)) != NS_OK) return bail(st);
-            e = fused_alloc(c->groups[gi], ps, (const float2 *)f->tw, kSeriesCap, c->stream);
+            FftRes *f[3];
+            if ((st = get_fft3(c, c->runs[members[order[gi]][0]].g, f)) != NS_OK) return bail(st);
+            e = fused_alloc(c->groups[gi], ps, (const float2 *)f[0]->tw, (const float2 *)f[1]->tw,
+                            (const float2 *)f[2]->tw, kSeriesCap, c->stream);
             if (e != cudaSuccess) return bail(fail_cuda(nullptr, e));
             const std::vector<int> &mem = members[order[gi]];
             for (size_t j = 0; j < mem.size(); j++) {
@@ -1325,8 +1344,10 @@ ns_status ns_field_spectrum(ns_ctx *c, int run, int field, double *spec, int nbi
     if (field != 0 && !(field == 1 && r.p.mhd)) return NS_ERR_ARG;
     const int nb = grid_nbins(r.g);
     const long off = (long)field * 3 * r.M;
-    if (use_fused(c))
+    if (use_fused(c) && c->groups[r.group].cube)
         NS_CK(fused_spectrum(c->groups[r.group], r.gidx, field, nb, c->spec, c->ens, c->stream));
+    else if (use_fused(c))   // a grid or box: the shells of the plain form on the expanded state
+        NS_CK(fused_grid_spectrum(c, r, field, nb, c->spec, c->ens, false));
     else if (c->prec == NS_FP64)
         NS_CK(plain_spectrum<double>((const double2 *)r.un + off, r.g, nb, c->spec, c->ens, c->stream));
     else
@@ -1372,8 +1393,10 @@ ns_status ns_energy_spectra(ns_ctx *c, int first, int count, double *spec, int n
         Run &r = c->runs[first + i];
         const int nb = grid_nbins(r.g);
         double *sp = c->bspec + 2 * slice * i, *en = sp + slice;
-        if (use_fused(c))
+        if (use_fused(c) && c->groups[r.group].cube)
             NS_CK(fused_spectrum(c->groups[r.group], r.gidx, 0, nb, sp, en, c->stream));
+        else if (use_fused(c))
+            NS_CK(fused_grid_spectrum(c, r, 0, nb, sp, en, false));
         else if (c->prec == NS_FP64)
             NS_CK(plain_spectrum<double>((const double2 *)r.un, r.g, nb, sp, en, c->stream));
         else
@@ -1438,8 +1461,10 @@ ns_status ns_helicity(ns_ctx *c, int run, double *spec, int nbins, double *helic
         return NS_ERR_ARG;
     Run &r = c->runs[run];
     const int nb = grid_nbins(r.g);
-    if (use_fused(c))
+    if (use_fused(c) && c->groups[r.group].cube)
         NS_CK(fused_helicity(c->groups[r.group], r.gidx, nb, c->spec, c->ens, c->stream));
+    else if (use_fused(c))
+        NS_CK(fused_grid_spectrum(c, r, 0, nb, c->spec, c->ens, true));
     else if (c->prec == NS_FP64)
         NS_CK(plain_helicity<double>((const double2 *)r.un, r.g, nb, c->spec, c->ens, c->stream));
     else

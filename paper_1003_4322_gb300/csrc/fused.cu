@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <string>
 #include <mutex>
 #include <vector>
@@ -148,7 +149,9 @@ k_fused_z(float2 *buf, long fs, int N, int Mz, long nlines, int L, long brun, Pl
 }
 
 // Two modes per thread and iteration, every operand load issued before any
-// arithmetic, so that enough bytes are in flight to stream HBM.
+// arithmetic, so that enough bytes are in flight to stream HBM.  GRID: the
+// state of a grid or box (fz_update_mode_grid).
+template <bool GRID>
 __global__ void __launch_bounds__(256)
 k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__restrict__ nl,
                const float *__restrict__ etab, const FzRunParams *__restrict__ rp, FzUpdate u,
@@ -186,12 +189,20 @@ k_fused_update(float2 *__restrict__ a, float2 *__restrict__ a1, const float2 *__
         for (int i = 0; i < 2; i++) {
             if (i == 1 && !has1) break;
             const long m = i ? m1 : m0;
-            const FzMode r = fz_update_mode(m, u, q, etab, inv, v[i][0], v[i][1], v[i][2], b[i][0],
-                                            b[i][1], b[i][2], c[i][0], c[i][1], c[i][2]);
+            FzMode r;
+            if constexpr (GRID)
+                r = fz_update_mode_grid(m, u, q, etab, v[i][0], v[i][1], v[i][2], b[i][0], b[i][1], b[i][2],
+                                        c[i][0], c[i][1], c[i][2]);
+            else
+                r = fz_update_mode(m, u, q, etab, inv, v[i][0], v[i][1], v[i][2], b[i][0], b[i][1], b[i][2],
+                                   c[i][0], c[i][1], c[i][2]);
             dst[m] = r.o0;
             dst[M + m] = r.o1;
             dst[2 * M + m] = r.o2;
-            if (two) fz_accumulate(r, e_acc, o_acc);
+            if (two) {
+                if constexpr (GRID) fz_accumulate_grid(r, e_acc, o_acc);
+                else fz_accumulate(r, e_acc, o_acc);
+            }
         }
     }
     if (two) {
@@ -232,45 +243,58 @@ k_fz_energy_final(const double *__restrict__ part, int nparts, double *series, i
 
 // ---------------------------------------------------------------- state transfer
 
-// cnt full kx planes starting at kx0 (FP64 half layout, plane = n (n/2+1)
+// The half layout [N_x][N_y][N_z/2+1] and the compact one of a group: the
+// axis lengths, the kept |m| and compact rows along x and y, the kept kz,
+// and the sphere of the spherical rule in integers (D = lcm N_i, q_i = D / N_i).
+struct FzHalfGeom {
+    int nx, ny, nz, K, Ky, Mx, My, Mz;
+    long D, qx, qy, qz;
+};
+static FzHalfGeom half_geom(const FusedRun &f) {
+    return FzHalfGeom{f.n, f.ny, f.nz, f.K, f.Ky, f.Mx, f.My, f.Mz, f.D, f.qx, f.qy, f.qz};
+}
+
+// cnt full kx planes starting at kx0 (FP64 half layout, plane = N_y (N_z/2+1)
 // modes) -> compact rows; modes outside the sphere (dealias = 1) dropped.
 __global__ void k_fz_load(const double2 *__restrict__ src, float2 *__restrict__ dst, int kx0, int cnt,
-                          int n, int K, int Mx, int Mz, int dealias) {
-    const int nh = n / 2 + 1;
-    const long total = (long)cnt * Mx * Mz;
+                          FzHalfGeom g, int dealias) {
+    const int nh = g.nz / 2 + 1;
+    const long total = (long)cnt * g.My * g.Mz;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-        const int kz = (int)(i % Mz);
-        const int iky = (int)((i / Mz) % Mx);
-        const int p = (int)(i / ((long)Mz * Mx));
+        const int kz = (int)(i % g.Mz);
+        const int iky = (int)((i / g.Mz) % g.My);
+        const int p = (int)(i / ((long)g.Mz * g.My));
         const int fx = kx0 + p;
-        const int ikx = fz_compact(fx, n, K, Mx);
+        const int ikx = fz_compact(fx, g.nx, g.K, g.Mx);
         if (ikx < 0) continue;
-        const int ky = fz_compact_signed(iky, Mx, K);
-        const int fy = ky >= 0 ? ky : ky + n;
-        const int kx = fz_full_signed(fx, n);
-        double2 v = src[(long)p * n * nh + (long)fy * nh + kz];
-        if (dealias == 1 && 9L * (kx * kx + ky * ky + kz * kz) >= (long)n * n) v = make_double2(0.0, 0.0);
-        dst[((long)ikx * Mx + iky) * Mz + kz] = make_float2((float)v.x, (float)v.y);
+        const int ky = fz_compact_signed(iky, g.My, g.Ky);
+        const int fy = ky >= 0 ? ky : ky + g.ny;
+        const int kx = fz_full_signed(fx, g.nx);
+        double2 v = src[(long)p * g.ny * nh + (long)fy * nh + kz];
+        const long ax = kx * g.qx, ay = ky * g.qy, az = kz * g.qz;
+        if (dealias == 1 && 9 * (ax * ax + ay * ay + az * az) >= g.D * g.D) v = make_double2(0.0, 0.0);
+        dst[((long)ikx * g.My + iky) * g.Mz + kz] = make_float2((float)v.x, (float)v.y);
     }
 }
 
-// compact -> cnt full kx planes starting at kx0 (zeros outside the kept set)
-__global__ void k_fz_store(const float2 *__restrict__ src, double2 *__restrict__ dst, int kx0, int cnt,
-                           int n, int K, int Mx, int Mz) {
-    const int nh = n / 2 + 1;
-    const long total = (long)cnt * n * nh;
+NSK_DEV void fz_put(double2 *d, float2 v) { *d = make_double2((double)v.x, (double)v.y); }
+NSK_DEV void fz_put(float2 *d, float2 v) { *d = v; }
+
+// compact -> cnt full kx planes starting at kx0 (zeros outside the kept set),
+// FP64 (state transfer) or FP32 (the input of the grid spectra)
+template <typename D2>
+__global__ void k_fz_store(const float2 *__restrict__ src, D2 *__restrict__ dst, int kx0, int cnt, FzHalfGeom g) {
+    const int nh = g.nz / 2 + 1;
+    const long total = (long)cnt * g.ny * nh;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
         const int kz = (int)(i % nh);
-        const int fy = (int)((i / nh) % n);
-        const int p = (int)(i / ((long)nh * n));
-        const int ikx = fz_compact(kx0 + p, n, K, Mx);
-        const int iky = fz_compact(fy, n, K, Mx);
-        double2 v = make_double2(0.0, 0.0);
-        if (ikx >= 0 && iky >= 0 && kz < Mz) {
-            const float2 s = src[((long)ikx * Mx + iky) * Mz + kz];
-            v = make_double2((double)s.x, (double)s.y);
-        }
-        dst[i] = v;
+        const int fy = (int)((i / nh) % g.ny);
+        const int p = (int)(i / ((long)nh * g.ny));
+        const int ikx = fz_compact(kx0 + p, g.nx, g.K, g.Mx);
+        const int iky = fz_compact(fy, g.ny, g.Ky, g.My);
+        float2 v = make_float2(0.f, 0.f);
+        if (ikx >= 0 && iky >= 0 && kz < g.Mz) v = src[((long)ikx * g.My + iky) * g.Mz + kz];
+        fz_put(dst + i, v);
     }
 }
 
@@ -467,9 +491,9 @@ static ZrCtl zr_ctl(const FusedRun &f) {
 
 static cudaError_t launch_zr(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
     ZctKernel z;
-    if (!zr_lookup(f.n, cfg.pl.E, cfg.ct, &z) || f.Mz != (f.n - 1) / 3 + 1) return cudaErrorInvalidValue;
-    long nlines = (long)f.n * f.n;
-    long fs = (long)f.n * f.n * f.Mz;
+    if (!zr_lookup(f.nz, cfg.pl.E, cfg.ct, &z) || f.Mz != (f.nz - 1) / 3 + 1) return cudaErrorInvalidValue;
+    long nlines = (long)f.n * f.ny;
+    long fs = (long)f.n * f.ny * f.Mz;
     long brun = f.sB;
     if (z.bulk_bytes) {
         // bulk copies: every copy starts on a 16-byte boundary and moves a
@@ -488,7 +512,7 @@ static cudaError_t launch_zr(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
     const long per_run = resident_blocks(z.k, z.threads, z.smem) / f.nr;
     if (per_run >= 1 && blocks > per_run) blocks = per_run;
     float2 *buf = f.bbuf;
-    const float2 *tw = f.tw;
+    const float2 *tw = f.twz;
     ZrCtl ctl = zr_ctl(f);
     void *args[] = {(void *)&buf, (void *)&fs, (void *)&nlines, (void *)&brun, (void *)&tw, (void *)&ctl};
     return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem,
@@ -497,16 +521,16 @@ static cudaError_t launch_zr(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
 
 static cudaError_t launch_z_ct(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
     ZctKernel z;
-    if (!zct_lookup(f.n, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
+    if (!zct_lookup(f.nz, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(z.k, z.smem);
     if (e != cudaSuccess) return e;
-    long nlines = (long)f.n * f.n;
+    long nlines = (long)f.n * f.ny;
     const long blocks = (nlines + z.lines_per_block - 1) / z.lines_per_block;
     float2 *buf = f.bbuf;
-    long fs = (long)f.n * f.n * f.Mz;
+    long fs = (long)f.n * f.ny * f.Mz;
     int Mz = f.Mz;
     long brun = f.sB;
-    const float2 *tw = f.tw;
+    const float2 *tw = f.twz;
     void *args[] = {(void *)&buf, (void *)&fs, (void *)&Mz, (void *)&nlines, (void *)&brun, (void *)&tw};
     return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem,
                             s);
@@ -517,19 +541,19 @@ static cudaError_t launch_z(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
     if (cfg.kind == 2) return launch_zr(f, cfg, s);
     const void *k = z_for(cfg.pl.E);
     if (!k) return cudaErrorInvalidValue;
-    const int n = f.n / 2, Tn = n / cfg.pl.E;
+    const int n = f.nz / 2, Tn = n / cfg.pl.E;
     const int L = cfg.ct;
-    if (L < 1 || 6 * L * Tn > 256) return cudaErrorInvalidValue;
+    if (L < 1 || 6 * L * Tn > 256 || cfg.pl.n != n) return cudaErrorInvalidValue;
     const size_t smem = (size_t)6 * L * fz_line_stride(n) * sizeof(float2);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
-    const long nlines = (long)f.n * f.n;
+    const long nlines = (long)f.n * f.ny;
     const long blocks = (nlines + L - 1) / L;
     float2 *buf = f.bbuf;
-    long fs = (long)f.n * f.n * f.Mz;
-    int N = f.n, Mz = f.Mz;
+    long fs = (long)f.n * f.ny * f.Mz;
+    int N = f.nz, Mz = f.Mz;
     Plan q = cfg.pl;
-    const float2 *tw = f.tw;
+    const float2 *tw = f.twz;
     int LL = L;
     long brun = f.sB;
     void *args[] = {(void *)&buf, (void *)&fs, (void *)&N, (void *)&Mz, (void *)&nlines, (void *)&LL,
@@ -538,34 +562,52 @@ static cudaError_t launch_z(FusedRun &f, const PassCfg &cfg, cudaStream_t s) {
 }
 
 // Pass descriptors of one RK2 stage reading the state src.
+// Layouts: A out [6][iky][x][kz], B out [6][y][x][kz] (pass C in place), D
+// out [3][x][iky][kz], E out compact [3][ikx][iky][kz]; on the cube
+// N_y = N_x = n and My = Mx.
 static void pass_descs(const FusedRun &f, const float2 *src, FzPass &A, FzPass &B, FzPass &D, FzPass &Ep) {
-    const int N = f.n, K = f.K, Mx = f.Mx, Mz = f.Mz;
-    const long MxMz = (long)Mx * Mz, NMz = (long)N * Mz;
+    const int Nx = f.n, Ny = f.ny, K = f.K, Mx = f.Mx, My = f.My, Mz = f.Mz;
+    const long MyMz = (long)My * Mz, NxMz = (long)Nx * Mz;
     const long S3 = 3 * f.M;
-    A = FzPass{src, f.abuf, MxMz, f.M, MxMz, (long)Mx * NMz, Mz, NMz, 6, Mz, K, Mx, S3, f.sA, Mz};
-    B = FzPass{f.abuf, f.bbuf, NMz, (long)Mx * NMz, NMz, (long)N * NMz, NMz, Mz, 6, Mz, K, Mx, f.sA, f.sB, Mz};
-    D = FzPass{f.bbuf, f.abuf, NMz, (long)N * NMz, NMz, (long)N * MxMz, Mz, MxMz, 3, Mz, K, Mx, f.sB, f.sA, Mz};
-    Ep = FzPass{f.abuf, f.nl, MxMz, (long)N * MxMz, MxMz, f.M, MxMz, Mz, 3, Mz, K, Mx, f.sA, S3, Mz};
+    A = FzPass{src, f.abuf, MyMz, f.M, MyMz, (long)My * NxMz, Mz, NxMz, 6, Mz, K, Mx, S3, f.sA, Mz};
+    B = FzPass{f.abuf, f.bbuf, NxMz, (long)My * NxMz, NxMz, (long)Ny * NxMz, NxMz, Mz, 6, Mz, f.Ky, My, f.sA,
+               f.sB, Mz};
+    D = FzPass{f.bbuf, f.abuf, NxMz, (long)Ny * NxMz, NxMz, (long)Nx * MyMz, Mz, MyMz, 3, Mz, f.Ky, My, f.sB,
+               f.sA, Mz};
+    Ep = FzPass{f.abuf, f.nl, MyMz, (long)Nx * MyMz, MyMz, f.M, MyMz, Mz, 3, Mz, K, Mx, f.sA, S3, Mz};
+    if (!f.cube) {   // the curl of pass A: y compaction and the box
+        A.Ko = f.Ky;
+        A.Mo = My;
+        A.sx = f.sx;
+        A.sy = f.sy;
+        A.sz = f.sz;
+    }
 }
 
-static cudaError_t run_pass_ct(FusedRun &f, int which, const PassCfg &cfg, const FzPass &ps,
+// Transform length, twiddle table and default plan of pass 0..3 (A, B, D, E).
+static int pass_len(const FusedRun &f, int pass) { return pass == 1 || pass == 2 ? f.ny : f.n; }
+static const float2 *pass_tw(const FusedRun &f, int pass) { return pass == 1 || pass == 2 ? f.twy : f.tw; }
+static const Plan &pass_plan(const FusedRun &f, int pass) { return pass == 1 || pass == 2 ? f.plY : f.plN; }
+
+static cudaError_t run_pass_ct(FusedRun &f, int pass, const PassCfg &cfg, const FzPass &ps,
                                cudaStream_t s) {
     FzsKernel z;
-    if (!fzs_lookup(which, f.n, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
+    const int which = pass < 2 ? pass : 2;
+    if (!fzs_lookup(which, pass_len(f, pass), cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(z.k, z.smem);
     if (e != cudaSuccess) return e;
     const long tiles = (ps.ncols + cfg.ct - 1) / cfg.ct;
     const long blocks = tiles * ps.nfields;
     if (blocks > 0x7fffffffL) return cudaErrorInvalidValue;
     FzPass p = ps;
-    const float2 *tw = f.tw;
+    const float2 *tw = pass_tw(f, pass);
     void *args[] = {(void *)&p, (void *)&tw};
     return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem, s);
 }
 
 static cudaError_t run_pass_k(FusedRun &f, int pass, const PassCfg &cfg, const FzPass &ps, cudaStream_t s) {
     FzsKernel z;
-    if (!fzk_lookup(pass, f.n, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
+    if (!f.cube || !fzk_lookup(pass, f.n, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(z.k, z.smem);
     if (e != cudaSuccess) return e;
     const long tiles = (ps.ncols + cfg.ct - 1) / cfg.ct;
@@ -581,12 +623,13 @@ static cudaError_t run_pass_k(FusedRun &f, int pass, const PassCfg &cfg, const F
 static cudaError_t run_pass(FusedRun &f, int pass, const PassCfg &cfg, const FzPass &ps, cudaStream_t s) {
     if (cfg.kind == 2) return run_pass_k(f, pass, cfg, ps, s);
     const int which = pass < 2 ? pass : 2;
-    if (cfg.kind == 1) return run_pass_ct(f, which, cfg, ps, s);
+    if (cfg.kind == 1) return run_pass_ct(f, pass, cfg, ps, s);
     const int E = cfg.pl.E;
     const void *k = which == 0 ? strided_for<+1, true, false, true>(E)
                   : which == 1 ? strided_for<+1, true, false, false>(E)
                                : strided_for<-1, false, true, false>(E);
-    return launch_strided(k, ps, cfg.pl, f.tw, cfg.ct, f.nr, s);
+    if (cfg.pl.n != pass_len(f, pass)) return cudaErrorInvalidValue;
+    return launch_strided(k, ps, cfg.pl, pass_tw(f, pass), cfg.ct, f.nr, s);
 }
 
 // Induction update of the MHD form's magnetic block: N_b = i k x nb / N^3
@@ -660,8 +703,28 @@ static cudaError_t launch_zm(FusedRun &f, int E, int wpb, cudaStream_t s) {
 
 // The separate update kernel, u.nparts blocks (partials) per run.
 static cudaError_t launch_update_n(FusedRun &f, const FzUpdate &u, cudaStream_t s) {
-    k_fused_update<<<dim3(u.nparts, f.nr), 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, f.rp, u, f.part);
+    if (f.cube) k_fused_update<false><<<dim3(u.nparts, f.nr), 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, f.rp, u, f.part);
+    else k_fused_update<true><<<dim3(u.nparts, f.nr), 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, f.rp, u, f.part);
     return cudaGetLastError();
+}
+
+// Update arguments of stage `stage` with nparts partial sums per run.
+static FzUpdate make_update(const FusedRun &f, int stage, int nparts) {
+    FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.M, f.nk2, nparts};
+    if (!f.cube) {
+        u.My = f.My;
+        u.Ky = f.Ky;
+        u.inv = (float)(1.0 / ((double)f.n * f.ny * f.nz));
+        u.sx = f.sx;
+        u.sy = f.sy;
+        u.sz = f.sz;
+        u.D = f.D;
+        u.qx = f.qx;
+        u.qy = f.qy;
+        u.qz = f.qz;
+        u.k2tab = f.k2tab;
+    }
+    return u;
 }
 
 // Column tiles (and energy partials per run) of pass E fused with the update.
@@ -675,7 +738,7 @@ static cudaError_t launch_eu(FusedRun &f, int E, int ct, int stage, cudaStream_t
     cudaError_t e = allow_smem(z.k, z.smem);
     if (e != cudaSuccess) return e;
     const long tiles = eu_tiles(f, ct);
-    FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.M, f.nk2, (int)tiles};
+    FzUpdate u = make_update(f, stage, (int)tiles);
     const float2 *din = f.abuf, *tw = f.tw;
     float2 *a = f.a, *a1 = f.a1;
     const float *etab = f.etab;
@@ -859,20 +922,29 @@ static bool pick_best(std::vector<std::pair<float, Cfg>> &cands, TimeOf time_of,
 
 static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
     static std::mutex mu;
-    static std::map<int, TunedCfgs> cache;
+    static std::map<int, TunedCfgs> cache;   // cubes, by N (also in the plan-cache file)
+    static std::map<std::tuple<int, int, int>, TunedCfgs> gcache;   // grids, for the process
     static bool loaded = false;
+    const auto gkey = std::make_tuple(f.n, f.ny, f.nz);
     {
         std::lock_guard<std::mutex> g(mu);
         if (!loaded) {
             plan_cache_read(cache);
             loaded = true;
         }
-        auto it = cache.find(f.n);
-        if (it != cache.end()) {
-            for (int i = 0; i < 4; i++) f.sp[i] = it->second.s[i];
-            f.zc = it->second.c;
-            f.eu_E = it->second.eu_E;
-            f.eu_ct = it->second.eu_ct;
+        const TunedCfgs *hit = nullptr;
+        if (f.cube) {
+            auto it = cache.find(f.n);
+            if (it != cache.end()) hit = &it->second;
+        } else {
+            auto it = gcache.find(gkey);
+            if (it != gcache.end()) hit = &it->second;
+        }
+        if (hit) {
+            for (int i = 0; i < 4; i++) f.sp[i] = hit->s[i];
+            f.zc = hit->c;
+            f.eu_E = hit->eu_E;
+            f.eu_ct = hit->eu_ct;
             return cudaSuccess;
         }
     }
@@ -888,18 +960,19 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
             return time_launch([&]() { return run_pass(f, i, cfg, P[i], s); }, s, r);
         };
         const int Es[] = {8, 12, 16, 32};
-        for (int kind = 2; kind >= 1; kind--)
+        const int len = pass_len(f, i);
+        for (int kind = f.cube ? 2 : 1; kind >= 1; kind--)   // constant-geometry kernels: cubes only
             for (int E : Es)
                 for (int ct = 8; ct <= 16; ct *= 2) {
                     FzsKernel z;
-                    if (kind == 1 ? !fzs_lookup(which[i], f.n, E, ct, &z) : !fzk_lookup(i, f.n, E, ct, &z))
+                    if (kind == 1 ? !fzs_lookup(which[i], len, E, ct, &z) : !fzk_lookup(i, f.n, E, ct, &z))
                         continue;
-                    PassCfg cfg{f.plN, ct, kind};
+                    PassCfg cfg{pass_plan(f, i), ct, kind};
                     cfg.pl.E = E;
                     const float ms = time_of(cfg, reps);
                     if (ms > 0.f) cands.push_back({ms, cfg});
                 }
-        for (const Plan &pl : plan_candidates(f.n)) {
+        for (const Plan &pl : plan_candidates(len)) {
             const int T = pl.n / pl.E;
             for (int ct = 8; ct <= 16; ct *= 2) {
                 if (ct * T > 512 || (ct * T < 32 && ct < 16)) continue;
@@ -919,7 +992,7 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
         for (int zE : zEs)
         for (int wpb = 1; wpb <= 4; wpb *= 2) {
             ZctKernel z;
-            if (!zct_lookup(f.n, zE, wpb, &z)) continue;
+            if (!zct_lookup(f.nz, zE, wpb, &z)) continue;
             PassCfg cfg{f.plH, wpb, 1};
             cfg.pl.E = zE;
             const float ms = time_of(cfg, reps);
@@ -933,13 +1006,13 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
         for (int zE : zrEs)
             for (int tile : zrTiles) {
                 ZctKernel z;
-                if (!zr_lookup(f.n, zE, tile, &z)) continue;
+                if (!zr_lookup(f.nz, zE, tile, &z)) continue;
                 PassCfg cfg{f.plH, tile, 2};
                 cfg.pl.E = zE;
                 const float ms = time_of(cfg, reps);
                 if (ms > 0.f) cands.push_back({ms, cfg});
             }
-        for (const Plan &pl : plan_candidates(f.n / 2)) {
+        for (const Plan &pl : plan_candidates(f.nz / 2)) {
             const int Tn = pl.n / pl.E;
             for (int L = 1; 6 * L * Tn <= 256; L *= 2) {
                 PassCfg cfg{pl, L, 0};
@@ -949,9 +1022,10 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
         }
         if (!pick_best(cands, time_of, &f.zc)) return cudaErrorInvalidValue;
     }
-    // pass E then the update, against pass E fused with the update (stage 2)
-    {
-        FzUpdate u{f.n, f.K, f.Mx, f.Mz, 2, f.M, f.nk2, f.nparts_upd};
+    // pass E then the update, against pass E fused with the update (stage 2;
+    // its kernels are compiled for the cube)
+    if (f.cube) {
+        FzUpdate u = make_update(f, 2, f.nparts_upd);
         const float sep = time_launch([&]() { return run_pass(f, 3, f.sp[3], P[3], s); }, s, reps) +
                           time_launch([&]() { return launch_update_n(f, u, s); }, s, reps);
         float best = sep > 0.f ? sep : -1.f;
@@ -975,32 +1049,82 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
     t.c = f.zc;
     t.eu_E = f.eu_E;
     t.eu_ct = f.eu_ct;
+    if (!f.cube) {
+        gcache[gkey] = t;
+        return cudaSuccess;
+    }
     cache[f.n] = t;
     plan_cache_write(cache);
     return cudaSuccess;
 }
 
+static long gcd_l(long a, long b) { return b ? gcd_l(b, a % b) : a; }
+
+// Grid and box of a run: (N_x, N_y, N_z) and l_i (0 in the parameters: N, 1).
+static void run_dims(const ns_run_params &p, int d[3], double l[3]) {
+    d[0] = p.n;
+    d[1] = p.ny > 0 ? p.ny : p.n;
+    d[2] = p.nz > 0 ? p.nz : p.n;
+    l[0] = p.lx > 0 ? p.lx : 1.0;
+    l[1] = p.ly > 0 ? p.ly : 1.0;
+    l[2] = p.lz > 0 ? p.lz : 1.0;
+}
+
+bool fused_grid_supported(const ns_run_params &p) {
+    int d[3];
+    double l[3];
+    run_dims(p, d, l);
+    const bool cube = d[0] == d[1] && d[0] == d[2] && l[0] == 1.0 && l[1] == 1.0 && l[2] == 1.0;
+    return cube || (!p.mhd && (p.dealias == 0 || p.dealias == 1));
+}
+
 cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, const float2 *tw,
-                        int series_cap, cudaStream_t s) {
+                        const float2 *twy, const float2 *twz, int series_cap, cudaStream_t s) {
     if (runs.empty()) return cudaErrorInvalidValue;
     f.p = runs;
     f.nr = (int)runs.size();
-    f.n = runs[0].n;
-    for (const ns_run_params &q : runs)
-        if (q.n != f.n) return cudaErrorInvalidValue;
-    f.K = (f.n - 1) / 3;     // largest k with 3k < n
+    int d[3];
+    double l[3];
+    run_dims(runs[0], d, l);
+    for (const ns_run_params &q : runs) {
+        int dq[3];
+        double lq[3];
+        run_dims(q, dq, lq);
+        for (int i = 0; i < 3; i++)
+            if (dq[i] != d[i] || lq[i] != l[i]) return cudaErrorInvalidValue;
+    }
+    f.n = d[0];
+    f.ny = d[1];
+    f.nz = d[2];
+    f.unit = l[0] == 1.0 && l[1] == 1.0 && l[2] == 1.0;
+    f.cube = f.unit && f.n == f.ny && f.n == f.nz;
+    f.K = (f.n - 1) / 3;     // largest m with 3m < N_i, per axis
+    f.Ky = (f.ny - 1) / 3;
+    f.Kz = (f.nz - 1) / 3;
     f.Mx = 2 * f.K + 1;
-    f.Mz = f.K + 1;
+    f.My = 2 * f.Ky + 1;
+    f.Mz = f.Kz + 1;
+    f.sx = (float)(1.0 / l[0]);
+    f.sy = (float)(1.0 / l[1]);
+    f.sz = (float)(1.0 / l[2]);
+    f.D = (long)f.n / gcd_l(f.n, f.ny) * f.ny;
+    f.D = f.D / gcd_l(f.D, f.nz) * f.nz;
+    f.qx = f.D / f.n;
+    f.qy = f.D / f.ny;
+    f.qz = f.D / f.nz;
     f.tw = tw;
+    f.twy = f.cube ? tw : twy;
+    f.twz = f.cube ? tw : twz;
     f.cap = series_cap;
-    if (!make_plan(f.n, &f.plN) || !make_plan(f.n / 2, &f.plH)) return cudaErrorInvalidValue;
-    f.M = (long)f.Mx * f.Mx * f.Mz;
-    f.sA = 6L * f.Mx * f.n * f.Mz;          // also holds D (3 fields)
-    f.sB = 6L * f.n * f.n * f.Mz;           // also holds C (3 fields)
+    if (!make_plan(f.n, &f.plN) || !make_plan(f.ny, &f.plY) || !make_plan(f.nz / 2, &f.plH))
+        return cudaErrorInvalidValue;
+    f.M = (long)f.Mx * f.My * f.Mz;
+    f.sA = 6L * f.My * f.n * f.Mz;          // also holds D (3 fields)
+    f.sB = 6L * f.ny * f.n * f.Mz;          // also holds C (3 fields)
     const long S3 = 3 * f.M, nr = f.nr;
     f.mhd = runs[0].mhd != 0;
     for (const ns_run_params &q : runs)
-        if ((q.mhd != 0) != f.mhd) return cudaErrorInvalidValue;
+        if ((q.mhd != 0) != f.mhd || !fused_grid_supported(q)) return cudaErrorInvalidValue;
     const int nb = f.mhd ? 2 : 1;            // blocks: velocity (and magnetic)
     f.blk_s = nr * S3;
     f.blk_A = nr * f.sA;
@@ -1013,18 +1137,47 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     if ((e = dev_malloc((void **)&f.bbuf, nb * nr * f.sB * sizeof(float2))) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(f.a, 0, nb * nr * S3 * sizeof(float2), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(f.a1, 0, nb * nr * S3 * sizeof(float2), s)) != cudaSuccess) return e;
-    // factor tables exp(-nu k^2 dt) in FP64, rounded once, and per-run parameters
-    f.nk2 = 3 * f.K * f.K + 1;
+    // factor tables exp(-nu k^2 dt) in FP64, rounded once (the cube: by integer
+    // k^2; a grid or box: per axis by compact index, exp(-nu (m_i / l_i)^2 dt)),
+    // and per-run parameters
+    f.nk2 = f.cube ? 3 * f.K * f.K + 1 : f.Mx + f.My + f.Mz;
     std::vector<float> h((size_t)nr * f.nk2);
     std::vector<FzRunParams> hp(nr);
     for (long r = 0; r < nr; r++) {
         const ns_run_params &q = runs[r];
-        for (int k2 = 0; k2 < f.nk2; k2++) h[r * f.nk2 + k2] = (float)exp(-q.nu * (double)k2 * q.dt);
-        hp[r] = FzRunParams{(float)q.dt, (float)q.force_amp, q.force_k, q.dealias, (float)q.rot};
+        if (f.cube) {
+            for (int k2 = 0; k2 < f.nk2; k2++) h[r * f.nk2 + k2] = (float)exp(-q.nu * (double)k2 * q.dt);
+        } else {
+            const int Ms[3] = {f.Mx, f.My, f.Mz}, Ks[3] = {f.K, f.Ky, f.Kz};
+            for (int a = 0, o = 0; a < 3; o += Ms[a], a++)
+                for (int i = 0; i < Ms[a]; i++) {
+                    const int m = a < 2 && i > Ks[a] ? i - Ms[a] : i;
+                    const double k = (double)m / l[a];
+                    h[r * f.nk2 + o + i] = (float)exp(-q.nu * k * k * q.dt);
+                }
+        }
+        hp[r] = FzRunParams{(float)q.dt, (float)q.force_amp, q.force_k, q.dealias, (float)q.rot,
+                            (int)lround(q.force_k * l[0]), (int)lround(q.force_k * l[1]),
+                            (int)lround(q.force_k * l[2])};
     }
     if ((e = dev_malloc((void **)&f.etab, h.size() * sizeof(float))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(f.etab, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
+    if (!f.cube) {   // (m_i / l_i)^2 per axis in FP64, split into FP32 hi + lo
+        std::vector<float2> k2h;
+        const int Ms[3] = {f.Mx, f.My, f.Mz}, Ks[3] = {f.K, f.Ky, f.Kz};
+        for (int a = 0; a < 3; a++)
+            for (int i = 0; i < Ms[a]; i++) {
+                const int m = a < 2 && i > Ks[a] ? i - Ms[a] : i;
+                const double k = (double)m / l[a], v = k * k;
+                const float hi = (float)v;
+                k2h.push_back(make_float2(hi, (float)(v - (double)hi)));
+            }
+        if ((e = dev_malloc((void **)&f.k2tab, k2h.size() * sizeof(float2))) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(f.k2tab, k2h.data(), k2h.size() * sizeof(float2), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return e;
+    }
     if (f.mhd) {   // exp(-eta k^2 dt) per run
         for (long r = 0; r < nr; r++)
             for (int k2 = 0; k2 < f.nk2; k2++)
@@ -1048,8 +1201,8 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     if ((e = cudaMemsetAsync(f.counter, 0, nr * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if ((e = prepare_fused_kernels()) != cudaSuccess) return e;
     const int ct = default_ct(sizeof(float2), f.n);
-    for (int i = 0; i < 4; i++) f.sp[i] = PassCfg{f.plN, ct};
-    f.zc = PassCfg{f.plH, std::max(1, 192 / (6 * (f.n / 2 / f.plH.E)))};
+    for (int i = 0; i < 4; i++) f.sp[i] = PassCfg{pass_plan(f, i), ct};
+    f.zc = PassCfg{f.plH, std::max(1, 192 / (6 * (f.nz / 2 / f.plH.E)))};
     cudaError_t e2 = fused_autotune(f, s);
     if (e2 != cudaSuccess) return e2;
     // Diagnostic override of pass E + update: NS_FORCE_EU="off" (separate
@@ -1058,7 +1211,7 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
         int E = 0, ct = 0;
         FzsKernel z;
         if (strcmp(fe, "off") == 0) f.eu_E = f.eu_ct = 0;
-        else if (sscanf(fe, "%d,%d", &E, &ct) == 2 && fzeu_lookup(f.n, E, ct, &z)) {
+        else if (f.cube && sscanf(fe, "%d,%d", &E, &ct) == 2 && fzeu_lookup(f.n, E, ct, &z)) {
             f.eu_E = E;
             f.eu_ct = ct;
         }
@@ -1075,11 +1228,11 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
         int kind = -1, E = 0, tile = 0;
         PassCfg c;
         ZctKernel z;
-        if (sscanf(fz, "%d,%d,%d", &kind, &E, &tile) == 3 && cfg_from_triple(f.n, kind, E, tile, true, c)) {
-            const bool ok = kind == 2   ? zr_lookup(f.n, E, tile, &z)
-                            : kind == 1 ? zct_lookup(f.n, E, tile, &z)
+        if (sscanf(fz, "%d,%d,%d", &kind, &E, &tile) == 3 && cfg_from_triple(f.nz, kind, E, tile, true, c)) {
+            const bool ok = kind == 2   ? zr_lookup(f.nz, E, tile, &z)
+                            : kind == 1 ? zct_lookup(f.nz, E, tile, &z)
                                         : (kind == 0 && z_for(E) && tile >= 1 &&
-                                           6 * tile * (f.n / 2 / E) <= 256);
+                                           6 * tile * (f.nz / 2 / E) <= 256);
             if (ok) f.zc = c;
         }
     }
@@ -1087,24 +1240,25 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     // (kind 1 or 2) applies to each pass that has such a kernel compiled.
     if (const char *fs = getenv("NS_FORCE_STRIDED")) {
         int kind = -1, E = 0, ct = 0;
-        PassCfg c;
-        if (sscanf(fs, "%d,%d,%d", &kind, &E, &ct) == 3 && (kind == 1 || kind == 2) &&
-            cfg_from_triple(f.n, kind, E, ct, false, c))
+        if (sscanf(fs, "%d,%d,%d", &kind, &E, &ct) == 3 && (kind == 1 || kind == 2) && (kind == 1 || f.cube))
             for (int i = 0; i < 4; i++) {
                 FzsKernel z;
+                PassCfg ci;
+                if (!cfg_from_triple(pass_len(f, i), kind, E, ct, false, ci)) continue;
                 const bool ok = kind == 2 ? fzk_lookup(i, f.n, E, ct, &z)
-                                          : fzs_lookup(i < 2 ? i : 2, f.n, E, ct, &z);
-                if (ok) f.sp[i] = c;
+                                          : fzs_lookup(i < 2 ? i : 2, pass_len(f, i), E, ct, &z);
+                if (ok) f.sp[i] = ci;
             }
     }
     return cudaSuccess;
 }
 
 void fused_free(FusedRun &f) {
-    void *ps[] = {f.a, f.a1, f.nl, f.abuf, f.bbuf, f.etab, f.etab_b, f.rp, f.part, f.series, f.counter};
+    void *ps[] = {f.a, f.a1, f.nl, f.abuf, f.bbuf, f.etab, f.etab_b, f.rp, f.part, f.series, f.counter, f.k2tab};
     for (void *p : ps)
         if (p) dev_free(p);
     f.a = f.a1 = f.nl = f.abuf = f.bbuf = nullptr;
+    f.k2tab = nullptr;
     f.etab = f.etab_b = nullptr;
     f.rp = nullptr;
     f.part = f.series = nullptr;
@@ -1112,7 +1266,8 @@ void fused_free(FusedRun &f) {
 }
 
 static cudaError_t launch_update(FusedRun &f, const FzUpdate &u, cudaStream_t s) {
-    k_fused_update<<<dim3(f.nparts, f.nr), 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, f.rp, u, f.part);
+    if (f.cube) k_fused_update<false><<<dim3(f.nparts, f.nr), 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, f.rp, u, f.part);
+    else k_fused_update<true><<<dim3(f.nparts, f.nr), 256, 0, s>>>(f.a, f.a1, f.nl, f.etab, f.rp, u, f.part);
     return cudaGetLastError();
 }
 
@@ -1148,7 +1303,7 @@ static cudaError_t fused_step_mhd(FusedRun &f, int *flags, cudaStream_t s, Trace
         if ((e = NSK_TIMED(tr, "fused_D_y_forward", run_pass(f, 2, f.sp[2], Dm, s))) != cudaSuccess) return e;
         if ((e = NSK_TIMED(tr, "fused_E_x_forward", run_pass(f, 3, f.sp[3], Ep, s))) != cudaSuccess) return e;
         if ((e = NSK_TIMED(tr, "fused_E_x_forward", run_pass(f, 3, f.sp[3], Em, s))) != cudaSuccess) return e;
-        FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.M, f.nk2, f.nparts};
+        FzUpdate u = make_update(f, stage, f.nparts);
         if ((e = NSK_TIMED(tr, "fused_update", launch_update(f, u, s))) != cudaSuccess) return e;
         e = NSK_TIMED(tr, "fused_update_b",
                       (k_fused_update_b<<<dim3(f.nparts_upd, f.nr), 256, 0, s>>>(
@@ -1181,7 +1336,7 @@ cudaError_t fused_step(FusedRun &f, int *flags, cudaStream_t s, Tracer *tr) {
         }
         e = NSK_TIMED(tr, "fused_E_x_forward", run_pass(f, 3, f.sp[3], Ep, s));
         if (e != cudaSuccess) return e;
-        FzUpdate u{f.n, f.K, f.Mx, f.Mz, stage, f.M, f.nk2, f.nparts};
+        FzUpdate u = make_update(f, stage, f.nparts);
         e = NSK_TIMED(tr, "fused_update", launch_update(f, u, s));
         if (e != cudaSuccess) return e;
     }
@@ -1229,8 +1384,8 @@ int fused_describe(const FusedRun &f, char *out, int len) {
 
 cudaError_t fused_set_state(FusedRun &f, int run, int field, const double2 *src, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s) {
-    const int n = f.n, nh = n / 2 + 1;
-    const long plane = (long)n * nh, M = (long)n * plane;
+    const int n = f.n, nh = f.nz / 2 + 1;
+    const long plane = (long)f.ny * nh, M = (long)n * plane;
     const int pc = on_device ? n : (int)std::max<size_t>(1, staging_bytes / (plane * sizeof(double2)));
     if (field != 0 && !(field == 1 && f.mhd)) return cudaErrorInvalidValue;
     float2 *a = f.a + field * f.blk_s + (long)run * 3 * f.M;
@@ -1249,9 +1404,9 @@ cudaError_t fused_set_state(FusedRun &f, int run, int field, const double2 *src,
                         return e;
                     p = (const double2 *)staging;
                 }
-                const long work = (long)cnt * f.Mx * f.Mz;
-                k_fz_load<<<grid_of(work, 256, 152L * 16), 256, 0, s>>>(p, a + c * f.M, kx0, cnt, n, f.K,
-                                                                      f.Mx, f.Mz, dealias);
+                const long work = (long)cnt * f.My * f.Mz;
+                k_fz_load<<<grid_of(work, 256, 152L * 16), 256, 0, s>>>(p, a + c * f.M, kx0, cnt, half_geom(f),
+                                                                      dealias);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
                 if (!on_device && (e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
             }
@@ -1262,8 +1417,8 @@ cudaError_t fused_set_state(FusedRun &f, int run, int field, const double2 *src,
 
 cudaError_t fused_get_state(FusedRun &f, int run, int field, double2 *dst, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s) {
-    const int n = f.n, nh = n / 2 + 1;
-    const long plane = (long)n * nh, M = (long)n * plane;
+    const int n = f.n, nh = f.nz / 2 + 1;
+    const long plane = (long)f.ny * nh, M = (long)n * plane;
     const int pc = on_device ? n : (int)std::max<size_t>(1, staging_bytes / (plane * sizeof(double2)));
     if (field != 0 && !(field == 1 && f.mhd)) return cudaErrorInvalidValue;
     const float2 *a = f.a + field * f.blk_s + (long)run * 3 * f.M;
@@ -1274,8 +1429,8 @@ cudaError_t fused_get_state(FusedRun &f, int run, int field, double2 *dst, int o
             double2 *out = dst + c * M + (long)kx0 * plane;
             double2 *d = on_device ? out : (double2 *)staging;
             const long work = (long)cnt * plane;
-            k_fz_store<<<grid_of(work, 256, 152L * 16), 256, 0, s>>>(a + c * f.M, d, kx0, cnt, n, f.K,
-                                                                   f.Mx, f.Mz);
+            k_fz_store<double2><<<grid_of(work, 256, 152L * 16), 256, 0, s>>>(a + c * f.M, d, kx0, cnt,
+                                                                            half_geom(f));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if (!on_device) {
                 if ((e = cudaMemcpyAsync(out, staging, work * sizeof(double2), cudaMemcpyDeviceToHost,
@@ -1284,6 +1439,18 @@ cudaError_t fused_get_state(FusedRun &f, int run, int field, double2 *dst, int o
                 if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
             }
         }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t fused_expand(FusedRun &f, int run, int field, float2 *dst, cudaStream_t s) {
+    if (field != 0 && !(field == 1 && f.mhd)) return cudaErrorInvalidValue;
+    const float2 *a = f.a + field * f.blk_s + (long)run * 3 * f.M;
+    const long M = (long)f.n * f.ny * (f.nz / 2 + 1);
+    for (int c = 0; c < 3; c++) {
+        k_fz_store<float2><<<grid_of(M, 256, 152L * 16), 256, 0, s>>>(a + c * f.M, dst + c * M, 0, f.n, half_geom(f));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

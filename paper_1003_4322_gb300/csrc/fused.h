@@ -78,19 +78,29 @@ struct FzRunParams {
     float dt, force_amp;
     int force_k, dealias;
     float rot;   // rotation rate about z (Coriolis -2 rot z x u)
+    int mfx, mfy, mfz;   // grids and boxes: k_f as the grid index k_f l_i along each axis
 };
 
-// A group of nr runs of the fused form that share the grid size N; their
+// A group of nr runs of the fused form that share the grid (and box); their
 // buffers are contiguous ([run][...]) so that one launch per pass (grid y =
 // run) advances all of them.  Compact state layout [c][ikx][iky][kz] with
-// ikx, iky in [0, Mx) (index k for k >= 0, k + Mx for k < 0) and kz in
-// [0, Mz): only the modes the cubic 2/3 rule keeps, |kx|, |ky|, kz <= K.
+// ikx in [0, Mx), iky in [0, My) (index m for m >= 0, m + Mx or m + My for
+// m < 0) and kz in [0, Mz): only the modes the 2/3 rule keeps along every
+// axis, |m_x| <= K, |m_y| <= Ky, m_z <= Kz.  On the cube N_x = N_y = N_z = n,
+// Ky = Kz = K and My = Mx.
 struct FusedRun {
     int nr = 0;
     std::vector<ns_run_params> p;   // per run
-    int n = 0, K = 0, Mx = 0, Mz = 0;
-    long M = 0;                  // compact modes per component, Mx * Mx * Mz
-    Plan plN{}, plH{};           // default plans of length n (x, y) and n/2 (z)
+    int n = 0, K = 0, Mx = 0, Mz = 0;   // n = N_x; K, Mx: along x
+    int ny = 0, nz = 0, Ky = 0, Kz = 0, My = 0;
+    bool cube = true;            // N_x = N_y = N_z on the unit box
+    bool unit = true;            // the unit box: integer wavenumbers, factor table by k^2
+    float sx = 1.f, sy = 1.f, sz = 1.f;   // wavenumber per grid index, 1 / l_i
+    long D = 0, qx = 0, qy = 0, qz = 0;   // lcm(N_i) and D / N_i (the sphere in integers)
+    long M = 0;                  // compact modes per component, Mx * My * Mz
+    Plan plN{}, plH{};           // default plans of length n (x) and N_z / 2 (z)
+    Plan plY{};                  // and of length N_y (y)
+    const float2 *twy = nullptr, *twz = nullptr;   // tables of lengths N_y, N_z (tw: N_x)
     PassCfg sp[4];               // passes A, B, D, E (chosen by the autotuner)
     PassCfg zc;                  // pass C
     int eu_E = 0, eu_ct = 0;     // pass E fused with the update (fused_keu.cu); 0: separate kernels
@@ -111,7 +121,9 @@ struct FusedRun {
     float2 *bbuf = nullptr;      // pass B output (6 fields), pass C in place (3)     [nr][sB]
     long sA = 0, sB = 0;         // per-run elements of abuf and bbuf
     float *etab = nullptr;       // exp(-nu k^2 dt) by integer k^2 <= 3 K^2            [nr][nk2]
+                                 // (a grid or box: per axis by compact index,        [nr][Mx + My + Mz])
     int nk2 = 0;
+    float2 *k2tab = nullptr;     // a grid or box: (m_i / l_i)^2 as FP32 pairs hi + lo, [Mx + My + Mz]
     FzRunParams *rp = nullptr;   // [nr]
     int nparts = 0;              // energy partial sums per run (update kernel blocks)
     double *part = nullptr;      // [nr][nparts][2]
@@ -122,8 +134,17 @@ struct FusedRun {
 
 bool fused_enabled();
 // Allocate a group for runs (all of the same N) and tune its passes.
+// tw, twy, twz: the tables exp(-2 pi i t / N_i), t < N_i, of the three axes
+// (the same table thrice on the cube).
 cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, const float2 *tw,
-                        int series_cap, cudaStream_t s);
+                        const float2 *twy, const float2 *twz, int series_cap, cudaStream_t s);
+// Whether the fused form covers a run on a grid of N_x x N_y x N_z points on
+// the box of sides 2 pi l_i (the cube always; a grid or box for the
+// Navier-Stokes equations with the cubic or spherical 2/3 rule).
+bool fused_grid_supported(const ns_run_params &p);
+// The full FP32 half layout [3][N_x][N_y][N_z/2+1] of one run's field from
+// the compact state (zeros outside the kept modes), into dst.
+cudaError_t fused_expand(FusedRun &f, int run, int field, float2 *dst, cudaStream_t s);
 void fused_free(FusedRun &f);
 cudaError_t fused_set_state(FusedRun &f, int run, int field, const double2 *src, int on_device, void *staging,
                             size_t staging_bytes, cudaStream_t s);

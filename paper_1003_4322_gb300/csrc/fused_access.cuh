@@ -23,9 +23,14 @@ struct FzPass {
     long ifs, irs;       // input field / row strides (complex elements)
     long ofs, ors, obs;  // output field / row strides; outer stride of a column
     int nfields;         // output fields handled by the grid
-    int Mz, K, Mx;
+    int Mz, K, Mx;       // kept kz; kept |k| and compact rows along the transform axis
     long irun, orun;     // input / output strides between the runs of a group (grid y)
     long ibs;            // input outer stride of a column (input element: ou * ibs + iz)
+    // pass A of a grid or box: the compaction of the outer (y) index and the
+    // wavenumber per grid index along x, y, z (1 / l_i) for the curl; Mo = 0:
+    // the outer index is compacted like the rows (K, Mx) and the scales are 1
+    int Ko = 0, Mo = 0;
+    float sx = 1.f, sy = 1.f, sz = 1.f;
 };
 
 // One column of a strided pass: grid x is fields x tiles (field fastest),
@@ -58,9 +63,14 @@ template <bool IN_C, bool OUT_C, bool CURL> struct FzColumn {
         } else {
             const float2 *b = in + r * ps.irs + ou * ps.ibs + iz;
             if (f < 3) return b[f * ps.ifs];
-            const float kx = (float)fz_full_signed(e, n);
-            const float ky = (float)fz_compact_signed((int)ou, ps.Mx, ps.K);
-            const float kz = (float)iz;
+            float kx = (float)fz_full_signed(e, n);
+            float ky = (float)fz_compact_signed((int)ou, ps.Mx, ps.K);
+            float kz = (float)iz;
+            if (ps.Mo) {   // a grid or a box
+                kx *= ps.sx;
+                ky = (float)fz_compact_signed((int)ou, ps.Mo, ps.Ko) * ps.sy;
+                kz *= ps.sz;
+            }
             float2 p, q;
             float sp, sq;
             if (f == 3) { p = b[2 * ps.ifs]; sp = ky; q = b[ps.ifs]; sq = kz; }   // i(ky az - kz ay)

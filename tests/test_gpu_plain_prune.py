@@ -21,7 +21,7 @@ CASES = [
     ("fp64", dict(n=24, nu=0.02, eta=0.03, dt=2e-3, mhd=1)),
     ("fp64", dict(n=24, ny=16, nz=12, lx=1.5, ly=1.0, lz=0.75, nu=0.01, dt=2e-3, rot=1.5, dealias=1)),
     ("fp64", dict(n=12, ny=36, nz=24, nu=0.02, dt=2e-3, force_amp=0.5, force_k=3, dealias=2)),
-    ("fp32", dict(n=12, ny=36, nz=24, nu=0.02, dt=2e-3, force_amp=0.5, force_k=3)),
+    ("fp32", dict(n=12, ny=36, nz=24, nu=0.02, dt=2e-3, force_amp=0.5, force_k=3, dealias=2)),
     ("fp32", dict(n=16, ny=12, nz=24, lx=1.0, ly=0.75, lz=1.5, nu=0.02, eta=0.03, dt=2e-3, mhd=1)),
 ]
 
