@@ -39,11 +39,12 @@
  *   a1 = E (a + dt N(a)),  a_next = E a / 2 + (a1 + dt N(a1)) / 2.
  * Supported N: 2^a 3^b with N >= 8, N even and N <= 1024; other N give
  *   NS_ERR_UNSUPPORTED_N.
- * Precision: NS_FP64 is the plain form (unfused, unpruned, FP64
- *   throughout).  NS_FP32 is the fused form (pruned FP32 transforms and
- *   nonlinear term); its twiddle and integrating-factor tables are generated
- *   in FP64 and rounded once, and its energy, enstrophy and spectrum sums
- *   accumulate in FP64.
+ * Precision: NS_FP64 is the plain form (unfused, FP64 throughout, in the
+ *   full half layout; its transforms skip the lines the dealiasing rule
+ *   zeroes or discards, with the same result bit for bit).  NS_FP32 is the
+ *   fused form (pruned FP32 transforms and nonlinear term); its twiddle and
+ *   integrating-factor tables are generated in FP64 and rounded once, and its
+ *   energy, enstrophy and spectrum sums accumulate in FP64.
  *
  * Ownership: the caller owns every pointer it passes; the context owns its
  *   internal device buffers and frees them in ns_destroy.  Nothing is kept
@@ -115,9 +116,11 @@ typedef struct {
                           context uses the plain FP32 form.  0:
                           Navier-Stokes. */
     int ny, nz;        /* grid points along y and z (0: n), each 2^a 3^b,
-                          even, >= 8; a grid other than n^3, or a box side
-                          other than 2 pi, makes the context use the plain
-                          form in either precision */
+                          even, >= 8.  On a grid other than n^3 or a box
+                          side other than 2 pi, FP32 Navier-Stokes runs with
+                          dealias 0 or 1 keep the fused form; MHD and
+                          dealias 2 there make the context use the plain
+                          form */
     double lx, ly, lz; /* box sides in units of 2 pi (0: 1); with forcing,
                           every force_k * l_i must be an integer (the ABC
                           field periodic on the box) */
