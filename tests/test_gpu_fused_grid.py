@@ -112,3 +112,32 @@ def test_fused_grid_group_equals_runs_alone(ns):
         together = [s.get_state(run=i) for i in range(len(runs))]
     for i, (a, b) in enumerate(zip(alone, together)):
         assert np.array_equal(a, b), i
+
+
+def test_fused_cube_and_grids_in_one_context(ns):
+    """A cube and two grids in one FP32 context: three groups of the fused
+    form on concurrent branches of one CUDA graph, each bitwise equal to its
+    run done alone."""
+    from paper_1003_4322_gb300 import _native as nat
+    from paper_1003_4322_gb300.solver import Solver
+    runs = [dict(n=64, nu=0.01, dt=1e-3, force_amp=0.5, force_k=2),
+            dict(n=64, ny=48, nz=96, lx=1.0, ly=0.75, lz=1.5, nu=0.02, dt=1e-3, rot=0.5),
+            dict(n=96, ny=96, nz=48, lz=0.5, nu=5e-3, dt=1e-3, force_amp=0.3, force_k=2, dealias=1)]
+    starts = [inputs.random_solenoidal_grid(_dims(r), _box(r), 0.5, 4.0, 1.0, seed=400 + i,
+                                           dealias=r.get("dealias", 0)) for i, r in enumerate(runs)]
+    alone = []
+    for r, a in zip(runs, starts):
+        with Solver([r], prec="fp32") as s:
+            s.set_state(a)
+            s.step(3)
+            alone.append(s.get_state())
+    with Solver(runs, prec="fp32") as s:
+        for i in range(len(runs)):
+            d = nat.ns_describe_run(s.ctx, i)
+            assert d["form"] == "fused FP32" and d["grid"] == list(_dims(runs[i])), d
+        for i, a in enumerate(starts):
+            s.set_state(a, run=i)
+        s.step(3)
+        together = [s.get_state(run=i) for i in range(len(runs))]
+    for i, (a, b) in enumerate(zip(alone, together)):
+        assert np.array_equal(a, b), i
