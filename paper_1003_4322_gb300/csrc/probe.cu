@@ -1,5 +1,5 @@
 // probe.cu -- ns_alu_peak: the measured FMA rate of the device, the ALU roof
-// against which the plain FP64 form's transforms are judged.
+// of the plain FP64 form's transforms.
 //
 // Every thread runs CH independent FMA chains x <- x a + b for a given number
 // of iterations, so that issue, not latency, bounds the kernel; the grid fills
