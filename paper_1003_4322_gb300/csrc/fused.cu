@@ -374,15 +374,22 @@ static bool fzs_lookup(int which, int N, int E, int CT, FzsKernel *o) {
                       : fzs_lookup_DE(N, E, CT, o);
 }
 
-// Constant-geometry kernel of pass 0..3 (A, B, D, E).
-static bool fzk_lookup(int pass, int N, int E, int CT, FzsKernel *o) {
+// Constant-geometry kernel of pass 0..3 (A, B, D, E) on the grid nx x ny x nz.
+static bool fzk_lookup(int pass, int nx, int ny, int nz, int E, int CT, FzsKernel *o) {
     switch (pass) {
-    case 0: return fzk_lookup_A(N, E, CT, o);
-    case 1: return fzk_lookup_B(N, E, CT, o);
-    case 2: return fzk_lookup_D(N, E, CT, o);
-    case 3: return fzk_lookup_E(N, E, CT, o);
+    case 0: return fzk_lookup_A(nx, ny, nz, E, CT, o);
+    case 1: return fzk_lookup_B(nx, ny, nz, E, CT, o);
+    case 2: return fzk_lookup_D(nx, ny, nz, E, CT, o);
+    case 3: return fzk_lookup_E(nx, ny, nz, E, CT, o);
     }
     return false;
+}
+
+// The same for a run: the kernels of a cube keep the unit box, so a cube on
+// another box has none.
+static bool fzk_for(const FusedRun &f, int pass, int E, int CT, FzsKernel *o) {
+    if (!f.cube && f.n == f.ny && f.n == f.nz) return false;
+    return fzk_lookup(pass, f.n, f.ny, f.nz, E, CT, o);
 }
 
 cudaError_t prepare_fused_kernels() {
@@ -424,12 +431,23 @@ cudaError_t prepare_fused_kernels() {
                 }
                 for (int pass = 0; pass < 5; pass++) {
                     FzsKernel z;
-                    if (pass < 4 ? fzk_lookup(pass, N, E, ct, &z) : fzeu_lookup(N, E, ct, &z)) {
+                    if (pass < 4 ? fzk_lookup(pass, N, N, N, E, ct, &z) : fzeu_lookup(N, E, ct, &z)) {
                         cudaError_t e = allow_smem(z.k, 48 * 1024 + 1);
                         if (e != cudaSuccess) return e;
                     }
                 }
             }
+#define NSK_CASE(nx_, ny_, nz_, e_, ct_) {nx_, ny_, nz_, e_, ct_},
+    static const int grids[][5] = {NSK_FZK_GRIDS(NSK_CASE)};
+#undef NSK_CASE
+    for (const auto &g : grids)
+        for (int pass = 0; pass < 4; pass++) {
+            FzsKernel z;
+            if (fzk_lookup(pass, g[0], g[1], g[2], g[3], g[4], &z)) {
+                cudaError_t e = allow_smem(z.k, 48 * 1024 + 1);
+                if (e != cudaSuccess) return e;
+            }
+        }
     const int Es[] = {4, 6, 8, 9, 12, 16};
     for (int E : Es) {
         const void *ks[] = {strided_for<+1, true, false, true>(E), strided_for<+1, true, false, false>(E),
@@ -607,15 +625,16 @@ static cudaError_t run_pass_ct(FusedRun &f, int pass, const PassCfg &cfg, const 
 
 static cudaError_t run_pass_k(FusedRun &f, int pass, const PassCfg &cfg, const FzPass &ps, cudaStream_t s) {
     FzsKernel z;
-    if (!f.cube || !fzk_lookup(pass, f.n, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
+    if (!fzk_for(f, pass, cfg.pl.E, cfg.ct, &z)) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(z.k, z.smem);
     if (e != cudaSuccess) return e;
     const long tiles = (ps.ncols + cfg.ct - 1) / cfg.ct;
     const long blocks = tiles * ps.nfields;
     if (blocks > 0x7fffffffL) return cudaErrorInvalidValue;
-    const float2 *in = ps.in, *tw = f.tw;
+    const float2 *in = ps.in, *tw = pass_tw(f, pass);
     float2 *out = ps.out;
-    void *args[] = {(void *)&in, (void *)&out, (void *)&tw};
+    float3 sc = make_float3(f.sx, f.sy, f.sz);
+    void *args[] = {(void *)&in, (void *)&out, (void *)&tw, (void *)&sc};
     return cudaLaunchKernel(z.k, dim3((unsigned)blocks, (unsigned)f.nr), dim3(z.threads), args, z.smem, s);
 }
 
@@ -961,11 +980,11 @@ static cudaError_t fused_autotune(FusedRun &f, cudaStream_t s) {
         };
         const int Es[] = {8, 12, 16, 32};
         const int len = pass_len(f, i);
-        for (int kind = f.cube ? 2 : 1; kind >= 1; kind--)   // constant-geometry kernels: cubes only
+        for (int kind = 2; kind >= 1; kind--)
             for (int E : Es)
                 for (int ct = 8; ct <= 16; ct *= 2) {
                     FzsKernel z;
-                    if (kind == 1 ? !fzs_lookup(which[i], len, E, ct, &z) : !fzk_lookup(i, f.n, E, ct, &z))
+                    if (kind == 1 ? !fzs_lookup(which[i], len, E, ct, &z) : !fzk_for(f, i, E, ct, &z))
                         continue;
                     PassCfg cfg{pass_plan(f, i), ct, kind};
                     cfg.pl.E = E;
@@ -1240,12 +1259,12 @@ cudaError_t fused_alloc(FusedRun &f, const std::vector<ns_run_params> &runs, con
     // (kind 1 or 2) applies to each pass that has such a kernel compiled.
     if (const char *fs = getenv("NS_FORCE_STRIDED")) {
         int kind = -1, E = 0, ct = 0;
-        if (sscanf(fs, "%d,%d,%d", &kind, &E, &ct) == 3 && (kind == 1 || kind == 2) && (kind == 1 || f.cube))
+        if (sscanf(fs, "%d,%d,%d", &kind, &E, &ct) == 3 && (kind == 1 || kind == 2))
             for (int i = 0; i < 4; i++) {
                 FzsKernel z;
                 PassCfg ci;
                 if (!cfg_from_triple(pass_len(f, i), kind, E, ct, false, ci)) continue;
-                const bool ok = kind == 2 ? fzk_lookup(i, f.n, E, ct, &z)
+                const bool ok = kind == 2 ? fzk_for(f, i, E, ct, &z)
                                           : fzs_lookup(i < 2 ? i : 2, pass_len(f, i), E, ct, &z);
                 if (ok) f.sp[i] = ci;
             }

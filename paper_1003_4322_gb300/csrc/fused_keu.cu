@@ -52,14 +52,14 @@ k_fzeu(const float2 *__restrict__ din, float2 *__restrict__ a, float2 *__restric
     const bool two = u.stage == 2;
     float2 *dst = two ? a : a1;
     const int iky = cc / G::Mz, kz = cc - (cc / G::Mz) * G::Mz;
-    const int ky = iky <= G::K ? iky : iky - G::Mx;
+    const int ky = iky <= G::Ky ? iky : iky - G::My;
     DfAcc e_acc, o_acc;
 #pragma unroll
     for (int j = 0; j < E; j++) {
         const int e = slot + j * T;
-        const int ikx = FzColK<N, FZ_E>::compact(e);
+        const int ikx = FzColK<N, N, N, FZ_E>::compact(e);
         if (!valid || ikx < 0) continue;
-        const long m = (long)ikx * G::MxMz + cc;
+        const long m = (long)ikx * G::MyMz + cc;
         const float2 z = make_float2(0.f, 0.f);
         const float2 b0 = a[m], b1 = a[M + m], b2 = a[2 * M + m];
         const float2 c0 = two ? a1[m] : z, c1 = two ? a1[M + m] : z, c2 = two ? a1[2 * M + m] : z;

@@ -141,3 +141,43 @@ def test_fused_cube_and_grids_in_one_context(ns):
         together = [s.get_state(run=i) for i in range(len(runs))]
     for i, (a, b) in enumerate(zip(alone, together)):
         assert np.array_equal(a, b), i
+
+
+def _passes(desc):
+    return {k: v for k, v in desc["passes"].items() if k in ("A_x_inverse_curl", "B_y_inverse",
+                                                             "D_y_forward", "E_x_forward")}
+
+
+@pytest.mark.parametrize("dims,E,ct,steps,oracle_check", [((96, 96, 48), 12, 8, 3, True),
+                                                        ((96, 96, 48), 12, 16, 3, True),
+                                                        ((512, 512, 256), 16, 8, 2, False),
+                                                        ((512, 512, 256), 32, 16, 2, False)])
+def test_constant_geometry_grid_kernels(ns, dims, E, ct, steps, oracle_check, monkeypatch):
+    """Passes A, B, D, E on the kernels with the grid's whole geometry fixed
+    at compile time (the box (2 pi, 2 pi, pi) of the 512 x 512 x 256
+    workload, and the same box at 96 x 96 x 48), forced through
+    NS_FORCE_STRIDED, against the runtime-stride kernels of the same length
+    and shape (the same FFT and curl arithmetic) and, on the small grid,
+    against the FP64 oracle."""
+    from paper_1003_4322_gb300 import _native as nat
+    from paper_1003_4322_gb300.solver import Solver
+    nx, ny, nz = dims
+    run = dict(n=nx, ny=ny, nz=nz, lz=0.5, nu=5e-3, dt=1e-3, force_amp=0.3, force_k=2)
+    a0 = inputs.random_solenoidal_grid(dims, _box(run), 0.5, 4.0, 1.0, seed=500)
+    got = {}
+    for kind, name in ((2, "constant geometry"), (1, "compile-time length")):
+        monkeypatch.setenv("NS_FORCE_STRIDED", f"{kind},{E},{ct}")
+        with Solver([run], prec="fp32") as s:
+            passes = _passes(nat.ns_describe_run(s.ctx, 0))
+            assert all(p["kernel"] == name and p["E"] == E and p["cols_per_cta"] == ct
+                       for p in passes.values()), passes
+            s.set_state(a0)
+            s.step(steps)
+            got[kind] = s.get_state()
+    d = rel_l2(got[2], got[1])
+    print(f"grid {dims} E={E} ct={ct}: constant geometry vs runtime strides rel-L2 {d:.2e}, "
+          f"bitwise {np.array_equal(got[2], got[1])}")
+    assert np.abs(got[2]).max() > 0 and d < 1e-6
+    if oracle_check:
+        ref = oracle.step(a0, _params(run), steps)
+        assert rel_l2(got[2], ref) < TOL
