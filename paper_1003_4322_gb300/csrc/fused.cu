@@ -912,8 +912,7 @@ static void plan_cache_write(const std::map<int, TunedCfgs> &cache) {
 // Choose, per pass, the kernel (runtime or compile-time length), the radix
 // split E and the tile (columns per CTA for the strided passes, lines or warps
 // per CTA for pass C) that run fastest on this run's own buffers; results
-// are kept per grid (N_x, N_y, N_z) for the life of the process, and those of
-// cubes also in the plan cache file.
+// are kept per N for the life of the process (and in the plan cache file).
 // The final choice of a sweep.  The sweep times every candidate over a few
 // launches; candidates within a few percent of each other are then ordered
 // by noise as much as by speed.  So the three fastest are timed again over
