@@ -81,6 +81,38 @@ def test_fused_pass_bytes_follow_the_pruned_shapes(n):
         assert got == modes * c64, (name, got, modes * c64)
 
 
+@pytest.mark.parametrize("dims", [(512, 512, 256), (64, 96, 128), (48, 24, 36)])
+def test_fused_pass_bytes_on_grids(dims):
+    """On a grid of N_x x N_y x N_z points the kept wavenumbers are per axis,
+    K_i the largest with 3 K_i < N_i: the compact state [3][2K_x+1][2K_y+1][K_z+1],
+    pass A/D fields [.][2K_y+1][N_x][K_z+1], pass B/C fields [.][N_y][N_x][K_z+1].
+    The transforms run along x in passes A and E (2K_y+1 by K_z+1 columns)
+    and along y in B and D (N_x by K_z+1 columns)."""
+    nx, ny, nz = dims
+    Kx, Ky, Kz = ((m - 1) // 3 for m in dims)
+    assert all(3 * k < m <= 3 * k + 3 for k, m in zip((Kx, Ky, Kz), dims))
+    c64 = np.dtype(np.complex64).itemsize
+    S = (2 * Kx + 1) * (2 * Ky + 1) * (Kz + 1)
+    Ax = (2 * Ky + 1) * nx * (Kz + 1)
+    Bx = ny * nx * (Kz + 1)
+    want = {
+        "fused_A_x_inverse_curl": (3 * S + 6 * Ax, 6 * (2 * Ky + 1) * (Kz + 1), nx),
+        "fused_B_y_inverse": (6 * Ax + 6 * Bx, 6 * nx * (Kz + 1), ny),
+        "fused_D_y_forward": (3 * Bx + 3 * Ax, 3 * nx * (Kz + 1), ny),
+        "fused_E_x_forward": (3 * Ax + 3 * S, 3 * (2 * Ky + 1) * (Kz + 1), nx),
+        "fused_C_z_nonlinear": (9 * Bx, None, None),
+    }
+    for name, (modes, lines, length) in want.items():
+        got, flops = bench.kernel_model(name, dims, "fp32")
+        assert got == modes * c64, (name, got, modes * c64)
+        if lines is not None:   # 5 L log2 L per complex line of length L
+            assert flops == pytest.approx(lines * 5 * length * np.log2(length)), name
+    # the 512 x 512 x 256 box: K = (170, 170, 85), pass C moves 1,623,195,648 bytes
+    if dims == (512, 512, 256):
+        assert (Kx, Ky, Kz) == (170, 170, 85)
+        assert bench.kernel_model("fused_C_z_nonlinear", dims, "fp32")[0] == 1623195648
+
+
 def test_roofline_arithmetic_on_a_synthetic_census():
     peaks = {"hbm_gbs": 6000.0, "sm_max_mhz": 2000.0, "source": "measured"}
     w = {"n": 256, "name": "none"}
